@@ -1,0 +1,243 @@
+/*
+ * oracle.c -- plain CPU reference of the ARTS single-pulse search hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the correctness oracle: tests, the
+ * package smoke check and the benchmark's CPU-baseline leg may call it; the
+ * product path never does.  It shares no code, header, table or constant
+ * generator with the CUDA library.
+ *
+ * Everything is written as the definitions of the paper's AMBER stages
+ * (Sec. "AMBER": downsampling, dedispersion, integration, S/N evaluation,
+ * candidate selection), in the simplest loops that compute them:
+ *   - delays in FP64 from the cold-plasma dispersion law, rounded half away
+ *     from zero (llround), in units of D * t_samp;
+ *   - downsampling = exact integer sum of D consecutive samples;
+ *   - brute-force dedispersion with synthesized-beam gather, exact int64 sums;
+ *   - per-series mean / population standard deviation, two-pass FP64;
+ *   - sliding boxcar of width w (exact int64 sum), S/N = (B - w mu)/(sigma sqrt w);
+ *   - candidate when S/N strictly exceeds the threshold ("exceeds", Sec.
+ *     "Candidate selection"); one candidate per (SB, DM, width, time), no
+ *     clustering.
+ * Where the paper is silent (constant, rounding, statistics, boxcar form)
+ * the reading taken is stated at the function that applies it.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -fPIC -shared (see build.py).
+ * -ffp-contract=off keeps every FP64 expression in the written order.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Dispersion constant in s MHz^2 / (pc cm^-3).  The paper quotes no value;
+ * this is the standard cold-plasma constant 1/(2.41e-4). */
+#define ORACLE_KDM 4148.808
+
+void oracle_set_threads(int32_t n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int32_t oracle_get_threads(void) {
+#ifdef _OPENMP
+    return (int32_t)omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Sec. "Dedispersion" (brute-force incoherent dedispersion): channel c of
+ * trial DM_i is delayed, relative to the highest channel, by
+ *     K_DM * DM_i * (f_c^-2 - f_top^-2) / (D * t_samp)   samples,
+ * rounded half away from zero.  DM_i = dm0 + i * ddm is formed afresh for
+ * each i.  Returns the largest delay; *n_near_tie counts real-valued delays
+ * whose fractional part lies within 1e-9 of one half (rounding there is
+ * sensitive to the last bit of the FP64 evaluation). */
+int64_t oracle_delays(int32_t n_chan, const double* freq_mhz, double t_samp_s,
+                      double dm0, double ddm, int32_t n_dm, int32_t downsamp,
+                      int64_t* out, int64_t* n_near_tie) {
+    double f_top = freq_mhz[0];
+    for (int32_t c = 1; c < n_chan; c++)
+        if (freq_mhz[c] > f_top) f_top = freq_mhz[c];
+    int64_t dmax = 0, ties = 0;
+    for (int32_t i = 0; i < n_dm; i++) {
+        double dm = dm0 + (double)i * ddm;
+        for (int32_t c = 0; c < n_chan; c++) {
+            double f = freq_mhz[c];
+            double x = ((ORACLE_KDM * dm) * (1.0 / (f * f) - 1.0 / (f_top * f_top)))
+                       / ((double)downsamp * t_samp_s);
+            double frac = x - floor(x);
+            if (fabs(frac - 0.5) < 1e-9) ties++;
+            int64_t d = (int64_t)llround(x);
+            out[(int64_t)i * n_chan + c] = d;
+            if (d > dmax) dmax = d;
+        }
+    }
+    if (n_near_tie) *n_near_tie = ties;
+    return dmax;
+}
+
+/* Sec. "Downsampling": y[r][j] = sum_{k<D} x[r][j*D + k], j < floor(n_in/D). */
+void oracle_downsample(const uint8_t* x, int64_t rows, int64_t n_in, int64_t pitch,
+                       int32_t downsamp, uint32_t* y) {
+    int64_t n_y = n_in / downsamp;
+    for (int64_t r = 0; r < rows; r++)
+        for (int64_t j = 0; j < n_y; j++) {
+            uint32_t s = 0;
+            for (int32_t k = 0; k < downsamp; k++) s += x[r * pitch + j * downsamp + k];
+            y[r * n_y + j] = s;
+        }
+}
+
+/* Sec. "Dedispersion" with the synthesized-beam formation of Sec.
+ * "Hierarchical beam forming": SB s takes channel c from TAB sb_map[s][c];
+ *     S[s][i][t] = sum_c y[sb_map[s][c]][c][t + d[i][c]],  t < n_out.
+ * One series, plain loops, exact int64. */
+static void dedisperse_one(const uint32_t* y, int32_t n_chan, int64_t n_y,
+                           const int32_t* sb_row, const int64_t* d_row, int64_t n_out,
+                           int64_t* acc) {
+    for (int64_t t = 0; t < n_out; t++) acc[t] = 0;
+    for (int32_t c = 0; c < n_chan; c++) {
+        const uint32_t* row = y + ((int64_t)sb_row[c] * n_chan + c) * n_y;
+        int64_t off = d_row[c];
+        for (int64_t t = 0; t < n_out; t++) acc[t] += (int64_t)row[t + off];
+    }
+}
+
+/* Full dedispersion for all (SB, DM) pairs; the caller guarantees
+ * n_out + max delay <= n_y. */
+void oracle_dedisperse(const uint32_t* y, int32_t n_tab, int32_t n_chan, int64_t n_y,
+                       const int32_t* sb_map, int32_t n_sb, const int64_t* delays,
+                       int32_t n_dm, int64_t n_out, int64_t* series) {
+    (void)n_tab;
+    int64_t n_series = (int64_t)n_sb * n_dm;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t q = 0; q < n_series; q++) {
+        int32_t s = (int32_t)(q / n_dm), i = (int32_t)(q % n_dm);
+        dedisperse_one(y, n_chan, n_y, sb_map + (int64_t)s * n_chan,
+                       delays + (int64_t)i * n_chan, n_out, series + q * n_out);
+    }
+}
+
+/* Sec. "S/N evaluation" (method left open by the paper): mean and population
+ * standard deviation of the series over its own n samples, two-pass FP64. */
+void oracle_stats(const int64_t* s, int64_t n, double* mean, double* std) {
+    int64_t sum = 0;
+    for (int64_t t = 0; t < n; t++) sum += s[t];
+    double mu = (double)sum / (double)n;
+    double ss = 0.0;
+    for (int64_t t = 0; t < n; t++) {
+        double d = (double)s[t] - mu;
+        ss += d * d;
+    }
+    *mean = mu;
+    *std = sqrt(ss / (double)n);
+}
+
+/* Sec. "Integration" + "S/N evaluation": sliding boxcar of width w,
+ * B(t) = sum_{k<w} s[t+k] for t in [0, n-w], and
+ * snr(t) = (B(t) - w*mean) / (std * sqrt(w)).  Writes n-w+1 values. */
+void oracle_boxcar_snr(const int64_t* s, int64_t n, int32_t w, double mean, double std,
+                       double* snr) {
+    double norm = std * sqrt((double)w);
+    for (int64_t t = 0; t + w <= n; t++) {
+        int64_t b = 0;
+        for (int32_t k = 0; k < w; k++) b += s[t + k];
+        snr[t] = ((double)b - (double)w * mean) / norm;
+    }
+}
+
+typedef struct {
+    int32_t sb, dm_index, downsamp, width_native;
+    int64_t t_native;
+    double dm, snr;
+} oracle_cand; /* 40 bytes */
+
+/* The whole hot path for one chunk: for every range r of the DM plan,
+ * downsample by D_r, dedisperse every (SB, DM) pair, compute the series
+ * statistics, run every boxcar width and keep (Sec. "Candidate selection")
+ * each (sb, dm, width, t) whose S/N strictly exceeds thr.  Widths are in
+ * range samples; a candidate reports width * D_r and t * D_r + t_offset in
+ * native samples.  dm_index is global over the concatenated ranges.
+ * Series with zero standard deviation emit nothing.
+ * series_or_null, if given, receives int64 series per range, packed
+ * [range][sb][dm][floor(n_out/D_r)].  Returns the total candidate count;
+ * only the first cap are stored (order unspecified).  Returns -1 on a short
+ * input (n_in < D_r * (floor(n_out/D_r) + max delay_r) for some r) and -2
+ * on allocation failure. */
+int64_t oracle_search(const uint8_t* x, int32_t n_tab, int32_t n_chan, int64_t n_in,
+                      int64_t pitch, const int32_t* sb_map, int32_t n_sb,
+                      const double* freq_mhz, double t_samp_s, int32_t n_range,
+                      const double* dm0, const double* ddm, const int32_t* n_dm,
+                      const int32_t* downsamp, const int32_t* n_width,
+                      const int32_t* widths, double thr, int64_t n_out,
+                      int64_t t_offset_native, oracle_cand* cands, int64_t cap,
+                      int64_t* series_or_null) {
+    int64_t count = 0;
+    int32_t dm_base = 0, w_base = 0;
+    int64_t series_base = 0;
+    for (int32_t r = 0; r < n_range; r++) {
+        int32_t D = downsamp[r];
+        int64_t n_y = n_in / D, n_r = n_out / D;
+        int64_t* d = (int64_t*)malloc(sizeof(int64_t) * (size_t)n_dm[r] * (size_t)n_chan);
+        uint32_t* y = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)n_tab * (size_t)n_chan * (size_t)n_y);
+        if (!d || !y) { free(d); free(y); return -2; }
+        int64_t dmax = oracle_delays(n_chan, freq_mhz, t_samp_s, dm0[r], ddm[r], n_dm[r], D, d, NULL);
+        if (n_r + dmax > n_y) { free(d); free(y); return -1; }
+        oracle_downsample(x, (int64_t)n_tab * n_chan, n_in, pitch, D, y);
+        int64_t n_series = (int64_t)n_sb * n_dm[r];
+#pragma omp parallel
+        {
+            int64_t* acc = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_r > 0 ? n_r : 1));
+            double* snr = (double*)malloc(sizeof(double) * (size_t)(n_r > 0 ? n_r : 1));
+#pragma omp for schedule(dynamic, 1)
+            for (int64_t q = 0; q < n_series; q++) {
+                int32_t s = (int32_t)(q / n_dm[r]), i = (int32_t)(q % n_dm[r]);
+                dedisperse_one(y, n_chan, n_y, sb_map + (int64_t)s * n_chan,
+                               d + (int64_t)i * n_chan, n_r, acc);
+                if (series_or_null)
+                    memcpy(series_or_null + series_base + q * n_r, acc, sizeof(int64_t) * (size_t)n_r);
+                if (n_r == 0) continue;
+                double mu, sd;
+                oracle_stats(acc, n_r, &mu, &sd);
+                if (!(sd > 0.0)) continue;
+                for (int32_t k = 0; k < n_width[r]; k++) {
+                    int32_t w = widths[w_base + k];
+                    if (w > n_r) continue;
+                    oracle_boxcar_snr(acc, n_r, w, mu, sd, snr);
+                    for (int64_t t = 0; t + w <= n_r; t++) {
+                        if (snr[t] > thr) {
+                            int64_t slot;
+#pragma omp atomic capture
+                            slot = count++;
+                            if (slot < cap) {
+                                oracle_cand* o = cands + slot;
+                                o->sb = s;
+                                o->dm_index = dm_base + i;
+                                o->downsamp = D;
+                                o->width_native = w * D;
+                                o->t_native = t * D + t_offset_native;
+                                o->dm = dm0[r] + (double)i * ddm[r];
+                                o->snr = snr[t];
+                            }
+                        }
+                    }
+                }
+            }
+            free(acc);
+            free(snr);
+        }
+        free(d);
+        free(y);
+        dm_base += n_dm[r];
+        w_base += n_width[r];
+        series_base += n_series * n_r;
+    }
+    return count;
+}
