@@ -1,0 +1,423 @@
+#!/usr/bin/env python3
+"""Benchmark of the B300 single-pulse search hot path.
+
+One step = one full search (downsampling when the plan has it, SB-gather +
+dedispersion, statistics, boxcar S/N, threshold + compaction) of one 1.024 s
+chunk of synthetic ARTS-shaped data, through the C ABI.  Metric: DM-trial
+samples per second (SBs x DM trials x output samples, each range counted at
+its own rate), whole job over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl fdd|reference]
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle (the
+only reference this project has: the paper's AMBER code is not part of it)
+on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+K_DM = 4148.808  # s MHz^2 / (pc cm^-3), for placing injected pulses only
+WIDTHS = [1, 2, 4, 8, 16, 32, 64]
+
+WORKLOADS = {
+    # 1 SB, 1536 ch, 1.024 s chunk, DM 0-409.4 step 0.2 (2048 trials), widths 1..64
+    "arts_single_sb": dict(n_tab=1, n_sb=1, n_chan=1536, n_out=synth.ARTS_CHUNK, seed=2, n_pulses=10,
+                           pulse_tabs=[0], thr=8.0,
+                           ranges=[dict(dm0=0.0, ddm=0.2, n_dm=2048, downsamp=1, widths=WIDTHS)]),
+    # 12 TABs -> 71 SBs (seeded piecewise-constant SB table), same DM plan
+    "arts_71sb": dict(n_tab=12, n_sb=71, n_chan=1536, n_out=synth.ARTS_CHUNK, seed=3, n_pulses=5,
+                      pulse_tabs=[0, 3, 5, 8, 11], thr=8.0,
+                      ranges=[dict(dm0=0.0, ddm=0.2, n_dm=2048, downsamp=1, widths=WIDTHS)]),
+    # 71 SBs, 4-range plan 0-5000 with downsampling 1/2/4/8
+    "arts_71sb_4range": dict(n_tab=12, n_sb=71, n_chan=1536, n_out=synth.ARTS_CHUNK, seed=4, n_pulses=5,
+                             pulse_tabs=[0, 3, 5, 8, 11], thr=8.0,
+                             ranges=[dict(dm0=0.0, ddm=0.2, n_dm=2048, downsamp=1, widths=WIDTHS),
+                                     dict(dm0=409.6, ddm=0.8, n_dm=1024, downsamp=2, widths=WIDTHS),
+                                     dict(dm0=1228.8, ddm=1.6, n_dm=1024, downsamp=4, widths=WIDTHS),
+                                     dict(dm0=2867.2, ddm=3.2, n_dm=667, downsamp=8, widths=WIDTHS)]),
+}
+
+N_SM = 148
+INT_LANES_PER_SM = 128
+ADDS_PER_LANE_OP = 2        # one IADD3 adds two operands
+SM_MAX_MHZ_NOMINAL = 2032.0
+PROFILE = os.path.join(ROOT, "profiles", "k_dedisp_arts_single_sb.md")
+DEDISP_SRC = os.path.join(ROOT, "paper_2205_12362_b300", "csrc", "k_dedisp.cu")
+
+
+# ----------------------------------------------------------------- workload
+def arrivals(freqs, dm, t_samp):
+    """Per-channel arrival offsets (samples) of a dispersed pulse: the signal model."""
+    f_top = freqs.max()
+    return np.rint(K_DM * dm * (freqs ** -2 - f_top ** -2) / t_samp).astype(np.int64)
+
+
+def max_delay_native(freqs, ranges, t_samp):
+    out = 0
+    for r in ranges:
+        dm_last = r["dm0"] + (r["n_dm"] - 1) * r["ddm"]
+        d = np.rint(K_DM * dm_last * (freqs.min() ** -2 - freqs.max() ** -2) / (r["downsamp"] * t_samp))
+        out = max(out, int(d + 1) * r["downsamp"])
+    return out
+
+
+def make_workload(name):
+    w = dict(WORKLOADS[name])
+    f = synth.channel_freqs(w["n_chan"])
+    t = synth.ARTS_T_SAMP_S
+    n_in = w["n_out"] + max_delay_native(f, w["ranges"], t) + 16
+    dm_hi = min(400.0, w["ranges"][-1]["dm0"] + w["ranges"][-1]["n_dm"] * w["ranges"][-1]["ddm"])
+    prm = synth.random_pulses(w["seed"], w["n_pulses"], w["pulse_tabs"], 50.0, dm_hi, [1, 2, 4, 8, 16, 32],
+                              8.0, 50.0, 200, w["n_out"] - 200)
+    pulses = [dict(tab=p["tab"], start=p["t0"] + arrivals(f, p["dm"], t), width=p["width"],
+                   amp=synth.pulse_amplitude(p["snr"], w["n_chan"], p["width"])) for p in prm]
+    x = synth.filterbank(w["seed"], w["n_tab"], w["n_chan"], n_in, pulses=pulses)
+    if w["n_tab"] == 1:
+        sb = np.zeros((w["n_sb"], w["n_chan"]), np.int16)
+    else:
+        sb = synth.sb_map_piecewise(w["seed"], w["n_sb"], w["n_chan"], w["n_tab"]).astype(np.int16)
+    return w, f, t, x, sb, n_in
+
+
+def units_per_step(w):
+    return sum(w["n_sb"] * r["n_dm"] * (w["n_out"] // r["downsamp"]) for r in w["ranges"])
+
+
+def adds_per_step(w):
+    return sum(w["n_sb"] * r["n_dm"] * (w["n_out"] // r["downsamp"]) * w["n_chan"] for r in w["ranges"])
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        self.t0 = time.time()
+
+    def mark(self):
+        return time.time()
+
+    def stop(self, t_lo, t_hi):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for ln in open(self.path):
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        # samples are ~100 ms apart from start(); keep those inside [t_lo, t_hi] by position
+        n = len(rows)
+        span = max(time.time() - self.t0, 1e-3)
+        lo = int(max(0, (t_lo - self.t0) / span * n))
+        hi = int(min(n, (t_hi - self.t0) / span * n + 1))
+        sel = rows[lo:hi] or rows
+        sm = [float(r[1]) for r in sel if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in sel if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        for r in sel:
+            for name, val in (("hw_slowdown", r[5]), ("hw_thermal_slowdown", r[6]),
+                              ("sw_thermal_slowdown", r[7]), ("sw_power_cap", r[8])):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sel),
+                "power_w_max": max(float(r[3]) for r in sel if re.match(r"^[0-9.]+$", r[3])) if any(
+                    re.match(r"^[0-9.]+$", r[3]) for r in sel) else None}
+
+
+# ----------------------------------------------------------------- oracle (CPU baseline)
+def oracle_sample_rate(x, sb, f, t, w, n_in, target_s):
+    """Time the oracle as it stands on a bounded sample (leading DM trials of
+    each range, first SB) and return (samples/s, cores, description)."""
+    import oracle
+    cores = oracle.get_threads()
+
+    def run(frac):
+        rr = [dict(r, n_dm=max(1, int(r["n_dm"] * frac))) for r in w["ranges"]]
+        units = sum(r["n_dm"] * (w["n_out"] // r["downsamp"]) for r in rr)
+        t0 = time.perf_counter()
+        oracle.search(x, sb[:1], f, t, rr, w["thr"], w["n_out"], n_in=n_in)
+        return units, time.perf_counter() - t0, rr
+
+    u, dt, _ = run(1.0 / 64)
+    frac = min(1.0, (1.0 / 64) * target_s / max(dt, 1e-3))
+    u, dt, rr = run(frac)
+    desc = "SB 0 of %d, first %s DM trials of each range (%s), full %d-sample chunk, %d channels" % (
+        w["n_sb"], "/".join(str(r["n_dm"]) for r in rr), "/".join(str(r["n_dm"]) for r in w["ranges"]),
+        w["n_out"], w["n_chan"])
+    return u / dt, cores, desc, dt, rr
+
+
+# ----------------------------------------------------------------- profile evidence
+def profile_traffic():
+    """DRAM bytes per dedispersion launch from the committed ncu summary, or
+    None when the kernel source changed since the counters were taken."""
+    if not os.path.exists(PROFILE):
+        return None
+    text = open(PROFILE).read()
+    m_sha = re.search(r"source_sha1:\s*([0-9a-f]{40})", text)
+    m_b = re.search(r"dram_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b:
+        return None
+    sha = hashlib.sha1(open(DEDISP_SRC, "rb").read()).hexdigest()
+    return float(m_b.group(1)) if sha == m_sha.group(1) else None
+
+
+# ----------------------------------------------------------------- arms
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "fdd" else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def run_fdd(args):
+    import torch
+
+    import paper_2205_12362_b300 as fdd
+
+    world, rank, local, dist = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w, f, t, x, sb, n_in = make_workload(args.workload)
+    plan = fdd.Plan(w["n_tab"], w["n_chan"], w["n_sb"], f, t, w["ranges"], w["thr"], sb)
+    host = torch.from_numpy(x).pin_memory()
+    tabs = host.to(dev)
+    ws = torch.empty(plan.workspace_size(n_in, w["n_out"], with_series=True), dtype=torch.uint8, device=dev)
+    cap = 1 << 20
+    cands = torch.empty((cap, 8), dtype=torch.int32, device=dev)
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
+    stream = torch.cuda.current_stream()
+    plan.set_timing(True)
+
+    def step():
+        return plan.search(tabs, n_in, w["n_out"], cap=cap, workspace=ws, cands=cands, count=count,
+                           stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_lo = time.time()
+    step_ms, stage_ms, launches = [], {}, 0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()                      # evict the input from L2 between steps
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        st = plan.stage_times()
+        launches += len(st)
+        for name, r, ms in st:
+            stage_ms.setdefault("%s[%d]" % (name, r), []).append(ms)
+    torch.cuda.synchronize()
+    wall1 = time.perf_counter()
+    if dist:
+        dist.barrier()
+    t_hi = time.time()
+    clocks = sampler.stop(t_lo, t_hi)
+
+    dev_s = sum(step_ms) / 1e3
+    if dist:
+        tt = torch.tensor([dev_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dev_s = float(tt.item())
+    units = units_per_step(w) * args.steps * world
+    value = units / dev_s
+
+    # end-to-end through the public API with host buffers: H2D of the chunk
+    # from pinned memory, search, D2H of the count and the candidate records.
+    e2e_units, h2d, d2h = 0, 0, 0
+    cnt_host = torch.zeros(1, dtype=torch.int64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 200))
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        tabs.copy_(host, non_blocking=True)
+        step()
+        cnt_host.copy_(count, non_blocking=True)
+        torch.cuda.synchronize()
+        n = min(int(cnt_host.item()), cap)
+        got = cands[:n].cpu()
+        h2d += host.numel()
+        d2h += 8 + got.numel() * 4
+        e2e_units += units_per_step(w)
+    te1 = time.perf_counter()
+    e2e_s = te1 - te0
+    if dist:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return None
+
+    # roofline of the dominant kernel (dedispersion): channel-adds per launch
+    ded = [v for k, v in stage_ms.items() if k.startswith("dedisperse")]
+    ded_ms = float(np.mean([np.mean(v) for v in ded])) if ded else None
+    adds_launch = adds_per_step(w) / max(1, len(ded))
+    sm_mhz = clocks.get("sm_mhz")
+    peak = N_SM * INT_LANES_PER_SM * ADDS_PER_LANE_OP * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    achieved = adds_launch / (ded_ms / 1e3) / 1e12 if ded_ms else None
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": profile_traffic(),
+            "kernel": "k_dedisp", "units_per_launch": adds_launch,
+            "peak_basis": "148 SM x 128 INT32 lanes x 2 adds/IADD3 x 2032 MHz (derived; no measured INT peak)",
+            "peak_at_sampled_clock": (peak * sm_mhz / SM_MAX_MHZ_NOMINAL) if sm_mhz else None,
+            "avg_launch_ms": ded_ms}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, cores, desc, secs, _ = oracle_sample_rate(x, sb, f, t, w, n_in, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "samples/s", "cores": cores, "kind": "oracle", "sample": desc,
+               "seconds": secs}
+
+    line = {
+        "metric": "DM-trial samples/s (beams x DMs x samples)",
+        "value": value,
+        "unit": "samples/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": sum(step_ms) / len(step_ms),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n_tab": w["n_tab"], "n_sb": w["n_sb"], "n_chan": w["n_chan"],
+                   "n_out": w["n_out"], "n_in": n_in,
+                   "dm_plan": [[r["dm0"], r["ddm"], r["n_dm"], r["downsamp"]] for r in w["ranges"]],
+                   "widths": WIDTHS, "snr_thresh": w["thr"], "l2": "flushed (256 MB write) between steps",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_units * world / e2e_s, "unit": "samples/s",
+                "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
+                "steps": e2e_steps},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "stages_ms": {k: float(np.mean(v)) for k, v in stage_ms.items()},
+        "wall_s": wall1 - wall0,
+    }
+    if dist:
+        dist.destroy_process_group()
+    return line
+
+
+def run_reference(args):
+    world, rank, local, dist = dist_setup(args)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return None
+    import oracle
+    w, f, t, x, sb, n_in = make_workload(args.workload)
+    per_step = max(0.5, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
+    _, cores, desc, _, rr = oracle_sample_rate(x, sb, f, t, w, n_in, per_step)
+    units = sum(r["n_dm"] * (w["n_out"] // r["downsamp"]) for r in rr)
+    for _ in range(args.warmup):
+        oracle.search(x, sb[:1], f, t, rr, w["thr"], w["n_out"], n_in=n_in)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.search(x, sb[:1], f, t, rr, w["thr"], w["n_out"], n_in=n_in)
+    dt = time.perf_counter() - t0
+    value = units * args.steps / dt
+    line = {
+        "impl": "reference",
+        "metric": "DM-trial samples/s (beams x DMs x samples)",
+        "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / max(1, args.steps) * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64/f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n_tab": w["n_tab"], "n_sb": w["n_sb"], "n_chan": w["n_chan"],
+                   "n_out": w["n_out"], "n_in": n_in,
+                   "dm_plan": [[r["dm0"], r["ddm"], r["n_dm"], r["downsamp"]] for r in w["ranges"]],
+                   "widths": WIDTHS, "snr_thresh": w["thr"]},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    if dist:
+        dist.destroy_process_group()
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--workload", default="arts_single_sb", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="fdd", choices=["fdd", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    line = run_fdd(args) if args.impl == "fdd" else run_reference(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

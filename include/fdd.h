@@ -1,0 +1,199 @@
+/*
+ * fdd.h -- C ABI of the B300 single-pulse (FRB) search hot path.
+ *
+ * The library implements, as CUDA kernels for sm_103a, the per-chunk search
+ * the paper's AMBER pipeline runs on each compound beam (Sec. "AMBER"):
+ * downsampling, brute-force incoherent dedispersion with synthesized-beam
+ * (SB) formation, boxcar integration over pulse widths, S/N evaluation and
+ * candidate selection.  Inputs follow the paper's data description: 8-bit
+ * Stokes-I filterbank per tied-array beam (TAB), time the fastest index
+ * (Sec. "Data formats"; Sec. "Dedicated ARTS TABF on Central Uniboards").
+ * The output record carries the fields the paper's candidate files hold:
+ * beam, downsampling factor, arrival time, width, DM and S/N (Sec. "DARC").
+ *
+ * Conventions shared by every call:
+ *   - Pointers named d_* are DEVICE pointers (cudaMalloc / torch CUDA
+ *     tensors) owned by the caller; everything else is host memory.
+ *   - Calls that take a cudaStream_t only enqueue work on that stream and
+ *     return; results are valid once the stream has been synchronised.
+ *   - Return value: FDD_OK (0) or a negative FDD_ERR_* code.  Argument
+ *     errors are detected on the host before anything is enqueued.  A CUDA
+ *     runtime failure returns FDD_ERR_CUDA; fdd_last_error_message() then
+ *     holds the runtime's text (per thread).
+ *   - The library owns the plan's device tables (delay offsets, SB map) and
+ *     frees them in fdd_plan_destroy.  It never allocates per-call memory:
+ *     scratch ("workspace") is a caller buffer sized by fdd_workspace_size.
+ *   - A plan may be used from one host thread at a time.  Searches on
+ *     different streams may overlap if each has its own workspace,
+ *     candidate buffer and counter.
+ */
+#ifndef FDD_H
+#define FDD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* fdd_stream_t; /* same type as cudaStream_t; NULL = legacy default stream */
+
+enum {
+    FDD_OK = 0,
+    FDD_ERR_INVALID_ARG = -1,  /* bad size, pointer, plan field or sb_map entry */
+    FDD_ERR_SHORT_INPUT = -2,  /* n_in < n_out + max delay of some range (native samples) */
+    FDD_ERR_NO_MEMORY = -3,    /* device or host allocation of plan tables failed */
+    FDD_ERR_MISALIGNED = -4,   /* device pointer or row pitch not 16-byte aligned */
+    FDD_ERR_UNSUPPORTED = -5,  /* plan outside the kernels' limits (see FDD_MAX_*) */
+    FDD_ERR_CUDA = -6,         /* CUDA runtime error; see fdd_last_error_message() */
+    FDD_ERR_WORKSPACE = -7     /* workspace smaller than fdd_workspace_size() */
+};
+
+#define FDD_MAX_WIDTHS 16      /* boxcar widths per DM range */
+#define FDD_MAX_WIDTH 1024     /* largest boxcar width, in range samples */
+#define FDD_MAX_CHANNELS 16384
+#define FDD_MAX_TABS 256
+
+/* One range of the DM plan (paper Table "dedispersion setup": each GPU
+ * covers a DM range with its own step; Sec. "Downsampling" lets a range run
+ * at a reduced time resolution).  Trial i of the range has
+ * DM_i = dm0 + i * ddm (formed afresh, not accumulated). */
+typedef struct {
+    double dm0;            /* first trial DM, pc cm^-3, >= 0 */
+    double ddm;            /* DM step, > 0 */
+    int32_t n_dm;          /* number of trials, >= 1 */
+    int32_t downsamp;      /* D >= 1: the range works on sums of D native samples */
+    int32_t n_width;       /* 1..FDD_MAX_WIDTHS */
+    const int32_t* widths; /* host [n_width]: boxcar widths in range samples, 1..FDD_MAX_WIDTH */
+} fdd_range;
+
+/* Plan description.  Channel order is free; the highest frequency is the
+ * dedispersion reference (its delay is 0 for every DM). */
+typedef struct {
+    int32_t n_tab;                /* TABs per compound beam (12 in ARTS), 1..FDD_MAX_TABS */
+    int32_t n_chan;               /* channels (1536 in ARTS), 1..FDD_MAX_CHANNELS */
+    int32_t n_sb;                 /* synthesized beams to search (71 in ARTS), >= 1 */
+    const double* chan_freq_mhz;  /* host [n_chan]: channel centre frequencies, > 0 */
+    double t_samp_s;              /* native sampling time (81.92e-6 in ARTS), > 0 */
+    int32_t n_range;              /* >= 1 */
+    const fdd_range* ranges;      /* host [n_range] */
+    float snr_thresh;             /* candidate when S/N > snr_thresh (strict) */
+} fdd_plan_desc;
+
+/* One candidate (32 bytes, POD).  Fields after Sec. "DARC" candidate files:
+ * SB index, DM-trial index (global over the concatenated ranges), the range's
+ * downsampling factor, boxcar width and window start in NATIVE samples (start
+ * = t * D + t_offset_native of the search call), trial DM and S/N. */
+typedef struct {
+    int32_t sb;
+    int32_t dm_index;
+    int32_t downsamp;
+    int32_t width_native;
+    int64_t t_native;
+    float dm;
+    float snr;
+} fdd_candidate;
+
+typedef struct fdd_plan fdd_plan;
+
+/* Build a plan: computes every range's integer delay table on the host in
+ * FP64,
+ *     d[i][c] = llround(4148.808 * DM_i * (f_c^-2 - f_top^-2) / (D * t_samp)),
+ * (Sec. "Dedispersion"; the cold-plasma constant is not printed in the paper)
+ * and uploads it, with the SB map, to the current CUDA device.
+ * sb_map_host: host int16 [n_sb][n_chan]; SB s takes channel c from TAB
+ * sb_map_host[s*n_chan + c], which must lie in [0, n_tab) (Sec.
+ * "Hierarchical beam forming": SBs are per-channel selections of TABs).
+ * On success *out receives the plan (free with fdd_plan_destroy).
+ * Errors: INVALID_ARG, UNSUPPORTED, NO_MEMORY, CUDA. */
+int fdd_plan_create(const fdd_plan_desc* desc, const int16_t* sb_map_host, fdd_plan** out);
+
+/* Free the plan and its device tables.  NULL is accepted.  The caller makes
+ * sure no enqueued search still uses it. */
+int fdd_plan_destroy(fdd_plan* plan);
+
+/* Largest delay over all ranges, in native samples (max_r D_r * max d_r):
+ * a search of n_out output samples needs n_in >= n_out + max_delay_native
+ * input samples per channel. */
+int fdd_plan_max_delay(const fdd_plan* plan, int64_t* max_delay_native);
+
+/* Number of DM trials summed over all ranges (the length of the global
+ * dm_index axis). */
+int fdd_plan_total_dms(const fdd_plan* plan, int64_t* n_dm_total);
+
+/* Copy range r's integer delay table (int32 [n_dm][n_chan], units of D_r
+ * native samples) to host memory dst (n_dm * n_chan entries). */
+int fdd_plan_delays(const fdd_plan* plan, int32_t r, int32_t* dst);
+
+/* Bytes of device workspace a search of (n_in, n_out) needs.
+ * If the caller passes d_series to fdd_search, the series live there and the
+ * workspace shrinks by fdd_series_size(). */
+int fdd_workspace_size(const fdd_plan* plan, int64_t n_in, int64_t n_out, int32_t with_series,
+                       size_t* bytes);
+
+/* Bytes of the dedispersed-series buffer: int32, packed per range as
+ * [range][sb][dm][floor(n_out / D_r)]. */
+int fdd_series_size(const fdd_plan* plan, int64_t n_out, size_t* bytes);
+
+/* Search one chunk of every SB of the plan.
+ *   d_tabs        device uint8 [n_tab][n_chan][pitch]: TAB filterbanks; the
+ *                 first n_in samples of each row are data.  16-byte aligned.
+ *   pitch         row pitch in samples (bytes), multiple of 16, >= n_in.
+ *   n_out         output samples (native) to search; range r produces
+ *                 floor(n_out / D_r) samples per series, and downsampling
+ *                 bins start at input sample 0.
+ *   t_offset_native  added to every candidate's t_native (stream position).
+ *   d_workspace   >= fdd_workspace_size(plan, n_in, n_out, d_series == NULL).
+ *   d_cands       device [cap] candidate records (order unspecified).
+ *   d_count       device uint64: set to the TRUE number of candidates; only
+ *                 the first min(count, cap) records are written, so
+ *                 count > cap signals an overflow.
+ *   d_series      NULL, or device int32 buffer of fdd_series_size() bytes that
+ *                 receives every dedispersed series (for verification).
+ * Stages per range: downsample (D > 1), SB-gather + dedispersion with exact
+ * int32 sums, series statistics, boxcar S/N over the range's widths, warp-
+ * ballot threshold and compaction.  Asynchronous on stream.
+ * Errors (host-side, nothing enqueued): INVALID_ARG, SHORT_INPUT, MISALIGNED,
+ * WORKSPACE; CUDA on a launch failure. */
+int fdd_search(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitch, int64_t n_out,
+               int64_t t_offset_native, void* d_workspace, size_t workspace_bytes,
+               fdd_candidate* d_cands, int64_t cap, uint64_t* d_count, int32_t* d_series,
+               fdd_stream_t stream);
+
+/* Stage entry point (Sec. "Downsampling"): d_out[row][j] =
+ * sum_{k<D} d_in[row][j*D + k] for j < floor(n_in / D), rows = n_rows.
+ * d_in uint8 rows at in_pitch bytes; d_out uint16 rows at out_pitch
+ * elements (multiple of 8).  Both 16-byte aligned.  1 <= D <= 257. */
+int fdd_downsample_u8(const uint8_t* d_in, int64_t n_rows, int64_t n_in, int64_t in_pitch,
+                      int32_t downsamp, uint16_t* d_out, int64_t out_pitch, fdd_stream_t stream);
+
+/* Per-stage GPU timing (tracing; the paper reports AMBER's time per stage,
+ * Sec. "Computing performance").  With timing enabled, fdd_search records a
+ * CUDA event pair around every kernel it enqueues; the pairs are reused by
+ * the next search.  Enabling creates the events on the current device. */
+int fdd_plan_set_timing(fdd_plan* plan, int32_t enable);
+
+/* Elapsed time of each stage of the last timed fdd_search on this plan,
+ * in enqueue order.  Call after that search's stream has been synchronised
+ * (FDD_ERR_CUDA "not ready" otherwise).  For stage k: kind[k] = 0
+ * downsample, 1 SB-gather + dedispersion, 2 boxcar S/N + threshold;
+ * range[k] = DM range index (downsample: its factor D); ms[k] milliseconds.
+ * Writes min(max_n, stages) entries; *n_stages receives the stage count. */
+int fdd_plan_stage_times(fdd_plan* plan, int32_t max_n, int32_t* kind, int32_t* range, float* ms,
+                         int32_t* n_stages);
+
+/* Human-readable text of an FDD_* code (static string). */
+const char* fdd_error_string(int code);
+
+/* Text of the last CUDA error seen by this thread inside the library. */
+const char* fdd_last_error_message(void);
+
+/* Library version string. */
+const char* fdd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDD_H */

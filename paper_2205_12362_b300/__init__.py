@@ -1,0 +1,302 @@
+"""B300-native hot path of the ARTS real-time single-pulse search.
+
+A thin Python binding (ctypes) over the C ABI of ``libfdd.so`` (declared in
+``include/fdd.h``).  Every stage of the search -- downsampling, synthesized-
+beam gather + brute-force dedispersion, series statistics, boxcar S/N,
+threshold and compaction -- runs in the library's CUDA kernels; this module
+only marshals arguments.  PyTorch supplies device memory and streams.
+
+There is no CPU fallback: if the library is missing, importing the binding
+works but every call raises ``FddUnavailable``.
+"""
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH
+
+__all__ = ["Plan", "FddError", "FddUnavailable", "CAND_DTYPE", "decode_candidates", "downsample_u8",
+           "library_path", "version"]
+
+CAND_DTYPE = np.dtype([("sb", np.int32), ("dm_index", np.int32), ("downsamp", np.int32),
+                       ("width_native", np.int32), ("t_native", np.int64), ("dm", np.float32),
+                       ("snr", np.float32)])
+assert CAND_DTYPE.itemsize == 32
+
+FDD_MAX_WIDTHS = 16
+
+
+class FddError(RuntimeError):
+    def __init__(self, code, where):
+        msg = "%s failed: %s (%d)" % (where, _lib_raw().fdd_error_string(code).decode(), code)
+        detail = _lib_raw().fdd_last_error_message().decode()
+        if detail:
+            msg += ": " + detail
+        super().__init__(msg)
+        self.code = code
+
+
+class FddUnavailable(RuntimeError):
+    pass
+
+
+class _Range(ctypes.Structure):
+    _fields_ = [("dm0", ctypes.c_double), ("ddm", ctypes.c_double), ("n_dm", ctypes.c_int32),
+                ("downsamp", ctypes.c_int32), ("n_width", ctypes.c_int32),
+                ("widths", ctypes.POINTER(ctypes.c_int32))]
+
+
+class _PlanDesc(ctypes.Structure):
+    _fields_ = [("n_tab", ctypes.c_int32), ("n_chan", ctypes.c_int32), ("n_sb", ctypes.c_int32),
+                ("chan_freq_mhz", ctypes.POINTER(ctypes.c_double)), ("t_samp_s", ctypes.c_double),
+                ("n_range", ctypes.c_int32), ("ranges", ctypes.POINTER(_Range)),
+                ("snr_thresh", ctypes.c_float)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_SZ = ctypes.c_size_t
+
+
+def library_path():
+    return _LIB_PATH
+
+
+def _lib_raw():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise FddUnavailable("libfdd.so is not built (python -m paper_2205_12362_b300.build); "
+                             "there is no CPU fallback")
+    L = ctypes.CDLL(_LIB_PATH)
+    L.fdd_version.restype = ctypes.c_char_p
+    L.fdd_error_string.restype = ctypes.c_char_p
+    L.fdd_error_string.argtypes = [ctypes.c_int]
+    L.fdd_last_error_message.restype = ctypes.c_char_p
+    L.fdd_plan_create.argtypes = [ctypes.POINTER(_PlanDesc), _P, ctypes.POINTER(_P)]
+    L.fdd_plan_destroy.argtypes = [_P]
+    L.fdd_plan_max_delay.argtypes = [_P, ctypes.POINTER(_I64)]
+    L.fdd_plan_total_dms.argtypes = [_P, ctypes.POINTER(_I64)]
+    L.fdd_plan_delays.argtypes = [_P, _I32, _P]
+    L.fdd_workspace_size.argtypes = [_P, _I64, _I64, _I32, ctypes.POINTER(_SZ)]
+    L.fdd_series_size.argtypes = [_P, _I64, ctypes.POINTER(_SZ)]
+    L.fdd_search.argtypes = [_P, _P, _I64, _I64, _I64, _I64, _P, _SZ, _P, _I64, _P, _P, _P]
+    L.fdd_downsample_u8.argtypes = [_P, _I64, _I64, _I64, _I32, _P, _I64, _P]
+    L.fdd_plan_set_timing.argtypes = [_P, _I32]
+    L.fdd_plan_stage_times.argtypes = [_P, _I32, _P, _P, _P, ctypes.POINTER(_I32)]
+    _lib = L
+    return L
+
+
+def version():
+    return _lib_raw().fdd_version().decode()
+
+
+def _check(code, where):
+    if code != 0:
+        raise FddError(code, where)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, name, dtype=None):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must have dtype %s" % (name, dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass
+class SearchResult:
+    cands: "object"     # torch.int32 [cap, 8] raw 32-byte records on the device
+    count: "object"     # torch.int64 [1] on the device (true count; > cap means overflow)
+    series: "object"    # torch.int32 flat series buffer or None
+    cap: int
+
+    def candidates(self):
+        """Copy to host and decode (sorted by sb, dm_index, width, t)."""
+        n = int(self.count.item())
+        return decode_candidates(self.cands, min(n, self.cap)), n
+
+
+def decode_candidates(cands, n):
+    raw = cands[:n].contiguous().cpu().numpy().view(np.uint8).reshape(-1)
+    arr = raw.view(CAND_DTYPE).copy()
+    return np.sort(arr, order=["sb", "dm_index", "width_native", "t_native"])
+
+
+class Plan:
+    """A DM plan over SBs of one compound beam (include/fdd.h: fdd_plan_create).
+
+    ranges: list of dicts {dm0, ddm, n_dm, downsamp, widths}.
+    sb_map: int array [n_sb][n_chan] of TAB indices (n_tab = 1, zeros: plain
+    single-beam search).
+    """
+
+    def __init__(self, n_tab, n_chan, n_sb, chan_freq_mhz, t_samp_s, ranges, snr_thresh, sb_map):
+        L = _lib_raw()
+        self._freq = np.ascontiguousarray(chan_freq_mhz, dtype=np.float64)
+        if self._freq.size != n_chan:
+            raise ValueError("chan_freq_mhz must have n_chan entries")
+        sb = np.ascontiguousarray(sb_map, dtype=np.int16)
+        if sb.shape != (n_sb, n_chan):
+            raise ValueError("sb_map must be [n_sb][n_chan]")
+        self.ranges = [dict(dm0=float(r["dm0"]), ddm=float(r["ddm"]), n_dm=int(r["n_dm"]),
+                            downsamp=int(r.get("downsamp", 1)), widths=[int(w) for w in r["widths"]])
+                       for r in ranges]
+        self._widths = [np.ascontiguousarray(r["widths"], dtype=np.int32) for r in self.ranges]
+        rr = (_Range * len(self.ranges))()
+        for k, r in enumerate(self.ranges):
+            rr[k].dm0, rr[k].ddm, rr[k].n_dm = r["dm0"], r["ddm"], r["n_dm"]
+            rr[k].downsamp, rr[k].n_width = r["downsamp"], len(r["widths"])
+            rr[k].widths = self._widths[k].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        desc = _PlanDesc(n_tab, n_chan, n_sb, self._freq.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                         float(t_samp_s), len(self.ranges), rr, float(snr_thresh))
+        h = ctypes.c_void_p()
+        _check(L.fdd_plan_create(ctypes.byref(desc), sb.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)),
+               "fdd_plan_create")
+        self._h = h
+        self.n_tab, self.n_chan, self.n_sb = int(n_tab), int(n_chan), int(n_sb)
+        self.t_samp_s = float(t_samp_s)
+        self.snr_thresh = float(snr_thresh)
+
+    # -- queries
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def max_delay(self):
+        v = _I64()
+        _check(_lib_raw().fdd_plan_max_delay(self._h, ctypes.byref(v)), "fdd_plan_max_delay")
+        return int(v.value)
+
+    @property
+    def n_dm_total(self):
+        v = _I64()
+        _check(_lib_raw().fdd_plan_total_dms(self._h, ctypes.byref(v)), "fdd_plan_total_dms")
+        return int(v.value)
+
+    def delays(self, r):
+        out = np.empty((self.ranges[r]["n_dm"], self.n_chan), dtype=np.int32)
+        _check(_lib_raw().fdd_plan_delays(self._h, int(r), out.ctypes.data_as(ctypes.c_void_p)),
+               "fdd_plan_delays")
+        return out
+
+    def workspace_size(self, n_in, n_out, with_series=True):
+        v = _SZ()
+        _check(_lib_raw().fdd_workspace_size(self._h, int(n_in), int(n_out), int(bool(with_series)),
+                                             ctypes.byref(v)), "fdd_workspace_size")
+        return int(v.value)
+
+    def series_size(self, n_out):
+        v = _SZ()
+        _check(_lib_raw().fdd_series_size(self._h, int(n_out), ctypes.byref(v)), "fdd_series_size")
+        return int(v.value)
+
+    def series_views(self, series, n_out):
+        """Split a flat series buffer into per-range [n_sb][n_dm][n_out // D] views."""
+        out, off = [], 0
+        for r in self.ranges:
+            nr = int(n_out) // r["downsamp"]
+            k = self.n_sb * r["n_dm"] * nr
+            out.append(series[off:off + k].view(self.n_sb, r["n_dm"], nr))
+            off += k
+        return out
+
+    # -- the hot path
+    def search(self, tabs, n_in, n_out, t_offset=0, cap=1 << 16, workspace=None, cands=None, count=None,
+               series=None, want_series=False, stream=None):
+        """Search one chunk (include/fdd.h: fdd_search).  tabs: CUDA uint8
+        [n_tab][n_chan][pitch], pitch a multiple of 16.  Buffers not given
+        are allocated with torch on tabs' device."""
+        torch = _torch()
+        if tabs.dim() != 3 or tuple(tabs.shape[:2]) != (self.n_tab, self.n_chan):
+            raise ValueError("tabs must be [n_tab][n_chan][pitch]")
+        pitch = int(tabs.shape[2])
+        dev = tabs.device
+        if want_series and series is None:
+            series = torch.empty(self.series_size(n_out) // 4, dtype=torch.int32, device=dev)
+        ws_bytes = self.workspace_size(n_in, n_out, with_series=series is None)
+        if workspace is None:
+            workspace = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+        if cands is None:
+            cands = torch.empty((max(int(cap), 1), 8), dtype=torch.int32, device=dev)
+        cap = int(cands.shape[0])
+        if count is None:
+            count = torch.zeros(1, dtype=torch.int64, device=dev)
+        code = _lib_raw().fdd_search(
+            self._h, _dev_ptr(tabs, "tabs", torch.uint8), int(n_in), pitch, int(n_out), int(t_offset),
+            _dev_ptr(workspace, "workspace"), int(workspace.numel() * workspace.element_size()),
+            _dev_ptr(cands, "cands"), cap, _dev_ptr(count, "count"),
+            _dev_ptr(series, "series", torch.int32) if series is not None else None,
+            _stream_handle(stream))
+        _check(code, "fdd_search")
+        return SearchResult(cands=cands, count=count, series=series, cap=cap)
+
+    def set_timing(self, enable=True):
+        _check(_lib_raw().fdd_plan_set_timing(self._h, int(bool(enable))), "fdd_plan_set_timing")
+
+    STAGE_NAMES = {0: "downsample", 1: "dedisperse", 2: "boxcar_snr"}
+
+    def stage_times(self):
+        """[(stage name, range or D, ms)] of the last timed search (after sync)."""
+        n = _I32()
+        _check(_lib_raw().fdd_plan_stage_times(self._h, 0, None, None, None, ctypes.byref(n)),
+               "fdd_plan_stage_times")
+        k = int(n.value)
+        kind = np.zeros(max(k, 1), np.int32)
+        rng = np.zeros(max(k, 1), np.int32)
+        ms = np.zeros(max(k, 1), np.float32)
+        _check(_lib_raw().fdd_plan_stage_times(self._h, k, kind.ctypes.data_as(ctypes.c_void_p),
+                                               rng.ctypes.data_as(ctypes.c_void_p),
+                                               ms.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n)),
+               "fdd_plan_stage_times")
+        return [(self.STAGE_NAMES[int(kind[i])], int(rng[i]), float(ms[i])) for i in range(k)]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib_raw().fdd_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def downsample_u8(x, n_in, downsamp, out=None, stream=None):
+    """Time downsampling (include/fdd.h: fdd_downsample_u8) of every row of a
+    CUDA uint8 tensor [..., pitch]; returns uint16 [..., out_pitch]."""
+    torch = _torch()
+    pitch = int(x.shape[-1])
+    rows = int(np.prod(x.shape[:-1]))
+    n_y = int(n_in) // int(downsamp)
+    out_pitch = (n_y + 7) // 8 * 8
+    if out is None:
+        out = torch.empty(tuple(x.shape[:-1]) + (max(out_pitch, 8),), dtype=torch.int16, device=x.device)
+    code = _lib_raw().fdd_downsample_u8(_dev_ptr(x, "x", torch.uint8), rows, int(n_in), pitch,
+                                        int(downsamp), _dev_ptr(out, "out"), int(out.shape[-1]),
+                                        _stream_handle(stream))
+    _check(code, "fdd_downsample_u8")
+    return out

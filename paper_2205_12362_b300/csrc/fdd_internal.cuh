@@ -1,0 +1,76 @@
+// fdd_internal.cuh -- declarations shared by the library's own .cu files.
+// Not installed; the public interface is include/fdd.h.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fdd.h"
+
+namespace fdd {
+
+// ---------------------------------------------------------------------------
+// Dedispersion kernel variants (template instantiations of k_dedisp).
+//   E     bytes per input sample: 1 = raw uint8 filterbank, 2 = uint16 sums
+//         written by the downsampler
+//   NW    32-bit words per lane per DM trial (a lane covers NW * 4/E samples)
+//   DPW   DM trials per warp
+//   WARPS warps per block; the block covers BD = WARPS * DPW trials and
+//         T = 32 * NW * (4/E) output samples
+struct DedispVariant {
+    int E, NW, DPW, WARPS;
+    int bd() const { return WARPS * DPW; }
+    int tile() const { return 32 * NW * (4 / E); }
+    int threads() const { return WARPS * 32; }
+};
+
+int num_dedisp_variants();
+const DedispVariant& dedisp_variant(int idx);
+
+struct DedispArgs {
+    const uint8_t* in;          // row (tab, c) starts at in + (tab * n_chan + c) * pitch_bytes
+    int64_t pitch_bytes;        // multiple of 16
+    int64_t n_valid;            // valid samples per row (elements of E bytes)
+    const int16_t* sb_map;      // [n_sb][n_chan]
+    const int32_t* base;        // [n_blk][n_chan]: first staged sample of (DM block, channel), aligned to 16/E
+    const int32_t* off;         // [n_dm][n_chan]: byte offset of trial (i, c) inside its channel slot
+    int32_t* series;            // [n_sb][n_dm][n_out]
+    unsigned long long* stat;   // [n_sb * n_dm][2]: sum S, sum S^2
+    int32_t n_chan;
+    int32_t n_dm;
+    int32_t n_out;
+    int32_t n_sb;
+    int32_t Lw;                 // 32-bit words per staged copy row
+    int32_t CC;                 // channels per smem stage (divides 256 when E == 1)
+};
+
+// Shared-memory bytes of one dedispersion block.
+size_t dedisp_smem_bytes(const DedispVariant& v, int Lw, int CC);
+cudaError_t launch_dedisp(int variant, const DedispArgs& a, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+struct BoxcarArgs {
+    const int32_t* series;              // [n_sb][n_dm][n_out] of this range
+    const unsigned long long* stat;     // [n_sb * n_dm][2]
+    fdd_candidate* cands;
+    unsigned long long* count;
+    int64_t cap;
+    int64_t t_offset;
+    double dm0, ddm;
+    int32_t n_sb, n_dm, n_out;
+    int32_t dm_index0;
+    int32_t D;
+    int32_t n_width;
+    int32_t wmax;
+    float thr;
+    int32_t widths[FDD_MAX_WIDTHS];
+    float inv_sqrt_w[FDD_MAX_WIDTHS];
+};
+
+cudaError_t launch_boxcar(const BoxcarArgs& a, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+cudaError_t launch_downsample(const uint8_t* in, int64_t n_rows, int64_t n_in, int64_t in_pitch,
+                              int D, uint16_t* out, int64_t out_pitch, cudaStream_t s);
+
+}  // namespace fdd

@@ -1,0 +1,496 @@
+// fdd_plan.cu -- host side of the C ABI: plan construction (delay tables,
+// staged-offset tables, kernel variant per range), workspace layout and the
+// per-chunk search orchestration.  Every stage of the search itself runs in
+// the CUDA kernels of k_downsample.cu, k_dedisp.cu and k_boxcar.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fdd_internal.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+// Cold-plasma dispersion constant, s MHz^2 / (pc cm^-3).  The paper gives no
+// value; 4148.808 is the standard constant.
+constexpr double kDispersionConstant = 4148.808;
+
+constexpr size_t kSmemBudget = 112 * 1024;  // two blocks per SM fit in 228 KB
+
+int cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return FDD_ERR_CUDA;
+}
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+struct RangeState {
+    double dm0 = 0, ddm = 0;
+    int32_t n_dm = 0, D = 1, n_width = 0;
+    int32_t widths[FDD_MAX_WIDTHS] = {};
+    int32_t wmax = 1;
+    int32_t dm_index0 = 0;
+    int32_t dmax = 0;                 // largest delay, range samples
+    std::vector<int32_t> delay;       // [n_dm][n_chan]
+    // kernel configuration and its device tables
+    int variant = -1;
+    int32_t Lw = 0, CC = 0;
+    int32_t* d_off = nullptr;         // [n_dm][n_chan]
+    int32_t* d_base = nullptr;        // [n_blk][n_chan]
+};
+
+struct fdd_plan {
+    int32_t n_tab = 0, n_chan = 0, n_sb = 0;
+    double t_samp = 0;
+    float thr = 0;
+    std::vector<double> freq;
+    std::vector<int16_t> sb_map;
+    int16_t* d_sb_map = nullptr;
+    std::vector<RangeState> ranges;
+    std::vector<int32_t> ds_factors;  // distinct D > 1
+    int64_t max_delay_native = 0;
+    int64_t n_dm_total = 0;
+    int device = 0;
+    // stage timing (fdd_plan_set_timing)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;          // 2 per stage, grown on demand
+    std::vector<int32_t> st_kind, st_range;
+};
+
+namespace {
+
+void free_range_tables(RangeState& r) {
+    if (r.d_off) cudaFree(r.d_off);
+    if (r.d_base) cudaFree(r.d_base);
+    r.d_off = nullptr;
+    r.d_base = nullptr;
+}
+
+// Build the staged-offset tables of range r for kernel variant v.
+int configure_range(fdd_plan* p, RangeState& r, int variant) {
+    const fdd::DedispVariant& v = fdd::dedisp_variant(variant);
+    const int E = v.E, BD = v.bd(), NW = v.NW;
+    const int A = 16 / E;  // alignment of the staged row start, in samples
+    const int n_chan = p->n_chan;
+    const int n_blk = (r.n_dm + BD - 1) / BD;
+    std::vector<int32_t> base(static_cast<size_t>(n_blk) * n_chan);
+    int64_t max_span_words = 0;
+    for (int b = 0; b < n_blk; b++) {
+        const int ia = b * BD, ib = std::min(r.n_dm, (b + 1) * BD);
+        for (int c = 0; c < n_chan; c++) {
+            int32_t lo = r.delay[static_cast<size_t>(ia) * n_chan + c], hi = lo;
+            for (int i = ia; i < ib; i++) {
+                const int32_t d = r.delay[static_cast<size_t>(i) * n_chan + c];
+                lo = std::min(lo, d);
+                hi = std::max(hi, d);
+            }
+            const int32_t bs = lo / A * A;
+            base[static_cast<size_t>(b) * n_chan + c] = bs;
+            max_span_words = std::max<int64_t>(max_span_words, (static_cast<int64_t>(hi - bs) * E) >> 2);
+        }
+    }
+    const int64_t Lw = static_cast<int64_t>(align_up(static_cast<size_t>(max_span_words + 32 * NW), 4));
+    int CC = 0;
+    for (int cc : {16, 8, 4, 2, 1}) {
+        if (fdd::dedisp_smem_bytes(v, static_cast<int>(Lw), cc) <= kSmemBudget) {
+            CC = cc;
+            break;
+        }
+    }
+    if (CC == 0 || Lw > (1 << 20))
+        return fail(FDD_ERR_UNSUPPORTED, "DM step too large for one block's staged rows; lower ddm or raise downsamp");
+    std::vector<int32_t> off(static_cast<size_t>(r.n_dm) * n_chan);
+    for (int i = 0; i < r.n_dm; i++) {
+        const int b = i / BD;
+        for (int c = 0; c < n_chan; c++) {
+            const int32_t o = (r.delay[static_cast<size_t>(i) * n_chan + c] - base[static_cast<size_t>(b) * n_chan + c]) * E;
+            const int32_t q = (o & 3) / E;
+            off[static_cast<size_t>(i) * n_chan + c] = q * static_cast<int32_t>(Lw) * 4 + (o & ~3);
+        }
+    }
+    free_range_tables(r);
+    cudaError_t e = cudaMalloc(&r.d_off, off.size() * sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(offset table)");
+    e = cudaMalloc(&r.d_base, base.size() * sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(base table)");
+    e = cudaMemcpy(r.d_off, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(offset table)");
+    e = cudaMemcpy(r.d_base, base.data(), base.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(base table)");
+    r.variant = variant;
+    r.Lw = static_cast<int32_t>(Lw);
+    r.CC = CC;
+    return FDD_OK;
+}
+
+int default_variant(int E) {
+    for (int k = 0; k < fdd::num_dedisp_variants(); k++)
+        if (fdd::dedisp_variant(k).E == E) return k;
+    return -1;
+}
+
+struct Layout {
+    size_t series = 0, series_bytes = 0;
+    size_t stat = 0, stat_bytes = 0;
+    std::vector<size_t> series_r;   // element offset of range r inside the series buffer
+    std::vector<size_t> stat_r;     // series-index offset of range r inside the stat buffer
+    std::vector<size_t> ds_off;     // per distinct D (plan order)
+    std::vector<int64_t> ds_pitch;  // uint16 elements
+    size_t total = 0;
+};
+
+Layout make_layout(const fdd_plan* p, int64_t n_in, int64_t n_out, bool with_series) {
+    Layout L;
+    size_t series_elems = 0, n_series = 0;
+    for (const RangeState& r : p->ranges) {
+        L.series_r.push_back(series_elems);
+        L.stat_r.push_back(n_series);
+        const size_t nr = static_cast<size_t>(n_out / r.D);
+        series_elems += static_cast<size_t>(p->n_sb) * r.n_dm * nr;
+        n_series += static_cast<size_t>(p->n_sb) * r.n_dm;
+    }
+    L.series_bytes = series_elems * sizeof(int32_t);
+    L.stat_bytes = n_series * 2 * sizeof(unsigned long long);
+    size_t cur = 0;
+    if (with_series) {
+        L.series = cur;
+        cur = align_up(cur + L.series_bytes, 256);
+    }
+    L.stat = cur;
+    cur = align_up(cur + L.stat_bytes, 256);
+    for (int32_t D : p->ds_factors) {
+        const int64_t pitch = static_cast<int64_t>(align_up(static_cast<size_t>(n_in / D), 8));
+        L.ds_pitch.push_back(pitch);
+        L.ds_off.push_back(cur);
+        cur = align_up(cur + static_cast<size_t>(p->n_tab) * p->n_chan * pitch * sizeof(uint16_t), 256);
+    }
+    L.total = std::max<size_t>(cur, 256);
+    return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fdd_version(void) { return "fdd 0.1 (sm_103a)"; }
+
+const char* fdd_error_string(int code) {
+    switch (code) {
+        case FDD_OK: return "ok";
+        case FDD_ERR_INVALID_ARG: return "invalid argument";
+        case FDD_ERR_SHORT_INPUT: return "input shorter than n_out + maximum delay";
+        case FDD_ERR_NO_MEMORY: return "out of memory";
+        case FDD_ERR_MISALIGNED: return "pointer or pitch not 16-byte aligned";
+        case FDD_ERR_UNSUPPORTED: return "plan outside the kernels' limits";
+        case FDD_ERR_CUDA: return "CUDA runtime error";
+        case FDD_ERR_WORKSPACE: return "workspace too small";
+        default: return "unknown error";
+    }
+}
+
+const char* fdd_last_error_message(void) { return g_last_error.c_str(); }
+
+int fdd_plan_create(const fdd_plan_desc* desc, const int16_t* sb_map_host, fdd_plan** out) {
+    if (!desc || !sb_map_host || !out) return fail(FDD_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (desc->n_tab < 1 || desc->n_tab > FDD_MAX_TABS || desc->n_chan < 1 || desc->n_chan > FDD_MAX_CHANNELS ||
+        desc->n_sb < 1 || desc->n_range < 1 || !desc->ranges || !desc->chan_freq_mhz || !(desc->t_samp_s > 0))
+        return fail(FDD_ERR_INVALID_ARG, "bad plan dimensions");
+    for (int c = 0; c < desc->n_chan; c++)
+        if (!(desc->chan_freq_mhz[c] > 0) || !std::isfinite(desc->chan_freq_mhz[c]))
+            return fail(FDD_ERR_INVALID_ARG, "channel frequencies must be positive and finite");
+    for (int64_t k = 0; k < static_cast<int64_t>(desc->n_sb) * desc->n_chan; k++)
+        if (sb_map_host[k] < 0 || sb_map_host[k] >= desc->n_tab)
+            return fail(FDD_ERR_INVALID_ARG, "sb_map entry outside [0, n_tab)");
+
+    fdd_plan* p = new (std::nothrow) fdd_plan();
+    if (!p) return fail(FDD_ERR_NO_MEMORY, "host allocation");
+    cudaGetDevice(&p->device);
+    p->n_tab = desc->n_tab;
+    p->n_chan = desc->n_chan;
+    p->n_sb = desc->n_sb;
+    p->t_samp = desc->t_samp_s;
+    p->thr = desc->snr_thresh;
+    p->freq.assign(desc->chan_freq_mhz, desc->chan_freq_mhz + desc->n_chan);
+    p->sb_map.assign(sb_map_host, sb_map_host + static_cast<size_t>(desc->n_sb) * desc->n_chan);
+    const double f_top = *std::max_element(p->freq.begin(), p->freq.end());
+
+    int32_t dm_index = 0;
+    for (int ri = 0; ri < desc->n_range; ri++) {
+        const fdd_range& in = desc->ranges[ri];
+        if (!(in.dm0 >= 0) || !(in.ddm > 0) || in.n_dm < 1 || in.downsamp < 1 || in.downsamp > 257 ||
+            in.n_width < 1 || in.n_width > FDD_MAX_WIDTHS || !in.widths) {
+            fdd_plan_destroy(p);
+            return fail(FDD_ERR_INVALID_ARG, "bad DM range");
+        }
+        RangeState r;
+        r.dm0 = in.dm0;
+        r.ddm = in.ddm;
+        r.n_dm = in.n_dm;
+        r.D = in.downsamp;
+        r.n_width = in.n_width;
+        r.wmax = 1;
+        for (int k = 0; k < in.n_width; k++) {
+            if (in.widths[k] < 1 || in.widths[k] > FDD_MAX_WIDTH) {
+                fdd_plan_destroy(p);
+                return fail(FDD_ERR_INVALID_ARG, "boxcar width outside [1, FDD_MAX_WIDTH]");
+            }
+            r.widths[k] = in.widths[k];
+            r.wmax = std::max(r.wmax, in.widths[k]);
+        }
+        r.dm_index0 = dm_index;
+        dm_index += in.n_dm;
+        // Delay table: cold-plasma law, FP64, same operation order for every
+        // entry, rounded half away from zero.
+        r.delay.resize(static_cast<size_t>(r.n_dm) * p->n_chan);
+        int64_t dmax = 0;
+        for (int i = 0; i < r.n_dm; i++) {
+            const double dm = r.dm0 + static_cast<double>(i) * r.ddm;
+            for (int c = 0; c < p->n_chan; c++) {
+                const double f = p->freq[c];
+                const double x = ((kDispersionConstant * dm) * (1.0 / (f * f) - 1.0 / (f_top * f_top))) /
+                                 (static_cast<double>(r.D) * p->t_samp);
+                const long long d = std::llround(x);
+                if (d < 0 || d > (1LL << 28)) {
+                    fdd_plan_destroy(p);
+                    return fail(FDD_ERR_UNSUPPORTED, "delay out of range");
+                }
+                r.delay[static_cast<size_t>(i) * p->n_chan + c] = static_cast<int32_t>(d);
+                dmax = std::max<int64_t>(dmax, d);
+            }
+        }
+        r.dmax = static_cast<int32_t>(dmax);
+        p->max_delay_native = std::max<int64_t>(p->max_delay_native, dmax * r.D);
+        p->ranges.push_back(std::move(r));
+        if (in.downsamp > 1 &&
+            std::find(p->ds_factors.begin(), p->ds_factors.end(), in.downsamp) == p->ds_factors.end())
+            p->ds_factors.push_back(in.downsamp);
+    }
+    p->n_dm_total = dm_index;
+
+    cudaError_t e = cudaMalloc(&p->d_sb_map, p->sb_map.size() * sizeof(int16_t));
+    if (e != cudaSuccess) {
+        fdd_plan_destroy(p);
+        return cuda_fail(e, "cudaMalloc(sb_map)");
+    }
+    e = cudaMemcpy(p->d_sb_map, p->sb_map.data(), p->sb_map.size() * sizeof(int16_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        fdd_plan_destroy(p);
+        return cuda_fail(e, "cudaMemcpy(sb_map)");
+    }
+    for (RangeState& r : p->ranges) {
+        const int rc = configure_range(p, r, default_variant(r.D == 1 ? 1 : 2));
+        if (rc != FDD_OK) {
+            fdd_plan_destroy(p);
+            return rc;
+        }
+    }
+    *out = p;
+    return FDD_OK;
+}
+
+int fdd_plan_destroy(fdd_plan* plan) {
+    if (!plan) return FDD_OK;
+    for (cudaEvent_t e : plan->ev) cudaEventDestroy(e);
+    for (RangeState& r : plan->ranges) free_range_tables(r);
+    if (plan->d_sb_map) cudaFree(plan->d_sb_map);
+    delete plan;
+    return FDD_OK;
+}
+
+int fdd_plan_max_delay(const fdd_plan* plan, int64_t* max_delay_native) {
+    if (!plan || !max_delay_native) return fail(FDD_ERR_INVALID_ARG, "null argument");
+    *max_delay_native = plan->max_delay_native;
+    return FDD_OK;
+}
+
+int fdd_plan_total_dms(const fdd_plan* plan, int64_t* n_dm_total) {
+    if (!plan || !n_dm_total) return fail(FDD_ERR_INVALID_ARG, "null argument");
+    *n_dm_total = plan->n_dm_total;
+    return FDD_OK;
+}
+
+int fdd_plan_delays(const fdd_plan* plan, int32_t r, int32_t* dst) {
+    if (!plan || !dst || r < 0 || r >= static_cast<int32_t>(plan->ranges.size()))
+        return fail(FDD_ERR_INVALID_ARG, "bad range index");
+    const RangeState& rs = plan->ranges[r];
+    std::memcpy(dst, rs.delay.data(), rs.delay.size() * sizeof(int32_t));
+    return FDD_OK;
+}
+
+int fdd_workspace_size(const fdd_plan* plan, int64_t n_in, int64_t n_out, int32_t with_series, size_t* bytes) {
+    if (!plan || !bytes || n_in < 0 || n_out < 0) return fail(FDD_ERR_INVALID_ARG, "bad argument");
+    *bytes = make_layout(plan, n_in, n_out, with_series != 0).total;
+    return FDD_OK;
+}
+
+int fdd_series_size(const fdd_plan* plan, int64_t n_out, size_t* bytes) {
+    if (!plan || !bytes || n_out < 0) return fail(FDD_ERR_INVALID_ARG, "bad argument");
+    *bytes = make_layout(plan, 0, n_out, true).series_bytes;
+    return FDD_OK;
+}
+
+int fdd_search(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitch, int64_t n_out,
+               int64_t t_offset_native, void* d_workspace, size_t workspace_bytes, fdd_candidate* d_cands,
+               int64_t cap, uint64_t* d_count, int32_t* d_series, fdd_stream_t stream) {
+    if (!plan || !d_tabs || !d_workspace || !d_count || (cap > 0 && !d_cands) || cap < 0 || n_in < 0 ||
+        n_out < 0 || pitch < n_in)
+        return fail(FDD_ERR_INVALID_ARG, "bad search argument");
+    if (n_out > (1LL << 30) || n_in > (1LL << 31) - 64)
+        return fail(FDD_ERR_UNSUPPORTED, "chunk longer than the kernels' 32-bit sample indexing");
+    if ((reinterpret_cast<uintptr_t>(d_tabs) & 15) || (pitch & 15) ||
+        (reinterpret_cast<uintptr_t>(d_workspace) & 255) || (reinterpret_cast<uintptr_t>(d_series) & 15))
+        return fail(FDD_ERR_MISALIGNED, "d_tabs/pitch must be 16-byte aligned, workspace 256-byte aligned");
+    for (const RangeState& r : plan->ranges)
+        if (n_out / r.D + r.dmax > n_in / r.D)
+            return fail(FDD_ERR_SHORT_INPUT, "n_in < n_out + max delay for some DM range");
+    const bool own_series = (d_series == nullptr);
+    const Layout L = make_layout(plan, n_in, n_out, own_series);
+    if (workspace_bytes < L.total) return fail(FDD_ERR_WORKSPACE, "workspace smaller than fdd_workspace_size()");
+
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    uint8_t* ws = static_cast<uint8_t*>(d_workspace);
+    plan->st_kind.clear();
+    plan->st_range.clear();
+    // Record an event pair around one stage when timing is on.
+    auto stage_begin = [&](int kind, int range) -> cudaError_t {
+        if (!plan->timing) return cudaSuccess;
+        const size_t k = plan->st_kind.size();
+        while (plan->ev.size() < 2 * (k + 1)) {
+            cudaEvent_t e;
+            const cudaError_t err = cudaEventCreate(&e);
+            if (err != cudaSuccess) return err;
+            plan->ev.push_back(e);
+        }
+        plan->st_kind.push_back(kind);
+        plan->st_range.push_back(range);
+        return cudaEventRecord(plan->ev[2 * k], s);
+    };
+    auto stage_end = [&]() -> cudaError_t {
+        if (!plan->timing) return cudaSuccess;
+        return cudaEventRecord(plan->ev[2 * (plan->st_kind.size() - 1) + 1], s);
+    };
+    int32_t* series = own_series ? reinterpret_cast<int32_t*>(ws + L.series) : d_series;
+    unsigned long long* stat = reinterpret_cast<unsigned long long*>(ws + L.stat);
+
+    cudaError_t e = cudaMemsetAsync(stat, 0, L.stat_bytes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(stat)");
+    e = cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(count)");
+
+    for (size_t k = 0; k < plan->ds_factors.size(); k++) {
+        if ((e = stage_begin(0, plan->ds_factors[k])) != cudaSuccess) return cuda_fail(e, "timing event");
+        e = fdd::launch_downsample(d_tabs, static_cast<int64_t>(plan->n_tab) * plan->n_chan, n_in, pitch,
+                                   plan->ds_factors[k], reinterpret_cast<uint16_t*>(ws + L.ds_off[k]),
+                                   L.ds_pitch[k], s);
+        if (e != cudaSuccess) return cuda_fail(e, "downsample launch");
+        if ((e = stage_end()) != cudaSuccess) return cuda_fail(e, "timing event");
+    }
+
+    for (size_t ri = 0; ri < plan->ranges.size(); ri++) {
+        const RangeState& r = plan->ranges[ri];
+        const int64_t nr = n_out / r.D;
+        if (nr == 0) continue;
+        fdd::DedispArgs a{};
+        if (r.D == 1) {
+            a.in = d_tabs;
+            a.pitch_bytes = pitch;
+        } else {
+            const size_t k = std::find(plan->ds_factors.begin(), plan->ds_factors.end(), r.D) - plan->ds_factors.begin();
+            a.in = ws + L.ds_off[k];
+            a.pitch_bytes = L.ds_pitch[k] * 2;
+        }
+        a.n_valid = n_in / r.D;
+        a.sb_map = plan->d_sb_map;
+        a.base = r.d_base;
+        a.off = r.d_off;
+        a.series = series + L.series_r[ri];
+        a.stat = stat + 2 * L.stat_r[ri];
+        a.n_chan = plan->n_chan;
+        a.n_dm = r.n_dm;
+        a.n_out = static_cast<int32_t>(nr);
+        a.n_sb = plan->n_sb;
+        a.Lw = r.Lw;
+        a.CC = r.CC;
+        if ((e = stage_begin(1, static_cast<int>(ri))) != cudaSuccess) return cuda_fail(e, "timing event");
+        e = fdd::launch_dedisp(r.variant, a, s);
+        if (e != cudaSuccess) return cuda_fail(e, "dedispersion launch");
+        if ((e = stage_end()) != cudaSuccess) return cuda_fail(e, "timing event");
+
+        fdd::BoxcarArgs b{};
+        b.series = a.series;
+        b.stat = a.stat;
+        b.cands = d_cands;
+        b.count = reinterpret_cast<unsigned long long*>(d_count);
+        b.cap = cap;
+        b.t_offset = t_offset_native;
+        b.dm0 = r.dm0;
+        b.ddm = r.ddm;
+        b.n_sb = plan->n_sb;
+        b.n_dm = r.n_dm;
+        b.n_out = static_cast<int32_t>(nr);
+        b.dm_index0 = r.dm_index0;
+        b.D = r.D;
+        b.n_width = r.n_width;
+        b.wmax = r.wmax;
+        b.thr = plan->thr;
+        for (int k = 0; k < r.n_width; k++) {
+            b.widths[k] = r.widths[k];
+            b.inv_sqrt_w[k] = static_cast<float>(1.0 / std::sqrt(static_cast<double>(r.widths[k])));
+        }
+        if ((e = stage_begin(2, static_cast<int>(ri))) != cudaSuccess) return cuda_fail(e, "timing event");
+        e = fdd::launch_boxcar(b, s);
+        if (e != cudaSuccess) return cuda_fail(e, "boxcar launch");
+        if ((e = stage_end()) != cudaSuccess) return cuda_fail(e, "timing event");
+    }
+    return FDD_OK;
+}
+
+int fdd_plan_set_timing(fdd_plan* plan, int32_t enable) {
+    if (!plan) return fail(FDD_ERR_INVALID_ARG, "null plan");
+    plan->timing = enable != 0;
+    return FDD_OK;
+}
+
+int fdd_plan_stage_times(fdd_plan* plan, int32_t max_n, int32_t* kind, int32_t* range, float* ms,
+                         int32_t* n_stages) {
+    if (!plan || !n_stages || max_n < 0 || (max_n > 0 && (!kind || !range || !ms)))
+        return fail(FDD_ERR_INVALID_ARG, "bad argument");
+    const int32_t n = static_cast<int32_t>(plan->st_kind.size());
+    *n_stages = n;
+    for (int32_t k = 0; k < n && k < max_n; k++) {
+        kind[k] = plan->st_kind[k];
+        range[k] = plan->st_range[k];
+        const cudaError_t e = cudaEventElapsedTime(&ms[k], plan->ev[2 * k], plan->ev[2 * k + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "stage timing not ready");
+    }
+    return FDD_OK;
+}
+
+int fdd_downsample_u8(const uint8_t* d_in, int64_t n_rows, int64_t n_in, int64_t in_pitch, int32_t downsamp,
+                      uint16_t* d_out, int64_t out_pitch, fdd_stream_t stream) {
+    if (!d_in || !d_out || n_rows < 0 || n_in < 0 || in_pitch < n_in || downsamp < 1 || downsamp > 257 ||
+        out_pitch < n_in / downsamp)
+        return fail(FDD_ERR_INVALID_ARG, "bad downsample argument");
+    if ((reinterpret_cast<uintptr_t>(d_in) & 15) || (reinterpret_cast<uintptr_t>(d_out) & 15) || (in_pitch & 15) ||
+        (out_pitch & 7))
+        return fail(FDD_ERR_MISALIGNED, "downsample buffers must be 16-byte aligned, out_pitch a multiple of 8");
+    cudaError_t e = fdd::launch_downsample(d_in, n_rows, n_in, in_pitch, downsamp, d_out, out_pitch,
+                                           reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "downsample launch");
+    return FDD_OK;
+}
+
+}  // extern "C"

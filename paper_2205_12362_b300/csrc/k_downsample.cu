@@ -1,0 +1,106 @@
+// k_downsample.cu -- time downsampling of 8-bit filterbank rows.
+//
+// Paper Sec. "Downsampling": reduce the time resolution before dedispersion,
+// used for high-DM ranges where intra-channel smearing already exceeds the
+// native sampling time.  out[r][j] = sum_{k<D} in[r][j*D + k] for
+// j < floor(n_in / D); exact uint16 sums (D <= 257), bins aligned to input
+// sample 0.  Done on the TABs, before the SB gather: gather and time sums
+// commute, and there are fewer TAB rows than SB rows.
+//
+// HBM-bound: each thread reads 8*D consecutive bytes with 16-byte (or 8-byte
+// for D = 1) vector loads and writes 8 uint16 with one 16-byte store; rows
+// ride on gridDim.y.  Ragged tails and D not dividing 16 take a scalar path.
+#include "fdd_internal.cuh"
+
+namespace fdd {
+
+namespace {
+
+template <int D>
+__device__ __forceinline__ void sum8_vec(const uint8_t* src, uint16_t* dst) {
+    uint32_t s[8];
+    if constexpr (D == 1) {
+        const uint2 v = *reinterpret_cast<const uint2*>(src);
+        const uint32_t w[2] = {v.x, v.y};
+#pragma unroll
+        for (int j = 0; j < 8; j++) s[j] = (w[j >> 2] >> (8 * (j & 3))) & 0xFFu;
+    } else {
+        constexpr int NV = (8 * D) / 16;  // uint4 loads
+        uint32_t w[4 * NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            const uint4 x = *reinterpret_cast<const uint4*>(src + 16 * v);
+            w[4 * v + 0] = x.x; w[4 * v + 1] = x.y; w[4 * v + 2] = x.z; w[4 * v + 3] = x.w;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            uint32_t acc = 0;
+#pragma unroll
+            for (int k = 0; k < D; k++) {
+                const int b = j * D + k;
+                acc += (w[b >> 2] >> (8 * (b & 3))) & 0xFFu;
+            }
+            s[j] = acc;
+        }
+    }
+    uint4 o;
+    o.x = s[0] | (s[1] << 16);
+    o.y = s[2] | (s[3] << 16);
+    o.z = s[4] | (s[5] << 16);
+    o.w = s[6] | (s[7] << 16);
+    *reinterpret_cast<uint4*>(dst) = o;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_downsample(const uint8_t* __restrict__ in, int64_t in_pitch, int64_t n_in,
+                                                    int runtime_d, uint16_t* __restrict__ out, int64_t out_pitch) {
+    const int64_t row = blockIdx.y;
+    const int dd = (D > 0) ? D : runtime_d;
+    const int64_t n_y = n_in / dd;
+    const int64_t j0 = 8 * (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
+    if (j0 >= n_y) return;
+    const uint8_t* src = in + row * in_pitch;
+    uint16_t* dst = out + row * out_pitch;
+    if constexpr (D > 0) {
+        if (j0 + 8 <= n_y) {
+            sum8_vec<D>(src + j0 * D, dst + j0);
+            return;
+        }
+    }
+    const int64_t jn = min(j0 + 8, n_y);
+    for (int64_t j = j0; j < jn; j++) {
+        uint32_t acc = 0;
+        for (int k = 0; k < dd; k++) acc += src[j * dd + k];
+        dst[j] = static_cast<uint16_t>(acc);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_downsample(const uint8_t* in, int64_t n_rows, int64_t n_in, int64_t in_pitch, int D,
+                              uint16_t* out, int64_t out_pitch, cudaStream_t s) {
+    const int64_t n_y = n_in / D;
+    if (n_rows == 0 || n_y == 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t per_block = 8LL * threads;
+    const int64_t kMaxRows = 65535;  // gridDim.y limit
+    for (int64_t r0 = 0; r0 < n_rows; r0 += kMaxRows) {
+        const int64_t nr = n_rows - r0 < kMaxRows ? n_rows - r0 : kMaxRows;
+        const uint8_t* src = in + r0 * in_pitch;
+        uint16_t* dst = out + r0 * out_pitch;
+        dim3 grid(static_cast<unsigned>((n_y + per_block - 1) / per_block), static_cast<unsigned>(nr));
+        switch (D) {
+            case 1: k_downsample<1><<<grid, threads, 0, s>>>(src, in_pitch, n_in, D, dst, out_pitch); break;
+            case 2: k_downsample<2><<<grid, threads, 0, s>>>(src, in_pitch, n_in, D, dst, out_pitch); break;
+            case 4: k_downsample<4><<<grid, threads, 0, s>>>(src, in_pitch, n_in, D, dst, out_pitch); break;
+            case 8: k_downsample<8><<<grid, threads, 0, s>>>(src, in_pitch, n_in, D, dst, out_pitch); break;
+            case 16: k_downsample<16><<<grid, threads, 0, s>>>(src, in_pitch, n_in, D, dst, out_pitch); break;
+            default: k_downsample<0><<<grid, threads, 0, s>>>(src, in_pitch, n_in, D, dst, out_pitch); break;
+        }
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace fdd

@@ -1,0 +1,68 @@
+"""CPU-side checks of the C ABI: the library builds, loads, exports every
+function include/fdd.h declares, and rejects bad plans on the host before any
+device work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "fdd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fdd_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2205_12362_b300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = header_functions()
+    for must in ("fdd_plan_create", "fdd_plan_destroy", "fdd_search", "fdd_workspace_size",
+                 "fdd_downsample_u8", "fdd_error_string"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in header_functions():
+        assert hasattr(lib, name), name
+
+
+def test_error_strings_and_version(lib):
+    lib.fdd_error_string.restype = ctypes.c_char_p
+    lib.fdd_version.restype = ctypes.c_char_p
+    assert lib.fdd_error_string(0) == b"ok"
+    assert b"short" in lib.fdd_error_string(-2).lower() or b"input" in lib.fdd_error_string(-2).lower()
+    assert b"sm_103a" in lib.fdd_version()
+
+
+def test_host_rejects_bad_plans(lib):
+    import paper_2205_12362_b300 as fdd
+    f = np.linspace(1220, 1520, 8)
+    good = [dict(dm0=0.0, ddm=1.0, n_dm=4, downsamp=1, widths=[1, 2])]
+    with pytest.raises(fdd.FddError) as e:   # TAB index out of range
+        fdd.Plan(2, 8, 1, f, 81.92e-6, good, 8.0, np.full((1, 8), 2))
+    assert e.value.code == -1
+    with pytest.raises(fdd.FddError):        # negative DM step
+        fdd.Plan(1, 8, 1, f, 81.92e-6, [dict(dm0=0.0, ddm=-1.0, n_dm=4, widths=[1])], 8.0, np.zeros((1, 8)))
+    with pytest.raises(fdd.FddError):        # width beyond the limit
+        fdd.Plan(1, 8, 1, f, 81.92e-6, [dict(dm0=0.0, ddm=1.0, n_dm=4, widths=[5000])], 8.0, np.zeros((1, 8)))
+    with pytest.raises(fdd.FddError):        # non-positive frequency
+        fdd.Plan(1, 8, 1, np.zeros(8), 81.92e-6, good, 8.0, np.zeros((1, 8)))
+    with pytest.raises(ValueError):          # sb_map shape
+        fdd.Plan(1, 8, 2, f, 81.92e-6, good, 8.0, np.zeros((1, 8)))
+
+
+def test_candidate_record_layout():
+    import paper_2205_12362_b300 as fdd
+    assert fdd.CAND_DTYPE.itemsize == 32
+    assert [fdd.CAND_DTYPE.fields[k][1] for k in ("sb", "dm_index", "downsamp", "width_native",
+                                                  "t_native", "dm", "snr")] == [0, 4, 8, 12, 16, 24, 28]

@@ -1,0 +1,237 @@
+"""CUDA path vs the oracle, element by element, through the C ABI.
+
+Tolerances: dedispersed series bit-exact (exact integer sums on both sides);
+S/N within 1e-4 relative (floor 1) of the FP64 oracle; candidate sets equal
+after ignoring candidates whose oracle S/N is within 1e-3 of the threshold
+(see tests/_cmp.py)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests._cmp import compare_candidates, oracle_candidate_superset
+
+pytestmark = pytest.mark.gpu
+
+T_SAMP = synth.ARTS_T_SAMP_S
+
+
+@pytest.fixture(scope="module")
+def fdd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2205_12362_b300 as m
+    return m
+
+
+def to_dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def run_both(fdd, x, sb_map, freqs, ranges, thr, n_out, n_in, t_offset=0, cap=1 << 20):
+    n_tab, n_chan, _ = x.shape
+    plan = fdd.Plan(n_tab, n_chan, sb_map.shape[0], freqs, T_SAMP, ranges, thr, sb_map)
+    res = plan.search(to_dev(x), n_in, n_out, t_offset=t_offset, cap=cap, want_series=True)
+    import torch
+    torch.cuda.synchronize()
+    gpu, n = res.candidates()
+    assert n == len(gpu), "GPU candidate buffer overflowed (cap %d, count %d)" % (cap, n)
+    g_series = [s.cpu().numpy() for s in plan.series_views(res.series, n_out)]
+    ora, o_series = oracle_candidate_superset(x, sb_map, freqs, T_SAMP, ranges, thr, n_out, n_in,
+                                              t_offset=t_offset, return_series=True)
+    return plan, gpu, g_series, ora, o_series
+
+
+def tiny_config():
+    n_chan, n_out = 128, 4096
+    f = synth.channel_freqs(n_chan)
+    d = oracle.delays(f, T_SAMP, 0.0, 1.0, 256)
+    n_in = n_out + int(d.max())
+    start = 1500 + oracle.delays(f, T_SAMP, 100.0, 1.0, 1)[0]
+    x = synth.filterbank(1, 1, n_chan, n_in, pulses=[dict(tab=0, start=start, width=4, amp=24.0)])
+    ranges = [dict(dm0=0.0, ddm=1.0, n_dm=256, downsamp=1, widths=[1, 2, 4, 8, 16])]
+    return x, f, ranges, n_in, n_out
+
+
+def test_tiny_plain_search(fdd):
+    x, f, ranges, n_in, n_out = tiny_config()
+    sb = np.zeros((1, 128), np.int16)
+    plan, gpu, gs, ora, os_ = run_both(fdd, x, sb, f, ranges, 8.0, n_out, n_in)
+    assert (gs[0] == os_[0]).all()
+    assert compare_candidates(gpu, ora, 8.0) > 0
+    best = gpu[np.argmax(gpu["snr"])]
+    assert abs(int(best["dm_index"]) - 100) <= 2
+
+
+def test_library_delay_table_matches_oracle(fdd):
+    f = synth.channel_freqs(1536)
+    ranges = [dict(dm0=0.0, ddm=0.2, n_dm=2048, downsamp=1, widths=[1]),
+              dict(dm0=409.6, ddm=0.8, n_dm=1024, downsamp=2, widths=[1]),
+              dict(dm0=2867.2, ddm=3.2, n_dm=667, downsamp=8, widths=[1])]
+    plan = fdd.Plan(1, 1536, 1, f, T_SAMP, ranges, 8.0, np.zeros((1, 1536)))
+    for r, rg in enumerate(ranges):
+        want = oracle.delays(f, T_SAMP, rg["dm0"], rg["ddm"], rg["n_dm"], rg["downsamp"])
+        assert (plan.delays(r) == want).all()
+    assert plan.max_delay == max(int(oracle.delays(f, T_SAMP, rg["dm0"], rg["ddm"], rg["n_dm"],
+                                                   rg["downsamp"]).max()) * rg["downsamp"] for rg in ranges)
+
+
+@pytest.mark.parametrize("seed,n_chan,n_out", [(0, 37, 1001), (1, 64, 777), (2, 300, 2050), (3, 16, 96)])
+def test_multi_range_sb_gather_ragged(fdd, seed, n_chan, n_out):
+    rng = np.random.default_rng(seed)
+    n_tab, n_sb = 3, 5
+    f = synth.channel_freqs(n_chan)
+    ranges = [dict(dm0=0.0, ddm=2.0, n_dm=19, downsamp=1, widths=[1, 2, 4, 64]),
+              dict(dm0=38.0, ddm=4.0, n_dm=7, downsamp=2, widths=[1, 3, 8]),
+              dict(dm0=66.0, ddm=6.0, n_dm=9, downsamp=3, widths=[2, 5]),
+              dict(dm0=120.0, ddm=8.0, n_dm=33, downsamp=4, widths=[1, 16]),
+              dict(dm0=384.0, ddm=16.0, n_dm=5, downsamp=8, widths=[1, 2, 500])]
+    need = max(int(oracle.delays(f, T_SAMP, r["dm0"], r["ddm"], r["n_dm"], r["downsamp"]).max())
+               * r["downsamp"] + (n_out // r["downsamp"]) * r["downsamp"] for r in ranges)
+    n_in = need + int(rng.integers(0, 9))
+    x = synth.filterbank(seed + 100, n_tab, n_chan, n_in)
+    sb = rng.integers(0, n_tab, size=(n_sb, n_chan)).astype(np.int16)
+    plan, gpu, gs, ora, os_ = run_both(fdd, x, sb, f, ranges, 3.0, n_out, n_in, t_offset=12345)
+    for r in range(len(ranges)):
+        assert gs[r].shape == os_[r].shape
+        assert (gs[r] == os_[r]).all(), "series of range %d differ" % r
+    assert compare_candidates(gpu, ora, 3.0) > 10
+
+
+def test_swar_flush_saturated(fdd):
+    # 600 channels of 255 (more than 257 channels per 16-bit lane) plus noise rows
+    n_chan, n_out = 600, 700
+    f = synth.channel_freqs(n_chan)
+    ranges = [dict(dm0=0.0, ddm=1.0, n_dm=40, downsamp=1, widths=[1]),
+              dict(dm0=40.0, ddm=2.0, n_dm=20, downsamp=8, widths=[1])]
+    need = max(int(oracle.delays(f, T_SAMP, r["dm0"], r["ddm"], r["n_dm"], r["downsamp"]).max())
+               * r["downsamp"] + n_out for r in ranges)
+    x = np.full((2, n_chan, synth.padded_pitch(need)), 255, np.uint8)
+    x[1] = synth.filterbank(5, 1, n_chan, need, pitch=x.shape[2])[0]
+    sb = np.zeros((3, n_chan), np.int16)
+    sb[1] = 1
+    sb[2, ::2] = 1
+    plan, gpu, gs, ora, os_ = run_both(fdd, x, sb, f, ranges, 8.0, n_out, need)
+    assert (gs[0][0] == 255 * n_chan).all()
+    assert (gs[1][0] == 255 * 8 * n_chan).all()
+    for r in range(2):
+        assert (gs[r] == os_[r]).all()
+    compare_candidates(gpu, ora, 8.0)
+
+
+@pytest.mark.parametrize("D", [1, 2, 3, 4, 8, 16])
+def test_downsample_stage(fdd, D):
+    rng = np.random.default_rng(D)
+    n_in = 1000 + D
+    x = rng.integers(0, 256, size=(3, 5, synth.padded_pitch(n_in)), dtype=np.int64).astype(np.uint8)
+    out = fdd.downsample_u8(to_dev(x), n_in, D)
+    got = out.cpu().numpy().view(np.uint16)[..., : n_in // D]
+    want = oracle.downsample(x, D, n_in=n_in)
+    assert (got == want).all()
+
+
+def arts_single_sb():
+    n_chan, n_out = 1536, synth.ARTS_CHUNK
+    f = synth.channel_freqs(n_chan)
+    d = oracle.delays(f, T_SAMP, 0.0, 0.2, 2048)
+    n_in = n_out + int(d.max())
+    prm = synth.random_pulses(2, 10, [0], 50.0, 400.0, [1, 2, 4, 8, 16, 32], 8.0, 50.0, 200, n_out - 200)
+    pulses = []
+    for p in prm:
+        dm_grid = round(p["dm"] / 0.2) * 0.2
+        start = p["t0"] + oracle.delays(f, T_SAMP, dm_grid, 1.0, 1)[0]
+        pulses.append(dict(tab=0, start=start, width=p["width"],
+                           amp=synth.pulse_amplitude(p["snr"], n_chan, p["width"])))
+    x = synth.filterbank(2, 1, n_chan, n_in, pulses=pulses)
+    ranges = [dict(dm0=0.0, ddm=0.2, n_dm=2048, downsamp=1, widths=[1, 2, 4, 8, 16, 32, 64])]
+    return x, f, ranges, n_in, n_out, prm
+
+
+def test_arts_single_sb_full_size(fdd):
+    x, f, ranges, n_in, n_out, prm = arts_single_sb()
+    plan, gpu, gs, ora, os_ = run_both(fdd, x, np.zeros((1, 1536), np.int16), f, ranges, 8.0, n_out, n_in)
+    assert (gs[0] == os_[0]).all()
+    n = compare_candidates(gpu, ora, 8.0)
+    assert n > 0
+    # recall: every injected pulse is found near its DM and time
+    for p in prm:
+        near = gpu[(np.abs(gpu["dm"] - p["dm"]) < 2.0) & (np.abs(gpu["t_native"] - p["t0"]) < 64)]
+        assert len(near) > 0, p
+
+
+def test_fused_71_sb_sampled(fdd):
+    import torch
+    n_tab, n_chan, n_sb, n_out = 12, 1536, 71, synth.ARTS_CHUNK
+    f = synth.channel_freqs(n_chan)
+    ranges = [dict(dm0=0.0, ddm=0.2, n_dm=2048, downsamp=1, widths=[1, 2, 4, 8, 16, 32, 64])]
+    n_in = n_out + int(oracle.delays(f, T_SAMP, 0.0, 0.2, 2048).max())
+    prm = synth.random_pulses(3, 5, [0, 3, 5, 8, 11], 50.0, 400.0, [1, 4, 16], 10.0, 40.0, 300, n_out - 300)
+    pulses = [dict(tab=p["tab"], start=p["t0"] + oracle.delays(f, T_SAMP, p["dm"], 1.0, 1)[0],
+                   width=p["width"], amp=synth.pulse_amplitude(p["snr"], n_chan, p["width"])) for p in prm]
+    x = synth.filterbank(3, n_tab, n_chan, n_in, pulses=pulses)
+    sb = synth.sb_map_piecewise(3, n_sb, n_chan, n_tab).astype(np.int16)
+    plan = fdd.Plan(n_tab, n_chan, n_sb, f, T_SAMP, ranges, 8.0, sb)
+    res = plan.search(to_dev(x), n_in, n_out, cap=1 << 21, want_series=True)
+    torch.cuda.synchronize()
+    gpu, n = res.candidates()
+    assert n == len(gpu)
+    series = plan.series_views(res.series, n_out)[0]
+    rng = np.random.default_rng(0)
+    for s in sorted(set([0, 70] + rng.integers(1, 70, size=1).tolist())):
+        ora, os_ = oracle_candidate_superset(x, sb[s:s + 1], f, T_SAMP, ranges, 8.0, n_out, n_in,
+                                             return_series=True)
+        dms = rng.integers(0, 2048, size=64)
+        assert (series[s, dms].cpu().numpy() == os_[0][0, dms]).all()
+        ora = ora.copy()
+        ora["sb"] = s
+        compare_candidates(gpu[gpu["sb"] == s], ora, 8.0)
+
+
+def test_overflow_reports_true_count(fdd):
+    import torch
+    x, f, ranges, n_in, n_out = tiny_config()
+    plan = fdd.Plan(1, 128, 1, f, T_SAMP, ranges, 3.0, np.zeros((1, 128)))
+    full = plan.search(to_dev(x), n_in, n_out, cap=1 << 20)
+    torch.cuda.synchronize()
+    all_c, n = full.candidates()
+    assert n > 100
+    small = plan.search(to_dev(x), n_in, n_out, cap=50)
+    torch.cuda.synchronize()
+    part, n2 = small.candidates()
+    assert n2 == n and len(part) == 50
+    full_set = set(map(tuple, np.stack([all_c["dm_index"], all_c["width_native"], all_c["t_native"]], 1).tolist()))
+    assert set(map(tuple, np.stack([part["dm_index"], part["width_native"], part["t_native"]], 1).tolist())) <= full_set
+
+
+def test_host_errors(fdd):
+    import torch
+    x, f, ranges, n_in, n_out = tiny_config()
+    plan = fdd.Plan(1, 128, 1, f, T_SAMP, ranges, 8.0, np.zeros((1, 128)))
+    dx = to_dev(x)
+    with pytest.raises(fdd.FddError) as e:
+        plan.search(dx, n_in - 1, n_out)
+    assert e.value.code == -2
+    odd = torch.zeros((1, 128, x.shape[2] + 4), dtype=torch.uint8, device="cuda")
+    with pytest.raises(fdd.FddError) as e:
+        plan.search(odd, n_in, n_out)
+    assert e.value.code == -4
+    ws = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(fdd.FddError) as e:
+        plan.search(dx, n_in, n_out, workspace=ws)
+    assert e.value.code == -7
+
+
+def test_repeat_is_deterministic(fdd):
+    import torch
+    x, f, ranges, n_in, n_out = tiny_config()
+    plan = fdd.Plan(1, 128, 1, f, T_SAMP, ranges, 6.0, np.zeros((1, 128)))
+    dx = to_dev(x)
+    a = plan.search(dx, n_in, n_out, want_series=True)
+    b = plan.search(dx, n_in, n_out, want_series=True)
+    torch.cuda.synchronize()
+    assert torch.equal(a.series, b.series)
+    ca, na = a.candidates()
+    cb, nb = b.candidates()
+    assert na == nb and (ca == cb).all()
