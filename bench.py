@@ -177,9 +177,13 @@ def oracle_sample_rate(x, sb, f, t, w, n_in, target_s):
         oracle.search(x, sb[:1], f, t, rr, w["thr"], w["n_out"], n_in=n_in)
         return units, time.perf_counter() - t0, rr
 
-    u, dt, _ = run(1.0 / 64)
-    frac = min(1.0, (1.0 / 64) * target_s / max(dt, 1e-3))
+    frac = 1.0 / 64
     u, dt, rr = run(frac)
+    for _ in range(4):                       # grow the sample toward target_s of CPU work
+        if dt >= 0.5 * target_s or frac >= 1.0:
+            break
+        frac = min(1.0, frac * 0.9 * target_s / max(dt, 1e-3))
+        u, dt, rr = run(frac)
     desc = "SB 0 of %d, first %s DM trials of each range (%s), full %d-sample chunk, %d channels" % (
         w["n_sb"], "/".join(str(r["n_dm"]) for r in rr), "/".join(str(r["n_dm"]) for r in w["ranges"]),
         w["n_out"], w["n_chan"])
@@ -236,6 +240,9 @@ def run_fdd(args):
     count = torch.zeros(1, dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
     stream = torch.cuda.current_stream()
+    tuned = None
+    if not args.no_autotune:
+        tuned = plan.autotune(tabs, n_in, w["n_out"], reps=3, workspace=ws, stream=stream)
     plan.set_timing(True)
 
     def step():
@@ -257,6 +264,7 @@ def run_fdd(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     wall0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed")
     for _ in range(args.steps):
         flush.zero_()                      # evict the input from L2 between steps
         e0.record(stream)
@@ -268,6 +276,7 @@ def run_fdd(args):
         launches += len(st)
         for name, r, ms in st:
             stage_ms.setdefault("%s[%d]" % (name, r), []).append(ms)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     wall1 = time.perf_counter()
     if dist:
@@ -358,6 +367,7 @@ def run_fdd(args):
         "gpu_launches": launches,
         "clocks": clocks,
         "stages_ms": {k: float(np.mean(v)) for k, v in stage_ms.items()},
+        "kernel_config": [plan.get_config(r) for r in range(len(w["ranges"]))],
         "wall_s": wall1 - wall0,
     }
     if dist:
@@ -411,6 +421,7 @@ def main():
     ap.add_argument("--impl", default="fdd", choices=["fdd", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -168,6 +168,47 @@ int fdd_search(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitc
 int fdd_downsample_u8(const uint8_t* d_in, int64_t n_rows, int64_t n_in, int64_t in_pitch,
                       int32_t downsamp, uint16_t* d_out, int64_t out_pitch, fdd_stream_t stream);
 
+/* Kernel configuration of one DM range's dedispersion launch (the paper's
+ * AMBER picks its kernel configuration per platform and observation by
+ * auto-tuning, Sec. "AMBER"; this library does the same with its own tuner).
+ * Fields: variant index, DM trials per block, output samples per block,
+ * channels per shared-memory stage, threads per block, 32-bit words per
+ * staged row copy, and the mean launch time the tuner measured (ms, 0 if the
+ * range was not tuned). */
+typedef struct {
+    int32_t variant;
+    int32_t dm_per_block;
+    int32_t tile;
+    int32_t chan_per_stage;
+    int32_t threads;
+    int32_t row_words;
+    float tuned_ms;
+} fdd_kernel_config;
+
+/* Number of compiled dedispersion kernel variants (valid variant indices are
+ * 0 .. n-1); *bytes_per_sample of variant v is 1 (native-rate ranges) or 2
+ * (downsampled ranges). */
+int fdd_num_variants(int32_t* n);
+int fdd_variant_info(int32_t variant, int32_t* bytes_per_sample, int32_t* dm_per_block, int32_t* tile,
+                     int32_t* threads);
+
+/* Current kernel configuration of range r. */
+int fdd_plan_get_config(const fdd_plan* plan, int32_t r, fdd_kernel_config* out);
+
+/* Set range r's kernel variant and channels per stage (0 = largest that
+ * fits); rebuilds the range's device tables.  Synchronous.  Errors:
+ * INVALID_ARG (variant for the other sample width), UNSUPPORTED (does not
+ * fit), NO_MEMORY / CUDA. */
+int fdd_plan_set_config(fdd_plan* plan, int32_t r, int32_t variant, int32_t chan_per_stage);
+
+/* Auto-tune every range: time each compatible (variant, channels per stage)
+ * on the given chunk, `reps` launches each, and keep the fastest.  Arguments
+ * as fdd_search; the workspace must be sized with_series = 1.  Synchronous
+ * (returns after the stream has drained); results are reproducible only up
+ * to timing noise. */
+int fdd_plan_autotune(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitch, int64_t n_out,
+                      void* d_workspace, size_t workspace_bytes, int32_t reps, fdd_stream_t stream);
+
 /* Per-stage GPU timing (tracing; the paper reports AMBER's time per stage,
  * Sec. "Computing performance").  With timing enabled, fdd_search records a
  * CUDA event pair around every kernel it enqueues; the pairs are reused by

@@ -18,7 +18,7 @@ import numpy as np
 from .build import LIB as _LIB_PATH
 
 __all__ = ["Plan", "FddError", "FddUnavailable", "CAND_DTYPE", "decode_candidates", "downsample_u8",
-           "library_path", "version"]
+           "library_path", "version", "variants"]
 
 CAND_DTYPE = np.dtype([("sb", np.int32), ("dm_index", np.int32), ("downsamp", np.int32),
                        ("width_native", np.int32), ("t_native", np.int64), ("dm", np.float32),
@@ -46,6 +46,15 @@ class _Range(ctypes.Structure):
     _fields_ = [("dm0", ctypes.c_double), ("ddm", ctypes.c_double), ("n_dm", ctypes.c_int32),
                 ("downsamp", ctypes.c_int32), ("n_width", ctypes.c_int32),
                 ("widths", ctypes.POINTER(ctypes.c_int32))]
+
+
+class KernelConfig(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("dm_per_block", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("chan_per_stage", ctypes.c_int32), ("threads", ctypes.c_int32), ("row_words", ctypes.c_int32),
+                ("tuned_ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class _PlanDesc(ctypes.Structure):
@@ -88,6 +97,12 @@ def _lib_raw():
     L.fdd_search.argtypes = [_P, _P, _I64, _I64, _I64, _I64, _P, _SZ, _P, _I64, _P, _P, _P]
     L.fdd_downsample_u8.argtypes = [_P, _I64, _I64, _I64, _I32, _P, _I64, _P]
     L.fdd_plan_set_timing.argtypes = [_P, _I32]
+    L.fdd_num_variants.argtypes = [ctypes.POINTER(_I32)]
+    L.fdd_variant_info.argtypes = [_I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                                   ctypes.POINTER(_I32)]
+    L.fdd_plan_get_config.argtypes = [_P, _I32, ctypes.POINTER(KernelConfig)]
+    L.fdd_plan_set_config.argtypes = [_P, _I32, _I32, _I32]
+    L.fdd_plan_autotune.argtypes = [_P, _P, _I64, _I64, _I64, _P, _SZ, _I32, _P]
     L.fdd_plan_stage_times.argtypes = [_P, _I32, _P, _P, _P, ctypes.POINTER(_I32)]
     _lib = L
     return L
@@ -95,6 +110,21 @@ def _lib_raw():
 
 def version():
     return _lib_raw().fdd_version().decode()
+
+
+def variants():
+    """[{index, bytes_per_sample, dm_per_block, tile, threads}] of the compiled dedispersion kernels."""
+    L = _lib_raw()
+    n = _I32()
+    _check(L.fdd_num_variants(ctypes.byref(n)), "fdd_num_variants")
+    out = []
+    for v in range(n.value):
+        e, bd, t, th = _I32(), _I32(), _I32(), _I32()
+        _check(L.fdd_variant_info(v, ctypes.byref(e), ctypes.byref(bd), ctypes.byref(t), ctypes.byref(th)),
+               "fdd_variant_info")
+        out.append(dict(index=v, bytes_per_sample=e.value, dm_per_block=bd.value, tile=t.value,
+                        threads=th.value))
+    return out
 
 
 def _check(code, where):
@@ -252,6 +282,28 @@ class Plan:
             _stream_handle(stream))
         _check(code, "fdd_search")
         return SearchResult(cands=cands, count=count, series=series, cap=cap)
+
+    def get_config(self, r):
+        c = KernelConfig()
+        _check(_lib_raw().fdd_plan_get_config(self._h, int(r), ctypes.byref(c)), "fdd_plan_get_config")
+        return c.as_dict()
+
+    def set_config(self, r, variant, chan_per_stage=0):
+        _check(_lib_raw().fdd_plan_set_config(self._h, int(r), int(variant), int(chan_per_stage)),
+               "fdd_plan_set_config")
+
+    def autotune(self, tabs, n_in, n_out, reps=3, workspace=None, stream=None):
+        """Time every compatible kernel configuration per DM range on this
+        chunk and keep the fastest (include/fdd.h: fdd_plan_autotune)."""
+        torch = _torch()
+        if workspace is None:
+            workspace = torch.empty(self.workspace_size(n_in, n_out, with_series=True), dtype=torch.uint8,
+                                    device=tabs.device)
+        _check(_lib_raw().fdd_plan_autotune(self._h, _dev_ptr(tabs, "tabs", torch.uint8), int(n_in),
+                                            int(tabs.shape[2]), int(n_out), _dev_ptr(workspace, "workspace"),
+                                            int(workspace.numel()), int(reps), _stream_handle(stream)),
+               "fdd_plan_autotune")
+        return [self.get_config(r) for r in range(len(self.ranges))]
 
     def set_timing(self, enable=True):
         _check(_lib_raw().fdd_plan_set_timing(self._h, int(bool(enable))), "fdd_plan_set_timing")

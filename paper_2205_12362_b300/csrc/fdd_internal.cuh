@@ -17,8 +17,10 @@ namespace fdd {
 //   DPW   DM trials per warp
 //   WARPS warps per block; the block covers BD = WARPS * DPW trials and
 //         T = 32 * NW * (4/E) output samples
+//   MAXIT 16-byte staging chunks per thread per channel stage (register
+//         budget of the software pipeline)
 struct DedispVariant {
-    int E, NW, DPW, WARPS;
+    int E, NW, DPW, WARPS, MAXIT;
     int bd() const { return WARPS * DPW; }
     int tile() const { return 32 * NW * (4 / E); }
     int threads() const { return WARPS * 32; }
@@ -33,7 +35,7 @@ struct DedispArgs {
     int64_t n_valid;            // valid samples per row (elements of E bytes)
     const int16_t* sb_map;      // [n_sb][n_chan]
     const int32_t* base;        // [n_blk][n_chan]: first staged sample of (DM block, channel), aligned to 16/E
-    const int32_t* off;         // [n_dm][n_chan]: byte offset of trial (i, c) inside its channel slot
+    const int32_t* off;         // [n_blk][n_chan][BD]: byte offset of trial (i, c) inside its channel slot
     int32_t* series;            // [n_sb][n_dm][n_out]
     unsigned long long* stat;   // [n_sb * n_dm][2]: sum S, sum S^2
     int32_t n_chan;
@@ -46,6 +48,9 @@ struct DedispArgs {
 
 // Shared-memory bytes of one dedispersion block.
 size_t dedisp_smem_bytes(const DedispVariant& v, int Lw, int CC);
+// Whether channel-stage size CC fits variant v's staging registers, offset
+// prefetch and the shared-memory budget for rows of Lw words.
+bool dedisp_cc_ok(const DedispVariant& v, int Lw, int CC, size_t smem_budget);
 cudaError_t launch_dedisp(int variant, const DedispArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------------------

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -47,6 +48,7 @@ struct RangeState {
     // kernel configuration and its device tables
     int variant = -1;
     int32_t Lw = 0, CC = 0;
+    float tuned_ms = 0.f;
     int32_t* d_off = nullptr;         // [n_dm][n_chan]
     int32_t* d_base = nullptr;        // [n_blk][n_chan]
 };
@@ -78,14 +80,22 @@ void free_range_tables(RangeState& r) {
     r.d_base = nullptr;
 }
 
-// Build the staged-offset tables of range r for kernel variant v.
-int configure_range(fdd_plan* p, RangeState& r, int variant) {
-    const fdd::DedispVariant& v = fdd::dedisp_variant(variant);
+struct HostTables {
+    std::vector<int32_t> base;  // [n_blk][n_chan]
+    std::vector<int32_t> off;   // [n_blk][n_chan][BD]
+    int32_t Lw = 0;
+};
+
+// Staged-row geometry of range r for kernel variant v: for every (DM block,
+// channel) the aligned first staged sample, and for every trial its byte
+// offset (copy q = misalignment, aligned word) inside the channel slot.
+HostTables build_tables(const fdd_plan* p, const RangeState& r, const fdd::DedispVariant& v) {
     const int E = v.E, BD = v.bd(), NW = v.NW;
     const int A = 16 / E;  // alignment of the staged row start, in samples
     const int n_chan = p->n_chan;
     const int n_blk = (r.n_dm + BD - 1) / BD;
-    std::vector<int32_t> base(static_cast<size_t>(n_blk) * n_chan);
+    HostTables h;
+    h.base.resize(static_cast<size_t>(n_blk) * n_chan);
     int64_t max_span_words = 0;
     for (int b = 0; b < n_blk; b++) {
         const int ia = b * BD, ib = std::min(r.n_dm, (b + 1) * BD);
@@ -97,40 +107,61 @@ int configure_range(fdd_plan* p, RangeState& r, int variant) {
                 hi = std::max(hi, d);
             }
             const int32_t bs = lo / A * A;
-            base[static_cast<size_t>(b) * n_chan + c] = bs;
+            h.base[static_cast<size_t>(b) * n_chan + c] = bs;
             max_span_words = std::max<int64_t>(max_span_words, (static_cast<int64_t>(hi - bs) * E) >> 2);
         }
     }
     const int64_t Lw = static_cast<int64_t>(align_up(static_cast<size_t>(max_span_words + 32 * NW), 4));
-    int CC = 0;
-    for (int cc : {16, 8, 4, 2, 1}) {
-        if (fdd::dedisp_smem_bytes(v, static_cast<int>(Lw), cc) <= kSmemBudget) {
-            CC = cc;
-            break;
-        }
-    }
-    if (CC == 0 || Lw > (1 << 20))
-        return fail(FDD_ERR_UNSUPPORTED, "DM step too large for one block's staged rows; lower ddm or raise downsamp");
-    std::vector<int32_t> off(static_cast<size_t>(r.n_dm) * n_chan);
-    for (int i = 0; i < r.n_dm; i++) {
-        const int b = i / BD;
-        for (int c = 0; c < n_chan; c++) {
-            const int32_t o = (r.delay[static_cast<size_t>(i) * n_chan + c] - base[static_cast<size_t>(b) * n_chan + c]) * E;
-            const int32_t q = (o & 3) / E;
-            off[static_cast<size_t>(i) * n_chan + c] = q * static_cast<int32_t>(Lw) * 4 + (o & ~3);
-        }
-    }
+    h.Lw = Lw > (1 << 20) ? -1 : static_cast<int32_t>(Lw);
+    if (h.Lw < 0) return h;
+    h.off.resize(static_cast<size_t>(n_blk) * n_chan * BD);
+    for (int b = 0; b < n_blk; b++)
+        for (int c = 0; c < n_chan; c++)
+            for (int jj = 0; jj < BD; jj++) {
+                const int i = std::min(b * BD + jj, r.n_dm - 1);  // padding trials repeat the last one
+                const int32_t o = (r.delay[static_cast<size_t>(i) * n_chan + c] -
+                                   h.base[static_cast<size_t>(b) * n_chan + c]) * E;
+                const int32_t q = (o & 3) / E;
+                h.off[(static_cast<size_t>(b) * n_chan + c) * BD + jj] = q * h.Lw * 4 + (o & ~3);
+            }
+    return h;
+}
+
+int pick_cc(const fdd::DedispVariant& v, int Lw) {
+    for (int cc : {32, 16, 8, 4, 2})
+        if (fdd::dedisp_cc_ok(v, Lw, cc, kSmemBudget)) return cc;
+    return 0;
+}
+
+int upload_tables(RangeState& r, const HostTables& h) {
     free_range_tables(r);
-    cudaError_t e = cudaMalloc(&r.d_off, off.size() * sizeof(int32_t));
+    cudaError_t e = cudaMalloc(&r.d_off, h.off.size() * sizeof(int32_t));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(offset table)");
-    e = cudaMalloc(&r.d_base, base.size() * sizeof(int32_t));
+    e = cudaMalloc(&r.d_base, h.base.size() * sizeof(int32_t));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(base table)");
-    e = cudaMemcpy(r.d_off, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(r.d_off, h.off.data(), h.off.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(offset table)");
-    e = cudaMemcpy(r.d_base, base.data(), base.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(r.d_base, h.base.data(), h.base.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(base table)");
+    return FDD_OK;
+}
+
+// Configure range r for kernel variant `variant` with channel stage CC
+// (0 = the largest that fits).
+int configure_range(fdd_plan* p, RangeState& r, int variant, int CC) {
+    if (variant < 0 || variant >= fdd::num_dedisp_variants())
+        return fail(FDD_ERR_INVALID_ARG, "kernel variant out of range");
+    const fdd::DedispVariant& v = fdd::dedisp_variant(variant);
+    if (v.E != (r.D == 1 ? 1 : 2)) return fail(FDD_ERR_INVALID_ARG, "kernel variant for the wrong sample width");
+    const HostTables h = build_tables(p, r, v);
+    if (h.Lw < 0) return fail(FDD_ERR_UNSUPPORTED, "DM step too large for one block's staged rows");
+    if (CC == 0) CC = pick_cc(v, h.Lw);
+    if (CC == 0 || !fdd::dedisp_cc_ok(v, h.Lw, CC, kSmemBudget))
+        return fail(FDD_ERR_UNSUPPORTED, "DM step too large for one block's staged rows; lower ddm or raise downsamp");
+    const int rc = upload_tables(r, h);
+    if (rc != FDD_OK) return rc;
     r.variant = variant;
-    r.Lw = static_cast<int32_t>(Lw);
+    r.Lw = h.Lw;
     r.CC = CC;
     return FDD_OK;
 }
@@ -178,6 +209,48 @@ Layout make_layout(const fdd_plan* p, int64_t n_in, int64_t n_out, bool with_ser
     }
     L.total = std::max<size_t>(cur, 256);
     return L;
+}
+
+fdd::DedispArgs dedisp_args(const fdd_plan* plan, const RangeState& r, size_t ri, const Layout& L,
+                            const uint8_t* d_tabs, int64_t pitch, uint8_t* ws, int32_t* series,
+                            unsigned long long* stat, int64_t n_in, int64_t n_out) {
+    fdd::DedispArgs a{};
+    if (r.D == 1) {
+        a.in = d_tabs;
+        a.pitch_bytes = pitch;
+    } else {
+        const size_t k = std::find(plan->ds_factors.begin(), plan->ds_factors.end(), r.D) - plan->ds_factors.begin();
+        a.in = ws + L.ds_off[k];
+        a.pitch_bytes = L.ds_pitch[k] * 2;
+    }
+    a.n_valid = n_in / r.D;
+    a.sb_map = plan->d_sb_map;
+    a.base = r.d_base;
+    a.off = r.d_off;
+    a.series = series + L.series_r[ri];
+    a.stat = stat + 2 * L.stat_r[ri];
+    a.n_chan = plan->n_chan;
+    a.n_dm = r.n_dm;
+    a.n_out = static_cast<int32_t>(n_out / r.D);
+    a.n_sb = plan->n_sb;
+    a.Lw = r.Lw;
+    a.CC = r.CC;
+    return a;
+}
+
+int check_search_args(const fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitch, int64_t n_out,
+                      const void* d_workspace, const void* d_series) {
+    if (!plan || !d_tabs || !d_workspace || n_in < 0 || n_out < 0 || pitch < n_in)
+        return fail(FDD_ERR_INVALID_ARG, "bad search argument");
+    if (n_out > (1LL << 30) || n_in > (1LL << 31) - 64)
+        return fail(FDD_ERR_UNSUPPORTED, "chunk longer than the kernels' 32-bit sample indexing");
+    if ((reinterpret_cast<uintptr_t>(d_tabs) & 15) || (pitch & 15) ||
+        (reinterpret_cast<uintptr_t>(d_workspace) & 255) || (reinterpret_cast<uintptr_t>(d_series) & 15))
+        return fail(FDD_ERR_MISALIGNED, "d_tabs/pitch must be 16-byte aligned, workspace 256-byte aligned");
+    for (const RangeState& r : plan->ranges)
+        if (n_out / r.D + r.dmax > n_in / r.D)
+            return fail(FDD_ERR_SHORT_INPUT, "n_in < n_out + max delay for some DM range");
+    return FDD_OK;
 }
 
 }  // namespace
@@ -291,7 +364,10 @@ int fdd_plan_create(const fdd_plan_desc* desc, const int16_t* sb_map_host, fdd_p
         return cuda_fail(e, "cudaMemcpy(sb_map)");
     }
     for (RangeState& r : p->ranges) {
-        const int rc = configure_range(p, r, default_variant(r.D == 1 ? 1 : 2));
+        int rc = FDD_ERR_UNSUPPORTED;
+        const int E = (r.D == 1) ? 1 : 2;
+        for (int k = default_variant(E); k >= 0 && k < fdd::num_dedisp_variants() && rc != FDD_OK; k++)
+            if (fdd::dedisp_variant(k).E == E) rc = configure_range(p, r, k, 0);
         if (rc != FDD_OK) {
             fdd_plan_destroy(p);
             return rc;
@@ -345,17 +421,11 @@ int fdd_series_size(const fdd_plan* plan, int64_t n_out, size_t* bytes) {
 int fdd_search(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitch, int64_t n_out,
                int64_t t_offset_native, void* d_workspace, size_t workspace_bytes, fdd_candidate* d_cands,
                int64_t cap, uint64_t* d_count, int32_t* d_series, fdd_stream_t stream) {
-    if (!plan || !d_tabs || !d_workspace || !d_count || (cap > 0 && !d_cands) || cap < 0 || n_in < 0 ||
-        n_out < 0 || pitch < n_in)
-        return fail(FDD_ERR_INVALID_ARG, "bad search argument");
-    if (n_out > (1LL << 30) || n_in > (1LL << 31) - 64)
-        return fail(FDD_ERR_UNSUPPORTED, "chunk longer than the kernels' 32-bit sample indexing");
-    if ((reinterpret_cast<uintptr_t>(d_tabs) & 15) || (pitch & 15) ||
-        (reinterpret_cast<uintptr_t>(d_workspace) & 255) || (reinterpret_cast<uintptr_t>(d_series) & 15))
-        return fail(FDD_ERR_MISALIGNED, "d_tabs/pitch must be 16-byte aligned, workspace 256-byte aligned");
-    for (const RangeState& r : plan->ranges)
-        if (n_out / r.D + r.dmax > n_in / r.D)
-            return fail(FDD_ERR_SHORT_INPUT, "n_in < n_out + max delay for some DM range");
+    if (!d_count || (cap > 0 && !d_cands) || cap < 0) return fail(FDD_ERR_INVALID_ARG, "bad search argument");
+    {
+        const int rc = check_search_args(plan, d_tabs, n_in, pitch, n_out, d_workspace, d_series);
+        if (rc != FDD_OK) return rc;
+    }
     const bool own_series = (d_series == nullptr);
     const Layout L = make_layout(plan, n_in, n_out, own_series);
     if (workspace_bytes < L.total) return fail(FDD_ERR_WORKSPACE, "workspace smaller than fdd_workspace_size()");
@@ -403,27 +473,7 @@ int fdd_search(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitc
         const RangeState& r = plan->ranges[ri];
         const int64_t nr = n_out / r.D;
         if (nr == 0) continue;
-        fdd::DedispArgs a{};
-        if (r.D == 1) {
-            a.in = d_tabs;
-            a.pitch_bytes = pitch;
-        } else {
-            const size_t k = std::find(plan->ds_factors.begin(), plan->ds_factors.end(), r.D) - plan->ds_factors.begin();
-            a.in = ws + L.ds_off[k];
-            a.pitch_bytes = L.ds_pitch[k] * 2;
-        }
-        a.n_valid = n_in / r.D;
-        a.sb_map = plan->d_sb_map;
-        a.base = r.d_base;
-        a.off = r.d_off;
-        a.series = series + L.series_r[ri];
-        a.stat = stat + 2 * L.stat_r[ri];
-        a.n_chan = plan->n_chan;
-        a.n_dm = r.n_dm;
-        a.n_out = static_cast<int32_t>(nr);
-        a.n_sb = plan->n_sb;
-        a.Lw = r.Lw;
-        a.CC = r.CC;
+        const fdd::DedispArgs a = dedisp_args(plan, r, ri, L, d_tabs, pitch, ws, series, stat, n_in, n_out);
         if ((e = stage_begin(1, static_cast<int>(ri))) != cudaSuccess) return cuda_fail(e, "timing event");
         e = fdd::launch_dedisp(r.variant, a, s);
         if (e != cudaSuccess) return cuda_fail(e, "dedispersion launch");
@@ -456,6 +506,127 @@ int fdd_search(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitc
         if ((e = stage_end()) != cudaSuccess) return cuda_fail(e, "timing event");
     }
     return FDD_OK;
+}
+
+int fdd_num_variants(int32_t* n) {
+    if (!n) return fail(FDD_ERR_INVALID_ARG, "null argument");
+    *n = fdd::num_dedisp_variants();
+    return FDD_OK;
+}
+
+int fdd_variant_info(int32_t variant, int32_t* bytes_per_sample, int32_t* dm_per_block, int32_t* tile,
+                     int32_t* threads) {
+    if (variant < 0 || variant >= fdd::num_dedisp_variants()) return fail(FDD_ERR_INVALID_ARG, "bad variant");
+    const fdd::DedispVariant& v = fdd::dedisp_variant(variant);
+    if (bytes_per_sample) *bytes_per_sample = v.E;
+    if (dm_per_block) *dm_per_block = v.bd();
+    if (tile) *tile = v.tile();
+    if (threads) *threads = v.threads();
+    return FDD_OK;
+}
+
+int fdd_plan_get_config(const fdd_plan* plan, int32_t r, fdd_kernel_config* out) {
+    if (!plan || !out || r < 0 || r >= static_cast<int32_t>(plan->ranges.size()))
+        return fail(FDD_ERR_INVALID_ARG, "bad range index");
+    const RangeState& rs = plan->ranges[r];
+    const fdd::DedispVariant& v = fdd::dedisp_variant(rs.variant);
+    out->variant = rs.variant;
+    out->dm_per_block = v.bd();
+    out->tile = v.tile();
+    out->chan_per_stage = rs.CC;
+    out->threads = v.threads();
+    out->row_words = rs.Lw;
+    out->tuned_ms = rs.tuned_ms;
+    return FDD_OK;
+}
+
+int fdd_plan_set_config(fdd_plan* plan, int32_t r, int32_t variant, int32_t chan_per_stage) {
+    if (!plan || r < 0 || r >= static_cast<int32_t>(plan->ranges.size()) || chan_per_stage < 0)
+        return fail(FDD_ERR_INVALID_ARG, "bad range index");
+    RangeState& rs = plan->ranges[r];
+    const int old_variant = rs.variant, old_cc = rs.CC;
+    const int rc = configure_range(plan, rs, variant, chan_per_stage);
+    if (rc != FDD_OK && old_variant >= 0) configure_range(plan, rs, old_variant, old_cc);
+    if (rc == FDD_OK) rs.tuned_ms = 0.f;
+    return rc;
+}
+
+int fdd_plan_autotune(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitch, int64_t n_out,
+                      void* d_workspace, size_t workspace_bytes, int32_t reps, fdd_stream_t stream) {
+    {
+        const int rc = check_search_args(plan, d_tabs, n_in, pitch, n_out, d_workspace, nullptr);
+        if (rc != FDD_OK) return rc;
+    }
+    if (reps < 1) reps = 1;
+    const Layout L = make_layout(plan, n_in, n_out, true);
+    if (workspace_bytes < L.total) return fail(FDD_ERR_WORKSPACE, "workspace smaller than fdd_workspace_size()");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    uint8_t* ws = static_cast<uint8_t*>(d_workspace);
+    int32_t* series = reinterpret_cast<int32_t*>(ws + L.series);
+    unsigned long long* stat = reinterpret_cast<unsigned long long*>(ws + L.stat);
+    cudaError_t e;
+    for (size_t k = 0; k < plan->ds_factors.size(); k++) {
+        e = fdd::launch_downsample(d_tabs, static_cast<int64_t>(plan->n_tab) * plan->n_chan, n_in, pitch,
+                                   plan->ds_factors[k], reinterpret_cast<uint16_t*>(ws + L.ds_off[k]),
+                                   L.ds_pitch[k], s);
+        if (e != cudaSuccess) return cuda_fail(e, "downsample launch");
+    }
+    cudaEvent_t ev0, ev1;
+    if ((e = cudaEventCreate(&ev0)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    if ((e = cudaEventCreate(&ev1)) != cudaSuccess) {
+        cudaEventDestroy(ev0);
+        return cuda_fail(e, "cudaEventCreate");
+    }
+    int rc = FDD_OK;
+    for (size_t ri = 0; ri < plan->ranges.size() && rc == FDD_OK; ri++) {
+        RangeState& r = plan->ranges[ri];
+        if (n_out / r.D == 0) continue;
+        const int E = (r.D == 1) ? 1 : 2;
+        int best_v = r.variant, best_cc = r.CC;
+        float best = 1e30f;
+        for (int v = 0; v < fdd::num_dedisp_variants() && rc == FDD_OK; v++) {
+            const fdd::DedispVariant& dv = fdd::dedisp_variant(v);
+            if (dv.E != E) continue;
+            const HostTables h = build_tables(plan, r, dv);
+            if (h.Lw < 0) continue;
+            bool uploaded = false;
+            for (int cc : {8, 16, 32, 64}) {
+                if (!fdd::dedisp_cc_ok(dv, h.Lw, cc, kSmemBudget)) continue;
+                if (!uploaded) {
+                    if ((rc = upload_tables(r, h)) != FDD_OK) break;
+                    uploaded = true;
+                }
+                r.variant = v;
+                r.Lw = h.Lw;
+                r.CC = cc;
+                const fdd::DedispArgs a = dedisp_args(plan, r, ri, L, d_tabs, pitch, ws, series, stat, n_in, n_out);
+                if ((e = fdd::launch_dedisp(v, a, s)) != cudaSuccess) { rc = cuda_fail(e, "tuning launch"); break; }
+                cudaEventRecord(ev0, s);
+                for (int k = 0; k < reps && e == cudaSuccess; k++) e = fdd::launch_dedisp(v, a, s);
+                cudaEventRecord(ev1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
+                if (e != cudaSuccess) { rc = cuda_fail(e, "tuning launch"); break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev0, ev1);
+                ms /= reps;
+                if (std::getenv("FDD_TUNE_VERBOSE"))
+                    std::fprintf(stderr, "fdd tune: range %zu variant %d (bd %d tile %d threads %d) cc %d: %.4f ms\n",
+                                 ri, v, dv.bd(), dv.tile(), dv.threads(), cc, ms);
+                if (ms < best) {
+                    best = ms;
+                    best_v = v;
+                    best_cc = cc;
+                }
+            }
+        }
+        if (rc == FDD_OK) {
+            rc = configure_range(plan, r, best_v, best_cc);
+            if (rc == FDD_OK) r.tuned_ms = best;
+        }
+    }
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    return rc;
 }
 
 int fdd_plan_set_timing(fdd_plan* plan, int32_t enable) {

@@ -7,95 +7,143 @@
 // the S/N stage.
 //
 // Design (B300): the work is shift-and-add, not a contraction, so no tensor
-// cores.  Every output costs one byte read from shared memory and one add;
-// both the LDS bandwidth and the integer pipe are the limits.  To reach them:
+// cores.  Every channel-add needs its input byte from shared memory, so the
+// LDS bandwidth and the integer issue rate are the limits.  To approach them:
 //   * A block owns BD = WARPS*DPW consecutive DM trials and T output samples
-//     of one SB.  Channels are streamed in stages of CC; for each channel the
-//     input bytes covering [t0 + min_i d, t0 + max_i d + T) of the TAB that
-//     the SB selects (the gather is free: it only picks the source row) are
-//     staged in shared memory in 4/E copies, copy q shifted by q*E bytes, so
-//     that every trial's 4-byte word is an aligned LDS.32 whatever its delay.
-//   * A warp reads 32 consecutive words per (trial, channel): conflict-free.
-//   * SWAR accumulation for uint8 samples: acc_all += x (mod 2^32) and
-//     acc_odd += bytes 1,3 of x in 16-bit lanes.  Bytes 0,2 are recovered as
-//     acc_all - (acc_odd << 8).  Lanes hold <= 256 channels of 255, so they
-//     are flushed into int32 totals every 256 channels.  For uint16 samples
-//     (downsampled ranges) acc_all += x and acc_hi += x >> 16 are exact
-//     without flushing.  That is 2 integer ops per 4 (or 2) channel-adds.
-//   * Per-trial staged offsets (copy, word) are precomputed on the host into
-//     a table, so the inner loop is LDS + PRMT/SHF + IADD only.
+//     of one SB.  Channels are streamed in stages of CC.  For each channel the
+//     input bytes covering [t0 + min_i d, t0 + max_i d + T) of the TAB the SB
+//     selects (the gather only picks the source row) are staged in shared
+//     memory as 4/E copies, copy q shifted by q*E bytes, so every trial's
+//     4-byte word is one aligned, conflict-free LDS.32 whatever its delay.
+//   * Staging is software-pipelined: the global loads of stage k+1 are issued
+//     into registers before stage k is computed and written to shared memory
+//     after it, so L2 latency hides behind the adds.
+//   * SWAR accumulation for uint8 samples: acc_a += x (mod 2^32) and acc_b +=
+//     bytes 1,3 of x in 16-bit lanes (one PRMT); bytes 0,2 are recovered as
+//     acc_a - (acc_b << 8).  Lanes hold <= 256 channels of 255 and are folded
+//     into int32 totals every 256 channels.  uint16 samples (downsampled
+//     ranges) use acc_a += x, acc_b += x >> 16, exact without folding.
+//     Channels are taken in pairs so each accumulator update is one IADD3.
+//   * Per-trial staged offsets come from a host table laid out
+//     [DM block][channel][trial], so a stage's offsets are one coalesced read.
 #include "fdd_internal.cuh"
 
 namespace fdd {
 
 namespace {
 
-// Staged row layout in shared memory, per channel slot:
-//   copy q (q < NC) occupies Lw words; word j of copy q holds the 4 bytes at
-//   byte offset 4*j + q*E of the global row segment starting at the block's
-//   aligned base sample.
-template <int E>
-__device__ __forceinline__ void stage_channels(const DedispArgs& a, uint8_t* s_rows, int slot_bytes,
-                                               int c0, int ncc, int sb, int blk, int t0) {
-    constexpr int NC = 4 / E;
-    const int chunks = a.Lw >> 2;  // 16-byte chunks per copy row
-    const int items = ncc * chunks;
-    const int64_t limit = a.n_valid * E;  // valid bytes per row
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int cc = it / chunks;
-        const int m = it - cc * chunks;
-        const int c = c0 + cc;
-        const int tab = a.sb_map[(int64_t)sb * a.n_chan + c];
-        const uint8_t* row = a.in + ((int64_t)tab * a.n_chan + c) * a.pitch_bytes;
-        const int64_t b0 = (int64_t)(t0 + a.base[(int64_t)blk * a.n_chan + c]) * E + 16 * (int64_t)m;
-        uint32_t g[5];
-        if (b0 + 20 <= limit) {
-            const uint4 v = __ldg(reinterpret_cast<const uint4*>(row + b0));
-            g[0] = v.x; g[1] = v.y; g[2] = v.z; g[3] = v.w;
-            g[4] = __ldg(reinterpret_cast<const uint32_t*>(row + b0 + 16));
-        } else {
-#pragma unroll
-            for (int k = 0; k < 5; k++) {
-                uint32_t w = 0;
-#pragma unroll
-                for (int b = 0; b < 4; b++) {
-                    const int64_t p = b0 + 4 * k + b;
-                    const uint32_t byte = (p < limit) ? (uint32_t)row[p] : 0u;
-                    w |= byte << (8 * b);
-                }
-                g[k] = w;
-            }
-        }
-        uint8_t* dst = s_rows + cc * slot_bytes + 16 * m;
-#pragma unroll
-        for (int q = 0; q < NC; q++) {
-            uint4 o;
-            o.x = __funnelshift_r(g[0], g[1], 8 * q * E);
-            o.y = __funnelshift_r(g[1], g[2], 8 * q * E);
-            o.z = __funnelshift_r(g[2], g[3], 8 * q * E);
-            o.w = __funnelshift_r(g[3], g[4], 8 * q * E);
-            *reinterpret_cast<uint4*>(dst + q * a.Lw * 4) = o;
-        }
+template <int N>
+__device__ __forceinline__ void load_offsets(const int32_t* p, int32_t (&o)[N]) {
+    if constexpr (N == 1) {
+        o[0] = p[0];
+    } else if constexpr (N == 2) {
+        const int2 v = *reinterpret_cast<const int2*>(p);
+        o[0] = v.x;
+        o[1] = v.y;
+    } else {
+        static_assert(N == 4, "DPW must be 1, 2 or 4");
+        const int4 v = *reinterpret_cast<const int4*>(p);
+        o[0] = v.x;
+        o[1] = v.y;
+        o[2] = v.z;
+        o[3] = v.w;
     }
 }
 
-template <int E, int NW, int DPW, int WARPS>
+template <int E, int NW, int DPW, int WARPS, int MAXIT>
 __global__ void __launch_bounds__(WARPS * 32) k_dedisp(const DedispArgs a) {
-    constexpr int NC = 4 / E;
-    constexpr int SPW = 4 / E;
-    constexpr int BD = WARPS * DPW;
+    constexpr int NC = 4 / E;       // byte-shifted copies of each staged row
+    constexpr int SPW = 4 / E;      // samples per 32-bit word
+    constexpr int BD = WARPS * DPW; // DM trials per block
     constexpr int T = 32 * NW * SPW;
+    constexpr int NT = WARPS * 32;
+    static_assert(BD % 4 == 0, "BD must be a multiple of 4");
     extern __shared__ __align__(16) uint8_t smem[];
 
     const int CC = a.CC;
-    const int slot_bytes = NC * a.Lw * 4;
+    const int Lw = a.Lw;
+    const int chunks = Lw >> 2;  // 16-byte chunks per copy row
+    const int slot_bytes = NC * Lw * 4;
     uint8_t* s_rows = smem;
     int32_t* s_off = reinterpret_cast<int32_t*>(smem + CC * slot_bytes);  // [CC][BD]
 
-    const int tile = blockIdx.x, blk = blockIdx.y, sb = blockIdx.z;
-    const int t0 = tile * T;
+    const int blk = blockIdx.y, sb = blockIdx.z;
+    const int t0 = blockIdx.x * T;
     const int i0 = blk * BD;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t limit = a.n_valid * E;  // valid bytes per input row
+    const int16_t* sbm = a.sb_map + (int64_t)sb * a.n_chan;
+    const int32_t* base_blk = a.base + (int64_t)blk * a.n_chan;
+    const int32_t* off_blk = a.off + (int64_t)blk * a.n_chan * BD;
+
+    // ---- staging registers (one stage in flight)
+    uint4 pv[MAXIT];
+    uint32_t pn[MAXIT];
+    int4 po = make_int4(0, 0, 0, 0);
+
+    auto stage_load = [&](int c0, int ncc) {
+        const int items = ncc * chunks;
+#pragma unroll
+        for (int u = 0; u < MAXIT; u++) {
+            const int it = threadIdx.x + u * NT;
+            if (it < items) {
+                const int cc = it / chunks;
+                const int m = it - cc * chunks;
+                const int c = c0 + cc;
+                const uint8_t* row = a.in + ((int64_t)sbm[c] * a.n_chan + c) * a.pitch_bytes;
+                const int64_t b0 = (int64_t)(t0 + base_blk[c]) * E + 16 * (int64_t)m;
+                if (b0 + 20 <= limit) {
+                    pv[u] = __ldg(reinterpret_cast<const uint4*>(row + b0));
+                    pn[u] = __ldg(reinterpret_cast<const uint32_t*>(row + b0 + 16));
+                } else {
+                    uint32_t g[5];
+#pragma unroll
+                    for (int k = 0; k < 5; k++) {
+                        uint32_t w = 0;
+#pragma unroll
+                        for (int b = 0; b < 4; b++) {
+                            const int64_t p = b0 + 4 * k + b;
+                            w |= ((p < limit) ? (uint32_t)row[p] : 0u) << (8 * b);
+                        }
+                        g[k] = w;
+                    }
+                    pv[u] = make_uint4(g[0], g[1], g[2], g[3]);
+                    pn[u] = g[4];
+                }
+            }
+        }
+        if (threadIdx.x < ncc * (BD / 4))
+            po = __ldg(reinterpret_cast<const int4*>(off_blk + (int64_t)c0 * BD) + threadIdx.x);
+    };
+
+    auto stage_store = [&](int ncc) {
+        const int items = ncc * chunks;
+#pragma unroll
+        for (int u = 0; u < MAXIT; u++) {
+            const int it = threadIdx.x + u * NT;
+            if (it < items) {
+                const int cc = it / chunks;
+                const int m = it - cc * chunks;
+                uint8_t* dst = s_rows + cc * slot_bytes + 16 * m;
+                const uint32_t g0 = pv[u].x, g1 = pv[u].y, g2 = pv[u].z, g3 = pv[u].w, g4 = pn[u];
+#pragma unroll
+                for (int q = 0; q < NC; q++) {
+                    uint4 o;
+                    o.x = __funnelshift_r(g0, g1, 8 * q * E);
+                    o.y = __funnelshift_r(g1, g2, 8 * q * E);
+                    o.z = __funnelshift_r(g2, g3, 8 * q * E);
+                    o.w = __funnelshift_r(g3, g4, 8 * q * E);
+                    *reinterpret_cast<uint4*>(dst + q * Lw * 4) = o;
+                }
+            }
+        }
+        if (threadIdx.x < ncc * (BD / 4)) {
+            const int cc = (threadIdx.x * 4) / BD;
+            const int add = cc * slot_bytes;
+            reinterpret_cast<int4*>(s_off)[threadIdx.x] =
+                make_int4(po.x + add, po.y + add, po.z + add, po.w + add);
+        }
+    };
 
     uint32_t acc_a[DPW][NW], acc_b[DPW][NW];
     uint32_t tot[DPW][NW][SPW];
@@ -109,16 +157,15 @@ __global__ void __launch_bounds__(WARPS * 32) k_dedisp(const DedispArgs a) {
             for (int e = 0; e < SPW; e++) tot[j][k][e] = 0u;
         }
 
-    // E == 1: fold the 16-bit SWAR lanes into the int32 totals (must happen
-    // before a lane holds more than 257 channels of <= 255).
+    // E == 1: fold the 16-bit SWAR lanes into the int32 totals.
     auto flush = [&]() {
         if constexpr (E == 1) {
 #pragma unroll
             for (int j = 0; j < DPW; j++)
 #pragma unroll
                 for (int k = 0; k < NW; k++) {
-                    const uint32_t odd = acc_b[j][k];                  // bytes 1,3
-                    const uint32_t even = acc_a[j][k] - (odd << 8);    // bytes 0,2
+                    const uint32_t odd = acc_b[j][k];                // bytes 1,3
+                    const uint32_t even = acc_a[j][k] - (odd << 8);  // bytes 0,2
                     tot[j][k][0] += even & 0xFFFFu;
                     tot[j][k][1] += odd & 0xFFFFu;
                     tot[j][k][2] += even >> 16;
@@ -128,45 +175,68 @@ __global__ void __launch_bounds__(WARPS * 32) k_dedisp(const DedispArgs a) {
                 }
         }
     };
+    auto split = [](uint32_t x) -> uint32_t {
+        if constexpr (E == 1)
+            return __byte_perm(x, 0u, 0x4341);  // bytes 1,3 -> 16-bit lanes
+        else
+            return x >> 16;                     // high uint16 sample
+    };
 
     const uint8_t* s_lane = s_rows + 4 * lane;
-    int since_flush = 0;  // channels held in the 16-bit lanes (E == 1)
-    for (int c0 = 0; c0 < a.n_chan; c0 += CC) {
-        const int ncc = min(CC, a.n_chan - c0);
-        __syncthreads();  // previous stage fully consumed
-        stage_channels<E>(a, s_rows, slot_bytes, c0, ncc, sb, blk, t0);
-        for (int idx = threadIdx.x; idx < ncc * BD; idx += blockDim.x) {
-            const int cc = idx / BD, jj = idx - cc * BD;
-            const int i = min(i0 + jj, a.n_dm - 1);
-            s_off[idx] = a.off[(int64_t)i * a.n_chan + c0 + cc] + cc * slot_bytes;
-        }
-        __syncthreads();
+    const int32_t* s_off_w = s_off + warp * DPW;
 
-        if (E == 1) {
+    int ncc = min(CC, a.n_chan);
+    stage_load(0, ncc);
+    stage_store(ncc);
+    __syncthreads();
+
+    int since_flush = 0;
+    for (int c0 = 0; c0 < a.n_chan; c0 += CC) {
+        const int c1 = c0 + CC;
+        const int ncc_next = (c1 < a.n_chan) ? min(CC, a.n_chan - c1) : 0;
+        if (ncc_next) stage_load(c1, ncc_next);  // in flight during the adds below
+
+        if constexpr (E == 1) {
             if (since_flush + ncc > 256) {
                 flush();
                 since_flush = 0;
             }
             since_flush += ncc;
         }
-#pragma unroll 2
-        for (int cc = 0; cc < ncc; cc++) {
-            const uint32_t* p[DPW];
-#pragma unroll
-            for (int j = 0; j < DPW; j++)
-                p[j] = reinterpret_cast<const uint32_t*>(s_lane + s_off[cc * BD + warp * DPW + j]);
+        int cc = 0;
+#pragma unroll 1
+        for (; cc + 1 < ncc; cc += 2) {
+            int32_t o0[DPW], o1[DPW];
+            load_offsets<DPW>(s_off_w + cc * BD, o0);
+            load_offsets<DPW>(s_off_w + (cc + 1) * BD, o1);
 #pragma unroll
             for (int j = 0; j < DPW; j++)
 #pragma unroll
                 for (int k = 0; k < NW; k++) {
-                    const uint32_t x = p[j][32 * k];
-                    acc_a[j][k] += x;
-                    if constexpr (E == 1)
-                        acc_b[j][k] += __byte_perm(x, 0u, 0x4341);  // bytes 1,3 -> 16-bit lanes
-                    else
-                        acc_b[j][k] += x >> 16;                     // high uint16 sample
+                    const uint32_t x0 = *reinterpret_cast<const uint32_t*>(s_lane + o0[j] + 128 * k);
+                    const uint32_t x1 = *reinterpret_cast<const uint32_t*>(s_lane + o1[j] + 128 * k);
+                    acc_a[j][k] = acc_a[j][k] + x0 + x1;
+                    acc_b[j][k] = acc_b[j][k] + split(x0) + split(x1);
                 }
         }
+        if (cc < ncc) {
+            int32_t o0[DPW];
+            load_offsets<DPW>(s_off_w + cc * BD, o0);
+#pragma unroll
+            for (int j = 0; j < DPW; j++)
+#pragma unroll
+                for (int k = 0; k < NW; k++) {
+                    const uint32_t x0 = *reinterpret_cast<const uint32_t*>(s_lane + o0[j] + 128 * k);
+                    acc_a[j][k] += x0;
+                    acc_b[j][k] += split(x0);
+                }
+        }
+        __syncthreads();  // stage fully consumed
+        if (ncc_next) {
+            stage_store(ncc_next);
+            __syncthreads();
+        }
+        ncc = ncc_next;
     }
     if constexpr (E == 1) {
         flush();
@@ -220,11 +290,24 @@ struct Entry {
     KernelFn fn;
 };
 
-#define FDD_V(E, NW, DPW, WARPS) {{E, NW, DPW, WARPS}, k_dedisp<E, NW, DPW, WARPS>}
+#define FDD_V(E, NW, DPW, WARPS, MAXIT) {{E, NW, DPW, WARPS, MAXIT}, k_dedisp<E, NW, DPW, WARPS, MAXIT>}
 const Entry kEntries[] = {
-    FDD_V(1, 4, 2, 8),  FDD_V(1, 4, 2, 16), FDD_V(1, 4, 4, 8), FDD_V(1, 8, 1, 16), FDD_V(1, 8, 2, 8),
-    FDD_V(1, 2, 4, 8),
-    FDD_V(2, 4, 2, 8),  FDD_V(2, 4, 2, 16), FDD_V(2, 4, 4, 8), FDD_V(2, 8, 2, 8),  FDD_V(2, 8, 1, 16),
+    // uint8 input (native-rate ranges)
+    FDD_V(1, 4, 2, 8, 4),    // BD 16, T 512, 256 threads
+    FDD_V(1, 4, 2, 16, 2),   // BD 32, T 512, 512 threads
+    FDD_V(1, 4, 4, 8, 4),    // BD 32, T 512, 256 threads
+    FDD_V(1, 2, 4, 8, 4),    // BD 32, T 256, 256 threads
+    FDD_V(1, 2, 2, 16, 2),   // BD 32, T 256, 512 threads
+    FDD_V(1, 8, 1, 16, 2),   // BD 16, T 1024, 512 threads
+    FDD_V(1, 4, 1, 16, 2),   // BD 16, T 512, 512 threads
+    FDD_V(1, 2, 4, 16, 2),   // BD 64, T 256, 512 threads
+    // uint16 input (downsampled ranges)
+    FDD_V(2, 4, 2, 8, 4),    // BD 16, T 256
+    FDD_V(2, 4, 2, 16, 2),   // BD 32, T 256
+    FDD_V(2, 4, 4, 8, 4),    // BD 32, T 256
+    FDD_V(2, 8, 2, 8, 4),    // BD 16, T 512
+    FDD_V(2, 8, 1, 16, 2),   // BD 16, T 512
+    FDD_V(2, 2, 4, 16, 2),   // BD 64, T 128
 };
 #undef FDD_V
 
@@ -236,6 +319,13 @@ const DedispVariant& dedisp_variant(int idx) { return kEntries[idx].v; }
 
 size_t dedisp_smem_bytes(const DedispVariant& v, int Lw, int CC) {
     return static_cast<size_t>(CC) * (4 / v.E) * Lw * 4 + static_cast<size_t>(CC) * v.bd() * 4;
+}
+
+bool dedisp_cc_ok(const DedispVariant& v, int Lw, int CC, size_t smem_budget) {
+    if (CC < 1 || CC > 256) return false;
+    if (static_cast<int64_t>(CC) * (Lw / 4) > static_cast<int64_t>(v.MAXIT) * v.threads()) return false;
+    if (CC * (v.bd() / 4) > v.threads()) return false;
+    return dedisp_smem_bytes(v, Lw, CC) <= smem_budget;
 }
 
 cudaError_t launch_dedisp(int variant, const DedispArgs& a, cudaStream_t s) {

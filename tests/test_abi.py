@@ -66,3 +66,13 @@ def test_candidate_record_layout():
     assert fdd.CAND_DTYPE.itemsize == 32
     assert [fdd.CAND_DTYPE.fields[k][1] for k in ("sb", "dm_index", "downsamp", "width_native",
                                                   "t_native", "dm", "snr")] == [0, 4, 8, 12, 16, 24, 28]
+
+
+def test_variant_table():
+    import paper_2205_12362_b300 as fdd
+    vs = fdd.variants()
+    assert len(vs) >= 4
+    assert {v["bytes_per_sample"] for v in vs} == {1, 2}
+    for v in vs:
+        assert v["dm_per_block"] % 4 == 0 and v["threads"] % 32 == 0
+        assert v["tile"] > 0 and v["tile"] % 128 == 0

@@ -235,3 +235,76 @@ def test_repeat_is_deterministic(fdd):
     ca, na = a.candidates()
     cb, nb = b.candidates()
     assert na == nb and (ca == cb).all()
+
+
+def variant_case():
+    rng = np.random.default_rng(42)
+    n_tab, n_chan, n_sb, n_out = 2, 70, 3, 1500
+    f = synth.channel_freqs(n_chan)
+    ranges = [dict(dm0=0.0, ddm=1.5, n_dm=45, downsamp=1, widths=[1, 4, 16]),
+              dict(dm0=67.5, ddm=3.0, n_dm=37, downsamp=2, widths=[1, 8])]
+    need = max(int(oracle.delays(f, T_SAMP, r["dm0"], r["ddm"], r["n_dm"], r["downsamp"]).max())
+               * r["downsamp"] + n_out for r in ranges) + 3
+    x = synth.filterbank(77, n_tab, n_chan, need)
+    sb = rng.integers(0, n_tab, size=(n_sb, n_chan)).astype(np.int16)
+    return x, f, ranges, sb, need, n_out
+
+
+@pytest.fixture(scope="module")
+def variant_oracle():
+    x, f, ranges, sb, n_in, n_out = variant_case()
+    ora, os_ = oracle_candidate_superset(x, sb, f, T_SAMP, ranges, 4.0, n_out, n_in, return_series=True)
+    return ora, os_
+
+
+def _all_variants():
+    try:
+        import paper_2205_12362_b300 as m
+        return m.variants()
+    except Exception:
+        return []
+
+
+@pytest.mark.parametrize("v", _all_variants(), ids=lambda v: "v%d_E%d_bd%d_t%d" % (
+    v["index"], v["bytes_per_sample"], v["dm_per_block"], v["tile"]))
+@pytest.mark.parametrize("cc", [0, 2, 8])
+def test_every_kernel_variant(fdd, variant_oracle, v, cc):
+    import torch
+    x, f, ranges, sb, n_in, n_out = variant_case()
+    plan = fdd.Plan(x.shape[0], x.shape[1], sb.shape[0], f, T_SAMP, ranges, 4.0, sb)
+    r = 0 if v["bytes_per_sample"] == 1 else 1
+    plan.set_config(r, v["index"], cc)
+    cfg = plan.get_config(r)
+    assert cfg["variant"] == v["index"] and (cc == 0 or cfg["chan_per_stage"] == cc)
+    res = plan.search(to_dev(x), n_in, n_out, want_series=True, cap=1 << 18)
+    torch.cuda.synchronize()
+    ora, os_ = variant_oracle
+    g = plan.series_views(res.series, n_out)
+    assert (g[r].cpu().numpy() == os_[r]).all()
+    gpu, n = res.candidates()
+    compare_candidates(gpu, ora, 4.0)
+
+
+def test_wrong_width_variant_rejected(fdd):
+    x, f, ranges, sb, n_in, n_out = variant_case()
+    plan = fdd.Plan(x.shape[0], x.shape[1], sb.shape[0], f, T_SAMP, ranges, 4.0, sb)
+    v16 = [v for v in fdd.variants() if v["bytes_per_sample"] == 2][0]
+    with pytest.raises(fdd.FddError):
+        plan.set_config(0, v16["index"])
+    assert plan.get_config(0)["variant"] >= 0
+
+
+def test_autotune_then_parity(fdd, variant_oracle):
+    import torch
+    x, f, ranges, sb, n_in, n_out = variant_case()
+    plan = fdd.Plan(x.shape[0], x.shape[1], sb.shape[0], f, T_SAMP, ranges, 4.0, sb)
+    dx = to_dev(x)
+    cfgs = plan.autotune(dx, n_in, n_out, reps=2)
+    assert all(c["tuned_ms"] > 0 for c in cfgs)
+    res = plan.search(dx, n_in, n_out, want_series=True, cap=1 << 18)
+    torch.cuda.synchronize()
+    ora, os_ = variant_oracle
+    for g, o in zip(plan.series_views(res.series, n_out), os_):
+        assert (g.cpu().numpy() == o).all()
+    gpu, n = res.candidates()
+    compare_candidates(gpu, ora, 4.0)
