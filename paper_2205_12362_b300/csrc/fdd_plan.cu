@@ -21,7 +21,8 @@ thread_local std::string g_last_error;
 // value; 4148.808 is the standard constant.
 constexpr double kDispersionConstant = 4148.808;
 
-constexpr size_t kSmemBudget = 112 * 1024;  // two blocks per SM fit in 228 KB
+constexpr size_t kSmemBudget = 200 * 1024;   // per block; the tuner weighs occupancy by timing
+constexpr size_t kDefaultSmem = 100 * 1024;  // untuned default: leave room for two blocks per SM
 
 int cuda_fail(cudaError_t e, const char* what) {
     g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
@@ -128,6 +129,8 @@ HostTables build_tables(const fdd_plan* p, const RangeState& r, const fdd::Dedis
 }
 
 int pick_cc(const fdd::DedispVariant& v, int Lw) {
+    for (int cc : {32, 16, 8, 4, 2})
+        if (fdd::dedisp_cc_ok(v, Lw, cc, kDefaultSmem)) return cc;
     for (int cc : {32, 16, 8, 4, 2})
         if (fdd::dedisp_cc_ok(v, Lw, cc, kSmemBudget)) return cc;
     return 0;
@@ -590,7 +593,7 @@ int fdd_plan_autotune(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64
             const HostTables h = build_tables(plan, r, dv);
             if (h.Lw < 0) continue;
             bool uploaded = false;
-            for (int cc : {8, 16, 32, 64}) {
+            for (int cc : {8, 16, 32, 48, 64}) {
                 if (!fdd::dedisp_cc_ok(dv, h.Lw, cc, kSmemBudget)) continue;
                 if (!uploaded) {
                     if ((rc = upload_tables(r, h)) != FDD_OK) break;

@@ -23,7 +23,9 @@
 //     acc_a - (acc_b << 8).  Lanes hold <= 256 channels of 255 and are folded
 //     into int32 totals every 256 channels.  uint16 samples (downsampled
 //     ranges) use acc_a += x, acc_b += x >> 16, exact without folding.
-//     Channels are taken in pairs so each accumulator update is one IADD3.
+//     Channels are taken in groups of four: every accumulator update is one
+//     IADD3 over two channels, the group's loads are all issued before its
+//     adds, and the next group's offsets are fetched ahead.
 //   * Per-trial staged offsets come from a host table laid out
 //     [DM block][channel][trial], so a stage's offsets are one coalesced read.
 #include "fdd_internal.cuh"
@@ -48,6 +50,13 @@ __device__ __forceinline__ void load_offsets(const int32_t* p, int32_t (&o)[N]) 
         o[2] = v.z;
         o[3] = v.w;
     }
+}
+
+// 32-bit shared-window load (keeps address arithmetic in 32 bits).
+__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
 }
 
 template <int E, int NW, int DPW, int WARPS, int MAXIT>
@@ -182,7 +191,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_dedisp(const DedispArgs a) {
             return x >> 16;                     // high uint16 sample
     };
 
-    const uint8_t* s_lane = s_rows + 4 * lane;
+    const uint32_t s_lane32 = static_cast<uint32_t>(__cvta_generic_to_shared(s_rows)) + 4u * lane;
     const int32_t* s_off_w = s_off + warp * DPW;
 
     int ncc = min(CC, a.n_chan);
@@ -203,30 +212,57 @@ __global__ void __launch_bounds__(WARPS * 32) k_dedisp(const DedispArgs a) {
             }
             since_flush += ncc;
         }
+        // Channels in groups of four: offsets of the next group are fetched
+        // before this group's 4*DPW*NW loads, and all loads of a group are
+        // issued before its adds, so LDS latency overlaps within a warp.
         int cc = 0;
+        int32_t og[4][DPW];
+        if (ncc >= 4) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) load_offsets<DPW>(s_off_w + u * BD, og[u]);
+        }
 #pragma unroll 1
-        for (; cc + 1 < ncc; cc += 2) {
-            int32_t o0[DPW], o1[DPW];
-            load_offsets<DPW>(s_off_w + cc * BD, o0);
-            load_offsets<DPW>(s_off_w + (cc + 1) * BD, o1);
+        for (; cc + 3 < ncc; cc += 4) {
+            int32_t on[4][DPW];
+            const bool more = cc + 7 < ncc;
+            if (more) {
+#pragma unroll
+                for (int u = 0; u < 4; u++) load_offsets<DPW>(s_off_w + (cc + 4 + u) * BD, on[u]);
+            }
+            uint32_t x[4][DPW][NW];
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+#pragma unroll
+                for (int j = 0; j < DPW; j++) {
+                    const uint32_t ad = s_lane32 + static_cast<uint32_t>(og[u][j]);
+#pragma unroll
+                    for (int k = 0; k < NW; k++) x[u][j][k] = lds32(ad + 128u * k);
+                }
 #pragma unroll
             for (int j = 0; j < DPW; j++)
 #pragma unroll
                 for (int k = 0; k < NW; k++) {
-                    const uint32_t x0 = *reinterpret_cast<const uint32_t*>(s_lane + o0[j] + 128 * k);
-                    const uint32_t x1 = *reinterpret_cast<const uint32_t*>(s_lane + o1[j] + 128 * k);
-                    acc_a[j][k] = acc_a[j][k] + x0 + x1;
-                    acc_b[j][k] = acc_b[j][k] + split(x0) + split(x1);
+                    acc_a[j][k] = acc_a[j][k] + x[0][j][k] + x[1][j][k];
+                    acc_b[j][k] = acc_b[j][k] + split(x[0][j][k]) + split(x[1][j][k]);
+                    acc_a[j][k] = acc_a[j][k] + x[2][j][k] + x[3][j][k];
+                    acc_b[j][k] = acc_b[j][k] + split(x[2][j][k]) + split(x[3][j][k]);
                 }
+            if (more) {
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+#pragma unroll
+                    for (int j = 0; j < DPW; j++) og[u][j] = on[u][j];
+            }
         }
-        if (cc < ncc) {
+#pragma unroll 1
+        for (; cc < ncc; cc++) {  // remainder (n_chan not a multiple of 4)
             int32_t o0[DPW];
             load_offsets<DPW>(s_off_w + cc * BD, o0);
 #pragma unroll
             for (int j = 0; j < DPW; j++)
 #pragma unroll
                 for (int k = 0; k < NW; k++) {
-                    const uint32_t x0 = *reinterpret_cast<const uint32_t*>(s_lane + o0[j] + 128 * k);
+                    const uint32_t x0 = lds32(s_lane32 + static_cast<uint32_t>(o0[j]) + 128u * k);
                     acc_a[j][k] += x0;
                     acc_b[j][k] += split(x0);
                 }
@@ -294,20 +330,19 @@ struct Entry {
 const Entry kEntries[] = {
     // uint8 input (native-rate ranges)
     FDD_V(1, 4, 2, 8, 4),    // BD 16, T 512, 256 threads
-    FDD_V(1, 4, 2, 16, 2),   // BD 32, T 512, 512 threads
+    FDD_V(1, 4, 2, 16, 4),   // BD 32, T 512, 512 threads
     FDD_V(1, 4, 4, 8, 4),    // BD 32, T 512, 256 threads
     FDD_V(1, 2, 4, 8, 4),    // BD 32, T 256, 256 threads
-    FDD_V(1, 2, 2, 16, 2),   // BD 32, T 256, 512 threads
-    FDD_V(1, 8, 1, 16, 2),   // BD 16, T 1024, 512 threads
-    FDD_V(1, 4, 1, 16, 2),   // BD 16, T 512, 512 threads
-    FDD_V(1, 2, 4, 16, 2),   // BD 64, T 256, 512 threads
+    FDD_V(1, 2, 2, 16, 4),   // BD 32, T 256, 512 threads
+    FDD_V(1, 4, 1, 16, 4),   // BD 16, T 512, 512 threads
+    FDD_V(1, 2, 4, 16, 4),   // BD 64, T 256, 512 threads
+    FDD_V(1, 1, 4, 16, 4),   // BD 64, T 128, 512 threads
     // uint16 input (downsampled ranges)
     FDD_V(2, 4, 2, 8, 4),    // BD 16, T 256
-    FDD_V(2, 4, 2, 16, 2),   // BD 32, T 256
+    FDD_V(2, 4, 2, 16, 4),   // BD 32, T 256
     FDD_V(2, 4, 4, 8, 4),    // BD 32, T 256
     FDD_V(2, 8, 2, 8, 4),    // BD 16, T 512
-    FDD_V(2, 8, 1, 16, 2),   // BD 16, T 512
-    FDD_V(2, 2, 4, 16, 2),   // BD 64, T 128
+    FDD_V(2, 2, 4, 16, 4),   // BD 64, T 128
 };
 #undef FDD_V
 
