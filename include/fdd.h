@@ -224,6 +224,33 @@ int fdd_plan_set_timing(fdd_plan* plan, int32_t enable);
 int fdd_plan_stage_times(fdd_plan* plan, int32_t max_n, int32_t* kind, int32_t* range, float* ms,
                          int32_t* n_stages);
 
+/* Allocation-free search (no counterpart in the paper: it exists for callers
+ * of this library that cannot allocate device memory at search time -- a
+ * real-time thread that must not block in the CUDA allocator, a process whose
+ * GPU memory is granted by an external arbiter only at start-up, code
+ * certified to allocate only during initialisation).
+ * Same as fdd_search, except that the workspace is a file-scope device array
+ * of FDD_STATIC_SCRATCH_BYTES inside the library instead of a caller buffer;
+ * the caller still passes inputs, candidates, counter and optional series.
+ *   - The call makes no cudaMalloc/cudaFree and calls no allocating routine.
+ *     Stage timing must be off on the plan (it creates CUDA events), else
+ *     FDD_ERR_INVALID_ARG.
+ *   - The first call on each device resolves the array's device address with
+ *     cudaGetSymbolAddress, with that device current; make that first call
+ *     before any stream capture.
+ *   - Searches whose fdd_workspace_size(..., d_series == NULL) exceeds
+ *     FDD_STATIC_SCRATCH_BYTES return FDD_ERR_WORKSPACE with a message.
+ *   - All calls on a device share the one array, which keeps the previous
+ *     call's contents (the call re-zeroes what must start at zero).  Calls
+ *     whose GPU work overlaps (other streams, other host threads) race on it:
+ *     serialise them.
+ *   - Every GPU that loads the library's device code holds the array until
+ *     the process exits. */
+#define FDD_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+int fdd_search_static(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitch, int64_t n_out,
+                      int64_t t_offset_native, fdd_candidate* d_cands, int64_t cap, uint64_t* d_count,
+                      int32_t* d_series, fdd_stream_t stream);
+
 /* Human-readable text of an FDD_* code (static string). */
 const char* fdd_error_string(int code);
 

@@ -103,6 +103,7 @@ def _lib_raw():
     L.fdd_plan_get_config.argtypes = [_P, _I32, ctypes.POINTER(KernelConfig)]
     L.fdd_plan_set_config.argtypes = [_P, _I32, _I32, _I32]
     L.fdd_plan_autotune.argtypes = [_P, _P, _I64, _I64, _I64, _P, _SZ, _I32, _P]
+    L.fdd_search_static.argtypes = [_P, _P, _I64, _I64, _I64, _I64, _P, _I64, _P, _P, _P]
     L.fdd_plan_stage_times.argtypes = [_P, _I32, _P, _P, _P, ctypes.POINTER(_I32)]
     _lib = L
     return L
@@ -324,6 +325,23 @@ class Plan:
                                                ms.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n)),
                "fdd_plan_stage_times")
         return [(self.STAGE_NAMES[int(kind[i])], int(rng[i]), float(ms[i])) for i in range(k)]
+
+    STATIC_SCRATCH_BYTES = 64 * 1024 * 1024
+
+    def search_static(self, tabs, n_in, n_out, cands, count, t_offset=0, series=None, stream=None):
+        """Allocation-free search (include/fdd.h: fdd_search_static): the
+        library's static device array is the workspace; every output buffer
+        is the caller's.  For callers that cannot allocate device memory at
+        search time."""
+        torch = _torch()
+        if tabs.dim() != 3 or tuple(tabs.shape[:2]) != (self.n_tab, self.n_chan):
+            raise ValueError("tabs must be [n_tab][n_chan][pitch]")
+        code = _lib_raw().fdd_search_static(
+            self._h, _dev_ptr(tabs, "tabs", torch.uint8), int(n_in), int(tabs.shape[2]), int(n_out),
+            int(t_offset), _dev_ptr(cands, "cands"), int(cands.shape[0]), _dev_ptr(count, "count"),
+            _dev_ptr(series, "series", torch.int32) if series is not None else None, _stream_handle(stream))
+        _check(code, "fdd_search_static")
+        return SearchResult(cands=cands, count=count, series=series, cap=int(cands.shape[0]))
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

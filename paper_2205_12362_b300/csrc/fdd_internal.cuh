@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "fdd.h"
@@ -77,5 +78,10 @@ cudaError_t launch_boxcar(const BoxcarArgs& a, cudaStream_t s);
 // ---------------------------------------------------------------------------
 cudaError_t launch_downsample(const uint8_t* in, int64_t n_rows, int64_t n_in, int64_t in_pitch,
                               int D, uint16_t* out, int64_t out_pitch, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Library-internal helpers shared between host files.
+bool plan_timing_enabled(const fdd_plan* plan);
+void set_last_error(const std::string& msg);
 
 }  // namespace fdd

@@ -258,6 +258,11 @@ int check_search_args(const fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in,
 
 }  // namespace
 
+namespace fdd {
+bool plan_timing_enabled(const fdd_plan* plan) { return plan && plan->timing; }
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace fdd
+
 extern "C" {
 
 const char* fdd_version(void) { return "fdd 0.1 (sm_103a)"; }
