@@ -231,23 +231,52 @@ def run_fdd(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w, f, t, x, sb, n_in = make_workload(args.workload)
+    mode = args.mode or w.get("mode", "plain")
     plan = fdd.Plan(w["n_tab"], w["n_chan"], w["n_sb"], f, t, w["ranges"], w["thr"], sb)
     host = torch.from_numpy(x).pin_memory()
     tabs = host.to(dev)
-    ws = torch.empty(plan.workspace_size(n_in, w["n_out"], with_series=True), dtype=torch.uint8, device=dev)
-    cap = 1 << 20
-    cands = torch.empty((cap, 8), dtype=torch.int32, device=dev)
-    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    cap = 1 << 22
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
     stream = torch.cuda.current_stream()
-    tuned = None
-    if not args.no_autotune:
-        tuned = plan.autotune(tabs, n_in, w["n_out"], reps=3, workspace=ws, stream=stream)
-    plan.set_timing(True)
+    plans = [plan]
+    if mode in ("plain", "per_sb"):
+        ws = torch.empty(plan.workspace_size(n_in, w["n_out"], with_series=True), dtype=torch.uint8, device=dev)
+        cands = torch.empty((cap, 8), dtype=torch.int32, device=dev)
+        count = torch.zeros(1, dtype=torch.int64, device=dev)
+        if not args.no_autotune:
+            plan.autotune(tabs, n_in, w["n_out"], reps=3, workspace=ws, stream=stream)
+        if mode == "per_sb":
+            # the plain per-beam path: one single-SB plan per SB, searched one after another
+            cfgs = [plan.get_config(r) for r in range(len(w["ranges"]))]
+            plans = []
+            for s_i in range(w["n_sb"]):
+                p1 = fdd.Plan(w["n_tab"], w["n_chan"], 1, f, t, w["ranges"], w["thr"], sb[s_i:s_i + 1])
+                for r, c in enumerate(cfgs):
+                    p1.set_config(r, c["variant"], c["chan_per_stage"])
+                plans.append(p1)
+            ws = torch.empty(plans[0].workspace_size(n_in, w["n_out"], with_series=True), dtype=torch.uint8,
+                             device=dev)
+        for p_ in plans:
+            p_.set_timing(True)
 
-    def step():
-        return plan.search(tabs, n_in, w["n_out"], cap=cap, workspace=ws, cands=cands, count=count,
-                           stream=stream)
+        def step():
+            for p_ in plans:
+                p_.search(tabs, n_in, w["n_out"], cap=cap, workspace=ws, cands=cands, count=count, stream=stream)
+    else:
+        job = plan.make_job(tabs, n_in, w["n_out"], cap=cap)
+        cands, count = job.cands, job.count
+        plan.batch_prepare(w["n_out"])
+        if not args.no_autotune:
+            plan.batch_autotune([job], w["n_out"], reps=2, stream=stream)
+        plan.set_timing(True)
+        if mode == "graph":
+            graph = fdd.Graph(plan, [job], w["n_out"])
+
+            def step():
+                graph.launch(stream)
+        else:
+            def step():
+                plan.search_batch([job], w["n_out"], stream=stream)
 
     for _ in range(args.warmup):
         step()
@@ -272,10 +301,15 @@ def run_fdd(args):
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        st = plan.stage_times()
-        launches += len(st)
-        for name, r, ms in st:
-            stage_ms.setdefault("%s[%d]" % (name, r), []).append(ms)
+        per_step = {}
+        for p_ in plans:
+            st = p_.stage_times()
+            launches += len(st)
+            for name, r, ms in st:
+                key = "%s[%d]" % (name, r)
+                per_step[key] = per_step.get(key, 0.0) + ms
+        for key, ms in per_step.items():
+            stage_ms.setdefault(key, []).append(ms)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     wall1 = time.perf_counter()
@@ -323,14 +357,17 @@ def run_fdd(args):
 
     # roofline of the dominant kernel (dedispersion): channel-adds per launch
     ded = [v for k, v in stage_ms.items() if k.startswith("dedisperse")]
-    ded_ms = float(np.mean([np.mean(v) for v in ded])) if ded else None
-    adds_launch = adds_per_step(w) / max(1, len(ded))
+    ded_ms_step = float(sum(np.mean(v) for v in ded)) if ded else None   # all dedispersion work of a step
+    n_ded_launches = len(ded) * len(plans)
+    ded_ms = ded_ms_step / max(1, n_ded_launches) if ded else None
+    adds_launch = adds_per_step(w) / max(1, n_ded_launches)
     sm_mhz = clocks.get("sm_mhz")
     peak = N_SM * INT_LANES_PER_SM * ADDS_PER_LANE_OP * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
     achieved = adds_launch / (ded_ms / 1e3) / 1e12 if ded_ms else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s",
             "frac": (achieved / peak) if achieved else None, "traffic": profile_traffic(),
-            "kernel": "k_dedisp", "units_per_launch": adds_launch,
+            "kernel": "k_dedisp_persistent" if mode in ("batched", "graph") else "k_dedisp",
+            "units_per_launch": adds_launch,
             "peak_basis": "148 SM x 128 INT32 lanes x 2 adds/IADD3 x 2032 MHz (derived; no measured INT peak)",
             "peak_at_sampled_clock": (peak * sm_mhz / SM_MAX_MHZ_NOMINAL) if sm_mhz else None,
             "avg_launch_ms": ded_ms}
@@ -358,7 +395,7 @@ def run_fdd(args):
                    "n_out": w["n_out"], "n_in": n_in,
                    "dm_plan": [[r["dm0"], r["ddm"], r["n_dm"], r["downsamp"]] for r in w["ranges"]],
                    "widths": WIDTHS, "snr_thresh": w["thr"], "l2": "flushed (256 MB write) between steps",
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single", "mode": mode},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_units * world / e2e_s, "unit": "samples/s",
@@ -367,7 +404,8 @@ def run_fdd(args):
         "gpu_launches": launches,
         "clocks": clocks,
         "stages_ms": {k: float(np.mean(v)) for k, v in stage_ms.items()},
-        "kernel_config": [plan.get_config(r) for r in range(len(w["ranges"]))],
+        "kernel_config": ([plan.get_config(r) for r in range(len(w["ranges"]))] if mode in ("plain", "per_sb")
+                          else plan.batch_config()),
         "wall_s": wall1 - wall0,
     }
     if dist:
@@ -422,6 +460,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--mode", default=None, choices=["plain", "per_sb", "batched", "graph"],
+                    help="plain: per-range launches over all SBs; per_sb: one plan per SB (the plain per-beam "
+                         "path); batched: one persistent launch over everything; graph: the batched search "
+                         "replayed from a CUDA graph (default: the workload's own)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -54,6 +54,8 @@ enum {
 #define FDD_MAX_WIDTH 1024     /* largest boxcar width, in range samples */
 #define FDD_MAX_CHANNELS 16384
 #define FDD_MAX_TABS 256
+#define FDD_MAX_RANGES 8       /* DM ranges per plan in batched searches */
+#define FDD_MAX_BATCH_JOBS 64  /* chunks per batched search */
 
 /* One range of the DM plan (paper Table "dedispersion setup": each GPU
  * covers a DM range with its own step; Sec. "Downsampling" lets a range run
@@ -209,6 +211,59 @@ int fdd_plan_set_config(fdd_plan* plan, int32_t r, int32_t variant, int32_t chan
 int fdd_plan_autotune(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitch, int64_t n_out,
                       void* d_workspace, size_t workspace_bytes, int32_t reps, fdd_stream_t stream);
 
+/* ---------------------------------------------------------------------
+ * Batched search (the paper runs one AMBER instance per DM range on each of
+ * three GPUs per compound beam, Sec. "Computing performance"; here one GPU
+ * searches many chunks, all ranges and all SBs in one persistent launch).
+ * One job = one chunk of one compound beam; all jobs of a batch share the
+ * plan and n_out. */
+typedef struct {
+    const uint8_t* d_tabs;    /* device uint8 [n_tab][n_chan][pitch], 16-byte aligned */
+    int64_t n_in;             /* samples of data per row, >= n_out + max delay */
+    int64_t pitch;            /* multiple of 16 */
+    int64_t t_offset_native;  /* added to the job's candidate t_native */
+    void* d_workspace;        /* >= fdd_workspace_size(plan, n_in, n_out, d_series == NULL), 256-aligned */
+    size_t workspace_bytes;
+    fdd_candidate* d_cands;   /* device [cap] */
+    int64_t cap;
+    uint64_t* d_count;        /* device: true candidate count of this job */
+    int32_t* d_series;        /* NULL, or fdd_series_size() bytes for this job's series */
+} fdd_job;
+
+/* Prepare the plan's batched tables for chunks of n_out native samples with
+ * persistent-kernel variant `variant` (-1: keep the current one, or 0).
+ * Allocates and synchronises; must precede any capture of fdd_search_batch.
+ * Errors: UNSUPPORTED (more than FDD_MAX_RANGES ranges or 4 distinct D). */
+int fdd_batch_prepare(fdd_plan* plan, int64_t n_out, int32_t variant);
+
+/* Search n_jobs (1..FDD_MAX_BATCH_JOBS) chunks in four launches: prep,
+ * downsample, one persistent dedispersion launch over every (job, range, SB,
+ * DM block, time tile), one boxcar/threshold launch.  Results per job are
+ * identical to fdd_search on that job alone.  Prepares on first use of an
+ * n_out (not allowed while the stream is capturing).  Batched searches of
+ * one plan must not overlap on the GPU (they share the work counter). */
+int fdd_search_batch(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int64_t n_out, fdd_stream_t stream);
+
+/* Time every persistent variant on these jobs (`reps` batches each), keep
+ * the fastest.  Synchronous. */
+int fdd_batch_autotune(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int64_t n_out, int32_t reps,
+                       fdd_stream_t stream);
+
+/* Current persistent configuration: variant, resident grid, threads per
+ * block, DM trials per block, tuned batch time (ms, 0 if untuned). */
+int fdd_batch_config(const fdd_plan* plan, int32_t* variant, int32_t* grid, int32_t* threads,
+                     int32_t* dm_per_block, float* tuned_ms);
+
+/* A CUDA graph of fdd_search_batch for fixed jobs: create captures and
+ * instantiates it; launch replays it on a stream; update re-captures for new
+ * job buffers/offsets (same n_jobs) and updates the executable graph in
+ * place; destroy frees it.  The plan must outlive the graph. */
+typedef struct fdd_graph fdd_graph;
+int fdd_graph_create(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int64_t n_out, fdd_graph** out);
+int fdd_graph_update(fdd_graph* graph, const fdd_job* jobs, int32_t n_jobs);
+int fdd_graph_launch(fdd_graph* graph, fdd_stream_t stream);
+int fdd_graph_destroy(fdd_graph* graph);
+
 /* Per-stage GPU timing (tracing; the paper reports AMBER's time per stage,
  * Sec. "Computing performance").  With timing enabled, fdd_search records a
  * CUDA event pair around every kernel it enqueues; the pairs are reused by
@@ -216,10 +271,11 @@ int fdd_plan_autotune(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64
 int fdd_plan_set_timing(fdd_plan* plan, int32_t enable);
 
 /* Elapsed time of each stage of the last timed fdd_search on this plan,
- * in enqueue order.  Call after that search's stream has been synchronised
- * (FDD_ERR_CUDA "not ready" otherwise).  For stage k: kind[k] = 0
- * downsample, 1 SB-gather + dedispersion, 2 boxcar S/N + threshold;
- * range[k] = DM range index (downsample: its factor D); ms[k] milliseconds.
+ * in enqueue order (also of the last batched search or graph launch).  Call
+ * after that search's stream has been synchronised (FDD_ERR_CUDA "not ready"
+ * otherwise).  For stage k: kind[k] = 0 downsample, 1 SB-gather +
+ * dedispersion, 2 boxcar S/N + threshold, 3 batch prep; range[k] = DM range
+ * index (downsample: its factor D; batched stages: -1); ms[k] milliseconds.
  * Writes min(max_n, stages) entries; *n_stages receives the stage count. */
 int fdd_plan_stage_times(fdd_plan* plan, int32_t max_n, int32_t* kind, int32_t* range, float* ms,
                          int32_t* n_stages);

@@ -18,7 +18,7 @@ import numpy as np
 from .build import LIB as _LIB_PATH
 
 __all__ = ["Plan", "FddError", "FddUnavailable", "CAND_DTYPE", "decode_candidates", "downsample_u8",
-           "library_path", "version", "variants"]
+           "library_path", "version", "variants", "Job", "Graph"]
 
 CAND_DTYPE = np.dtype([("sb", np.int32), ("dm_index", np.int32), ("downsamp", np.int32),
                        ("width_native", np.int32), ("t_native", np.int64), ("dm", np.float32),
@@ -55,6 +55,13 @@ class KernelConfig(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class _Job(ctypes.Structure):
+    _fields_ = [("d_tabs", ctypes.c_void_p), ("n_in", ctypes.c_int64), ("pitch", ctypes.c_int64),
+                ("t_offset_native", ctypes.c_int64), ("d_workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t), ("d_cands", ctypes.c_void_p), ("cap", ctypes.c_int64),
+                ("d_count", ctypes.c_void_p), ("d_series", ctypes.c_void_p)]
 
 
 class _PlanDesc(ctypes.Structure):
@@ -103,6 +110,15 @@ def _lib_raw():
     L.fdd_plan_get_config.argtypes = [_P, _I32, ctypes.POINTER(KernelConfig)]
     L.fdd_plan_set_config.argtypes = [_P, _I32, _I32, _I32]
     L.fdd_plan_autotune.argtypes = [_P, _P, _I64, _I64, _I64, _P, _SZ, _I32, _P]
+    L.fdd_batch_prepare.argtypes = [_P, _I64, _I32]
+    L.fdd_search_batch.argtypes = [_P, ctypes.POINTER(_Job), _I32, _I64, _P]
+    L.fdd_batch_autotune.argtypes = [_P, ctypes.POINTER(_Job), _I32, _I64, _I32, _P]
+    L.fdd_batch_config.argtypes = [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                                   ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_float)]
+    L.fdd_graph_create.argtypes = [_P, ctypes.POINTER(_Job), _I32, _I64, ctypes.POINTER(_P)]
+    L.fdd_graph_update.argtypes = [_P, ctypes.POINTER(_Job), _I32]
+    L.fdd_graph_launch.argtypes = [_P, _P]
+    L.fdd_graph_destroy.argtypes = [_P]
     L.fdd_search_static.argtypes = [_P, _P, _I64, _I64, _I64, _I64, _P, _I64, _P, _P, _P]
     L.fdd_plan_stage_times.argtypes = [_P, _I32, _P, _P, _P, ctypes.POINTER(_I32)]
     _lib = L
@@ -167,6 +183,70 @@ class SearchResult:
         """Copy to host and decode (sorted by sb, dm_index, width, t)."""
         n = int(self.count.item())
         return decode_candidates(self.cands, min(n, self.cap)), n
+
+
+@dataclass
+class Job:
+    """One chunk of a batched search (include/fdd.h: fdd_job).  Tensors are
+    CUDA tensors owned by the caller; `workspace` must be sized by
+    Plan.workspace_size(n_in, n_out, with_series=series is None)."""
+    tabs: "object"
+    n_in: int
+    workspace: "object"
+    cands: "object"
+    count: "object"
+    t_offset: int = 0
+    series: "object" = None
+
+    def result(self):
+        return SearchResult(cands=self.cands, count=self.count, series=self.series, cap=int(self.cands.shape[0]))
+
+
+def _jobs_array(jobs):
+    import torch
+    arr = (_Job * len(jobs))()
+    for k, j in enumerate(jobs):
+        arr[k].d_tabs = _dev_ptr(j.tabs, "tabs", torch.uint8).value
+        arr[k].n_in = int(j.n_in)
+        arr[k].pitch = int(j.tabs.shape[2])
+        arr[k].t_offset_native = int(j.t_offset)
+        arr[k].d_workspace = _dev_ptr(j.workspace, "workspace").value
+        arr[k].workspace_bytes = int(j.workspace.numel() * j.workspace.element_size())
+        arr[k].d_cands = _dev_ptr(j.cands, "cands").value
+        arr[k].cap = int(j.cands.shape[0])
+        arr[k].d_count = _dev_ptr(j.count, "count").value
+        arr[k].d_series = _dev_ptr(j.series, "series", torch.int32).value if j.series is not None else None
+    return arr
+
+
+class Graph:
+    """CUDA graph of a batched search over fixed jobs (include/fdd.h: fdd_graph_*)."""
+
+    def __init__(self, plan, jobs, n_out):
+        h = ctypes.c_void_p()
+        self._plan = plan
+        self._jobs = list(jobs)
+        _check(_lib_raw().fdd_graph_create(plan.handle, _jobs_array(self._jobs), len(self._jobs), int(n_out),
+                                           ctypes.byref(h)), "fdd_graph_create")
+        self._h = h
+
+    def update(self, jobs):
+        self._jobs = list(jobs)
+        _check(_lib_raw().fdd_graph_update(self._h, _jobs_array(self._jobs), len(self._jobs)), "fdd_graph_update")
+
+    def launch(self, stream=None):
+        _check(_lib_raw().fdd_graph_launch(self._h, _stream_handle(stream)), "fdd_graph_launch")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib_raw().fdd_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def decode_candidates(cands, n):
@@ -309,7 +389,7 @@ class Plan:
     def set_timing(self, enable=True):
         _check(_lib_raw().fdd_plan_set_timing(self._h, int(bool(enable))), "fdd_plan_set_timing")
 
-    STAGE_NAMES = {0: "downsample", 1: "dedisperse", 2: "boxcar_snr"}
+    STAGE_NAMES = {0: "downsample", 1: "dedisperse", 2: "boxcar_snr", 3: "batch_prep"}
 
     def stage_times(self):
         """[(stage name, range or D, ms)] of the last timed search (after sync)."""
@@ -325,6 +405,39 @@ class Plan:
                                                ms.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n)),
                "fdd_plan_stage_times")
         return [(self.STAGE_NAMES[int(kind[i])], int(rng[i]), float(ms[i])) for i in range(k)]
+
+    # -- batched search
+    def make_job(self, tabs, n_in, n_out, t_offset=0, cap=1 << 16, want_series=False):
+        """Allocate a Job's output buffers and workspace with torch on tabs' device."""
+        torch = _torch()
+        dev = tabs.device
+        series = torch.empty(self.series_size(n_out) // 4, dtype=torch.int32, device=dev) if want_series else None
+        ws = torch.empty(self.workspace_size(n_in, n_out, with_series=series is None), dtype=torch.uint8, device=dev)
+        cands = torch.empty((max(int(cap), 1), 8), dtype=torch.int32, device=dev)
+        count = torch.zeros(1, dtype=torch.int64, device=dev)
+        return Job(tabs=tabs, n_in=int(n_in), workspace=ws, cands=cands, count=count, t_offset=int(t_offset),
+                   series=series)
+
+    def batch_prepare(self, n_out, variant=-1):
+        _check(_lib_raw().fdd_batch_prepare(self._h, int(n_out), int(variant)), "fdd_batch_prepare")
+
+    def search_batch(self, jobs, n_out, stream=None):
+        """All jobs in four launches (include/fdd.h: fdd_search_batch)."""
+        _check(_lib_raw().fdd_search_batch(self._h, _jobs_array(jobs), len(jobs), int(n_out),
+                                           _stream_handle(stream)), "fdd_search_batch")
+        return [j.result() for j in jobs]
+
+    def batch_autotune(self, jobs, n_out, reps=2, stream=None):
+        _check(_lib_raw().fdd_batch_autotune(self._h, _jobs_array(jobs), len(jobs), int(n_out), int(reps),
+                                             _stream_handle(stream)), "fdd_batch_autotune")
+        return self.batch_config()
+
+    def batch_config(self):
+        v, g, t, bd = _I32(), _I32(), _I32(), _I32()
+        ms = ctypes.c_float()
+        _check(_lib_raw().fdd_batch_config(self._h, ctypes.byref(v), ctypes.byref(g), ctypes.byref(t),
+                                           ctypes.byref(bd), ctypes.byref(ms)), "fdd_batch_config")
+        return dict(variant=v.value, grid=g.value, threads=t.value, dm_per_block=bd.value, tuned_ms=ms.value)
 
     STATIC_SCRATCH_BYTES = 64 * 1024 * 1024
 

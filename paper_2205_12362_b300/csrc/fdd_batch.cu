@@ -1,0 +1,387 @@
+// fdd_batch.cu -- host side of the batched search and its CUDA graphs.
+//
+// A batch is up to FDD_MAX_BATCH_JOBS chunks ("jobs") of one plan with the
+// same output length.  fdd_search_batch enqueues four launches whatever the
+// number of jobs, ranges and SBs: prep (zero moments and counters),
+// downsample (every job x every distinct D), ONE persistent dedispersion
+// launch over every (job, range, SB, DM block, time tile), and one boxcar
+// launch over every series.  Nothing is allocated or synchronised in the
+// call once fdd_batch_prepare has run for the chunk length, so the sequence
+// can be captured (fdd_graph_*).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <new>
+#include <vector>
+
+#include "fdd_plan_impl.h"
+
+using namespace fdd::host;
+
+namespace {
+
+void free_batch(BatchState& b) {
+    for (BatchRangeTables& t : b.tables) {
+        if (t.d_off) cudaFree(t.d_off);
+        if (t.d_base) cudaFree(t.d_base);
+    }
+    b.tables.clear();
+    if (b.d_ranges) cudaFree(b.d_ranges);
+    b.d_ranges = nullptr;
+    b.n_out = -1;
+}
+
+int batch_eligible(const fdd_plan* p) {
+    if (static_cast<int>(p->ranges.size()) > fdd::kMaxRanges)
+        return fail(FDD_ERR_UNSUPPORTED, "batched search supports at most FDD_MAX_RANGES DM ranges");
+    if (static_cast<int>(p->ds_factors.size()) > fdd::kMaxDs)
+        return fail(FDD_ERR_UNSUPPORTED, "batched search supports at most 4 distinct downsampling factors");
+    return FDD_OK;
+}
+
+// Build the batched-variant tables and the per-range descriptors for chunks
+// of n_out native output samples.  Allocates and synchronises.
+int prepare(fdd_plan* p, int64_t n_out, int variant) {
+    int rc = batch_eligible(p);
+    if (rc != FDD_OK) return rc;
+    if (variant < 0) variant = 0;
+    if (variant >= fdd::num_persistent_variants()) return fail(FDD_ERR_INVALID_ARG, "batch variant out of range");
+    BatchState& b = p->batch;
+    free_batch(b);
+    if (!b.d_counter) {
+        cudaError_t e = cudaMalloc(&b.d_counter, 256);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(batch counter)");
+    }
+    const fdd::PersistentVariant& pv = fdd::persistent_variant(variant);
+    const Layout L = make_layout(p, 0, n_out, true);
+    b.h_ranges.assign(p->ranges.size(), fdd::BatchRange{});
+    b.tables.assign(p->ranges.size(), BatchRangeTables{});
+    int64_t items = 0;
+    size_t smem = 0;
+    for (size_t ri = 0; ri < p->ranges.size(); ri++) {
+        const RangeState& r = p->ranges[ri];
+        const int E = (r.D == 1) ? 1 : 2;
+        const fdd::DedispVariant v = pv.as(E);
+        const HostTables h = build_tables(p, r, v);
+        if (h.Lw < 0) return fail(FDD_ERR_UNSUPPORTED, "DM step too large for one block's staged rows");
+        const int CC = pick_cc(v, h.Lw);
+        if (CC == 0) return fail(FDD_ERR_UNSUPPORTED, "DM step too large for one block's staged rows");
+        BatchRangeTables& t = b.tables[ri];
+        if ((rc = upload_tables(&t.d_off, &t.d_base, h)) != FDD_OK) return rc;
+        t.Lw = h.Lw;
+        t.CC = CC;
+        smem = std::max(smem, fdd::dedisp_smem_bytes(v, h.Lw, CC));
+        fdd::BatchRange& R = b.h_ranges[ri];
+        R.base = t.d_base;
+        R.off = t.d_off;
+        R.E = E;
+        R.D = r.D;
+        R.ds_index = (r.D == 1) ? -1
+                                : static_cast<int32_t>(std::find(p->ds_factors.begin(), p->ds_factors.end(), r.D) -
+                                                       p->ds_factors.begin());
+        R.n_dm = r.n_dm;
+        R.n_blk = (r.n_dm + v.bd() - 1) / v.bd();
+        R.n_out = static_cast<int32_t>(n_out / r.D);
+        R.n_tiles = (R.n_out + v.tile() - 1) / v.tile();
+        R.Lw = h.Lw;
+        R.CC = CC;
+        R.item_off = items;
+        items += static_cast<int64_t>(p->n_sb) * R.n_blk * R.n_tiles;
+        R.series_elem_off = static_cast<int64_t>(L.series_r[ri]);
+        R.series_off = static_cast<int64_t>(L.stat_r[ri]);
+        R.dm0 = r.dm0;
+        R.ddm = r.ddm;
+        R.dm_index0 = r.dm_index0;
+        R.n_width = r.n_width;
+        R.wmax = r.wmax;
+        for (int k = 0; k < FDD_MAX_WIDTHS; k++) {
+            R.widths[k] = r.widths[k];
+            R.inv_sqrt_w[k] = k < r.n_width ? static_cast<float>(1.0 / std::sqrt(static_cast<double>(r.widths[k]))) : 0.f;
+        }
+    }
+    cudaError_t e = cudaMalloc(&b.d_ranges, sizeof(fdd::BatchRange) * b.h_ranges.size());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(batch ranges)");
+    e = cudaMemcpy(b.d_ranges, b.h_ranges.data(), sizeof(fdd::BatchRange) * b.h_ranges.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(batch ranges)");
+    int per_sm = 0;
+    if ((e = fdd::persistent_occupancy(variant, smem, &per_sm)) != cudaSuccess) return cuda_fail(e, "occupancy");
+    if (per_sm < 1) return fail(FDD_ERR_UNSUPPORTED, "persistent kernel does not fit on an SM");
+    int sms = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device)) != cudaSuccess)
+        return cuda_fail(e, "device attribute");
+    b.variant = variant;
+    b.items_per_job = items;
+    b.series_per_job = static_cast<int64_t>(L.stat_bytes / (2 * sizeof(unsigned long long)));
+    b.grid = per_sm * sms;
+    b.smem = smem;
+    b.n_out = n_out;
+    b.tuned_ms = 0.f;
+    return FDD_OK;
+}
+
+int fill_params(const fdd_plan* p, const fdd_job* jobs, int32_t n_jobs, int64_t n_out, fdd::BatchParams& P) {
+    if (!jobs || n_jobs < 1 || n_jobs > fdd::kMaxBatchJobs) return fail(FDD_ERR_INVALID_ARG, "n_jobs outside [1, FDD_MAX_BATCH_JOBS]");
+    const BatchState& b = p->batch;
+    P = fdd::BatchParams{};
+    P.ranges = b.d_ranges;
+    P.sb_map = p->d_sb_map;
+    P.counter = b.d_counter;
+    P.items_per_job = b.items_per_job;
+    P.series_per_job = b.series_per_job;
+    P.n_range = static_cast<int32_t>(p->ranges.size());
+    P.n_jobs = n_jobs;
+    P.n_sb = p->n_sb;
+    P.n_chan = p->n_chan;
+    P.n_tab = p->n_tab;
+    P.n_ds = static_cast<int32_t>(p->ds_factors.size());
+    for (int k = 0; k < P.n_ds; k++) P.ds_factor[k] = p->ds_factors[k];
+    for (int j = 0; j < n_jobs; j++) {
+        const fdd_job& J = jobs[j];
+        if (!J.d_count || (J.cap > 0 && !J.d_cands) || J.cap < 0) return fail(FDD_ERR_INVALID_ARG, "bad job output buffers");
+        int rc = check_search_args(p, J.d_tabs, J.n_in, J.pitch, n_out, J.d_workspace, J.d_series);
+        if (rc != FDD_OK) return rc;
+        const Layout L = make_layout(p, J.n_in, n_out, J.d_series == nullptr);
+        if (J.workspace_bytes < L.total) return fail(FDD_ERR_WORKSPACE, "job workspace smaller than fdd_workspace_size()");
+        uint8_t* ws = static_cast<uint8_t*>(J.d_workspace);
+        fdd::BatchJob& B = P.jobs[j];
+        B.tabs = J.d_tabs;
+        B.tab_pitch = J.pitch;
+        B.n_in = J.n_in;
+        for (int k = 0; k < P.n_ds; k++) {
+            B.ds[k] = reinterpret_cast<uint16_t*>(ws + L.ds_off[k]);
+            B.ds_pitch[k] = L.ds_pitch[k];
+        }
+        B.series = J.d_series ? J.d_series : reinterpret_cast<int32_t*>(ws + L.series);
+        B.stat = reinterpret_cast<unsigned long long*>(ws + L.stat);
+        B.cands = J.d_cands;
+        B.cap = J.cap;
+        B.count = reinterpret_cast<unsigned long long*>(J.d_count);
+        B.t_offset = J.t_offset_native;
+    }
+    return FDD_OK;
+}
+
+// The four launches of a batch, each inside a stage-timing event pair when
+// the plan's timing is on (the events become graph nodes under capture).
+int enqueue(fdd_plan* p, const fdd::BatchParams& P, cudaStream_t s) {
+    int wmax = 1;
+    for (const RangeState& r : p->ranges) wmax = std::max(wmax, r.wmax);
+    stage_reset(p);
+    cudaError_t e;
+    if ((e = stage_begin(p, 3, -1, s)) != cudaSuccess) return cuda_fail(e, "timing event");
+    if ((e = fdd::launch_batch_prep(P, s)) != cudaSuccess) return cuda_fail(e, "batch prep launch");
+    if ((e = stage_end(p, s)) != cudaSuccess) return cuda_fail(e, "timing event");
+    if (P.n_ds > 0) {
+        if ((e = stage_begin(p, 0, -1, s)) != cudaSuccess) return cuda_fail(e, "timing event");
+        if ((e = fdd::launch_batch_downsample(P, s)) != cudaSuccess) return cuda_fail(e, "batch downsample launch");
+        if ((e = stage_end(p, s)) != cudaSuccess) return cuda_fail(e, "timing event");
+    }
+    if ((e = stage_begin(p, 1, -1, s)) != cudaSuccess) return cuda_fail(e, "timing event");
+    if ((e = fdd::launch_dedisp_persistent(p->batch.variant, P, p->batch.grid, p->batch.smem, s)) != cudaSuccess)
+        return cuda_fail(e, "persistent dedispersion launch");
+    if ((e = stage_end(p, s)) != cudaSuccess) return cuda_fail(e, "timing event");
+    if ((e = stage_begin(p, 2, -1, s)) != cudaSuccess) return cuda_fail(e, "timing event");
+    if ((e = fdd::launch_boxcar_batch(P, wmax, p->thr, s)) != cudaSuccess) return cuda_fail(e, "batch boxcar launch");
+    if ((e = stage_end(p, s)) != cudaSuccess) return cuda_fail(e, "timing event");
+    return FDD_OK;
+}
+
+}  // namespace
+
+struct fdd_graph {
+    fdd_plan* plan = nullptr;
+    int32_t n_jobs = 0;
+    int64_t n_out = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+};
+
+namespace {
+
+int capture(fdd_graph* g, const fdd::BatchParams& P, cudaGraph_t* out) {
+    cudaError_t e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    const int rc = enqueue(g->plan, P, g->cap_stream);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(g->cap_stream, &graph);
+    if (rc != FDD_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    *out = graph;
+    return FDD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fdd_batch_prepare(fdd_plan* plan, int64_t n_out, int32_t variant) {
+    if (!plan || n_out < 0) return fail(FDD_ERR_INVALID_ARG, "bad argument");
+    return prepare(plan, n_out, variant);
+}
+
+int fdd_search_batch(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int64_t n_out, fdd_stream_t stream) {
+    if (!plan || n_out < 0) return fail(FDD_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (plan->batch.n_out != n_out) {
+        cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(s, &st);
+        if (st != cudaStreamCaptureStatusNone)
+            return fail(FDD_ERR_INVALID_ARG, "call fdd_batch_prepare for this n_out before capturing");
+        const int rc = prepare(plan, n_out, plan->batch.variant);
+        if (rc != FDD_OK) return rc;
+    }
+    fdd::BatchParams P;
+    const int rc = fill_params(plan, jobs, n_jobs, n_out, P);
+    if (rc != FDD_OK) return rc;
+    return enqueue(plan, P, s);
+}
+
+int fdd_batch_autotune(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int64_t n_out, int32_t reps,
+                       fdd_stream_t stream) {
+    if (!plan || n_out < 0) return fail(FDD_ERR_INVALID_ARG, "bad argument");
+    if (reps < 1) reps = 1;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t ev0, ev1;
+    cudaError_t e;
+    if ((e = cudaEventCreate(&ev0)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    if ((e = cudaEventCreate(&ev1)) != cudaSuccess) {
+        cudaEventDestroy(ev0);
+        return cuda_fail(e, "cudaEventCreate");
+    }
+    int best = -1;
+    float best_ms = 1e30f;
+    int rc = FDD_OK;
+    for (int v = 0; v < fdd::num_persistent_variants(); v++) {
+        if (prepare(plan, n_out, v) != FDD_OK) continue;  // variant does not fit this plan
+        fdd::BatchParams P;
+        if ((rc = fill_params(plan, jobs, n_jobs, n_out, P)) != FDD_OK) break;
+        if ((rc = enqueue(plan, P, s)) != FDD_OK) break;  // warm-up
+        cudaEventRecord(ev0, s);
+        for (int k = 0; k < reps && rc == FDD_OK; k++) rc = enqueue(plan, P, s);
+        cudaEventRecord(ev1, s);
+        if (rc != FDD_OK) break;
+        if ((e = cudaEventSynchronize(ev1)) != cudaSuccess) {
+            rc = cuda_fail(e, "batch tuning");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        ms /= reps;
+        if (std::getenv("FDD_TUNE_VERBOSE")) {
+            const fdd::PersistentVariant& pv = fdd::persistent_variant(v);
+            std::fprintf(stderr, "fdd batch tune: variant %d (bd %d threads %d) grid %d: %.4f ms\n", v, pv.bd(),
+                         pv.threads(), plan->batch.grid, ms);
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (rc != FDD_OK) return rc;
+    if (best < 0) return fail(FDD_ERR_UNSUPPORTED, "no persistent variant fits this plan");
+    rc = prepare(plan, n_out, best);
+    if (rc == FDD_OK) plan->batch.tuned_ms = best_ms;
+    return rc;
+}
+
+int fdd_batch_config(const fdd_plan* plan, int32_t* variant, int32_t* grid, int32_t* threads, int32_t* dm_per_block,
+                     float* tuned_ms) {
+    if (!plan) return fail(FDD_ERR_INVALID_ARG, "null plan");
+    const BatchState& b = plan->batch;
+    if (b.variant < 0) return fail(FDD_ERR_INVALID_ARG, "batch not prepared");
+    const fdd::PersistentVariant& pv = fdd::persistent_variant(b.variant);
+    if (variant) *variant = b.variant;
+    if (grid) *grid = b.grid;
+    if (threads) *threads = pv.threads();
+    if (dm_per_block) *dm_per_block = pv.bd();
+    if (tuned_ms) *tuned_ms = b.tuned_ms;
+    return FDD_OK;
+}
+
+int fdd_graph_create(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int64_t n_out, fdd_graph** out) {
+    if (!plan || !out || n_out < 0) return fail(FDD_ERR_INVALID_ARG, "bad argument");
+    *out = nullptr;
+    if (plan->batch.n_out != n_out) {
+        const int rc = prepare(plan, n_out, plan->batch.variant);
+        if (rc != FDD_OK) return rc;
+    }
+    fdd::BatchParams P;
+    int rc = fill_params(plan, jobs, n_jobs, n_out, P);
+    if (rc != FDD_OK) return rc;
+    fdd_graph* g = new (std::nothrow) fdd_graph();
+    if (!g) return fail(FDD_ERR_NO_MEMORY, "host allocation");
+    g->plan = plan;
+    g->n_jobs = n_jobs;
+    g->n_out = n_out;
+    cudaError_t e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_fail(e, "cudaStreamCreate");
+    }
+    if ((rc = capture(g, P, &g->graph)) != FDD_OK) {
+        fdd_graph_destroy(g);
+        return rc;
+    }
+    if ((e = cudaGraphInstantiate(&g->exec, g->graph, 0)) != cudaSuccess) {
+        fdd_graph_destroy(g);
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    *out = g;
+    return FDD_OK;
+}
+
+int fdd_graph_update(fdd_graph* g, const fdd_job* jobs, int32_t n_jobs) {
+    if (!g || n_jobs != g->n_jobs) return fail(FDD_ERR_INVALID_ARG, "graph update needs the same number of jobs");
+    if (g->plan->batch.n_out != g->n_out) return fail(FDD_ERR_INVALID_ARG, "plan re-prepared for another n_out");
+    fdd::BatchParams P;
+    int rc = fill_params(g->plan, jobs, n_jobs, g->n_out, P);
+    if (rc != FDD_OK) return rc;
+    cudaGraph_t fresh = nullptr;
+    if ((rc = capture(g, P, &fresh)) != FDD_OK) return rc;
+    cudaGraphExecUpdateResultInfo info;
+    cudaError_t e = cudaGraphExecUpdate(g->exec, fresh, &info);
+    if (e != cudaSuccess) {  // topology changed: instantiate afresh
+        cudaGetLastError();
+        cudaGraphExec_t exec = nullptr;
+        if ((e = cudaGraphInstantiate(&exec, fresh, 0)) != cudaSuccess) {
+            cudaGraphDestroy(fresh);
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        cudaGraphExecDestroy(g->exec);
+        g->exec = exec;
+    }
+    cudaGraphDestroy(g->graph);
+    g->graph = fresh;
+    return FDD_OK;
+}
+
+int fdd_graph_launch(fdd_graph* g, fdd_stream_t stream) {
+    if (!g || !g->exec) return fail(FDD_ERR_INVALID_ARG, "null graph");
+    const cudaError_t e = cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    return FDD_OK;
+}
+
+int fdd_graph_destroy(fdd_graph* g) {
+    if (!g) return FDD_OK;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    delete g;
+    return FDD_OK;
+}
+
+}  // extern "C"
+
+void fdd_free_batch_state(fdd_plan* plan) {
+    free_batch(plan->batch);
+    if (plan->batch.d_counter) cudaFree(plan->batch.d_counter);
+    plan->batch.d_counter = nullptr;
+}

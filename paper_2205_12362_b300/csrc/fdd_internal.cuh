@@ -80,6 +80,73 @@ cudaError_t launch_downsample(const uint8_t* in, int64_t n_rows, int64_t n_in, i
                               int D, uint16_t* out, int64_t out_pitch, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
+// Batched search: many chunks ("jobs") of one plan, every range, in one
+// prep launch, one downsample launch, ONE persistent dedispersion launch and
+// one boxcar launch.  Jobs travel as kernel parameters (graph-capturable,
+// nothing to stage); per-range geometry lives in a plan-owned device table.
+constexpr int kMaxBatchJobs = FDD_MAX_BATCH_JOBS;
+constexpr int kMaxRanges = FDD_MAX_RANGES;
+constexpr int kMaxDs = 4;  // distinct downsampling factors per plan (batched)
+
+struct BatchRange {
+    const int32_t* base;          // batched-variant tables of this range
+    const int32_t* off;
+    int32_t E, D, ds_index;       // ds_index: -1 = raw input, else index into job.ds
+    int32_t n_dm, n_blk, n_tiles, n_out;
+    int32_t Lw, CC;
+    int64_t item_off;             // first work item of this range inside a job
+    int64_t series_elem_off;      // first series element of this range inside a job's series buffer
+    int64_t series_off;           // first series index (sb*n_dm + i) of this range inside a job
+    // S/N stage
+    double dm0, ddm;
+    int32_t dm_index0, n_width, wmax, pad_;
+    int32_t widths[FDD_MAX_WIDTHS];
+    float inv_sqrt_w[FDD_MAX_WIDTHS];
+};
+
+struct BatchJob {
+    const uint8_t* tabs;          // [n_tab][n_chan][tab_pitch]
+    int64_t tab_pitch;
+    int64_t n_in;
+    uint16_t* ds[kMaxDs];         // downsampled copies, one per distinct D
+    int64_t ds_pitch[kMaxDs];     // elements
+    int32_t* series;              // all ranges, packed as the per-range search does
+    unsigned long long* stat;     // [series_per_job][2]
+    fdd_candidate* cands;
+    int64_t cap;
+    unsigned long long* count;
+    int64_t t_offset;
+};
+
+struct BatchParams {
+    const BatchRange* ranges;     // device [n_range]
+    const int16_t* sb_map;
+    unsigned long long* counter;  // work-item counter, zeroed by the prep launch
+    int64_t items_per_job;
+    int64_t series_per_job;
+    int32_t n_range, n_jobs, n_sb, n_chan, n_tab, n_ds;
+    int32_t ds_factor[kMaxDs];
+    BatchJob jobs[kMaxBatchJobs];
+};
+
+// Persistent dedispersion variants (E is per work item, so one kernel serves
+// raw and downsampled ranges).
+struct PersistentVariant {
+    int NW, DPW, WARPS, MAXIT;
+    int bd() const { return WARPS * DPW; }
+    int threads() const { return WARPS * 32; }
+    DedispVariant as(int E) const { return DedispVariant{E, NW, DPW, WARPS, MAXIT}; }
+};
+int num_persistent_variants();
+const PersistentVariant& persistent_variant(int idx);
+// Resident blocks per SM of persistent variant idx with `smem` bytes of dynamic shared memory.
+cudaError_t persistent_occupancy(int idx, size_t smem, int* blocks_per_sm);
+cudaError_t launch_batch_prep(const BatchParams& p, cudaStream_t s);
+cudaError_t launch_batch_downsample(const BatchParams& p, cudaStream_t s);
+cudaError_t launch_dedisp_persistent(int idx, const BatchParams& p, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_boxcar_batch(const BatchParams& p, int wmax_all, float thr, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
 // Library-internal helpers shared between host files.
 bool plan_timing_enabled(const fdd_plan* plan);
 void set_last_error(const std::string& msg);

@@ -11,7 +11,7 @@
 #include <string>
 #include <vector>
 
-#include "fdd_internal.cuh"
+#include "fdd_plan_impl.h"
 
 namespace {
 
@@ -21,8 +21,10 @@ thread_local std::string g_last_error;
 // value; 4148.808 is the standard constant.
 constexpr double kDispersionConstant = 4148.808;
 
-constexpr size_t kSmemBudget = 200 * 1024;   // per block; the tuner weighs occupancy by timing
-constexpr size_t kDefaultSmem = 100 * 1024;  // untuned default: leave room for two blocks per SM
+}  // namespace
+
+namespace fdd {
+namespace host {
 
 int cuda_fail(cudaError_t e, const char* what) {
     g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
@@ -36,61 +38,42 @@ int fail(int code, const std::string& msg) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-}  // namespace
-
-struct RangeState {
-    double dm0 = 0, ddm = 0;
-    int32_t n_dm = 0, D = 1, n_width = 0;
-    int32_t widths[FDD_MAX_WIDTHS] = {};
-    int32_t wmax = 1;
-    int32_t dm_index0 = 0;
-    int32_t dmax = 0;                 // largest delay, range samples
-    std::vector<int32_t> delay;       // [n_dm][n_chan]
-    // kernel configuration and its device tables
-    int variant = -1;
-    int32_t Lw = 0, CC = 0;
-    float tuned_ms = 0.f;
-    int32_t* d_off = nullptr;         // [n_dm][n_chan]
-    int32_t* d_base = nullptr;        // [n_blk][n_chan]
-};
-
-struct fdd_plan {
-    int32_t n_tab = 0, n_chan = 0, n_sb = 0;
-    double t_samp = 0;
-    float thr = 0;
-    std::vector<double> freq;
-    std::vector<int16_t> sb_map;
-    int16_t* d_sb_map = nullptr;
-    std::vector<RangeState> ranges;
-    std::vector<int32_t> ds_factors;  // distinct D > 1
-    int64_t max_delay_native = 0;
-    int64_t n_dm_total = 0;
-    int device = 0;
-    // stage timing (fdd_plan_set_timing)
-    bool timing = false;
-    std::vector<cudaEvent_t> ev;          // 2 per stage, grown on demand
-    std::vector<int32_t> st_kind, st_range;
-};
-
-namespace {
-
-void free_range_tables(RangeState& r) {
-    if (r.d_off) cudaFree(r.d_off);
-    if (r.d_base) cudaFree(r.d_base);
-    r.d_off = nullptr;
-    r.d_base = nullptr;
+void stage_reset(fdd_plan* plan) {
+    plan->st_kind.clear();
+    plan->st_range.clear();
 }
 
-struct HostTables {
-    std::vector<int32_t> base;  // [n_blk][n_chan]
-    std::vector<int32_t> off;   // [n_blk][n_chan][BD]
-    int32_t Lw = 0;
-};
+// Record the opening event of a timed stage (no-op unless timing is on).
+cudaError_t stage_begin(fdd_plan* plan, int kind, int range, cudaStream_t s) {
+    if (!plan->timing) return cudaSuccess;
+    const size_t k = plan->st_kind.size();
+    while (plan->ev.size() < 2 * (k + 1)) {
+        cudaEvent_t e;
+        const cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return err;
+        plan->ev.push_back(e);
+    }
+    plan->st_kind.push_back(kind);
+    plan->st_range.push_back(range);
+    return cudaEventRecord(plan->ev[2 * k], s);
+}
+
+cudaError_t stage_end(fdd_plan* plan, cudaStream_t s) {
+    if (!plan->timing) return cudaSuccess;
+    return cudaEventRecord(plan->ev[2 * (plan->st_kind.size() - 1) + 1], s);
+}
+
+}  // namespace host
+}  // namespace fdd
+
+using namespace fdd::host;
+
+void fdd_free_batch_state(fdd_plan* plan);  // fdd_batch.cu
 
 // Staged-row geometry of range r for kernel variant v: for every (DM block,
 // channel) the aligned first staged sample, and for every trial its byte
 // offset (copy q = misalignment, aligned word) inside the channel slot.
-HostTables build_tables(const fdd_plan* p, const RangeState& r, const fdd::DedispVariant& v) {
+HostTables fdd::host::build_tables(const fdd_plan* p, const RangeState& r, const fdd::DedispVariant& v) {
     const int E = v.E, BD = v.bd(), NW = v.NW;
     const int A = 16 / E;  // alignment of the staged row start, in samples
     const int n_chan = p->n_chan;
@@ -128,7 +111,7 @@ HostTables build_tables(const fdd_plan* p, const RangeState& r, const fdd::Dedis
     return h;
 }
 
-int pick_cc(const fdd::DedispVariant& v, int Lw) {
+int fdd::host::pick_cc(const fdd::DedispVariant& v, int Lw) {
     for (int cc : {32, 16, 8, 4, 2})
         if (fdd::dedisp_cc_ok(v, Lw, cc, kDefaultSmem)) return cc;
     for (int cc : {32, 16, 8, 4, 2})
@@ -136,56 +119,19 @@ int pick_cc(const fdd::DedispVariant& v, int Lw) {
     return 0;
 }
 
-int upload_tables(RangeState& r, const HostTables& h) {
-    free_range_tables(r);
-    cudaError_t e = cudaMalloc(&r.d_off, h.off.size() * sizeof(int32_t));
+int fdd::host::upload_tables(int32_t** d_off, int32_t** d_base, const HostTables& h) {
+    cudaError_t e = cudaMalloc(d_off, h.off.size() * sizeof(int32_t));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(offset table)");
-    e = cudaMalloc(&r.d_base, h.base.size() * sizeof(int32_t));
+    e = cudaMalloc(d_base, h.base.size() * sizeof(int32_t));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(base table)");
-    e = cudaMemcpy(r.d_off, h.off.data(), h.off.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(*d_off, h.off.data(), h.off.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(offset table)");
-    e = cudaMemcpy(r.d_base, h.base.data(), h.base.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(*d_base, h.base.data(), h.base.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(base table)");
     return FDD_OK;
 }
 
-// Configure range r for kernel variant `variant` with channel stage CC
-// (0 = the largest that fits).
-int configure_range(fdd_plan* p, RangeState& r, int variant, int CC) {
-    if (variant < 0 || variant >= fdd::num_dedisp_variants())
-        return fail(FDD_ERR_INVALID_ARG, "kernel variant out of range");
-    const fdd::DedispVariant& v = fdd::dedisp_variant(variant);
-    if (v.E != (r.D == 1 ? 1 : 2)) return fail(FDD_ERR_INVALID_ARG, "kernel variant for the wrong sample width");
-    const HostTables h = build_tables(p, r, v);
-    if (h.Lw < 0) return fail(FDD_ERR_UNSUPPORTED, "DM step too large for one block's staged rows");
-    if (CC == 0) CC = pick_cc(v, h.Lw);
-    if (CC == 0 || !fdd::dedisp_cc_ok(v, h.Lw, CC, kSmemBudget))
-        return fail(FDD_ERR_UNSUPPORTED, "DM step too large for one block's staged rows; lower ddm or raise downsamp");
-    const int rc = upload_tables(r, h);
-    if (rc != FDD_OK) return rc;
-    r.variant = variant;
-    r.Lw = h.Lw;
-    r.CC = CC;
-    return FDD_OK;
-}
-
-int default_variant(int E) {
-    for (int k = 0; k < fdd::num_dedisp_variants(); k++)
-        if (fdd::dedisp_variant(k).E == E) return k;
-    return -1;
-}
-
-struct Layout {
-    size_t series = 0, series_bytes = 0;
-    size_t stat = 0, stat_bytes = 0;
-    std::vector<size_t> series_r;   // element offset of range r inside the series buffer
-    std::vector<size_t> stat_r;     // series-index offset of range r inside the stat buffer
-    std::vector<size_t> ds_off;     // per distinct D (plan order)
-    std::vector<int64_t> ds_pitch;  // uint16 elements
-    size_t total = 0;
-};
-
-Layout make_layout(const fdd_plan* p, int64_t n_in, int64_t n_out, bool with_series) {
+fdd::host::Layout fdd::host::make_layout(const fdd_plan* p, int64_t n_in, int64_t n_out, bool with_series) {
     Layout L;
     size_t series_elems = 0, n_series = 0;
     for (const RangeState& r : p->ranges) {
@@ -214,6 +160,58 @@ Layout make_layout(const fdd_plan* p, int64_t n_in, int64_t n_out, bool with_ser
     return L;
 }
 
+int fdd::host::check_search_args(const fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitch, int64_t n_out,
+                      const void* d_workspace, const void* d_series) {
+    if (!plan || !d_tabs || !d_workspace || n_in < 0 || n_out < 0 || pitch < n_in)
+        return fail(FDD_ERR_INVALID_ARG, "bad search argument");
+    if (n_out > (1LL << 30) || n_in > (1LL << 31) - 64)
+        return fail(FDD_ERR_UNSUPPORTED, "chunk longer than the kernels' 32-bit sample indexing");
+    if ((reinterpret_cast<uintptr_t>(d_tabs) & 15) || (pitch & 15) ||
+        (reinterpret_cast<uintptr_t>(d_workspace) & 255) || (reinterpret_cast<uintptr_t>(d_series) & 15))
+        return fail(FDD_ERR_MISALIGNED, "d_tabs/pitch must be 16-byte aligned, workspace 256-byte aligned");
+    for (const RangeState& r : plan->ranges)
+        if (n_out / r.D + r.dmax > n_in / r.D)
+            return fail(FDD_ERR_SHORT_INPUT, "n_in < n_out + max delay for some DM range");
+    return FDD_OK;
+}
+
+namespace {
+
+void free_range_tables(RangeState& r) {
+    if (r.d_off) cudaFree(r.d_off);
+    if (r.d_base) cudaFree(r.d_base);
+    r.d_off = nullptr;
+    r.d_base = nullptr;
+}
+
+// Configure range r for kernel variant `variant` with channel stage CC
+// (0 = the largest that fits).
+int configure_range(fdd_plan* p, RangeState& r, int variant, int CC) {
+    if (variant < 0 || variant >= fdd::num_dedisp_variants())
+        return fail(FDD_ERR_INVALID_ARG, "kernel variant out of range");
+    const fdd::DedispVariant& v = fdd::dedisp_variant(variant);
+    if (v.E != (r.D == 1 ? 1 : 2)) return fail(FDD_ERR_INVALID_ARG, "kernel variant for the wrong sample width");
+    const HostTables h = build_tables(p, r, v);
+    if (h.Lw < 0) return fail(FDD_ERR_UNSUPPORTED, "DM step too large for one block's staged rows");
+    if (CC == 0) CC = pick_cc(v, h.Lw);
+    if (CC == 0 || !fdd::dedisp_cc_ok(v, h.Lw, CC, kSmemBudget))
+        return fail(FDD_ERR_UNSUPPORTED, "DM step too large for one block's staged rows; lower ddm or raise downsamp");
+    free_range_tables(r);
+    const int rc = upload_tables(&r.d_off, &r.d_base, h);
+    if (rc != FDD_OK) return rc;
+    r.variant = variant;
+    r.Lw = h.Lw;
+    r.CC = CC;
+    return FDD_OK;
+}
+
+int default_variant(int E) {
+    for (int k = 0; k < fdd::num_dedisp_variants(); k++)
+        if (fdd::dedisp_variant(k).E == E) return k;
+    return -1;
+}
+
+
 fdd::DedispArgs dedisp_args(const fdd_plan* plan, const RangeState& r, size_t ri, const Layout& L,
                             const uint8_t* d_tabs, int64_t pitch, uint8_t* ws, int32_t* series,
                             unsigned long long* stat, int64_t n_in, int64_t n_out) {
@@ -241,20 +239,6 @@ fdd::DedispArgs dedisp_args(const fdd_plan* plan, const RangeState& r, size_t ri
     return a;
 }
 
-int check_search_args(const fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitch, int64_t n_out,
-                      const void* d_workspace, const void* d_series) {
-    if (!plan || !d_tabs || !d_workspace || n_in < 0 || n_out < 0 || pitch < n_in)
-        return fail(FDD_ERR_INVALID_ARG, "bad search argument");
-    if (n_out > (1LL << 30) || n_in > (1LL << 31) - 64)
-        return fail(FDD_ERR_UNSUPPORTED, "chunk longer than the kernels' 32-bit sample indexing");
-    if ((reinterpret_cast<uintptr_t>(d_tabs) & 15) || (pitch & 15) ||
-        (reinterpret_cast<uintptr_t>(d_workspace) & 255) || (reinterpret_cast<uintptr_t>(d_series) & 15))
-        return fail(FDD_ERR_MISALIGNED, "d_tabs/pitch must be 16-byte aligned, workspace 256-byte aligned");
-    for (const RangeState& r : plan->ranges)
-        if (n_out / r.D + r.dmax > n_in / r.D)
-            return fail(FDD_ERR_SHORT_INPUT, "n_in < n_out + max delay for some DM range");
-    return FDD_OK;
-}
 
 }  // namespace
 
@@ -387,6 +371,7 @@ int fdd_plan_create(const fdd_plan_desc* desc, const int16_t* sb_map_host, fdd_p
 
 int fdd_plan_destroy(fdd_plan* plan) {
     if (!plan) return FDD_OK;
+    fdd_free_batch_state(plan);
     for (cudaEvent_t e : plan->ev) cudaEventDestroy(e);
     for (RangeState& r : plan->ranges) free_range_tables(r);
     if (plan->d_sb_map) cudaFree(plan->d_sb_map);
@@ -440,26 +425,9 @@ int fdd_search(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitc
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     uint8_t* ws = static_cast<uint8_t*>(d_workspace);
-    plan->st_kind.clear();
-    plan->st_range.clear();
-    // Record an event pair around one stage when timing is on.
-    auto stage_begin = [&](int kind, int range) -> cudaError_t {
-        if (!plan->timing) return cudaSuccess;
-        const size_t k = plan->st_kind.size();
-        while (plan->ev.size() < 2 * (k + 1)) {
-            cudaEvent_t e;
-            const cudaError_t err = cudaEventCreate(&e);
-            if (err != cudaSuccess) return err;
-            plan->ev.push_back(e);
-        }
-        plan->st_kind.push_back(kind);
-        plan->st_range.push_back(range);
-        return cudaEventRecord(plan->ev[2 * k], s);
-    };
-    auto stage_end = [&]() -> cudaError_t {
-        if (!plan->timing) return cudaSuccess;
-        return cudaEventRecord(plan->ev[2 * (plan->st_kind.size() - 1) + 1], s);
-    };
+    fdd::host::stage_reset(plan);
+    auto stage_begin = [&](int kind, int range) { return fdd::host::stage_begin(plan, kind, range, s); };
+    auto stage_end = [&]() { return fdd::host::stage_end(plan, s); };
     int32_t* series = own_series ? reinterpret_cast<int32_t*>(ws + L.series) : d_series;
     unsigned long long* stat = reinterpret_cast<unsigned long long*>(ws + L.stat);
 
@@ -601,7 +569,8 @@ int fdd_plan_autotune(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64
             for (int cc : {8, 16, 32, 48, 64}) {
                 if (!fdd::dedisp_cc_ok(dv, h.Lw, cc, kSmemBudget)) continue;
                 if (!uploaded) {
-                    if ((rc = upload_tables(r, h)) != FDD_OK) break;
+                    free_range_tables(r);
+                    if ((rc = upload_tables(&r.d_off, &r.d_base, h)) != FDD_OK) break;
                     uploaded = true;
                 }
                 r.variant = v;

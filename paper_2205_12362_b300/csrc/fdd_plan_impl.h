@@ -1,0 +1,106 @@
+// fdd_plan_impl.h -- host-side plan state shared by the library's host files
+// (fdd_plan.cu: plans, per-range search, tuner; fdd_batch.cu: batched search
+// and graphs).  Not installed.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "fdd_internal.cuh"
+
+struct RangeState {
+    double dm0 = 0, ddm = 0;
+    int32_t n_dm = 0, D = 1, n_width = 0;
+    int32_t widths[FDD_MAX_WIDTHS] = {};
+    int32_t wmax = 1;
+    int32_t dm_index0 = 0;
+    int32_t dmax = 0;                 // largest delay, range samples
+    std::vector<int32_t> delay;       // [n_dm][n_chan]
+    // per-range launch: kernel configuration and its device tables
+    int variant = -1;
+    int32_t Lw = 0, CC = 0;
+    float tuned_ms = 0.f;
+    int32_t* d_off = nullptr;         // [n_blk][n_chan][BD]
+    int32_t* d_base = nullptr;        // [n_blk][n_chan]
+};
+
+// Device tables of one range for the batched persistent kernel.
+struct BatchRangeTables {
+    int32_t Lw = 0, CC = 0;
+    int32_t* d_off = nullptr;
+    int32_t* d_base = nullptr;
+};
+
+struct BatchState {
+    int variant = -1;                      // persistent kernel variant
+    int64_t n_out = -1;                    // chunk length the tables below were prepared for
+    std::vector<BatchRangeTables> tables;  // per range
+    fdd::BatchRange* d_ranges = nullptr;   // device copy of the per-range descriptors
+    std::vector<fdd::BatchRange> h_ranges;
+    unsigned long long* d_counter = nullptr;  // work-item counter of the persistent launch
+    int64_t items_per_job = 0;
+    int64_t series_per_job = 0;
+    int grid = 0;                          // resident blocks of the persistent launch
+    size_t smem = 0;
+    float tuned_ms = 0.f;
+};
+
+struct fdd_plan {
+    int32_t n_tab = 0, n_chan = 0, n_sb = 0;
+    double t_samp = 0;
+    float thr = 0;
+    std::vector<double> freq;
+    std::vector<int16_t> sb_map;
+    int16_t* d_sb_map = nullptr;
+    std::vector<RangeState> ranges;
+    std::vector<int32_t> ds_factors;  // distinct D > 1
+    int64_t max_delay_native = 0;
+    int64_t n_dm_total = 0;
+    int device = 0;
+    // stage timing (fdd_plan_set_timing)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;          // 2 per stage, grown on demand
+    std::vector<int32_t> st_kind, st_range;
+    BatchState batch;
+};
+
+namespace fdd {
+namespace host {
+
+constexpr size_t kSmemBudget = 200 * 1024;   // per block; the tuner weighs occupancy by timing
+constexpr size_t kDefaultSmem = 100 * 1024;  // untuned default: leave room for two blocks per SM
+
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+size_t align_up(size_t x, size_t a);
+
+// Stage timing (fdd_plan_set_timing): an event pair per enqueued kernel.
+// Kinds: 0 downsample, 1 dedispersion, 2 boxcar/threshold, 3 batch prep.
+void stage_reset(fdd_plan* plan);
+cudaError_t stage_begin(fdd_plan* plan, int kind, int range, cudaStream_t s);
+cudaError_t stage_end(fdd_plan* plan, cudaStream_t s);
+
+struct HostTables {
+    std::vector<int32_t> base;  // [n_blk][n_chan]
+    std::vector<int32_t> off;   // [n_blk][n_chan][BD]
+    int32_t Lw = 0;
+};
+HostTables build_tables(const fdd_plan* p, const RangeState& r, const DedispVariant& v);
+int upload_tables(int32_t** d_off, int32_t** d_base, const HostTables& h);
+int pick_cc(const DedispVariant& v, int Lw);
+
+struct Layout {
+    size_t series = 0, series_bytes = 0;
+    size_t stat = 0, stat_bytes = 0;
+    std::vector<size_t> series_r;   // element offset of range r inside the series buffer
+    std::vector<size_t> stat_r;     // series-index offset of range r inside the stat buffer
+    std::vector<size_t> ds_off;     // per distinct D (plan order)
+    std::vector<int64_t> ds_pitch;  // uint16 elements
+    size_t total = 0;
+};
+Layout make_layout(const fdd_plan* p, int64_t n_in, int64_t n_out, bool with_series);
+int check_search_args(const fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitch, int64_t n_out,
+                      const void* d_workspace, const void* d_series);
+
+}  // namespace host
+}  // namespace fdd

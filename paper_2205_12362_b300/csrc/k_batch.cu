@@ -1,0 +1,194 @@
+// k_batch.cu -- kernels of the batched search: many chunks ("jobs") of one
+// plan and all of its DM ranges in four launches (prep, downsample, one
+// persistent dedispersion launch, boxcar).  Jobs arrive as kernel parameters
+// (BatchParams), so the whole sequence can be captured in a CUDA graph.
+//
+// The persistent dedispersion kernel keeps every SM busy across ranges of
+// uneven length and sample width: resident blocks pull work items (job,
+// range, SB, DM block, time tile) from one atomic counter.  Items of one
+// (job, range, SB, time tile) differ only in DM block and are consecutive, so
+// blocks running at the same time share staged input rows in L2.  Each item
+// runs the same dedisp_tile as the per-range kernel, instantiated for raw
+// (uint8) and downsampled (uint16) samples.
+#include <algorithm>
+
+#include "boxcar_series.cuh"
+#include "dedisp_tile.cuh"
+#include "downsample_chunk.cuh"
+
+namespace fdd {
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_batch_prep(const BatchParams p) {
+    const BatchJob& J = p.jobs[blockIdx.y];
+    const int64_t words = 2 * p.series_per_job;
+    for (int64_t i = blockIdx.x * 256LL + threadIdx.x; i < words; i += 256LL * gridDim.x) J.stat[i] = 0ULL;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *J.count = 0ULL;
+        if (blockIdx.y == 0) *p.counter = 0ULL;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_batch_downsample(const BatchParams p, int64_t rows) {
+    const int job = blockIdx.z / p.n_ds, k = blockIdx.z - job * p.n_ds;
+    const BatchJob& J = p.jobs[job];
+    const int D = p.ds_factor[k];
+    const int64_t n_y = J.n_in / D;
+    const int64_t j0 = 8 * (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
+    if (j0 >= n_y) return;
+    for (int64_t row = blockIdx.y; row < rows; row += gridDim.y)
+        detail::downsample_chunk(J.tabs + row * J.tab_pitch, J.ds[k] + row * J.ds_pitch[k], n_y, D, j0);
+}
+
+template <int NW, int DPW, int WARPS, int MAXIT>
+__global__ void __launch_bounds__(WARPS * 32) k_dedisp_persistent(const BatchParams p) {
+    __shared__ unsigned long long s_item;
+    const unsigned long long total = static_cast<unsigned long long>(p.items_per_job) * p.n_jobs;
+    for (;;) {
+        __syncthreads();  // previous item's shared-memory reads are done
+        if (threadIdx.x == 0) s_item = atomicAdd(p.counter, 1ULL);
+        __syncthreads();
+        const unsigned long long it = s_item;
+        if (it >= total) break;
+        const int job = static_cast<int>(it / p.items_per_job);
+        int64_t rest = static_cast<int64_t>(it - static_cast<unsigned long long>(job) * p.items_per_job);
+        int r = 0;
+        while (r + 1 < p.n_range && rest >= p.ranges[r + 1].item_off) r++;
+        const BatchRange& R = p.ranges[r];
+        rest -= R.item_off;
+        const int blk = static_cast<int>(rest % R.n_blk);
+        rest /= R.n_blk;
+        const int tile = static_cast<int>(rest % R.n_tiles);
+        const int sb = static_cast<int>(rest / R.n_tiles);
+        const BatchJob& J = p.jobs[job];
+        DedispArgs a;
+        if (R.ds_index < 0) {
+            a.in = J.tabs;
+            a.pitch_bytes = J.tab_pitch;
+        } else {
+            a.in = reinterpret_cast<const uint8_t*>(J.ds[R.ds_index]);
+            a.pitch_bytes = J.ds_pitch[R.ds_index] * 2;
+        }
+        a.n_valid = J.n_in / R.D;
+        a.sb_map = p.sb_map;
+        a.base = R.base;
+        a.off = R.off;
+        a.series = J.series + R.series_elem_off;
+        a.stat = J.stat + 2 * R.series_off;
+        a.n_chan = p.n_chan;
+        a.n_dm = R.n_dm;
+        a.n_out = R.n_out;
+        a.n_sb = p.n_sb;
+        a.Lw = R.Lw;
+        a.CC = R.CC;
+        if (R.E == 1)
+            detail::dedisp_tile<1, NW, DPW, WARPS, MAXIT>(a, tile, blk, sb);
+        else
+            detail::dedisp_tile<2, NW, DPW, WARPS, MAXIT>(a, tile, blk, sb);
+    }
+}
+
+__global__ void __launch_bounds__(detail::kThreads) k_boxcar_batch(const BatchParams p, const float thr) {
+    const int64_t gq = blockIdx.x;
+    const int job = static_cast<int>(gq / p.series_per_job);
+    int64_t q = gq - static_cast<int64_t>(job) * p.series_per_job;
+    int r = 0;
+    while (r + 1 < p.n_range && q >= p.ranges[r + 1].series_off) r++;
+    const BatchRange& R = p.ranges[r];
+    q -= R.series_off;
+    if (R.n_out == 0) return;
+    const BatchJob& J = p.jobs[job];
+    BoxcarArgs a;
+    a.series = J.series + R.series_elem_off;
+    a.stat = J.stat + 2 * R.series_off;
+    a.cands = J.cands;
+    a.count = J.count;
+    a.cap = J.cap;
+    a.t_offset = J.t_offset;
+    a.dm0 = R.dm0;
+    a.ddm = R.ddm;
+    a.n_sb = p.n_sb;
+    a.n_dm = R.n_dm;
+    a.n_out = R.n_out;
+    a.dm_index0 = R.dm_index0;
+    a.D = R.D;
+    a.n_width = R.n_width;
+    a.wmax = R.wmax;
+    a.thr = thr;
+    for (int k = 0; k < FDD_MAX_WIDTHS; k++) {
+        a.widths[k] = R.widths[k];
+        a.inv_sqrt_w[k] = R.inv_sqrt_w[k];
+    }
+    detail::boxcar_series(a, q);
+}
+
+using PersistentFn = void (*)(const BatchParams);
+
+struct PEntry {
+    PersistentVariant v;
+    PersistentFn fn;
+};
+
+#define FDD_P(NW, DPW, WARPS, MAXIT) {{NW, DPW, WARPS, MAXIT}, k_dedisp_persistent<NW, DPW, WARPS, MAXIT>}
+const PEntry kPEntries[] = {
+    FDD_P(4, 2, 16, 4),  // BD 32, T 512 (uint8) / 256 (uint16), 512 threads
+    FDD_P(2, 4, 16, 4),  // BD 64, T 256 / 128, 512 threads
+    FDD_P(4, 2, 8, 4),   // BD 16, T 512 / 256, 256 threads
+    FDD_P(2, 4, 8, 4),   // BD 32, T 256 / 128, 256 threads
+    FDD_P(4, 1, 16, 4),  // BD 16, T 512 / 256, 512 threads
+};
+#undef FDD_P
+
+}  // namespace
+
+int num_persistent_variants() { return static_cast<int>(sizeof(kPEntries) / sizeof(kPEntries[0])); }
+
+const PersistentVariant& persistent_variant(int idx) { return kPEntries[idx].v; }
+
+cudaError_t persistent_occupancy(int idx, size_t smem, int* blocks_per_sm) {
+    const PEntry& e = kPEntries[idx];
+    cudaError_t err = cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (err != cudaSuccess) return err;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, e.fn, e.v.threads(), smem);
+}
+
+cudaError_t launch_batch_prep(const BatchParams& p, cudaStream_t s) {
+    const int64_t words = 2 * p.series_per_job;
+    const int gx = static_cast<int>(std::min<int64_t>(1024, std::max<int64_t>(1, (words + 4095) / 4096)));
+    k_batch_prep<<<dim3(gx, p.n_jobs), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_downsample(const BatchParams& p, cudaStream_t s) {
+    if (p.n_ds == 0) return cudaSuccess;
+    int64_t n_in_max = 0;
+    int d_min = 1 << 30;
+    for (int j = 0; j < p.n_jobs; j++) n_in_max = std::max<int64_t>(n_in_max, p.jobs[j].n_in);
+    for (int k = 0; k < p.n_ds; k++) d_min = std::min(d_min, p.ds_factor[k]);
+    const int64_t n_y = n_in_max / d_min;
+    if (n_y == 0) return cudaSuccess;
+    const int64_t rows = static_cast<int64_t>(p.n_tab) * p.n_chan;
+    dim3 grid(static_cast<unsigned>((n_y + 8 * 256 - 1) / (8 * 256)),
+              static_cast<unsigned>(std::min<int64_t>(rows, 65535)), static_cast<unsigned>(p.n_jobs * p.n_ds));
+    k_batch_downsample<<<grid, 256, 0, s>>>(p, rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dedisp_persistent(int idx, const BatchParams& p, int grid, size_t smem, cudaStream_t s) {
+    const PEntry& e = kPEntries[idx];
+    cudaError_t err = cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (err != cudaSuccess) return err;
+    e.fn<<<grid, e.v.threads(), smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_boxcar_batch(const BatchParams& p, int wmax_all, float thr, cudaStream_t s) {
+    const long long blocks = static_cast<long long>(p.n_jobs) * p.series_per_job;
+    if (blocks == 0) return cudaSuccess;
+    const size_t smem = detail::boxcar_smem_bytes(wmax_all);
+    k_boxcar_batch<<<static_cast<unsigned>(blocks), detail::kThreads, smem, s>>>(p, thr);
+    return cudaGetLastError();
+}
+
+}  // namespace fdd

@@ -10,46 +10,11 @@
 // HBM-bound: each thread reads 8*D consecutive bytes with 16-byte (or 8-byte
 // for D = 1) vector loads and writes 8 uint16 with one 16-byte store; rows
 // ride on gridDim.y.  Ragged tails and D not dividing 16 take a scalar path.
-#include "fdd_internal.cuh"
+#include "downsample_chunk.cuh"
 
 namespace fdd {
 
 namespace {
-
-template <int D>
-__device__ __forceinline__ void sum8_vec(const uint8_t* src, uint16_t* dst) {
-    uint32_t s[8];
-    if constexpr (D == 1) {
-        const uint2 v = *reinterpret_cast<const uint2*>(src);
-        const uint32_t w[2] = {v.x, v.y};
-#pragma unroll
-        for (int j = 0; j < 8; j++) s[j] = (w[j >> 2] >> (8 * (j & 3))) & 0xFFu;
-    } else {
-        constexpr int NV = (8 * D) / 16;  // uint4 loads
-        uint32_t w[4 * NV];
-#pragma unroll
-        for (int v = 0; v < NV; v++) {
-            const uint4 x = *reinterpret_cast<const uint4*>(src + 16 * v);
-            w[4 * v + 0] = x.x; w[4 * v + 1] = x.y; w[4 * v + 2] = x.z; w[4 * v + 3] = x.w;
-        }
-#pragma unroll
-        for (int j = 0; j < 8; j++) {
-            uint32_t acc = 0;
-#pragma unroll
-            for (int k = 0; k < D; k++) {
-                const int b = j * D + k;
-                acc += (w[b >> 2] >> (8 * (b & 3))) & 0xFFu;
-            }
-            s[j] = acc;
-        }
-    }
-    uint4 o;
-    o.x = s[0] | (s[1] << 16);
-    o.y = s[2] | (s[3] << 16);
-    o.z = s[4] | (s[5] << 16);
-    o.w = s[6] | (s[7] << 16);
-    *reinterpret_cast<uint4*>(dst) = o;
-}
 
 template <int D>
 __global__ void __launch_bounds__(256) k_downsample(const uint8_t* __restrict__ in, int64_t in_pitch, int64_t n_in,
@@ -63,7 +28,7 @@ __global__ void __launch_bounds__(256) k_downsample(const uint8_t* __restrict__ 
     uint16_t* dst = out + row * out_pitch;
     if constexpr (D > 0) {
         if (j0 + 8 <= n_y) {
-            sum8_vec<D>(src + j0 * D, dst + j0);
+            detail::sum8_vec<D>(src + j0 * D, dst + j0);
             return;
         }
     }

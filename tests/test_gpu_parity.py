@@ -308,3 +308,98 @@ def test_autotune_then_parity(fdd, variant_oracle):
         assert (g.cpu().numpy() == o).all()
     gpu, n = res.candidates()
     compare_candidates(gpu, ora, 4.0)
+
+
+# ---------------------------------------------------------------- batched search
+def batch_case(seed, n_in_extra):
+    rng = np.random.default_rng(seed)
+    n_tab, n_chan, n_sb, n_out = 3, 96, 4, 2100
+    f = synth.channel_freqs(n_chan)
+    ranges = [dict(dm0=0.0, ddm=1.0, n_dm=70, downsamp=1, widths=[1, 2, 8]),
+              dict(dm0=70.0, ddm=2.0, n_dm=33, downsamp=2, widths=[1, 4]),
+              dict(dm0=136.0, ddm=4.0, n_dm=20, downsamp=4, widths=[2]),
+              dict(dm0=216.0, ddm=8.0, n_dm=9, downsamp=8, widths=[1, 3])]
+    need = max(int(oracle.delays(f, T_SAMP, r["dm0"], r["ddm"], r["n_dm"], r["downsamp"]).max())
+               * r["downsamp"] + n_out for r in ranges)
+    sb = np.random.default_rng(99).integers(0, n_tab, size=(n_sb, n_chan)).astype(np.int16)
+    n_in = need + n_in_extra
+    start = 800 + oracle.delays(f, T_SAMP, 40.0 + 3 * seed, 1.0, 1)[0]
+    x = synth.filterbank(300 + seed, n_tab, n_chan, n_in, pulses=[dict(tab=seed % n_tab, start=start, width=4,
+                                                                       amp=22.0)])
+    return x, f, ranges, sb, n_in, n_out
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+def test_batched_equals_single(fdd, variant):
+    import torch
+    cases = [batch_case(s, e) for s, e in [(0, 0), (1, 7), (2, 33)]]
+    x0, f, ranges, sb, _, n_out = cases[0]
+    plan = fdd.Plan(x0.shape[0], x0.shape[1], sb.shape[0], f, T_SAMP, ranges, 5.0, sb)
+    plan.batch_prepare(n_out, variant)
+    assert plan.batch_config()["variant"] == variant
+    jobs, singles = [], []
+    for k, (x, _, _, _, n_in, _) in enumerate(cases):
+        dx = to_dev(x)
+        jobs.append(plan.make_job(dx, n_in, n_out, t_offset=1000 * k, cap=1 << 16, want_series=(k != 1)))
+        singles.append(plan.search(dx, n_in, n_out, t_offset=1000 * k, cap=1 << 16, want_series=True))
+    res = plan.search_batch(jobs, n_out)
+    torch.cuda.synchronize()
+    for k, (r, s1) in enumerate(zip(res, singles)):
+        if r.series is not None:
+            assert torch.equal(r.series, s1.series), "job %d series" % k
+        cb, nb = r.candidates()
+        cs, ns = s1.candidates()
+        assert nb == ns and (cb == cs).all(), "job %d candidates" % k
+    # and against the oracle for one job
+    x, f, ranges, sb, n_in, n_out = cases[2]
+    ora, os_ = oracle_candidate_superset(x, sb, f, T_SAMP, ranges, 5.0, n_out, n_in, t_offset=2000,
+                                         return_series=True)
+    for g, o in zip(plan.series_views(res[2].series, n_out), os_):
+        assert (g.cpu().numpy() == o).all()
+    compare_candidates(res[2].candidates()[0], ora, 5.0)
+
+
+def test_batch_graph_and_update(fdd):
+    import torch
+    cases = [batch_case(s, 0) for s in (3, 4)]
+    x0, f, ranges, sb, n_in, n_out = cases[0]
+    plan = fdd.Plan(x0.shape[0], x0.shape[1], sb.shape[0], f, T_SAMP, ranges, 5.0, sb)
+    plan.batch_prepare(n_out)
+    dxs = [to_dev(c[0]) for c in cases]
+    jobs = [plan.make_job(dx, c[4], n_out, t_offset=7, want_series=True) for dx, c in zip(dxs, cases)]
+    ref = [plan.search(dx, c[4], n_out, t_offset=7, want_series=True) for dx, c in zip(dxs, cases)]
+    g = fdd.Graph(plan, jobs, n_out)
+    for _ in range(2):
+        g.launch()
+        torch.cuda.synchronize()
+        for j, r in zip(jobs, ref):
+            assert torch.equal(j.series, r.series)
+            a, na = j.result().candidates()
+            b, nb = r.candidates()
+            assert na == nb and (a == b).all()
+    # swap the inputs and shift the time offsets through an update
+    jobs2 = [plan.make_job(dx, c[4], n_out, t_offset=5000, want_series=True) for dx, c in zip(dxs[::-1], cases[::-1])]
+    g.update(jobs2)
+    g.launch()
+    torch.cuda.synchronize()
+    for j, r in zip(jobs2, ref[::-1]):
+        assert torch.equal(j.series, r.series)
+        a, na = j.result().candidates()
+        b, nb = r.candidates()
+        assert na == nb
+        assert (a["t_native"] - b["t_native"] == 5000 - 7).all()
+    g.close()
+
+
+def test_batch_autotune_keeps_parity(fdd):
+    import torch
+    x, f, ranges, sb, n_in, n_out = batch_case(5, 0)
+    plan = fdd.Plan(x.shape[0], x.shape[1], sb.shape[0], f, T_SAMP, ranges, 5.0, sb)
+    dx = to_dev(x)
+    job = plan.make_job(dx, n_in, n_out, want_series=True)
+    cfg = plan.batch_autotune([job], n_out, reps=1)
+    assert cfg["tuned_ms"] > 0 and cfg["grid"] > 0
+    res = plan.search_batch([job], n_out)[0]
+    ref = plan.search(dx, n_in, n_out, want_series=True)
+    torch.cuda.synchronize()
+    assert torch.equal(res.series, ref.series)
