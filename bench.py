@@ -302,7 +302,7 @@ def run_fdd(args):
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         per_step = {}
-        for p_ in plans:
+        for p_ in (plans if mode != "graph" else []):
             st = p_.stage_times()
             launches += len(st)
             for name, r, ms in st:
@@ -313,6 +313,16 @@ def run_fdd(args):
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     wall1 = time.perf_counter()
+    if mode == "graph":
+        # graphs carry no stage events: the kernels' own times come from the
+        # same batched launches run directly, right after the timed loop
+        launches = (3 + int(any(r["downsamp"] > 1 for r in w["ranges"]))) * args.steps
+        for _ in range(min(args.steps, 20)):
+            flush.zero_()
+            plan.search_batch([job], w["n_out"], stream=stream)
+            stream.synchronize()
+            for name, r, ms in plan.stage_times():
+                stage_ms.setdefault("%s[%d]" % (name, r), []).append(ms)
     if dist:
         dist.barrier()
     t_hi = time.time()

@@ -257,7 +257,8 @@ int fdd_batch_config(const fdd_plan* plan, int32_t* variant, int32_t* grid, int3
 /* A CUDA graph of fdd_search_batch for fixed jobs: create captures and
  * instantiates it; launch replays it on a stream; update re-captures for new
  * job buffers/offsets (same n_jobs) and updates the executable graph in
- * place; destroy frees it.  The plan must outlive the graph. */
+ * place; destroy frees it.  The plan must outlive the graph.  Graphs carry
+ * no stage-timing events (time a graph launch as a whole). */
 typedef struct fdd_graph fdd_graph;
 int fdd_graph_create(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int64_t n_out, fdd_graph** out);
 int fdd_graph_update(fdd_graph* graph, const fdd_job* jobs, int32_t n_jobs);

@@ -203,7 +203,12 @@ namespace {
 int capture(fdd_graph* g, const fdd::BatchParams& P, cudaGraph_t* out) {
     cudaError_t e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    // Events recorded under capture only order nodes; they carry no timestamps,
+    // so stage timing is left out of graphs.
+    const bool timing = g->plan->timing;
+    g->plan->timing = false;
     const int rc = enqueue(g->plan, P, g->cap_stream);
+    g->plan->timing = timing;
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(g->cap_stream, &graph);
     if (rc != FDD_OK) {

@@ -20,7 +20,7 @@ namespace fdd {
 
 namespace {
 
-__global__ void __launch_bounds__(256) k_batch_prep(const BatchParams p) {
+__global__ void __launch_bounds__(256) k_batch_prep(const __grid_constant__ BatchParams p) {
     const BatchJob& J = p.jobs[blockIdx.y];
     const int64_t words = 2 * p.series_per_job;
     for (int64_t i = blockIdx.x * 256LL + threadIdx.x; i < words; i += 256LL * gridDim.x) J.stat[i] = 0ULL;
@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256) k_batch_prep(const BatchParams p) {
     }
 }
 
-__global__ void __launch_bounds__(256) k_batch_downsample(const BatchParams p, int64_t rows) {
+__global__ void __launch_bounds__(256) k_batch_downsample(const __grid_constant__ BatchParams p, int64_t rows) {
     const int job = blockIdx.z / p.n_ds, k = blockIdx.z - job * p.n_ds;
     const BatchJob& J = p.jobs[job];
     const int D = p.ds_factor[k];
@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256) k_batch_downsample(const BatchParams p, i
 }
 
 template <int NW, int DPW, int WARPS, int MAXIT>
-__global__ void __launch_bounds__(WARPS * 32) k_dedisp_persistent(const BatchParams p) {
+__global__ void __launch_bounds__(WARPS * 32) k_dedisp_persistent(const __grid_constant__ BatchParams p) {
     __shared__ unsigned long long s_item;
     const unsigned long long total = static_cast<unsigned long long>(p.items_per_job) * p.n_jobs;
     for (;;) {
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_dedisp_persistent(const BatchPar
     }
 }
 
-__global__ void __launch_bounds__(detail::kThreads) k_boxcar_batch(const BatchParams p, const float thr) {
+__global__ void __launch_bounds__(detail::kThreads) k_boxcar_batch(const __grid_constant__ BatchParams p, const float thr) {
     const int64_t gq = blockIdx.x;
     const int job = static_cast<int>(gq / p.series_per_job);
     int64_t q = gq - static_cast<int64_t>(job) * p.series_per_job;
@@ -132,11 +132,11 @@ struct PEntry {
 
 #define FDD_P(NW, DPW, WARPS, MAXIT) {{NW, DPW, WARPS, MAXIT}, k_dedisp_persistent<NW, DPW, WARPS, MAXIT>}
 const PEntry kPEntries[] = {
-    FDD_P(4, 2, 16, 4),  // BD 32, T 512 (uint8) / 256 (uint16), 512 threads
-    FDD_P(2, 4, 16, 4),  // BD 64, T 256 / 128, 512 threads
+    FDD_P(4, 2, 16, 2),  // BD 32, T 512 (uint8) / 256 (uint16), 512 threads
+    FDD_P(2, 4, 16, 2),  // BD 64, T 256 / 128, 512 threads
     FDD_P(4, 2, 8, 4),   // BD 16, T 512 / 256, 256 threads
     FDD_P(2, 4, 8, 4),   // BD 32, T 256 / 128, 256 threads
-    FDD_P(4, 1, 16, 4),  // BD 16, T 512 / 256, 512 threads
+    FDD_P(4, 1, 16, 2),  // BD 16, T 512 / 256, 512 threads
 };
 #undef FDD_P
 
