@@ -236,9 +236,10 @@ typedef struct {
  * Errors: UNSUPPORTED (more than FDD_MAX_RANGES ranges or 4 distinct D). */
 int fdd_batch_prepare(fdd_plan* plan, int64_t n_out, int32_t variant);
 
-/* Search n_jobs (1..FDD_MAX_BATCH_JOBS) chunks in four launches: prep,
- * downsample, one persistent dedispersion launch over every (job, range, SB,
- * DM block, time tile), one boxcar/threshold launch.  Results per job are
+/* Search n_jobs (1..FDD_MAX_BATCH_JOBS) chunks in at most five launches:
+ * prep, downsample, persistent dedispersion over every (job, range, SB, DM
+ * block, time tile) -- one launch for the native-rate ranges and one for the
+ * downsampled ranges -- and one boxcar/threshold launch.  Results per job are
  * identical to fdd_search on that job alone.  Prepares on first use of an
  * n_out (not allowed while the stream is capturing).  Batched searches of
  * one plan must not overlap on the GPU (they share the work counter). */

@@ -42,7 +42,7 @@ int batch_eligible(const fdd_plan* p) {
 
 // Build the batched-variant tables and the per-range descriptors for chunks
 // of n_out native output samples.  Allocates and synchronises.
-int prepare(fdd_plan* p, int64_t n_out, int variant) {
+int prepare(fdd_plan* p, int64_t n_out, int variant, bool big_stages = false) {
     int rc = batch_eligible(p);
     if (rc != FDD_OK) return rc;
     if (variant < 0) variant = 0;
@@ -50,28 +50,35 @@ int prepare(fdd_plan* p, int64_t n_out, int variant) {
     BatchState& b = p->batch;
     free_batch(b);
     if (!b.d_counter) {
-        cudaError_t e = cudaMalloc(&b.d_counter, 256);
+        cudaError_t e = cudaMalloc(&b.d_counter, 256);  // two counters used
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(batch counter)");
     }
     const fdd::PersistentVariant& pv = fdd::persistent_variant(variant);
     const Layout L = make_layout(p, 0, n_out, true);
     b.h_ranges.assign(p->ranges.size(), fdd::BatchRange{});
     b.tables.assign(p->ranges.size(), BatchRangeTables{});
-    int64_t items = 0;
-    size_t smem = 0;
+    int64_t items[2] = {0, 0};
+    size_t smem[2] = {0, 0};
     for (size_t ri = 0; ri < p->ranges.size(); ri++) {
         const RangeState& r = p->ranges[ri];
         const int E = (r.D == 1) ? 1 : 2;
         const fdd::DedispVariant v = pv.as(E);
         const HostTables h = build_tables(p, r, v);
         if (h.Lw < 0) return fail(FDD_ERR_UNSUPPORTED, "DM step too large for one block's staged rows");
-        const int CC = pick_cc(v, h.Lw);
+        int CC = 0;
+        if (big_stages)
+            for (int cc : {64, 48, 32, 16, 8, 4, 2})
+                if (fdd::dedisp_cc_ok(v, h.Lw, cc, kSmemBudget)) {
+                    CC = cc;
+                    break;
+                }
+        if (CC == 0) CC = pick_cc(v, h.Lw);
         if (CC == 0) return fail(FDD_ERR_UNSUPPORTED, "DM step too large for one block's staged rows");
         BatchRangeTables& t = b.tables[ri];
         if ((rc = upload_tables(&t.d_off, &t.d_base, h)) != FDD_OK) return rc;
         t.Lw = h.Lw;
         t.CC = CC;
-        smem = std::max(smem, fdd::dedisp_smem_bytes(v, h.Lw, CC));
+        smem[E - 1] = std::max(smem[E - 1], fdd::dedisp_smem_bytes(v, h.Lw, CC));
         fdd::BatchRange& R = b.h_ranges[ri];
         R.base = t.d_base;
         R.off = t.d_off;
@@ -86,8 +93,8 @@ int prepare(fdd_plan* p, int64_t n_out, int variant) {
         R.n_tiles = (R.n_out + v.tile() - 1) / v.tile();
         R.Lw = h.Lw;
         R.CC = CC;
-        R.item_off = items;
-        items += static_cast<int64_t>(p->n_sb) * R.n_blk * R.n_tiles;
+        R.item_off = items[E - 1];
+        items[E - 1] += static_cast<int64_t>(p->n_sb) * R.n_blk * R.n_tiles;
         R.series_elem_off = static_cast<int64_t>(L.series_r[ri]);
         R.series_off = static_cast<int64_t>(L.stat_r[ri]);
         R.dm0 = r.dm0;
@@ -104,17 +111,23 @@ int prepare(fdd_plan* p, int64_t n_out, int variant) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(batch ranges)");
     e = cudaMemcpy(b.d_ranges, b.h_ranges.data(), sizeof(fdd::BatchRange) * b.h_ranges.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(batch ranges)");
-    int per_sm = 0;
-    if ((e = fdd::persistent_occupancy(variant, smem, &per_sm)) != cudaSuccess) return cuda_fail(e, "occupancy");
-    if (per_sm < 1) return fail(FDD_ERR_UNSUPPORTED, "persistent kernel does not fit on an SM");
     int sms = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device)) != cudaSuccess)
         return cuda_fail(e, "device attribute");
+    for (int E = 1; E <= 2; E++) {
+        b.grid_e[E - 1] = 0;
+        b.smem_e[E - 1] = smem[E - 1];
+        b.items_per_job_e[E - 1] = items[E - 1];
+        if (items[E - 1] == 0) continue;
+        int per_sm = 0;
+        if ((e = fdd::persistent_occupancy(variant, E, smem[E - 1], &per_sm)) != cudaSuccess)
+            return cuda_fail(e, "occupancy");
+        if (per_sm < 1) return fail(FDD_ERR_UNSUPPORTED, "persistent kernel does not fit on an SM");
+        b.grid_e[E - 1] = per_sm * sms;
+    }
     b.variant = variant;
-    b.items_per_job = items;
+    b.big_stages = big_stages;
     b.series_per_job = static_cast<int64_t>(L.stat_bytes / (2 * sizeof(unsigned long long)));
-    b.grid = per_sm * sms;
-    b.smem = smem;
     b.n_out = n_out;
     b.tuned_ms = 0.f;
     return FDD_OK;
@@ -127,7 +140,8 @@ int fill_params(const fdd_plan* p, const fdd_job* jobs, int32_t n_jobs, int64_t 
     P.ranges = b.d_ranges;
     P.sb_map = p->d_sb_map;
     P.counter = b.d_counter;
-    P.items_per_job = b.items_per_job;
+    P.items_per_job_e[0] = b.items_per_job_e[0];
+    P.items_per_job_e[1] = b.items_per_job_e[1];
     P.series_per_job = b.series_per_job;
     P.n_range = static_cast<int32_t>(p->ranges.size());
     P.n_jobs = n_jobs;
@@ -177,10 +191,14 @@ int enqueue(fdd_plan* p, const fdd::BatchParams& P, cudaStream_t s) {
         if ((e = fdd::launch_batch_downsample(P, s)) != cudaSuccess) return cuda_fail(e, "batch downsample launch");
         if ((e = stage_end(p, s)) != cudaSuccess) return cuda_fail(e, "timing event");
     }
-    if ((e = stage_begin(p, 1, -1, s)) != cudaSuccess) return cuda_fail(e, "timing event");
-    if ((e = fdd::launch_dedisp_persistent(p->batch.variant, P, p->batch.grid, p->batch.smem, s)) != cudaSuccess)
-        return cuda_fail(e, "persistent dedispersion launch");
-    if ((e = stage_end(p, s)) != cudaSuccess) return cuda_fail(e, "timing event");
+    for (int E = 1; E <= 2; E++) {
+        if (p->batch.items_per_job_e[E - 1] == 0) continue;
+        if ((e = stage_begin(p, 1, -E, s)) != cudaSuccess) return cuda_fail(e, "timing event");
+        if ((e = fdd::launch_dedisp_persistent(p->batch.variant, E, P, p->batch.grid_e[E - 1], p->batch.smem_e[E - 1],
+                                               s)) != cudaSuccess)
+            return cuda_fail(e, "persistent dedispersion launch");
+        if ((e = stage_end(p, s)) != cudaSuccess) return cuda_fail(e, "timing event");
+    }
     if ((e = stage_begin(p, 2, -1, s)) != cudaSuccess) return cuda_fail(e, "timing event");
     if ((e = fdd::launch_boxcar_batch(P, wmax, p->thr, s)) != cudaSuccess) return cuda_fail(e, "batch boxcar launch");
     if ((e = stage_end(p, s)) != cudaSuccess) return cuda_fail(e, "timing event");
@@ -237,7 +255,7 @@ int fdd_search_batch(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int64_
         cudaStreamIsCapturing(s, &st);
         if (st != cudaStreamCaptureStatusNone)
             return fail(FDD_ERR_INVALID_ARG, "call fdd_batch_prepare for this n_out before capturing");
-        const int rc = prepare(plan, n_out, plan->batch.variant);
+        const int rc = prepare(plan, n_out, plan->batch.variant, plan->batch.big_stages);
         if (rc != FDD_OK) return rc;
     }
     fdd::BatchParams P;
@@ -259,10 +277,13 @@ int fdd_batch_autotune(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int6
         return cuda_fail(e, "cudaEventCreate");
     }
     int best = -1;
+    bool best_big = false;
     float best_ms = 1e30f;
     int rc = FDD_OK;
-    for (int v = 0; v < fdd::num_persistent_variants(); v++) {
-        if (prepare(plan, n_out, v) != FDD_OK) continue;  // variant does not fit this plan
+    for (int vb = 0; vb < 2 * fdd::num_persistent_variants(); vb++) {
+        const int v = vb >> 1;
+        const bool big = (vb & 1) != 0;
+        if (prepare(plan, n_out, v, big) != FDD_OK) continue;  // variant does not fit this plan
         fdd::BatchParams P;
         if ((rc = fill_params(plan, jobs, n_jobs, n_out, P)) != FDD_OK) break;
         if ((rc = enqueue(plan, P, s)) != FDD_OK) break;  // warm-up
@@ -279,19 +300,21 @@ int fdd_batch_autotune(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int6
         ms /= reps;
         if (std::getenv("FDD_TUNE_VERBOSE")) {
             const fdd::PersistentVariant& pv = fdd::persistent_variant(v);
-            std::fprintf(stderr, "fdd batch tune: variant %d (bd %d threads %d) grid %d: %.4f ms\n", v, pv.bd(),
-                         pv.threads(), plan->batch.grid, ms);
+            std::fprintf(stderr, "fdd batch tune: variant %d (bd %d threads %d) %s stages, grid %d/%d: %.4f ms\n", v,
+                         pv.bd(), pv.threads(), big ? "large" : "default", plan->batch.grid_e[0],
+                         plan->batch.grid_e[1], ms);
         }
         if (ms < best_ms) {
             best_ms = ms;
             best = v;
+            best_big = big;
         }
     }
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
     if (rc != FDD_OK) return rc;
     if (best < 0) return fail(FDD_ERR_UNSUPPORTED, "no persistent variant fits this plan");
-    rc = prepare(plan, n_out, best);
+    rc = prepare(plan, n_out, best, best_big);
     if (rc == FDD_OK) plan->batch.tuned_ms = best_ms;
     return rc;
 }
@@ -303,7 +326,7 @@ int fdd_batch_config(const fdd_plan* plan, int32_t* variant, int32_t* grid, int3
     if (b.variant < 0) return fail(FDD_ERR_INVALID_ARG, "batch not prepared");
     const fdd::PersistentVariant& pv = fdd::persistent_variant(b.variant);
     if (variant) *variant = b.variant;
-    if (grid) *grid = b.grid;
+    if (grid) *grid = b.grid_e[0] ? b.grid_e[0] : b.grid_e[1];
     if (threads) *threads = pv.threads();
     if (dm_per_block) *dm_per_block = pv.bd();
     if (tuned_ms) *tuned_ms = b.tuned_ms;
@@ -314,7 +337,7 @@ int fdd_graph_create(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int64_
     if (!plan || !out || n_out < 0) return fail(FDD_ERR_INVALID_ARG, "bad argument");
     *out = nullptr;
     if (plan->batch.n_out != n_out) {
-        const int rc = prepare(plan, n_out, plan->batch.variant);
+        const int rc = prepare(plan, n_out, plan->batch.variant, plan->batch.big_stages);
         if (rc != FDD_OK) return rc;
     }
     fdd::BatchParams P;

@@ -94,7 +94,7 @@ struct BatchRange {
     int32_t E, D, ds_index;       // ds_index: -1 = raw input, else index into job.ds
     int32_t n_dm, n_blk, n_tiles, n_out;
     int32_t Lw, CC;
-    int64_t item_off;             // first work item of this range inside a job
+    int64_t item_off;             // first work item of this range among the job's ranges of the same E
     int64_t series_elem_off;      // first series element of this range inside a job's series buffer
     int64_t series_off;           // first series index (sb*n_dm + i) of this range inside a job
     // S/N stage
@@ -121,16 +121,16 @@ struct BatchJob {
 struct BatchParams {
     const BatchRange* ranges;     // device [n_range]
     const int16_t* sb_map;
-    unsigned long long* counter;  // work-item counter, zeroed by the prep launch
-    int64_t items_per_job;
+    unsigned long long* counter;  // [2] work-item counters (raw, downsampled), zeroed by the prep launch
+    int64_t items_per_job_e[2];   // work items per job of raw / downsampled ranges
     int64_t series_per_job;
     int32_t n_range, n_jobs, n_sb, n_chan, n_tab, n_ds;
     int32_t ds_factor[kMaxDs];
     BatchJob jobs[kMaxBatchJobs];
 };
 
-// Persistent dedispersion variants (E is per work item, so one kernel serves
-// raw and downsampled ranges).
+// Persistent dedispersion variants (instantiated for raw and downsampled
+// samples; one launch per sample width present in the plan).
 struct PersistentVariant {
     int NW, DPW, WARPS, MAXIT;
     int bd() const { return WARPS * DPW; }
@@ -140,10 +140,10 @@ struct PersistentVariant {
 int num_persistent_variants();
 const PersistentVariant& persistent_variant(int idx);
 // Resident blocks per SM of persistent variant idx with `smem` bytes of dynamic shared memory.
-cudaError_t persistent_occupancy(int idx, size_t smem, int* blocks_per_sm);
+cudaError_t persistent_occupancy(int idx, int E, size_t smem, int* blocks_per_sm);
 cudaError_t launch_batch_prep(const BatchParams& p, cudaStream_t s);
 cudaError_t launch_batch_downsample(const BatchParams& p, cudaStream_t s);
-cudaError_t launch_dedisp_persistent(int idx, const BatchParams& p, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_dedisp_persistent(int idx, int E, const BatchParams& p, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_boxcar_batch(const BatchParams& p, int wmax_all, float thr, cudaStream_t s);
 
 // ---------------------------------------------------------------------------

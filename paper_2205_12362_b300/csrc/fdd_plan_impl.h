@@ -33,15 +33,16 @@ struct BatchRangeTables {
 
 struct BatchState {
     int variant = -1;                      // persistent kernel variant
+    bool big_stages = false;               // channel stages sized to the full shared-memory budget
     int64_t n_out = -1;                    // chunk length the tables below were prepared for
     std::vector<BatchRangeTables> tables;  // per range
     fdd::BatchRange* d_ranges = nullptr;   // device copy of the per-range descriptors
     std::vector<fdd::BatchRange> h_ranges;
-    unsigned long long* d_counter = nullptr;  // work-item counter of the persistent launch
-    int64_t items_per_job = 0;
+    unsigned long long* d_counter = nullptr;  // work-item counters of the persistent launches
+    int64_t items_per_job_e[2] = {0, 0};   // raw / downsampled work items per job
     int64_t series_per_job = 0;
-    int grid = 0;                          // resident blocks of the persistent launch
-    size_t smem = 0;
+    int grid_e[2] = {0, 0};                // resident blocks of each persistent launch
+    size_t smem_e[2] = {0, 0};
     float tuned_ms = 0.f;
 };
 

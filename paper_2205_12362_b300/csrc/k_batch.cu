@@ -3,9 +3,11 @@
 // persistent dedispersion launch, boxcar).  Jobs arrive as kernel parameters
 // (BatchParams), so the whole sequence can be captured in a CUDA graph.
 //
-// The persistent dedispersion kernel keeps every SM busy across ranges of
-// uneven length and sample width: resident blocks pull work items (job,
-// range, SB, DM block, time tile) from one atomic counter.  Items of one
+// The persistent dedispersion kernels keep every SM busy across ranges of
+// uneven length: resident blocks pull work items (job, range, SB, DM block,
+// time tile) from an atomic counter.  One persistent launch serves all raw
+// (uint8) ranges and one all downsampled (uint16) ranges, so each keeps the
+// register budget of its own sample width.  Items of one
 // (job, range, SB, time tile) differ only in DM block and are consecutive, so
 // blocks running at the same time share staged input rows in L2.  Each item
 // runs the same dedisp_tile as the per-range kernel, instantiated for raw
@@ -26,7 +28,10 @@ __global__ void __launch_bounds__(256) k_batch_prep(const __grid_constant__ Batc
     for (int64_t i = blockIdx.x * 256LL + threadIdx.x; i < words; i += 256LL * gridDim.x) J.stat[i] = 0ULL;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *J.count = 0ULL;
-        if (blockIdx.y == 0) *p.counter = 0ULL;
+        if (blockIdx.y == 0) {
+            p.counter[0] = 0ULL;
+            p.counter[1] = 0ULL;
+        }
     }
 }
 
@@ -41,20 +46,23 @@ __global__ void __launch_bounds__(256) k_batch_downsample(const __grid_constant_
         detail::downsample_chunk(J.tabs + row * J.tab_pitch, J.ds[k] + row * J.ds_pitch[k], n_y, D, j0);
 }
 
-template <int NW, int DPW, int WARPS, int MAXIT>
+template <int E, int NW, int DPW, int WARPS, int MAXIT>
 __global__ void __launch_bounds__(WARPS * 32) k_dedisp_persistent(const __grid_constant__ BatchParams p) {
     __shared__ unsigned long long s_item;
-    const unsigned long long total = static_cast<unsigned long long>(p.items_per_job) * p.n_jobs;
+    const int64_t per_job = p.items_per_job_e[E - 1];
+    const unsigned long long total = static_cast<unsigned long long>(per_job) * p.n_jobs;
+    unsigned long long* counter = p.counter + (E - 1);
     for (;;) {
         __syncthreads();  // previous item's shared-memory reads are done
-        if (threadIdx.x == 0) s_item = atomicAdd(p.counter, 1ULL);
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1ULL);
         __syncthreads();
         const unsigned long long it = s_item;
         if (it >= total) break;
-        const int job = static_cast<int>(it / p.items_per_job);
-        int64_t rest = static_cast<int64_t>(it - static_cast<unsigned long long>(job) * p.items_per_job);
-        int r = 0;
-        while (r + 1 < p.n_range && rest >= p.ranges[r + 1].item_off) r++;
+        const int job = static_cast<int>(it / per_job);
+        int64_t rest = static_cast<int64_t>(it - static_cast<unsigned long long>(job) * per_job);
+        int r = -1;  // last range of this sample width whose first item is <= rest
+        for (int k = 0; k < p.n_range; k++)
+            if (p.ranges[k].E == E && p.ranges[k].item_off <= rest) r = k;
         const BatchRange& R = p.ranges[r];
         rest -= R.item_off;
         const int blk = static_cast<int>(rest % R.n_blk);
@@ -82,10 +90,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_dedisp_persistent(const __grid_c
         a.n_sb = p.n_sb;
         a.Lw = R.Lw;
         a.CC = R.CC;
-        if (R.E == 1)
-            detail::dedisp_tile<1, NW, DPW, WARPS, MAXIT>(a, tile, blk, sb);
-        else
-            detail::dedisp_tile<2, NW, DPW, WARPS, MAXIT>(a, tile, blk, sb);
+        detail::dedisp_tile<E, NW, DPW, WARPS, MAXIT>(a, tile, blk, sb);
     }
 }
 
@@ -127,16 +132,17 @@ using PersistentFn = void (*)(const BatchParams);
 
 struct PEntry {
     PersistentVariant v;
-    PersistentFn fn;
+    PersistentFn fn[2];  // raw (uint8) and downsampled (uint16) work items
 };
 
-#define FDD_P(NW, DPW, WARPS, MAXIT) {{NW, DPW, WARPS, MAXIT}, k_dedisp_persistent<NW, DPW, WARPS, MAXIT>}
+#define FDD_P(NW, DPW, WARPS, MAXIT) \
+    {{NW, DPW, WARPS, MAXIT}, {k_dedisp_persistent<1, NW, DPW, WARPS, MAXIT>, k_dedisp_persistent<2, NW, DPW, WARPS, MAXIT>}}
 const PEntry kPEntries[] = {
-    FDD_P(4, 2, 16, 2),  // BD 32, T 512 (uint8) / 256 (uint16), 512 threads
-    FDD_P(2, 4, 16, 2),  // BD 64, T 256 / 128, 512 threads
+    FDD_P(4, 2, 16, 4),  // BD 32, T 512 (uint8) / 256 (uint16), 512 threads
+    FDD_P(2, 4, 16, 4),  // BD 64, T 256 / 128, 512 threads
     FDD_P(4, 2, 8, 4),   // BD 16, T 512 / 256, 256 threads
     FDD_P(2, 4, 8, 4),   // BD 32, T 256 / 128, 256 threads
-    FDD_P(4, 1, 16, 2),  // BD 16, T 512 / 256, 512 threads
+    FDD_P(4, 1, 16, 4),  // BD 16, T 512 / 256, 512 threads
 };
 #undef FDD_P
 
@@ -146,11 +152,12 @@ int num_persistent_variants() { return static_cast<int>(sizeof(kPEntries) / size
 
 const PersistentVariant& persistent_variant(int idx) { return kPEntries[idx].v; }
 
-cudaError_t persistent_occupancy(int idx, size_t smem, int* blocks_per_sm) {
+cudaError_t persistent_occupancy(int idx, int E, size_t smem, int* blocks_per_sm) {
     const PEntry& e = kPEntries[idx];
-    cudaError_t err = cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t err =
+        cudaFuncSetAttribute(e.fn[E - 1], cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (err != cudaSuccess) return err;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, e.fn, e.v.threads(), smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, e.fn[E - 1], e.v.threads(), smem);
 }
 
 cudaError_t launch_batch_prep(const BatchParams& p, cudaStream_t s) {
@@ -175,11 +182,12 @@ cudaError_t launch_batch_downsample(const BatchParams& p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_dedisp_persistent(int idx, const BatchParams& p, int grid, size_t smem, cudaStream_t s) {
+cudaError_t launch_dedisp_persistent(int idx, int E, const BatchParams& p, int grid, size_t smem, cudaStream_t s) {
     const PEntry& e = kPEntries[idx];
-    cudaError_t err = cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t err =
+        cudaFuncSetAttribute(e.fn[E - 1], cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (err != cudaSuccess) return err;
-    e.fn<<<grid, e.v.threads(), smem, s>>>(p);
+    e.fn[E - 1]<<<grid, e.v.threads(), smem, s>>>(p);
     return cudaGetLastError();
 }
 
