@@ -47,7 +47,9 @@ enum {
     FDD_ERR_MISALIGNED = -4,   /* device pointer or row pitch not 16-byte aligned */
     FDD_ERR_UNSUPPORTED = -5,  /* plan outside the kernels' limits (see FDD_MAX_*) */
     FDD_ERR_CUDA = -6,         /* CUDA runtime error; see fdd_last_error_message() */
-    FDD_ERR_WORKSPACE = -7     /* workspace smaller than fdd_workspace_size() */
+    FDD_ERR_WORKSPACE = -7,    /* workspace smaller than fdd_workspace_size() */
+    FDD_ERR_SEQUENCE = -8,     /* serving: chunk out of sequence (dropped/late/duplicate/reordered) */
+    FDD_ERR_BUSY = -9          /* serving: beam backlogged, retry after fdd_server_poll */
 };
 
 #define FDD_MAX_WIDTHS 16      /* boxcar widths per DM range */
@@ -231,7 +233,8 @@ typedef struct {
 } fdd_job;
 
 /* Prepare the plan's batched tables for chunks of n_out native samples with
- * persistent-kernel variant `variant` (-1: keep the current one, or 0).
+ * persistent-kernel variant `variant` (-1: keep the current, possibly tuned,
+ * configuration; variant 0 if none).
  * Allocates and synchronises; must precede any capture of fdd_search_batch.
  * Errors: UNSUPPORTED (more than FDD_MAX_RANGES ranges or 4 distinct D). */
 int fdd_batch_prepare(fdd_plan* plan, int64_t n_out, int32_t variant);
@@ -265,6 +268,85 @@ int fdd_graph_create(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int64_
 int fdd_graph_update(fdd_graph* graph, const fdd_job* jobs, int32_t n_jobs);
 int fdd_graph_launch(fdd_graph* graph, fdd_stream_t stream);
 int fdd_graph_destroy(fdd_graph* graph);
+
+/* ---------------------------------------------------------------------
+ * Serving runtime (the paper's real-time operation: every compound beam's
+ * 1.024 s chunks are searched as they arrive, each output needing the next
+ * max-delay of input; Sec. "AMBER", Sec. "Computing performance").
+ * One server, one plan, many beams.  Per beam the server keeps two device
+ * window buffers of chunk + max delay samples (rounded up to whole chunks);
+ * a complete window is queued; "slots" (workspace + candidate buffers) are
+ * allocated once from free HBM; fdd_server_poll launches every queued
+ * window that finds a free slot as one batched search (continuous
+ * batching), retires finished ones and copies their candidates to host.
+ * Window w of a beam searches outputs [w*chunk, (w+1)*chunk) (t_native of its
+ * candidates is absolute) and is complete once the chunk holding its last
+ * needed sample has arrived. */
+typedef struct fdd_server fdd_server;
+
+typedef struct {
+    int32_t n_beams;           /* compound beams */
+    int64_t chunk_len;         /* native samples per arriving chunk (12500 in ARTS) */
+    int32_t max_slots;         /* cap on in-flight windows; 0 = as many as HBM allows */
+    double hbm_reserve_frac;   /* part of free HBM left unused, in [0, 1) */
+    int64_t hbm_budget_bytes;  /* > 0: treat free HBM as at most this (admission tests) */
+    int64_t cap_per_window;    /* candidate records kept per window */
+} fdd_server_desc;
+
+typedef struct {
+    int32_t beam;
+    int64_t window;            /* window index of the beam */
+    int64_t t0_native;         /* first output sample (absolute) */
+    double t_arrival;          /* caller's arrival time of the completing chunk (fdd_now clock) */
+    double t_ready;            /* window queued */
+    double t_launch;           /* window launched */
+    double t_done;             /* results seen by fdd_server_poll */
+    int64_t n_cands;           /* true candidate count */
+    int64_t n_cands_kept;      /* records returned (<= cap_per_window) */
+    int64_t cand_offset;       /* offset of this window's records in the candidate array */
+    int32_t batch_jobs;        /* windows in the batch it ran in */
+} fdd_window_result;
+
+typedef struct {
+    int32_t n_slots, slots_busy, queued;
+    int64_t max_queued, launched, done, batches;
+    int64_t window_len;        /* input samples per window */
+    int64_t ring_bytes_per_beam, slot_bytes;
+} fdd_server_stats;
+
+/* Monotonic clock (seconds) used for all server timestamps. */
+double fdd_now(void);
+
+/* Create a server.  Allocates every beam's buffers, then slots from free HBM
+ * (FDD_ERR_NO_MEMORY if not even one slot fits: admission refused), and
+ * prepares the plan's batched search for chunk_len. */
+int fdd_server_create(fdd_plan* plan, const fdd_server_desc* desc, fdd_server** out);
+int fdd_server_destroy(fdd_server* server);
+
+/* Deliver chunk `seq` (0, 1, 2, ... per beam) of `beam`: host memory
+ * uint8 [n_tab][n_chan][chunk_len] (pinned for asynchronous copies; it may be
+ * reused once the call returns only if pageable).  FDD_ERR_SEQUENCE for a
+ * dropped/late/duplicate/reordered chunk (state unchanged); FDD_ERR_BUSY if
+ * the beam's previous window still waits for a slot (call fdd_server_poll,
+ * then retry). */
+int fdd_server_push(fdd_server* server, int32_t beam, int64_t seq, const uint8_t* host_chunk, double t_arrival);
+
+/* Drop a beam's partial window and expect chunk next_seq next (after a gap). */
+int fdd_server_reset_beam(fdd_server* server, int32_t beam, int64_t next_seq);
+
+/* Retire finished searches and launch queued windows on free slots.  Never
+ * blocks. */
+int fdd_server_poll(fdd_server* server);
+
+/* Poll until nothing is queued or running (blocks). */
+int fdd_server_drain(fdd_server* server);
+
+/* Hand out finished windows in completion order: up to max_results records
+ * and their candidates (at most cands_cap records in total). */
+int fdd_server_results(fdd_server* server, fdd_window_result* out, int32_t max_results, fdd_candidate* cands,
+                       int64_t cands_cap, int32_t* n_results, int64_t* n_cands);
+
+int fdd_server_info(const fdd_server* server, fdd_server_stats* stats);
 
 /* Per-stage GPU timing (tracing; the paper reports AMBER's time per stage,
  * Sec. "Computing performance").  With timing enabled, fdd_search records a

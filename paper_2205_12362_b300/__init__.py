@@ -18,7 +18,7 @@ import numpy as np
 from .build import LIB as _LIB_PATH
 
 __all__ = ["Plan", "FddError", "FddUnavailable", "CAND_DTYPE", "decode_candidates", "downsample_u8",
-           "library_path", "version", "variants", "Job", "Graph"]
+           "library_path", "version", "variants", "Job", "Graph", "Server", "now"]
 
 CAND_DTYPE = np.dtype([("sb", np.int32), ("dm_index", np.int32), ("downsamp", np.int32),
                        ("width_native", np.int32), ("t_native", np.int64), ("dm", np.float32),
@@ -62,6 +62,26 @@ class _Job(ctypes.Structure):
                 ("t_offset_native", ctypes.c_int64), ("d_workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("d_cands", ctypes.c_void_p), ("cap", ctypes.c_int64),
                 ("d_count", ctypes.c_void_p), ("d_series", ctypes.c_void_p)]
+
+
+class _ServerDesc(ctypes.Structure):
+    _fields_ = [("n_beams", ctypes.c_int32), ("chunk_len", ctypes.c_int64), ("max_slots", ctypes.c_int32),
+                ("hbm_reserve_frac", ctypes.c_double), ("hbm_budget_bytes", ctypes.c_int64),
+                ("cap_per_window", ctypes.c_int64)]
+
+
+class _WindowResult(ctypes.Structure):
+    _fields_ = [("beam", ctypes.c_int32), ("window", ctypes.c_int64), ("t0_native", ctypes.c_int64),
+                ("t_arrival", ctypes.c_double), ("t_ready", ctypes.c_double), ("t_launch", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("n_cands", ctypes.c_int64), ("n_cands_kept", ctypes.c_int64),
+                ("cand_offset", ctypes.c_int64), ("batch_jobs", ctypes.c_int32)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("n_slots", ctypes.c_int32), ("slots_busy", ctypes.c_int32), ("queued", ctypes.c_int32),
+                ("max_queued", ctypes.c_int64), ("launched", ctypes.c_int64), ("done", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("window_len", ctypes.c_int64),
+                ("ring_bytes_per_beam", ctypes.c_int64), ("slot_bytes", ctypes.c_int64)]
 
 
 class _PlanDesc(ctypes.Structure):
@@ -119,6 +139,16 @@ def _lib_raw():
     L.fdd_graph_update.argtypes = [_P, ctypes.POINTER(_Job), _I32]
     L.fdd_graph_launch.argtypes = [_P, _P]
     L.fdd_graph_destroy.argtypes = [_P]
+    L.fdd_now.restype = ctypes.c_double
+    L.fdd_server_create.argtypes = [_P, ctypes.POINTER(_ServerDesc), ctypes.POINTER(_P)]
+    L.fdd_server_destroy.argtypes = [_P]
+    L.fdd_server_push.argtypes = [_P, _I32, _I64, _P, ctypes.c_double]
+    L.fdd_server_reset_beam.argtypes = [_P, _I32, _I64]
+    L.fdd_server_poll.argtypes = [_P]
+    L.fdd_server_drain.argtypes = [_P]
+    L.fdd_server_results.argtypes = [_P, ctypes.POINTER(_WindowResult), _I32, _P, _I64, ctypes.POINTER(_I32),
+                                     ctypes.POINTER(_I64)]
+    L.fdd_server_info.argtypes = [_P, ctypes.POINTER(_ServerStats)]
     L.fdd_search_static.argtypes = [_P, _P, _I64, _I64, _I64, _I64, _P, _I64, _P, _P, _P]
     L.fdd_plan_stage_times.argtypes = [_P, _I32, _P, _P, _P, ctypes.POINTER(_I32)]
     _lib = L
@@ -240,6 +270,92 @@ class Graph:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             _lib_raw().fdd_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+FDD_ERR_SEQUENCE = -8
+FDD_ERR_BUSY = -9
+
+
+def now():
+    """The serving runtime's monotonic clock (seconds)."""
+    return float(_lib_raw().fdd_now())
+
+
+class Server:
+    """Serving runtime (include/fdd.h: fdd_server_*): per-beam device window
+    buffers, slots sized from free HBM, continuous batching of complete
+    windows onto the GPU."""
+
+    def __init__(self, plan, n_beams, chunk_len, max_slots=0, hbm_reserve_frac=0.1, hbm_budget_bytes=0,
+                 cap_per_window=1 << 15):
+        d = _ServerDesc(int(n_beams), int(chunk_len), int(max_slots), float(hbm_reserve_frac),
+                        int(hbm_budget_bytes), int(cap_per_window))
+        h = ctypes.c_void_p()
+        _check(_lib_raw().fdd_server_create(plan.handle, ctypes.byref(d), ctypes.byref(h)), "fdd_server_create")
+        self._h = h
+        self._plan = plan
+        self.n_beams, self.chunk_len, self.cap_per_window = int(n_beams), int(chunk_len), int(cap_per_window)
+
+    def push(self, beam, seq, chunk, t_arrival=None):
+        """Deliver a host chunk (numpy uint8 or pinned CPU torch tensor,
+        [n_tab][n_chan][chunk_len], contiguous).  Returns 0, FDD_ERR_BUSY or
+        FDD_ERR_SEQUENCE; raises on other errors."""
+        need = self._plan.n_tab * self._plan.n_chan * self.chunk_len
+        if int(np.prod(chunk.shape)) != need:
+            raise ValueError("chunk must hold n_tab * n_chan * chunk_len samples")
+        if hasattr(chunk, "data_ptr"):
+            if chunk.is_cuda or not chunk.is_contiguous() or chunk.element_size() != 1:
+                raise ValueError("chunk must be a contiguous host uint8 tensor")
+            ptr = chunk.data_ptr()
+        else:
+            if not chunk.flags["C_CONTIGUOUS"] or chunk.dtype != np.uint8:
+                raise ValueError("chunk must be a contiguous uint8 array")
+            ptr = chunk.ctypes.data
+        t = now() if t_arrival is None else float(t_arrival)
+        code = _lib_raw().fdd_server_push(self._h, int(beam), int(seq), ctypes.c_void_p(ptr), t)
+        if code in (0, FDD_ERR_BUSY, FDD_ERR_SEQUENCE):
+            return code
+        raise FddError(code, "fdd_server_push")
+
+    def reset_beam(self, beam, next_seq):
+        return _lib_raw().fdd_server_reset_beam(self._h, int(beam), int(next_seq))
+
+    def poll(self):
+        _check(_lib_raw().fdd_server_poll(self._h), "fdd_server_poll")
+
+    def drain(self):
+        _check(_lib_raw().fdd_server_drain(self._h), "fdd_server_drain")
+
+    def results(self, max_results=4096):
+        """[(window-record dict, candidates structured array)] in completion order."""
+        out = (_WindowResult * max_results)()
+        cap = max_results * self.cap_per_window
+        cands = np.zeros(cap, dtype=CAND_DTYPE)
+        n, nc = _I32(), _I64()
+        _check(_lib_raw().fdd_server_results(self._h, out, int(max_results), cands.ctypes.data_as(ctypes.c_void_p),
+                                             int(cap), ctypes.byref(n), ctypes.byref(nc)), "fdd_server_results")
+        res = []
+        for k in range(n.value):
+            r = {f: getattr(out[k], f) for f, _ in _WindowResult._fields_}
+            c = cands[r["cand_offset"]:r["cand_offset"] + r["n_cands_kept"]].copy()
+            res.append((r, np.sort(c, order=["sb", "dm_index", "width_native", "t_native"])))
+        return res
+
+    def info(self):
+        st = _ServerStats()
+        _check(_lib_raw().fdd_server_info(self._h, ctypes.byref(st)), "fdd_server_info")
+        return {f: getattr(st, f) for f, _ in _ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib_raw().fdd_server_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

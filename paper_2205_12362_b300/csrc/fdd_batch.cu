@@ -45,7 +45,10 @@ int batch_eligible(const fdd_plan* p) {
 int prepare(fdd_plan* p, int64_t n_out, int variant, bool big_stages = false) {
     int rc = batch_eligible(p);
     if (rc != FDD_OK) return rc;
-    if (variant < 0) variant = 0;
+    if (variant < 0) {  // keep the current (possibly tuned) configuration
+        variant = p->batch.variant >= 0 ? p->batch.variant : 0;
+        big_stages = p->batch.big_stages;
+    }
     if (variant >= fdd::num_persistent_variants()) return fail(FDD_ERR_INVALID_ARG, "batch variant out of range");
     BatchState& b = p->batch;
     free_batch(b);
@@ -244,7 +247,7 @@ extern "C" {
 
 int fdd_batch_prepare(fdd_plan* plan, int64_t n_out, int32_t variant) {
     if (!plan || n_out < 0) return fail(FDD_ERR_INVALID_ARG, "bad argument");
-    return prepare(plan, n_out, variant);
+    return prepare(plan, n_out, variant, false);
 }
 
 int fdd_search_batch(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int64_t n_out, fdd_stream_t stream) {

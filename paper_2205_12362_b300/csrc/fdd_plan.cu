@@ -261,6 +261,8 @@ const char* fdd_error_string(int code) {
         case FDD_ERR_UNSUPPORTED: return "plan outside the kernels' limits";
         case FDD_ERR_CUDA: return "CUDA runtime error";
         case FDD_ERR_WORKSPACE: return "workspace too small";
+        case FDD_ERR_SEQUENCE: return "chunk out of sequence";
+        case FDD_ERR_BUSY: return "beam backlogged";
         default: return "unknown error";
     }
 }
