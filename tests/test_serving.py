@@ -95,12 +95,13 @@ def test_serving_results_match_standalone(fdd, max_slots):
         assert len(ref) == len(c) and (ref == c).all(), "beam %d window %d differs from the stand-alone search" % (b, w)
     if max_slots != 1:
         assert mixed, "no window was batched with another"
-    # one window against the oracle
-    b, w = 1, 1
+    # one window holding an injected pulse (beam 1: t0 = 1537) against the oracle
+    b, w = 1, 3
     _, win = standalone(fdd, plan, streams[b], w, chunk, n_in)
     ora, _ = oracle_candidate_superset(win, sb, f, T_SAMP, ranges, 6.0, chunk, n_in, t_offset=w * chunk)
     compare_candidates(results[(b, w)][1], ora, 6.0)
     assert len(results[(b, w)][1]) > 0
+    assert sum(len(c) for _, c in results.values()) > 0
     srv.close()
 
 
