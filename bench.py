@@ -34,6 +34,9 @@ K_DM = 4148.808  # s MHz^2 / (pc cm^-3), for placing injected pulses only
 WIDTHS = [1, 2, 4, 8, 16, 32, 64]
 
 WORKLOADS = {
+    # 1 beam, 128 ch, 4096 samples, DM 0-255 step 1, widths 1..16 (the small parity case)
+    "tiny": dict(n_tab=1, n_sb=1, n_chan=128, n_out=4096, seed=1, n_pulses=1, pulse_tabs=[0], thr=8.0,
+                 ranges=[dict(dm0=0.0, ddm=1.0, n_dm=256, downsamp=1, widths=[1, 2, 4, 8, 16])]),
     # 1 SB, 1536 ch, 1.024 s chunk, DM 0-409.4 step 0.2 (2048 trials), widths 1..64
     "arts_single_sb": dict(n_tab=1, n_sb=1, n_chan=1536, n_out=synth.ARTS_CHUNK, seed=2, n_pulses=10,
                            pulse_tabs=[0], thr=8.0,
@@ -222,6 +225,16 @@ def dist_setup(args):
     return world, rank, local, pg
 
 
+def reduce_max(value, dist, device):
+    """Max of a per-rank scalar over all ranks (the job's time is the slowest rank's)."""
+    if not dist:
+        return value
+    import torch
+    tt = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
 def run_fdd(args):
     import torch
 
@@ -328,11 +341,7 @@ def run_fdd(args):
     t_hi = time.time()
     clocks = sampler.stop(t_lo, t_hi)
 
-    dev_s = sum(step_ms) / 1e3
-    if dist:
-        tt = torch.tensor([dev_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dev_s = float(tt.item())
+    dev_s = reduce_max(sum(step_ms) / 1e3, dist, dev)
     units = units_per_step(w) * args.steps * world
     value = units / dev_s
 
@@ -354,11 +363,7 @@ def run_fdd(args):
         d2h += 8 + got.numel() * 4
         e2e_units += units_per_step(w)
     te1 = time.perf_counter()
-    e2e_s = te1 - te0
-    if dist:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = reduce_max(te1 - te0, dist, dev)
 
     if rank != 0:
         if dist:
@@ -427,11 +432,12 @@ def run_reference(args):
     world, rank, local, dist = dist_setup(args)
     if rank != 0:
         if dist:
+            dist.barrier()
             dist.destroy_process_group()
         return None
     import oracle
     w, f, t, x, sb, n_in = make_workload(args.workload)
-    per_step = max(0.5, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
+    per_step = max(0.05, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
     _, cores, desc, _, rr = oracle_sample_rate(x, sb, f, t, w, n_in, per_step)
     units = sum(r["n_dm"] * (w["n_out"] // r["downsamp"]) for r in rr)
     for _ in range(args.warmup):
@@ -456,6 +462,7 @@ def run_reference(args):
         "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     if dist:
+        dist.barrier()
         dist.destroy_process_group()
     return line
 
