@@ -190,11 +190,27 @@ typedef struct {
 } fdd_kernel_config;
 
 /* Number of compiled dedispersion kernel variants (valid variant indices are
- * 0 .. n-1); *bytes_per_sample of variant v is 1 (native-rate ranges) or 2
- * (downsampled ranges). */
+ * 0 .. n-1).  *bytes_per_sample of variant v is 1 (native-rate ranges) or 2
+ * (downsampled ranges); *group is 0 for brute-force variants and the channel
+ * group size G of pattern-factored variants (exact: within a block of
+ * trials, channel groups with equal relative delays share one partial sum;
+ * native-rate ranges only).  Any output pointer may be NULL. */
 int fdd_num_variants(int32_t* n);
 int fdd_variant_info(int32_t variant, int32_t* bytes_per_sample, int32_t* dm_per_block, int32_t* tile,
-                     int32_t* threads);
+                     int32_t* threads, int32_t* group);
+
+/* Diagnostics: the tables of pattern-factored variant `variant` (a global
+ * variant index with *group > 0) for native-rate range r of a plan
+ * description, built on the host only (no GPU), for inspection and CPU
+ * checks of the kernel's shared-memory addressing.  info[0..7] receives Lw
+ * (raw row words; < 0 if the layout does not fit), pattern-region bytes,
+ * groups, stages, ints per descriptor, shared-memory bytes, descriptors,
+ * DM blocks.  Array arguments may be NULL (sizes first, then data): base
+ * [n_blk][n_chan], goff [n_blk][n_groups][BD], pdesc [n_desc][desc_ints],
+ * pd_idx [n_blk][n_stages][2], delays [n_dm][n_chan]. */
+int fdd_fact_tables_host(const fdd_plan_desc* desc, const int16_t* sb_map_host, int32_t range, int32_t variant,
+                         int32_t chan_per_stage, int64_t* info, int32_t* base, int32_t* goff, int32_t* pdesc,
+                         int32_t* pd_idx, int32_t* delays);
 
 /* Current kernel configuration of range r. */
 int fdd_plan_get_config(const fdd_plan* plan, int32_t r, fdd_kernel_config* out);

@@ -126,7 +126,7 @@ def _lib_raw():
     L.fdd_plan_set_timing.argtypes = [_P, _I32]
     L.fdd_num_variants.argtypes = [ctypes.POINTER(_I32)]
     L.fdd_variant_info.argtypes = [_I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32),
-                                   ctypes.POINTER(_I32)]
+                                   ctypes.POINTER(_I32), ctypes.POINTER(_I32)]
     L.fdd_plan_get_config.argtypes = [_P, _I32, ctypes.POINTER(KernelConfig)]
     L.fdd_plan_set_config.argtypes = [_P, _I32, _I32, _I32]
     L.fdd_plan_autotune.argtypes = [_P, _P, _I64, _I64, _I64, _P, _SZ, _I32, _P]
@@ -149,6 +149,7 @@ def _lib_raw():
     L.fdd_server_results.argtypes = [_P, ctypes.POINTER(_WindowResult), _I32, _P, _I64, ctypes.POINTER(_I32),
                                      ctypes.POINTER(_I64)]
     L.fdd_server_info.argtypes = [_P, ctypes.POINTER(_ServerStats)]
+    L.fdd_fact_tables_host.argtypes = [ctypes.POINTER(_PlanDesc), _P, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P]
     L.fdd_search_static.argtypes = [_P, _P, _I64, _I64, _I64, _I64, _P, _I64, _P, _P, _P]
     L.fdd_plan_stage_times.argtypes = [_P, _I32, _P, _P, _P, ctypes.POINTER(_I32)]
     _lib = L
@@ -160,17 +161,18 @@ def version():
 
 
 def variants():
-    """[{index, bytes_per_sample, dm_per_block, tile, threads}] of the compiled dedispersion kernels."""
+    """[{index, bytes_per_sample, dm_per_block, tile, threads, group}] of the compiled dedispersion
+    kernels (group > 0: pattern-factored kernel with channel groups of that size)."""
     L = _lib_raw()
     n = _I32()
     _check(L.fdd_num_variants(ctypes.byref(n)), "fdd_num_variants")
     out = []
     for v in range(n.value):
-        e, bd, t, th = _I32(), _I32(), _I32(), _I32()
-        _check(L.fdd_variant_info(v, ctypes.byref(e), ctypes.byref(bd), ctypes.byref(t), ctypes.byref(th)),
-               "fdd_variant_info")
+        e, bd, t, th, g = _I32(), _I32(), _I32(), _I32(), _I32()
+        _check(L.fdd_variant_info(v, ctypes.byref(e), ctypes.byref(bd), ctypes.byref(t), ctypes.byref(th),
+                                  ctypes.byref(g)), "fdd_variant_info")
         out.append(dict(index=v, bytes_per_sample=e.value, dm_per_block=bd.value, tile=t.value,
-                        threads=th.value))
+                        threads=th.value, group=g.value))
     return out
 
 
@@ -363,6 +365,51 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def _plan_desc(n_tab, n_chan, n_sb, chan_freq_mhz, t_samp_s, ranges, snr_thresh, keep):
+    freq = np.ascontiguousarray(chan_freq_mhz, dtype=np.float64)
+    rs = [dict(dm0=float(r["dm0"]), ddm=float(r["ddm"]), n_dm=int(r["n_dm"]), downsamp=int(r.get("downsamp", 1)),
+               widths=[int(w) for w in r["widths"]]) for r in ranges]
+    ws = [np.ascontiguousarray(r["widths"], dtype=np.int32) for r in rs]
+    rr = (_Range * len(rs))()
+    for k, r in enumerate(rs):
+        rr[k].dm0, rr[k].ddm, rr[k].n_dm = r["dm0"], r["ddm"], r["n_dm"]
+        rr[k].downsamp, rr[k].n_width = r["downsamp"], len(r["widths"])
+        rr[k].widths = ws[k].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    keep.extend([freq, ws, rr])
+    return _PlanDesc(n_tab, n_chan, n_sb, freq.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(t_samp_s),
+                     len(rs), rr, float(snr_thresh))
+
+
+def fact_tables_host(n_tab, n_chan, n_sb, chan_freq_mhz, t_samp_s, ranges, sb_map, r, variant, chan_per_stage):
+    """Host-only build of the pattern-factored kernel's tables (include/fdd.h:
+    fdd_fact_tables_host), for inspection and CPU checks.  Needs no GPU."""
+    L = _lib_raw()
+    keep = []
+    desc = _plan_desc(n_tab, n_chan, n_sb, chan_freq_mhz, t_samp_s, ranges, 0.0, keep)
+    sb = np.ascontiguousarray(sb_map, dtype=np.int16)
+    info = np.zeros(8, np.int64)
+    args = [ctypes.byref(desc), sb.ctypes.data_as(ctypes.c_void_p), int(r), int(variant), int(chan_per_stage),
+            info.ctypes.data_as(ctypes.c_void_p)]
+    _check(L.fdd_fact_tables_host(*args, None, None, None, None, None), "fdd_fact_tables_host")
+    Lw, pat_bytes, n_groups, n_stages, desc_ints, smem, n_desc, n_blk = [int(v) for v in info]
+    out = dict(Lw=Lw, pat_bytes=pat_bytes, n_groups=n_groups, n_stages=n_stages, desc_ints=desc_ints,
+               smem_bytes=smem, n_desc=n_desc, n_blk=n_blk)
+    if Lw < 0:
+        return out
+    v = variants()[int(variant)]
+    bd = v["dm_per_block"]
+    n_dm = int(ranges[r]["n_dm"])
+    out["base"] = np.zeros((n_blk, n_chan), np.int32)
+    out["goff"] = np.zeros((n_blk, n_groups, bd), np.int32)
+    out["pdesc"] = np.zeros((max(n_desc, 1), desc_ints), np.int32)
+    out["pd_idx"] = np.zeros((n_blk, n_stages, 2), np.int32)
+    out["delays"] = np.zeros((n_dm, n_chan), np.int32)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check(L.fdd_fact_tables_host(*args, ptr(out["base"]), ptr(out["goff"]), ptr(out["pdesc"]), ptr(out["pd_idx"]),
+                                  ptr(out["delays"])), "fdd_fact_tables_host")
+    return out
 
 
 def decode_candidates(cands, n):

@@ -1,0 +1,174 @@
+// fdd_fact.cu -- host tables of the pattern-factored dedispersion kernel.
+//
+// Brute-force dedispersion adds, for trial i, channel c's sample at
+// t + d[i][c].  Split the channels into groups of G consecutive channels and
+// write d[i][c] = ref_i,g + rel_i,g,c with ref_i,g the smallest delay of the
+// group.  Every trial whose relative delays rel_i,g,* are equal ("pattern")
+// adds the same group partial sum R_p(tau) = sum_{c in g} X_c(tau + rel_c),
+// only shifted by ref_i,g.  Within a block of consecutive trials a group has
+// few distinct patterns (about 4 for G = 4 and 10 for G = 8 over 64 trials on
+// the ARTS band), so the kernel builds each pattern's partial sums once per
+// block in shared memory and every trial reads one 16-bit partial per group
+// instead of G bytes.  The sums are the same integers in another order: the
+// result is bit-identical to brute force.
+//
+// For a range, kernel variant and channel-stage size this file computes:
+//   base  [n_blk][n_chan]        first staged sample of each channel's raw row
+//   goff  [n_blk][n_groups][BD]  shared-memory byte offset of trial jj's pattern
+//                                row word for group g (copy = offset parity)
+//   pdesc per (block, stage) the list of pattern rows to build:
+//         {dst copy 0, dst copy 1, units of 4 samples, src offset per channel}
+//   pd_idx [n_blk][n_stages][2]  (first descriptor, count)
+// and the raw row length Lw and the pattern region size of the layout.
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "fdd_plan_impl.h"
+
+using namespace fdd::host;
+
+namespace fdd {
+namespace host {
+
+FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactVariant& v, int CC) {
+    FactTables ft;
+    const int G = v.G, BD = v.bd(), T = v.tile();
+    const int n_chan = p->n_chan;
+    const int n_blk = (r.n_dm + BD - 1) / BD;
+    const int n_groups = (n_chan + G - 1) / G;
+    const int n_stages = (n_chan + CC - 1) / CC;
+    const int gps = CC / G;
+    ft.n_groups = n_groups;
+    ft.n_stages = n_stages;
+    ft.desc_ints = v.desc_ints();
+    ft.base.assign(static_cast<size_t>(n_blk) * n_chan, 0);
+    ft.goff.assign(static_cast<size_t>(n_blk) * n_groups * BD, 0);
+    ft.pd_idx.assign(static_cast<size_t>(n_blk) * n_stages * 2, 0);
+    auto D = [&](int i, int c) { return r.delay[static_cast<size_t>(i) * n_chan + c]; };
+
+    // raw row starts (aligned to 16 samples) and the largest staged span
+    int64_t max_need = 0;  // bytes of a staged row that some read touches
+    for (int b = 0; b < n_blk; b++) {
+        const int ia = b * BD, ib = std::min(r.n_dm, (b + 1) * BD);
+        for (int c = 0; c < n_chan; c++) {
+            int32_t lo = D(ia, c);
+            for (int i = ia; i < ib; i++) lo = std::min(lo, D(i, c));
+            ft.base[static_cast<size_t>(b) * n_chan + c] = lo / 16 * 16;
+        }
+    }
+    // patterns per (block, group), pattern rows per (block, stage)
+    struct Pat {
+        std::vector<int32_t> rel;
+        int32_t rmin = 0, rmax = 0;
+    };
+    int64_t pat_region = 0;
+    std::vector<int32_t> trial_pat(BD), trial_ref(BD);
+    for (int b = 0; b < n_blk; b++) {
+        const int ia = b * BD, ib = std::min(r.n_dm, (b + 1) * BD);
+        for (int s = 0; s < n_stages; s++) {
+            int64_t cursor = 0;  // bytes of pattern rows of this (block, stage)
+            const int first_desc = static_cast<int>(ft.pdesc.size() / ft.desc_ints);
+            for (int gl = 0; gl < gps; gl++) {
+                const int g = s * gps + gl;
+                if (g >= n_groups) break;
+                const int c0 = g * G;
+                const int gn = std::min(G, n_chan - c0);
+                std::map<std::vector<int32_t>, int> index;
+                std::vector<Pat> pats;
+                for (int jj = 0; jj < BD; jj++) {
+                    const int i = std::min(ia + jj, r.n_dm - 1);  // padding trials repeat the last one
+                    int32_t ref = D(i, c0);
+                    for (int k = 1; k < gn; k++) ref = std::min(ref, D(i, c0 + k));
+                    std::vector<int32_t> rel(gn);
+                    for (int k = 0; k < gn; k++) rel[k] = D(i, c0 + k) - ref;
+                    auto it = index.find(rel);
+                    int pi;
+                    if (it == index.end()) {
+                        pi = static_cast<int>(pats.size());
+                        index.emplace(rel, pi);
+                        Pat pt;
+                        pt.rel = rel;
+                        pt.rmin = pt.rmax = ref;
+                        pats.push_back(pt);
+                    } else {
+                        pi = it->second;
+                        pats[pi].rmin = std::min(pats[pi].rmin, ref);
+                        pats[pi].rmax = std::max(pats[pi].rmax, ref);
+                    }
+                    trial_pat[jj] = pi;
+                    trial_ref[jj] = ref;
+                }
+                (void)ib;
+                std::vector<int32_t> dst0(pats.size()), dst1(pats.size());
+                for (size_t pi = 0; pi < pats.size(); pi++) {
+                    const Pat& pt = pats[pi];
+                    const int32_t span = pt.rmax - pt.rmin;
+                    const int32_t nw4 = (span + T) / 4 + 2;  // units of 4 samples built
+                    const int32_t lpw = 2 * nw4;             // 32-bit words per copy
+                    dst0[pi] = static_cast<int32_t>(cursor);
+                    dst1[pi] = static_cast<int32_t>(cursor + 4LL * lpw);
+                    cursor += 8LL * lpw;
+                    std::vector<int32_t> d(ft.desc_ints, 0);
+                    d[0] = dst0[pi];  // relative to the pattern region; made absolute below
+                    d[1] = dst1[pi];
+                    d[2] = nw4;
+                    for (int k = 0; k < G; k++) {
+                        if (k < gn) {
+                            const int c = c0 + k;
+                            const int32_t o = pt.rmin + pt.rel[k] - ft.base[static_cast<size_t>(b) * n_chan + c];
+                            // channel slot cc, copy (o & 3), aligned word (o & ~3); slot bases added below
+                            d[3 + k] = ((c - s * CC) << 20) | ((o & 3) << 18) | (o & ~3);
+                            max_need = std::max<int64_t>(max_need, static_cast<int64_t>(o) + 4LL * nw4 + 4);
+                        } else {
+                            d[3 + k] = -1;  // missing channel: the zero row
+                        }
+                    }
+                    ft.pdesc.insert(ft.pdesc.end(), d.begin(), d.end());
+                }
+                for (int jj = 0; jj < BD; jj++) {
+                    const int pi = trial_pat[jj];
+                    const int32_t o = trial_ref[jj] - pats[pi].rmin;
+                    const int32_t dst = (o & 1) ? dst1[pi] : dst0[pi];
+                    ft.goff[(static_cast<size_t>(b) * n_groups + g) * BD + jj] = dst + 4 * (o >> 1);
+                }
+            }
+            const int n_desc = static_cast<int>(ft.pdesc.size() / ft.desc_ints) - first_desc;
+            ft.pd_idx[(static_cast<size_t>(b) * n_stages + s) * 2] = first_desc;
+            ft.pd_idx[(static_cast<size_t>(b) * n_stages + s) * 2 + 1] = n_desc;
+            pat_region = std::max(pat_region, cursor);
+        }
+    }
+    // raw row words: every staged read (brute-force span and pattern builds)
+    const int64_t need_words = (max_need + 3) / 4;
+    const int64_t Lw = static_cast<int64_t>(align_up(static_cast<size_t>(need_words + 1), 4));
+    if (Lw > (1 << 16) || pat_region > (1 << 20)) {
+        ft.Lw = -1;
+        return ft;
+    }
+    ft.Lw = static_cast<int32_t>(Lw);
+    ft.pat_bytes = static_cast<int32_t>(align_up(static_cast<size_t>(pat_region), 16));
+    // resolve shared-memory addresses: [zero row | raw slots | patterns | goff x2]
+    const int64_t zero_bytes = 4LL * ft.Lw;
+    const int64_t slot_bytes = 4LL * 4 * ft.Lw;
+    const int64_t pat_base = zero_bytes + slot_bytes * CC;
+    for (size_t di = 0; di < ft.pdesc.size(); di += ft.desc_ints) {
+        ft.pdesc[di] += static_cast<int32_t>(pat_base);
+        ft.pdesc[di + 1] += static_cast<int32_t>(pat_base);
+        for (int k = 0; k < G; k++) {
+            int32_t& e = ft.pdesc[di + 3 + k];
+            if (e < 0) {
+                e = 0;  // zero row at the start of shared memory
+            } else {
+                const int32_t cc = e >> 20, q = (e >> 18) & 3, w = e & ((1 << 18) - 1);
+                e = static_cast<int32_t>(zero_bytes + slot_bytes * cc + 4LL * ft.Lw * q + w);
+            }
+        }
+    }
+    for (int32_t& g : ft.goff) g += static_cast<int32_t>(pat_base);
+    ft.smem_bytes = static_cast<size_t>(pat_base + ft.pat_bytes) + 2ull * gps * BD * 4;
+    return ft;
+}
+
+}  // namespace host
+}  // namespace fdd

@@ -55,6 +55,38 @@ bool dedisp_cc_ok(const DedispVariant& v, int Lw, int CC, size_t smem_budget);
 cudaError_t launch_dedisp(int variant, const DedispArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
+// Pattern-factored dedispersion (k_dedisp_fact.cu; tables from fdd_fact.cu).
+//   G     channels per group; NW, DPW, WARPS as above; samples per word are
+//         16-bit pattern partials, so T = 64 * NW
+struct FactVariant {
+    int G, NW, DPW, WARPS, MAXIT;
+    int bd() const { return WARPS * DPW; }
+    int tile() const { return 64 * NW; }
+    int threads() const { return WARPS * 32; }
+    int desc_ints() const { return (3 + G + 3) / 4 * 4; }
+};
+
+struct FactArgs {
+    const uint8_t* in;          // raw uint8 rows (tab, c) at in + (tab * n_chan + c) * pitch_bytes
+    int64_t pitch_bytes;
+    int64_t n_valid;            // valid samples per row
+    const int16_t* sb_map;      // [n_sb][n_chan]
+    const int32_t* base;        // [n_blk][n_chan]
+    const int32_t* goff;        // [n_blk][n_groups][BD]
+    const int32_t* pdesc;       // pattern-row descriptors
+    const int32_t* pd_idx;      // [n_blk][n_stages][2]
+    int32_t* series;            // [n_sb][n_dm][n_out]
+    unsigned long long* stat;   // [n_sb * n_dm][2]
+    int32_t n_chan, n_dm, n_out, n_sb;
+    int32_t Lw, CC, n_stages, n_groups, pat_bytes;
+};
+
+int num_fact_variants();
+const FactVariant& fact_variant(int idx);
+bool fact_cc_ok(const FactVariant& v, int Lw, int CC);
+cudaError_t launch_dedisp_fact(int variant, const FactArgs& a, size_t smem, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
 struct BoxcarArgs {
     const int32_t* series;              // [n_sb][n_dm][n_out] of this range
     const unsigned long long* stat;     // [n_sb * n_dm][2]

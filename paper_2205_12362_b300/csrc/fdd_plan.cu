@@ -177,18 +177,70 @@ int fdd::host::check_search_args(const fdd_plan* plan, const uint8_t* d_tabs, in
 
 namespace {
 
+void free_fact_tables(RangeState& r) {
+    for (int32_t** ptr : {&r.d_fbase, &r.d_goff, &r.d_pdesc, &r.d_pdidx}) {
+        if (*ptr) cudaFree(*ptr);
+        *ptr = nullptr;
+    }
+    r.fact = -1;
+}
+
 void free_range_tables(RangeState& r) {
     if (r.d_off) cudaFree(r.d_off);
     if (r.d_base) cudaFree(r.d_base);
     r.d_off = nullptr;
     r.d_base = nullptr;
+    free_fact_tables(r);
+}
+
+int upload_vec(int32_t** dst, const std::vector<int32_t>& v, const char* what) {
+    cudaError_t e = cudaMalloc(dst, std::max<size_t>(v.size(), 4) * sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    if (!v.empty() && (e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, what);
+    return FDD_OK;
+}
+
+// Configure range r for pattern-factored variant fv with CC channels per
+// stage (0 = the largest that fits).
+int configure_fact(fdd_plan* p, RangeState& r, int fv, int CC) {
+    if (fv < 0 || fv >= fdd::num_fact_variants()) return fail(FDD_ERR_INVALID_ARG, "kernel variant out of range");
+    if (r.D != 1) return fail(FDD_ERR_INVALID_ARG, "the factored kernel serves native-rate ranges only");
+    const fdd::FactVariant& v = fdd::fact_variant(fv);
+    FactTables best;
+    int best_cc = 0;
+    for (int cc : {64, 48, 32, 16, 8}) {
+        if (CC != 0 && cc != CC) continue;
+        if (cc % v.G) continue;
+        FactTables ft = build_fact_tables(p, r, v, cc);
+        if (ft.Lw < 0 || !fdd::fact_cc_ok(v, ft.Lw, cc) || ft.smem_bytes > kSmemBudget) continue;
+        best = std::move(ft);
+        best_cc = cc;
+        break;
+    }
+    if (best_cc == 0) return fail(FDD_ERR_UNSUPPORTED, "factored kernel does not fit this range and stage size");
+    free_fact_tables(r);
+    int rc;
+    if ((rc = upload_vec(&r.d_fbase, best.base, "factored base table")) != FDD_OK) return rc;
+    if ((rc = upload_vec(&r.d_goff, best.goff, "factored offset table")) != FDD_OK) return rc;
+    if ((rc = upload_vec(&r.d_pdesc, best.pdesc, "factored descriptors")) != FDD_OK) return rc;
+    if ((rc = upload_vec(&r.d_pdidx, best.pd_idx, "factored descriptor index")) != FDD_OK) return rc;
+    r.fact = fv;
+    r.f_CC = best_cc;
+    r.f_Lw = best.Lw;
+    r.f_pat_bytes = best.pat_bytes;
+    r.f_n_stages = best.n_stages;
+    r.f_n_groups = best.n_groups;
+    r.f_smem = best.smem_bytes;
+    return FDD_OK;
 }
 
 // Configure range r for kernel variant `variant` with channel stage CC
 // (0 = the largest that fits).
 int configure_range(fdd_plan* p, RangeState& r, int variant, int CC) {
-    if (variant < 0 || variant >= fdd::num_dedisp_variants())
-        return fail(FDD_ERR_INVALID_ARG, "kernel variant out of range");
+    if (variant >= fdd::num_dedisp_variants())  // factored variants follow the brute-force ones
+        return configure_fact(p, r, variant - fdd::num_dedisp_variants(), CC);
+    if (variant < 0) return fail(FDD_ERR_INVALID_ARG, "kernel variant out of range");
     const fdd::DedispVariant& v = fdd::dedisp_variant(variant);
     if (v.E != (r.D == 1 ? 1 : 2)) return fail(FDD_ERR_INVALID_ARG, "kernel variant for the wrong sample width");
     const HostTables h = build_tables(p, r, v);
@@ -203,6 +255,36 @@ int configure_range(fdd_plan* p, RangeState& r, int variant, int CC) {
     r.Lw = h.Lw;
     r.CC = CC;
     return FDD_OK;
+}
+
+// Launch range r's dedispersion kernel (brute force or pattern-factored).
+cudaError_t launch_range_dedisp(const RangeState& r, const fdd::DedispArgs& a, cudaStream_t s) {
+    if (r.fact < 0) return fdd::launch_dedisp(r.variant, a, s);
+    fdd::FactArgs fa{};
+    fa.in = a.in;
+    fa.pitch_bytes = a.pitch_bytes;
+    fa.n_valid = a.n_valid;
+    fa.sb_map = a.sb_map;
+    fa.base = r.d_fbase;
+    fa.goff = r.d_goff;
+    fa.pdesc = r.d_pdesc;
+    fa.pd_idx = r.d_pdidx;
+    fa.series = a.series;
+    fa.stat = a.stat;
+    fa.n_chan = a.n_chan;
+    fa.n_dm = a.n_dm;
+    fa.n_out = a.n_out;
+    fa.n_sb = a.n_sb;
+    fa.Lw = r.f_Lw;
+    fa.CC = r.f_CC;
+    fa.n_stages = r.f_n_stages;
+    fa.n_groups = r.f_n_groups;
+    fa.pat_bytes = r.f_pat_bytes;
+    return fdd::launch_dedisp_fact(r.fact, fa, r.f_smem, s);
+}
+
+int range_variant_index(const RangeState& r) {
+    return r.fact >= 0 ? fdd::num_dedisp_variants() + r.fact : r.variant;
 }
 
 int default_variant(int E) {
@@ -247,6 +329,80 @@ bool plan_timing_enabled(const fdd_plan* plan) { return plan && plan->timing; }
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 }  // namespace fdd
 
+// Host part of plan construction: validation and every range's delay table.
+static int build_host_plan(const fdd_plan_desc* desc, const int16_t* sb_map_host, fdd_plan* p) {
+    if (!desc || !sb_map_host) return fail(FDD_ERR_INVALID_ARG, "null argument");
+    if (desc->n_tab < 1 || desc->n_tab > FDD_MAX_TABS || desc->n_chan < 1 || desc->n_chan > FDD_MAX_CHANNELS ||
+        desc->n_sb < 1 || desc->n_sb > 65535 || desc->n_range < 1 || !desc->ranges || !desc->chan_freq_mhz ||
+        !(desc->t_samp_s > 0))
+        return fail(FDD_ERR_INVALID_ARG, "bad plan dimensions");
+    for (int c = 0; c < desc->n_chan; c++)
+        if (!(desc->chan_freq_mhz[c] > 0) || !std::isfinite(desc->chan_freq_mhz[c]))
+            return fail(FDD_ERR_INVALID_ARG, "channel frequencies must be positive and finite");
+    for (int64_t k = 0; k < static_cast<int64_t>(desc->n_sb) * desc->n_chan; k++)
+        if (sb_map_host[k] < 0 || sb_map_host[k] >= desc->n_tab)
+            return fail(FDD_ERR_INVALID_ARG, "sb_map entry outside [0, n_tab)");
+    p->n_tab = desc->n_tab;
+    p->n_chan = desc->n_chan;
+    p->n_sb = desc->n_sb;
+    p->t_samp = desc->t_samp_s;
+    p->thr = desc->snr_thresh;
+    p->freq.assign(desc->chan_freq_mhz, desc->chan_freq_mhz + desc->n_chan);
+    p->sb_map.assign(sb_map_host, sb_map_host + static_cast<size_t>(desc->n_sb) * desc->n_chan);
+    const double f_top = *std::max_element(p->freq.begin(), p->freq.end());
+    int32_t dm_index = 0;
+    for (int ri = 0; ri < desc->n_range; ri++) {
+        const fdd_range& in = desc->ranges[ri];
+        if (!(in.dm0 >= 0) || !(in.ddm > 0) || in.n_dm < 1 || in.downsamp < 1 || in.downsamp > 257 ||
+            in.n_width < 1 || in.n_width > FDD_MAX_WIDTHS || !in.widths) {
+            return fail(FDD_ERR_INVALID_ARG, "bad DM range");
+        }
+        RangeState r;
+        r.dm0 = in.dm0;
+        r.ddm = in.ddm;
+        r.n_dm = in.n_dm;
+        r.D = in.downsamp;
+        r.n_width = in.n_width;
+        r.wmax = 1;
+        for (int k = 0; k < in.n_width; k++) {
+            if (in.widths[k] < 1 || in.widths[k] > FDD_MAX_WIDTH) {
+                return fail(FDD_ERR_INVALID_ARG, "boxcar width outside [1, FDD_MAX_WIDTH]");
+            }
+            r.widths[k] = in.widths[k];
+            r.wmax = std::max(r.wmax, in.widths[k]);
+        }
+        r.dm_index0 = dm_index;
+        dm_index += in.n_dm;
+        // Delay table: cold-plasma law, FP64, same operation order for every
+        // entry, rounded half away from zero.
+        r.delay.resize(static_cast<size_t>(r.n_dm) * p->n_chan);
+        int64_t dmax = 0;
+        for (int i = 0; i < r.n_dm; i++) {
+            const double dm = r.dm0 + static_cast<double>(i) * r.ddm;
+            for (int c = 0; c < p->n_chan; c++) {
+                const double f = p->freq[c];
+                const double x = ((kDispersionConstant * dm) * (1.0 / (f * f) - 1.0 / (f_top * f_top))) /
+                                 (static_cast<double>(r.D) * p->t_samp);
+                const long long d = std::llround(x);
+                if (d < 0 || d > (1LL << 28)) {
+                    return fail(FDD_ERR_UNSUPPORTED, "delay out of range");
+                }
+                r.delay[static_cast<size_t>(i) * p->n_chan + c] = static_cast<int32_t>(d);
+                dmax = std::max<int64_t>(dmax, d);
+            }
+        }
+        r.dmax = static_cast<int32_t>(dmax);
+        p->max_delay_native = std::max<int64_t>(p->max_delay_native, dmax * r.D);
+        p->ranges.push_back(std::move(r));
+        if (in.downsamp > 1 &&
+            std::find(p->ds_factors.begin(), p->ds_factors.end(), in.downsamp) == p->ds_factors.end())
+            p->ds_factors.push_back(in.downsamp);
+    }
+    p->n_dm_total = dm_index;
+
+    return FDD_OK;
+}
+
 extern "C" {
 
 const char* fdd_version(void) { return "fdd 0.1 (sm_103a)"; }
@@ -272,80 +428,14 @@ const char* fdd_last_error_message(void) { return g_last_error.c_str(); }
 int fdd_plan_create(const fdd_plan_desc* desc, const int16_t* sb_map_host, fdd_plan** out) {
     if (!desc || !sb_map_host || !out) return fail(FDD_ERR_INVALID_ARG, "null argument");
     *out = nullptr;
-    if (desc->n_tab < 1 || desc->n_tab > FDD_MAX_TABS || desc->n_chan < 1 || desc->n_chan > FDD_MAX_CHANNELS ||
-        desc->n_sb < 1 || desc->n_range < 1 || !desc->ranges || !desc->chan_freq_mhz || !(desc->t_samp_s > 0))
-        return fail(FDD_ERR_INVALID_ARG, "bad plan dimensions");
-    for (int c = 0; c < desc->n_chan; c++)
-        if (!(desc->chan_freq_mhz[c] > 0) || !std::isfinite(desc->chan_freq_mhz[c]))
-            return fail(FDD_ERR_INVALID_ARG, "channel frequencies must be positive and finite");
-    for (int64_t k = 0; k < static_cast<int64_t>(desc->n_sb) * desc->n_chan; k++)
-        if (sb_map_host[k] < 0 || sb_map_host[k] >= desc->n_tab)
-            return fail(FDD_ERR_INVALID_ARG, "sb_map entry outside [0, n_tab)");
-
     fdd_plan* p = new (std::nothrow) fdd_plan();
     if (!p) return fail(FDD_ERR_NO_MEMORY, "host allocation");
-    cudaGetDevice(&p->device);
-    p->n_tab = desc->n_tab;
-    p->n_chan = desc->n_chan;
-    p->n_sb = desc->n_sb;
-    p->t_samp = desc->t_samp_s;
-    p->thr = desc->snr_thresh;
-    p->freq.assign(desc->chan_freq_mhz, desc->chan_freq_mhz + desc->n_chan);
-    p->sb_map.assign(sb_map_host, sb_map_host + static_cast<size_t>(desc->n_sb) * desc->n_chan);
-    const double f_top = *std::max_element(p->freq.begin(), p->freq.end());
-
-    int32_t dm_index = 0;
-    for (int ri = 0; ri < desc->n_range; ri++) {
-        const fdd_range& in = desc->ranges[ri];
-        if (!(in.dm0 >= 0) || !(in.ddm > 0) || in.n_dm < 1 || in.downsamp < 1 || in.downsamp > 257 ||
-            in.n_width < 1 || in.n_width > FDD_MAX_WIDTHS || !in.widths) {
-            fdd_plan_destroy(p);
-            return fail(FDD_ERR_INVALID_ARG, "bad DM range");
-        }
-        RangeState r;
-        r.dm0 = in.dm0;
-        r.ddm = in.ddm;
-        r.n_dm = in.n_dm;
-        r.D = in.downsamp;
-        r.n_width = in.n_width;
-        r.wmax = 1;
-        for (int k = 0; k < in.n_width; k++) {
-            if (in.widths[k] < 1 || in.widths[k] > FDD_MAX_WIDTH) {
-                fdd_plan_destroy(p);
-                return fail(FDD_ERR_INVALID_ARG, "boxcar width outside [1, FDD_MAX_WIDTH]");
-            }
-            r.widths[k] = in.widths[k];
-            r.wmax = std::max(r.wmax, in.widths[k]);
-        }
-        r.dm_index0 = dm_index;
-        dm_index += in.n_dm;
-        // Delay table: cold-plasma law, FP64, same operation order for every
-        // entry, rounded half away from zero.
-        r.delay.resize(static_cast<size_t>(r.n_dm) * p->n_chan);
-        int64_t dmax = 0;
-        for (int i = 0; i < r.n_dm; i++) {
-            const double dm = r.dm0 + static_cast<double>(i) * r.ddm;
-            for (int c = 0; c < p->n_chan; c++) {
-                const double f = p->freq[c];
-                const double x = ((kDispersionConstant * dm) * (1.0 / (f * f) - 1.0 / (f_top * f_top))) /
-                                 (static_cast<double>(r.D) * p->t_samp);
-                const long long d = std::llround(x);
-                if (d < 0 || d > (1LL << 28)) {
-                    fdd_plan_destroy(p);
-                    return fail(FDD_ERR_UNSUPPORTED, "delay out of range");
-                }
-                r.delay[static_cast<size_t>(i) * p->n_chan + c] = static_cast<int32_t>(d);
-                dmax = std::max<int64_t>(dmax, d);
-            }
-        }
-        r.dmax = static_cast<int32_t>(dmax);
-        p->max_delay_native = std::max<int64_t>(p->max_delay_native, dmax * r.D);
-        p->ranges.push_back(std::move(r));
-        if (in.downsamp > 1 &&
-            std::find(p->ds_factors.begin(), p->ds_factors.end(), in.downsamp) == p->ds_factors.end())
-            p->ds_factors.push_back(in.downsamp);
+    const int hrc = build_host_plan(desc, sb_map_host, p);
+    if (hrc != FDD_OK) {
+        delete p;
+        return hrc;
     }
-    p->n_dm_total = dm_index;
+    cudaGetDevice(&p->device);
 
     cudaError_t e = cudaMalloc(&p->d_sb_map, p->sb_map.size() * sizeof(int16_t));
     if (e != cudaSuccess) {
@@ -453,7 +543,7 @@ int fdd_search(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitc
         if (nr == 0) continue;
         const fdd::DedispArgs a = dedisp_args(plan, r, ri, L, d_tabs, pitch, ws, series, stat, n_in, n_out);
         if ((e = stage_begin(1, static_cast<int>(ri))) != cudaSuccess) return cuda_fail(e, "timing event");
-        e = fdd::launch_dedisp(r.variant, a, s);
+        e = launch_range_dedisp(r, a, s);
         if (e != cudaSuccess) return cuda_fail(e, "dedispersion launch");
         if ((e = stage_end()) != cudaSuccess) return cuda_fail(e, "timing event");
 
@@ -488,18 +578,29 @@ int fdd_search(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitc
 
 int fdd_num_variants(int32_t* n) {
     if (!n) return fail(FDD_ERR_INVALID_ARG, "null argument");
-    *n = fdd::num_dedisp_variants();
+    *n = fdd::num_dedisp_variants() + fdd::num_fact_variants();
     return FDD_OK;
 }
 
 int fdd_variant_info(int32_t variant, int32_t* bytes_per_sample, int32_t* dm_per_block, int32_t* tile,
-                     int32_t* threads) {
-    if (variant < 0 || variant >= fdd::num_dedisp_variants()) return fail(FDD_ERR_INVALID_ARG, "bad variant");
+                     int32_t* threads, int32_t* group) {
+    const int nb = fdd::num_dedisp_variants();
+    if (variant < 0 || variant >= nb + fdd::num_fact_variants()) return fail(FDD_ERR_INVALID_ARG, "bad variant");
+    if (variant >= nb) {
+        const fdd::FactVariant& v = fdd::fact_variant(variant - nb);
+        if (bytes_per_sample) *bytes_per_sample = 1;
+        if (dm_per_block) *dm_per_block = v.bd();
+        if (tile) *tile = v.tile();
+        if (threads) *threads = v.threads();
+        if (group) *group = v.G;
+        return FDD_OK;
+    }
     const fdd::DedispVariant& v = fdd::dedisp_variant(variant);
     if (bytes_per_sample) *bytes_per_sample = v.E;
     if (dm_per_block) *dm_per_block = v.bd();
     if (tile) *tile = v.tile();
     if (threads) *threads = v.threads();
+    if (group) *group = 0;
     return FDD_OK;
 }
 
@@ -507,13 +608,22 @@ int fdd_plan_get_config(const fdd_plan* plan, int32_t r, fdd_kernel_config* out)
     if (!plan || !out || r < 0 || r >= static_cast<int32_t>(plan->ranges.size()))
         return fail(FDD_ERR_INVALID_ARG, "bad range index");
     const RangeState& rs = plan->ranges[r];
-    const fdd::DedispVariant& v = fdd::dedisp_variant(rs.variant);
-    out->variant = rs.variant;
-    out->dm_per_block = v.bd();
-    out->tile = v.tile();
-    out->chan_per_stage = rs.CC;
-    out->threads = v.threads();
-    out->row_words = rs.Lw;
+    out->variant = range_variant_index(rs);
+    if (rs.fact >= 0) {
+        const fdd::FactVariant& v = fdd::fact_variant(rs.fact);
+        out->dm_per_block = v.bd();
+        out->tile = v.tile();
+        out->chan_per_stage = rs.f_CC;
+        out->threads = v.threads();
+        out->row_words = rs.f_Lw;
+    } else {
+        const fdd::DedispVariant& v = fdd::dedisp_variant(rs.variant);
+        out->dm_per_block = v.bd();
+        out->tile = v.tile();
+        out->chan_per_stage = rs.CC;
+        out->threads = v.threads();
+        out->row_words = rs.Lw;
+    }
     out->tuned_ms = rs.tuned_ms;
     return FDD_OK;
 }
@@ -522,7 +632,7 @@ int fdd_plan_set_config(fdd_plan* plan, int32_t r, int32_t variant, int32_t chan
     if (!plan || r < 0 || r >= static_cast<int32_t>(plan->ranges.size()) || chan_per_stage < 0)
         return fail(FDD_ERR_INVALID_ARG, "bad range index");
     RangeState& rs = plan->ranges[r];
-    const int old_variant = rs.variant, old_cc = rs.CC;
+    const int old_variant = range_variant_index(rs), old_cc = rs.fact >= 0 ? rs.f_CC : rs.CC;
     const int rc = configure_range(plan, rs, variant, chan_per_stage);
     if (rc != FDD_OK && old_variant >= 0) configure_range(plan, rs, old_variant, old_cc);
     if (rc == FDD_OK) rs.tuned_ms = 0.f;
@@ -598,6 +708,31 @@ int fdd_plan_autotune(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64
                 }
             }
         }
+        for (int fv = 0; E == 1 && fv < fdd::num_fact_variants() && rc == FDD_OK; fv++) {
+            for (int cc : {16, 32, 48, 64}) {
+                if (configure_fact(plan, r, fv, cc) != FDD_OK) continue;  // does not fit
+                const fdd::DedispArgs a = dedisp_args(plan, r, ri, L, d_tabs, pitch, ws, series, stat, n_in, n_out);
+                if ((e = launch_range_dedisp(r, a, s)) != cudaSuccess) { rc = cuda_fail(e, "tuning launch"); break; }
+                cudaEventRecord(ev0, s);
+                for (int k = 0; k < reps && e == cudaSuccess; k++) e = launch_range_dedisp(r, a, s);
+                cudaEventRecord(ev1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
+                if (e != cudaSuccess) { rc = cuda_fail(e, "tuning launch"); break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev0, ev1);
+                ms /= reps;
+                if (std::getenv("FDD_TUNE_VERBOSE")) {
+                    const fdd::FactVariant& fvv = fdd::fact_variant(fv);
+                    std::fprintf(stderr, "fdd tune: range %zu factored variant %d (G %d bd %d tile %d) cc %d: %.4f ms\n",
+                                 ri, fdd::num_dedisp_variants() + fv, fvv.G, fvv.bd(), fvv.tile(), cc, ms);
+                }
+                if (ms < best) {
+                    best = ms;
+                    best_v = fdd::num_dedisp_variants() + fv;
+                    best_cc = cc;
+                }
+            }
+        }
         if (rc == FDD_OK) {
             rc = configure_range(plan, r, best_v, best_cc);
             if (rc == FDD_OK) r.tuned_ms = best;
@@ -606,6 +741,39 @@ int fdd_plan_autotune(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
     return rc;
+}
+
+int fdd_fact_tables_host(const fdd_plan_desc* desc, const int16_t* sb_map_host, int32_t range, int32_t variant,
+                         int32_t chan_per_stage, int64_t* info, int32_t* base, int32_t* goff, int32_t* pdesc,
+                         int32_t* pd_idx, int32_t* delays) {
+    if (!info) return fail(FDD_ERR_INVALID_ARG, "null info");
+    fdd_plan p;
+    int rc = build_host_plan(desc, sb_map_host, &p);
+    if (rc != FDD_OK) return rc;
+    const int fv = variant - fdd::num_dedisp_variants();
+    if (range < 0 || range >= static_cast<int32_t>(p.ranges.size()) || fv < 0 || fv >= fdd::num_fact_variants() ||
+        p.ranges[range].D != 1 || chan_per_stage < 1)
+        return fail(FDD_ERR_INVALID_ARG, "bad range, variant or stage size");
+    const fdd::FactVariant& v = fdd::fact_variant(fv);
+    if (chan_per_stage % v.G) return fail(FDD_ERR_INVALID_ARG, "stage size must be a multiple of G");
+    const RangeState& r = p.ranges[range];
+    const FactTables ft = build_fact_tables(&p, r, v, chan_per_stage);
+    const int64_t n_blk = (r.n_dm + v.bd() - 1) / v.bd();
+    info[0] = ft.Lw;
+    info[1] = ft.pat_bytes;
+    info[2] = ft.n_groups;
+    info[3] = ft.n_stages;
+    info[4] = ft.desc_ints;
+    info[5] = static_cast<int64_t>(ft.smem_bytes);
+    info[6] = ft.desc_ints ? static_cast<int64_t>(ft.pdesc.size()) / ft.desc_ints : 0;
+    info[7] = n_blk;
+    if (ft.Lw < 0) return FDD_OK;
+    if (base) std::memcpy(base, ft.base.data(), ft.base.size() * sizeof(int32_t));
+    if (goff) std::memcpy(goff, ft.goff.data(), ft.goff.size() * sizeof(int32_t));
+    if (pdesc) std::memcpy(pdesc, ft.pdesc.data(), ft.pdesc.size() * sizeof(int32_t));
+    if (pd_idx) std::memcpy(pd_idx, ft.pd_idx.data(), ft.pd_idx.size() * sizeof(int32_t));
+    if (delays) std::memcpy(delays, r.delay.data(), r.delay.size() * sizeof(int32_t));
+    return FDD_OK;
 }
 
 int fdd_plan_set_timing(fdd_plan* plan, int32_t enable) {

@@ -22,6 +22,14 @@ struct RangeState {
     float tuned_ms = 0.f;
     int32_t* d_off = nullptr;         // [n_blk][n_chan][BD]
     int32_t* d_base = nullptr;        // [n_blk][n_chan]
+    // pattern-factored kernel (fact >= 0 selects it instead of `variant`)
+    int fact = -1;
+    int32_t f_CC = 0, f_Lw = 0, f_pat_bytes = 0, f_n_stages = 0, f_n_groups = 0;
+    size_t f_smem = 0;
+    int32_t* d_fbase = nullptr;
+    int32_t* d_goff = nullptr;
+    int32_t* d_pdesc = nullptr;
+    int32_t* d_pdidx = nullptr;
 };
 
 // Device tables of one range for the batched persistent kernel.
@@ -89,6 +97,15 @@ struct HostTables {
 HostTables build_tables(const fdd_plan* p, const RangeState& r, const DedispVariant& v);
 int upload_tables(int32_t** d_off, int32_t** d_base, const HostTables& h);
 int pick_cc(const DedispVariant& v, int Lw);
+
+struct FactTables {
+    std::vector<int32_t> base, goff, pdesc, pd_idx;
+    int32_t Lw = 0, pat_bytes = 0, n_groups = 0, n_stages = 0, desc_ints = 0;
+    size_t smem_bytes = 0;
+};
+// Tables of the pattern-factored kernel for range r, variant v and CC
+// channels per stage (Lw < 0: does not fit).
+FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactVariant& v, int CC);
 
 struct Layout {
     size_t series = 0, series_bytes = 0;

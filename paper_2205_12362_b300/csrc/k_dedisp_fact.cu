@@ -1,0 +1,334 @@
+// k_dedisp_fact.cu -- pattern-factored exact dedispersion (native-rate
+// ranges).  Same result as k_dedisp, bit for bit; fewer shared-memory reads
+// per channel-add.  See fdd_fact.cu for the factorisation and its tables.
+//
+// Block = BD trials x T = 64*NW output samples of one SB.  Per channel stage:
+//   1. staging (as k_dedisp): the SB's TAB row of every channel, 4 byte-shifted
+//      copies, software-pipelined through registers;
+//   2. build: each warp takes pattern rows of the stage's channel groups; a
+//      lane forms 4 consecutive samples of R_p(tau) = sum_k X_k(tau + rel_k)
+//      from one aligned LDS.32 per channel (bytes split into even/odd 16-bit
+//      lanes with PRMT) and stores them as two copies of 16-bit pairs, the
+//      second shifted by one sample (the neighbouring lane's first sample
+//      comes by shuffle), so every trial's offset is an aligned LDS.32;
+//   3. accumulate: each trial adds, per group, one word of two 16-bit
+//      partials: acc_a += w, acc_b += w >> 16 (exact; low halves recovered as
+//      acc_a - (acc_b << 16)), two groups per IADD3.
+// The next stage's global loads are in flight during the build, and its
+// staging stores overlap the accumulation (which only reads pattern rows).
+#include "fdd_internal.cuh"
+
+namespace fdd {
+
+namespace {
+
+__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ void sts32(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void sts64(uint32_t addr, uint32_t a, uint32_t b) {
+    asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void load_offsets(const int32_t* p, int32_t (&o)[N]) {
+    if constexpr (N == 1) {
+        o[0] = p[0];
+    } else if constexpr (N == 2) {
+        const int2 v = *reinterpret_cast<const int2*>(p);
+        o[0] = v.x;
+        o[1] = v.y;
+    } else {
+        static_assert(N == 4, "DPW must be 1, 2 or 4");
+        const int4 v = *reinterpret_cast<const int4*>(p);
+        o[0] = v.x;
+        o[1] = v.y;
+        o[2] = v.z;
+        o[3] = v.w;
+    }
+}
+
+// Build one pattern row (whole warp).  d: descriptor {dst0, dst1, nw4,
+// src[G]} in global memory; s0: shared window address of dynamic smem.
+template <int G>
+__device__ __forceinline__ void build_row(const int32_t* __restrict__ d, uint32_t s0, int lane) {
+    const int4 h = __ldg(reinterpret_cast<const int4*>(d));
+    const uint32_t dst0 = s0 + static_cast<uint32_t>(h.x), dst1 = s0 + static_cast<uint32_t>(h.y);
+    const int nw4 = h.z;
+    uint32_t src[G];
+    src[0] = s0 + static_cast<uint32_t>(h.w);
+#pragma unroll
+    for (int k = 1; k < G; k++) src[k] = s0 + static_cast<uint32_t>(__ldg(d + 3 + k));
+    uint32_t pend_b = 0;
+    for (int jb = 0; jb < nw4; jb += 32) {
+        const int j = jb + lane;
+        uint32_t ev = 0, od = 0;
+        if (j < nw4) {
+#pragma unroll
+            for (int k = 0; k < G; k += 2) {
+                const uint32_t x0 = lds32(src[k] + 4u * j);
+                const uint32_t x1 = lds32(src[k + 1] + 4u * j);
+                ev = ev + __byte_perm(x0, 0u, 0x4240) + __byte_perm(x1, 0u, 0x4240);  // samples 0,2
+                od = od + __byte_perm(x0, 0u, 0x4341) + __byte_perm(x1, 0u, 0x4341);  // samples 1,3
+            }
+        }
+        const uint32_t A = __byte_perm(ev, od, 0x5410);   // [R0, R1]
+        const uint32_t B = __byte_perm(ev, od, 0x7632);   // [R2, R3]
+        const uint32_t C = __byte_perm(od, ev, 0x7610);   // [R1, R2]
+        const uint32_t next_a = __shfl_down_sync(0xffffffffu, A, 1);
+        const uint32_t first_a = __shfl_sync(0xffffffffu, A, 0);
+        if (j < nw4) {
+            sts64(dst0 + 8u * j, A, B);
+            sts32(dst1 + 8u * j, C);
+            if (lane < 31) sts32(dst1 + 8u * j + 4u, __byte_perm(B, next_a, 0x5432));  // [R3, R4]
+        }
+        if (lane == 31 && jb > 0) sts32(dst1 + 8u * (jb - 1) + 4u, __byte_perm(pend_b, first_a, 0x5432));
+        pend_b = B;
+    }
+    if (lane == 31 && nw4 > 0 && (nw4 & 31) == 0) sts32(dst1 + 8u * (nw4 - 1) + 4u, __byte_perm(pend_b, 0u, 0x5432));
+}
+
+template <int G, int NW, int DPW, int WARPS, int MAXIT>
+__global__ void __launch_bounds__(WARPS * 32) k_dedisp_fact(const FactArgs a) {
+    constexpr int BD = WARPS * DPW;
+    constexpr int T = 64 * NW;
+    constexpr int NT = WARPS * 32;
+    constexpr int DI = (3 + G + 3) / 4 * 4;
+    static_assert(BD % 4 == 0, "BD must be a multiple of 4");
+    extern __shared__ __align__(16) uint8_t smem[];
+
+    const int Lw = a.Lw, CC = a.CC;
+    const int chunks = Lw >> 2;
+    const int gps = CC / G;
+    const int slot_bytes = 16 * Lw;
+    uint8_t* s_raw = smem + 4 * Lw;
+    int32_t* s_goff = reinterpret_cast<int32_t*>(smem + 4 * Lw + CC * slot_bytes + a.pat_bytes);  // [2][gps][BD]
+    const uint32_t s0 = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+
+    const int blk = blockIdx.y, sb = blockIdx.z;
+    const int t0 = blockIdx.x * T;
+    const int i0 = blk * BD;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t limit = a.n_valid;  // valid bytes per input row
+    const int16_t* sbm = a.sb_map + (int64_t)sb * a.n_chan;
+    const int32_t* base_blk = a.base + (int64_t)blk * a.n_chan;
+    const int32_t* goff_blk = a.goff + (int64_t)blk * a.n_groups * BD;
+    const int32_t* pd_blk = a.pd_idx + (int64_t)blk * a.n_stages * 2;
+
+    for (int i = threadIdx.x; i < Lw; i += NT) reinterpret_cast<uint32_t*>(smem)[i] = 0u;  // zero row
+
+    uint4 pv[MAXIT];
+    uint32_t pn[MAXIT];
+    int4 po = make_int4(0, 0, 0, 0);
+
+    auto stage_load = [&](int s) {
+        const int c0 = s * CC;
+        const int ncc = min(CC, a.n_chan - c0);
+        const int ngs = (ncc + G - 1) / G;
+        const int items = ncc * chunks;
+#pragma unroll
+        for (int u = 0; u < MAXIT; u++) {
+            const int it = threadIdx.x + u * NT;
+            if (it < items) {
+                const int cc = it / chunks;
+                const int m = it - cc * chunks;
+                const int c = c0 + cc;
+                const uint8_t* row = a.in + ((int64_t)sbm[c] * a.n_chan + c) * a.pitch_bytes;
+                const int64_t b0 = (int64_t)(t0 + base_blk[c]) + 16 * (int64_t)m;
+                if (b0 + 20 <= limit) {
+                    pv[u] = __ldg(reinterpret_cast<const uint4*>(row + b0));
+                    pn[u] = __ldg(reinterpret_cast<const uint32_t*>(row + b0 + 16));
+                } else {
+                    uint32_t g[5];
+#pragma unroll
+                    for (int k = 0; k < 5; k++) {
+                        uint32_t w = 0;
+#pragma unroll
+                        for (int b = 0; b < 4; b++) {
+                            const int64_t p = b0 + 4 * k + b;
+                            w |= ((p < limit) ? (uint32_t)row[p] : 0u) << (8 * b);
+                        }
+                        g[k] = w;
+                    }
+                    pv[u] = make_uint4(g[0], g[1], g[2], g[3]);
+                    pn[u] = g[4];
+                }
+            }
+        }
+        if (threadIdx.x < ngs * (BD / 4))
+            po = __ldg(reinterpret_cast<const int4*>(goff_blk + (int64_t)(s * gps) * BD) + threadIdx.x);
+    };
+
+    auto stage_store = [&](int s, int buf) {
+        const int c0 = s * CC;
+        const int ncc = min(CC, a.n_chan - c0);
+        const int ngs = (ncc + G - 1) / G;
+        const int items = ncc * chunks;
+#pragma unroll
+        for (int u = 0; u < MAXIT; u++) {
+            const int it = threadIdx.x + u * NT;
+            if (it < items) {
+                const int cc = it / chunks;
+                const int m = it - cc * chunks;
+                uint8_t* dst = s_raw + cc * slot_bytes + 16 * m;
+                const uint32_t g0 = pv[u].x, g1 = pv[u].y, g2 = pv[u].z, g3 = pv[u].w, g4 = pn[u];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    uint4 o;
+                    o.x = __funnelshift_r(g0, g1, 8 * q);
+                    o.y = __funnelshift_r(g1, g2, 8 * q);
+                    o.z = __funnelshift_r(g2, g3, 8 * q);
+                    o.w = __funnelshift_r(g3, g4, 8 * q);
+                    *reinterpret_cast<uint4*>(dst + q * Lw * 4) = o;
+                }
+            }
+        }
+        if (threadIdx.x < ngs * (BD / 4)) reinterpret_cast<int4*>(s_goff + buf * gps * BD)[threadIdx.x] = po;
+    };
+
+    uint32_t acc_a[DPW][NW], acc_b[DPW][NW];
+#pragma unroll
+    for (int j = 0; j < DPW; j++)
+#pragma unroll
+        for (int k = 0; k < NW; k++) {
+            acc_a[j][k] = 0u;
+            acc_b[j][k] = 0u;
+        }
+
+    const uint32_t s_lane = s0 + 4u * lane;
+    stage_load(0);
+    stage_store(0, 0);
+    __syncthreads();
+
+    for (int s = 0; s < a.n_stages; s++) {
+        const int buf = s & 1;
+        const bool next = s + 1 < a.n_stages;
+        const int ngs = (min(CC, a.n_chan - s * CC) + G - 1) / G;
+        if (next) stage_load(s + 1);  // in flight during the build
+        const int first = pd_blk[2 * s], n_desc = pd_blk[2 * s + 1];
+        for (int d = warp; d < n_desc; d += WARPS) build_row<G>(a.pdesc + (int64_t)(first + d) * DI, s0, lane);
+        __syncthreads();  // pattern rows complete; raw rows free
+        if (next) stage_store(s + 1, buf ^ 1);
+        const int32_t* go = s_goff + buf * gps * BD + warp * DPW;
+        int gl = 0;
+#pragma unroll 1
+        for (; gl + 1 < ngs; gl += 2) {
+            int32_t o0[DPW], o1[DPW];
+            load_offsets<DPW>(go + gl * BD, o0);
+            load_offsets<DPW>(go + (gl + 1) * BD, o1);
+            uint32_t x[2][DPW][NW];
+#pragma unroll
+            for (int j = 0; j < DPW; j++)
+#pragma unroll
+                for (int k = 0; k < NW; k++) {
+                    x[0][j][k] = lds32(s_lane + static_cast<uint32_t>(o0[j]) + 128u * k);
+                    x[1][j][k] = lds32(s_lane + static_cast<uint32_t>(o1[j]) + 128u * k);
+                }
+#pragma unroll
+            for (int j = 0; j < DPW; j++)
+#pragma unroll
+                for (int k = 0; k < NW; k++) {
+                    acc_a[j][k] = acc_a[j][k] + x[0][j][k] + x[1][j][k];
+                    acc_b[j][k] = acc_b[j][k] + (x[0][j][k] >> 16) + (x[1][j][k] >> 16);
+                }
+        }
+        if (gl < ngs) {
+            int32_t o0[DPW];
+            load_offsets<DPW>(go + gl * BD, o0);
+#pragma unroll
+            for (int j = 0; j < DPW; j++)
+#pragma unroll
+                for (int k = 0; k < NW; k++) {
+                    const uint32_t x0 = lds32(s_lane + static_cast<uint32_t>(o0[j]) + 128u * k);
+                    acc_a[j][k] += x0;
+                    acc_b[j][k] += x0 >> 16;
+                }
+        }
+        __syncthreads();  // pattern rows consumed; next stage's rows and offsets visible
+    }
+
+    // Epilogue: two samples per word; write the series and fold the moments.
+#pragma unroll
+    for (int j = 0; j < DPW; j++) {
+        const int i = i0 + warp * DPW + j;
+        if (i >= a.n_dm) continue;  // warp-uniform
+        const int64_t q = (int64_t)sb * a.n_dm + i;
+        int32_t* row = a.series + q * a.n_out;
+        long long s1 = 0;
+        unsigned long long s2 = 0;
+#pragma unroll
+        for (int k = 0; k < NW; k++) {
+            const uint32_t hi = acc_b[j][k];
+            const uint32_t lo = acc_a[j][k] - (hi << 16);
+            const int t = t0 + 2 * (lane + 32 * k);
+            if (t < a.n_out) {
+                row[t] = static_cast<int32_t>(lo);
+                s1 += lo;
+                s2 += static_cast<unsigned long long>(lo) * lo;
+            }
+            if (t + 1 < a.n_out) {
+                row[t + 1] = static_cast<int32_t>(hi);
+                s1 += hi;
+                s2 += static_cast<unsigned long long>(hi) * hi;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0) {
+            atomicAdd(a.stat + 2 * q, static_cast<unsigned long long>(s1));
+            atomicAdd(a.stat + 2 * q + 1, s2);
+        }
+    }
+}
+
+using FactFn = void (*)(const FactArgs);
+
+struct FEntry {
+    FactVariant v;
+    FactFn fn;
+};
+
+#define FDD_F(G, NW, DPW, WARPS, MAXIT) {{G, NW, DPW, WARPS, MAXIT}, k_dedisp_fact<G, NW, DPW, WARPS, MAXIT>}
+const FEntry kFEntries[] = {
+    FDD_F(8, 4, 4, 16, 4),  // G 8, BD 64, T 256, 512 threads
+    FDD_F(8, 4, 2, 16, 4),  // G 8, BD 32, T 256
+    FDD_F(4, 4, 4, 16, 4),  // G 4, BD 64, T 256
+    FDD_F(8, 2, 4, 16, 4),  // G 8, BD 64, T 128
+    FDD_F(8, 8, 2, 16, 4),  // G 8, BD 32, T 512
+    FDD_F(4, 8, 2, 16, 4),  // G 4, BD 32, T 512
+};
+#undef FDD_F
+
+}  // namespace
+
+int num_fact_variants() { return static_cast<int>(sizeof(kFEntries) / sizeof(kFEntries[0])); }
+
+const FactVariant& fact_variant(int idx) { return kFEntries[idx].v; }
+
+bool fact_cc_ok(const FactVariant& v, int Lw, int CC) {
+    if (CC < v.G || CC % v.G != 0 || CC > 256) return false;
+    if (static_cast<int64_t>(CC) * (Lw / 4) > static_cast<int64_t>(v.MAXIT) * v.threads()) return false;
+    if ((CC / v.G) * (v.bd() / 4) > v.threads()) return false;
+    return true;
+}
+
+cudaError_t launch_dedisp_fact(int variant, const FactArgs& a, size_t smem, cudaStream_t s) {
+    const FEntry& e = kFEntries[variant];
+    cudaError_t err = cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (err != cudaSuccess) return err;
+    const int T = e.v.tile(), BD = e.v.bd();
+    dim3 grid((a.n_out + T - 1) / T, (a.n_dm + BD - 1) / BD, a.n_sb);
+    e.fn<<<grid, e.v.threads(), smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace fdd

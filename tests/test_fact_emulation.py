@@ -1,0 +1,170 @@
+"""CPU checks of the pattern-factored dedispersion kernel's shared-memory
+addressing and arithmetic: the library's own host tables
+(fdd_fact_tables_host) drive a numpy emulation of every block of the kernel
+-- raw staging in 4 byte-shifted copies, pattern-row builds (even/odd byte
+lanes, PRMT packing, the shifted copy with the neighbouring lane's sample),
+and the per-trial accumulation -- which must stay inside each shared-memory
+region and reproduce the oracle's brute-force series exactly."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+T_SAMP = synth.ARTS_T_SAMP_S
+
+
+def prmt(a, b, sel):
+    """Byte permute of two uint32 arrays (selector nibbles pick bytes of b:a)."""
+    a = np.asarray(a, np.uint64)
+    b = np.asarray(b, np.uint64)
+    src = (b << np.uint64(32)) | a
+    out = np.zeros_like(a)
+    for n in range(4):
+        k = (sel >> (4 * n)) & 7
+        out |= ((src >> np.uint64(8 * k)) & np.uint64(0xFF)) << np.uint64(8 * n)
+    return out.astype(np.uint32)
+
+
+class Smem:
+    def __init__(self, n):
+        self.m = np.full(n, 0xCD, np.uint8)
+
+    def rd32(self, addr, lo, hi):
+        addr = np.asarray(addr, np.int64)
+        assert (addr >= lo).all() and (addr + 4 <= hi).all(), "read outside [%d, %d)" % (lo, hi)
+        assert (addr % 4 == 0).all()
+        b = self.m[addr[..., None] + np.arange(4)]
+        return (b.astype(np.uint32) << (8 * np.arange(4, dtype=np.uint32))).sum(-1).astype(np.uint32)
+
+    def wr32(self, addr, val, lo, hi):
+        addr = np.asarray(addr, np.int64)
+        assert (addr >= lo).all() and (addr + 4 <= hi).all(), "write outside [%d, %d)" % (lo, hi)
+        assert (addr % 4 == 0).all()
+        val = np.asarray(val, np.uint32)
+        for k in range(4):
+            self.m[addr + k] = ((val >> np.uint32(8 * k)) & np.uint32(0xFF)).astype(np.uint8)
+
+
+def emulate(x, n_valid, sb_map, tb, v, CC, n_dm, n_out):
+    G, BD, T = v["group"], v["dm_per_block"], v["tile"]
+    NW = T // 64
+    Lw, pat_bytes, smem_bytes = tb["Lw"], tb["pat_bytes"], tb["smem_bytes"]
+    n_chan = x.shape[1]
+    gps = CC // G
+    zero_hi = 4 * Lw
+    raw_lo, raw_hi = zero_hi, zero_hi + CC * 16 * Lw
+    pat_lo, pat_hi = raw_hi, raw_hi + pat_bytes
+    goff_lo = pat_hi
+    assert goff_lo + 2 * gps * BD * 4 == smem_bytes
+    n_sb = sb_map.shape[0]
+    S = np.zeros((n_sb, n_dm, n_out), np.int64)
+    lanes = np.arange(32)
+    for sb in range(n_sb):
+        for blk in range(tb["n_blk"]):
+            for tile in range((n_out + T - 1) // T):
+                t0 = tile * T
+                sm = Smem(smem_bytes)
+                sm.m[:zero_hi] = 0
+                acc = np.zeros((BD, T), np.int64)
+                goff_buf = {}
+                for s in range(tb["n_stages"]):
+                    c0 = s * CC
+                    ncc = min(CC, n_chan - c0)
+                    ngs = (ncc + G - 1) // G
+                    for cc in range(ncc):          # raw staging
+                        c = c0 + cc
+                        start = t0 + tb["base"][blk, c]
+                        idx = start + np.arange(4 * Lw + 4)
+                        row = x[sb_map[sb, c], c]
+                        byts = np.where(idx < n_valid, row[np.minimum(idx, row.size - 1)], 0).astype(np.uint32)
+                        for q in range(4):
+                            w = byts[q:q + 4 * Lw].reshape(Lw, 4)
+                            words = (w << (8 * np.arange(4, dtype=np.uint32))).sum(-1)
+                            sm.wr32(raw_lo + cc * 16 * Lw + q * 4 * Lw + 4 * np.arange(Lw), words, raw_lo, raw_hi)
+                    goff_buf[s % 2] = tb["goff"][blk, s * gps:s * gps + ngs]
+                    first, n_desc = tb["pd_idx"][blk, s]
+                    sm.m[pat_lo:pat_hi] = 0xAB       # stale pattern bytes from an earlier stage
+                    for d in tb["pdesc"][first:first + n_desc]:   # pattern-row builds
+                        dst0, dst1, nw4 = int(d[0]), int(d[1]), int(d[2])
+                        src = d[3:3 + G].astype(np.int64)
+                        j = np.arange(nw4)
+                        ev = np.zeros(nw4, np.uint32)
+                        od = np.zeros(nw4, np.uint32)
+                        for k in range(G):
+                            lo = 0 if src[k] < zero_hi else raw_lo
+                            hi = zero_hi if src[k] < zero_hi else raw_hi
+                            xw = sm.rd32(src[k] + 4 * j, lo, hi)
+                            ev = (ev + prmt(xw, 0, 0x4240)).astype(np.uint32)
+                            od = (od + prmt(xw, 0, 0x4341)).astype(np.uint32)
+                        A = prmt(ev, od, 0x5410)
+                        B = prmt(ev, od, 0x7632)
+                        C = prmt(od, ev, 0x7610)
+                        A_next = np.append(A[1:], np.uint32(0))
+                        D = prmt(B, A_next, 0x5432)
+                        sm.wr32(dst0 + 8 * j, A, pat_lo, pat_hi)
+                        sm.wr32(dst0 + 8 * j + 4, B, pat_lo, pat_hi)
+                        sm.wr32(dst1 + 8 * j, C, pat_lo, pat_hi)
+                        sm.wr32(dst1 + 8 * j + 4, D, pat_lo, pat_hi)
+                    go = goff_buf[s % 2]
+                    for gl in range(ngs):             # accumulation
+                        for jj in range(BD):
+                            o = int(go[gl, jj])
+                            addr = o + 4 * lanes[None, :] + 128 * np.arange(NW)[:, None]
+                            wv = sm.rd32(addr, pat_lo, pat_hi)
+                            lo16 = (wv & 0xFFFF).astype(np.int64)
+                            hi16 = (wv >> 16).astype(np.int64)
+                            tt = 2 * (lanes[None, :] + 32 * np.arange(NW)[:, None])
+                            acc[jj, tt.ravel()] += lo16.ravel()
+                            acc[jj, tt.ravel() + 1] += hi16.ravel()
+                for jj in range(BD):
+                    i = blk * BD + jj
+                    if i < n_dm:
+                        nt = min(T, n_out - t0)
+                        S[sb, i, t0:t0 + nt] = acc[jj, :nt]
+    return S
+
+
+def fact_variants():
+    try:
+        import paper_2205_12362_b300 as fdd
+        return [v for v in fdd.variants() if v["group"] > 0]
+    except Exception:
+        return []
+
+
+@pytest.mark.parametrize("v", fact_variants(), ids=lambda v: "v%d_G%d_bd%d_t%d" % (
+    v["index"], v["group"], v["dm_per_block"], v["tile"]))
+@pytest.mark.parametrize("CC", [8, 16])
+def test_factored_kernel_emulation(v, CC):
+    import paper_2205_12362_b300 as fdd
+    if CC % v["group"]:
+        pytest.skip("stage size not a multiple of G")
+    rng = np.random.default_rng(v["index"] + CC)
+    n_tab, n_chan, n_sb, n_out = 2, 37, 2, 300
+    f = synth.channel_freqs(n_chan)
+    n_dm = v["dm_per_block"] + 5
+    ranges = [dict(dm0=3.0, ddm=2.5, n_dm=n_dm, downsamp=1, widths=[1])]
+    d = oracle.delays(f, T_SAMP, 3.0, 2.5, n_dm)
+    n_in = n_out + int(d.max()) + 3
+    x = rng.integers(0, 256, size=(n_tab, n_chan, synth.padded_pitch(n_in)), dtype=np.int64).astype(np.uint8)
+    sb = rng.integers(0, n_tab, size=(n_sb, n_chan)).astype(np.int16)
+    tb = fdd.fact_tables_host(n_tab, n_chan, n_sb, f, T_SAMP, ranges, sb, 0, v["index"], CC)
+    assert tb["Lw"] > 0
+    assert (tb["delays"] == d).all()
+    S = emulate(x, n_in, sb, tb, v, CC, n_dm, n_out)
+    want = oracle.dedisperse(oracle.downsample(x, 1, n_in=n_in), sb, d, n_out)
+    assert (S == want).all()
+
+
+def test_factored_tables_share_patterns():
+    """On the ARTS band the factored tables need far fewer pattern rows than
+    trials x groups (the source of the kernel's saving)."""
+    import paper_2205_12362_b300 as fdd
+    v = [v for v in fact_variants() if v["group"] == 8 and v["dm_per_block"] == 64][0]
+    f = synth.channel_freqs(1536)
+    ranges = [dict(dm0=0.0, ddm=0.2, n_dm=256, downsamp=1, widths=[1])]
+    tb = fdd.fact_tables_host(1, 1536, 1, f, T_SAMP, ranges, np.zeros((1, 1536)), 0, v["index"], 32)
+    rows = tb["n_desc"]
+    trial_group_pairs = tb["n_blk"] * tb["n_groups"] * v["dm_per_block"]
+    assert rows < trial_group_pairs / 4
