@@ -258,6 +258,12 @@ def run_fdd(args):
         count = torch.zeros(1, dtype=torch.int64, device=dev)
         if not args.no_autotune:
             plan.autotune(tabs, n_in, w["n_out"], reps=3, workspace=ws, stream=stream)
+        if args.variant is not None:
+            for r in range(len(w["ranges"])):
+                try:
+                    plan.set_config(r, args.variant, args.cc)
+                except fdd.FddError:
+                    pass  # variant for the other sample width
         if mode == "per_sb":
             # the plain per-beam path: one single-SB plan per SB, searched one after another
             cfgs = [plan.get_config(r) for r in range(len(w["ranges"]))]
@@ -569,6 +575,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--variant", type=int, default=None, help="force this dedispersion kernel variant")
+    ap.add_argument("--cc", type=int, default=0, help="with --variant: channels per stage (0 = largest fitting)")
     ap.add_argument("--serve", action="store_true", help="serving measurement instead of the step benchmark")
     ap.add_argument("--beams", default="1,2,3,4,8", help="--serve: compound-beam counts to run")
     ap.add_argument("--seconds", type=float, default=20.0, help="--serve: stream length per run")

@@ -71,7 +71,8 @@ def test_serving_results_match_standalone(fdd, max_slots):
     n_in = info["window_len"]
     assert max_slots == 0 or info["n_slots"] == max_slots
     results = {}
-    # interleave beams; poll between pushes; retry on backpressure
+    # interleave beams; poll only every other round so that windows of several
+    # beams wait together and go out in shared batches; retry on backpressure
     for k in range(n_chunks):
         for b, x in enumerate(streams):
             while True:
@@ -80,6 +81,7 @@ def test_serving_results_match_standalone(fdd, max_slots):
                     break
                 assert code == fdd.FDD_ERR_BUSY
                 srv.drain()
+        if k % 2:
             srv.poll()
     srv.drain()
     for r, c in srv.results():
