@@ -20,6 +20,8 @@
 //         {dst copy 0, dst copy 1, units of 4 samples, src offset per channel}
 //   pd_idx [n_blk][n_stages][2]  (first descriptor, count)
 // and the raw row length Lw and the pattern region size of the layout.
+// Shared memory: [zero row | CC raw slots | pattern rows | 2 x stage offsets |
+// stage descriptors].
 #include <algorithm>
 #include <map>
 #include <vector>
@@ -134,6 +136,7 @@ FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactV
                 }
             }
             const int n_desc = static_cast<int>(ft.pdesc.size() / ft.desc_ints) - first_desc;
+            ft.max_desc = std::max(ft.max_desc, n_desc);
             ft.pd_idx[(static_cast<size_t>(b) * n_stages + s) * 2] = first_desc;
             ft.pd_idx[(static_cast<size_t>(b) * n_stages + s) * 2 + 1] = n_desc;
             pat_region = std::max(pat_region, cursor);
@@ -166,7 +169,8 @@ FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactV
         }
     }
     for (int32_t& g : ft.goff) g += static_cast<int32_t>(pat_base);
-    ft.smem_bytes = static_cast<size_t>(pat_base + ft.pat_bytes) + 2ull * gps * BD * 4;
+    ft.smem_bytes = static_cast<size_t>(pat_base + ft.pat_bytes) + 2ull * gps * BD * 4 +
+                    static_cast<size_t>(ft.max_desc) * ft.desc_ints * 4;
     return ft;
 }
 

@@ -83,7 +83,7 @@ struct FactArgs {
 
 int num_fact_variants();
 const FactVariant& fact_variant(int idx);
-bool fact_cc_ok(const FactVariant& v, int Lw, int CC);
+bool fact_cc_ok(const FactVariant& v, int Lw, int CC, int max_desc);
 cudaError_t launch_dedisp_fact(int variant, const FactArgs& a, size_t smem, cudaStream_t s);
 
 // ---------------------------------------------------------------------------

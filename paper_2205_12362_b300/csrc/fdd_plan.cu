@@ -213,7 +213,7 @@ int configure_fact(fdd_plan* p, RangeState& r, int fv, int CC) {
         if (CC != 0 && cc != CC) continue;
         if (cc % v.G) continue;
         FactTables ft = build_fact_tables(p, r, v, cc);
-        if (ft.Lw < 0 || !fdd::fact_cc_ok(v, ft.Lw, cc) || ft.smem_bytes > kSmemBudget) continue;
+        if (ft.Lw < 0 || !fdd::fact_cc_ok(v, ft.Lw, cc, ft.max_desc) || ft.smem_bytes > kSmemBudget) continue;
         best = std::move(ft);
         best_cc = cc;
         break;

@@ -101,6 +101,7 @@ int pick_cc(const DedispVariant& v, int Lw);
 struct FactTables {
     std::vector<int32_t> base, goff, pdesc, pd_idx;
     int32_t Lw = 0, pat_bytes = 0, n_groups = 0, n_stages = 0, desc_ints = 0;
+    int32_t max_desc = 0;  // most pattern rows of one (block, stage)
     size_t smem_bytes = 0;
 };
 // Tables of the pattern-factored kernel for range r, variant v and CC

@@ -5,15 +5,17 @@
 // Block = BD trials x T = 64*NW output samples of one SB.  Per channel stage:
 //   1. staging (as k_dedisp): the SB's TAB row of every channel, 4 byte-shifted
 //      copies, software-pipelined through registers;
-//   2. build: each warp takes pattern rows of the stage's channel groups; a
-//      lane forms 4 consecutive samples of R_p(tau) = sum_k X_k(tau + rel_k)
-//      from one aligned LDS.32 per channel (bytes split into even/odd 16-bit
-//      lanes with PRMT) and stores them as two copies of 16-bit pairs, the
+//   2. build: each warp takes pattern rows of the stage's channel groups
+//      (descriptors staged in shared memory with the raw rows); a lane forms
+//      4 consecutive samples of R_p(tau) = sum_k X_k(tau + rel_k) from one
+//      aligned LDS.32 per channel (odd bytes split off with one PRMT, even
+//      bytes recovered by subtraction) and stores them as two copies of
+//      16-bit pairs, the
 //      second shifted by one sample (the neighbouring lane's first sample
 //      comes by shuffle), so every trial's offset is an aligned LDS.32;
 //   3. accumulate: each trial adds, per group, one word of two 16-bit
-//      partials: acc_a += w, acc_b += w >> 16 (exact; low halves recovered as
-//      acc_a - (acc_b << 16)), two groups per IADD3.
+//      partials into 16-bit lanes (two groups per IADD3), folded into 32-bit
+//      totals before a lane holds more than 256 channels.
 // The next stage's global loads are in flight during the build, and its
 // staging stores overlap the accumulation (which only reads pattern rows).
 #include "fdd_internal.cuh"
@@ -54,30 +56,36 @@ __device__ __forceinline__ void load_offsets(const int32_t* p, int32_t (&o)[N]) 
     }
 }
 
-// Build one pattern row (whole warp).  d: descriptor {dst0, dst1, nw4,
-// src[G]} in global memory; s0: shared window address of dynamic smem.
+// Build one pattern row (whole warp).  d: shared-window address of the
+// descriptor {dst0, dst1, nw4, src[G]}; s0: shared window of dynamic smem.
+// Per lane and 4-sample unit: acc_a = sum of the G raw words (bytes overlap),
+// acc_b = sum of bytes 1,3 in 16-bit lanes (one PRMT per word); samples 0,2
+// are acc_a - (acc_b << 8) (lanes hold <= 257 * 255).
 template <int G>
-__device__ __forceinline__ void build_row(const int32_t* __restrict__ d, uint32_t s0, int lane) {
-    const int4 h = __ldg(reinterpret_cast<const int4*>(d));
-    const uint32_t dst0 = s0 + static_cast<uint32_t>(h.x), dst1 = s0 + static_cast<uint32_t>(h.y);
-    const int nw4 = h.z;
-    uint32_t src[G];
-    src[0] = s0 + static_cast<uint32_t>(h.w);
+__device__ __forceinline__ void build_row(uint32_t d, uint32_t s0, int lane) {
+    uint32_t dst0, dst1, nw4u, src[G];
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(dst0), "=r"(dst1), "=r"(nw4u), "=r"(src[0]) : "r"(d));
 #pragma unroll
-    for (int k = 1; k < G; k++) src[k] = s0 + static_cast<uint32_t>(__ldg(d + 3 + k));
+    for (int k = 1; k < G; k++) src[k] = s0 + lds32(d + 4u * (3 + k));
+    src[0] += s0;
+    dst0 += s0;
+    dst1 += s0;
+    const int nw4 = static_cast<int>(nw4u);
     uint32_t pend_b = 0;
     for (int jb = 0; jb < nw4; jb += 32) {
         const int j = jb + lane;
-        uint32_t ev = 0, od = 0;
+        uint32_t acc_a = 0, acc_b = 0;
         if (j < nw4) {
 #pragma unroll
             for (int k = 0; k < G; k += 2) {
                 const uint32_t x0 = lds32(src[k] + 4u * j);
                 const uint32_t x1 = lds32(src[k + 1] + 4u * j);
-                ev = ev + __byte_perm(x0, 0u, 0x4240) + __byte_perm(x1, 0u, 0x4240);  // samples 0,2
-                od = od + __byte_perm(x0, 0u, 0x4341) + __byte_perm(x1, 0u, 0x4341);  // samples 1,3
+                acc_a = acc_a + x0 + x1;
+                acc_b = acc_b + __byte_perm(x0, 0u, 0x4341) + __byte_perm(x1, 0u, 0x4341);
             }
         }
+        const uint32_t od = acc_b;                  // [R1, R3]
+        const uint32_t ev = acc_a - (acc_b << 8);   // [R0, R2]
         const uint32_t A = __byte_perm(ev, od, 0x5410);   // [R0, R1]
         const uint32_t B = __byte_perm(ev, od, 0x7632);   // [R2, R3]
         const uint32_t C = __byte_perm(od, ev, 0x7610);   // [R1, R2]
@@ -109,7 +117,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_dedisp_fact(const FactArgs a) {
     const int slot_bytes = 16 * Lw;
     uint8_t* s_raw = smem + 4 * Lw;
     int32_t* s_goff = reinterpret_cast<int32_t*>(smem + 4 * Lw + CC * slot_bytes + a.pat_bytes);  // [2][gps][BD]
+    int32_t* s_desc = s_goff + 2 * gps * BD;  // [max_desc][DI] of the stage being built
     const uint32_t s0 = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    const uint32_t s_desc32 = static_cast<uint32_t>(__cvta_generic_to_shared(s_desc));
 
     const int blk = blockIdx.y, sb = blockIdx.z;
     const int t0 = blockIdx.x * T;
@@ -126,6 +136,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_dedisp_fact(const FactArgs a) {
     uint4 pv[MAXIT];
     uint32_t pn[MAXIT];
     int4 po = make_int4(0, 0, 0, 0);
+    int4 pdv = make_int4(0, 0, 0, 0);
+    int n_desc_next = 0;
 
     auto stage_load = [&](int s) {
         const int c0 = s * CC;
@@ -163,6 +175,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_dedisp_fact(const FactArgs a) {
         }
         if (threadIdx.x < ngs * (BD / 4))
             po = __ldg(reinterpret_cast<const int4*>(goff_blk + (int64_t)(s * gps) * BD) + threadIdx.x);
+        const int first = pd_blk[2 * s];
+        n_desc_next = pd_blk[2 * s + 1];
+        if (threadIdx.x < n_desc_next * (DI / 4))
+            pdv = __ldg(reinterpret_cast<const int4*>(a.pdesc + (int64_t)first * DI) + threadIdx.x);
     };
 
     auto stage_store = [&](int s, int buf) {
@@ -190,31 +206,53 @@ __global__ void __launch_bounds__(WARPS * 32) k_dedisp_fact(const FactArgs a) {
             }
         }
         if (threadIdx.x < ngs * (BD / 4)) reinterpret_cast<int4*>(s_goff + buf * gps * BD)[threadIdx.x] = po;
+        if (threadIdx.x < n_desc_next * (DI / 4)) reinterpret_cast<int4*>(s_desc)[threadIdx.x] = pdv;
     };
 
-    uint32_t acc_a[DPW][NW], acc_b[DPW][NW];
+    // Per output word: acc = two 16-bit partial sums (samples 2m, 2m+1); a
+    // lane gains <= G*255 per group, so lanes are folded into the 32-bit
+    // totals before they hold more than 256 channels.
+    uint32_t acc[DPW][NW], tot_lo[DPW][NW], tot_hi[DPW][NW];
 #pragma unroll
     for (int j = 0; j < DPW; j++)
 #pragma unroll
         for (int k = 0; k < NW; k++) {
-            acc_a[j][k] = 0u;
-            acc_b[j][k] = 0u;
+            acc[j][k] = 0u;
+            tot_lo[j][k] = 0u;
+            tot_hi[j][k] = 0u;
         }
+    auto fold = [&]() {
+#pragma unroll
+        for (int j = 0; j < DPW; j++)
+#pragma unroll
+            for (int k = 0; k < NW; k++) {
+                tot_lo[j][k] += acc[j][k] & 0xFFFFu;
+                tot_hi[j][k] += acc[j][k] >> 16;
+                acc[j][k] = 0u;
+            }
+    };
 
     const uint32_t s_lane = s0 + 4u * lane;
     stage_load(0);
     stage_store(0, 0);
     __syncthreads();
 
+    int since_fold = 0;  // channels held in the 16-bit lanes
     for (int s = 0; s < a.n_stages; s++) {
         const int buf = s & 1;
         const bool next = s + 1 < a.n_stages;
-        const int ngs = (min(CC, a.n_chan - s * CC) + G - 1) / G;
+        const int ncc = min(CC, a.n_chan - s * CC);
+        const int ngs = (ncc + G - 1) / G;
+        const int n_desc = n_desc_next;
         if (next) stage_load(s + 1);  // in flight during the build
-        const int first = pd_blk[2 * s], n_desc = pd_blk[2 * s + 1];
-        for (int d = warp; d < n_desc; d += WARPS) build_row<G>(a.pdesc + (int64_t)(first + d) * DI, s0, lane);
-        __syncthreads();  // pattern rows complete; raw rows free
+        for (int d = warp; d < n_desc; d += WARPS) build_row<G>(s_desc32 + 4u * DI * d, s0, lane);
+        __syncthreads();  // pattern rows complete; raw rows and descriptors free
         if (next) stage_store(s + 1, buf ^ 1);
+        if (since_fold + ncc > 256) {
+            fold();
+            since_fold = 0;
+        }
+        since_fold += ncc;
         const int32_t* go = s_goff + buf * gps * BD + warp * DPW;
         int gl = 0;
 #pragma unroll 1
@@ -233,10 +271,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_dedisp_fact(const FactArgs a) {
 #pragma unroll
             for (int j = 0; j < DPW; j++)
 #pragma unroll
-                for (int k = 0; k < NW; k++) {
-                    acc_a[j][k] = acc_a[j][k] + x[0][j][k] + x[1][j][k];
-                    acc_b[j][k] = acc_b[j][k] + (x[0][j][k] >> 16) + (x[1][j][k] >> 16);
-                }
+                for (int k = 0; k < NW; k++) acc[j][k] = acc[j][k] + x[0][j][k] + x[1][j][k];
         }
         if (gl < ngs) {
             int32_t o0[DPW];
@@ -244,14 +279,11 @@ __global__ void __launch_bounds__(WARPS * 32) k_dedisp_fact(const FactArgs a) {
 #pragma unroll
             for (int j = 0; j < DPW; j++)
 #pragma unroll
-                for (int k = 0; k < NW; k++) {
-                    const uint32_t x0 = lds32(s_lane + static_cast<uint32_t>(o0[j]) + 128u * k);
-                    acc_a[j][k] += x0;
-                    acc_b[j][k] += x0 >> 16;
-                }
+                for (int k = 0; k < NW; k++) acc[j][k] += lds32(s_lane + static_cast<uint32_t>(o0[j]) + 128u * k);
         }
-        __syncthreads();  // pattern rows consumed; next stage's rows and offsets visible
+        __syncthreads();  // pattern rows consumed; next stage's rows, offsets, descriptors visible
     }
+    fold();
 
     // Epilogue: two samples per word; write the series and fold the moments.
 #pragma unroll
@@ -264,8 +296,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_dedisp_fact(const FactArgs a) {
         unsigned long long s2 = 0;
 #pragma unroll
         for (int k = 0; k < NW; k++) {
-            const uint32_t hi = acc_b[j][k];
-            const uint32_t lo = acc_a[j][k] - (hi << 16);
+            const uint32_t hi = tot_hi[j][k];
+            const uint32_t lo = tot_lo[j][k];
             const int t = t0 + 2 * (lane + 32 * k);
             if (t < a.n_out) {
                 row[t] = static_cast<int32_t>(lo);
@@ -314,8 +346,9 @@ int num_fact_variants() { return static_cast<int>(sizeof(kFEntries) / sizeof(kFE
 
 const FactVariant& fact_variant(int idx) { return kFEntries[idx].v; }
 
-bool fact_cc_ok(const FactVariant& v, int Lw, int CC) {
+bool fact_cc_ok(const FactVariant& v, int Lw, int CC, int max_desc) {
     if (CC < v.G || CC % v.G != 0 || CC > 256) return false;
+    if (max_desc * (v.desc_ints() / 4) > v.threads()) return false;
     if (static_cast<int64_t>(CC) * (Lw / 4) > static_cast<int64_t>(v.MAXIT) * v.threads()) return false;
     if ((CC / v.G) * (v.bd() / 4) > v.threads()) return false;
     return true;

@@ -56,7 +56,10 @@ def emulate(x, n_valid, sb_map, tb, v, CC, n_dm, n_out):
     raw_lo, raw_hi = zero_hi, zero_hi + CC * 16 * Lw
     pat_lo, pat_hi = raw_hi, raw_hi + pat_bytes
     goff_lo = pat_hi
-    assert goff_lo + 2 * gps * BD * 4 == smem_bytes
+    desc_lo = goff_lo + 2 * gps * BD * 4
+    max_desc = int(tb["pd_idx"][..., 1].max())
+    assert desc_lo + max_desc * tb["desc_ints"] * 4 == smem_bytes
+    assert desc_lo % 16 == 0 and max_desc * (tb["desc_ints"] // 4) <= v["threads"]
     n_sb = sb_map.shape[0]
     S = np.zeros((n_sb, n_dm, n_out), np.int64)
     lanes = np.arange(32)
