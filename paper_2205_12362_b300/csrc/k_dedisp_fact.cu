@@ -56,23 +56,35 @@ __device__ __forceinline__ void load_offsets(const int32_t* p, int32_t (&o)[N]) 
     }
 }
 
-// Build one pattern row (whole warp).  d: shared-window address of the
-// descriptor {dst0, dst1, nw4, src[G]}; s0: shared window of dynamic smem.
-// Per lane and 4-sample unit: acc_a = sum of the G raw words (bytes overlap),
-// acc_b = sum of bytes 1,3 in 16-bit lanes (one PRMT per word); samples 0,2
-// are acc_a - (acc_b << 8) (lanes hold <= 257 * 255).
+// Pattern-row builds (whole warp).  A row descriptor in shared memory is
+// {dst0, dst1, nw4, src[G]}: copy-0 and copy-1 destinations, units of 4
+// samples, and the staged raw word of unit 0 for each channel.  Per lane and
+// unit: acc_a = sum of the G raw words (bytes overlap), acc_b = sum of bytes
+// 1,3 in 16-bit lanes (one PRMT per word); samples 0,2 are acc_a - (acc_b <<
+// 8) (lanes hold <= 257 * 255).  Copy 0 stores [R0,R1],[R2,R3]; copy 1 stores
+// [R1,R2],[R3,R4], R4 being the next lane's R0 (shuffle; across a 32-unit
+// step it comes from lane 0 of the next step).
 template <int G>
-__device__ __forceinline__ void build_row(uint32_t d, uint32_t s0, int lane) {
-    uint32_t dst0, dst1, nw4u, src[G];
-    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(dst0), "=r"(dst1), "=r"(nw4u), "=r"(src[0]) : "r"(d));
+struct RowState {
+    uint32_t dst0, dst1, src[G];
+    int nw4;
+    uint32_t pend_b;
+
+    __device__ __forceinline__ void load(uint32_t d, uint32_t s0) {
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(dst0), "=r"(dst1), "=r"(nw4), "=r"(src[0])
+                     : "r"(d));
 #pragma unroll
-    for (int k = 1; k < G; k++) src[k] = s0 + lds32(d + 4u * (3 + k));
-    src[0] += s0;
-    dst0 += s0;
-    dst1 += s0;
-    const int nw4 = static_cast<int>(nw4u);
-    uint32_t pend_b = 0;
-    for (int jb = 0; jb < nw4; jb += 32) {
+        for (int k = 1; k < G; k++) src[k] = s0 + lds32(d + 4u * (3 + k));
+        src[0] += s0;
+        dst0 += s0;
+        dst1 += s0;
+        pend_b = 0;
+    }
+
+    // One 32-unit step starting at unit jb (jb < nw4 or the row is done).
+    __device__ __forceinline__ void step(int jb, int lane) {
+        if (jb >= nw4) return;  // warp-uniform
         const int j = jb + lane;
         uint32_t acc_a = 0, acc_b = 0;
         if (j < nw4) {
@@ -84,11 +96,11 @@ __device__ __forceinline__ void build_row(uint32_t d, uint32_t s0, int lane) {
                 acc_b = acc_b + __byte_perm(x0, 0u, 0x4341) + __byte_perm(x1, 0u, 0x4341);
             }
         }
-        const uint32_t od = acc_b;                  // [R1, R3]
-        const uint32_t ev = acc_a - (acc_b << 8);   // [R0, R2]
-        const uint32_t A = __byte_perm(ev, od, 0x5410);   // [R0, R1]
-        const uint32_t B = __byte_perm(ev, od, 0x7632);   // [R2, R3]
-        const uint32_t C = __byte_perm(od, ev, 0x7610);   // [R1, R2]
+        const uint32_t od = acc_b;                       // [R1, R3]
+        const uint32_t ev = acc_a - (acc_b << 8);        // [R0, R2]
+        const uint32_t A = __byte_perm(ev, od, 0x5410);  // [R0, R1]
+        const uint32_t B = __byte_perm(ev, od, 0x7632);  // [R2, R3]
+        const uint32_t C = __byte_perm(od, ev, 0x7610);  // [R1, R2]
         const uint32_t next_a = __shfl_down_sync(0xffffffffu, A, 1);
         const uint32_t first_a = __shfl_sync(0xffffffffu, A, 0);
         if (j < nw4) {
@@ -99,7 +111,33 @@ __device__ __forceinline__ void build_row(uint32_t d, uint32_t s0, int lane) {
         if (lane == 31 && jb > 0) sts32(dst1 + 8u * (jb - 1) + 4u, __byte_perm(pend_b, first_a, 0x5432));
         pend_b = B;
     }
-    if (lane == 31 && nw4 > 0 && (nw4 & 31) == 0) sts32(dst1 + 8u * (nw4 - 1) + 4u, __byte_perm(pend_b, 0u, 0x5432));
+
+    __device__ __forceinline__ void finish(int lane) {
+        if (lane == 31 && nw4 > 0 && (nw4 & 31) == 0)
+            sts32(dst1 + 8u * (nw4 - 1) + 4u, __byte_perm(pend_b, 0u, 0x5432));
+    }
+};
+
+// Rows d0 and d1 (d1 == 0xffffffff: none) interleaved step by step, so a
+// lane has two independent build chains in flight.
+template <int G>
+__device__ __forceinline__ void build_rows(uint32_t d0, uint32_t d1, uint32_t s0, int lane) {
+    RowState<G> a, b;
+    a.load(d0, s0);
+    const bool two = d1 != 0xffffffffu;
+    if (two) {
+        b.load(d1, s0);
+    } else {
+        b.nw4 = 0;
+        b.pend_b = 0;
+    }
+    const int n = max(a.nw4, b.nw4);
+    for (int jb = 0; jb < n; jb += 32) {
+        a.step(jb, lane);
+        b.step(jb, lane);
+    }
+    a.finish(lane);
+    if (two) b.finish(lane);
 }
 
 template <int G, int NW, int DPW, int WARPS, int MAXIT>
@@ -245,7 +283,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_dedisp_fact(const FactArgs a) {
         const int ngs = (ncc + G - 1) / G;
         const int n_desc = n_desc_next;
         if (next) stage_load(s + 1);  // in flight during the build
-        for (int d = warp; d < n_desc; d += WARPS) build_row<G>(s_desc32 + 4u * DI * d, s0, lane);
+        for (int d = 2 * warp; d < n_desc; d += 2 * WARPS)
+            build_rows<G>(s_desc32 + 4u * DI * d, d + 1 < n_desc ? s_desc32 + 4u * DI * (d + 1) : 0xffffffffu, s0, lane);
         __syncthreads();  // pattern rows complete; raw rows and descriptors free
         if (next) stage_store(s + 1, buf ^ 1);
         if (since_fold + ncc > 256) {
