@@ -46,13 +46,24 @@ __device__ __forceinline__ void load_offsets(const int32_t* p, int32_t (&o)[N]) 
         const int2 v = *reinterpret_cast<const int2*>(p);
         o[0] = v.x;
         o[1] = v.y;
-    } else {
-        static_assert(N == 4, "DPW must be 1, 2 or 4");
+    } else if constexpr (N == 4) {
         const int4 v = *reinterpret_cast<const int4*>(p);
         o[0] = v.x;
         o[1] = v.y;
         o[2] = v.z;
         o[3] = v.w;
+    } else {
+        static_assert(N == 8, "DPW must be 1, 2, 4 or 8");
+        const int4 v = *reinterpret_cast<const int4*>(p);
+        const int4 w = *reinterpret_cast<const int4*>(p + 4);
+        o[0] = v.x;
+        o[1] = v.y;
+        o[2] = v.z;
+        o[3] = v.w;
+        o[4] = w.x;
+        o[5] = w.y;
+        o[6] = w.z;
+        o[7] = w.w;
     }
 }
 
@@ -141,7 +152,7 @@ __device__ __forceinline__ void build_rows(uint32_t d0, uint32_t d1, uint32_t s0
 }
 
 template <int G, int NW, int DPW, int WARPS, int MAXIT>
-__global__ void __launch_bounds__(WARPS * 32) k_dedisp_fact(const FactArgs a) {
+__global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1) k_dedisp_fact(const FactArgs a) {
     constexpr int BD = WARPS * DPW;
     constexpr int T = 64 * NW;
     constexpr int NT = WARPS * 32;
@@ -376,6 +387,10 @@ const FEntry kFEntries[] = {
     FDD_F(8, 2, 4, 16, 4),  // G 8, BD 64, T 128
     FDD_F(8, 8, 2, 16, 4),  // G 8, BD 32, T 512
     FDD_F(4, 8, 2, 16, 4),  // G 4, BD 32, T 512
+    FDD_F(4, 2, 8, 8, 4),   // G 4, BD 64, T 128, 256 threads (two blocks per SM)
+    FDD_F(4, 4, 4, 8, 4),   // G 4, BD 32, T 256, 256 threads
+    FDD_F(8, 2, 8, 8, 4),   // G 8, BD 64, T 128, 256 threads
+    FDD_F(4, 4, 8, 8, 4),   // G 4, BD 64, T 256, 256 threads
 };
 #undef FDD_F
 
