@@ -391,6 +391,8 @@ const FEntry kFEntries[] = {
     FDD_F(4, 4, 4, 8, 4),   // G 4, BD 32, T 256, 256 threads
     FDD_F(8, 2, 8, 8, 4),   // G 8, BD 64, T 128, 256 threads
     FDD_F(4, 4, 8, 8, 4),   // G 4, BD 64, T 256, 256 threads
+    FDD_F(4, 4, 2, 32, 1),  // G 4, BD 64, T 256, 1024 threads (32 warps for latency hiding)
+    FDD_F(4, 4, 1, 32, 1),  // G 4, BD 32, T 256, 1024 threads
 };
 #undef FDD_F
 

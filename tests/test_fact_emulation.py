@@ -154,6 +154,8 @@ def test_factored_kernel_emulation(v, CC):
     sb = rng.integers(0, n_tab, size=(n_sb, n_chan)).astype(np.int16)
     tb = fdd.fact_tables_host(n_tab, n_chan, n_sb, f, T_SAMP, ranges, sb, 0, v["index"], CC)
     assert tb["Lw"] > 0
+    if int(tb["pd_idx"][..., 1].max()) * (tb["desc_ints"] // 4) > v["threads"]:
+        pytest.skip("layout the library refuses (stage descriptors exceed one int4 per thread)")
     assert (tb["delays"] == d).all()
     S = emulate(x, n_in, sb, tb, v, CC, n_dm, n_out)
     want = oracle.dedisperse(oracle.downsample(x, 1, n_in=n_in), sb, d, n_out)
