@@ -305,38 +305,23 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1) k_dedisp_fac
         since_fold += ncc;
         const int32_t* go = s_goff + buf * gps * BD + warp * DPW;
         int gl = 0;
-        int32_t oa[DPW], ob[DPW];  // offsets of the current group pair, fetched one pair ahead
-        if (ngs >= 2) {
-            load_offsets<DPW>(go, oa);
-            load_offsets<DPW>(go + BD, ob);
-        }
 #pragma unroll 1
         for (; gl + 1 < ngs; gl += 2) {
-            int32_t na[DPW], nb[DPW];
-            const bool more = gl + 3 < ngs;
-            if (more) {
-                load_offsets<DPW>(go + (gl + 2) * BD, na);
-                load_offsets<DPW>(go + (gl + 3) * BD, nb);
-            }
+            int32_t o0[DPW], o1[DPW];
+            load_offsets<DPW>(go + gl * BD, o0);
+            load_offsets<DPW>(go + (gl + 1) * BD, o1);
             uint32_t x[2][DPW][NW];
 #pragma unroll
             for (int j = 0; j < DPW; j++)
 #pragma unroll
                 for (int k = 0; k < NW; k++) {
-                    x[0][j][k] = lds32(s_lane + static_cast<uint32_t>(oa[j]) + 128u * k);
-                    x[1][j][k] = lds32(s_lane + static_cast<uint32_t>(ob[j]) + 128u * k);
+                    x[0][j][k] = lds32(s_lane + static_cast<uint32_t>(o0[j]) + 128u * k);
+                    x[1][j][k] = lds32(s_lane + static_cast<uint32_t>(o1[j]) + 128u * k);
                 }
 #pragma unroll
             for (int j = 0; j < DPW; j++)
 #pragma unroll
                 for (int k = 0; k < NW; k++) acc[j][k] = acc[j][k] + x[0][j][k] + x[1][j][k];
-            if (more) {
-#pragma unroll
-                for (int j = 0; j < DPW; j++) {
-                    oa[j] = na[j];
-                    ob[j] = nb[j];
-                }
-            }
         }
         if (gl < ngs) {
             int32_t o0[DPW];
