@@ -58,8 +58,7 @@ N_SM = 148
 INT_LANES_PER_SM = 128
 ADDS_PER_LANE_OP = 2        # one IADD3 adds two operands
 SM_MAX_MHZ_NOMINAL = 2032.0
-PROFILE = os.path.join(ROOT, "profiles", "k_dedisp_arts_single_sb.md")
-DEDISP_SRC = os.path.join(ROOT, "paper_2205_12362_b300", "csrc", "k_dedisp.cu")
+CSRC = os.path.join(ROOT, "paper_2205_12362_b300", "csrc")
 
 
 # ----------------------------------------------------------------- workload
@@ -194,17 +193,20 @@ def oracle_sample_rate(x, sb, f, t, w, n_in, target_s):
 
 
 # ----------------------------------------------------------------- profile evidence
-def profile_traffic():
-    """DRAM bytes per dedispersion launch from the committed ncu summary, or
-    None when the kernel source changed since the counters were taken."""
-    if not os.path.exists(PROFILE):
+def profile_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summary profiles/<kernel>_<workload>.md, or None when there is none or the
+    kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload))
+    src = os.path.join(CSRC, kernel + ".cu")
+    if not os.path.exists(path) or not os.path.exists(src):
         return None
-    text = open(PROFILE).read()
+    text = open(path).read()
     m_sha = re.search(r"source_sha1:\s*([0-9a-f]{40})", text)
     m_b = re.search(r"dram_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
     if not m_sha or not m_b:
         return None
-    sha = hashlib.sha1(open(DEDISP_SRC, "rb").read()).hexdigest()
+    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
     return float(m_b.group(1)) if sha == m_sha.group(1) else None
 
 
@@ -385,10 +387,19 @@ def run_fdd(args):
     sm_mhz = clocks.get("sm_mhz")
     peak = N_SM * INT_LANES_PER_SM * ADDS_PER_LANE_OP * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
     achieved = adds_launch / (ded_ms / 1e3) / 1e12 if ded_ms else None
+    cfgs = [plan.get_config(r) for r in range(len(w["ranges"]))] if mode in ("plain", "per_sb") else []
+    n_brute = sum(1 for v in fdd.variants() if v["group"] == 0)
+    if mode in ("batched", "graph"):
+        kname = "k_batch"
+    else:
+        kname = "k_dedisp_fact" if cfgs and cfgs[0]["variant"] >= n_brute else "k_dedisp"
+    ratio = float(np.mean([c["work_ratio"] for c in cfgs])) if cfgs else 1.0
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": profile_traffic(),
-            "kernel": "k_dedisp_persistent" if mode in ("batched", "graph") else "k_dedisp",
-            "units_per_launch": adds_launch,
+            "frac": (achieved / peak) if achieved else None, "traffic": profile_traffic(kname, args.workload),
+            "kernel": kname, "units_per_launch": adds_launch,
+            "method_adds_per_launch": adds_launch * ratio,
+            "method_note": "achieved counts brute-force channel-adds; the configured kernel performs "
+                           "method_adds_per_launch integer adds (pattern-factored kernels reuse partial sums)",
             "peak_basis": "148 SM x 128 INT32 lanes x 2 adds/IADD3 x 2032 MHz (derived; no measured INT peak)",
             "peak_at_sampled_clock": (peak * sm_mhz / SM_MAX_MHZ_NOMINAL) if sm_mhz else None,
             "avg_launch_ms": ded_ms}

@@ -177,8 +177,8 @@ int fdd_downsample_u8(const uint8_t* d_in, int64_t n_rows, int64_t n_in, int64_t
  * auto-tuning, Sec. "AMBER"; this library does the same with its own tuner).
  * Fields: variant index, DM trials per block, output samples per block,
  * channels per shared-memory stage, threads per block, 32-bit words per
- * staged row copy, and the mean launch time the tuner measured (ms, 0 if the
- * range was not tuned). */
+ * staged row copy, the mean launch time the tuner measured (ms, 0 if the
+ * range was not tuned), and the kernel's adds per brute-force channel-add. */
 typedef struct {
     int32_t variant;
     int32_t dm_per_block;
@@ -187,6 +187,8 @@ typedef struct {
     int32_t threads;
     int32_t row_words;
     float tuned_ms;
+    float work_ratio;  /* integer adds the configured kernel performs per brute-force channel-add (1 for
+                          brute force; < 1 for the pattern-factored kernel: pattern builds + per-trial adds) */
 } fdd_kernel_config;
 
 /* Number of compiled dedispersion kernel variants (valid variant indices are

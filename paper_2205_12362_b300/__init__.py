@@ -51,7 +51,7 @@ class _Range(ctypes.Structure):
 class KernelConfig(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("dm_per_block", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("chan_per_stage", ctypes.c_int32), ("threads", ctypes.c_int32), ("row_words", ctypes.c_int32),
-                ("tuned_ms", ctypes.c_float)]
+                ("tuned_ms", ctypes.c_float), ("work_ratio", ctypes.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -65,6 +65,7 @@ FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactV
         int32_t rmin = 0, rmax = 0;
     };
     int64_t pat_region = 0;
+    double adds_fact = 0, adds_brute = 0;  // per time tile
     std::vector<int32_t> trial_pat(BD), trial_ref(BD);
     for (int b = 0; b < n_blk; b++) {
         const int ia = b * BD, ib = std::min(r.n_dm, (b + 1) * BD);
@@ -128,6 +129,10 @@ FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactV
                     }
                     ft.pdesc.insert(ft.pdesc.end(), d.begin(), d.end());
                 }
+                const int valid = std::min(BD, r.n_dm - ia);
+                adds_brute += static_cast<double>(valid) * gn * T;
+                adds_fact += static_cast<double>(valid) * T;  // one pattern partial per trial and sample
+                for (const Pat& pt : pats) adds_fact += static_cast<double>((pt.rmax - pt.rmin) + T) * (gn - 1);
                 for (int jj = 0; jj < BD; jj++) {
                     const int pi = trial_pat[jj];
                     const int32_t o = trial_ref[jj] - pats[pi].rmin;
@@ -142,6 +147,7 @@ FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactV
             pat_region = std::max(pat_region, cursor);
         }
     }
+    ft.work_ratio = adds_brute > 0 ? adds_fact / adds_brute : 1.0;
     // raw row words: every staged read (brute-force span and pattern builds)
     const int64_t need_words = (max_need + 3) / 4;
     const int64_t Lw = static_cast<int64_t>(align_up(static_cast<size_t>(need_words + 1), 4));

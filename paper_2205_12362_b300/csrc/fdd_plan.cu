@@ -232,6 +232,7 @@ int configure_fact(fdd_plan* p, RangeState& r, int fv, int CC) {
     r.f_n_stages = best.n_stages;
     r.f_n_groups = best.n_groups;
     r.f_smem = best.smem_bytes;
+    r.f_work_ratio = static_cast<float>(best.work_ratio);
     return FDD_OK;
 }
 
@@ -616,6 +617,7 @@ int fdd_plan_get_config(const fdd_plan* plan, int32_t r, fdd_kernel_config* out)
         out->chan_per_stage = rs.f_CC;
         out->threads = v.threads();
         out->row_words = rs.f_Lw;
+        out->work_ratio = rs.f_work_ratio;
     } else {
         const fdd::DedispVariant& v = fdd::dedisp_variant(rs.variant);
         out->dm_per_block = v.bd();
@@ -623,6 +625,7 @@ int fdd_plan_get_config(const fdd_plan* plan, int32_t r, fdd_kernel_config* out)
         out->chan_per_stage = rs.CC;
         out->threads = v.threads();
         out->row_words = rs.Lw;
+        out->work_ratio = 1.f;
     }
     out->tuned_ms = rs.tuned_ms;
     return FDD_OK;
