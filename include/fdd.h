@@ -209,8 +209,7 @@ int fdd_variant_info(int32_t variant, int32_t* bytes_per_sample, int32_t* dm_per
  * groups, stages, ints per descriptor, shared-memory bytes, descriptors,
  * DM blocks.  Array arguments may be NULL (sizes first, then data): base
  * [n_blk][n_chan], goff [n_blk][n_groups][BD], pdesc [n_desc][desc_ints],
- * pd_idx [n_blk][n_stages][4] (first descriptor, count, 31-unit build items
- * per row, 0), delays [n_dm][n_chan]. */
+ * pd_idx [n_blk][n_stages][2], delays [n_dm][n_chan]. */
 int fdd_fact_tables_host(const fdd_plan_desc* desc, const int16_t* sb_map_host, int32_t range, int32_t variant,
                          int32_t chan_per_stage, int64_t* info, int32_t* base, int32_t* goff, int32_t* pdesc,
                          int32_t* pd_idx, int32_t* delays);

@@ -18,7 +18,7 @@
 //                                row word for group g (copy = offset parity)
 //   pdesc per (block, stage) the list of pattern rows to build:
 //         {dst copy 0, dst copy 1, units of 4 samples, src offset per channel}
-//   pd_idx [n_blk][n_stages][4]  (first descriptor, count, 31-unit build items per row, 0)
+//   pd_idx [n_blk][n_stages][2]  (first descriptor, count)
 // and the raw row length Lw and the pattern region size of the layout.
 // Shared memory: [zero row | CC raw slots | pattern rows | 2 x stage offsets |
 // stage descriptors].
@@ -46,7 +46,7 @@ FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactV
     ft.desc_ints = v.desc_ints();
     ft.base.assign(static_cast<size_t>(n_blk) * n_chan, 0);
     ft.goff.assign(static_cast<size_t>(n_blk) * n_groups * BD, 0);
-    ft.pd_idx.assign(static_cast<size_t>(n_blk) * n_stages * 4, 0);
+    ft.pd_idx.assign(static_cast<size_t>(n_blk) * n_stages * 2, 0);
     auto D = [&](int i, int c) { return r.delay[static_cast<size_t>(i) * n_chan + c]; };
 
     // raw row starts (aligned to 16 samples) and the largest staged span
@@ -72,7 +72,6 @@ FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactV
         for (int s = 0; s < n_stages; s++) {
             int64_t cursor = 0;  // bytes of pattern rows of this (block, stage)
             const int first_desc = static_cast<int>(ft.pdesc.size() / ft.desc_ints);
-            int32_t max_nw4 = 0;
             for (int gl = 0; gl < gps; gl++) {
                 const int g = s * gps + gl;
                 if (g >= n_groups) break;
@@ -109,7 +108,6 @@ FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactV
                     const Pat& pt = pats[pi];
                     const int32_t span = pt.rmax - pt.rmin;
                     const int32_t nw4 = (span + T) / 4 + 2;  // units of 4 samples built
-                    max_nw4 = std::max(max_nw4, nw4);
                     const int32_t lpw = 2 * nw4;             // 32-bit words per copy
                     dst0[pi] = static_cast<int32_t>(cursor);
                     dst1[pi] = static_cast<int32_t>(cursor + 4LL * lpw);
@@ -144,9 +142,8 @@ FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactV
             }
             const int n_desc = static_cast<int>(ft.pdesc.size() / ft.desc_ints) - first_desc;
             ft.max_desc = std::max(ft.max_desc, n_desc);
-            ft.pd_idx[(static_cast<size_t>(b) * n_stages + s) * 4] = first_desc;
-            ft.pd_idx[(static_cast<size_t>(b) * n_stages + s) * 4 + 1] = n_desc;
-            ft.pd_idx[(static_cast<size_t>(b) * n_stages + s) * 4 + 2] = (max_nw4 + 30) / 31;  // 31-unit items per row
+            ft.pd_idx[(static_cast<size_t>(b) * n_stages + s) * 2] = first_desc;
+            ft.pd_idx[(static_cast<size_t>(b) * n_stages + s) * 2 + 1] = n_desc;
             pat_region = std::max(pat_region, cursor);
         }
     }

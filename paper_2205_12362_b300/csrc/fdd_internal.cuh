@@ -74,7 +74,7 @@ struct FactArgs {
     const int32_t* base;        // [n_blk][n_chan]
     const int32_t* goff;        // [n_blk][n_groups][BD]
     const int32_t* pdesc;       // pattern-row descriptors
-    const int32_t* pd_idx;      // [n_blk][n_stages][4]: first descriptor, count, build items per row
+    const int32_t* pd_idx;      // [n_blk][n_stages][2]
     int32_t* series;            // [n_sb][n_dm][n_out]
     unsigned long long* stat;   // [n_sb * n_dm][2]
     int32_t n_chan, n_dm, n_out, n_sb;

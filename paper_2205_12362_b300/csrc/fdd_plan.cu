@@ -774,7 +774,7 @@ int fdd_fact_tables_host(const fdd_plan_desc* desc, const int16_t* sb_map_host, 
     if (base) std::memcpy(base, ft.base.data(), ft.base.size() * sizeof(int32_t));
     if (goff) std::memcpy(goff, ft.goff.data(), ft.goff.size() * sizeof(int32_t));
     if (pdesc) std::memcpy(pdesc, ft.pdesc.data(), ft.pdesc.size() * sizeof(int32_t));
-    if (pd_idx) std::memcpy(pd_idx, ft.pd_idx.data(), ft.pd_idx.size() * sizeof(int32_t));  // [n_blk][n_stages][4]
+    if (pd_idx) std::memcpy(pd_idx, ft.pd_idx.data(), ft.pd_idx.size() * sizeof(int32_t));
     if (delays) std::memcpy(delays, r.delay.data(), r.delay.size() * sizeof(int32_t));
     return FDD_OK;
 }

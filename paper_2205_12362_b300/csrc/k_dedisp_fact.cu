@@ -67,22 +67,21 @@ __device__ __forceinline__ void load_offsets(const int32_t* p, int32_t (&o)[N]) 
     }
 }
 
-// Pattern-row builds.  A row descriptor in shared memory is {dst0, dst1,
-// nw4, src[G]}: copy-0 and copy-1 destinations, units of 4 samples, and the
-// staged raw word of unit 0 for each channel.  Work is cut into items of 31
-// units (row, step) dealt evenly over the warps.  Lane l computes unit
-// 31*step + l: acc_a = sum of the G raw words (bytes overlap), acc_b = sum of
-// bytes 1,3 in 16-bit lanes (one PRMT per word); samples 0,2 are acc_a -
-// (acc_b << 8) (lanes hold <= 257 * 255).  Lanes 0..30 store copy 0
-// [R0,R1],[R2,R3] and copy 1 [R1,R2],[R3,R4], R4 being lane l+1's R0 by
-// shuffle; lane 31 computes the next item's first unit only for that shuffle.
+// Pattern-row builds (whole warp).  A row descriptor in shared memory is
+// {dst0, dst1, nw4, src[G]}: copy-0 and copy-1 destinations, units of 4
+// samples, and the staged raw word of unit 0 for each channel.  Per lane and
+// unit: acc_a = sum of the G raw words (bytes overlap), acc_b = sum of bytes
+// 1,3 in 16-bit lanes (one PRMT per word); samples 0,2 are acc_a - (acc_b <<
+// 8) (lanes hold <= 257 * 255).  Copy 0 stores [R0,R1],[R2,R3]; copy 1 stores
+// [R1,R2],[R3,R4], R4 being the next lane's R0 (shuffle; across a 32-unit
+// step it comes from lane 0 of the next step).
 template <int G>
-struct BuildItem {
+struct RowState {
     uint32_t dst0, dst1, src[G];
-    int nw4, jb;
-    bool live;
+    int nw4;
+    uint32_t pend_b;
 
-    __device__ __forceinline__ void load(uint32_t d, uint32_t s0, int step) {
+    __device__ __forceinline__ void load(uint32_t d, uint32_t s0) {
         asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
                      : "=r"(dst0), "=r"(dst1), "=r"(nw4), "=r"(src[0])
                      : "r"(d));
@@ -91,12 +90,12 @@ struct BuildItem {
         src[0] += s0;
         dst0 += s0;
         dst1 += s0;
-        jb = 31 * step;
-        live = jb < nw4;
+        pend_b = 0;
     }
 
-    __device__ __forceinline__ void run(int lane) {
-        if (!live) return;  // warp-uniform
+    // One 32-unit step starting at unit jb (jb < nw4 or the row is done).
+    __device__ __forceinline__ void step(int jb, int lane) {
+        if (jb >= nw4) return;  // warp-uniform
         const int j = jb + lane;
         uint32_t acc_a = 0, acc_b = 0;
         if (j < nw4) {
@@ -114,12 +113,43 @@ struct BuildItem {
         const uint32_t B = __byte_perm(ev, od, 0x7632);  // [R2, R3]
         const uint32_t C = __byte_perm(od, ev, 0x7610);  // [R1, R2]
         const uint32_t next_a = __shfl_down_sync(0xffffffffu, A, 1);
-        if (lane < 31 && j < nw4) {
+        const uint32_t first_a = __shfl_sync(0xffffffffu, A, 0);
+        if (j < nw4) {
             sts64(dst0 + 8u * j, A, B);
-            sts64(dst1 + 8u * j, C, __byte_perm(B, next_a, 0x5432));  // [R1,R2], [R3,R4]
+            sts32(dst1 + 8u * j, C);
+            if (lane < 31) sts32(dst1 + 8u * j + 4u, __byte_perm(B, next_a, 0x5432));  // [R3, R4]
         }
+        if (lane == 31 && jb > 0) sts32(dst1 + 8u * (jb - 1) + 4u, __byte_perm(pend_b, first_a, 0x5432));
+        pend_b = B;
+    }
+
+    __device__ __forceinline__ void finish(int lane) {
+        if (lane == 31 && nw4 > 0 && (nw4 & 31) == 0)
+            sts32(dst1 + 8u * (nw4 - 1) + 4u, __byte_perm(pend_b, 0u, 0x5432));
     }
 };
+
+// Rows d0 and d1 (d1 == 0xffffffff: none) interleaved step by step, so a
+// lane has two independent build chains in flight.
+template <int G>
+__device__ __forceinline__ void build_rows(uint32_t d0, uint32_t d1, uint32_t s0, int lane) {
+    RowState<G> a, b;
+    a.load(d0, s0);
+    const bool two = d1 != 0xffffffffu;
+    if (two) {
+        b.load(d1, s0);
+    } else {
+        b.nw4 = 0;
+        b.pend_b = 0;
+    }
+    const int n = max(a.nw4, b.nw4);
+    for (int jb = 0; jb < n; jb += 32) {
+        a.step(jb, lane);
+        b.step(jb, lane);
+    }
+    a.finish(lane);
+    if (two) b.finish(lane);
+}
 
 template <int G, int NW, int DPW, int WARPS, int MAXIT>
 __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1) k_dedisp_fact(const FactArgs a) {
@@ -148,7 +178,7 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1) k_dedisp_fac
     const int16_t* sbm = a.sb_map + (int64_t)sb * a.n_chan;
     const int32_t* base_blk = a.base + (int64_t)blk * a.n_chan;
     const int32_t* goff_blk = a.goff + (int64_t)blk * a.n_groups * BD;
-    const int32_t* pd_blk = a.pd_idx + (int64_t)blk * a.n_stages * 4;  // {first, count, steps, -}
+    const int32_t* pd_blk = a.pd_idx + (int64_t)blk * a.n_stages * 2;
 
     for (int i = threadIdx.x; i < Lw; i += NT) reinterpret_cast<uint32_t*>(smem)[i] = 0u;  // zero row
 
@@ -156,7 +186,7 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1) k_dedisp_fac
     uint32_t pn[MAXIT];
     int4 po = make_int4(0, 0, 0, 0);
     int4 pdv = make_int4(0, 0, 0, 0);
-    int n_desc_next = 0, steps_next = 0;
+    int n_desc_next = 0;
 
     auto stage_load = [&](int s) {
         const int c0 = s * CC;
@@ -194,10 +224,8 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1) k_dedisp_fac
         }
         if (threadIdx.x < ngs * (BD / 4))
             po = __ldg(reinterpret_cast<const int4*>(goff_blk + (int64_t)(s * gps) * BD) + threadIdx.x);
-        const int4 pd = *reinterpret_cast<const int4*>(pd_blk + 4 * s);
-        const int first = pd.x;
-        n_desc_next = pd.y;
-        steps_next = pd.z;
+        const int first = pd_blk[2 * s];
+        n_desc_next = pd_blk[2 * s + 1];
         if (threadIdx.x < n_desc_next * (DI / 4))
             pdv = __ldg(reinterpret_cast<const int4*>(a.pdesc + (int64_t)first * DI) + threadIdx.x);
     };
@@ -265,21 +293,9 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1) k_dedisp_fac
         const int ncc = min(CC, a.n_chan - s * CC);
         const int ngs = (ncc + G - 1) / G;
         const int n_desc = n_desc_next;
-        const int steps = steps_next;  // 31-unit items per row in this stage
         if (next) stage_load(s + 1);  // in flight during the build
-        const int n_items = n_desc * steps;
-        for (int it = warp; it < n_items; it += 2 * WARPS) {  // two items per warp at a time
-            BuildItem<G> p, q;
-            p.load(s_desc32 + 4u * DI * (it / steps), s0, it % steps);
-            const int it2 = it + WARPS;
-            if (it2 < n_items) {
-                q.load(s_desc32 + 4u * DI * (it2 / steps), s0, it2 % steps);
-            } else {
-                q.live = false;
-            }
-            p.run(lane);
-            q.run(lane);
-        }
+        for (int d = 2 * warp; d < n_desc; d += 2 * WARPS)
+            build_rows<G>(s_desc32 + 4u * DI * d, d + 1 < n_desc ? s_desc32 + 4u * DI * (d + 1) : 0xffffffffu, s0, lane);
         __syncthreads();  // pattern rows complete; raw rows and descriptors free
         if (next) stage_store(s + 1, buf ^ 1);
         if (since_fold + ncc > 256) {

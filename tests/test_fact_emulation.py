@@ -86,11 +86,10 @@ def emulate(x, n_valid, sb_map, tb, v, CC, n_dm, n_out):
                             words = (w << (8 * np.arange(4, dtype=np.uint32))).sum(-1)
                             sm.wr32(raw_lo + cc * 16 * Lw + q * 4 * Lw + 4 * np.arange(Lw), words, raw_lo, raw_hi)
                     goff_buf[s % 2] = tb["goff"][blk, s * gps:s * gps + ngs]
-                    first, n_desc, steps, _ = tb["pd_idx"][blk, s]
+                    first, n_desc = tb["pd_idx"][blk, s]
                     sm.m[pat_lo:pat_hi] = 0xAB       # stale pattern bytes from an earlier stage
                     for d in tb["pdesc"][first:first + n_desc]:   # pattern-row builds
                         dst0, dst1, nw4 = int(d[0]), int(d[1]), int(d[2])
-                        assert 31 * steps >= nw4, "build items do not cover the row"
                         src = d[3:3 + G].astype(np.int64)
                         j = np.arange(nw4)
                         ev = np.zeros(nw4, np.uint32)
