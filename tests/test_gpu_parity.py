@@ -405,3 +405,49 @@ def test_batch_autotune_keeps_parity(fdd):
     ref = plan.search(dx, n_in, n_out, want_series=True)
     torch.cuda.synchronize()
     assert torch.equal(res.series, ref.series)
+
+
+def test_four_range_71_sb_batched_sampled(fdd):
+    """The 4-range 0-5000 plan over 71 SBs at full size, in the batched
+    launch configuration the benchmark and serving loop use; one SB checked
+    against the oracle on sampled series of every range and on all its
+    candidates."""
+    import torch
+    n_tab, n_chan, n_sb, n_out = 12, 1536, 71, synth.ARTS_CHUNK
+    f = synth.channel_freqs(n_chan)
+    W = [1, 2, 4, 8, 16, 32, 64]
+    ranges = [dict(dm0=0.0, ddm=0.2, n_dm=2048, downsamp=1, widths=W),
+              dict(dm0=409.6, ddm=0.8, n_dm=1024, downsamp=2, widths=W),
+              dict(dm0=1228.8, ddm=1.6, n_dm=1024, downsamp=4, widths=W),
+              dict(dm0=2867.2, ddm=3.2, n_dm=667, downsamp=8, widths=W)]
+    sb = synth.sb_map_piecewise(4, n_sb, n_chan, n_tab).astype(np.int16)
+    plan = fdd.Plan(n_tab, n_chan, n_sb, f, T_SAMP, ranges, 8.0, sb)
+    n_in = n_out + plan.max_delay
+    s_chk = 17
+    prm = [dict(dm=300.0, t0=3000, width=4, snr=30.0), dict(dm=900.0, t0=6000, width=8, snr=40.0),
+           dict(dm=2000.0, t0=8000, width=16, snr=40.0), dict(dm=4000.0, t0=9000, width=32, snr=45.0)]
+    tabs_of_sb = sorted(set(sb[s_chk].tolist()))
+    pulses = [dict(tab=t, start=p["t0"] + oracle.delays(f, T_SAMP, p["dm"], 1.0, 1)[0], width=p["width"],
+                   amp=synth.pulse_amplitude(p["snr"], n_chan, p["width"])) for p in prm for t in tabs_of_sb]
+    x = synth.filterbank(4, n_tab, n_chan, n_in, pulses=pulses)
+    dx = to_dev(x)
+    plan.batch_prepare(n_out)
+    job = plan.make_job(dx, n_in, n_out, cap=1 << 22, want_series=True)
+    res = plan.search_batch([job], n_out)[0]
+    torch.cuda.synchronize()
+    gpu, n = res.candidates()
+    assert n == len(gpu)
+    views = plan.series_views(res.series, n_out)
+    ora, os_ = oracle_candidate_superset(x, sb[s_chk:s_chk + 1], f, T_SAMP, ranges, 8.0, n_out, n_in,
+                                         return_series=True)
+    rng = np.random.default_rng(4)
+    for r in range(4):
+        dms = rng.integers(0, ranges[r]["n_dm"], size=32)
+        assert (views[r][s_chk, dms].cpu().numpy() == os_[r][0, dms]).all(), "range %d" % r
+    ora = ora.copy()
+    ora["sb"] = s_chk
+    compare_candidates(gpu[gpu["sb"] == s_chk], ora, 8.0)
+    for p in prm:   # every injected pulse is found in the checked SB
+        near = gpu[(gpu["sb"] == s_chk) & (np.abs(gpu["dm"] - p["dm"]) < 0.02 * p["dm"] + 3)
+                   & (np.abs(gpu["t_native"] - p["t0"]) < 4 * p["width"] + 16)]
+        assert len(near) > 0, p
