@@ -122,6 +122,12 @@ int fdd_plan_destroy(fdd_plan* plan);
  * input samples per channel. */
 int fdd_plan_max_delay(const fdd_plan* plan, int64_t* max_delay_native);
 
+/* Plan summary for a search of n_out native output samples: the largest
+ * delay (as fdd_plan_max_delay) and the workspace bytes of a search with
+ * n_in = n_out + max_delay_native whose series stay in the workspace (as
+ * fdd_workspace_size(plan, n_in, n_out, 1, ...)). */
+int fdd_plan_info(const fdd_plan* plan, int64_t n_out, int64_t* max_delay_native, int64_t* workspace_bytes);
+
 /* Number of DM trials summed over all ranges (the length of the global
  * dm_index axis). */
 int fdd_plan_total_dms(const fdd_plan* plan, int64_t* n_dm_total);
@@ -365,6 +371,55 @@ int fdd_server_results(fdd_server* server, fdd_window_result* out, int32_t max_r
                        int64_t cands_cap, int32_t* n_results, int64_t* n_cands);
 
 int fdd_server_info(const fdd_server* server, fdd_server_stats* stats);
+
+/* ---------------------------------------------------------------------
+ * Per-beam streaming search (the paper's real-time search of one compound
+ * beam: every 1.024 s chunk is searched with the following max delay of
+ * data appended; Sec. "AMBER", Sec. "Computing performance").  The caller
+ * pushes the beam's chunks from DEVICE memory in order; the stream keeps the
+ * delay overlap in two device buffers of ceil((chunk + max delay) / chunk)
+ * chunks each (owned by the stream, freed by fdd_stream_close) and searches
+ * window w -- native outputs [w*chunk, (w+1)*chunk), candidate t_native
+ * absolute -- with fdd_search as soon as its last needed chunk is pushed
+ * (window 0 after chunk ceil((chunk + max delay) / chunk) - 1, then one
+ * window per chunk).  Downsampling bins start at each window's first
+ * sample.  For many beams on one GPU with batching and admission control,
+ * use the fdd_server_* runtime below.  Not thread-safe per stream object. */
+typedef struct fdd_stream fdd_stream;
+
+/* Open a stream for compound beam beam_id (a label used in error messages)
+ * with chunks of chunk_len native samples; cap = candidate records kept per
+ * window.  Allocates the buffers, a search workspace and the candidate
+ * buffer on the current device.  Errors: INVALID_ARG, CUDA (allocation). */
+int fdd_stream_open(fdd_plan* plan, int32_t beam_id, int64_t chunk_len, int64_t cap, fdd_stream** out);
+
+/* Push chunk `seq` (0, 1, 2, ...): device uint8 [n_tab][n_chan] rows of
+ * chunk_len samples at chunk_pitch bytes (>= chunk_len, any alignment).
+ * Enqueues on `stream` the copy into the stream's buffer and, when the push
+ * completes a window, that window's search and the carry of its overlap;
+ * the chunk buffer may be reused once those have run.  A push is ordered
+ * after the previous push of the same object even on another CUDA stream.
+ * Errors: SEQUENCE (seq is not the next chunk; nothing enqueued),
+ * INVALID_ARG, CUDA. */
+int fdd_stream_push(fdd_stream* st, const uint8_t* d_chunk, int64_t chunk_pitch, int64_t seq, fdd_stream_t stream);
+
+/* Results of the window searched last, if no fdd_stream_results call has
+ * taken them yet: enqueues, on the CUDA stream of the last push, a copy of
+ * the first min(true count, cap, stream cap) candidate records to device
+ * d_cands and of the window's TRUE candidate count to device *d_count, and
+ * sets host *t0_native to the window's first output sample.  With no new
+ * window, enqueues nothing and sets *t0_native = -1.  Each window that
+ * completes replaces the previous window's results: call after every push
+ * to see every window. */
+int fdd_stream_results(fdd_stream* st, fdd_candidate* d_cands, int64_t cap, uint64_t* d_count, int64_t* t0_native);
+
+/* Wait for the stream's last push, free everything it owns.  NULL accepted. */
+int fdd_stream_close(fdd_stream* st);
+
+/* Host helper: sort n host candidate records in place by (sb, dm_index,
+ * width_native, t_native), the order used to compare candidate sets (the
+ * search itself emits them in no particular order). */
+int fdd_sort_candidates(fdd_candidate* cands, int64_t n);
 
 /* Per-stage GPU timing (tracing; the paper reports AMBER's time per stage,
  * Sec. "Computing performance").  With timing enabled, fdd_search records a

@@ -152,6 +152,12 @@ def _lib_raw():
     L.fdd_fact_tables_host.argtypes = [ctypes.POINTER(_PlanDesc), _P, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P]
     L.fdd_search_static.argtypes = [_P, _P, _I64, _I64, _I64, _I64, _P, _I64, _P, _P, _P]
     L.fdd_plan_stage_times.argtypes = [_P, _I32, _P, _P, _P, ctypes.POINTER(_I32)]
+    L.fdd_plan_info.argtypes = [_P, _I64, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]
+    L.fdd_stream_open.argtypes = [_P, _I32, _I64, _I64, ctypes.POINTER(_P)]
+    L.fdd_stream_push.argtypes = [_P, _P, _I64, _I64, _P]
+    L.fdd_stream_results.argtypes = [_P, _P, _I64, _P, ctypes.POINTER(_I64)]
+    L.fdd_stream_close.argtypes = [_P]
+    L.fdd_sort_candidates.argtypes = [_P, _I64]
     _lib = L
     return L
 
@@ -367,6 +373,67 @@ class Server:
             pass
 
 
+class Stream:
+    """Per-beam streaming search (include/fdd.h: fdd_stream_*): chunks are
+    pushed from device memory in order; each completed window is searched on
+    the device."""
+
+    def __init__(self, plan, beam_id, chunk_len, cap=1 << 15):
+        h = ctypes.c_void_p()
+        _check(_lib_raw().fdd_stream_open(plan.handle, int(beam_id), int(chunk_len), int(cap), ctypes.byref(h)),
+               "fdd_stream_open")
+        self._h = h
+        self._plan = plan
+        self.chunk_len, self.cap = int(chunk_len), int(cap)
+
+    def push(self, chunk, seq, stream=None):
+        """chunk: CUDA uint8 tensor [n_tab][n_chan][>= chunk_len] (rows at its
+        last-dimension pitch).  Returns 0 or FDD_ERR_SEQUENCE; raises on
+        other errors."""
+        import torch
+        if chunk.dim() != 3 or chunk.shape[0] != self._plan.n_tab or chunk.shape[1] != self._plan.n_chan:
+            raise ValueError("chunk must be [n_tab][n_chan][pitch]")
+        if chunk.shape[2] < self.chunk_len:
+            raise ValueError("chunk pitch shorter than chunk_len")
+        code = _lib_raw().fdd_stream_push(self._h, _dev_ptr(chunk, "chunk", torch.uint8), int(chunk.shape[2]),
+                                          int(seq), _stream_handle(stream))
+        if code in (0, FDD_ERR_SEQUENCE):
+            return code
+        raise FddError(code, "fdd_stream_push")
+
+    def results(self, cands, count):
+        """Enqueue the last window's records into device `cands` (int32
+        [cap, 8]) and its true count into device `count` (int64 [1]); returns
+        the window's first output sample, or -1 if no new window."""
+        import torch
+        t0 = _I64()
+        _check(_lib_raw().fdd_stream_results(self._h, _dev_ptr(cands, "cands", torch.int32), int(cands.shape[0]),
+                                             _dev_ptr(count, "count", torch.int64), ctypes.byref(t0)),
+               "fdd_stream_results")
+        return int(t0.value)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib_raw().fdd_stream_close(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sort_candidates(cands):
+    """Sort a host structured array of CAND_DTYPE records in place with the
+    library's fdd_sort_candidates; returns it."""
+    if cands.dtype != CAND_DTYPE or not cands.flags["C_CONTIGUOUS"]:
+        raise ValueError("cands must be a contiguous CAND_DTYPE array")
+    _check(_lib_raw().fdd_sort_candidates(cands.ctypes.data_as(ctypes.c_void_p), int(cands.size)),
+           "fdd_sort_candidates")
+    return cands
+
+
 def _plan_desc(n_tab, n_chan, n_sb, chan_freq_mhz, t_samp_s, ranges, snr_thresh, keep):
     freq = np.ascontiguousarray(chan_freq_mhz, dtype=np.float64)
     rs = [dict(dm0=float(r["dm0"]), ddm=float(r["ddm"]), n_dm=int(r["n_dm"]), downsamp=int(r.get("downsamp", 1)),
@@ -463,6 +530,13 @@ class Plan:
         v = _I64()
         _check(_lib_raw().fdd_plan_max_delay(self._h, ctypes.byref(v)), "fdd_plan_max_delay")
         return int(v.value)
+
+    def info(self, n_out):
+        """(max delay in native samples, workspace bytes of an n_out search)
+        (include/fdd.h: fdd_plan_info)."""
+        md, ws = _I64(), _I64()
+        _check(_lib_raw().fdd_plan_info(self._h, int(n_out), ctypes.byref(md), ctypes.byref(ws)), "fdd_plan_info")
+        return int(md.value), int(ws.value)
 
     @property
     def n_dm_total(self):

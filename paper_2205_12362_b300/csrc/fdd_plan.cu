@@ -478,6 +478,14 @@ int fdd_plan_max_delay(const fdd_plan* plan, int64_t* max_delay_native) {
     return FDD_OK;
 }
 
+int fdd_plan_info(const fdd_plan* plan, int64_t n_out, int64_t* max_delay_native, int64_t* workspace_bytes) {
+    if (!plan || n_out < 0 || !max_delay_native || !workspace_bytes) return fail(FDD_ERR_INVALID_ARG, "bad argument");
+    *max_delay_native = plan->max_delay_native;
+    *workspace_bytes =
+        static_cast<int64_t>(make_layout(plan, n_out + plan->max_delay_native, n_out, true).total);
+    return FDD_OK;
+}
+
 int fdd_plan_total_dms(const fdd_plan* plan, int64_t* n_dm_total) {
     if (!plan || !n_dm_total) return fail(FDD_ERR_INVALID_ARG, "null argument");
     *n_dm_total = plan->n_dm_total;

@@ -26,8 +26,9 @@ def lib():
 
 def test_header_declares_the_boundary():
     names = header_functions()
-    for must in ("fdd_plan_create", "fdd_plan_destroy", "fdd_search", "fdd_workspace_size",
-                 "fdd_downsample_u8", "fdd_error_string"):
+    for must in ("fdd_plan_create", "fdd_plan_destroy", "fdd_plan_info", "fdd_search", "fdd_workspace_size",
+                 "fdd_downsample_u8", "fdd_stream_open", "fdd_stream_push", "fdd_stream_results",
+                 "fdd_stream_close", "fdd_sort_candidates", "fdd_error_string"):
         assert must in names
 
 
@@ -76,3 +77,23 @@ def test_variant_table():
     for v in vs:
         assert v["dm_per_block"] % 4 == 0 and v["threads"] % 32 == 0
         assert v["tile"] > 0 and v["tile"] % 128 == 0
+
+
+def test_sort_candidates_host_helper():
+    """fdd_sort_candidates (host) orders records by (sb, dm_index, width,
+    t) exactly as numpy's lexicographic sort of the same fields."""
+    import paper_2205_12362_b300 as m
+    rng = np.random.default_rng(3)
+    a = np.zeros(5000, dtype=m.CAND_DTYPE)
+    a["sb"] = rng.integers(0, 4, a.size)
+    a["dm_index"] = rng.integers(0, 30, a.size)
+    a["width_native"] = rng.choice([1, 2, 4, 8], a.size)
+    a["t_native"] = rng.integers(-5, 10 ** 10, a.size)
+    a["snr"] = rng.random(a.size)
+    want = np.sort(a.copy(), order=["sb", "dm_index", "width_native", "t_native"])
+    got = m.sort_candidates(a)
+    keys = ["sb", "dm_index", "width_native", "t_native"]
+    for k in keys:
+        assert (got[k] == want[k]).all()
+    assert sorted(got["snr"].tolist()) == sorted(want["snr"].tolist())
+    m.sort_candidates(np.zeros(0, dtype=m.CAND_DTYPE))
