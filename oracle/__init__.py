@@ -9,8 +9,9 @@ Functions follow the paper's AMBER stages (Sec. "AMBER"): ``delays``
 (Sec. "Dedispersion", cold-plasma law), ``downsample`` (Sec.
 "Downsampling"), ``dedisperse`` (Sec. "Dedispersion" with the SB formation of
 Sec. "Hierarchical beam forming"), ``stats`` / ``boxcar_snr`` (Sec.
-"Integration", "S/N evaluation") and ``search`` (all stages plus Sec.
-"Candidate selection").  Pins for each live in tests/test_oracle_*.py.
+"Integration", "S/N evaluation"), ``search`` (all stages plus Sec.
+"Candidate selection") and ``cluster`` (the optional DM-width clustering of
+Sec. "AMBER").  Pins for each live in tests/test_oracle_*.py.
 """
 import ctypes
 import os
@@ -48,6 +49,8 @@ def lib():
         L.oracle_search.argtypes = [_P, _I32, _I32, _I64, _I64, _P, _I32, _P, _D, _I32,
                                     _P, _P, _P, _P, _P, _P, _D, _I64, _I64, _P, _I64, _P]
         L.oracle_search.restype = _I64
+        L.oracle_cluster.argtypes = [_P, _I64, _P]
+        L.oracle_cluster.restype = _I64
         _lib = L
     return _lib
 
@@ -176,3 +179,19 @@ def search(x, sb_map, freq_mhz, t_samp_s, ranges, snr_thresh, n_out, n_in=None,
             out_series.append(series[off:off + k].reshape(m.shape[0], int(r["n_dm"]), nr))
             off += k
     return got, int(n), out_series
+
+
+def cluster(cands):
+    """DM-width clustering (oracle.c: oracle_cluster) of a structured array of
+    candidates with the fields of CAND_DTYPE (any float type for dm/snr;
+    records are taken in the given order, which decides exact ties).
+    Returns the kept records as a CAND_DTYPE array sorted by (sb, dm_index,
+    width_native, t_native)."""
+    a = np.zeros(len(cands), dtype=CAND_DTYPE)
+    for f in CAND_DTYPE.names:
+        a[f] = cands[f]
+    out = np.zeros(max(len(a), 1), dtype=CAND_DTYPE)
+    n = lib().oracle_cluster(_ptr(a), len(a), _ptr(out))
+    if n < 0:
+        raise MemoryError("oracle allocation failed")
+    return np.sort(out[:n], order=["sb", "dm_index", "width_native", "t_native"])

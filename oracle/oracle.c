@@ -241,3 +241,77 @@ int64_t oracle_search(const uint8_t* x, int32_t n_tab, int32_t n_chan, int64_t n
     }
     return count;
 }
+
+/* ------------------------------------------------------------------------
+ * DM-width clustering of a candidate list (Sec. "AMBER", paragraph
+ * "Clustering (optional)"), in the two steps the paper gives:
+ *   1. among candidates of one SB at the same time and the same DM trial
+ *      (different pulse widths) keep the one with the highest S/N;
+ *   2. among the survivors of one SB at the same time, a group of
+ *      neighbouring DM trials (dm_index k, k+1, k+2, ... with no gap) keeps
+ *      only its highest-S/N candidate.
+ * Readings (the paper is silent on them): "time" is the window start
+ * t_native, compared exactly; clustering is per SB; DM neighbours are
+ * consecutive global dm_index values (so a group may cross a DM-range
+ * boundary); ties keep the smaller width in step 1, then the earlier record
+ * of the input list, and the smaller dm_index in step 2.
+ * Writes the kept records to out (in (sb, t, dm) order) and returns how many.
+ * Returns -2 on allocation failure. */
+static const oracle_cand* g_cl_in; /* qsort context (single-threaded) */
+
+static int cl_cmp(const void* pa, const void* pb) {
+    int64_t a = *(const int64_t*)pa, b = *(const int64_t*)pb;
+    const oracle_cand *x = g_cl_in + a, *y = g_cl_in + b;
+    if (x->sb != y->sb) return x->sb < y->sb ? -1 : 1;
+    if (x->t_native != y->t_native) return x->t_native < y->t_native ? -1 : 1;
+    if (x->dm_index != y->dm_index) return x->dm_index < y->dm_index ? -1 : 1;
+    if (x->width_native != y->width_native) return x->width_native < y->width_native ? -1 : 1;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+int64_t oracle_cluster(const oracle_cand* in, int64_t n, oracle_cand* out) {
+    if (n <= 0) return 0;
+    int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t* keep = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    if (!idx || !keep) { free(idx); free(keep); return -2; }
+    for (int64_t k = 0; k < n; k++) idx[k] = k;
+    g_cl_in = in;
+    qsort(idx, (size_t)n, sizeof(int64_t), cl_cmp);
+    /* step 1: one candidate per (sb, t, dm): the highest S/N; the sort order
+     * puts smaller widths, then earlier records, first, and only a strictly
+     * higher S/N replaces the one kept */
+    int64_t m = 0;
+    for (int64_t k = 0; k < n; k++) {
+        const oracle_cand* c = in + idx[k];
+        if (m > 0) {
+            const oracle_cand* p = in + keep[m - 1];
+            if (p->sb == c->sb && p->t_native == c->t_native && p->dm_index == c->dm_index) {
+                if (c->snr > p->snr) keep[m - 1] = idx[k];
+                continue;
+            }
+        }
+        keep[m++] = idx[k];
+    }
+    /* step 2: runs of consecutive dm_index at one (sb, t) keep their highest
+     * S/N; scanning in dm order, only a strictly higher S/N replaces */
+    int64_t n_out = 0, best = -1, prev = -1;
+    for (int64_t k = 0; k < m; k++) {
+        const oracle_cand* c = in + keep[k];
+        int joins = 0;
+        if (prev >= 0) {
+            const oracle_cand* p = in + prev;
+            joins = p->sb == c->sb && p->t_native == c->t_native && c->dm_index == p->dm_index + 1;
+        }
+        if (!joins) {
+            if (best >= 0) out[n_out++] = in[best];
+            best = keep[k];
+        } else if (c->snr > in[best].snr) {
+            best = keep[k];
+        }
+        prev = keep[k];
+    }
+    if (best >= 0) out[n_out++] = in[best];
+    free(idx);
+    free(keep);
+    return n_out;
+}
