@@ -421,6 +421,29 @@ int fdd_stream_close(fdd_stream* st);
  * search itself emits them in no particular order). */
 int fdd_sort_candidates(fdd_candidate* cands, int64_t n);
 
+/* DM-width clustering of a candidate list (Sec. "AMBER", "Clustering
+ * (optional)"): among candidates of one SB at the same time (t_native) and
+ * DM trial, keep the highest S/N over widths; then every group of
+ * neighbouring DM trials (consecutive dm_index, no gap, possibly across a
+ * DM-range boundary) at that SB and time keeps only its highest-S/N
+ * candidate.  Ties keep the smaller width, then the earlier record of the
+ * input list (step 1), and the smaller dm_index (step 2).
+ *   d_in, d_in_count  device candidate list as written by fdd_search: the
+ *                     first min(*d_in_count, cap_in) records are clustered.
+ *   d_workspace       >= fdd_cluster_workspace_size(cap_in) bytes, 16-byte
+ *                     aligned (a hash table of about 48 * cap_in bytes).
+ *   d_out, cap_out    device output records (order unspecified); *d_out_count
+ *                     receives the TRUE number kept (> cap_out: overflow, the
+ *                     first cap_out written).
+ * Records with sb >= 8192, dm_index >= 2^21, or t_native more than 2^30 - 2
+ * samples after the list's earliest are passed through unclustered.
+ * Asynchronous on stream (five small launches).  cap_in <= 2^31.
+ * Errors: INVALID_ARG, MISALIGNED, WORKSPACE, CUDA. */
+int fdd_cluster_workspace_size(int64_t cap_in, size_t* bytes);
+int fdd_cluster(const fdd_candidate* d_in, const uint64_t* d_in_count, int64_t cap_in, void* d_workspace,
+                size_t workspace_bytes, fdd_candidate* d_out, int64_t cap_out, uint64_t* d_out_count,
+                fdd_stream_t stream);
+
 /* Per-stage GPU timing (tracing; the paper reports AMBER's time per stage,
  * Sec. "Computing performance").  With timing enabled, fdd_search records a
  * CUDA event pair around every kernel it enqueues; the pairs are reused by

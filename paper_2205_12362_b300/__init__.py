@@ -158,6 +158,8 @@ def _lib_raw():
     L.fdd_stream_results.argtypes = [_P, _P, _I64, _P, ctypes.POINTER(_I64)]
     L.fdd_stream_close.argtypes = [_P]
     L.fdd_sort_candidates.argtypes = [_P, _I64]
+    L.fdd_cluster_workspace_size.argtypes = [_I64, ctypes.POINTER(_SZ)]
+    L.fdd_cluster.argtypes = [_P, _P, _I64, _P, _SZ, _P, _I64, _P, _P]
     _lib = L
     return L
 
@@ -422,6 +424,31 @@ class Stream:
             self.close()
         except Exception:
             pass
+
+
+def cluster_workspace_size(cap_in):
+    v = _SZ()
+    _check(_lib_raw().fdd_cluster_workspace_size(int(cap_in), ctypes.byref(v)), "fdd_cluster_workspace_size")
+    return int(v.value)
+
+
+def cluster(cands, count, out, out_count, workspace=None, stream=None):
+    """DM-width clustering on the device (include/fdd.h: fdd_cluster).
+    cands: int32 CUDA tensor [cap_in, 8] of records, count: int64 [1] (true
+    count as written by a search); out: int32 [cap_out, 8], out_count:
+    int64 [1].  Asynchronous on `stream`."""
+    import torch
+    cap_in = int(cands.shape[0])
+    need = cluster_workspace_size(cap_in)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=cands.device)
+    _check(_lib_raw().fdd_cluster(_dev_ptr(cands, "cands", torch.int32), _dev_ptr(count, "count", torch.int64),
+                                  cap_in, _dev_ptr(workspace, "workspace"),
+                                  int(workspace.numel() * workspace.element_size()),
+                                  _dev_ptr(out, "out", torch.int32), int(out.shape[0]),
+                                  _dev_ptr(out_count, "out_count", torch.int64), _stream_handle(stream)),
+           "fdd_cluster")
+    return workspace
 
 
 def sort_candidates(cands):
