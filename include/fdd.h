@@ -204,6 +204,13 @@ typedef struct {
  * trials, channel groups with equal relative delays share one partial sum;
  * native-rate ranges only).  Any output pointer may be NULL. */
 int fdd_num_variants(int32_t* n);
+/* Kind of variant v: 0 brute force; 1 pattern-factored (native-rate ranges);
+ * 2 SB-factored (plans with >= 2 SBs: per DM-trial slab, every TAB is
+ * dedispersed over channel segments on which every SB keeps one TAB, and
+ * each SB adds the segment partials of the TABs it takes -- exact; the
+ * search workspace then holds a scratch of at most 4 GiB for the partials,
+ * counted by fdd_workspace_size). */
+int fdd_variant_kind(int32_t variant, int32_t* kind);
 int fdd_variant_info(int32_t variant, int32_t* bytes_per_sample, int32_t* dm_per_block, int32_t* tile,
                      int32_t* threads, int32_t* group);
 
@@ -443,6 +450,13 @@ int fdd_cluster_workspace_size(int64_t cap_in, size_t* bytes);
 int fdd_cluster(const fdd_candidate* d_in, const uint64_t* d_in_count, int64_t cap_in, void* d_workspace,
                 size_t workspace_bytes, fdd_candidate* d_out, int64_t cap_out, uint64_t* d_out_count,
                 fdd_stream_t stream);
+
+/* Cap (bytes) on the scratch the SB-factored kernel keeps in the search
+ * workspace for its partial sums (0 = default, 4 GiB).  The partials of a
+ * slab of DM trials must fit: a smaller cap means smaller slabs and more
+ * launches, never a different result; at least one DM block's worth is
+ * always reserved.  Changes fdd_workspace_size for plans with >= 2 SBs. */
+int fdd_plan_set_scratch_limit(fdd_plan* plan, int64_t bytes);
 
 /* Per-stage GPU timing (tracing; the paper reports AMBER's time per stage,
  * Sec. "Computing performance").  With timing enabled, fdd_search records a

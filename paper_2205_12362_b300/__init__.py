@@ -158,6 +158,8 @@ def _lib_raw():
     L.fdd_stream_results.argtypes = [_P, _P, _I64, _P, ctypes.POINTER(_I64)]
     L.fdd_stream_close.argtypes = [_P]
     L.fdd_sort_candidates.argtypes = [_P, _I64]
+    L.fdd_variant_kind.argtypes = [_I32, ctypes.POINTER(_I32)]
+    L.fdd_plan_set_scratch_limit.argtypes = [_P, _I64]
     L.fdd_cluster_workspace_size.argtypes = [_I64, ctypes.POINTER(_SZ)]
     L.fdd_cluster.argtypes = [_P, _P, _I64, _P, _SZ, _P, _I64, _P, _P]
     _lib = L
@@ -169,8 +171,9 @@ def version():
 
 
 def variants():
-    """[{index, bytes_per_sample, dm_per_block, tile, threads, group}] of the compiled dedispersion
-    kernels (group > 0: pattern-factored kernel with channel groups of that size)."""
+    """[{index, kind, bytes_per_sample, dm_per_block, tile, threads, group}] of the compiled
+    dedispersion kernels (kind 0 brute force, 1 pattern-factored with channel groups of size
+    `group`, 2 SB-factored)."""
     L = _lib_raw()
     n = _I32()
     _check(L.fdd_num_variants(ctypes.byref(n)), "fdd_num_variants")
@@ -179,7 +182,9 @@ def variants():
         e, bd, t, th, g = _I32(), _I32(), _I32(), _I32(), _I32()
         _check(L.fdd_variant_info(v, ctypes.byref(e), ctypes.byref(bd), ctypes.byref(t), ctypes.byref(th),
                                   ctypes.byref(g)), "fdd_variant_info")
-        out.append(dict(index=v, bytes_per_sample=e.value, dm_per_block=bd.value, tile=t.value,
+        k = _I32()
+        _check(L.fdd_variant_kind(v, ctypes.byref(k)), "fdd_variant_kind")
+        out.append(dict(index=v, kind=k.value, bytes_per_sample=e.value, dm_per_block=bd.value, tile=t.value,
                         threads=th.value, group=g.value))
     return out
 
@@ -557,6 +562,11 @@ class Plan:
         v = _I64()
         _check(_lib_raw().fdd_plan_max_delay(self._h, ctypes.byref(v)), "fdd_plan_max_delay")
         return int(v.value)
+
+    def set_scratch_limit(self, nbytes):
+        """Cap the SB-factored kernel's partial-sum scratch (include/fdd.h:
+        fdd_plan_set_scratch_limit; 0 = default)."""
+        _check(_lib_raw().fdd_plan_set_scratch_limit(self._h, int(nbytes)), "fdd_plan_set_scratch_limit")
 
     def info(self, n_out):
         """(max delay in native samples, workspace bytes of an n_out search)

@@ -87,6 +87,53 @@ bool fact_cc_ok(const FactVariant& v, int Lw, int CC, int max_desc);
 cudaError_t launch_dedisp_fact(int variant, const FactArgs& a, size_t smem, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
+// SB-factored dedispersion (k_sbf.cu; tables and slab loop in fdd_sbf.cu).
+// Channels are cut into segments on which every SB takes one TAB.  Pass 1
+// ("part") dedisperses every TAB over every segment into 16-bit partial
+// sums P[tab][seg][trial][t]; pass 2 ("comb") adds, for every SB, the
+// partials of the TABs it selects.  The sums are the same integers as brute
+// force, regrouped; partials of one TAB and segment serve every SB that
+// selects that TAB there.  Both passes run per slab of consecutive DM trials
+// so that P fits a bounded scratch buffer.
+struct SbfPartArgs {
+    const uint8_t* in;          // rows (tab, c) at in + (tab * n_chan + c) * pitch_bytes
+    int64_t pitch_bytes;
+    int64_t n_valid;            // valid samples per row
+    const int32_t* base;        // brute-force tables of the variant's BD: [n_blk][n_chan]
+    const int32_t* off;         // [n_blk][n_chan][BD]
+    const int4* stages;         // [n_stages]: first channel, channels, first segment, segments
+    const int2* segs;           // [n_seg]: first channel, channels
+    uint16_t* P;                // slab partials [tab][seg][slab_rows][Np]
+    int64_t tab_stride, seg_stride;  // elements
+    int32_t Np;                 // row pitch of P (elements, multiple of 512)
+    int32_t n_chan, n_dm, n_out, Lw, CC, n_stages;
+    int32_t i0, n_slab;         // slab trials [i0, i0 + n_slab); i0 a multiple of BD
+};
+
+struct SbfCombArgs {
+    const uint16_t* P;
+    int64_t tab_stride, seg_stride;
+    int32_t Np;
+    const uint8_t* seg_tab;     // [n_sb][seg_pitch]: TAB SB s takes on segment u (seg_pitch % 4 == 0)
+    int32_t seg_pitch;
+    int32_t* series;            // this range: [n_sb][n_dm][n_out]
+    unsigned long long* stat;   // this range: [n_sb * n_dm][2]
+    int32_t n_sb, n_seg, n_dm, n_out;
+    int32_t i0, n_slab;
+    int32_t flush;              // segments summed in 16-bit lanes between folds
+};
+
+int num_sbf_variants();
+const DedispVariant& sbf_variant(int idx);
+// Shared memory of a part block: CC channel rows (4/E copies) + offsets.
+size_t sbf_smem_bytes(const DedispVariant& v, int Lw, int CC);
+bool sbf_cc_ok(const DedispVariant& v, int Lw, int CC, size_t smem_budget);
+cudaError_t launch_sbf_part(int idx, const SbfPartArgs& a, int n_tab, cudaStream_t s);
+// SBs handled by one comb block (the grid's z covers ceil(n_sb / this)).
+int sbf_comb_sbs_per_block();
+cudaError_t launch_sbf_comb(const SbfCombArgs& a, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
 struct BoxcarArgs {
     const int32_t* series;              // [n_sb][n_dm][n_out] of this range
     const unsigned long long* stat;     // [n_sb * n_dm][2]

@@ -144,6 +144,11 @@ fdd::host::Layout fdd::host::make_layout(const fdd_plan* p, int64_t n_in, int64_
     L.series_bytes = series_elems * sizeof(int32_t);
     L.stat_bytes = n_series * 2 * sizeof(unsigned long long);
     size_t cur = 0;
+    L.sbf_bytes = sbf_scratch_bytes(p, n_out);
+    if (L.sbf_bytes) {
+        L.sbf = cur;
+        cur = align_up(cur + L.sbf_bytes, 256);
+    }
     if (with_series) {
         L.series = cur;
         cur = align_up(cur + L.series_bytes, 256);
@@ -185,12 +190,17 @@ void free_fact_tables(RangeState& r) {
     r.fact = -1;
 }
 
-void free_range_tables(RangeState& r) {
+void free_brute_tables(RangeState& r) {
     if (r.d_off) cudaFree(r.d_off);
     if (r.d_base) cudaFree(r.d_base);
     r.d_off = nullptr;
     r.d_base = nullptr;
+}
+
+void free_range_tables(RangeState& r) {
+    free_brute_tables(r);
     free_fact_tables(r);
+    free_sbf_tables(r, false);
 }
 
 int upload_vec(int32_t** dst, const std::vector<int32_t>& v, const char* what) {
@@ -220,6 +230,7 @@ int configure_fact(fdd_plan* p, RangeState& r, int fv, int CC) {
     }
     if (best_cc == 0) return fail(FDD_ERR_UNSUPPORTED, "factored kernel does not fit this range and stage size");
     free_fact_tables(r);
+    free_sbf_tables(r, false);
     int rc;
     if ((rc = upload_vec(&r.d_fbase, best.base, "factored base table")) != FDD_OK) return rc;
     if ((rc = upload_vec(&r.d_goff, best.goff, "factored offset table")) != FDD_OK) return rc;
@@ -239,6 +250,15 @@ int configure_fact(fdd_plan* p, RangeState& r, int fv, int CC) {
 // Configure range r for kernel variant `variant` with channel stage CC
 // (0 = the largest that fits).
 int configure_range(fdd_plan* p, RangeState& r, int variant, int CC) {
+    const int nbf = fdd::num_dedisp_variants() + fdd::num_fact_variants();
+    if (variant >= nbf) {  // SB-factored variants follow the pattern-factored ones
+        const int rc = configure_sbf(p, r, variant - nbf, CC);
+        if (rc == FDD_OK) {
+            free_brute_tables(r);
+            free_fact_tables(r);
+        }
+        return rc;
+    }
     if (variant >= fdd::num_dedisp_variants())  // factored variants follow the brute-force ones
         return configure_fact(p, r, variant - fdd::num_dedisp_variants(), CC);
     if (variant < 0) return fail(FDD_ERR_INVALID_ARG, "kernel variant out of range");
@@ -285,7 +305,15 @@ cudaError_t launch_range_dedisp(const RangeState& r, const fdd::DedispArgs& a, c
 }
 
 int range_variant_index(const RangeState& r) {
+    if (r.sbf >= 0) return fdd::num_dedisp_variants() + fdd::num_fact_variants() + r.sbf;
     return r.fact >= 0 ? fdd::num_dedisp_variants() + r.fact : r.variant;
+}
+
+// Dedispersion of one range with whichever kernel it is configured for.
+cudaError_t launch_range(const fdd_plan* p, const RangeState& r, const fdd::DedispArgs& a, const Layout& L,
+                         uint8_t* ws, cudaStream_t s) {
+    if (r.sbf >= 0) return launch_range_sbf(p, r, a, ws + L.sbf, L.sbf_bytes, s);
+    return launch_range_dedisp(r, a, s);
 }
 
 int default_variant(int E) {
@@ -400,6 +428,11 @@ static int build_host_plan(const fdd_plan_desc* desc, const int16_t* sb_map_host
             p->ds_factors.push_back(in.downsamp);
     }
     p->n_dm_total = dm_index;
+    for (RangeState& r : p->ranges) {
+        r.segs = sbf_segments(p, r.D);
+        r.seg_maxlen = 0;
+        for (const int2& sg : r.segs) r.seg_maxlen = std::max(r.seg_maxlen, sg.y);
+    }
 
     return FDD_OK;
 }
@@ -466,7 +499,10 @@ int fdd_plan_destroy(fdd_plan* plan) {
     if (!plan) return FDD_OK;
     fdd_free_batch_state(plan);
     for (cudaEvent_t e : plan->ev) cudaEventDestroy(e);
-    for (RangeState& r : plan->ranges) free_range_tables(r);
+    for (RangeState& r : plan->ranges) {
+        free_range_tables(r);
+        free_sbf_tables(r, true);
+    }
     if (plan->d_sb_map) cudaFree(plan->d_sb_map);
     delete plan;
     return FDD_OK;
@@ -552,7 +588,7 @@ int fdd_search(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitc
         if (nr == 0) continue;
         const fdd::DedispArgs a = dedisp_args(plan, r, ri, L, d_tabs, pitch, ws, series, stat, n_in, n_out);
         if ((e = stage_begin(1, static_cast<int>(ri))) != cudaSuccess) return cuda_fail(e, "timing event");
-        e = launch_range_dedisp(r, a, s);
+        e = launch_range(plan, r, a, L, ws, s);
         if (e != cudaSuccess) return cuda_fail(e, "dedispersion launch");
         if ((e = stage_end()) != cudaSuccess) return cuda_fail(e, "timing event");
 
@@ -587,14 +623,30 @@ int fdd_search(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitc
 
 int fdd_num_variants(int32_t* n) {
     if (!n) return fail(FDD_ERR_INVALID_ARG, "null argument");
-    *n = fdd::num_dedisp_variants() + fdd::num_fact_variants();
+    *n = fdd::num_dedisp_variants() + fdd::num_fact_variants() + fdd::num_sbf_variants();
+    return FDD_OK;
+}
+
+int fdd_variant_kind(int32_t variant, int32_t* kind) {
+    const int nb = fdd::num_dedisp_variants(), nf = fdd::num_fact_variants(), ns = fdd::num_sbf_variants();
+    if (!kind || variant < 0 || variant >= nb + nf + ns) return fail(FDD_ERR_INVALID_ARG, "bad variant");
+    *kind = variant < nb ? 0 : (variant < nb + nf ? 1 : 2);
     return FDD_OK;
 }
 
 int fdd_variant_info(int32_t variant, int32_t* bytes_per_sample, int32_t* dm_per_block, int32_t* tile,
                      int32_t* threads, int32_t* group) {
-    const int nb = fdd::num_dedisp_variants();
-    if (variant < 0 || variant >= nb + fdd::num_fact_variants()) return fail(FDD_ERR_INVALID_ARG, "bad variant");
+    const int nb = fdd::num_dedisp_variants(), nf = fdd::num_fact_variants();
+    if (variant < 0 || variant >= nb + nf + fdd::num_sbf_variants()) return fail(FDD_ERR_INVALID_ARG, "bad variant");
+    if (variant >= nb + nf) {
+        const fdd::DedispVariant& v = fdd::sbf_variant(variant - nb - nf);
+        if (bytes_per_sample) *bytes_per_sample = v.E;
+        if (dm_per_block) *dm_per_block = v.bd();
+        if (tile) *tile = v.tile();
+        if (threads) *threads = v.threads();
+        if (group) *group = 0;
+        return FDD_OK;
+    }
     if (variant >= nb) {
         const fdd::FactVariant& v = fdd::fact_variant(variant - nb);
         if (bytes_per_sample) *bytes_per_sample = 1;
@@ -618,7 +670,15 @@ int fdd_plan_get_config(const fdd_plan* plan, int32_t r, fdd_kernel_config* out)
         return fail(FDD_ERR_INVALID_ARG, "bad range index");
     const RangeState& rs = plan->ranges[r];
     out->variant = range_variant_index(rs);
-    if (rs.fact >= 0) {
+    if (rs.sbf >= 0) {
+        const fdd::DedispVariant& v = fdd::sbf_variant(rs.sbf);
+        out->dm_per_block = v.bd();
+        out->tile = v.tile();
+        out->chan_per_stage = rs.s_CC;
+        out->threads = v.threads();
+        out->row_words = rs.s_Lw;
+        out->work_ratio = rs.s_work_ratio;
+    } else if (rs.fact >= 0) {
         const fdd::FactVariant& v = fdd::fact_variant(rs.fact);
         out->dm_per_block = v.bd();
         out->tile = v.tile();
@@ -643,7 +703,8 @@ int fdd_plan_set_config(fdd_plan* plan, int32_t r, int32_t variant, int32_t chan
     if (!plan || r < 0 || r >= static_cast<int32_t>(plan->ranges.size()) || chan_per_stage < 0)
         return fail(FDD_ERR_INVALID_ARG, "bad range index");
     RangeState& rs = plan->ranges[r];
-    const int old_variant = range_variant_index(rs), old_cc = rs.fact >= 0 ? rs.f_CC : rs.CC;
+    const int old_variant = range_variant_index(rs);
+    const int old_cc = rs.sbf >= 0 ? rs.s_CC : (rs.fact >= 0 ? rs.f_CC : rs.CC);
     const int rc = configure_range(plan, rs, variant, chan_per_stage);
     if (rc != FDD_OK && old_variant >= 0) configure_range(plan, rs, old_variant, old_cc);
     if (rc == FDD_OK) rs.tuned_ms = 0.f;
@@ -744,6 +805,33 @@ int fdd_plan_autotune(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64
                 }
             }
         }
+        const int nbf = fdd::num_dedisp_variants() + fdd::num_fact_variants();
+        for (int sv = 0; plan->n_sb >= 2 && sv < fdd::num_sbf_variants() && rc == FDD_OK; sv++) {
+            if (fdd::sbf_variant(sv).E != E) continue;
+            for (int cc : {16, 32, 48, 64}) {
+                if (configure_range(plan, r, nbf + sv, cc) != FDD_OK) continue;  // does not fit
+                const fdd::DedispArgs a = dedisp_args(plan, r, ri, L, d_tabs, pitch, ws, series, stat, n_in, n_out);
+                if ((e = launch_range(plan, r, a, L, ws, s)) != cudaSuccess) { rc = cuda_fail(e, "tuning launch"); break; }
+                cudaEventRecord(ev0, s);
+                for (int k = 0; k < reps && e == cudaSuccess; k++) e = launch_range(plan, r, a, L, ws, s);
+                cudaEventRecord(ev1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
+                if (e != cudaSuccess) { rc = cuda_fail(e, "tuning launch"); break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev0, ev1);
+                ms /= reps;
+                if (std::getenv("FDD_TUNE_VERBOSE")) {
+                    const fdd::DedispVariant& dv = fdd::sbf_variant(sv);
+                    std::fprintf(stderr, "fdd tune: range %zu SB-factored variant %d (bd %d tile %d) cc %d: %.4f ms\n",
+                                 ri, nbf + sv, dv.bd(), dv.tile(), cc, ms);
+                }
+                if (ms < best) {
+                    best = ms;
+                    best_v = nbf + sv;
+                    best_cc = cc;
+                }
+            }
+        }
         if (rc == FDD_OK) {
             rc = configure_range(plan, r, best_v, best_cc);
             if (rc == FDD_OK) r.tuned_ms = best;
@@ -784,6 +872,12 @@ int fdd_fact_tables_host(const fdd_plan_desc* desc, const int16_t* sb_map_host, 
     if (pdesc) std::memcpy(pdesc, ft.pdesc.data(), ft.pdesc.size() * sizeof(int32_t));
     if (pd_idx) std::memcpy(pd_idx, ft.pd_idx.data(), ft.pd_idx.size() * sizeof(int32_t));
     if (delays) std::memcpy(delays, r.delay.data(), r.delay.size() * sizeof(int32_t));
+    return FDD_OK;
+}
+
+int fdd_plan_set_scratch_limit(fdd_plan* plan, int64_t bytes) {
+    if (!plan || bytes < 0) return fail(FDD_ERR_INVALID_ARG, "bad argument");
+    plan->sbf_scratch_cap = bytes > 0 ? static_cast<size_t>(bytes) : kSbfScratchMax;
     return FDD_OK;
 }
 

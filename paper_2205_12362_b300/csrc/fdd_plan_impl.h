@@ -31,6 +31,18 @@ struct RangeState {
     int32_t* d_goff = nullptr;
     int32_t* d_pdesc = nullptr;
     int32_t* d_pdidx = nullptr;
+    // SB-factored kernel (sbf >= 0 selects it); segments are plan geometry
+    std::vector<int2> segs;           // channel segments on which every SB keeps one TAB
+    int32_t seg_maxlen = 0;
+    int2* d_segs = nullptr;           // device copy of segs
+    uint8_t* d_segtab = nullptr;      // [n_sb][seg_pitch]
+    int32_t seg_pitch = 0;
+    int sbf = -1;
+    int32_t s_CC = 0, s_Lw = 0, s_n_stages = 0, s_flush = 1;
+    float s_work_ratio = 1.f;
+    int32_t* d_sbase = nullptr;
+    int32_t* d_soff = nullptr;
+    int4* d_sstages = nullptr;
 };
 
 // Device tables of one range for the batched persistent kernel.
@@ -66,6 +78,7 @@ struct fdd_plan {
     std::vector<int32_t> ds_factors;  // distinct D > 1
     int64_t max_delay_native = 0;
     int64_t n_dm_total = 0;
+    size_t sbf_scratch_cap = size_t(4) << 30;  // SB-factored partial-sum scratch cap (fdd_plan_set_scratch_limit)
     int device = 0;
     // stage timing (fdd_plan_set_timing)
     bool timing = false;
@@ -111,6 +124,7 @@ struct FactTables {
 FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactVariant& v, int CC);
 
 struct Layout {
+    size_t sbf = 0, sbf_bytes = 0;  // scratch of the SB-factored kernel's partial sums
     size_t series = 0, series_bytes = 0;
     size_t stat = 0, stat_bytes = 0;
     std::vector<size_t> series_r;   // element offset of range r inside the series buffer
@@ -120,6 +134,17 @@ struct Layout {
     size_t total = 0;
 };
 Layout make_layout(const fdd_plan* p, int64_t n_in, int64_t n_out, bool with_series);
+// SB-factored kernel (fdd_sbf.cu).
+constexpr size_t kSbfScratchMax = size_t(4) << 30;
+std::vector<int2> sbf_segments(const fdd_plan* p, int D);
+size_t sbf_scratch_bytes(const fdd_plan* p, int64_t n_out);
+int configure_sbf(fdd_plan* p, RangeState& r, int sv, int CC);
+void free_sbf_tables(RangeState& r, bool geometry);
+// Adds per brute-force add of the SB-factored kernel for range r.
+double sbf_work_ratio(const fdd_plan* p, const RangeState& r);
+cudaError_t launch_range_sbf(const fdd_plan* p, const RangeState& r, const fdd::DedispArgs& a, uint8_t* scratch,
+                             size_t scratch_bytes, cudaStream_t s);
+
 int check_search_args(const fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitch, int64_t n_out,
                       const void* d_workspace, const void* d_series);
 

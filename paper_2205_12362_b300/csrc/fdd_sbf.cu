@@ -1,0 +1,206 @@
+// fdd_sbf.cu -- host side of the SB-factored dedispersion: channel segments,
+// channel stages, per-range configuration and the slab loop (kernels in
+// k_sbf.cu).
+//
+// Segments: maximal runs of consecutive channels on which every SB takes
+// the same TAB throughout, cut to at most min(16, 65535 / (255 D)) channels
+// so a segment's sum of D-sample sums fits a 16-bit lane.  Stages: whole
+// segments packed into at most CC channels.  The partial sums of a slab of
+// DM trials, [n_tab][n_seg][slab][Np] uint16, live in a scratch region of
+// the search workspace bounded by kSbfScratchMax; the slab is the largest
+// multiple of the variant's DM block that fits.
+#include <algorithm>
+
+#include "fdd_plan_impl.h"
+
+using namespace fdd::host;
+
+namespace {
+
+constexpr int kSbfSegMax = 16;
+
+int64_t round_up64(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+int64_t sbf_np(int64_t nr) { return round_up64(std::max<int64_t>(nr, 1), 512); }
+
+template <typename T>
+int upload(T** dst, const std::vector<T>& v, const char* what) {
+    cudaError_t e = cudaMalloc(dst, std::max<size_t>(v.size(), 1) * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    if (!v.empty() && (e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, what);
+    return FDD_OK;
+}
+
+// Slab of DM trials whose partial sums fit the scratch (a multiple of BD).
+int64_t slab_trials(const fdd_plan* p, const RangeState& r, int64_t nr, int BD, size_t scratch_bytes) {
+    const int64_t per_trial = static_cast<int64_t>(p->n_tab) * static_cast<int64_t>(r.segs.size()) * sbf_np(nr) * 2;
+    int64_t slab = static_cast<int64_t>(scratch_bytes) / per_trial / BD * BD;
+    return std::min<int64_t>(slab, round_up64(r.n_dm, BD));
+}
+
+}  // namespace
+
+namespace fdd {
+namespace host {
+
+std::vector<int2> sbf_segments(const fdd_plan* p, int D) {
+    const int max_len = std::max(1, std::min(kSbfSegMax, 65535 / (255 * D)));
+    std::vector<int2> segs;
+    int c0 = 0;
+    for (int c = 1; c <= p->n_chan; c++) {
+        bool cut = c == p->n_chan || c - c0 == max_len;
+        for (int s = 0; !cut && s < p->n_sb; s++)
+            cut = p->sb_map[static_cast<size_t>(s) * p->n_chan + c] != p->sb_map[static_cast<size_t>(s) * p->n_chan + c - 1];
+        if (cut) {
+            segs.push_back(make_int2(c0, c - c0));
+            c0 = c;
+        }
+    }
+    return segs;
+}
+
+size_t sbf_scratch_bytes(const fdd_plan* p, int64_t n_out) {
+    if (p->n_sb < 2) return 0;
+    size_t bytes = 0;
+    for (const RangeState& r : p->ranges) {
+        const int64_t nr = n_out / r.D;
+        if (nr == 0) continue;
+        const size_t per_trial = static_cast<size_t>(p->n_tab) * r.segs.size() * static_cast<size_t>(sbf_np(nr)) * 2;
+        const size_t full = per_trial * static_cast<size_t>(round_up64(r.n_dm, 64));
+        const size_t one_block = per_trial * 64;
+        bytes = std::max(bytes, std::min(full, std::max(p->sbf_scratch_cap, one_block)));
+    }
+    return align_up(bytes, 256);
+}
+
+double sbf_work_ratio(const fdd_plan* p, const RangeState& r) {
+    // per (trial, sample): n_tab * n_chan partial adds + n_sb * n_seg combine adds
+    const double brute = static_cast<double>(p->n_sb) * p->n_chan;
+    const double fact = static_cast<double>(p->n_tab) * p->n_chan + static_cast<double>(p->n_sb) * r.segs.size();
+    return fact / brute;
+}
+
+void free_sbf_tables(RangeState& r, bool geometry) {
+    for (int32_t** ptr : {&r.d_sbase, &r.d_soff}) {
+        if (*ptr) cudaFree(*ptr);
+        *ptr = nullptr;
+    }
+    if (r.d_sstages) cudaFree(r.d_sstages);
+    r.d_sstages = nullptr;
+    r.sbf = -1;
+    if (geometry) {
+        if (r.d_segs) cudaFree(r.d_segs);
+        if (r.d_segtab) cudaFree(r.d_segtab);
+        r.d_segs = nullptr;
+        r.d_segtab = nullptr;
+    }
+}
+
+// Configure range r for SB-factored variant sv with CC channels per stage
+// (0 = the largest that fits).  Tables of other kernels are left to the caller.
+int configure_sbf(fdd_plan* p, RangeState& r, int sv, int CC) {
+    if (sv < 0 || sv >= fdd::num_sbf_variants()) return fail(FDD_ERR_INVALID_ARG, "kernel variant out of range");
+    if (p->n_sb < 2) return fail(FDD_ERR_UNSUPPORTED, "the SB-factored kernel needs at least two SBs");
+    const fdd::DedispVariant& v = fdd::sbf_variant(sv);
+    if (v.E != (r.D == 1 ? 1 : 2)) return fail(FDD_ERR_INVALID_ARG, "kernel variant for the wrong sample width");
+    const HostTables h = build_tables(p, r, v);
+    if (h.Lw < 0) return fail(FDD_ERR_UNSUPPORTED, "DM step too large for one block's staged rows");
+    const int seg_max = r.seg_maxlen;
+    int cc_pick = 0;
+    for (int cc : {64, 48, 32, 16, 8, 4, 2, 1}) {
+        if (CC != 0 && cc != CC) continue;
+        if (cc < seg_max || !fdd::sbf_cc_ok(v, h.Lw, cc, kSmemBudget)) continue;
+        cc_pick = cc;
+        break;
+    }
+    if (cc_pick == 0) return fail(FDD_ERR_UNSUPPORTED, "SB-factored kernel does not fit this range and stage size");
+    std::vector<int4> stages;
+    for (size_t g = 0; g < r.segs.size(); g++) {
+        const int2 sg = r.segs[g];
+        if (!stages.empty() && stages.back().y + sg.y <= cc_pick) {
+            stages.back().y += sg.y;
+            stages.back().w += 1;
+        } else {
+            stages.push_back(make_int4(sg.x, sg.y, static_cast<int>(g), 1));
+        }
+    }
+    free_sbf_tables(r, false);
+    int rc;
+    if (!r.d_segs) {
+        if ((rc = upload(&r.d_segs, r.segs, "segment table")) != FDD_OK) return rc;
+        r.seg_pitch = static_cast<int32_t>(round_up64(static_cast<int64_t>(r.segs.size()), 4));
+        std::vector<uint8_t> tab(static_cast<size_t>(p->n_sb) * r.seg_pitch, 0);
+        for (int s = 0; s < p->n_sb; s++)
+            for (size_t g = 0; g < r.segs.size(); g++)
+                tab[static_cast<size_t>(s) * r.seg_pitch + g] =
+                    static_cast<uint8_t>(p->sb_map[static_cast<size_t>(s) * p->n_chan + r.segs[g].x]);
+        if ((rc = upload(&r.d_segtab, tab, "segment TAB table")) != FDD_OK) return rc;
+    }
+    if ((rc = upload(&r.d_sbase, h.base, "base table")) != FDD_OK) return rc;
+    if ((rc = upload(&r.d_soff, h.off, "offset table")) != FDD_OK) return rc;
+    if ((rc = upload(&r.d_sstages, stages, "stage table")) != FDD_OK) return rc;
+    r.sbf = sv;
+    r.s_CC = cc_pick;
+    r.s_Lw = h.Lw;
+    r.s_n_stages = static_cast<int32_t>(stages.size());
+    r.s_flush = std::max(1, 65535 / (seg_max * 255 * r.D));
+    r.s_work_ratio = static_cast<float>(sbf_work_ratio(p, r));
+    return FDD_OK;
+}
+
+cudaError_t launch_range_sbf(const fdd_plan* p, const RangeState& r, const fdd::DedispArgs& a, uint8_t* scratch,
+                             size_t scratch_bytes, cudaStream_t s) {
+    const fdd::DedispVariant& v = fdd::sbf_variant(r.sbf);
+    const int BD = v.bd();
+    const int64_t nr = a.n_out;
+    const int64_t Np = sbf_np(nr);
+    const int64_t slab = slab_trials(p, r, nr, BD, scratch_bytes);
+    if (slab < BD) return cudaErrorInvalidValue;  // scratch sized by sbf_scratch_bytes always holds one block
+    const int64_t n_seg = static_cast<int64_t>(r.segs.size());
+    fdd::SbfPartArgs pa{};
+    pa.in = a.in;
+    pa.pitch_bytes = a.pitch_bytes;
+    pa.n_valid = a.n_valid;
+    pa.base = r.d_sbase;
+    pa.off = r.d_soff;
+    pa.stages = r.d_sstages;
+    pa.segs = r.d_segs;
+    pa.P = reinterpret_cast<uint16_t*>(scratch);
+    pa.seg_stride = slab * Np;
+    pa.tab_stride = n_seg * slab * Np;
+    pa.Np = static_cast<int32_t>(Np);
+    pa.n_chan = p->n_chan;
+    pa.n_dm = r.n_dm;
+    pa.n_out = a.n_out;
+    pa.Lw = r.s_Lw;
+    pa.CC = r.s_CC;
+    pa.n_stages = r.s_n_stages;
+    fdd::SbfCombArgs ca{};
+    ca.P = pa.P;
+    ca.tab_stride = pa.tab_stride;
+    ca.seg_stride = pa.seg_stride;
+    ca.Np = pa.Np;
+    ca.seg_tab = r.d_segtab;
+    ca.seg_pitch = r.seg_pitch;
+    ca.series = a.series;
+    ca.stat = a.stat;
+    ca.n_sb = p->n_sb;
+    ca.n_seg = static_cast<int32_t>(n_seg);
+    ca.n_dm = r.n_dm;
+    ca.n_out = a.n_out;
+    ca.flush = r.s_flush;
+    for (int64_t i0 = 0; i0 < r.n_dm; i0 += slab) {
+        pa.i0 = static_cast<int32_t>(i0);
+        pa.n_slab = static_cast<int32_t>(std::min<int64_t>(slab, r.n_dm - i0));
+        cudaError_t e = fdd::launch_sbf_part(r.sbf, pa, p->n_tab, s);
+        if (e != cudaSuccess) return e;
+        ca.i0 = pa.i0;
+        ca.n_slab = pa.n_slab;
+        if ((e = fdd::launch_sbf_comb(ca, s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace host
+}  // namespace fdd

@@ -1,0 +1,382 @@
+// k_sbf.cu -- SB-factored dedispersion kernels.
+//
+// Every SB of a compound beam takes, channel by channel, the data of one of
+// the TABs (Sec. "Hierarchical beam forming"); on a segment of channels where
+// every SB keeps one TAB, the SB's dedispersed sum over the segment is the
+// same number as that TAB's sum over the segment.  So, with segments u,
+//     S[s][i][t] = sum_u P[tab(s, u)][u][i][t],
+//     P[k][u][i][t] = sum_{c in u} X[k][c][t + d[i][c]],
+// exactly (integer sums regrouped).  Per (trial, sample) brute force needs
+// n_sb * n_chan channel-adds; this needs n_tab * n_chan for P plus n_sb * n_seg
+// for S -- for 12 TABs, 71 SBs and 16-channel segments about 4.3x fewer.
+//
+// k_sbf_part computes P for a slab of DM trials: the brute-force block tile
+// of dedisp_tile.cuh (staged byte-shifted rows, SWAR adds), run per TAB with
+// channel stages made of whole segments, storing each segment's 16-bit sums
+// instead of summing all channels.  k_sbf_comb reads P (L1/L2-resident
+// rows, 4 samples per lane) and adds, for each SB, the rows its TABs select,
+// in 16-bit lanes folded into int32 every `flush` segments, then writes the
+// series and its moments like the brute-force epilogue.
+#include "dedisp_tile.cuh"
+
+namespace fdd {
+
+namespace {
+
+template <int E, int NW, int DPW, int WARPS, int MAXIT>
+__global__ void __launch_bounds__(WARPS * 32) k_sbf_part(const SbfPartArgs a) {
+    constexpr int NC = 4 / E;
+    constexpr int SPW = 4 / E;
+    constexpr int BD = WARPS * DPW;
+    constexpr int T = 32 * NW * SPW;
+    constexpr int NT = WARPS * 32;
+    extern __shared__ __align__(16) uint8_t smem[];
+
+    const int tab = blockIdx.z;
+    const int blk = a.i0 / BD + blockIdx.y;
+    const int Lw = a.Lw;
+    const int chunks = Lw >> 2;
+    const int slot_bytes = NC * Lw * 4;
+    uint8_t* s_rows = smem;
+    int32_t* s_off = reinterpret_cast<int32_t*>(smem + a.CC * slot_bytes);  // [CC][BD]
+
+    const int t0 = blockIdx.x * T;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t limit = a.n_valid * E;
+    const uint8_t* tab_rows = a.in + static_cast<int64_t>(tab) * a.n_chan * a.pitch_bytes;
+    const int32_t* base_blk = a.base + (int64_t)blk * a.n_chan;
+    const int32_t* off_blk = a.off + (int64_t)blk * a.n_chan * BD;
+
+    uint4 pv[MAXIT];
+    uint32_t pn[MAXIT];
+    int4 po = make_int4(0, 0, 0, 0);
+
+    auto stage_load = [&](int c0, int ncc) {
+        const int items = ncc * chunks;
+#pragma unroll
+        for (int u = 0; u < MAXIT; u++) {
+            const int it = threadIdx.x + u * NT;
+            if (it < items) {
+                const int cc = it / chunks;
+                const int m = it - cc * chunks;
+                const int c = c0 + cc;
+                const uint8_t* row = tab_rows + (int64_t)c * a.pitch_bytes;
+                const int64_t b0 = (int64_t)(t0 + base_blk[c]) * E + 16 * (int64_t)m;
+                if (b0 + 20 <= limit) {
+                    pv[u] = __ldg(reinterpret_cast<const uint4*>(row + b0));
+                    pn[u] = __ldg(reinterpret_cast<const uint32_t*>(row + b0 + 16));
+                } else {
+                    uint32_t g[5];
+#pragma unroll
+                    for (int k = 0; k < 5; k++) {
+                        uint32_t w = 0;
+#pragma unroll
+                        for (int b = 0; b < 4; b++) {
+                            const int64_t p = b0 + 4 * k + b;
+                            w |= ((p < limit) ? (uint32_t)row[p] : 0u) << (8 * b);
+                        }
+                        g[k] = w;
+                    }
+                    pv[u] = make_uint4(g[0], g[1], g[2], g[3]);
+                    pn[u] = g[4];
+                }
+            }
+        }
+        if (threadIdx.x < ncc * (BD / 4))
+            po = __ldg(reinterpret_cast<const int4*>(off_blk + (int64_t)c0 * BD) + threadIdx.x);
+    };
+
+    auto stage_store = [&](int ncc) {
+        const int items = ncc * chunks;
+#pragma unroll
+        for (int u = 0; u < MAXIT; u++) {
+            const int it = threadIdx.x + u * NT;
+            if (it < items) {
+                const int cc = it / chunks;
+                const int m = it - cc * chunks;
+                uint8_t* dst = s_rows + cc * slot_bytes + 16 * m;
+                const uint32_t g0 = pv[u].x, g1 = pv[u].y, g2 = pv[u].z, g3 = pv[u].w, g4 = pn[u];
+#pragma unroll
+                for (int q = 0; q < NC; q++) {
+                    uint4 o;
+                    o.x = __funnelshift_r(g0, g1, 8 * q * E);
+                    o.y = __funnelshift_r(g1, g2, 8 * q * E);
+                    o.z = __funnelshift_r(g2, g3, 8 * q * E);
+                    o.w = __funnelshift_r(g3, g4, 8 * q * E);
+                    *reinterpret_cast<uint4*>(dst + q * Lw * 4) = o;
+                }
+            }
+        }
+        if (threadIdx.x < ncc * (BD / 4)) {
+            const int cc = (threadIdx.x * 4) / BD;
+            const int add = cc * slot_bytes;
+            reinterpret_cast<int4*>(s_off)[threadIdx.x] = make_int4(po.x + add, po.y + add, po.z + add, po.w + add);
+        }
+    };
+
+    auto split = [](uint32_t x) -> uint32_t {
+        if constexpr (E == 1)
+            return __byte_perm(x, 0u, 0x4341);  // bytes 1,3 -> 16-bit lanes
+        else
+            return 0u;                          // uint16 lanes accumulate directly in acc_a
+    };
+
+    uint32_t acc_a[DPW][NW], acc_b[DPW][NW];
+#pragma unroll
+    for (int j = 0; j < DPW; j++)
+#pragma unroll
+        for (int k = 0; k < NW; k++) acc_a[j][k] = acc_b[j][k] = 0u;
+
+    const uint32_t s_lane32 = static_cast<uint32_t>(__cvta_generic_to_shared(s_rows)) + 4u * lane;
+    const int32_t* s_off_w = s_off + warp * DPW;
+
+    // Store the 16-bit sums of segment g and restart the accumulators.
+    auto store_segment = [&](int g) {
+#pragma unroll
+        for (int j = 0; j < DPW; j++) {
+            const int i = blk * BD + warp * DPW + j;
+            const bool valid = i < a.n_dm && i < a.i0 + a.n_slab;  // warp-uniform
+            uint16_t* row = a.P + tab * a.tab_stride + g * a.seg_stride + (int64_t)(i - a.i0) * a.Np;
+#pragma unroll
+            for (int k = 0; k < NW; k++) {
+                const int t = t0 + (lane + 32 * k) * SPW;
+                if (valid) {
+                    if constexpr (E == 1) {
+                        const uint32_t odd = acc_b[j][k];                // samples 1, 3
+                        const uint32_t even = acc_a[j][k] - (odd << 8);  // samples 0, 2
+                        *reinterpret_cast<uint2*>(row + t) =
+                            make_uint2(__byte_perm(even, odd, 0x5410), __byte_perm(even, odd, 0x7632));
+                    } else {
+                        *reinterpret_cast<uint32_t*>(row + t) = acc_a[j][k];
+                    }
+                }
+                acc_a[j][k] = 0u;
+                acc_b[j][k] = 0u;
+            }
+        }
+    };
+
+    int4 sd = __ldg(&a.stages[0]);  // first channel, channels, first segment, segments
+    stage_load(sd.x, sd.y);
+    stage_store(sd.y);
+    __syncthreads();
+
+    for (int st = 0; st < a.n_stages; st++) {
+        const int4 cur = sd;
+        const bool has_next = st + 1 < a.n_stages;
+        int4 nxt = cur;
+        if (has_next) {
+            nxt = __ldg(&a.stages[st + 1]);
+            stage_load(nxt.x, nxt.y);  // in flight during the adds below
+        }
+        for (int g = cur.z; g < cur.z + cur.w; g++) {
+            const int2 sg = __ldg(&a.segs[g]);
+            int cc = sg.x - cur.x;
+            const int cc_end = cc + sg.y;
+#pragma unroll 1
+            for (; cc + 3 < cc_end; cc += 4) {
+                int32_t og[4][DPW];
+#pragma unroll
+                for (int u = 0; u < 4; u++) detail::load_offsets<DPW>(s_off_w + (cc + u) * BD, og[u]);
+                uint32_t x[4][DPW][NW];
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+#pragma unroll
+                    for (int j = 0; j < DPW; j++) {
+                        const uint32_t ad = s_lane32 + static_cast<uint32_t>(og[u][j]);
+#pragma unroll
+                        for (int k = 0; k < NW; k++) x[u][j][k] = detail::lds32(ad + 128u * k);
+                    }
+#pragma unroll
+                for (int j = 0; j < DPW; j++)
+#pragma unroll
+                    for (int k = 0; k < NW; k++) {
+                        acc_a[j][k] = acc_a[j][k] + x[0][j][k] + x[1][j][k];
+                        acc_a[j][k] = acc_a[j][k] + x[2][j][k] + x[3][j][k];
+                        if constexpr (E == 1) {
+                            acc_b[j][k] = acc_b[j][k] + split(x[0][j][k]) + split(x[1][j][k]);
+                            acc_b[j][k] = acc_b[j][k] + split(x[2][j][k]) + split(x[3][j][k]);
+                        }
+                    }
+            }
+#pragma unroll 1
+            for (; cc < cc_end; cc++) {
+                int32_t o0[DPW];
+                detail::load_offsets<DPW>(s_off_w + cc * BD, o0);
+#pragma unroll
+                for (int j = 0; j < DPW; j++)
+#pragma unroll
+                    for (int k = 0; k < NW; k++) {
+                        const uint32_t x0 = detail::lds32(s_lane32 + static_cast<uint32_t>(o0[j]) + 128u * k);
+                        acc_a[j][k] += x0;
+                        if constexpr (E == 1) acc_b[j][k] += split(x0);
+                    }
+            }
+            store_segment(g);
+        }
+        __syncthreads();  // stage fully consumed
+        if (has_next) {
+            stage_store(nxt.y);
+            __syncthreads();
+            sd = nxt;
+        }
+    }
+}
+
+// Comb: block = CW warps x CSB SBs per warp, one DM trial, CSUB sub-tiles of
+// 128 samples (4 per lane).
+constexpr int CW = 12, CSB = 6, CSUB = 4, CT = 128;
+
+__global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const SbfCombArgs a) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i_s = blockIdx.y;
+    const int i = a.i0 + i_s;
+    const int sb0 = blockIdx.z * (CW * CSB) + warp * CSB;
+    const int nsb = min(CSB, a.n_sb - sb0);
+    if (nsb <= 0 || i >= a.n_dm) return;  // warp-uniform; no block barriers below
+    unsigned long long m1[CSB], m2[CSB];
+#pragma unroll
+    for (int j = 0; j < CSB; j++) m1[j] = m2[j] = 0ull;
+    const uint16_t* p_trial = a.P + static_cast<int64_t>(i_s) * a.Np;
+    const uint32_t tab_stride = static_cast<uint32_t>(a.tab_stride);  // < 2^31 (scratch bound)
+    const uint8_t* tabs_w = a.seg_tab + static_cast<int64_t>(sb0) * a.seg_pitch;
+
+    for (int sub = 0; sub < CSUB; sub++) {
+        const int tt = (blockIdx.x * CSUB + sub) * CT;
+        if (tt >= a.n_out) break;  // block-uniform
+        const int t = tt + 4 * lane;
+        uint32_t acc[CSB][2], tot[CSB][4];
+#pragma unroll
+        for (int j = 0; j < CSB; j++) {
+            acc[j][0] = acc[j][1] = 0u;
+            tot[j][0] = tot[j][1] = tot[j][2] = tot[j][3] = 0u;
+        }
+        auto fold = [&]() {
+#pragma unroll
+            for (int j = 0; j < CSB; j++) {
+                tot[j][0] += acc[j][0] & 0xFFFFu;
+                tot[j][1] += acc[j][0] >> 16;
+                tot[j][2] += acc[j][1] & 0xFFFFu;
+                tot[j][3] += acc[j][1] >> 16;
+                acc[j][0] = acc[j][1] = 0u;
+            }
+        };
+        int since = 0;
+        for (int u0 = 0; u0 < a.n_seg; u0 += 4) {
+            uint32_t tabs4[CSB];
+#pragma unroll
+            for (int j = 0; j < CSB; j++)
+                tabs4[j] = (j < nsb) ? __ldg(reinterpret_cast<const uint32_t*>(tabs_w + j * a.seg_pitch + u0)) : 0u;
+            const int nu = min(4, a.n_seg - u0);
+#pragma unroll
+            for (int du = 0; du < 4; du++) {
+                if (du < nu) {
+                    const uint16_t* pu = p_trial + static_cast<int64_t>(u0 + du) * a.seg_stride + t;
+#pragma unroll
+                    for (int j = 0; j < CSB; j++) {
+                        if (j < nsb) {
+                            const uint32_t k = (tabs4[j] >> (8 * du)) & 0xFFu;
+                            const uint2 v = __ldg(
+                                reinterpret_cast<const uint2*>(pu + static_cast<uint64_t>(k) * tab_stride));
+                            acc[j][0] += v.x;
+                            acc[j][1] += v.y;
+                        }
+                    }
+                    if (++since == a.flush) {
+                        fold();
+                        since = 0;
+                    }
+                }
+            }
+        }
+        fold();
+#pragma unroll
+        for (int j = 0; j < CSB; j++) {
+            if (j < nsb) {
+                int32_t* row = a.series + (static_cast<int64_t>(sb0 + j) * a.n_dm + i) * a.n_out;
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    if (t + e < a.n_out) {
+                        const uint32_t v = tot[j][e];
+                        row[t + e] = static_cast<int32_t>(v);
+                        m1[j] += v;
+                        m2[j] += static_cast<unsigned long long>(v) * v;
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < CSB; j++) {
+        unsigned long long s1 = m1[j], s2 = m2[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0 && j < nsb) {
+            const int64_t q = static_cast<int64_t>(sb0 + j) * a.n_dm + i;
+            atomicAdd(a.stat + 2 * q, s1);
+            atomicAdd(a.stat + 2 * q + 1, s2);
+        }
+    }
+}
+
+using PartFn = void (*)(const SbfPartArgs);
+
+struct Entry {
+    DedispVariant v;
+    PartFn fn;
+};
+
+#define FDD_S(E, NW, DPW, WARPS, MAXIT) {{E, NW, DPW, WARPS, MAXIT}, k_sbf_part<E, NW, DPW, WARPS, MAXIT>}
+const Entry kEntries[] = {
+    FDD_S(1, 4, 2, 8, 4),   // BD 16, T 512
+    FDD_S(1, 4, 4, 8, 4),   // BD 32, T 512
+    FDD_S(1, 2, 4, 8, 4),   // BD 32, T 256
+    FDD_S(1, 4, 2, 16, 4),  // BD 32, T 512, 512 threads
+    FDD_S(2, 4, 2, 8, 4),   // BD 16, T 256
+    FDD_S(2, 4, 4, 8, 4),   // BD 32, T 256
+    FDD_S(2, 8, 2, 8, 4),   // BD 16, T 512
+};
+#undef FDD_S
+
+}  // namespace
+
+int num_sbf_variants() { return static_cast<int>(sizeof(kEntries) / sizeof(kEntries[0])); }
+
+const DedispVariant& sbf_variant(int idx) { return kEntries[idx].v; }
+
+size_t sbf_smem_bytes(const DedispVariant& v, int Lw, int CC) {
+    return static_cast<size_t>(CC) * (4 / v.E) * Lw * 4 + static_cast<size_t>(CC) * v.bd() * 4;
+}
+
+bool sbf_cc_ok(const DedispVariant& v, int Lw, int CC, size_t smem_budget) {
+    if (CC < 1 || CC > 256) return false;
+    if (static_cast<int64_t>(CC) * (Lw / 4) > static_cast<int64_t>(v.MAXIT) * v.threads()) return false;
+    if (CC * (v.bd() / 4) > v.threads()) return false;
+    return sbf_smem_bytes(v, Lw, CC) <= smem_budget;
+}
+
+cudaError_t launch_sbf_part(int idx, const SbfPartArgs& a, int n_tab, cudaStream_t s) {
+    const Entry& e = kEntries[idx];
+    const size_t smem = sbf_smem_bytes(e.v, a.Lw, a.CC);
+    cudaError_t err = cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (err != cudaSuccess) return err;
+    const int T = e.v.tile(), BD = e.v.bd();
+    dim3 grid((a.n_out + T - 1) / T, (a.n_slab + BD - 1) / BD, n_tab);
+    e.fn<<<grid, e.v.threads(), smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+int sbf_comb_sbs_per_block() { return CW * CSB; }
+
+cudaError_t launch_sbf_comb(const SbfCombArgs& a, cudaStream_t s) {
+    const int per_block = CW * CSB;
+    const int n_valid = a.n_dm - a.i0 < a.n_slab ? a.n_dm - a.i0 : a.n_slab;
+    dim3 grid((a.n_out + CT * CSUB - 1) / (CT * CSUB), n_valid, (a.n_sb + per_block - 1) / per_block);
+    k_sbf_comb<<<grid, CW * 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace fdd

@@ -161,7 +161,8 @@ def test_arts_single_sb_full_size(fdd):
         assert len(near) > 0, p
 
 
-def test_fused_71_sb_sampled(fdd):
+@pytest.mark.parametrize("kernel", ["default", "sb_factored"])
+def test_fused_71_sb_sampled(fdd, kernel):
     import torch
     n_tab, n_chan, n_sb, n_out = 12, 1536, 71, synth.ARTS_CHUNK
     f = synth.channel_freqs(n_chan)
@@ -173,11 +174,20 @@ def test_fused_71_sb_sampled(fdd):
     x = synth.filterbank(3, n_tab, n_chan, n_in, pulses=pulses)
     sb = synth.sb_map_piecewise(3, n_sb, n_chan, n_tab).astype(np.int16)
     plan = fdd.Plan(n_tab, n_chan, n_sb, f, T_SAMP, ranges, 8.0, sb)
+    if kernel == "sb_factored":
+        v = [v for v in fdd.variants() if v["kind"] == 2 and v["bytes_per_sample"] == 1][0]
+        plan.set_config(0, v["index"])
+        assert plan.get_config(0)["work_ratio"] < 0.3
     res = plan.search(to_dev(x), n_in, n_out, cap=1 << 21, want_series=True)
     torch.cuda.synchronize()
     gpu, n = res.candidates()
     assert n == len(gpu)
     series = plan.series_views(res.series, n_out)[0]
+    # every SB at DM 0 (all delays 0) is its per-channel TAB selection summed
+    dm0 = np.zeros((n_sb, n_out), np.int64)
+    for c in range(n_chan):
+        dm0 += x[sb[:, c], c, :n_out]
+    assert (series[:, 0].cpu().numpy() == dm0).all()
     rng = np.random.default_rng(0)
     for s in sorted(set([0, 70] + rng.integers(1, 70, size=1).tolist())):
         ora, os_ = oracle_candidate_superset(x, sb[s:s + 1], f, T_SAMP, ranges, 8.0, n_out, n_in,
@@ -237,6 +247,18 @@ def test_repeat_is_deterministic(fdd):
     assert na == nb and (ca == cb).all()
 
 
+def segment_lengths(sb, cap):
+    """Lengths of the runs of channels on which every SB keeps one TAB, cut
+    at `cap` channels (the SB-factored kernel's segments)."""
+    n_chan = sb.shape[1]
+    out, c0 = [], 0
+    for c in range(1, n_chan + 1):
+        if c == n_chan or c - c0 == cap or (sb[:, c] != sb[:, c - 1]).any():
+            out.append(c - c0)
+            c0 = c
+    return out
+
+
 def variant_case():
     rng = np.random.default_rng(42)
     n_tab, n_chan, n_sb, n_out = 2, 70, 3, 1500
@@ -273,6 +295,8 @@ def test_every_kernel_variant(fdd, variant_oracle, v, cc):
     if v.get("group", 0) and cc and (cc % v["group"] or cc < v["group"]):
         pytest.skip("stage size not a multiple of the channel group")
     x, f, ranges, sb, n_in, n_out = variant_case()
+    if v["kind"] == 2 and cc and cc < max(segment_lengths(sb, 16)):
+        pytest.skip("stage size shorter than a channel segment")
     plan = fdd.Plan(x.shape[0], x.shape[1], sb.shape[0], f, T_SAMP, ranges, 4.0, sb)
     r = 0 if v["bytes_per_sample"] == 1 else 1
     plan.set_config(r, v["index"], cc)
@@ -451,3 +475,36 @@ def test_four_range_71_sb_batched_sampled(fdd):
         near = gpu[(gpu["sb"] == s_chk) & (np.abs(gpu["dm"] - p["dm"]) < 0.02 * p["dm"] + 3)
                    & (np.abs(gpu["t_native"] - p["t0"]) < 4 * p["width"] + 16)]
         assert len(near) > 0, p
+
+
+def test_sb_factored_piecewise_slabs(fdd):
+    """SB-factored kernels on a piecewise TAB table (16-channel segments) with
+    the partial-sum scratch capped so each range runs in several DM slabs;
+    every series bit-exact, candidates equal, for every SB-factored variant."""
+    import torch
+    n_tab, n_chan, n_sb, n_out = 6, 168, 20, 2000
+    f = synth.channel_freqs(n_chan)
+    ranges = [dict(dm0=0.0, ddm=1.0, n_dm=100, downsamp=1, widths=[1, 2, 8]),
+              dict(dm0=100.0, ddm=4.0, n_dm=41, downsamp=4, widths=[1, 4])]
+    sb = synth.sb_map_piecewise(9, n_sb, n_chan, n_tab).astype(np.int16)
+    sb[3, 40:47] = (sb[3, 40:47] + 1) % n_tab        # a few segments shorter than 16
+    n_in = max(int(oracle.delays(f, T_SAMP, r["dm0"], r["ddm"], r["n_dm"], r["downsamp"]).max())
+               * r["downsamp"] + n_out for r in ranges) + 5
+    pulses = [dict(tab=k % n_tab, start=t0 + oracle.delays(f, T_SAMP, dm, 1.0, 1)[0], width=w, amp=40.0)
+              for k, (t0, dm, w) in enumerate([(300, 30.0, 2), (900, 80.0, 4), (1500, 200.0, 8)])]
+    x = synth.filterbank(21, n_tab, n_chan, n_in, pulses=pulses)
+    ora, os_ = oracle_candidate_superset(x, sb, f, T_SAMP, ranges, 6.0, n_out, n_in, return_series=True)
+    dx = to_dev(x)
+    for v in [v for v in fdd.variants() if v["kind"] == 2]:
+        plan = fdd.Plan(n_tab, n_chan, n_sb, f, T_SAMP, ranges, 6.0, sb)
+        plan.set_scratch_limit(1)                 # one DM block per slab
+        r = 0 if v["bytes_per_sample"] == 1 else 1
+        plan.set_config(r, v["index"])
+        assert plan.get_config(r)["variant"] == v["index"]
+        res = plan.search(dx, n_in, n_out, want_series=True, cap=1 << 18)
+        torch.cuda.synchronize()
+        g = plan.series_views(res.series, n_out)
+        for k in range(2):
+            assert (g[k].cpu().numpy() == os_[k]).all(), (v, k)
+        gpu, n = res.candidates()
+        compare_candidates(gpu, ora, 6.0)
