@@ -267,16 +267,19 @@ def run_fdd(args):
                 except fdd.FddError:
                     pass  # variant for the other sample width
         if mode == "per_sb":
-            # the plain per-beam path: one single-SB plan per SB, searched one after another
-            cfgs = [plan.get_config(r) for r in range(len(w["ranges"]))]
+            # the plain per-beam path: one single-SB plan per SB, searched one after another, each
+            # with the configuration tuned for a single-SB plan
             plans = []
             for s_i in range(w["n_sb"]):
-                p1 = fdd.Plan(w["n_tab"], w["n_chan"], 1, f, t, w["ranges"], w["thr"], sb[s_i:s_i + 1])
-                for r, c in enumerate(cfgs):
-                    p1.set_config(r, c["variant"], c["chan_per_stage"])
-                plans.append(p1)
+                plans.append(fdd.Plan(w["n_tab"], w["n_chan"], 1, f, t, w["ranges"], w["thr"], sb[s_i:s_i + 1]))
             ws = torch.empty(plans[0].workspace_size(n_in, w["n_out"], with_series=True), dtype=torch.uint8,
                              device=dev)
+            if not args.no_autotune:
+                plans[0].autotune(tabs, n_in, w["n_out"], reps=3, workspace=ws, stream=stream)
+            cfgs = [plans[0].get_config(r) for r in range(len(w["ranges"]))]
+            for p1 in plans[1:]:
+                for r, c in enumerate(cfgs):
+                    p1.set_config(r, c["variant"], c["chan_per_stage"])
         for p_ in plans:
             p_.set_timing(True)
 
