@@ -118,9 +118,10 @@ struct SbfCombArgs {
     int32_t seg_pitch;
     int32_t* series;            // this range: [n_sb][n_dm][n_out]
     unsigned long long* stat;   // this range: [n_sb * n_dm][2]
-    int32_t n_sb, n_seg, n_dm, n_out;
+    int32_t n_sb, n_seg, n_dm, n_out, n_tab;
     int32_t i0, n_slab;
     int32_t flush;              // segments summed in 16-bit lanes between folds
+    int32_t uc;                 // segments per shared-memory chunk (sbf_comb_uc)
 };
 
 int num_sbf_variants();
@@ -131,6 +132,8 @@ bool sbf_cc_ok(const DedispVariant& v, int Lw, int CC, size_t smem_budget);
 cudaError_t launch_sbf_part(int idx, const SbfPartArgs& a, int n_tab, cudaStream_t s);
 // SBs handled by one comb block (the grid's z covers ceil(n_sb / this)).
 int sbf_comb_sbs_per_block();
+int sbf_comb_uc(int n_tab);
+size_t sbf_comb_smem_bytes(int n_tab);
 cudaError_t launch_sbf_comb(const SbfCombArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------------------

@@ -102,6 +102,8 @@ void free_sbf_tables(RangeState& r, bool geometry) {
 int configure_sbf(fdd_plan* p, RangeState& r, int sv, int CC) {
     if (sv < 0 || sv >= fdd::num_sbf_variants()) return fail(FDD_ERR_INVALID_ARG, "kernel variant out of range");
     if (p->n_sb < 2) return fail(FDD_ERR_UNSUPPORTED, "the SB-factored kernel needs at least two SBs");
+    if (fdd::sbf_comb_smem_bytes(p->n_tab) > kSmemBudget)
+        return fail(FDD_ERR_UNSUPPORTED, "too many TABs for the SB-factored kernel's shared-memory rows");
     const fdd::DedispVariant& v = fdd::sbf_variant(sv);
     if (v.E != (r.D == 1 ? 1 : 2)) return fail(FDD_ERR_INVALID_ARG, "kernel variant for the wrong sample width");
     const HostTables h = build_tables(p, r, v);
@@ -190,6 +192,8 @@ cudaError_t launch_range_sbf(const fdd_plan* p, const RangeState& r, const fdd::
     ca.n_dm = r.n_dm;
     ca.n_out = a.n_out;
     ca.flush = r.s_flush;
+    ca.n_tab = p->n_tab;
+    ca.uc = fdd::sbf_comb_uc(p->n_tab);
     for (int64_t i0 = 0; i0 < r.n_dm; i0 += slab) {
         pa.i0 = static_cast<int32_t>(i0);
         pa.n_slab = static_cast<int32_t>(std::min<int64_t>(slab, r.n_dm - i0));

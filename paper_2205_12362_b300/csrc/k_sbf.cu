@@ -223,61 +223,101 @@ __global__ void __launch_bounds__(WARPS * 32) k_sbf_part(const SbfPartArgs a) {
     }
 }
 
-// Comb: block = CW warps x CSB SBs per warp, one DM trial, CSUB sub-tiles of
-// 128 samples (4 per lane).
-constexpr int CW = 12, CSB = 6, CSUB = 4, CT = 128;
+// Comb: block = CW warps x CSB SBs per warp, one DM trial, CT = 128 samples
+// (4 per lane).  The partial rows of every TAB for UC segments at a time are
+// copied into shared memory with cp.async (double-buffered), so each row is
+// read from L2/HBM once per block and then serves every SB that selects it.
+constexpr int CW = 12, CSB = 6, CT = 128;
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ uint2 lds64(uint32_t addr) {
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
+    return v;
+}
 
 __global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const SbfCombArgs a) {
+    extern __shared__ __align__(16) uint8_t smem[];  // [2][n_tab][UC][CT] uint16
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i_s = blockIdx.y;
     const int i = a.i0 + i_s;
+    const int t0 = blockIdx.x * CT;
     const int sb0 = blockIdx.z * (CW * CSB) + warp * CSB;
-    const int nsb = min(CSB, a.n_sb - sb0);
-    if (nsb <= 0 || i >= a.n_dm) return;  // warp-uniform; no block barriers below
-    unsigned long long m1[CSB], m2[CSB];
-#pragma unroll
-    for (int j = 0; j < CSB; j++) m1[j] = m2[j] = 0ull;
-    const uint16_t* p_trial = a.P + static_cast<int64_t>(i_s) * a.Np;
-    const uint32_t tab_stride = static_cast<uint32_t>(a.tab_stride);  // < 2^31 (scratch bound)
-    const uint8_t* tabs_w = a.seg_tab + static_cast<int64_t>(sb0) * a.seg_pitch;
+    const int nsb = max(0, min(CSB, a.n_sb - sb0));  // warp-uniform; warps with none still copy
+    const int UC = a.uc;
+    const int n_chunks = (a.n_seg + UC - 1) / UC;
+    const uint32_t s_base = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    const uint32_t buf_bytes = static_cast<uint32_t>(a.n_tab) * UC * CT * 2;
+    const uint16_t* p_trial = a.P + static_cast<int64_t>(i_s) * a.Np + t0;
+    const uint8_t* tabs_w = a.seg_tab + static_cast<int64_t>(max(sb0, 0)) * a.seg_pitch;
 
-    for (int sub = 0; sub < CSUB; sub++) {
-        const int tt = (blockIdx.x * CSUB + sub) * CT;
-        if (tt >= a.n_out) break;  // block-uniform
-        const int t = tt + 4 * lane;
-        uint32_t acc[CSB][2], tot[CSB][4];
+    auto issue = [&](int ch, int buf) {
+        const int u0 = ch * UC;
+        const int nu = min(UC, a.n_seg - u0);
+        const int pieces = a.n_tab * nu * (CT / 8);  // 16-byte pieces
+        for (int idx = threadIdx.x; idx < pieces; idx += CW * 32) {
+            const int row = idx / (CT / 8), part = idx - row * (CT / 8);
+            const int k = row / nu, du = row - k * nu;
+            const uint16_t* src = p_trial + k * a.tab_stride + static_cast<int64_t>(u0 + du) * a.seg_stride + part * 8;
+            const uint32_t dst = s_base + buf * buf_bytes + static_cast<uint32_t>((k * UC + du) * CT + part * 8) * 2;
+            cp_async16(dst, src);
+        }
+        cp_async_commit();
+    };
+
+    uint32_t acc[CSB][2], tot[CSB][4];
+#pragma unroll
+    for (int j = 0; j < CSB; j++) {
+        acc[j][0] = acc[j][1] = 0u;
+        tot[j][0] = tot[j][1] = tot[j][2] = tot[j][3] = 0u;
+    }
+    auto fold = [&]() {
 #pragma unroll
         for (int j = 0; j < CSB; j++) {
+            tot[j][0] += acc[j][0] & 0xFFFFu;
+            tot[j][1] += acc[j][0] >> 16;
+            tot[j][2] += acc[j][1] & 0xFFFFu;
+            tot[j][3] += acc[j][1] >> 16;
             acc[j][0] = acc[j][1] = 0u;
-            tot[j][0] = tot[j][1] = tot[j][2] = tot[j][3] = 0u;
         }
-        auto fold = [&]() {
-#pragma unroll
-            for (int j = 0; j < CSB; j++) {
-                tot[j][0] += acc[j][0] & 0xFFFFu;
-                tot[j][1] += acc[j][0] >> 16;
-                tot[j][2] += acc[j][1] & 0xFFFFu;
-                tot[j][3] += acc[j][1] >> 16;
-                acc[j][0] = acc[j][1] = 0u;
-            }
-        };
-        int since = 0;
-        for (int u0 = 0; u0 < a.n_seg; u0 += 4) {
+    };
+
+    issue(0, 0);
+    int since = 0;
+    for (int ch = 0; ch < n_chunks; ch++) {
+        const int buf = ch & 1;
+        if (ch + 1 < n_chunks) {
+            issue(ch + 1, buf ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const int u0 = ch * UC;
+        const int nu = min(UC, a.n_seg - u0);
+        const uint32_t s_buf = s_base + buf * buf_bytes + 8u * lane;
+        for (int q = 0; q < nu; q += 4) {
             uint32_t tabs4[CSB];
 #pragma unroll
             for (int j = 0; j < CSB; j++)
-                tabs4[j] = (j < nsb) ? __ldg(reinterpret_cast<const uint32_t*>(tabs_w + j * a.seg_pitch + u0)) : 0u;
-            const int nu = min(4, a.n_seg - u0);
+                tabs4[j] = (j < nsb) ? __ldg(reinterpret_cast<const uint32_t*>(tabs_w + j * a.seg_pitch + u0 + q)) : 0u;
+            // u0 + q is a multiple of 4 when UC is (host guarantees UC % 4 == 0)
 #pragma unroll
-            for (int du = 0; du < 4; du++) {
-                if (du < nu) {
-                    const uint16_t* pu = p_trial + static_cast<int64_t>(u0 + du) * a.seg_stride + t;
+            for (int dq = 0; dq < 4; dq++) {
+                if (q + dq < nu) {
+                    const int du = q + dq;
 #pragma unroll
                     for (int j = 0; j < CSB; j++) {
                         if (j < nsb) {
-                            const uint32_t k = (tabs4[j] >> (8 * du)) & 0xFFu;
-                            const uint2 v = __ldg(
-                                reinterpret_cast<const uint2*>(pu + static_cast<uint64_t>(k) * tab_stride));
+                            const uint32_t k = (tabs4[j] >> (8 * dq)) & 0xFFu;
+                            const uint2 v = lds64(s_buf + ((k * UC + du) * CT) * 2);
                             acc[j][0] += v.x;
                             acc[j][1] += v.y;
                         }
@@ -289,35 +329,34 @@ __global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const SbfCombArgs a) {
                 }
             }
         }
-        fold();
+        __syncthreads();  // buffer free for the copy issued next iteration
+    }
+    fold();
+    const int t = t0 + 4 * lane;
 #pragma unroll
-        for (int j = 0; j < CSB; j++) {
-            if (j < nsb) {
-                int32_t* row = a.series + (static_cast<int64_t>(sb0 + j) * a.n_dm + i) * a.n_out;
+    for (int j = 0; j < CSB; j++) {
+        unsigned long long s1 = 0, s2 = 0;
+        if (j < nsb) {
+            int32_t* row = a.series + (static_cast<int64_t>(sb0 + j) * a.n_dm + i) * a.n_out;
 #pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    if (t + e < a.n_out) {
-                        const uint32_t v = tot[j][e];
-                        row[t + e] = static_cast<int32_t>(v);
-                        m1[j] += v;
-                        m2[j] += static_cast<unsigned long long>(v) * v;
-                    }
+            for (int e = 0; e < 4; e++) {
+                if (t + e < a.n_out) {
+                    const uint32_t v = tot[j][e];
+                    row[t + e] = static_cast<int32_t>(v);
+                    s1 += v;
+                    s2 += static_cast<unsigned long long>(v) * v;
                 }
             }
         }
-    }
-#pragma unroll
-    for (int j = 0; j < CSB; j++) {
-        unsigned long long s1 = m1[j], s2 = m2[j];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             s1 += __shfl_xor_sync(0xffffffffu, s1, o);
             s2 += __shfl_xor_sync(0xffffffffu, s2, o);
         }
         if (lane == 0 && j < nsb) {
-            const int64_t q = static_cast<int64_t>(sb0 + j) * a.n_dm + i;
-            atomicAdd(a.stat + 2 * q, s1);
-            atomicAdd(a.stat + 2 * q + 1, s2);
+            const int64_t qq = static_cast<int64_t>(sb0 + j) * a.n_dm + i;
+            atomicAdd(a.stat + 2 * qq, s1);
+            atomicAdd(a.stat + 2 * qq + 1, s2);
         }
     }
 }
@@ -371,11 +410,25 @@ cudaError_t launch_sbf_part(int idx, const SbfPartArgs& a, int n_tab, cudaStream
 
 int sbf_comb_sbs_per_block() { return CW * CSB; }
 
+int sbf_comb_uc(int n_tab) {
+    // two buffers of n_tab x UC rows of CT uint16 in at most 64 KB; UC a multiple of 4
+    int uc = (64 * 1024) / (2 * n_tab * CT * 2) / 4 * 4;
+    return uc < 4 ? 4 : (uc > 16 ? 16 : uc);
+}
+
+size_t sbf_comb_smem(int n_tab, int uc) { return 2ull * n_tab * uc * CT * 2; }
+
+size_t sbf_comb_smem_bytes(int n_tab) { return sbf_comb_smem(n_tab, sbf_comb_uc(n_tab)); }
+
 cudaError_t launch_sbf_comb(const SbfCombArgs& a, cudaStream_t s) {
     const int per_block = CW * CSB;
     const int n_valid = a.n_dm - a.i0 < a.n_slab ? a.n_dm - a.i0 : a.n_slab;
-    dim3 grid((a.n_out + CT * CSUB - 1) / (CT * CSUB), n_valid, (a.n_sb + per_block - 1) / per_block);
-    k_sbf_comb<<<grid, CW * 32, 0, s>>>(a);
+    const size_t smem = sbf_comb_smem(a.n_tab, a.uc);
+    cudaError_t err = cudaFuncSetAttribute(k_sbf_comb, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(smem));
+    if (err != cudaSuccess) return err;
+    dim3 grid((a.n_out + CT - 1) / CT, n_valid, (a.n_sb + per_block - 1) / per_block);
+    k_sbf_comb<<<grid, CW * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
