@@ -328,7 +328,7 @@ def run_fdd(args):
         per_step = {}
         for p_ in (plans if mode != "graph" else []):
             st = p_.stage_times()
-            launches += len(st)
+            launches += p_.last_launches()
             for name, r, ms in st:
                 key = "%s[%d]" % (name, r)
                 per_step[key] = per_step.get(key, 0.0) + ms
@@ -340,11 +340,13 @@ def run_fdd(args):
     if mode == "graph":
         # graphs carry no stage events: the kernels' own times come from the
         # same batched launches run directly, right after the timed loop
-        launches = (3 + int(any(r["downsamp"] > 1 for r in w["ranges"]))) * args.steps
-        for _ in range(min(args.steps, 20)):
+        launches = 0
+        for k in range(min(args.steps, 20)):
             flush.zero_()
             plan.search_batch([job], w["n_out"], stream=stream)
             stream.synchronize()
+            if k == 0:
+                launches = plan.last_launches() * args.steps   # the graph replays these kernels
             for name, r, ms in plan.stage_times():
                 stage_ms.setdefault("%s[%d]" % (name, r), []).append(ms)
     if dist:
@@ -391,18 +393,24 @@ def run_fdd(args):
     peak = N_SM * INT_LANES_PER_SM * ADDS_PER_LANE_OP * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
     achieved = adds_launch / (ded_ms / 1e3) / 1e12 if ded_ms else None
     cfgs = [plan.get_config(r) for r in range(len(w["ranges"]))] if mode in ("plain", "per_sb") else []
-    n_brute = sum(1 for v in fdd.variants() if v["group"] == 0)
+    kinds = {v["index"]: v["kind"] for v in fdd.variants()}
+    kind_names = {0: "k_dedisp", 1: "k_dedisp_fact", 2: "k_sbf"}
     if mode in ("batched", "graph"):
-        kname = "k_batch"
+        sbf_batch = plan.batch_config()["variant"] == fdd.FDD_BATCH_SB_FACTORED
+        kname = "k_sbf" if sbf_batch else "k_batch"
+        if sbf_batch:
+            cfgs = [plan.get_config(r) for r in range(len(w["ranges"]))]
     else:
-        kname = "k_dedisp_fact" if cfgs and cfgs[0]["variant"] >= n_brute else "k_dedisp"
+        kname = kind_names[kinds[cfgs[0]["variant"]]] if cfgs else "k_dedisp"
     ratio = float(np.mean([c["work_ratio"] for c in cfgs])) if cfgs else 1.0
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s",
             "frac": (achieved / peak) if achieved else None, "traffic": profile_traffic(kname, args.workload),
             "kernel": kname, "units_per_launch": adds_launch,
             "method_adds_per_launch": adds_launch * ratio,
             "method_note": "achieved counts brute-force channel-adds; the configured kernel performs "
-                           "method_adds_per_launch integer adds (pattern-factored kernels reuse partial sums)",
+                           "method_adds_per_launch integer adds (the pattern-factored kernel reuses partial sums "
+                           "across DM trials, the SB-factored kernels (k_sbf_part + k_sbf_comb) reuse TAB x "
+                           "segment partial sums across SBs)",
             "peak_basis": "148 SM x 128 INT32 lanes x 2 adds/IADD3 x 2032 MHz (derived; no measured INT peak)",
             "peak_at_sampled_clock": (peak * sm_mhz / SM_MAX_MHZ_NOMINAL) if sm_mhz else None,
             "avg_launch_ms": ded_ms}

@@ -263,9 +263,15 @@ typedef struct {
     int32_t* d_series;        /* NULL, or fdd_series_size() bytes for this job's series */
 } fdd_job;
 
+/* Batch variant value selecting SB-factored mode: instead of the persistent
+ * launches, every job's ranges run their SB-factored kernels (2 launches per
+ * DM slab per range per job), with each range's SB-factored configuration
+ * (set where a range has none).  Plans with >= 2 SBs only. */
+#define FDD_BATCH_SB_FACTORED 1000
+
 /* Prepare the plan's batched tables for chunks of n_out native samples with
  * persistent-kernel variant `variant` (-1: keep the current, possibly tuned,
- * configuration; variant 0 if none).
+ * configuration; variant 0 if none; FDD_BATCH_SB_FACTORED: SB-factored mode).
  * Allocates and synchronises; must precede any capture of fdd_search_batch.
  * Errors: UNSUPPORTED (more than FDD_MAX_RANGES ranges or 4 distinct D). */
 int fdd_batch_prepare(fdd_plan* plan, int64_t n_out, int32_t variant);
@@ -279,13 +285,16 @@ int fdd_batch_prepare(fdd_plan* plan, int64_t n_out, int32_t variant);
  * one plan must not overlap on the GPU (they share the work counter). */
 int fdd_search_batch(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int64_t n_out, fdd_stream_t stream);
 
-/* Time every persistent variant on these jobs (`reps` batches each), keep
- * the fastest.  Synchronous. */
+/* Time every persistent variant on these jobs (`reps` batches each) and, for
+ * plans with >= 2 SBs, SB-factored mode with each range's SB-factored
+ * variant chosen greedily; keep the fastest.  Synchronous.  Ranges keep
+ * their previous per-range configuration unless SB-factored mode wins. */
 int fdd_batch_autotune(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int64_t n_out, int32_t reps,
                        fdd_stream_t stream);
 
 /* Current persistent configuration: variant, resident grid, threads per
- * block, DM trials per block, tuned batch time (ms, 0 if untuned). */
+ * block, DM trials per block, tuned batch time (ms, 0 if untuned).  In
+ * SB-factored mode: variant FDD_BATCH_SB_FACTORED, grid/threads/dm 0. */
 int fdd_batch_config(const fdd_plan* plan, int32_t* variant, int32_t* grid, int32_t* threads,
                      int32_t* dm_per_block, float* tuned_ms);
 
@@ -450,6 +459,10 @@ int fdd_cluster_workspace_size(int64_t cap_in, size_t* bytes);
 int fdd_cluster(const fdd_candidate* d_in, const uint64_t* d_in_count, int64_t cap_in, void* d_workspace,
                 size_t workspace_bytes, fdd_candidate* d_out, int64_t cap_out, uint64_t* d_out_count,
                 fdd_stream_t stream);
+
+/* Number of kernels the last fdd_search or fdd_search_batch on this plan
+ * enqueued (graph launches replay the last captured batch's kernels). */
+int fdd_plan_last_launches(const fdd_plan* plan, int64_t* n);
 
 /* Cap (bytes) on the scratch the SB-factored kernel keeps in the search
  * workspace for its partial sums (0 = default, 4 GiB).  The partials of a

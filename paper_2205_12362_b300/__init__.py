@@ -160,6 +160,7 @@ def _lib_raw():
     L.fdd_sort_candidates.argtypes = [_P, _I64]
     L.fdd_variant_kind.argtypes = [_I32, ctypes.POINTER(_I32)]
     L.fdd_plan_set_scratch_limit.argtypes = [_P, _I64]
+    L.fdd_plan_last_launches.argtypes = [_P, ctypes.POINTER(_I64)]
     L.fdd_cluster_workspace_size.argtypes = [_I64, ctypes.POINTER(_SZ)]
     L.fdd_cluster.argtypes = [_P, _P, _I64, _P, _SZ, _P, _I64, _P, _P]
     _lib = L
@@ -295,6 +296,7 @@ class Graph:
 
 
 FDD_ERR_SEQUENCE = -8
+FDD_BATCH_SB_FACTORED = 1000
 FDD_ERR_BUSY = -9
 
 
@@ -561,6 +563,13 @@ class Plan:
     def max_delay(self):
         v = _I64()
         _check(_lib_raw().fdd_plan_max_delay(self._h, ctypes.byref(v)), "fdd_plan_max_delay")
+        return int(v.value)
+
+    def last_launches(self):
+        """Kernels enqueued by the last search / batched search (include/fdd.h:
+        fdd_plan_last_launches)."""
+        v = _I64()
+        _check(_lib_raw().fdd_plan_last_launches(self._h, ctypes.byref(v)), "fdd_plan_last_launches")
         return int(v.value)
 
     def set_scratch_limit(self, nbytes):

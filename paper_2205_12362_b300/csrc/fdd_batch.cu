@@ -46,10 +46,18 @@ int prepare(fdd_plan* p, int64_t n_out, int variant, bool big_stages = false) {
     int rc = batch_eligible(p);
     if (rc != FDD_OK) return rc;
     if (variant < 0) {  // keep the current (possibly tuned) configuration
-        variant = p->batch.variant >= 0 ? p->batch.variant : 0;
+        variant = p->batch.sbf ? FDD_BATCH_SB_FACTORED : (p->batch.variant >= 0 ? p->batch.variant : 0);
         big_stages = p->batch.big_stages;
     }
-    if (variant >= fdd::num_persistent_variants()) return fail(FDD_ERR_INVALID_ARG, "batch variant out of range");
+    const bool sbf = variant == FDD_BATCH_SB_FACTORED;
+    if (sbf) {
+        // every range through its SB-factored configuration (the first fitting one if it has none)
+        for (RangeState& r : p->ranges)
+            if (r.sbf < 0 && (rc = configure_sbf_default(p, r)) != FDD_OK) return rc;
+        variant = 0;  // persistent tables are still built for the descriptors; no persistent launch runs
+    } else if (variant >= fdd::num_persistent_variants()) {
+        return fail(FDD_ERR_INVALID_ARG, "batch variant out of range");
+    }
     BatchState& b = p->batch;
     free_batch(b);
     if (!b.d_counter) {
@@ -97,7 +105,7 @@ int prepare(fdd_plan* p, int64_t n_out, int variant, bool big_stages = false) {
         R.Lw = h.Lw;
         R.CC = CC;
         R.item_off = items[E - 1];
-        items[E - 1] += static_cast<int64_t>(p->n_sb) * R.n_blk * R.n_tiles;
+        if (!sbf) items[E - 1] += static_cast<int64_t>(p->n_sb) * R.n_blk * R.n_tiles;
         R.series_elem_off = static_cast<int64_t>(L.series_r[ri]);
         R.series_off = static_cast<int64_t>(L.stat_r[ri]);
         R.dm0 = r.dm0;
@@ -129,6 +137,7 @@ int prepare(fdd_plan* p, int64_t n_out, int variant, bool big_stages = false) {
         b.grid_e[E - 1] = per_sm * sms;
     }
     b.variant = variant;
+    b.sbf = sbf;
     b.big_stages = big_stages;
     b.series_per_job = static_cast<int64_t>(L.stat_bytes / (2 * sizeof(unsigned long long)));
     b.n_out = n_out;
@@ -136,7 +145,22 @@ int prepare(fdd_plan* p, int64_t n_out, int variant, bool big_stages = false) {
     return FDD_OK;
 }
 
-int fill_params(const fdd_plan* p, const fdd_job* jobs, int32_t n_jobs, int64_t n_out, fdd::BatchParams& P) {
+// Per (job, range) arguments of the SB-factored launches of a batch.
+struct SbfJobRange {
+    fdd::DedispArgs a;
+    uint8_t* scratch;
+    size_t scratch_bytes;
+    int range;
+};
+
+struct BatchLaunch {
+    fdd::BatchParams P;
+    std::vector<SbfJobRange> sbf;
+};
+
+int fill_params(const fdd_plan* p, const fdd_job* jobs, int32_t n_jobs, int64_t n_out, BatchLaunch& BL) {
+    fdd::BatchParams& P = BL.P;
+    BL.sbf.clear();
     if (!jobs || n_jobs < 1 || n_jobs > fdd::kMaxBatchJobs) return fail(FDD_ERR_INVALID_ARG, "n_jobs outside [1, FDD_MAX_BATCH_JOBS]");
     const BatchState& b = p->batch;
     P = fdd::BatchParams{};
@@ -175,13 +199,35 @@ int fill_params(const fdd_plan* p, const fdd_job* jobs, int32_t n_jobs, int64_t 
         B.cap = J.cap;
         B.count = reinterpret_cast<unsigned long long*>(J.d_count);
         B.t_offset = J.t_offset_native;
+        if (!b.sbf) continue;
+        for (size_t ri = 0; ri < p->ranges.size(); ri++) {
+            const RangeState& r = p->ranges[ri];
+            const fdd::BatchRange& R = b.h_ranges[ri];
+            if (R.n_out == 0) continue;
+            SbfJobRange q{};
+            q.range = static_cast<int>(ri);
+            q.a.in = R.ds_index < 0 ? B.tabs : reinterpret_cast<const uint8_t*>(B.ds[R.ds_index]);
+            q.a.pitch_bytes = R.ds_index < 0 ? B.tab_pitch : B.ds_pitch[R.ds_index] * 2;
+            q.a.n_valid = B.n_in / r.D;
+            q.a.series = B.series + R.series_elem_off;
+            q.a.stat = B.stat + 2 * R.series_off;
+            q.a.n_chan = p->n_chan;
+            q.a.n_dm = r.n_dm;
+            q.a.n_out = R.n_out;
+            q.a.n_sb = p->n_sb;
+            q.scratch = ws + L.sbf;
+            q.scratch_bytes = L.sbf_bytes;
+            BL.sbf.push_back(q);
+        }
     }
     return FDD_OK;
 }
 
-// The four launches of a batch, each inside a stage-timing event pair when
+// The launches of a batch, each kind inside a stage-timing event pair when
 // the plan's timing is on (the events become graph nodes under capture).
-int enqueue(fdd_plan* p, const fdd::BatchParams& P, cudaStream_t s) {
+int enqueue(fdd_plan* p, const BatchLaunch& BL, cudaStream_t s) {
+    const fdd::BatchParams& P = BL.P;
+    int64_t n_launch = 1 + (P.n_ds > 0 ? 1 : 0) + 1;  // prep, downsample, boxcar
     int wmax = 1;
     for (const RangeState& r : p->ranges) wmax = std::max(wmax, r.wmax);
     stage_reset(p);
@@ -194,8 +240,17 @@ int enqueue(fdd_plan* p, const fdd::BatchParams& P, cudaStream_t s) {
         if ((e = fdd::launch_batch_downsample(P, s)) != cudaSuccess) return cuda_fail(e, "batch downsample launch");
         if ((e = stage_end(p, s)) != cudaSuccess) return cuda_fail(e, "timing event");
     }
+    if (!BL.sbf.empty()) {
+        if ((e = stage_begin(p, 1, -1, s)) != cudaSuccess) return cuda_fail(e, "timing event");
+        for (const SbfJobRange& q : BL.sbf)
+            if ((e = launch_range_sbf(p, p->ranges[q.range], q.a, q.scratch, q.scratch_bytes, s, &n_launch)) !=
+                cudaSuccess)
+                return cuda_fail(e, "SB-factored dedispersion launch");
+        if ((e = stage_end(p, s)) != cudaSuccess) return cuda_fail(e, "timing event");
+    }
     for (int E = 1; E <= 2; E++) {
         if (p->batch.items_per_job_e[E - 1] == 0) continue;
+        n_launch++;
         if ((e = stage_begin(p, 1, -E, s)) != cudaSuccess) return cuda_fail(e, "timing event");
         if ((e = fdd::launch_dedisp_persistent(p->batch.variant, E, P, p->batch.grid_e[E - 1], p->batch.smem_e[E - 1],
                                                s)) != cudaSuccess)
@@ -205,6 +260,7 @@ int enqueue(fdd_plan* p, const fdd::BatchParams& P, cudaStream_t s) {
     if ((e = stage_begin(p, 2, -1, s)) != cudaSuccess) return cuda_fail(e, "timing event");
     if ((e = fdd::launch_boxcar_batch(P, wmax, p->thr, s)) != cudaSuccess) return cuda_fail(e, "batch boxcar launch");
     if ((e = stage_end(p, s)) != cudaSuccess) return cuda_fail(e, "timing event");
+    p->last_launches = n_launch;
     return FDD_OK;
 }
 
@@ -221,7 +277,7 @@ struct fdd_graph {
 
 namespace {
 
-int capture(fdd_graph* g, const fdd::BatchParams& P, cudaGraph_t* out) {
+int capture(fdd_graph* g, const BatchLaunch& P, cudaGraph_t* out) {
     cudaError_t e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
     // Events recorded under capture only order nodes; they carry no timestamps,
@@ -261,7 +317,7 @@ int fdd_search_batch(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int64_
         const int rc = prepare(plan, n_out, plan->batch.variant, plan->batch.big_stages);
         if (rc != FDD_OK) return rc;
     }
-    fdd::BatchParams P;
+    BatchLaunch P;
     const int rc = fill_params(plan, jobs, n_jobs, n_out, P);
     if (rc != FDD_OK) return rc;
     return enqueue(plan, P, s);
@@ -287,7 +343,7 @@ int fdd_batch_autotune(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int6
         const int v = vb >> 1;
         const bool big = (vb & 1) != 0;
         if (prepare(plan, n_out, v, big) != FDD_OK) continue;  // variant does not fit this plan
-        fdd::BatchParams P;
+        BatchLaunch P;
         if ((rc = fill_params(plan, jobs, n_jobs, n_out, P)) != FDD_OK) break;
         if ((rc = enqueue(plan, P, s)) != FDD_OK) break;  // warm-up
         cudaEventRecord(ev0, s);
@@ -313,6 +369,58 @@ int fdd_batch_autotune(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int6
             best_big = big;
         }
     }
+    // SB-factored mode: per range, greedily, the fastest SB-factored variant (whole batch timed)
+    if (rc == FDD_OK && plan->n_sb >= 2) {
+        std::vector<std::pair<int, int>> saved;
+        for (const RangeState& r : plan->ranges) saved.emplace_back(range_config_index(r), range_config_cc(r));
+        bool ok = true;
+        for (RangeState& r : plan->ranges)
+            if (r.sbf < 0 && configure_sbf_default(plan, r) != FDD_OK) ok = false;
+        float sbf_ms = 1e30f;
+        for (size_t ri = 0; ok && ri < plan->ranges.size() && rc == FDD_OK; ri++) {
+            RangeState& r = plan->ranges[ri];
+            int keep = r.sbf, keep_cc = r.s_CC;
+            float keep_ms = 1e30f;
+            for (int sv = 0; sv < fdd::num_sbf_variants() && rc == FDD_OK; sv++) {
+                if (fdd::sbf_variant(sv).E != (r.D == 1 ? 1 : 2)) continue;
+                for (int cc : {16, 32, 64}) {
+                    if (configure_sbf(plan, r, sv, cc) != FDD_OK) continue;
+                    if (prepare(plan, n_out, FDD_BATCH_SB_FACTORED) != FDD_OK) continue;
+                    BatchLaunch P;
+                    if ((rc = fill_params(plan, jobs, n_jobs, n_out, P)) != FDD_OK) break;
+                    if ((rc = enqueue(plan, P, s)) != FDD_OK) break;
+                    cudaEventRecord(ev0, s);
+                    for (int k = 0; k < reps && rc == FDD_OK; k++) rc = enqueue(plan, P, s);
+                    cudaEventRecord(ev1, s);
+                    if (rc != FDD_OK) break;
+                    if ((e = cudaEventSynchronize(ev1)) != cudaSuccess) {
+                        rc = cuda_fail(e, "batch tuning");
+                        break;
+                    }
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, ev0, ev1);
+                    ms /= reps;
+                    if (std::getenv("FDD_TUNE_VERBOSE"))
+                        std::fprintf(stderr, "fdd batch tune: range %zu SB-factored variant %d cc %d: %.4f ms\n", ri,
+                                     sv, cc, ms);
+                    if (ms < keep_ms) {
+                        keep_ms = ms;
+                        keep = sv;
+                        keep_cc = cc;
+                    }
+                }
+            }
+            if (rc == FDD_OK && configure_sbf(plan, r, keep, keep_cc) != FDD_OK) ok = false;
+            sbf_ms = keep_ms;
+        }
+        if (rc == FDD_OK && ok && sbf_ms < best_ms) {
+            best_ms = sbf_ms;
+            best = FDD_BATCH_SB_FACTORED;
+        } else {
+            for (size_t ri = 0; ri < plan->ranges.size(); ri++)  // put the per-range configuration back
+                if (saved[ri].first >= 0) restore_range_config(plan, plan->ranges[ri], saved[ri].first, saved[ri].second);
+        }
+    }
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
     if (rc != FDD_OK) return rc;
@@ -328,6 +436,14 @@ int fdd_batch_config(const fdd_plan* plan, int32_t* variant, int32_t* grid, int3
     const BatchState& b = plan->batch;
     if (b.variant < 0) return fail(FDD_ERR_INVALID_ARG, "batch not prepared");
     const fdd::PersistentVariant& pv = fdd::persistent_variant(b.variant);
+    if (b.sbf) {
+        if (variant) *variant = FDD_BATCH_SB_FACTORED;
+        if (grid) *grid = 0;
+        if (threads) *threads = 0;
+        if (dm_per_block) *dm_per_block = 0;
+        if (tuned_ms) *tuned_ms = b.tuned_ms;
+        return FDD_OK;
+    }
     if (variant) *variant = b.variant;
     if (grid) *grid = b.grid_e[0] ? b.grid_e[0] : b.grid_e[1];
     if (threads) *threads = pv.threads();
@@ -343,7 +459,7 @@ int fdd_graph_create(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int64_
         const int rc = prepare(plan, n_out, plan->batch.variant, plan->batch.big_stages);
         if (rc != FDD_OK) return rc;
     }
-    fdd::BatchParams P;
+    BatchLaunch P;
     int rc = fill_params(plan, jobs, n_jobs, n_out, P);
     if (rc != FDD_OK) return rc;
     fdd_graph* g = new (std::nothrow) fdd_graph();
@@ -371,7 +487,7 @@ int fdd_graph_create(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int64_
 int fdd_graph_update(fdd_graph* g, const fdd_job* jobs, int32_t n_jobs) {
     if (!g || n_jobs != g->n_jobs) return fail(FDD_ERR_INVALID_ARG, "graph update needs the same number of jobs");
     if (g->plan->batch.n_out != g->n_out) return fail(FDD_ERR_INVALID_ARG, "plan re-prepared for another n_out");
-    fdd::BatchParams P;
+    BatchLaunch P;
     int rc = fill_params(g->plan, jobs, n_jobs, g->n_out, P);
     if (rc != FDD_OK) return rc;
     cudaGraph_t fresh = nullptr;

@@ -311,8 +311,9 @@ int range_variant_index(const RangeState& r) {
 
 // Dedispersion of one range with whichever kernel it is configured for.
 cudaError_t launch_range(const fdd_plan* p, const RangeState& r, const fdd::DedispArgs& a, const Layout& L,
-                         uint8_t* ws, cudaStream_t s) {
-    if (r.sbf >= 0) return launch_range_sbf(p, r, a, ws + L.sbf, L.sbf_bytes, s);
+                         uint8_t* ws, cudaStream_t s, int64_t* launches = nullptr) {
+    if (r.sbf >= 0) return launch_range_sbf(p, r, a, ws + L.sbf, L.sbf_bytes, s, launches);
+    if (launches) *launches += 1;
     return launch_range_dedisp(r, a, s);
 }
 
@@ -352,6 +353,14 @@ fdd::DedispArgs dedisp_args(const fdd_plan* plan, const RangeState& r, size_t ri
 
 
 }  // namespace
+
+int fdd::host::range_config_index(const RangeState& r) { return range_variant_index(r); }
+
+int fdd::host::range_config_cc(const RangeState& r) { return r.sbf >= 0 ? r.s_CC : (r.fact >= 0 ? r.f_CC : r.CC); }
+
+int fdd::host::restore_range_config(fdd_plan* p, RangeState& r, int variant, int CC) {
+    return configure_range(p, r, variant, CC);
+}
 
 namespace fdd {
 bool plan_timing_enabled(const fdd_plan* plan) { return plan && plan->timing; }
@@ -573,7 +582,10 @@ int fdd_search(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitc
     e = cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(count)");
 
+    int64_t n_launch = 0;
+    plan->last_launches = 0;
     for (size_t k = 0; k < plan->ds_factors.size(); k++) {
+        n_launch++;
         if ((e = stage_begin(0, plan->ds_factors[k])) != cudaSuccess) return cuda_fail(e, "timing event");
         e = fdd::launch_downsample(d_tabs, static_cast<int64_t>(plan->n_tab) * plan->n_chan, n_in, pitch,
                                    plan->ds_factors[k], reinterpret_cast<uint16_t*>(ws + L.ds_off[k]),
@@ -588,7 +600,7 @@ int fdd_search(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitc
         if (nr == 0) continue;
         const fdd::DedispArgs a = dedisp_args(plan, r, ri, L, d_tabs, pitch, ws, series, stat, n_in, n_out);
         if ((e = stage_begin(1, static_cast<int>(ri))) != cudaSuccess) return cuda_fail(e, "timing event");
-        e = launch_range(plan, r, a, L, ws, s);
+        e = launch_range(plan, r, a, L, ws, s, &n_launch);
         if (e != cudaSuccess) return cuda_fail(e, "dedispersion launch");
         if ((e = stage_end()) != cudaSuccess) return cuda_fail(e, "timing event");
 
@@ -616,8 +628,16 @@ int fdd_search(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitc
         if ((e = stage_begin(2, static_cast<int>(ri))) != cudaSuccess) return cuda_fail(e, "timing event");
         e = fdd::launch_boxcar(b, s);
         if (e != cudaSuccess) return cuda_fail(e, "boxcar launch");
+        n_launch++;
         if ((e = stage_end()) != cudaSuccess) return cuda_fail(e, "timing event");
     }
+    plan->last_launches = n_launch;
+    return FDD_OK;
+}
+
+int fdd_plan_last_launches(const fdd_plan* plan, int64_t* n) {
+    if (!plan || !n) return fail(FDD_ERR_INVALID_ARG, "null argument");
+    *n = plan->last_launches;
     return FDD_OK;
 }
 

@@ -54,6 +54,7 @@ struct BatchRangeTables {
 
 struct BatchState {
     int variant = -1;                      // persistent kernel variant
+    bool sbf = false;                      // every range through its SB-factored configuration instead
     bool big_stages = false;               // channel stages sized to the full shared-memory budget
     int64_t n_out = -1;                    // chunk length the tables below were prepared for
     std::vector<BatchRangeTables> tables;  // per range
@@ -85,6 +86,7 @@ struct fdd_plan {
     std::vector<cudaEvent_t> ev;          // 2 per stage, grown on demand
     std::vector<int32_t> st_kind, st_range;
     BatchState batch;
+    int64_t last_launches = 0;            // kernels enqueued by the last search / batched search
 };
 
 namespace fdd {
@@ -142,8 +144,16 @@ int configure_sbf(fdd_plan* p, RangeState& r, int sv, int CC);
 void free_sbf_tables(RangeState& r, bool geometry);
 // Adds per brute-force add of the SB-factored kernel for range r.
 double sbf_work_ratio(const fdd_plan* p, const RangeState& r);
+// Enqueues 2 launches per DM slab; *launches (if given) receives their number.
 cudaError_t launch_range_sbf(const fdd_plan* p, const RangeState& r, const fdd::DedispArgs& a, uint8_t* scratch,
-                             size_t scratch_bytes, cudaStream_t s);
+                             size_t scratch_bytes, cudaStream_t s, int64_t* launches = nullptr);
+// Global variant index / channels per stage of range r's current configuration,
+// and re-applying such a pair (fdd_plan.cu).
+int range_config_index(const RangeState& r);
+int range_config_cc(const RangeState& r);
+int restore_range_config(fdd_plan* p, RangeState& r, int variant, int CC);
+// First SB-factored variant that fits range r (CC = 0), configured; error if none.
+int configure_sbf_default(fdd_plan* p, RangeState& r);
 
 int check_search_args(const fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitch, int64_t n_out,
                       const void* d_workspace, const void* d_series);

@@ -151,8 +151,17 @@ int configure_sbf(fdd_plan* p, RangeState& r, int sv, int CC) {
     return FDD_OK;
 }
 
+int configure_sbf_default(fdd_plan* p, RangeState& r) {
+    int rc = fail(FDD_ERR_UNSUPPORTED, "no SB-factored variant fits this range");
+    for (int sv = 0; sv < fdd::num_sbf_variants(); sv++) {
+        if (fdd::sbf_variant(sv).E != (r.D == 1 ? 1 : 2)) continue;
+        if ((rc = configure_sbf(p, r, sv, 0)) == FDD_OK) return FDD_OK;
+    }
+    return rc;
+}
+
 cudaError_t launch_range_sbf(const fdd_plan* p, const RangeState& r, const fdd::DedispArgs& a, uint8_t* scratch,
-                             size_t scratch_bytes, cudaStream_t s) {
+                             size_t scratch_bytes, cudaStream_t s, int64_t* launches) {
     const fdd::DedispVariant& v = fdd::sbf_variant(r.sbf);
     const int BD = v.bd();
     const int64_t nr = a.n_out;
@@ -202,6 +211,7 @@ cudaError_t launch_range_sbf(const fdd_plan* p, const RangeState& r, const fdd::
         ca.i0 = pa.i0;
         ca.n_slab = pa.n_slab;
         if ((e = fdd::launch_sbf_comb(ca, s)) != cudaSuccess) return e;
+        if (launches) *launches += 2;
     }
     return cudaSuccess;
 }

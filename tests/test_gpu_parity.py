@@ -355,7 +355,7 @@ def batch_case(seed, n_in_extra):
     return x, f, ranges, sb, n_in, n_out
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 1000])   # 1000: FDD_BATCH_SB_FACTORED
 def test_batched_equals_single(fdd, variant):
     import torch
     cases = [batch_case(s, e) for s, e in [(0, 0), (1, 7), (2, 33)]]
@@ -385,12 +385,13 @@ def test_batched_equals_single(fdd, variant):
     compare_candidates(res[2].candidates()[0], ora, 5.0)
 
 
-def test_batch_graph_and_update(fdd):
+@pytest.mark.parametrize("variant", [-1, 1000])
+def test_batch_graph_and_update(fdd, variant):
     import torch
     cases = [batch_case(s, 0) for s in (3, 4)]
     x0, f, ranges, sb, n_in, n_out = cases[0]
     plan = fdd.Plan(x0.shape[0], x0.shape[1], sb.shape[0], f, T_SAMP, ranges, 5.0, sb)
-    plan.batch_prepare(n_out)
+    plan.batch_prepare(n_out, variant)
     dxs = [to_dev(c[0]) for c in cases]
     jobs = [plan.make_job(dx, c[4], n_out, t_offset=7, want_series=True) for dx, c in zip(dxs, cases)]
     ref = [plan.search(dx, c[4], n_out, t_offset=7, want_series=True) for dx, c in zip(dxs, cases)]
@@ -431,7 +432,8 @@ def test_batch_autotune_keeps_parity(fdd):
     assert torch.equal(res.series, ref.series)
 
 
-def test_four_range_71_sb_batched_sampled(fdd):
+@pytest.mark.parametrize("variant", [-1, 1000])
+def test_four_range_71_sb_batched_sampled(fdd, variant):
     """The 4-range 0-5000 plan over 71 SBs at full size, in the batched
     launch configuration the benchmark and serving loop use; one SB checked
     against the oracle on sampled series of every range and on all its
@@ -455,7 +457,7 @@ def test_four_range_71_sb_batched_sampled(fdd):
                    amp=synth.pulse_amplitude(p["snr"], n_chan, p["width"])) for p in prm for t in tabs_of_sb]
     x = synth.filterbank(4, n_tab, n_chan, n_in, pulses=pulses)
     dx = to_dev(x)
-    plan.batch_prepare(n_out)
+    plan.batch_prepare(n_out, variant)
     job = plan.make_job(dx, n_in, n_out, cap=1 << 22, want_series=True)
     res = plan.search_batch([job], n_out)[0]
     torch.cuda.synchronize()
