@@ -17,10 +17,17 @@
 // B_w(t) - w*m0 = P[t+w] - P[t] exactly.  Only the final
 // (Bc - w*(mu - m0)) * 1/(sigma sqrt(w)) is FP32.
 //
-// One block per series; tiles of 1024 outputs plus a (wmax-1) halo are
-// staged in shared memory and prefix-summed with warp shuffles.  Lanes of a
-// warp hold consecutive t for one width, so __ballot_sync + __popc give each
-// warp one atomicAdd on the global counter per width with any candidate.
+// One block per series; tiles of 4096 outputs plus a (wmax-1) halo are
+// staged in shared memory and prefix-summed with warp shuffles.  Every
+// (t, w) is first tested in integers, Bc > tau_w, with tau_w a bound a little
+// below the exact threshold crossing (thr / scale_w + offs_w, lowered by a
+// margin far larger than FP32 rounding), so almost every sample costs one
+// shared load, one subtraction and one compare per width.  Only warps where
+// some lane passes evaluate the FP32 S/N -- the same expression as always --
+// and the exact snr > thr, so the candidates are unchanged by the filter.
+// Lanes of a warp hold consecutive t for one width, so __ballot_sync + __popc
+// give each warp one atomicAdd on the global counter per width with any
+// candidate.
 #pragma once
 
 #include "fdd_internal.cuh"
@@ -29,8 +36,8 @@ namespace fdd {
 namespace detail {
 
 constexpr int kThreads = 256;
-constexpr int kTile = 1024;
-constexpr int kMaxSeg = (kTile + FDD_MAX_WIDTH - 1 + kThreads - 1) / kThreads;  // 8
+constexpr int kTile = 4096;
+constexpr int kMaxSeg = (kTile + FDD_MAX_WIDTH - 1 + kThreads - 1) / kThreads;  // 20
 
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp, uint32_t* total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -64,6 +71,7 @@ __device__ __forceinline__ void boxcar_series(const BoxcarArgs& a, const int64_t
     extern __shared__ uint32_t sP[];  // exclusive prefix sums, seg*kThreads + 1 entries
     __shared__ float s_scale[FDD_MAX_WIDTHS];
     __shared__ float s_offs[FDD_MAX_WIDTHS];
+    __shared__ int32_t s_tau[FDD_MAX_WIDTHS];  // integer pre-filter: Bc <= tau never exceeds thr
     __shared__ int32_t s_m0;
     __shared__ int32_t s_ok;
     __shared__ uint32_t s_warp[kThreads / 32];
@@ -87,6 +95,10 @@ __device__ __forceinline__ void boxcar_series(const BoxcarArgs& a, const int64_t
                 const double w = (double)a.widths[k];
                 s_scale[k] = (float)(1.0 / (sigma * sqrt(w)));
                 s_offs[k] = (float)(w * delta);
+                // exact crossing thr * sigma * sqrt(w) + w * delta, lowered by 1e-5 relative + 2
+                const double cross = (double)a.thr * sigma * sqrt(w) + w * delta;
+                const double lo = floor(cross - (1e-5 * fabs(cross) + 2.0));
+                s_tau[k] = lo < -2147483647.0 ? -2147483647 : (lo > 2147483646.0 ? 2147483646 : (int32_t)lo);
             }
         }
     }
@@ -123,18 +135,29 @@ __device__ __forceinline__ void boxcar_series(const BoxcarArgs& a, const int64_t
         if (threadIdx.x == 0) sP[seg * kThreads] = s_total;
         __syncthreads();
 
-        for (int wi = 0; wi < a.n_width; wi++) {
-            const int w = a.widths[wi];
-            const float scale = s_scale[wi], offs = s_offs[wi];
-#pragma unroll
-            for (int e = 0; e < kTile / kThreads; e++) {
-                const int tl = e * kThreads + threadIdx.x;
-                const int t = t0 + tl;
+        const int nw = a.n_width;
+#pragma unroll 1
+        for (int e = 0; e < kTile / kThreads; e++) {
+            const int tl = e * kThreads + threadIdx.x;
+            const int t = t0 + tl;
+            if (t0 + e * kThreads >= n) break;  // block-uniform
+            // integer pre-filter over every width
+            bool any = false;
+            if (t < n) {
+                const uint32_t p0 = sP[tl];
+                for (int wi = 0; wi < nw; wi++) {
+                    const int w = a.widths[wi];
+                    if (t + w <= n) any |= static_cast<int32_t>(sP[tl + w] - p0) > s_tau[wi];
+                }
+            }
+            if (!__any_sync(0xffffffffu, any)) continue;
+            for (int wi = 0; wi < nw; wi++) {
+                const int w = a.widths[wi];
                 bool pred = false;
                 float snr = 0.f;
                 if (t + w <= n) {
                     const int32_t bc = static_cast<int32_t>(sP[tl + w] - sP[tl]);
-                    snr = (static_cast<float>(bc) - offs) * scale;
+                    snr = (static_cast<float>(bc) - s_offs[wi]) * s_scale[wi];
                     pred = snr > a.thr;
                 }
                 const unsigned mask = __ballot_sync(0xffffffffu, pred);
