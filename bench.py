@@ -45,6 +45,10 @@ WORKLOADS = {
     "arts_71sb": dict(n_tab=12, n_sb=71, n_chan=1536, n_out=synth.ARTS_CHUNK, seed=3, n_pulses=5,
                       pulse_tabs=[0, 3, 5, 8, 11], thr=8.0,
                       ranges=[dict(dm0=0.0, ddm=0.2, n_dm=2048, downsamp=1, widths=WIDTHS)]),
+    # 71 SBs, DM 0-51.2 (256 trials): a small case of the 71-SB kernels for detailed profiles
+    "arts_71sb_256dm": dict(n_tab=12, n_sb=71, n_chan=1536, n_out=synth.ARTS_CHUNK, seed=3, n_pulses=5,
+                            pulse_tabs=[0, 3, 5, 8, 11], thr=8.0,
+                            ranges=[dict(dm0=0.0, ddm=0.2, n_dm=256, downsamp=1, widths=WIDTHS)]),
     # 71 SBs, 4-range plan 0-5000 with downsampling 1/2/4/8
     "arts_71sb_4range": dict(n_tab=12, n_sb=71, n_chan=1536, n_out=synth.ARTS_CHUNK, seed=4, n_pulses=5,
                              pulse_tabs=[0, 3, 5, 8, 11], thr=8.0,
@@ -248,6 +252,8 @@ def run_fdd(args):
     w, f, t, x, sb, n_in = make_workload(args.workload)
     mode = args.mode or w.get("mode", "plain")
     plan = fdd.Plan(w["n_tab"], w["n_chan"], w["n_sb"], f, t, w["ranges"], w["thr"], sb)
+    if args.scratch_mb:
+        plan.set_scratch_limit(args.scratch_mb << 20)
     host = torch.from_numpy(x).pin_memory()
     tabs = host.to(dev)
     cap = 1 << 22
@@ -599,6 +605,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--variant", type=int, default=None, help="force this dedispersion kernel variant")
     ap.add_argument("--cc", type=int, default=0, help="with --variant: channels per stage (0 = largest fitting)")
+    ap.add_argument("--scratch-mb", type=int, default=0,
+                    help="cap on the SB-factored kernel's partial-sum scratch (0 = library default)")
     ap.add_argument("--serve", action="store_true", help="serving measurement instead of the step benchmark")
     ap.add_argument("--beams", default="1,2,3,4,8", help="--serve: compound-beam counts to run")
     ap.add_argument("--seconds", type=float, default=20.0, help="--serve: stream length per run")
