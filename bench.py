@@ -45,10 +45,10 @@ WORKLOADS = {
     "arts_71sb": dict(n_tab=12, n_sb=71, n_chan=1536, n_out=synth.ARTS_CHUNK, seed=3, n_pulses=5,
                       pulse_tabs=[0, 3, 5, 8, 11], thr=8.0,
                       ranges=[dict(dm0=0.0, ddm=0.2, n_dm=2048, downsamp=1, widths=WIDTHS)]),
-    # 71 SBs, DM 0-51.2 (256 trials): a small case of the 71-SB kernels for detailed profiles
-    "arts_71sb_256dm": dict(n_tab=12, n_sb=71, n_chan=1536, n_out=synth.ARTS_CHUNK, seed=3, n_pulses=5,
+    # 71 SBs, DM 0-25.4 (128 trials): a small case of the 71-SB kernels for detailed profiles
+    "arts_71sb_128dm": dict(n_tab=12, n_sb=71, n_chan=1536, n_out=synth.ARTS_CHUNK, seed=3, n_pulses=5,
                             pulse_tabs=[0, 3, 5, 8, 11], thr=8.0,
-                            ranges=[dict(dm0=0.0, ddm=0.2, n_dm=256, downsamp=1, widths=WIDTHS)]),
+                            ranges=[dict(dm0=0.0, ddm=0.2, n_dm=128, downsamp=1, widths=WIDTHS)]),
     # 71 SBs, 4-range plan 0-5000 with downsampling 1/2/4/8
     "arts_71sb_4range": dict(n_tab=12, n_sb=71, n_chan=1536, n_out=synth.ARTS_CHUNK, seed=4, n_pulses=5,
                              pulse_tabs=[0, 3, 5, 8, 11], thr=8.0,
@@ -87,7 +87,8 @@ def make_workload(name):
     t = synth.ARTS_T_SAMP_S
     n_in = w["n_out"] + max_delay_native(f, w["ranges"], t) + 16
     dm_hi = min(400.0, w["ranges"][-1]["dm0"] + w["ranges"][-1]["n_dm"] * w["ranges"][-1]["ddm"])
-    prm = synth.random_pulses(w["seed"], w["n_pulses"], w["pulse_tabs"], 50.0, dm_hi, [1, 2, 4, 8, 16, 32],
+    dm_lo = min(50.0, 0.5 * dm_hi)
+    prm = synth.random_pulses(w["seed"], w["n_pulses"], w["pulse_tabs"], dm_lo, dm_hi, [1, 2, 4, 8, 16, 32],
                               8.0, 50.0, 200, w["n_out"] - 200)
     pulses = [dict(tab=p["tab"], start=p["t0"] + arrivals(f, p["dm"], t), width=p["width"],
                    amp=synth.pulse_amplitude(p["snr"], w["n_chan"], p["width"])) for p in prm]
