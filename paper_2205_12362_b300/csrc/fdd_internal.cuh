@@ -114,7 +114,7 @@ struct SbfCombArgs {
     const uint16_t* P;
     int64_t tab_stride, seg_stride;
     int32_t Np;
-    const uint8_t* seg_tab;     // [n_sb][seg_pitch]: TAB SB s takes on segment u (seg_pitch % 4 == 0)
+    const uint8_t* seg_tab;     // [n_sb][seg_pitch]: TAB SB s takes on segment u (seg_pitch % 8 == 0)
     int32_t seg_pitch;
     int32_t* series;            // this range: [n_sb][n_dm][n_out]
     unsigned long long* stat;   // this range: [n_sb * n_dm][2]

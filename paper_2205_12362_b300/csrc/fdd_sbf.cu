@@ -131,7 +131,7 @@ int configure_sbf(fdd_plan* p, RangeState& r, int sv, int CC) {
     int rc;
     if (!r.d_segs) {
         if ((rc = upload(&r.d_segs, r.segs, "segment table")) != FDD_OK) return rc;
-        r.seg_pitch = static_cast<int32_t>(round_up64(static_cast<int64_t>(r.segs.size()), 4));
+        r.seg_pitch = static_cast<int32_t>(round_up64(static_cast<int64_t>(r.segs.size()), 8));  // whole 8-segment chunks
         std::vector<uint8_t> tab(static_cast<size_t>(p->n_sb) * r.seg_pitch, 0);
         for (int s = 0; s < p->n_sb; s++)
             for (size_t g = 0; g < r.segs.size(); g++)

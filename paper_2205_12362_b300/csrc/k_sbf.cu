@@ -227,7 +227,11 @@ __global__ void __launch_bounds__(WARPS * 32) k_sbf_part(const SbfPartArgs a) {
 // (4 per lane).  The partial rows of every TAB for UC segments at a time are
 // copied into shared memory with cp.async (double-buffered), so each row is
 // read from L2/HBM once per block and then serves every SB that selects it.
-constexpr int CW = 12, CSB = 6, CT = 128;
+// A warp whose SBs run past n_sb repeats its last valid SB (results
+// discarded), so the inner loop has no per-SB branches.
+constexpr int CW = 12, CSB = 6, CT = 128, UC = 8;
+constexpr int kRowBytes = CT * 2;            // one partial row in shared memory
+constexpr int kTabBytes = UC * kRowBytes;    // UC rows of one TAB
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
@@ -250,24 +254,32 @@ __global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const SbfCombArgs a) {
     const int i = a.i0 + i_s;
     const int t0 = blockIdx.x * CT;
     const int sb0 = blockIdx.z * (CW * CSB) + warp * CSB;
-    const int nsb = max(0, min(CSB, a.n_sb - sb0));  // warp-uniform; warps with none still copy
-    const int UC = a.uc;
+    const int nsb = max(0, min(CSB, a.n_sb - sb0));  // warp-uniform
     const int n_chunks = (a.n_seg + UC - 1) / UC;
     const uint32_t s_base = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
-    const uint32_t buf_bytes = static_cast<uint32_t>(a.n_tab) * UC * CT * 2;
+    const uint32_t buf_bytes = static_cast<uint32_t>(a.n_tab) * kTabBytes;
     const uint16_t* p_trial = a.P + static_cast<int64_t>(i_s) * a.Np + t0;
-    const uint8_t* tabs_w = a.seg_tab + static_cast<int64_t>(max(sb0, 0)) * a.seg_pitch;
+    // the SBs of this warp (invalid slots repeat SB sb0 + nsb - 1, or SB 0 for an idle warp)
+    const uint8_t* tab_row[CSB];
+#pragma unroll
+    for (int j = 0; j < CSB; j++) {
+        const int sj = nsb > 0 ? sb0 + min(j, nsb - 1) : 0;
+        tab_row[j] = a.seg_tab + static_cast<int64_t>(sj) * a.seg_pitch;
+    }
 
+    // copy chunk ch (UC segments of every TAB) into buffer buf: 16 pieces of 16 B per row
     auto issue = [&](int ch, int buf) {
         const int u0 = ch * UC;
         const int nu = min(UC, a.n_seg - u0);
-        const int pieces = a.n_tab * nu * (CT / 8);  // 16-byte pieces
+        const int pieces = a.n_tab * UC * (CT / 8);
         for (int idx = threadIdx.x; idx < pieces; idx += CW * 32) {
-            const int row = idx / (CT / 8), part = idx - row * (CT / 8);
-            const int k = row / nu, du = row - k * nu;
-            const uint16_t* src = p_trial + k * a.tab_stride + static_cast<int64_t>(u0 + du) * a.seg_stride + part * 8;
-            const uint32_t dst = s_base + buf * buf_bytes + static_cast<uint32_t>((k * UC + du) * CT + part * 8) * 2;
-            cp_async16(dst, src);
+            const int part = idx & (CT / 8 - 1);
+            const int row = idx >> 4;  // CT / 8 == 16
+            const int du = row & (UC - 1), k = row >> 3;  // UC == 8
+            if (du < nu) {
+                const uint16_t* src = p_trial + k * a.tab_stride + static_cast<int64_t>(u0 + du) * a.seg_stride + part * 8;
+                cp_async16(s_base + buf * buf_bytes + static_cast<uint32_t>(row * kRowBytes + part * 16), src);
+            }
         }
         cp_async_commit();
     };
@@ -303,24 +315,23 @@ __global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const SbfCombArgs a) {
         const int u0 = ch * UC;
         const int nu = min(UC, a.n_seg - u0);
         const uint32_t s_buf = s_base + buf * buf_bytes + 8u * lane;
-        for (int q = 0; q < nu; q += 4) {
+#pragma unroll
+        for (int q = 0; q < UC; q += 4) {
             uint32_t tabs4[CSB];
 #pragma unroll
-            for (int j = 0; j < CSB; j++)
-                tabs4[j] = (j < nsb) ? __ldg(reinterpret_cast<const uint32_t*>(tabs_w + j * a.seg_pitch + u0 + q)) : 0u;
-            // u0 + q is a multiple of 4 when UC is (host guarantees UC % 4 == 0)
+            for (int j = 0; j < CSB; j++) tabs4[j] = __ldg(reinterpret_cast<const uint32_t*>(tab_row[j] + u0 + q));
 #pragma unroll
             for (int dq = 0; dq < 4; dq++) {
-                if (q + dq < nu) {
-                    const int du = q + dq;
+                const int du = q + dq;
+                if (du < nu) {  // block-uniform
 #pragma unroll
                     for (int j = 0; j < CSB; j++) {
-                        if (j < nsb) {
-                            const uint32_t k = (tabs4[j] >> (8 * dq)) & 0xFFu;
-                            const uint2 v = lds64(s_buf + ((k * UC + du) * CT) * 2);
-                            acc[j][0] += v.x;
-                            acc[j][1] += v.y;
-                        }
+                        // byte dq of tabs4 (the TAB) times kTabBytes (2048 = 2^11)
+                        const uint32_t koff = (dq <= 1 ? (tabs4[j] << (11 - 8 * dq)) : (tabs4[j] >> (8 * dq - 11))) &
+                                              (0xFFu << 11);
+                        const uint2 v = lds64(s_buf + koff + du * kRowBytes);
+                        acc[j][0] += v.x;
+                        acc[j][1] += v.y;
                     }
                     if (++since == a.flush) {
                         fold();
@@ -410,20 +421,14 @@ cudaError_t launch_sbf_part(int idx, const SbfPartArgs& a, int n_tab, cudaStream
 
 int sbf_comb_sbs_per_block() { return CW * CSB; }
 
-int sbf_comb_uc(int n_tab) {
-    // two buffers of n_tab x UC rows of CT uint16 in at most 64 KB; UC a multiple of 4
-    int uc = (64 * 1024) / (2 * n_tab * CT * 2) / 4 * 4;
-    return uc < 4 ? 4 : (uc > 16 ? 16 : uc);
-}
+int sbf_comb_uc(int) { return UC; }
 
-size_t sbf_comb_smem(int n_tab, int uc) { return 2ull * n_tab * uc * CT * 2; }
-
-size_t sbf_comb_smem_bytes(int n_tab) { return sbf_comb_smem(n_tab, sbf_comb_uc(n_tab)); }
+size_t sbf_comb_smem_bytes(int n_tab) { return 2ull * n_tab * kTabBytes; }
 
 cudaError_t launch_sbf_comb(const SbfCombArgs& a, cudaStream_t s) {
     const int per_block = CW * CSB;
     const int n_valid = a.n_dm - a.i0 < a.n_slab ? a.n_dm - a.i0 : a.n_slab;
-    const size_t smem = sbf_comb_smem(a.n_tab, a.uc);
+    const size_t smem = sbf_comb_smem_bytes(a.n_tab);
     cudaError_t err = cudaFuncSetAttribute(k_sbf_comb, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem));
     if (err != cudaSuccess) return err;
