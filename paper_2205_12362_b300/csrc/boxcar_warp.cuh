@@ -1,0 +1,202 @@
+// boxcar_warp.cuh -- boxcar S/N and compaction with one WARP per series, no
+// block barriers (used when every width is at most kWarpCS samples; the
+// block-per-series form in boxcar_series.cuh serves wider boxcars).
+//
+// Same method and numerics as boxcar_series.cuh (paper Sec. "Integration",
+// "S/N evaluation", "Candidate selection"): exact integer moments finalised
+// in FP64, series centred on m0 = round(mu), wrapping-uint32 prefix sums so
+// B_w(t) - w*m0 = P[t+w] - P[t] exactly, the integer pre-filter
+// Bc > tau_w, and for survivors snr = (Bc - w*(mu - m0)) * 1/(sigma sqrt w)
+// in FP32 against thr.
+//
+// Per warp, the series is walked in chunks of kWarpCS = 512 samples, lane l
+// holding samples 32*m + l (m < 16) so every global load and shared access
+// is coalesced / conflict-free.  The exclusive prefix of a chunk is one warp
+// scan per row of 32 plus a running carry; it goes to slot c mod 3 of a
+// per-warp shared ring (slot 0 is mirrored past slot 2 for the first wmax
+// entries), and chunk c-1 is evaluated once chunk c is in, so P[t + w] for
+// w <= 512 is always one contiguous read.
+#pragma once
+
+#include "fdd_internal.cuh"
+
+namespace fdd {
+namespace detail {
+
+constexpr int kWarpCS = 512;                      // samples per chunk
+constexpr int kWarpRows = kWarpCS / 32;           // rows of 32 per chunk
+constexpr int kWarpRing = 3 * kWarpCS + kWarpCS;  // three slots + mirror of slot 0, uint32 entries
+constexpr int kBoxWarps = 4;                      // warps (series) per block
+
+// One series as the warp needs it.
+struct BoxSeries {
+    const int32_t* S;                    // [n]
+    const unsigned long long* stat;      // [2]: sum S, sum S^2
+    const int32_t* widths;               // [n_width]
+    fdd_candidate* cands;
+    unsigned long long* count;
+    int64_t cap;
+    int64_t t_offset;
+    double dm;
+    int32_t n, n_width, sb, dm_index, D;
+    float thr;
+};
+
+// All 32 lanes of the warp call this with the same series; ring is the
+// warp's kWarpRing-entry shared buffer.  NWB >= n_width (compile-time bound).
+template <int NWB>
+__device__ __forceinline__ void boxcar_series_warp(const BoxSeries& v, uint32_t* ring) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int n = v.n;
+
+    // statistics on lane 0 (exact integer moments, FP64 finalisation)
+    double mu = 0.0, sigma = 0.0;
+    int ok = 0;
+    if (lane == 0) {
+        const long long sum = static_cast<long long>(v.stat[0]);
+        const unsigned long long sq = v.stat[1];
+        const __int128 num = (__int128)n * (__int128)sq - (__int128)sum * (__int128)sum;
+        ok = (n > 0) && (num > 0);
+        if (ok) {
+            mu = (double)sum / (double)n;
+            sigma = sqrt((double)num / ((double)n * (double)n));
+        }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) return;
+    mu = __shfl_sync(0xffffffffu, mu, 0);
+    sigma = __shfl_sync(0xffffffffu, sigma, 0);
+    const long long m0 = llrint(mu);
+    const double delta = mu - (double)m0;
+    // width k's constants on lane k
+    int32_t w_l = 0, tau_l = 0x7fffffff;
+    float scale_l = 0.f, offs_l = 0.f;
+    if (lane < v.n_width) {
+        w_l = v.widths[lane];
+        const double w = (double)w_l;
+        scale_l = (float)(1.0 / (sigma * sqrt(w)));
+        offs_l = (float)(w * delta);
+        // exact crossing thr * sigma * sqrt(w) + w * delta, lowered by 1e-5 relative + 2
+        const double cross = (double)v.thr * sigma * sqrt(w) + w * delta;
+        const double lo = floor(cross - (1e-5 * fabs(cross) + 2.0));
+        tau_l = lo < -2147483647.0 ? -2147483647 : (lo > 2147483646.0 ? 2147483646 : (int32_t)lo);
+    }
+    int32_t wk[NWB], tk[NWB];
+    uint32_t wb[NWB];  // byte offsets 4 * w
+    int wmax = 0;
+#pragma unroll
+    for (int k = 0; k < NWB; k++) {
+        wk[k] = __shfl_sync(0xffffffffu, w_l, k);
+        tk[k] = __shfl_sync(0xffffffffu, tau_l, k);  // lanes >= n_width hold "never"
+        wb[k] = 4u * static_cast<uint32_t>(wk[k]);
+        wmax = max(wmax, wk[k]);
+    }
+    const uint32_t m0u = static_cast<uint32_t>(m0);
+    const int n_chunks = n / kWarpCS + 1;  // covers prefix indices 0..n
+    const uint32_t ring_s = static_cast<uint32_t>(__cvta_generic_to_shared(ring));
+    uint32_t carry = 0;
+
+    for (int c = 0; c <= n_chunks; c++) {
+        if (c < n_chunks) {
+            // centred samples of chunk c (zero past the end), exclusive prefix, into slot c mod 3
+            const int base = c * kWarpCS;
+            uint32_t x[kWarpRows];
+#pragma unroll
+            for (int m = 0; m < kWarpRows; m++) {
+                const int t = base + 32 * m + lane;
+                x[m] = t < n ? static_cast<uint32_t>(__ldg(v.S + t)) - m0u : 0u;
+            }
+            const int slot = c % 3;
+#pragma unroll
+            for (int m = 0; m < kWarpRows; m++) {
+                uint32_t incl = x[m];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const uint32_t p = carry + incl - x[m];
+                const uint32_t at = ring_s + 4u * static_cast<uint32_t>(slot * kWarpCS + 32 * m + lane);
+                asm volatile("st.shared.u32 [%0], %1;" ::"r"(at), "r"(p) : "memory");
+                if (slot == 0 && 32 * m < wmax) {
+                    const uint32_t am = ring_s + 4u * static_cast<uint32_t>(3 * kWarpCS + 32 * m + lane);
+                    asm volatile("st.shared.u32 [%0], %1;" ::"r"(am), "r"(p) : "memory");
+                }
+                carry += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            __syncwarp();
+        }
+        if (c == 0) continue;
+        // evaluate chunk c-1: t = (c-1)*CS + 32*m + lane
+        const int e = c - 1;
+        const int ebase = e * kWarpCS;
+        if (ebase >= n) break;
+        const uint32_t s_slot = ring_s + 4u * static_cast<uint32_t>((e % 3) * kWarpCS + lane);
+        const bool interior = ebase + kWarpCS + wmax <= n;  // no window of this chunk passes the end
+#pragma unroll 2
+        for (int m = 0; m < kWarpRows; m++) {
+            const int t = ebase + 32 * m + lane;
+            const uint32_t a0 = s_slot + 128u * m;
+            uint32_t p0;
+            asm volatile("ld.shared.u32 %0, [%1];" : "=r"(p0) : "r"(a0));
+            bool any = false;
+            if (interior) {
+#pragma unroll
+                for (int k = 0; k < NWB; k++) {
+                    uint32_t pw;
+                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(pw) : "r"(a0 + wb[k]));
+                    any |= static_cast<int32_t>(pw - p0) > tk[k];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < NWB; k++) {
+                    uint32_t pw;
+                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(pw) : "r"(a0 + wb[k]));
+                    any |= (t + wk[k] <= n) && (static_cast<int32_t>(pw - p0) > tk[k]);
+                }
+            }
+            if (!__any_sync(0xffffffffu, any)) continue;
+            // exact FP32 S/N for this row, width by width
+            for (int k = 0; k < v.n_width; k++) {
+                const int w = __shfl_sync(0xffffffffu, w_l, k);
+                const float scale = __shfl_sync(0xffffffffu, scale_l, k);
+                const float offs = __shfl_sync(0xffffffffu, offs_l, k);
+                bool pred = false;
+                float snr = 0.f;
+                if (t + w <= n) {
+                    uint32_t pw;
+                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(pw) : "r"(a0 + 4u * w));
+                    const int32_t bc = static_cast<int32_t>(pw - p0);
+                    snr = (static_cast<float>(bc) - offs) * scale;
+                    pred = snr > v.thr;
+                }
+                const unsigned mask = __ballot_sync(0xffffffffu, pred);
+                if (mask) {
+                    const int leader = __ffs(mask) - 1;
+                    unsigned long long b0 = 0;
+                    if (lane == leader) b0 = atomicAdd(v.count, static_cast<unsigned long long>(__popc(mask)));
+                    b0 = __shfl_sync(0xffffffffu, b0, leader);
+                    if (pred) {
+                        const unsigned long long idx = b0 + __popc(mask & lt_mask);
+                        if (idx < static_cast<unsigned long long>(v.cap)) {
+                            fdd_candidate cd;
+                            cd.sb = v.sb;
+                            cd.dm_index = v.dm_index;
+                            cd.downsamp = v.D;
+                            cd.width_native = w * v.D;
+                            cd.t_native = static_cast<int64_t>(t) * v.D + v.t_offset;
+                            cd.dm = static_cast<float>(v.dm);
+                            cd.snr = snr;
+                            v.cands[idx] = cd;
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();  // slot e % 3 may be rewritten by chunk c + 2
+    }
+}
+
+}  // namespace detail
+}  // namespace fdd

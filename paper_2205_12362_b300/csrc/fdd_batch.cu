@@ -228,8 +228,11 @@ int fill_params(const fdd_plan* p, const fdd_job* jobs, int32_t n_jobs, int64_t 
 int enqueue(fdd_plan* p, const BatchLaunch& BL, cudaStream_t s) {
     const fdd::BatchParams& P = BL.P;
     int64_t n_launch = 1 + (P.n_ds > 0 ? 1 : 0) + 1;  // prep, downsample, boxcar
-    int wmax = 1;
-    for (const RangeState& r : p->ranges) wmax = std::max(wmax, r.wmax);
+    int wmax = 1, nwm = 1;
+    for (const RangeState& r : p->ranges) {
+        wmax = std::max(wmax, r.wmax);
+        nwm = std::max(nwm, r.n_width);
+    }
     stage_reset(p);
     cudaError_t e;
     if ((e = stage_begin(p, 3, -1, s)) != cudaSuccess) return cuda_fail(e, "timing event");
@@ -258,7 +261,7 @@ int enqueue(fdd_plan* p, const BatchLaunch& BL, cudaStream_t s) {
         if ((e = stage_end(p, s)) != cudaSuccess) return cuda_fail(e, "timing event");
     }
     if ((e = stage_begin(p, 2, -1, s)) != cudaSuccess) return cuda_fail(e, "timing event");
-    if ((e = fdd::launch_boxcar_batch(P, wmax, p->thr, s)) != cudaSuccess) return cuda_fail(e, "batch boxcar launch");
+    if ((e = fdd::launch_boxcar_batch(P, wmax, nwm, p->thr, s)) != cudaSuccess) return cuda_fail(e, "batch boxcar launch");
     if ((e = stage_end(p, s)) != cudaSuccess) return cuda_fail(e, "timing event");
     p->last_launches = n_launch;
     return FDD_OK;

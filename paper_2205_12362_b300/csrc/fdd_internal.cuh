@@ -226,7 +226,7 @@ cudaError_t persistent_occupancy(int idx, int E, size_t smem, int* blocks_per_sm
 cudaError_t launch_batch_prep(const BatchParams& p, cudaStream_t s);
 cudaError_t launch_batch_downsample(const BatchParams& p, cudaStream_t s);
 cudaError_t launch_dedisp_persistent(int idx, int E, const BatchParams& p, int grid, size_t smem, cudaStream_t s);
-cudaError_t launch_boxcar_batch(const BatchParams& p, int wmax_all, float thr, cudaStream_t s);
+cudaError_t launch_boxcar_batch(const BatchParams& p, int wmax_all, int n_width_max, float thr, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Library-internal helpers shared between host files.

@@ -15,6 +15,7 @@
 #include <algorithm>
 
 #include "boxcar_series.cuh"
+#include "boxcar_warp.cuh"
 #include "dedisp_tile.cuh"
 #include "downsample_chunk.cuh"
 
@@ -128,6 +129,41 @@ __global__ void __launch_bounds__(detail::kThreads) k_boxcar_batch(const __grid_
     detail::boxcar_series(a, q);
 }
 
+// Warp-per-series boxcar over every series of every job (all widths <= 512).
+template <int NWB>
+__global__ void __launch_bounds__(detail::kBoxWarps * 32)
+    k_boxcar_batch_warp(const __grid_constant__ BatchParams p, const float thr) {
+    __shared__ uint32_t ring[detail::kBoxWarps][detail::kWarpRing];
+    const int warp = threadIdx.x >> 5;
+    const int64_t gq = static_cast<int64_t>(blockIdx.x) * detail::kBoxWarps + warp;
+    if (gq >= static_cast<int64_t>(p.n_jobs) * p.series_per_job) return;  // warp-uniform
+    const int job = static_cast<int>(gq / p.series_per_job);
+    int64_t q = gq - static_cast<int64_t>(job) * p.series_per_job;
+    int r = 0;
+    while (r + 1 < p.n_range && q >= p.ranges[r + 1].series_off) r++;
+    const BatchRange& R = p.ranges[r];
+    q -= R.series_off;
+    if (R.n_out == 0) return;
+    const BatchJob& J = p.jobs[job];
+    const int i = static_cast<int>(q % R.n_dm);
+    detail::BoxSeries v;
+    v.S = J.series + R.series_elem_off + q * R.n_out;
+    v.stat = J.stat + 2 * (R.series_off + q);
+    v.widths = R.widths;
+    v.cands = J.cands;
+    v.count = J.count;
+    v.cap = J.cap;
+    v.t_offset = J.t_offset;
+    v.dm = R.dm0 + static_cast<double>(i) * R.ddm;
+    v.n = R.n_out;
+    v.n_width = R.n_width;
+    v.sb = static_cast<int>(q / R.n_dm);
+    v.dm_index = R.dm_index0 + i;
+    v.D = R.D;
+    v.thr = thr;
+    detail::boxcar_series_warp<NWB>(v, ring[warp]);
+}
+
 using PersistentFn = void (*)(const BatchParams);
 
 struct PEntry {
@@ -191,9 +227,19 @@ cudaError_t launch_dedisp_persistent(int idx, int E, const BatchParams& p, int g
     return cudaGetLastError();
 }
 
-cudaError_t launch_boxcar_batch(const BatchParams& p, int wmax_all, float thr, cudaStream_t s) {
+cudaError_t launch_boxcar_batch(const BatchParams& p, int wmax_all, int n_width_max, float thr, cudaStream_t s) {
     const long long blocks = static_cast<long long>(p.n_jobs) * p.series_per_job;
     if (blocks == 0) return cudaSuccess;
+    if (wmax_all <= detail::kWarpCS) {
+        const unsigned wb = static_cast<unsigned>((blocks + detail::kBoxWarps - 1) / detail::kBoxWarps);
+        if (n_width_max <= 4)
+            k_boxcar_batch_warp<4><<<wb, detail::kBoxWarps * 32, 0, s>>>(p, thr);
+        else if (n_width_max <= 8)
+            k_boxcar_batch_warp<8><<<wb, detail::kBoxWarps * 32, 0, s>>>(p, thr);
+        else
+            k_boxcar_batch_warp<16><<<wb, detail::kBoxWarps * 32, 0, s>>>(p, thr);
+        return cudaGetLastError();
+    }
     const size_t smem = detail::boxcar_smem_bytes(wmax_all);
     k_boxcar_batch<<<static_cast<unsigned>(blocks), detail::kThreads, smem, s>>>(p, thr);
     return cudaGetLastError();
