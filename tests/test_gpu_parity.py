@@ -517,3 +517,25 @@ def test_sb_factored_piecewise_slabs(fdd):
         gpu, n = res.candidates()
         compare_candidates(gpu, ora, 6.0)
     assert ran == {1, 2}
+
+
+def test_boxcar_width_sets(fdd):
+    """Both boxcar forms: one warp per series (widths <= 512; 4, 8 and 16
+    width slots) and one block per series (a width above 512), against the
+    oracle, with chunk-crossing and series-end windows."""
+    import torch
+    n_chan, n_out = 96, 3100
+    f = synth.channel_freqs(n_chan)
+    ranges = [dict(dm0=0.0, ddm=2.0, n_dm=24, downsamp=1, widths=list(range(1, 11))),   # 10 widths
+              dict(dm0=48.0, ddm=4.0, n_dm=12, downsamp=2, widths=[1, 600, 1024]),    # block path
+              dict(dm0=96.0, ddm=8.0, n_dm=6, downsamp=4, widths=[3, 511])]           # 4 slots, wide
+    n_in = max(int(oracle.delays(f, T_SAMP, r["dm0"], r["ddm"], r["n_dm"], r["downsamp"]).max())
+               * r["downsamp"] + n_out for r in ranges) + 3
+    pulses = [dict(tab=0, start=t0 + oracle.delays(f, T_SAMP, dm, 1.0, 1)[0], width=w, amp=30.0)
+              for t0, dm, w in [(505, 20.0, 3), (1530, 70.0, 40), (2900, 120.0, 300)]]
+    x = synth.filterbank(17, 1, n_chan, n_in, pulses=pulses)
+    sb = np.zeros((1, n_chan), np.int16)
+    plan, gpu, gs, ora, os_ = run_both(fdd, x, sb, f, ranges, 5.0, n_out, n_in)
+    for g, o in zip(gs, os_):
+        assert (g == o).all()
+    assert compare_candidates(gpu, ora, 5.0) > 0
