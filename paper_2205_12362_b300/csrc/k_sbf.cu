@@ -223,16 +223,15 @@ __global__ void __launch_bounds__(WARPS * 32) k_sbf_part(const SbfPartArgs a) {
     }
 }
 
-// Comb: block = CW warps x CSB SBs per warp, one DM trial, CT = 256 samples
-// (8 per lane, one 16-byte shared load per SB and segment).  The partial rows of every TAB for UC segments at a time are
+// Comb: block = CW warps x CSB SBs per warp, one DM trial, CT = 128 samples
+// (4 per lane).  The partial rows of every TAB for UC segments at a time are
 // copied into shared memory with cp.async (double-buffered), so each row is
 // read from L2/HBM once per block and then serves every SB that selects it.
 // A warp whose SBs run past n_sb repeats its last valid SB (results
 // discarded), so the inner loop has no per-SB branches.
-constexpr int CW = 24, CSB = 3, CT = 256, UC = 8;
+constexpr int CW = 12, CSB = 6, CT = 128, UC = 8;
 constexpr int kRowBytes = CT * 2;            // one partial row in shared memory
-constexpr int kTabBytes = UC * kRowBytes;    // UC rows of one TAB (2^12 bytes)
-constexpr int kPieces = CT / 8;              // 16-byte pieces per row
+constexpr int kTabBytes = UC * kRowBytes;    // UC rows of one TAB
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
@@ -242,13 +241,13 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
-__device__ __forceinline__ uint4 lds128(uint32_t addr) {
-    uint4 v;
-    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+__device__ __forceinline__ uint2 lds64(uint32_t addr) {
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
     return v;
 }
 
-__global__ void __launch_bounds__(CW * 32, 1) k_sbf_comb(const SbfCombArgs a) {
+__global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const SbfCombArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];  // [2][n_tab][UC][CT] uint16
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i_s = blockIdx.y;
@@ -272,10 +271,10 @@ __global__ void __launch_bounds__(CW * 32, 1) k_sbf_comb(const SbfCombArgs a) {
     auto issue = [&](int ch, int buf) {
         const int u0 = ch * UC;
         const int nu = min(UC, a.n_seg - u0);
-        const int pieces = a.n_tab * UC * kPieces;
+        const int pieces = a.n_tab * UC * (CT / 8);
         for (int idx = threadIdx.x; idx < pieces; idx += CW * 32) {
-            const int part = idx & (kPieces - 1);
-            const int row = idx >> 5;  // kPieces == 32
+            const int part = idx & (CT / 8 - 1);
+            const int row = idx >> 4;  // CT / 8 == 16
             const int du = row & (UC - 1), k = row >> 3;  // UC == 8
             if (du < nu) {
                 const uint16_t* src = p_trial + k * a.tab_stride + static_cast<int64_t>(u0 + du) * a.seg_stride + part * 8;
@@ -285,23 +284,21 @@ __global__ void __launch_bounds__(CW * 32, 1) k_sbf_comb(const SbfCombArgs a) {
         cp_async_commit();
     };
 
-    uint32_t acc[CSB][4], tot[CSB][8];
+    uint32_t acc[CSB][2], tot[CSB][4];
 #pragma unroll
-    for (int j = 0; j < CSB; j++)
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-            acc[j][e] = 0u;
-            tot[j][2 * e] = tot[j][2 * e + 1] = 0u;
-        }
+    for (int j = 0; j < CSB; j++) {
+        acc[j][0] = acc[j][1] = 0u;
+        tot[j][0] = tot[j][1] = tot[j][2] = tot[j][3] = 0u;
+    }
     auto fold = [&]() {
 #pragma unroll
-        for (int j = 0; j < CSB; j++)
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                tot[j][2 * e] += acc[j][e] & 0xFFFFu;
-                tot[j][2 * e + 1] += acc[j][e] >> 16;
-                acc[j][e] = 0u;
-            }
+        for (int j = 0; j < CSB; j++) {
+            tot[j][0] += acc[j][0] & 0xFFFFu;
+            tot[j][1] += acc[j][0] >> 16;
+            tot[j][2] += acc[j][1] & 0xFFFFu;
+            tot[j][3] += acc[j][1] >> 16;
+            acc[j][0] = acc[j][1] = 0u;
+        }
     };
 
     issue(0, 0);
@@ -317,7 +314,7 @@ __global__ void __launch_bounds__(CW * 32, 1) k_sbf_comb(const SbfCombArgs a) {
         __syncthreads();
         const int u0 = ch * UC;
         const int nu = min(UC, a.n_seg - u0);
-        const uint32_t s_buf = s_base + buf * buf_bytes + 16u * lane;
+        const uint32_t s_buf = s_base + buf * buf_bytes + 8u * lane;
 #pragma unroll
         for (int q = 0; q < UC; q += 4) {
             uint32_t tabs4[CSB];
@@ -329,14 +326,12 @@ __global__ void __launch_bounds__(CW * 32, 1) k_sbf_comb(const SbfCombArgs a) {
                 if (du < nu) {  // block-uniform
 #pragma unroll
                     for (int j = 0; j < CSB; j++) {
-                        // byte dq of tabs4 (the TAB) times kTabBytes (4096 = 2^12)
-                        const uint32_t koff = (dq <= 1 ? (tabs4[j] << (12 - 8 * dq)) : (tabs4[j] >> (8 * dq - 12))) &
-                                              (0xFFu << 12);
-                        const uint4 v = lds128(s_buf + koff + du * kRowBytes);
+                        // byte dq of tabs4 (the TAB) times kTabBytes (2048 = 2^11)
+                        const uint32_t koff = (dq <= 1 ? (tabs4[j] << (11 - 8 * dq)) : (tabs4[j] >> (8 * dq - 11))) &
+                                              (0xFFu << 11);
+                        const uint2 v = lds64(s_buf + koff + du * kRowBytes);
                         acc[j][0] += v.x;
                         acc[j][1] += v.y;
-                        acc[j][2] += v.z;
-                        acc[j][3] += v.w;
                     }
                     if (++since == a.flush) {
                         fold();
@@ -348,14 +343,14 @@ __global__ void __launch_bounds__(CW * 32, 1) k_sbf_comb(const SbfCombArgs a) {
         __syncthreads();  // buffer free for the copy issued next iteration
     }
     fold();
-    const int t = t0 + 8 * lane;
+    const int t = t0 + 4 * lane;
 #pragma unroll
     for (int j = 0; j < CSB; j++) {
         unsigned long long s1 = 0, s2 = 0;
         if (j < nsb) {
             int32_t* row = a.series + (static_cast<int64_t>(sb0 + j) * a.n_dm + i) * a.n_out;
 #pragma unroll
-            for (int e = 0; e < 8; e++) {
+            for (int e = 0; e < 4; e++) {
                 if (t + e < a.n_out) {
                     const uint32_t v = tot[j][e];
                     row[t + e] = static_cast<int32_t>(v);
