@@ -173,20 +173,11 @@ __global__ void __launch_bounds__(WARPS * 32) k_sbf_part(const SbfPartArgs a) {
             const int2 sg = __ldg(&a.segs[g]);
             int cc = sg.x - cur.x;
             const int cc_end = cc + sg.y;
-            // offsets of the next group of four are fetched while this group's words load
-            int32_t og[4][DPW];
-            if (cc + 3 < cc_end) {
-#pragma unroll
-                for (int u = 0; u < 4; u++) detail::load_offsets<DPW>(s_off_w + (cc + u) * BD, og[u]);
-            }
 #pragma unroll 1
             for (; cc + 3 < cc_end; cc += 4) {
-                int32_t on[4][DPW];
-                const bool more = cc + 7 < cc_end;
-                if (more) {
+                int32_t og[4][DPW];
 #pragma unroll
-                    for (int u = 0; u < 4; u++) detail::load_offsets<DPW>(s_off_w + (cc + 4 + u) * BD, on[u]);
-                }
+                for (int u = 0; u < 4; u++) detail::load_offsets<DPW>(s_off_w + (cc + u) * BD, og[u]);
                 uint32_t x[4][DPW][NW];
 #pragma unroll
                 for (int u = 0; u < 4; u++)
@@ -207,12 +198,6 @@ __global__ void __launch_bounds__(WARPS * 32) k_sbf_part(const SbfPartArgs a) {
                             acc_b[j][k] = acc_b[j][k] + split(x[2][j][k]) + split(x[3][j][k]);
                         }
                     }
-                if (more) {
-#pragma unroll
-                    for (int u = 0; u < 4; u++)
-#pragma unroll
-                        for (int j = 0; j < DPW; j++) og[u][j] = on[u][j];
-                }
             }
 #pragma unroll 1
             for (; cc < cc_end; cc++) {
