@@ -514,6 +514,23 @@ int fdd_search_static(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64
                       int64_t t_offset_native, fdd_candidate* d_cands, int64_t cap, uint64_t* d_count,
                       int32_t* d_series, fdd_stream_t stream);
 
+/* SB table from the array geometry (appendix "Tied-array beam simulations",
+ * "Synthesized Beams"): host int16 sb_map_out[n_sb][n_chan] (the plan's SB
+ * map), entry = TAB row n_TAB + n_tab/2 with n_TAB in [-n_tab/2, n_tab/2 - 1].
+ * SB s has index n_SB = s - n_sb/2 (0 = compound-beam centre); at f_max it
+ * takes TAB n_TAB = n_SB mod N (less N above N/2 - 1) of grating response
+ * n_gr = (n_SB - n_TAB)/N, and below f_max it switches to the neighbouring TAB
+ * k_{j+1} = k_j - sgn(n_SB) between the frequencies f_j at which successive TABs
+ * land on the SB's position, f_j = f_max (n_gr B_max + k_j alpha B_cq) /
+ * (n_gr B_max + n_TAB alpha B_cq), at 0.75 f_j + 0.25 f_{j+1} (even |n_SB|) or
+ * 0.25 f_j + 0.75 f_{j+1} (odd).  chan_per_subband > 1 makes every block of
+ * that many channels take the TAB chosen at the block's mean frequency (the
+ * system combines TABs in whole subbands).  Apertif-10: n_tab 12, alpha 0.80,
+ * B_max 1296 m, B_cq 144 m, f_max 1500 MHz, 71 SBs.  Host only; needs no GPU.
+ * Errors: INVALID_ARG (odd n_tab among others). */
+int fdd_sb_table(int32_t n_tab, int32_t n_sb, int32_t n_chan, const double* chan_freq_mhz, double f_max_mhz,
+                 double alpha, double b_max_m, double b_cq_m, int32_t chan_per_subband, int16_t* sb_map_out);
+
 /* Human-readable text of an FDD_* code (static string). */
 const char* fdd_error_string(int code);
 

@@ -195,3 +195,64 @@ def cluster(cands):
     if n < 0:
         raise MemoryError("oracle allocation failed")
     return np.sort(out[:n], order=["sb", "dm_index", "width_native", "t_native"])
+
+
+def sb_table(n_tab, n_sb, freq_mhz, f_max_mhz, alpha, b_max_m, b_cq_m, chan_per_subband=1):
+    """TAB row per (SB, channel) from the array geometry (appendix "Synthesized
+    beams"), written out in plain Python loops.  Returns int32[n_sb][n_chan].
+
+    SB s has index n_SB = s - n_sb // 2.  At f_max it takes TAB n_TAB of grating
+    response n_gr: n_TAB = n_SB mod N, minus N if above N/2 - 1, and
+    n_gr = (n_SB - n_TAB) / N.  Going down in frequency, TAB k_j = n_TAB - j*sgn(n_SB)
+    of the same grating response lands on the SB's position at
+        f_j = f_max * (n_gr*B_max + k_j*alpha*B_cq) / (n_gr*B_max + n_TAB*alpha*B_cq),
+    and the SB switches from k_j to k_{j+1} at 0.75 f_j + 0.25 f_{j+1} (even |n_SB|) or
+    0.25 f_j + 0.75 f_{j+1} (odd |n_SB|).  A TAB index outside [-N/2, N/2 - 1] is the
+    same TAB as the one N away (next grating response); the row is n_TAB + N/2 after
+    that wrap.  With chan_per_subband = G > 1 every block of G channels takes the TAB
+    chosen at the block's mean frequency."""
+    freq = [float(f) for f in freq_mhz]
+    n_chan = len(freq)
+    N = int(n_tab)
+    if N % 2:
+        raise ValueError("the index convention needs an even number of TABs")
+    out = np.zeros((n_sb, n_chan), dtype=np.int32)
+    for s in range(n_sb):
+        n_sb_idx = s - n_sb // 2
+        n_t = n_sb_idx % N
+        if n_t > N // 2 - 1:
+            n_t -= N
+        n_gr = (n_sb_idx - n_t) // N
+        sgn = (n_sb_idx > 0) - (n_sb_idx < 0)
+        w_hi, w_lo = (0.75, 0.25) if abs(n_sb_idx) % 2 == 0 else (0.25, 0.75)
+        den = n_gr * b_max_m + n_t * alpha * b_cq_m
+
+        def f_opt(j):
+            return f_max_mhz * (n_gr * b_max_m + (n_t - j * sgn) * alpha * b_cq_m) / den
+
+        def tab_at(f):
+            if sgn == 0:
+                return n_t
+            j = 0
+            while True:
+                f_sw = w_hi * f_opt(j) + w_lo * f_opt(j + 1)
+                if f >= f_sw or j > 4 * N + 64:
+                    break
+                j += 1
+            return n_t - j * sgn
+
+        def row(k):
+            while k > N // 2 - 1:
+                k -= N
+            while k < -(N // 2):
+                k += N
+            return k + N // 2
+
+        G = max(1, int(chan_per_subband))
+        for b0 in range(0, n_chan, G):
+            chans = range(b0, min(n_chan, b0 + G))
+            f_c = sum(freq[c] for c in chans) / len(chans)
+            r = row(tab_at(f_c))
+            for c in chans:
+                out[s, c] = r
+    return out

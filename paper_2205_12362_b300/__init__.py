@@ -161,6 +161,8 @@ def _lib_raw():
     L.fdd_variant_kind.argtypes = [_I32, ctypes.POINTER(_I32)]
     L.fdd_plan_set_scratch_limit.argtypes = [_P, _I64]
     L.fdd_plan_last_launches.argtypes = [_P, ctypes.POINTER(_I64)]
+    L.fdd_sb_table.argtypes = [_I32, _I32, _I32, _P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                               ctypes.c_double, _I32, _P]
     L.fdd_cluster_workspace_size.argtypes = [_I64, ctypes.POINTER(_SZ)]
     L.fdd_cluster.argtypes = [_P, _P, _I64, _P, _SZ, _P, _I64, _P, _P]
     _lib = L
@@ -456,6 +458,18 @@ def cluster(cands, count, out, out_count, workspace=None, stream=None):
                                   _dev_ptr(out_count, "out_count", torch.int64), _stream_handle(stream)),
            "fdd_cluster")
     return workspace
+
+
+def sb_table(n_tab, n_sb, chan_freq_mhz, f_max_mhz=1500.0, alpha=0.80, b_max_m=1296.0, b_cq_m=144.0,
+             chan_per_subband=1):
+    """int16 [n_sb][n_chan] SB table from the array geometry (include/fdd.h:
+    fdd_sb_table); defaults are Apertif-10's.  Host only."""
+    f = np.ascontiguousarray(chan_freq_mhz, dtype=np.float64)
+    out = np.zeros((int(n_sb), f.size), dtype=np.int16)
+    _check(_lib_raw().fdd_sb_table(int(n_tab), int(n_sb), f.size, f.ctypes.data_as(ctypes.c_void_p), float(f_max_mhz),
+                                   float(alpha), float(b_max_m), float(b_cq_m), int(chan_per_subband),
+                                   out.ctypes.data_as(ctypes.c_void_p)), "fdd_sb_table")
+    return out
 
 
 def sort_candidates(cands):
