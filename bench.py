@@ -45,6 +45,10 @@ WORKLOADS = {
     "arts_71sb": dict(n_tab=12, n_sb=71, n_chan=1536, n_out=synth.ARTS_CHUNK, seed=3, n_pulses=5,
                       pulse_tabs=[0, 3, 5, 8, 11], thr=8.0,
                       ranges=[dict(dm0=0.0, ddm=0.2, n_dm=2048, downsamp=1, widths=WIDTHS)]),
+    # 71 SBs from the array geometry (Apertif-10, TABs combined in 48-channel subbands), DM plan as above
+    "arts_71sb_geom": dict(n_tab=12, n_sb=71, n_chan=1536, n_out=synth.ARTS_CHUNK, seed=3, n_pulses=5,
+                           pulse_tabs=[0, 3, 5, 8, 11], thr=8.0, sb_table="geometry",
+                           ranges=[dict(dm0=0.0, ddm=0.2, n_dm=2048, downsamp=1, widths=WIDTHS)]),
     # 71 SBs, DM 0-25.4 (128 trials): a small case of the 71-SB kernels for detailed profiles
     "arts_71sb_128dm": dict(n_tab=12, n_sb=71, n_chan=1536, n_out=synth.ARTS_CHUNK, seed=3, n_pulses=5,
                             pulse_tabs=[0, 3, 5, 8, 11], thr=8.0,
@@ -81,7 +85,10 @@ def max_delay_native(freqs, ranges, t_samp):
     return out
 
 
-def make_workload(name):
+def make_workload(name, sb_table_fn=None):
+    """sb_table_fn(n_tab, n_sb, freqs, chan_per_subband) builds the geometry SB
+    table of workloads that ask for one (the library's on the measured arm,
+    the oracle's on the reference arm)."""
     w = dict(WORKLOADS[name])
     f = synth.channel_freqs(w["n_chan"])
     t = synth.ARTS_T_SAMP_S
@@ -95,6 +102,8 @@ def make_workload(name):
     x = synth.filterbank(w["seed"], w["n_tab"], w["n_chan"], n_in, pulses=pulses)
     if w["n_tab"] == 1:
         sb = np.zeros((w["n_sb"], w["n_chan"]), np.int16)
+    elif w.get("sb_table") == "geometry":
+        sb = np.asarray(sb_table_fn(w["n_tab"], w["n_sb"], f, 48), dtype=np.int16)
     else:
         sb = synth.sb_map_piecewise(w["seed"], w["n_sb"], w["n_chan"], w["n_tab"]).astype(np.int16)
     return w, f, t, x, sb, n_in
@@ -250,7 +259,8 @@ def run_fdd(args):
     world, rank, local, dist = dist_setup(args)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w, f, t, x, sb, n_in = make_workload(args.workload)
+    w, f, t, x, sb, n_in = make_workload(
+        args.workload, lambda nt, ns, fr, g: fdd.sb_table(nt, ns, fr, chan_per_subband=g))
     mode = args.mode or w.get("mode", "plain")
     plan = fdd.Plan(w["n_tab"], w["n_chan"], w["n_sb"], f, t, w["ranges"], w["thr"], sb)
     if args.scratch_mb:
@@ -471,7 +481,8 @@ def run_reference(args):
             dist.destroy_process_group()
         return None
     import oracle
-    w, f, t, x, sb, n_in = make_workload(args.workload)
+    w, f, t, x, sb, n_in = make_workload(
+        args.workload, lambda nt, ns, fr, g: oracle.sb_table(nt, ns, fr, 1500.0, 0.80, 1296.0, 144.0, g))
     per_step = max(0.05, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
     _, cores, desc, _, rr = oracle_sample_rate(x, sb, f, t, w, n_in, per_step)
     units = sum(r["n_dm"] * (w["n_out"] // r["downsamp"]) for r in rr)

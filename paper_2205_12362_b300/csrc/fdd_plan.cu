@@ -200,7 +200,7 @@ void free_brute_tables(RangeState& r) {
 void free_range_tables(RangeState& r) {
     free_brute_tables(r);
     free_fact_tables(r);
-    free_sbf_tables(r, false);
+    free_sbf_tables(r, true);
 }
 
 int upload_vec(int32_t** dst, const std::vector<int32_t>& v, const char* what) {
@@ -230,7 +230,7 @@ int configure_fact(fdd_plan* p, RangeState& r, int fv, int CC) {
     }
     if (best_cc == 0) return fail(FDD_ERR_UNSUPPORTED, "factored kernel does not fit this range and stage size");
     free_fact_tables(r);
-    free_sbf_tables(r, false);
+    free_sbf_tables(r, true);
     int rc;
     if ((rc = upload_vec(&r.d_fbase, best.base, "factored base table")) != FDD_OK) return rc;
     if ((rc = upload_vec(&r.d_goff, best.goff, "factored offset table")) != FDD_OK) return rc;
@@ -438,7 +438,7 @@ static int build_host_plan(const fdd_plan_desc* desc, const int16_t* sb_map_host
     }
     p->n_dm_total = dm_index;
     for (RangeState& r : p->ranges) {
-        r.segs = sbf_segments(p, r.D);
+        r.segs = sbf_segments(p, r.D, 16);
         r.seg_maxlen = 0;
         for (const int2& sg : r.segs) r.seg_maxlen = std::max(r.seg_maxlen, sg.y);
     }

@@ -32,9 +32,10 @@ struct RangeState {
     int32_t* d_pdesc = nullptr;
     int32_t* d_pdidx = nullptr;
     // SB-factored kernel (sbf >= 0 selects it); segments are plan geometry
-    std::vector<int2> segs;           // channel segments on which every SB keeps one TAB
+    std::vector<int2> segs;           // segments on which every SB keeps one TAB, cut at 16 channels (scratch sizing)
     int32_t seg_maxlen = 0;
-    int2* d_segs = nullptr;           // device copy of segs
+    int32_t s_n_seg = 0;              // segments of the configured SB-factored kernel (cut at its CC)
+    int2* d_segs = nullptr;           // configured segments
     uint8_t* d_segtab = nullptr;      // [n_sb][seg_pitch]
     int32_t seg_pitch = 0;
     int sbf = -1;
@@ -138,7 +139,7 @@ struct Layout {
 Layout make_layout(const fdd_plan* p, int64_t n_in, int64_t n_out, bool with_series);
 // SB-factored kernel (fdd_sbf.cu).
 constexpr size_t kSbfScratchMax = size_t(4) << 30;
-std::vector<int2> sbf_segments(const fdd_plan* p, int D);
+std::vector<int2> sbf_segments(const fdd_plan* p, int D, int cap);
 size_t sbf_scratch_bytes(const fdd_plan* p, int64_t n_out);
 int configure_sbf(fdd_plan* p, RangeState& r, int sv, int CC);
 void free_sbf_tables(RangeState& r, bool geometry);

@@ -3,9 +3,11 @@
 // k_sbf.cu).
 //
 // Segments: maximal runs of consecutive channels on which every SB takes
-// the same TAB throughout, cut to at most min(16, 65535 / (255 D)) channels
-// so a segment's sum of D-sample sums fits a 16-bit lane.  Stages: whole
-// segments packed into at most CC channels.  The partial sums of a slab of
+// the same TAB throughout, cut to at most min(CC, 65535 / (255 D)) channels
+// so a segment's sum of D-sample sums fits a 16-bit lane and a segment fits
+// one channel stage.  Stages: whole segments packed into at most CC
+// channels.  The scratch is sized for segments cut at 16 channels, which
+// no configuration with CC >= 16 exceeds in number.  The partial sums of a slab of
 // DM trials, [n_tab][n_seg][slab][Np] uint16, live in a scratch region of
 // the search workspace bounded by kSbfScratchMax; the slab is the largest
 // multiple of the variant's DM block that fits.
@@ -16,8 +18,6 @@
 using namespace fdd::host;
 
 namespace {
-
-constexpr int kSbfSegMax = 16;
 
 int64_t round_up64(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
@@ -34,7 +34,7 @@ int upload(T** dst, const std::vector<T>& v, const char* what) {
 
 // Slab of DM trials whose partial sums fit the scratch (a multiple of BD).
 int64_t slab_trials(const fdd_plan* p, const RangeState& r, int64_t nr, int BD, size_t scratch_bytes) {
-    const int64_t per_trial = static_cast<int64_t>(p->n_tab) * static_cast<int64_t>(r.segs.size()) * sbf_np(nr) * 2;
+    const int64_t per_trial = static_cast<int64_t>(p->n_tab) * static_cast<int64_t>(r.s_n_seg) * sbf_np(nr) * 2;
     int64_t slab = static_cast<int64_t>(scratch_bytes) / per_trial / BD * BD;
     return std::min<int64_t>(slab, round_up64(r.n_dm, BD));
 }
@@ -44,8 +44,8 @@ int64_t slab_trials(const fdd_plan* p, const RangeState& r, int64_t nr, int BD, 
 namespace fdd {
 namespace host {
 
-std::vector<int2> sbf_segments(const fdd_plan* p, int D) {
-    const int max_len = std::max(1, std::min(kSbfSegMax, 65535 / (255 * D)));
+std::vector<int2> sbf_segments(const fdd_plan* p, int D, int cap) {
+    const int max_len = std::max(1, std::min(cap, 65535 / (255 * D)));
     std::vector<int2> segs;
     int c0 = 0;
     for (int c = 1; c <= p->n_chan; c++) {
@@ -77,7 +77,7 @@ size_t sbf_scratch_bytes(const fdd_plan* p, int64_t n_out) {
 double sbf_work_ratio(const fdd_plan* p, const RangeState& r) {
     // per (trial, sample): n_tab * n_chan partial adds + n_sb * n_seg combine adds
     const double brute = static_cast<double>(p->n_sb) * p->n_chan;
-    const double fact = static_cast<double>(p->n_tab) * p->n_chan + static_cast<double>(p->n_sb) * r.segs.size();
+    const double fact = static_cast<double>(p->n_tab) * p->n_chan + static_cast<double>(p->n_sb) * r.s_n_seg;
     return fact / brute;
 }
 
@@ -108,18 +108,23 @@ int configure_sbf(fdd_plan* p, RangeState& r, int sv, int CC) {
     if (v.E != (r.D == 1 ? 1 : 2)) return fail(FDD_ERR_INVALID_ARG, "kernel variant for the wrong sample width");
     const HostTables h = build_tables(p, r, v);
     if (h.Lw < 0) return fail(FDD_ERR_UNSUPPORTED, "DM step too large for one block's staged rows");
-    const int seg_max = r.seg_maxlen;
     int cc_pick = 0;
+    std::vector<int2> segs;
     for (int cc : {64, 48, 32, 16, 8, 4, 2, 1}) {
         if (CC != 0 && cc != CC) continue;
-        if (cc < seg_max || !fdd::sbf_cc_ok(v, h.Lw, cc, kSmemBudget)) continue;
+        if (!fdd::sbf_cc_ok(v, h.Lw, cc, kSmemBudget)) continue;
+        std::vector<int2> sg = sbf_segments(p, r.D, cc);
+        if (sg.size() > r.segs.size()) continue;  // more segments than the scratch was sized for
         cc_pick = cc;
+        segs.swap(sg);
         break;
     }
     if (cc_pick == 0) return fail(FDD_ERR_UNSUPPORTED, "SB-factored kernel does not fit this range and stage size");
+    int seg_max = 1;
+    for (const int2& sg : segs) seg_max = std::max(seg_max, sg.y);
     std::vector<int4> stages;
-    for (size_t g = 0; g < r.segs.size(); g++) {
-        const int2 sg = r.segs[g];
+    for (size_t g = 0; g < segs.size(); g++) {
+        const int2 sg = segs[g];
         if (!stages.empty() && stages.back().y + sg.y <= cc_pick) {
             stages.back().y += sg.y;
             stages.back().w += 1;
@@ -127,21 +132,20 @@ int configure_sbf(fdd_plan* p, RangeState& r, int sv, int CC) {
             stages.push_back(make_int4(sg.x, sg.y, static_cast<int>(g), 1));
         }
     }
-    free_sbf_tables(r, false);
+    free_sbf_tables(r, true);
     int rc;
-    if (!r.d_segs) {
-        if ((rc = upload(&r.d_segs, r.segs, "segment table")) != FDD_OK) return rc;
-        r.seg_pitch = static_cast<int32_t>(round_up64(static_cast<int64_t>(r.segs.size()), 8));  // whole 8-segment chunks
-        std::vector<uint8_t> tab(static_cast<size_t>(p->n_sb) * r.seg_pitch, 0);
-        for (int s = 0; s < p->n_sb; s++)
-            for (size_t g = 0; g < r.segs.size(); g++)
-                tab[static_cast<size_t>(s) * r.seg_pitch + g] =
-                    static_cast<uint8_t>(p->sb_map[static_cast<size_t>(s) * p->n_chan + r.segs[g].x]);
-        if ((rc = upload(&r.d_segtab, tab, "segment TAB table")) != FDD_OK) return rc;
-    }
+    if ((rc = upload(&r.d_segs, segs, "segment table")) != FDD_OK) return rc;
+    r.seg_pitch = static_cast<int32_t>(round_up64(static_cast<int64_t>(segs.size()), 8));  // whole 8-segment chunks
+    std::vector<uint8_t> tab(static_cast<size_t>(p->n_sb) * r.seg_pitch, 0);
+    for (int s = 0; s < p->n_sb; s++)
+        for (size_t g = 0; g < segs.size(); g++)
+            tab[static_cast<size_t>(s) * r.seg_pitch + g] =
+                static_cast<uint8_t>(p->sb_map[static_cast<size_t>(s) * p->n_chan + segs[g].x]);
+    if ((rc = upload(&r.d_segtab, tab, "segment TAB table")) != FDD_OK) return rc;
     if ((rc = upload(&r.d_sbase, h.base, "base table")) != FDD_OK) return rc;
     if ((rc = upload(&r.d_soff, h.off, "offset table")) != FDD_OK) return rc;
     if ((rc = upload(&r.d_sstages, stages, "stage table")) != FDD_OK) return rc;
+    r.s_n_seg = static_cast<int32_t>(segs.size());
     r.sbf = sv;
     r.s_CC = cc_pick;
     r.s_Lw = h.Lw;
@@ -168,7 +172,7 @@ cudaError_t launch_range_sbf(const fdd_plan* p, const RangeState& r, const fdd::
     const int64_t Np = sbf_np(nr);
     const int64_t slab = slab_trials(p, r, nr, BD, scratch_bytes);
     if (slab < BD) return cudaErrorInvalidValue;  // scratch sized by sbf_scratch_bytes always holds one block
-    const int64_t n_seg = static_cast<int64_t>(r.segs.size());
+    const int64_t n_seg = r.s_n_seg;
     fdd::SbfPartArgs pa{};
     pa.in = a.in;
     pa.pitch_bytes = a.pitch_bytes;

@@ -539,3 +539,37 @@ def test_boxcar_width_sets(fdd):
     for g, o in zip(gs, os_):
         assert (g == o).all()
     assert compare_candidates(gpu, ora, 5.0) > 0
+
+
+def test_sb_factored_geometry_table(fdd):
+    """SB-factored kernels on the SB table the library builds from the array
+    geometry (Apertif-10, 71 SBs, TABs combined in 48-channel subbands):
+    segments longer than 16 channels, sampled SBs against the oracle, DM 0 of
+    every SB against a numpy gather-sum."""
+    import torch
+    n_tab, n_chan, n_sb, n_out = 12, 1536, 71, 2000
+    f = synth.channel_freqs(n_chan)
+    sb = fdd.sb_table(n_tab, n_sb, f, chan_per_subband=48)
+    ranges = [dict(dm0=0.0, ddm=0.4, n_dm=96, downsamp=1, widths=[1, 4, 16])]
+    n_in = n_out + int(oracle.delays(f, T_SAMP, 0.0, 0.4, 96).max()) + 3
+    pulses = [dict(tab=k, start=900 + oracle.delays(f, T_SAMP, 20.0, 1.0, 1)[0], width=4, amp=12.0) for k in (0, 5, 11)]
+    x = synth.filterbank(23, n_tab, n_chan, n_in, pulses=pulses)
+    plan = fdd.Plan(n_tab, n_chan, n_sb, f, T_SAMP, ranges, 7.0, sb)
+    v = [v for v in fdd.variants() if v["kind"] == 2 and v["bytes_per_sample"] == 1][0]
+    plan.set_config(0, v["index"])
+    cfg = plan.get_config(0)
+    assert cfg["chan_per_stage"] >= 48 and cfg["work_ratio"] < 0.15
+    res = plan.search(to_dev(x), n_in, n_out, want_series=True, cap=1 << 20)
+    torch.cuda.synchronize()
+    gpu, n = res.candidates()
+    series = plan.series_views(res.series, n_out)[0]
+    dm0 = np.zeros((n_sb, n_out), np.int64)
+    for c in range(n_chan):
+        dm0 += x[sb[:, c], c, :n_out]
+    assert (series[:, 0].cpu().numpy() == dm0).all()
+    for s in (0, 35, 52, 70):
+        ora, os_ = oracle_candidate_superset(x, sb[s:s + 1], f, T_SAMP, ranges, 7.0, n_out, n_in, return_series=True)
+        assert (series[s].cpu().numpy() == os_[0][0]).all()
+        ora = ora.copy()
+        ora["sb"] = s
+        compare_candidates(gpu[gpu["sb"] == s], ora, 7.0)
