@@ -47,7 +47,7 @@ def lib():
         L.oracle_stats.argtypes = [_P, _I64, _P, _P]
         L.oracle_boxcar_snr.argtypes = [_P, _I64, _I32, _D, _D, _P]
         L.oracle_search.argtypes = [_P, _I32, _I32, _I64, _I64, _P, _I32, _P, _D, _I32,
-                                    _P, _P, _P, _P, _P, _P, _D, _I64, _I64, _P, _I64, _P]
+                                    _P, _P, _P, _P, _P, _P, _D, _I64, _I64, _P, _I64, _P, _P, _P]
         L.oracle_search.restype = _I64
         L.oracle_cluster.argtypes = [_P, _I64, _P]
         L.oracle_cluster.restype = _I64
@@ -129,7 +129,9 @@ def search(x, sb_map, freq_mhz, t_samp_s, ranges, snr_thresh, n_out, n_in=None,
            t_offset_native=0, cap=1 << 20, return_series=False):
     """Run the whole hot path on x: uint8[n_tab][n_chan][pitch].
 
-    ranges: list of dicts {dm0, ddm, n_dm, downsamp, widths}.
+    ranges: list of dicts {dm0, ddm, n_dm, downsamp, widths} and optionally
+    subband=(G, K): that range uses the two-step subband dedispersion of
+    oracle.c (subbands of G channels, coarse DM blocks of K fine trials).
     Returns (candidates: structured array sorted by (sb, dm_index, width, t),
     total_count, series) where series is a list (one per range) of
     int64[n_sb][n_dm][n_out // D] or None.
@@ -152,6 +154,8 @@ def search(x, sb_map, freq_mhz, t_samp_s, ranges, snr_thresh, n_out, n_in=None,
     nw = np.array([len(r["widths"]) for r in ranges], dtype=np.int32)
     ws = np.ascontiguousarray(np.concatenate([np.asarray(r["widths"], dtype=np.int32)
                                               for r in ranges]), dtype=np.int32)
+    sub_g = np.array([int(r.get("subband", (0, 0))[0]) for r in ranges], dtype=np.int32)
+    sub_k = np.array([int(r.get("subband", (0, 1))[1]) for r in ranges], dtype=np.int32)
     cands = np.zeros(max(int(cap), 1), dtype=CAND_DTYPE)
     series = None
     if return_series:
@@ -162,7 +166,7 @@ def search(x, sb_map, freq_mhz, t_samp_s, ranges, snr_thresh, n_out, n_in=None,
                             float(t_samp_s), len(ranges), _ptr(dm0), _ptr(ddm), _ptr(ndm),
                             _ptr(ds), _ptr(nw), _ptr(ws), float(snr_thresh), int(n_out),
                             int(t_offset_native), _ptr(cands), int(cap),
-                            _ptr(series) if series is not None else None)
+                            _ptr(series) if series is not None else None, _ptr(sub_g), _ptr(sub_k))
     if n == -1:
         raise ValueError("input too short for the DM plan")
     if n < 0:

@@ -153,6 +153,109 @@ void oracle_boxcar_snr(const int64_t* s, int64_t n, int32_t w, double mean, doub
     }
 }
 
+/* Two-step subband dedispersion (Sec. "AMBER", "Dedispersion": besides a
+ * single step, the module dedisperses "using a more efficient two step
+ * process including subbanding"; Table "dedispersion setup": 32 subbands and
+ * a subbanding DM step 32x the fine step).  An approximation of brute force,
+ * written in the paper's order:
+ *   step 1, per subband b and coarse DM block q, the subband's channels are
+ *     aligned to the subband's own reference frequency at the block's coarse
+ *     DM:  P[tab][b][q][u] = sum_{c in b} y[tab][c][u + d1[q][c]];
+ *   step 2, per fine trial i of block q, the subbands are aligned at the fine
+ *     DM:  S[s][i][t] = sum_b P[tab(s,b)][b][q][t + d2[i][b]].
+ * Readings (the paper gives only the sizes): subband b = channels
+ * [b*G, (b+1)*G) (the last may be shorter); its reference f_b is its highest
+ * channel frequency; fine trial i belongs to block q = i / K whose DM is the
+ * block's midpoint DMc_q = dm0 + (q*K + (K-1)/2) * ddm;
+ *   d1[q][c] = llround(kDM*DMc_q*(1/f_c^2 - 1/f_b^2) / (D t)),
+ *   d2[i][b] = llround(kDM*DM_i*(1/f_b^2 - 1/f_top^2) / (D t)),
+ * in the same FP64 expression order as oracle_delays; the SB takes, for the
+ * whole subband, the TAB of the subband's first channel (tab(s,b)).
+ * n1 = n_out + max d2 samples of P are formed per (tab, b, q).  series gets
+ * n_sb*n_dm rows of n_out; returns -1 if n_y is too short, -2 on allocation
+ * failure, else the largest d1 + d2. */
+int64_t oracle_dedisperse_two_step(const uint32_t* y, int32_t n_tab, int32_t n_chan, int64_t n_y,
+                                   const double* freq_mhz, double t_samp_s, int32_t downsamp,
+                                   double dm0, double ddm, int32_t n_dm, int32_t G, int32_t K,
+                                   const int32_t* sb_map, int32_t n_sb, int64_t n_out, int64_t* series) {
+    const int32_t n_sub = (n_chan + G - 1) / G;
+    const int32_t n_q = (n_dm + K - 1) / K;
+    double f_top = freq_mhz[0];
+    for (int32_t c = 1; c < n_chan; c++)
+        if (freq_mhz[c] > f_top) f_top = freq_mhz[c];
+    double* f_ref = (double*)malloc(sizeof(double) * (size_t)n_sub);
+    int64_t* d1 = (int64_t*)malloc(sizeof(int64_t) * (size_t)n_q * (size_t)n_chan);
+    int64_t* d2 = (int64_t*)malloc(sizeof(int64_t) * (size_t)n_dm * (size_t)n_sub);
+    if (!f_ref || !d1 || !d2) { free(f_ref); free(d1); free(d2); return -2; }
+    for (int32_t b = 0; b < n_sub; b++) {
+        f_ref[b] = freq_mhz[b * G];
+        for (int32_t c = b * G; c < n_chan && c < (b + 1) * G; c++)
+            if (freq_mhz[c] > f_ref[b]) f_ref[b] = freq_mhz[c];
+    }
+    const double tD = (double)downsamp * t_samp_s;
+    int64_t d1max = 0, d2max = 0, dsum = 0;
+    for (int32_t q = 0; q < n_q; q++) {
+        const double dmc = dm0 + ((double)q * K + 0.5 * (double)(K - 1)) * ddm;
+        for (int32_t c = 0; c < n_chan; c++) {
+            const double f = freq_mhz[c], fb = f_ref[c / G];
+            const int64_t d = (int64_t)llround(((ORACLE_KDM * dmc) * (1.0 / (f * f) - 1.0 / (fb * fb))) / tD);
+            d1[(int64_t)q * n_chan + c] = d;
+            if (d > d1max) d1max = d;
+        }
+    }
+    for (int32_t i = 0; i < n_dm; i++) {
+        const double dm = dm0 + (double)i * ddm;
+        for (int32_t b = 0; b < n_sub; b++) {
+            const double fb = f_ref[b];
+            const int64_t d = (int64_t)llround(((ORACLE_KDM * dm) * (1.0 / (fb * fb) - 1.0 / (f_top * f_top))) / tD);
+            d2[(int64_t)i * n_sub + b] = d;
+            if (d > d2max) d2max = d;
+        }
+    }
+    for (int32_t i = 0; i < n_dm; i++)
+        for (int32_t c = 0; c < n_chan; c++) {
+            const int64_t v = d1[(int64_t)(i / K) * n_chan + c] + d2[(int64_t)i * n_sub + c / G];
+            if (v > dsum) dsum = v;
+        }
+    const int64_t n1 = n_out + d2max;
+    if (n1 + d1max > n_y || n_out + dsum > n_y) { free(f_ref); free(d1); free(d2); return -1; }
+    int64_t* P = (int64_t*)malloc(sizeof(int64_t) * (size_t)n_tab * (size_t)n_sub * (size_t)(n1 > 0 ? n1 : 1));
+    if (!P) { free(f_ref); free(d1); free(d2); return -2; }
+    for (int32_t q = 0; q < n_q; q++) {
+        /* step 1 for block q */
+#pragma omp parallel for schedule(static)
+        for (int64_t tb = 0; tb < (int64_t)n_tab * n_sub; tb++) {
+            const int32_t tab = (int32_t)(tb / n_sub), b = (int32_t)(tb % n_sub);
+            int64_t* prow = P + tb * n1;
+            for (int64_t u = 0; u < n1; u++) prow[u] = 0;
+            for (int32_t c = b * G; c < n_chan && c < (b + 1) * G; c++) {
+                const uint32_t* row = y + ((int64_t)tab * n_chan + c) * n_y;
+                const int64_t off = d1[(int64_t)q * n_chan + c];
+                for (int64_t u = 0; u < n1; u++) prow[u] += (int64_t)row[u + off];
+            }
+        }
+        /* step 2 for the fine trials of block q */
+        const int32_t i_end = (q + 1) * K < n_dm ? (q + 1) * K : n_dm;
+#pragma omp parallel for schedule(static)
+        for (int64_t si = 0; si < (int64_t)n_sb * (i_end - q * K); si++) {
+            const int32_t s = (int32_t)(si / (i_end - q * K)), i = q * K + (int32_t)(si % (i_end - q * K));
+            int64_t* acc = series + ((int64_t)s * n_dm + i) * n_out;
+            for (int64_t t = 0; t < n_out; t++) acc[t] = 0;
+            for (int32_t b = 0; b < n_sub; b++) {
+                const int32_t tab = sb_map[(int64_t)s * n_chan + b * G];
+                const int64_t* prow = P + ((int64_t)tab * n_sub + b) * n1;
+                const int64_t off = d2[(int64_t)i * n_sub + b];
+                for (int64_t t = 0; t < n_out; t++) acc[t] += prow[t + off];
+            }
+        }
+    }
+    free(P);
+    free(f_ref);
+    free(d1);
+    free(d2);
+    return dsum;
+}
+
 typedef struct {
     int32_t sb, dm_index, downsamp, width_native;
     int64_t t_native;
@@ -178,7 +281,7 @@ int64_t oracle_search(const uint8_t* x, int32_t n_tab, int32_t n_chan, int64_t n
                       const int32_t* downsamp, const int32_t* n_width,
                       const int32_t* widths, double thr, int64_t n_out,
                       int64_t t_offset_native, oracle_cand* cands, int64_t cap,
-                      int64_t* series_or_null) {
+                      int64_t* series_or_null, const int32_t* sub_chan, const int32_t* sub_k) {
     int64_t count = 0;
     int32_t dm_base = 0, w_base = 0;
     int64_t series_base = 0;
@@ -189,9 +292,18 @@ int64_t oracle_search(const uint8_t* x, int32_t n_tab, int32_t n_chan, int64_t n
         uint32_t* y = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)n_tab * (size_t)n_chan * (size_t)n_y);
         if (!d || !y) { free(d); free(y); return -2; }
         int64_t dmax = oracle_delays(n_chan, freq_mhz, t_samp_s, dm0[r], ddm[r], n_dm[r], D, d, NULL);
-        if (n_r + dmax > n_y) { free(d); free(y); return -1; }
+        const int two_step = sub_chan && sub_k && sub_chan[r] > 0;
+        if (!two_step && n_r + dmax > n_y) { free(d); free(y); return -1; }
         oracle_downsample(x, (int64_t)n_tab * n_chan, n_in, pitch, D, y);
         int64_t n_series = (int64_t)n_sb * n_dm[r];
+        int64_t* ts = NULL;  /* two-step series of this range */
+        if (two_step) {
+            ts = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_series > 0 ? n_series : 1) * (size_t)(n_r > 0 ? n_r : 1));
+            if (!ts) { free(d); free(y); return -2; }
+            const int64_t rc = oracle_dedisperse_two_step(y, n_tab, n_chan, n_y, freq_mhz, t_samp_s, D, dm0[r], ddm[r],
+                                                          n_dm[r], sub_chan[r], sub_k[r], sb_map, n_sb, n_r, ts);
+            if (rc < 0) { free(ts); free(d); free(y); return rc == -1 ? -1 : -2; }
+        }
 #pragma omp parallel
         {
             int64_t* acc = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_r > 0 ? n_r : 1));
@@ -199,8 +311,11 @@ int64_t oracle_search(const uint8_t* x, int32_t n_tab, int32_t n_chan, int64_t n
 #pragma omp for schedule(dynamic, 1)
             for (int64_t q = 0; q < n_series; q++) {
                 int32_t s = (int32_t)(q / n_dm[r]), i = (int32_t)(q % n_dm[r]);
-                dedisperse_one(y, n_chan, n_y, sb_map + (int64_t)s * n_chan,
-                               d + (int64_t)i * n_chan, n_r, acc);
+                if (ts)
+                    memcpy(acc, ts + q * n_r, sizeof(int64_t) * (size_t)n_r);
+                else
+                    dedisperse_one(y, n_chan, n_y, sb_map + (int64_t)s * n_chan,
+                                   d + (int64_t)i * n_chan, n_r, acc);
                 if (series_or_null)
                     memcpy(series_or_null + series_base + q * n_r, acc, sizeof(int64_t) * (size_t)n_r);
                 if (n_r == 0) continue;
@@ -233,6 +348,7 @@ int64_t oracle_search(const uint8_t* x, int32_t n_tab, int32_t n_chan, int64_t n
             free(acc);
             free(snr);
         }
+        free(ts);
         free(d);
         free(y);
         dm_base += n_dm[r];
