@@ -460,6 +460,28 @@ int fdd_cluster(const fdd_candidate* d_in, const uint64_t* d_in_count, int64_t c
                 size_t workspace_bytes, fdd_candidate* d_out, int64_t cap_out, uint64_t* d_out_count,
                 fdd_stream_t stream);
 
+/* Two-step subband dedispersion for range r (APPROXIMATE; the paper's AMBER
+ * can dedisperse "using a more efficient two step process including
+ * subbanding", Sec. "AMBER", "Dedispersion"; Table "dedispersion setup": 32
+ * subbands, subbanding DM step 32x the fine step).  Subbands of
+ * chan_per_subband channels are first aligned to their top channel at the
+ * midpoint DM of each block of dm_per_coarse fine trials, then the subbands
+ * are aligned at every fine DM:
+ *   d1[q][c] = llround(K*DMc_q*(f_c^-2 - f_b^-2)/(D t)),
+ *   d2[i][b] = llround(K*DM_i*(f_b^-2 - f_top^-2)/(D t)),
+ *   S[s][i][t] = sum_b sum_{c in b} y[tab(s,b)][c][t + d2[i][b] + d1[i/K'][c]]
+ * (f_b = top channel of subband b, DMc_q = dm0 + (q K' + (K'-1)/2) ddm,
+ * K' = dm_per_coarse).  About (n_chan/K' + n_sub) adds per trial and sample
+ * instead of n_chan; S/N of pulses narrower than the intra-subband smearing
+ * drops.  The SB map must keep one TAB per subband (FDD_ERR_UNSUPPORTED
+ * otherwise); chan_per_subband <= 64 and <= 65535 / (255 D).  Applies to
+ * fdd_search, fdd_search_static and streams; batched searches refuse plans
+ * with a range in this mode.  May raise fdd_plan_max_delay and
+ * fdd_workspace_size (re-query after the call).  chan_per_subband = 0
+ * restores exact dedispersion. */
+int fdd_plan_set_subband(fdd_plan* plan, int32_t r, int32_t chan_per_subband, int32_t dm_per_coarse);
+int fdd_plan_get_subband(const fdd_plan* plan, int32_t r, int32_t* chan_per_subband, int32_t* dm_per_coarse);
+
 /* Number of kernels the last fdd_search or fdd_search_batch on this plan
  * enqueued (graph launches replay the last captured batch's kernels). */
 int fdd_plan_last_launches(const fdd_plan* plan, int64_t* n);

@@ -161,6 +161,8 @@ def _lib_raw():
     L.fdd_variant_kind.argtypes = [_I32, ctypes.POINTER(_I32)]
     L.fdd_plan_set_scratch_limit.argtypes = [_P, _I64]
     L.fdd_plan_last_launches.argtypes = [_P, ctypes.POINTER(_I64)]
+    L.fdd_plan_set_subband.argtypes = [_P, _I32, _I32, _I32]
+    L.fdd_plan_get_subband.argtypes = [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]
     L.fdd_sb_table.argtypes = [_I32, _I32, _I32, _P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                ctypes.c_double, _I32, _P]
     L.fdd_cluster_workspace_size.argtypes = [_I64, ctypes.POINTER(_SZ)]
@@ -578,6 +580,17 @@ class Plan:
         v = _I64()
         _check(_lib_raw().fdd_plan_max_delay(self._h, ctypes.byref(v)), "fdd_plan_max_delay")
         return int(v.value)
+
+    def set_subband(self, r, chan_per_subband, dm_per_coarse):
+        """Two-step subband dedispersion (approximate) for range r; (0, 0)
+        restores exact dedispersion (include/fdd.h: fdd_plan_set_subband)."""
+        _check(_lib_raw().fdd_plan_set_subband(self._h, int(r), int(chan_per_subband), int(dm_per_coarse)),
+               "fdd_plan_set_subband")
+
+    def get_subband(self, r):
+        g, k = _I32(), _I32()
+        _check(_lib_raw().fdd_plan_get_subband(self._h, int(r), ctypes.byref(g), ctypes.byref(k)), "fdd_plan_get_subband")
+        return int(g.value), int(k.value)
 
     def last_launches(self):
         """Kernels enqueued by the last search / batched search (include/fdd.h:

@@ -89,6 +89,7 @@ __device__ __forceinline__ void dedisp_tile(const DedispArgs& a, int tile_x, int
     const int64_t limit = a.n_valid * E;  // valid bytes per input row
     const int16_t* sbm = a.sb_map + (int64_t)sb * a.n_chan;
     const int32_t* base_blk = a.base + (int64_t)blk * a.n_chan;
+    const uint8_t* in_blk = a.in + (a.blk_per_coarse > 0 ? (int64_t)(blk / a.blk_per_coarse) * a.coarse_stride : 0);
     const int32_t* off_blk = a.off + (int64_t)blk * a.n_chan * BD;
 
     // ---- staging registers (one stage in flight)
@@ -105,7 +106,7 @@ __device__ __forceinline__ void dedisp_tile(const DedispArgs& a, int tile_x, int
                 const int cc = it / chunks;
                 const int m = it - cc * chunks;
                 const int c = c0 + cc;
-                const uint8_t* row = a.in + ((int64_t)sbm[c] * a.n_chan + c) * a.pitch_bytes;
+                const uint8_t* row = in_blk + ((int64_t)sbm[c] * a.n_chan + c) * a.pitch_bytes;
                 const int64_t b0 = (int64_t)(t0 + base_blk[c]) * E + 16 * (int64_t)m;
                 if (b0 + 20 <= limit) {
                     pv[u] = __ldg(reinterpret_cast<const uint4*>(row + b0));

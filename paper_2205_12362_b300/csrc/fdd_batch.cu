@@ -33,6 +33,9 @@ void free_batch(BatchState& b) {
 }
 
 int batch_eligible(const fdd_plan* p) {
+    for (const RangeState& r : p->ranges)
+        if (r.sub_G > 0)
+            return fail(FDD_ERR_UNSUPPORTED, "batched search runs exact dedispersion only; a range is in subband mode");
     if (static_cast<int>(p->ranges.size()) > fdd::kMaxRanges)
         return fail(FDD_ERR_UNSUPPORTED, "batched search supports at most FDD_MAX_RANGES DM ranges");
     if (static_cast<int>(p->ds_factors.size()) > fdd::kMaxDs)

@@ -45,6 +45,10 @@ struct DedispArgs {
     int32_t n_sb;
     int32_t Lw;                 // 32-bit words per staged copy row
     int32_t CC;                 // channels per smem stage (divides 256 when E == 1)
+    // two-step subband mode, second step: DM block blk reads its rows coarse_stride bytes further per
+    // coarse block (blk / blk_per_coarse); 0 = off
+    int32_t blk_per_coarse;
+    int64_t coarse_stride;
 };
 
 // Shared-memory bytes of one dedispersion block.

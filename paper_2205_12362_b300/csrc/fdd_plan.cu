@@ -17,10 +17,6 @@ namespace {
 
 thread_local std::string g_last_error;
 
-// Cold-plasma dispersion constant, s MHz^2 / (pc cm^-3).  The paper gives no
-// value; 4148.808 is the standard constant.
-constexpr double kDispersionConstant = 4148.808;
-
 }  // namespace
 
 namespace fdd {
@@ -144,7 +140,7 @@ fdd::host::Layout fdd::host::make_layout(const fdd_plan* p, int64_t n_in, int64_
     L.series_bytes = series_elems * sizeof(int32_t);
     L.stat_bytes = n_series * 2 * sizeof(unsigned long long);
     size_t cur = 0;
-    L.sbf_bytes = sbf_scratch_bytes(p, n_out);
+    L.sbf_bytes = std::max(sbf_scratch_bytes(p, n_out), subband_scratch_bytes(p, n_out));
     if (L.sbf_bytes) {
         L.sbf = cur;
         cur = align_up(cur + L.sbf_bytes, 256);
@@ -312,6 +308,7 @@ int range_variant_index(const RangeState& r) {
 // Dedispersion of one range with whichever kernel it is configured for.
 cudaError_t launch_range(const fdd_plan* p, const RangeState& r, const fdd::DedispArgs& a, const Layout& L,
                          uint8_t* ws, cudaStream_t s, int64_t* launches = nullptr) {
+    if (r.sub_G > 0) return launch_range_subband(p, r, a, ws + L.sbf, L.sbf_bytes, s, launches);
     if (r.sbf >= 0) return launch_range_sbf(p, r, a, ws + L.sbf, L.sbf_bytes, s, launches);
     if (launches) *launches += 1;
     return launch_range_dedisp(r, a, s);
@@ -511,6 +508,7 @@ int fdd_plan_destroy(fdd_plan* plan) {
     for (RangeState& r : plan->ranges) {
         free_range_tables(r);
         free_sbf_tables(r, true);
+        free_subband_tables(r);
     }
     if (plan->d_sb_map) cudaFree(plan->d_sb_map);
     delete plan;
@@ -892,6 +890,33 @@ int fdd_fact_tables_host(const fdd_plan_desc* desc, const int16_t* sb_map_host, 
     if (pdesc) std::memcpy(pdesc, ft.pdesc.data(), ft.pdesc.size() * sizeof(int32_t));
     if (pd_idx) std::memcpy(pd_idx, ft.pd_idx.data(), ft.pd_idx.size() * sizeof(int32_t));
     if (delays) std::memcpy(delays, r.delay.data(), r.delay.size() * sizeof(int32_t));
+    return FDD_OK;
+}
+
+int fdd_plan_set_subband(fdd_plan* plan, int32_t r, int32_t chan_per_subband, int32_t dm_per_coarse) {
+    if (!plan || r < 0 || r >= static_cast<int32_t>(plan->ranges.size()) || chan_per_subband < 0 || dm_per_coarse < 0)
+        return fail(FDD_ERR_INVALID_ARG, "bad argument");
+    RangeState& rs = plan->ranges[r];
+    if (rs.sub_G == 0) rs.sub_dmax_exact = rs.dmax;
+    if (chan_per_subband == 0) {
+        free_subband_tables(rs);
+        rs.dmax = rs.sub_dmax_exact;
+    } else {
+        const int rc = configure_subband(plan, rs, chan_per_subband, dm_per_coarse);
+        if (rc != FDD_OK) return rc;
+        rs.dmax = std::max(rs.sub_dmax_exact, rs.sub_d1max + rs.sub_d2max);
+    }
+    plan->max_delay_native = 0;
+    for (const RangeState& q : plan->ranges)
+        plan->max_delay_native = std::max<int64_t>(plan->max_delay_native, static_cast<int64_t>(q.dmax) * q.D);
+    return FDD_OK;
+}
+
+int fdd_plan_get_subband(const fdd_plan* plan, int32_t r, int32_t* chan_per_subband, int32_t* dm_per_coarse) {
+    if (!plan || r < 0 || r >= static_cast<int32_t>(plan->ranges.size()) || !chan_per_subband || !dm_per_coarse)
+        return fail(FDD_ERR_INVALID_ARG, "bad argument");
+    *chan_per_subband = plan->ranges[r].sub_G;
+    *dm_per_coarse = plan->ranges[r].sub_K;
     return FDD_OK;
 }
 

@@ -44,6 +44,18 @@ struct RangeState {
     int32_t* d_sbase = nullptr;
     int32_t* d_soff = nullptr;
     int4* d_sstages = nullptr;
+    // two-step subband mode (approximate; sub_G > 0 selects it for fdd_search)
+    int32_t sub_G = 0, sub_K = 0, sub_n = 0, sub_nq = 0;   // channels per subband, fine trials per coarse DM
+    int32_t sub_d1max = 0, sub_d2max = 0, sub_dmax_exact = 0;
+    int sub_pv = -1, sub_bv = -1;                          // step-1 (SB-factored part) / step-2 (brute E=2) variants
+    int32_t sub_pCC = 0, sub_pLw = 0, sub_pstages = 0, sub_bCC = 0, sub_bLw = 0;
+    int32_t* d_sub_pbase = nullptr;
+    int32_t* d_sub_poff = nullptr;
+    int4* d_sub_pstages = nullptr;
+    int2* d_sub_psegs = nullptr;
+    int32_t* d_sub_bbase = nullptr;
+    int32_t* d_sub_boff = nullptr;
+    int16_t* d_sub_sbmap = nullptr;                       // [n_sb][sub_n]
 };
 
 // Device tables of one range for the batched persistent kernel.
@@ -93,6 +105,9 @@ struct fdd_plan {
 namespace fdd {
 namespace host {
 
+// Cold-plasma dispersion constant, s MHz^2 / (pc cm^-3).  The paper gives no
+// value; 4148.808 is the standard constant.
+constexpr double kDispersionConstant = 4148.808;
 constexpr size_t kSmemBudget = 200 * 1024;   // per block; the tuner weighs occupancy by timing
 constexpr size_t kDefaultSmem = 100 * 1024;  // untuned default: leave room for two blocks per SM
 
@@ -148,6 +163,13 @@ double sbf_work_ratio(const fdd_plan* p, const RangeState& r);
 // Enqueues 2 launches per DM slab; *launches (if given) receives their number.
 cudaError_t launch_range_sbf(const fdd_plan* p, const RangeState& r, const fdd::DedispArgs& a, uint8_t* scratch,
                              size_t scratch_bytes, cudaStream_t s, int64_t* launches = nullptr);
+// Two-step subband mode (fdd_subband.cu).
+int configure_subband(fdd_plan* p, RangeState& r, int G, int K);
+void free_subband_tables(RangeState& r);
+size_t subband_scratch_bytes(const fdd_plan* p, int64_t n_out);
+cudaError_t launch_range_subband(const fdd_plan* p, const RangeState& r, const fdd::DedispArgs& a, uint8_t* scratch,
+                                 size_t scratch_bytes, cudaStream_t s, int64_t* launches);
+
 // Global variant index / channels per stage of range r's current configuration,
 // and re-applying such a pair (fdd_plan.cu).
 int range_config_index(const RangeState& r);

@@ -72,6 +72,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_dedisp_persistent(const __grid_c
         const int sb = static_cast<int>(rest / R.n_tiles);
         const BatchJob& J = p.jobs[job];
         DedispArgs a;
+        a.blk_per_coarse = 0;
+        a.coarse_stride = 0;
         if (R.ds_index < 0) {
             a.in = J.tabs;
             a.pitch_bytes = J.tab_pitch;

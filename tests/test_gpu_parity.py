@@ -576,3 +576,53 @@ def test_sb_factored_geometry_table(fdd):
         ora = ora.copy()
         ora["sb"] = s
         compare_candidates(gpu[gpu["sb"] == s], ora, 7.0)
+
+
+@pytest.mark.parametrize("G,K", [(48, 32), (16, 16), (1, 32)])
+def test_subband_two_step_matches_oracle(fdd, G, K):
+    """Two-step subband dedispersion (approximate mode): series bit-exact and
+    candidates equal to the oracle's two-step definition, on a multi-SB plan
+    (SB map constant within 16-channel blocks) with a native and a
+    downsampled range."""
+    import torch
+    n_tab, n_chan, n_sb, n_out = 3, 384, 4, 3000
+    f = synth.channel_freqs(n_chan)
+    sb = synth.sb_map_piecewise(5, n_sb, n_chan, n_tab, sub=48).astype(np.int16)
+    ranges = [dict(dm0=20.0, ddm=0.5, n_dm=128, downsamp=1, widths=[1, 2, 8]),
+              dict(dm0=84.0, ddm=2.0, n_dm=64, downsamp=2, widths=[1, 4])]
+    plan = fdd.Plan(n_tab, n_chan, n_sb, f, T_SAMP, ranges, 6.0, sb)
+    exact_delay = plan.max_delay
+    for r in range(2):
+        plan.set_subband(r, G, K)
+        assert plan.get_subband(r) == (G, K)
+    assert plan.max_delay >= exact_delay - 2
+    n_in = n_out + plan.max_delay + 5
+    pulses = [dict(tab=k % n_tab, start=700 + 800 * k + oracle.delays(f, T_SAMP, dm, 1.0, 1)[0], width=w, amp=40.0)
+              for k, (dm, w) in enumerate([(40.0, 4), (70.0, 2), (150.0, 8)])]
+    x = synth.filterbank(31, n_tab, n_chan, n_in, pulses=pulses)
+    res = plan.search(to_dev(x), n_in, n_out, want_series=True, cap=1 << 18)
+    torch.cuda.synchronize()
+    oranges = [dict(r, subband=(G, K)) for r in ranges]
+    ora, os_ = oracle_candidate_superset(x, sb, f, T_SAMP, oranges, 6.0, n_out, n_in, return_series=True)
+    g = plan.series_views(res.series, n_out)
+    for k in range(2):
+        assert (g[k].cpu().numpy() == os_[k]).all(), k
+    gpu, n = res.candidates()
+    assert compare_candidates(gpu, ora, 6.0) > 0
+    # back to exact dedispersion
+    for r in range(2):
+        plan.set_subband(r, 0, 0)
+    assert plan.max_delay == exact_delay
+
+
+def test_subband_mode_refusals(fdd):
+    n_chan = 96
+    f = synth.channel_freqs(n_chan)
+    sb = synth.sb_map_piecewise(2, 3, n_chan, 2, sub=16).astype(np.int16)
+    ranges = [dict(dm0=0.0, ddm=1.0, n_dm=64, downsamp=1, widths=[1])]
+    plan = fdd.Plan(2, n_chan, 3, f, T_SAMP, ranges, 6.0, sb)
+    with pytest.raises(fdd.FddError):       # the SB map switches TAB inside a 32-channel subband
+        plan.set_subband(0, 32, 32)
+    plan.set_subband(0, 16, 32)
+    with pytest.raises(fdd.FddError):       # batched searches stay exact
+        plan.batch_prepare(1000)
