@@ -265,6 +265,12 @@ def run_fdd(args):
     plan = fdd.Plan(w["n_tab"], w["n_chan"], w["n_sb"], f, t, w["ranges"], w["thr"], sb)
     if args.scratch_mb:
         plan.set_scratch_limit(args.scratch_mb << 20)
+    if args.subband:
+        sg, sk = (int(v) for v in args.subband.split(","))
+        for r in range(len(w["ranges"])):
+            plan.set_subband(r, sg, sk)
+        n_in = max(n_in, w["n_out"] + plan.max_delay + 16)
+        x = np.ascontiguousarray(np.pad(x, ((0, 0), (0, 0), (0, max(0, synth.padded_pitch(n_in) - x.shape[2])))))
     host = torch.from_numpy(x).pin_memory()
     tabs = host.to(dev)
     cap = 1 << 22
@@ -455,7 +461,9 @@ def run_fdd(args):
                    "n_out": w["n_out"], "n_in": n_in,
                    "dm_plan": [[r["dm0"], r["ddm"], r["n_dm"], r["downsamp"]] for r in w["ranges"]],
                    "widths": WIDTHS, "snr_thresh": w["thr"], "l2": "flushed (256 MB write) between steps",
-                   "parallelism": "replicas" if world > 1 else "single", "mode": mode},
+                   "parallelism": "replicas" if world > 1 else "single", "mode": mode,
+                   "dedispersion": ("two-step subband %s (approximate)" % args.subband) if args.subband
+                   else "exact"},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_units * world / e2e_s, "unit": "samples/s",
@@ -617,6 +625,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--variant", type=int, default=None, help="force this dedispersion kernel variant")
     ap.add_argument("--cc", type=int, default=0, help="with --variant: channels per stage (0 = largest fitting)")
+    ap.add_argument("--subband", default=None,
+                    help="G,K: approximate two-step subband dedispersion (G channels per subband, K fine trials per "
+                         "coarse DM) instead of the exact kernels; not the benchmark's default")
     ap.add_argument("--scratch-mb", type=int, default=0,
                     help="cap on the SB-factored kernel's partial-sum scratch (0 = library default)")
     ap.add_argument("--serve", action="store_true", help="serving measurement instead of the step benchmark")
