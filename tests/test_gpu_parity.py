@@ -585,11 +585,11 @@ def test_subband_two_step_matches_oracle(fdd, G, K):
     (SB map constant within 16-channel blocks) with a native and a
     downsampled range."""
     import torch
-    n_tab, n_chan, n_sb, n_out = 3, 384, 4, 3000
+    n_tab, n_chan, n_sb, n_out = 3, 1536, 4, 3000
     f = synth.channel_freqs(n_chan)
     sb = synth.sb_map_piecewise(5, n_sb, n_chan, n_tab, sub=48).astype(np.int16)
-    ranges = [dict(dm0=20.0, ddm=0.5, n_dm=128, downsamp=1, widths=[1, 2, 8]),
-              dict(dm0=84.0, ddm=2.0, n_dm=64, downsamp=2, widths=[1, 4])]
+    ranges = [dict(dm0=20.0, ddm=0.2, n_dm=128, downsamp=1, widths=[1, 2, 8]),
+              dict(dm0=45.6, ddm=0.8, n_dm=64, downsamp=2, widths=[1, 4])]
     plan = fdd.Plan(n_tab, n_chan, n_sb, f, T_SAMP, ranges, 6.0, sb)
     exact_delay = plan.max_delay
     for r in range(2):
@@ -598,7 +598,7 @@ def test_subband_two_step_matches_oracle(fdd, G, K):
     assert plan.max_delay >= exact_delay - 2
     n_in = n_out + plan.max_delay + 5
     pulses = [dict(tab=k % n_tab, start=700 + 800 * k + oracle.delays(f, T_SAMP, dm, 1.0, 1)[0], width=w, amp=40.0)
-              for k, (dm, w) in enumerate([(40.0, 4), (70.0, 2), (150.0, 8)])]
+              for k, (dm, w) in enumerate([(30.0, 4), (40.0, 2), (80.0, 8)])]
     x = synth.filterbank(31, n_tab, n_chan, n_in, pulses=pulses)
     res = plan.search(to_dev(x), n_in, n_out, want_series=True, cap=1 << 18)
     torch.cuda.synchronize()
