@@ -431,3 +431,109 @@ int64_t oracle_cluster(const oracle_cand* in, int64_t n, oracle_cand* out) {
     free(keep);
     return n_out;
 }
+
+/* ------------------------------------------------------------------------
+ * RFI mitigation (Sec. "AMBER", "RFI mitigation (optional)"; Sec. "Fraction of
+ * data lost to RFI"): a time-domain filter for bright wide-band low-DM RFI and
+ * a frequency-domain filter for bright narrowband RFI, each applied
+ * iteratively (three iterations each in ARTS) to ever cleaner samples.  The
+ * filters' statistics are not given in the paper; readings:
+ *   time domain, per TAB: the zero-DM series z[t] = sum_c x[c][t]; each
+ *     iteration takes the mean mu and population std sigma of z over the
+ *     unflagged samples and flags every unflagged t with z[t] - mu > thr_t*sigma
+ *     (bright = positive excursions); flagged samples of every channel are
+ *     replaced by the channel's mean over the unflagged samples, rounded half
+ *     up;
+ *   frequency domain, per TAB, on the time-cleaned data: the channel sums
+ *     b[c] = sum_t x[c][t]; each iteration flags every unflagged channel with
+ *     |b[c] - mu| > thr_f*sigma (mu, sigma over unflagged channels; two-sided:
+ *     hot or dead channels); flagged channels are filled with the mean level
+ *     of the unflagged channels, sum b / (channels * n_in) rounded half up.
+ * Moments are exact integers; mu = S1/n and sigma = sqrt((n S2 - S1^2)/n^2) in
+ * FP64 in exactly this order.  x is modified in place ([n_tab][n_chan][pitch],
+ * first n_in samples); tflags [n_tab][n_in] and cflags [n_tab][n_chan] get 1
+ * for flagged samples / channels.  A threshold <= 0 disables its filter. */
+static void rfi_moments(const uint64_t* v, const uint8_t* flag, int64_t n, int64_t* cnt, double* mu, double* sigma) {
+    uint64_t s1 = 0;
+    unsigned __int128 s2 = 0;
+    int64_t k = 0;
+    for (int64_t j = 0; j < n; j++)
+        if (!flag[j]) {
+            s1 += v[j];
+            s2 += (unsigned __int128)v[j] * v[j];
+            k++;
+        }
+    *cnt = k;
+    if (k == 0) { *mu = 0; *sigma = 0; return; }
+    const __int128 num = (__int128)k * (__int128)s2 - (__int128)s1 * (__int128)s1;
+    *mu = (double)s1 / (double)k;
+    *sigma = sqrt((double)num / ((double)k * (double)k));
+}
+
+void oracle_rfi_clean(uint8_t* x, int32_t n_tab, int32_t n_chan, int64_t n_in, int64_t pitch,
+                      double time_thr, int32_t time_iters, double freq_thr, int32_t freq_iters,
+                      uint8_t* tflags, uint8_t* cflags) {
+    uint64_t* z = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n_in > 0 ? n_in : 1));
+    uint64_t* b = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)n_chan);
+    for (int32_t tab = 0; tab < n_tab; tab++) {
+        uint8_t* xt = x + (int64_t)tab * n_chan * pitch;
+        uint8_t* tf = tflags + (int64_t)tab * n_in;
+        uint8_t* cf = cflags + (int64_t)tab * n_chan;
+        memset(tf, 0, (size_t)n_in);
+        memset(cf, 0, (size_t)n_chan);
+        if (time_thr > 0) {
+            for (int64_t t = 0; t < n_in; t++) {
+                uint64_t s = 0;
+                for (int32_t c = 0; c < n_chan; c++) s += xt[(int64_t)c * pitch + t];
+                z[t] = s;
+            }
+            for (int32_t it = 0; it < time_iters; it++) {
+                int64_t k;
+                double mu, sigma;
+                rfi_moments(z, tf, n_in, &k, &mu, &sigma);
+                if (k == 0) break;
+                for (int64_t t = 0; t < n_in; t++)
+                    if (!tf[t] && (double)z[t] - mu > time_thr * sigma) tf[t] = 1;
+            }
+            int64_t n_ok = 0;
+            for (int64_t t = 0; t < n_in; t++) n_ok += !tf[t];
+            if (n_ok > 0 && n_ok < n_in)
+                for (int32_t c = 0; c < n_chan; c++) {
+                    uint8_t* row = xt + (int64_t)c * pitch;
+                    uint64_t s = 0;
+                    for (int64_t t = 0; t < n_in; t++)
+                        if (!tf[t]) s += row[t];
+                    const uint8_t m = (uint8_t)((2 * s + (uint64_t)n_ok) / (2 * (uint64_t)n_ok));
+                    for (int64_t t = 0; t < n_in; t++)
+                        if (tf[t]) row[t] = m;
+                }
+        }
+        if (freq_thr > 0) {
+            for (int32_t c = 0; c < n_chan; c++) {
+                uint64_t s = 0;
+                for (int64_t t = 0; t < n_in; t++) s += xt[(int64_t)c * pitch + t];
+                b[c] = s;
+            }
+            for (int32_t it = 0; it < freq_iters; it++) {
+                int64_t k;
+                double mu, sigma;
+                rfi_moments(b, cf, n_chan, &k, &mu, &sigma);
+                if (k == 0) break;
+                for (int32_t c = 0; c < n_chan; c++)
+                    if (!cf[c] && fabs((double)b[c] - mu) > freq_thr * sigma) cf[c] = 1;
+            }
+            uint64_t s = 0;
+            int64_t n_ok = 0;
+            for (int32_t c = 0; c < n_chan; c++)
+                if (!cf[c]) { s += b[c]; n_ok++; }
+            if (n_ok > 0 && n_ok < n_chan && n_in > 0) {
+                const uint64_t den = (uint64_t)n_ok * (uint64_t)n_in;
+                const uint8_t v = (uint8_t)((2 * s + den) / (2 * den));
+                for (int32_t c = 0; c < n_chan; c++)
+                    if (cf[c]) memset(xt + (int64_t)c * pitch, v, (size_t)n_in);
+            }
+        }
+    }
+    free(z);
+    free(b);
+}
