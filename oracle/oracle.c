@@ -449,25 +449,26 @@ int64_t oracle_cluster(const oracle_cand* in, int64_t n, oracle_cand* out) {
  *     |b[c] - mu| > thr_f*sigma (mu, sigma over unflagged channels; two-sided:
  *     hot or dead channels); flagged channels are filled with the mean level
  *     of the unflagged channels, sum b / (channels * n_in) rounded half up.
- * Moments are exact integers; mu = S1/n and sigma = sqrt((n S2 - S1^2)/n^2) in
- * FP64 in exactly this order.  x is modified in place ([n_tab][n_chan][pitch],
+ * Moments are exact integers (S1, S2 < 2^64); mu = S1/n, var = S2/n - mu*mu,
+ * sigma = sqrt(var) in FP64 in exactly this order (the flag decisions are
+ * taken in that precision).  x is modified in place ([n_tab][n_chan][pitch],
  * first n_in samples); tflags [n_tab][n_in] and cflags [n_tab][n_chan] get 1
  * for flagged samples / channels.  A threshold <= 0 disables its filter. */
 static void rfi_moments(const uint64_t* v, const uint8_t* flag, int64_t n, int64_t* cnt, double* mu, double* sigma) {
-    uint64_t s1 = 0;
-    unsigned __int128 s2 = 0;
+    uint64_t s1 = 0, s2 = 0;
     int64_t k = 0;
     for (int64_t j = 0; j < n; j++)
         if (!flag[j]) {
             s1 += v[j];
-            s2 += (unsigned __int128)v[j] * v[j];
+            s2 += v[j] * v[j];
             k++;
         }
     *cnt = k;
     if (k == 0) { *mu = 0; *sigma = 0; return; }
-    const __int128 num = (__int128)k * (__int128)s2 - (__int128)s1 * (__int128)s1;
     *mu = (double)s1 / (double)k;
-    *sigma = sqrt((double)num / ((double)k * (double)k));
+    const double m2 = (double)s2 / (double)k;
+    const double var = m2 - *mu * *mu;
+    *sigma = var > 0 ? sqrt(var) : 0.0;
 }
 
 void oracle_rfi_clean(uint8_t* x, int32_t n_tab, int32_t n_chan, int64_t n_in, int64_t pitch,
