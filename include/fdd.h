@@ -553,6 +553,42 @@ int fdd_search_static(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64
 int fdd_sb_table(int32_t n_tab, int32_t n_sb, int32_t n_chan, const double* chan_freq_mhz, double f_max_mhz,
                  double alpha, double b_max_m, double b_cq_m, int32_t chan_per_subband, int16_t* sb_map_out);
 
+/* RFI mitigation on TAB filterbanks, IN PLACE (Sec. "AMBER", "RFI mitigation
+ * (optional)": a time-domain filter for bright wide-band low-DM RFI and a
+ * frequency-domain filter for bright narrowband RFI, each applied
+ * iteratively -- three iterations each in ARTS, Sec. "Fraction of data lost
+ * to RFI").  The paper leaves the statistics to another publication; here,
+ * per TAB:
+ *   time domain: z[t] = sum_c x[c][t]; each iteration flags unflagged t with
+ *     z[t] - mu > time_thresh * sigma (mu, sigma over unflagged samples);
+ *     flagged samples of every channel become the channel's mean over the
+ *     unflagged samples, rounded half up;
+ *   frequency domain (after it): b[c] = sum_t x[c][t]; each iteration flags
+ *     unflagged channels with |b[c] - mu| > freq_thresh * sigma; flagged
+ *     channels are filled with the unflagged channels' mean level, rounded
+ *     half up.
+ * mu = S1/n, var = S2/n - mu^2, sigma = sqrt(var) in FP64 from exact 64-bit
+ * sums.  A threshold <= 0 disables that filter.  Run before fdd_search. */
+typedef struct {
+    double time_thresh;   /* sigmas, zero-DM filter (e.g. 4); <= 0: off */
+    int32_t time_iters;   /* 3 in ARTS */
+    double freq_thresh;   /* sigmas, channel filter (e.g. 4); <= 0: off */
+    int32_t freq_iters;   /* 3 in ARTS */
+} fdd_rfi_desc;
+
+/* Workspace bytes of fdd_rfi_clean for n_tab x n_chan x n_in. */
+int fdd_rfi_workspace_size(int32_t n_tab, int32_t n_chan, int64_t n_in, size_t* bytes);
+
+/* d_tabs: device uint8 [n_tab][n_chan][pitch], first n_in samples per row
+ * cleaned in place (16-byte aligned, pitch a multiple of 16).  d_time_flags
+ * (device uint8 [n_tab][n_in]) and d_chan_flags ([n_tab][n_chan]) receive 1
+ * for flagged samples / channels; either may be NULL.  Asynchronous on
+ * stream.  Errors: INVALID_ARG, MISALIGNED, WORKSPACE, UNSUPPORTED (moments
+ * would not fit 64 bits), CUDA. */
+int fdd_rfi_clean(const fdd_rfi_desc* desc, uint8_t* d_tabs, int32_t n_tab, int32_t n_chan, int64_t n_in,
+                  int64_t pitch, void* d_workspace, size_t workspace_bytes, uint8_t* d_time_flags,
+                  uint8_t* d_chan_flags, fdd_stream_t stream);
+
 /* Human-readable text of an FDD_* code (static string). */
 const char* fdd_error_string(int code);
 

@@ -84,6 +84,11 @@ class _ServerStats(ctypes.Structure):
                 ("ring_bytes_per_beam", ctypes.c_int64), ("slot_bytes", ctypes.c_int64)]
 
 
+class _RfiDesc(ctypes.Structure):
+    _fields_ = [("time_thresh", ctypes.c_double), ("time_iters", ctypes.c_int32),
+                ("freq_thresh", ctypes.c_double), ("freq_iters", ctypes.c_int32)]
+
+
 class _PlanDesc(ctypes.Structure):
     _fields_ = [("n_tab", ctypes.c_int32), ("n_chan", ctypes.c_int32), ("n_sb", ctypes.c_int32),
                 ("chan_freq_mhz", ctypes.POINTER(ctypes.c_double)), ("t_samp_s", ctypes.c_double),
@@ -162,6 +167,8 @@ def _lib_raw():
     L.fdd_plan_set_scratch_limit.argtypes = [_P, _I64]
     L.fdd_plan_last_launches.argtypes = [_P, ctypes.POINTER(_I64)]
     L.fdd_plan_set_subband.argtypes = [_P, _I32, _I32, _I32]
+    L.fdd_rfi_workspace_size.argtypes = [_I32, _I32, _I64, ctypes.POINTER(_SZ)]
+    L.fdd_rfi_clean.argtypes = [ctypes.POINTER(_RfiDesc), _P, _I32, _I32, _I64, _I64, _P, _SZ, _P, _P, _P]
     L.fdd_plan_get_subband.argtypes = [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]
     L.fdd_sb_table.argtypes = [_I32, _I32, _I32, _P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                ctypes.c_double, _I32, _P]
@@ -472,6 +479,26 @@ def sb_table(n_tab, n_sb, chan_freq_mhz, f_max_mhz=1500.0, alpha=0.80, b_max_m=1
                                    float(alpha), float(b_max_m), float(b_cq_m), int(chan_per_subband),
                                    out.ctypes.data_as(ctypes.c_void_p)), "fdd_sb_table")
     return out
+
+
+def rfi_clean(tabs, n_in, time_thresh=4.0, time_iters=3, freq_thresh=4.0, freq_iters=3, time_flags=None,
+              chan_flags=None, workspace=None, stream=None):
+    """RFI mitigation in place on a CUDA uint8 tensor [n_tab][n_chan][pitch]
+    (include/fdd.h: fdd_rfi_clean).  Optional CUDA uint8 outputs: time_flags
+    [n_tab][n_in], chan_flags [n_tab][n_chan]."""
+    import torch
+    n_tab, n_chan, pitch = (int(v) for v in tabs.shape)
+    need = _SZ()
+    _check(_lib_raw().fdd_rfi_workspace_size(n_tab, n_chan, int(n_in), ctypes.byref(need)), "fdd_rfi_workspace_size")
+    if workspace is None:
+        workspace = torch.empty(need.value, dtype=torch.uint8, device=tabs.device)
+    d = _RfiDesc(float(time_thresh), int(time_iters), float(freq_thresh), int(freq_iters))
+    _check(_lib_raw().fdd_rfi_clean(ctypes.byref(d), _dev_ptr(tabs, "tabs", torch.uint8), n_tab, n_chan, int(n_in), pitch,
+                                    _dev_ptr(workspace, "workspace"), int(workspace.numel()),
+                                    _dev_ptr(time_flags, "time_flags", torch.uint8) if time_flags is not None else None,
+                                    _dev_ptr(chan_flags, "chan_flags", torch.uint8) if chan_flags is not None else None,
+                                    _stream_handle(stream)), "fdd_rfi_clean")
+    return workspace
 
 
 def sort_candidates(cands):
