@@ -306,9 +306,10 @@ def run_fdd(args):
         for p_ in plans:
             p_.set_timing(True)
 
-        def step():
+        def step(src=None):
             for p_ in plans:
-                p_.search(tabs, n_in, w["n_out"], cap=cap, workspace=ws, cands=cands, count=count, stream=stream)
+                p_.search(tabs if src is None else src, n_in, w["n_out"], cap=cap, workspace=ws, cands=cands,
+                          count=count, stream=stream)
     else:
         job = plan.make_job(tabs, n_in, w["n_out"], cap=cap)
         cands, count = job.cands, job.count
@@ -381,23 +382,51 @@ def run_fdd(args):
     units = units_per_step(w) * args.steps * world
     value = units / dev_s
 
-    # end-to-end through the public API with host buffers: H2D of the chunk
-    # from pinned memory, search, D2H of the count and the candidate records.
+    # end-to-end through the public API with host buffers: every step copies its
+    # chunk host-to-device from pinned memory and reads its count and candidate
+    # records back.  Per-range modes double-buffer the input so the copy of step
+    # k+1 (copy stream) overlaps the search of step k, as a pipelined caller
+    # would; batched/graph modes search a fixed job buffer, copied in turn.
     e2e_units, h2d, d2h = 0, 0, 0
     cnt_host = torch.zeros(1, dtype=torch.int64).pin_memory()
     e2e_steps = max(1, min(args.steps, 200))
+    pipelined = mode in ("plain", "per_sb")
+    bufs = [tabs, torch.empty_like(tabs)] if pipelined else [tabs]
+    copy_stream = torch.cuda.Stream(device=dev)
+    ready = [torch.cuda.Event() for _ in bufs]
+    done = [torch.cuda.Event() for _ in bufs]
     torch.cuda.synchronize()
     te0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        tabs.copy_(host, non_blocking=True)
-        step()
+
+    def issue_copy(k):
+        b = k % len(bufs)
+        with torch.cuda.stream(copy_stream):
+            if k >= len(bufs):
+                copy_stream.wait_event(done[b])       # the buffer's previous search has finished
+            bufs[b].copy_(host, non_blocking=True)
+            ready[b].record(copy_stream)
+
+    issue_copy(0)
+    for k in range(e2e_steps):
+        b = k % len(bufs)
+        if pipelined and k + 1 < e2e_steps:
+            issue_copy(k + 1)
+        stream.wait_event(ready[b])
+        if pipelined:
+            step(bufs[b])
+        else:
+            step()
+        done[b].record(stream)
         cnt_host.copy_(count, non_blocking=True)
-        torch.cuda.synchronize()
+        stream.synchronize()
         n = min(int(cnt_host.item()), cap)
         got = cands[:n].cpu()
+        if not pipelined and k + 1 < e2e_steps:
+            issue_copy(k + 1)
         h2d += host.numel()
         d2h += 8 + got.numel() * 4
         e2e_units += units_per_step(w)
+    torch.cuda.synchronize()
     te1 = time.perf_counter()
     e2e_s = reduce_max(te1 - te0, dist, dev)
 
@@ -468,7 +497,7 @@ def run_fdd(args):
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_units * world / e2e_s, "unit": "samples/s",
                 "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
-                "steps": e2e_steps},
+                "steps": e2e_steps, "h2d_overlapped": pipelined},
         "gpu_launches": launches,
         "clocks": clocks,
         "stages_ms": {k: float(np.mean(v)) for k, v in stage_ms.items()},
