@@ -386,7 +386,6 @@ const Entry kEntries[] = {
     FDD_S(1, 2, 4, 8, 4),   // BD 32, T 256
     FDD_S(1, 4, 2, 16, 4),  // BD 32, T 512, 512 threads
     FDD_S(1, 4, 2, 8, 8),   // BD 16, T 512, stages of up to 48-60 channels
-    FDD_S(1, 4, 4, 16, 4),  // BD 64, T 512, 512 threads
     FDD_S(2, 4, 2, 8, 4),   // BD 16, T 256
     FDD_S(2, 4, 4, 8, 4),   // BD 32, T 256
     FDD_S(2, 8, 2, 8, 4),   // BD 16, T 512
