@@ -118,8 +118,7 @@ struct SbfCombArgs {
     const uint16_t* P;
     int64_t tab_stride, seg_stride;
     int32_t Np;
-    const uint32_t* seg_tab;    // [n_sb][seg_pitch]: TAB SB s takes on segment u, times
-                                //   sbf_comb_tab_bytes() (its rows' offset in shared memory); seg_pitch % 8 == 0
+    const uint8_t* seg_tab;     // [n_sb][seg_pitch]: TAB SB s takes on segment u (seg_pitch % 8 == 0)
     int32_t seg_pitch;
     int32_t* series;            // this range: [n_sb][n_dm][n_out]
     unsigned long long* stat;   // this range: [n_sb * n_dm][2]
@@ -138,7 +137,6 @@ cudaError_t launch_sbf_part(int idx, const SbfPartArgs& a, int n_tab, cudaStream
 // SBs handled by one comb block (the grid's z covers ceil(n_sb / this)).
 int sbf_comb_sbs_per_block();
 int sbf_comb_uc(int n_tab);
-uint32_t sbf_comb_tab_bytes();
 size_t sbf_comb_smem_bytes(int n_tab);
 cudaError_t launch_sbf_comb(const SbfCombArgs& a, cudaStream_t s);
 

@@ -36,7 +36,7 @@ struct RangeState {
     int32_t seg_maxlen = 0;
     int32_t s_n_seg = 0;              // segments of the configured SB-factored kernel (cut at its CC)
     int2* d_segs = nullptr;           // configured segments
-    uint32_t* d_segtab = nullptr;     // [n_sb][seg_pitch]: shared-memory offset of the TAB's rows
+    uint8_t* d_segtab = nullptr;      // [n_sb][seg_pitch]
     int32_t seg_pitch = 0;
     int sbf = -1;
     int32_t s_CC = 0, s_Lw = 0, s_n_stages = 0, s_flush = 1;

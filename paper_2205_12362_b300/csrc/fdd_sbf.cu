@@ -136,12 +136,11 @@ int configure_sbf(fdd_plan* p, RangeState& r, int sv, int CC) {
     int rc;
     if ((rc = upload(&r.d_segs, segs, "segment table")) != FDD_OK) return rc;
     r.seg_pitch = static_cast<int32_t>(round_up64(static_cast<int64_t>(segs.size()), 8));  // whole 8-segment chunks
-    std::vector<uint32_t> tab(static_cast<size_t>(p->n_sb) * r.seg_pitch, 0);
+    std::vector<uint8_t> tab(static_cast<size_t>(p->n_sb) * r.seg_pitch, 0);
     for (int s = 0; s < p->n_sb; s++)
         for (size_t g = 0; g < segs.size(); g++)
             tab[static_cast<size_t>(s) * r.seg_pitch + g] =
-                static_cast<uint32_t>(p->sb_map[static_cast<size_t>(s) * p->n_chan + segs[g].x]) *
-                fdd::sbf_comb_tab_bytes();
+                static_cast<uint8_t>(p->sb_map[static_cast<size_t>(s) * p->n_chan + segs[g].x]);
     if ((rc = upload(&r.d_segtab, tab, "segment TAB table")) != FDD_OK) return rc;
     if ((rc = upload(&r.d_sbase, h.base, "base table")) != FDD_OK) return rc;
     if ((rc = upload(&r.d_soff, h.off, "offset table")) != FDD_OK) return rc;

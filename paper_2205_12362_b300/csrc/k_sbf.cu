@@ -260,10 +260,12 @@ __global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const SbfCombArgs a) {
     const uint32_t buf_bytes = static_cast<uint32_t>(a.n_tab) * kTabBytes;
     const uint16_t* p_trial = a.P + static_cast<int64_t>(i_s) * a.Np + t0;
     // the SBs of this warp (invalid slots repeat SB sb0 + nsb - 1, or SB 0 for an idle warp)
-    // per SB: shared-memory byte offset of its TAB's rows, per segment (row of SB sb0, or of SB 0 for an
-    // idle warp; SB slots past n_sb repeat the warp's last SB)
-    const uint32_t* tab_base = a.seg_tab + static_cast<int64_t>(nsb > 0 ? sb0 : 0) * a.seg_pitch;
-    const int last = nsb > 0 ? nsb - 1 : 0;
+    const uint8_t* tab_row[CSB];
+#pragma unroll
+    for (int j = 0; j < CSB; j++) {
+        const int sj = nsb > 0 ? sb0 + min(j, nsb - 1) : 0;
+        tab_row[j] = a.seg_tab + static_cast<int64_t>(sj) * a.seg_pitch;
+    }
 
     // copy chunk ch (UC segments of every TAB) into buffer buf: 16 pieces of 16 B per row
     auto issue = [&](int ch, int buf) {
@@ -314,18 +316,19 @@ __global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const SbfCombArgs a) {
         const int nu = min(UC, a.n_seg - u0);
         const uint32_t s_buf = s_base + buf * buf_bytes + 8u * lane;
 #pragma unroll
-        for (int q = 0; q < UC; q += 2) {
-            uint2 koff2[CSB];
+        for (int q = 0; q < UC; q += 4) {
+            uint32_t tabs4[CSB];
 #pragma unroll
-            for (int j = 0; j < CSB; j++)
-                koff2[j] = __ldg(reinterpret_cast<const uint2*>(tab_base + min(j, last) * a.seg_pitch + u0 + q));
+            for (int j = 0; j < CSB; j++) tabs4[j] = __ldg(reinterpret_cast<const uint32_t*>(tab_row[j] + u0 + q));
 #pragma unroll
-            for (int dq = 0; dq < 2; dq++) {
+            for (int dq = 0; dq < 4; dq++) {
                 const int du = q + dq;
                 if (du < nu) {  // block-uniform
 #pragma unroll
                     for (int j = 0; j < CSB; j++) {
-                        const uint32_t koff = dq == 0 ? koff2[j].x : koff2[j].y;
+                        // byte dq of tabs4 (the TAB) times kTabBytes (2048 = 2^11)
+                        const uint32_t koff = (dq <= 1 ? (tabs4[j] << (11 - 8 * dq)) : (tabs4[j] >> (8 * dq - 11))) &
+                                              (0xFFu << 11);
                         const uint2 v = lds64(s_buf + koff + du * kRowBytes);
                         acc[j][0] += v.x;
                         acc[j][1] += v.y;
@@ -422,8 +425,6 @@ cudaError_t launch_sbf_part(int idx, const SbfPartArgs& a, int n_tab, cudaStream
 int sbf_comb_sbs_per_block() { return CW * CSB; }
 
 int sbf_comb_uc(int) { return UC; }
-
-uint32_t sbf_comb_tab_bytes() { return kTabBytes; }
 
 size_t sbf_comb_smem_bytes(int n_tab) { return 2ull * n_tab * kTabBytes; }
 
