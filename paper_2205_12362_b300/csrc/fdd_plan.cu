@@ -505,12 +505,6 @@ int fdd_plan_destroy(fdd_plan* plan) {
     if (!plan) return FDD_OK;
     fdd_free_batch_state(plan);
     for (cudaEvent_t e : plan->ev) cudaEventDestroy(e);
-    if (plan->side_stream) {
-        cudaStreamSynchronize(plan->side_stream);
-        cudaStreamDestroy(plan->side_stream);
-    }
-    for (cudaEvent_t e : plan->sbf_ev)
-        if (e) cudaEventDestroy(e);
     for (RangeState& r : plan->ranges) {
         free_range_tables(r);
         free_sbf_tables(r, true);

@@ -100,9 +100,6 @@ struct fdd_plan {
     std::vector<int32_t> st_kind, st_range;
     BatchState batch;
     int64_t last_launches = 0;            // kernels enqueued by the last search / batched search
-    // SB-factored slab pipeline: combine of slab k on side_stream overlaps the partials of slab k+1
-    cudaStream_t side_stream = nullptr;
-    cudaEvent_t sbf_ev[4] = {nullptr, nullptr, nullptr, nullptr};  // part done (2 halves), comb done (2 halves)
 };
 
 namespace fdd {

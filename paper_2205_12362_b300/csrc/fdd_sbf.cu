@@ -145,11 +145,6 @@ int configure_sbf(fdd_plan* p, RangeState& r, int sv, int CC) {
     if ((rc = upload(&r.d_sbase, h.base, "base table")) != FDD_OK) return rc;
     if ((rc = upload(&r.d_soff, h.off, "offset table")) != FDD_OK) return rc;
     if ((rc = upload(&r.d_sstages, stages, "stage table")) != FDD_OK) return rc;
-    if (!p->side_stream) {
-        cudaError_t e = cudaStreamCreateWithFlags(&p->side_stream, cudaStreamNonBlocking);
-        for (int k = 0; k < 4 && e == cudaSuccess; k++) e = cudaEventCreateWithFlags(&p->sbf_ev[k], cudaEventDisableTiming);
-        if (e != cudaSuccess) return cuda_fail(e, "SB-factored pipeline stream");
-    }
     r.s_n_seg = static_cast<int32_t>(segs.size());
     r.sbf = sv;
     r.s_CC = cc_pick;
@@ -212,50 +207,17 @@ cudaError_t launch_range_sbf(const fdd_plan* p, const RangeState& r, const fdd::
     ca.flush = r.s_flush;
     ca.n_tab = p->n_tab;
     ca.uc = fdd::sbf_comb_uc(p->n_tab);
-    if (slab >= r.n_dm || !p->side_stream) {  // one slab: nothing to overlap
-        for (int64_t i0 = 0; i0 < r.n_dm; i0 += slab) {
-            pa.i0 = static_cast<int32_t>(i0);
-            pa.n_slab = static_cast<int32_t>(std::min<int64_t>(slab, r.n_dm - i0));
-            cudaError_t e = fdd::launch_sbf_part(r.sbf, pa, p->n_tab, s);
-            if (e != cudaSuccess) return e;
-            ca.i0 = pa.i0;
-            ca.n_slab = pa.n_slab;
-            if ((e = fdd::launch_sbf_comb(ca, s)) != cudaSuccess) return e;
-            if (launches) *launches += 2;
-        }
-        return cudaSuccess;
-    }
-    // Two halves of the scratch: the partials of slab k+1 (caller's stream) are formed while slab k is
-    // combined (side stream); a half is refilled only after its previous combine has finished.
-    const int64_t half = slab_trials(p, r, nr, BD, scratch_bytes / 2 / 256 * 256);
-    if (half < BD) return cudaErrorInvalidValue;
-    const int64_t half_elems = static_cast<int64_t>(p->n_tab) * n_seg * half * Np;
-    pa.seg_stride = half * Np;
-    pa.tab_stride = n_seg * half * Np;
-    ca.seg_stride = pa.seg_stride;
-    ca.tab_stride = pa.tab_stride;
-    cudaStream_t s2 = p->side_stream;
-    cudaEvent_t const* part_done = p->sbf_ev;
-    cudaEvent_t const* comb_done = p->sbf_ev + 2;
-    cudaError_t e;
-    int k = 0;
-    for (int64_t i0 = 0; i0 < r.n_dm; i0 += half, k++) {
-        const int h = k & 1;
-        uint16_t* P = reinterpret_cast<uint16_t*>(scratch) + h * half_elems;
-        pa.P = P;
-        ca.P = P;
-        pa.i0 = ca.i0 = static_cast<int32_t>(i0);
-        pa.n_slab = ca.n_slab = static_cast<int32_t>(std::min<int64_t>(half, r.n_dm - i0));
-        if (k >= 2 && (e = cudaStreamWaitEvent(s, comb_done[h], 0)) != cudaSuccess) return e;
-        if ((e = fdd::launch_sbf_part(r.sbf, pa, p->n_tab, s)) != cudaSuccess) return e;
-        if ((e = cudaEventRecord(part_done[h], s)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(s2, part_done[h], 0)) != cudaSuccess) return e;
-        if ((e = fdd::launch_sbf_comb(ca, s2)) != cudaSuccess) return e;
-        if ((e = cudaEventRecord(comb_done[h], s2)) != cudaSuccess) return e;
+    for (int64_t i0 = 0; i0 < r.n_dm; i0 += slab) {
+        pa.i0 = static_cast<int32_t>(i0);
+        pa.n_slab = static_cast<int32_t>(std::min<int64_t>(slab, r.n_dm - i0));
+        cudaError_t e = fdd::launch_sbf_part(r.sbf, pa, p->n_tab, s);
+        if (e != cudaSuccess) return e;
+        ca.i0 = pa.i0;
+        ca.n_slab = pa.n_slab;
+        if ((e = fdd::launch_sbf_comb(ca, s)) != cudaSuccess) return e;
         if (launches) *launches += 2;
     }
-    // the caller's stream continues after the last combine (combines run in order on the side stream)
-    return cudaStreamWaitEvent(s, comb_done[(k - 1) & 1], 0);
+    return cudaSuccess;
 }
 
 }  // namespace host
