@@ -563,16 +563,19 @@ def run_serve(args):
     t = synth.ARTS_T_SAMP_S
     chunk = w["n_out"]
     rng = np.random.Generator(np.random.Philox(w["seed"] + 55))
-    # a pinned pool of pre-generated chunks (noise + a few injected pulses)
+    # a pinned pool of pre-generated chunks (noise + injected pulses whose whole sweep lies inside the
+    # chunk, so the window starting with a chunk holds its pulses whatever the chunk order)
     n_pool = args.pool
-    pool = []
+    pool, pool_pulses = [], []
+    sweep = int(arrivals(f, 400.0, t).max())
     for k in range(n_pool):
-        prm = synth.random_pulses(w["seed"] * 100 + k, 1, w["pulse_tabs"], 50.0, 400.0, [1, 2, 4, 8], 10.0, 40.0,
-                                  100, chunk - 100)
-        pulses = [dict(tab=p_["tab"], start=p_["t0"] + arrivals(f, p_["dm"], t) % chunk, width=p_["width"],
+        prm = synth.random_pulses(w["seed"] * 100 + k, 2, w["pulse_tabs"], 50.0, 400.0, [1, 2, 4, 8], 15.0, 40.0,
+                                  200, chunk - sweep - 200)
+        pulses = [dict(tab=p_["tab"], start=p_["t0"] + arrivals(f, p_["dm"], t), width=p_["width"],
                        amp=synth.pulse_amplitude(p_["snr"], w["n_chan"], p_["width"])) for p_ in prm]
         x = synth.filterbank(w["seed"] * 1000 + k, w["n_tab"], w["n_chan"], chunk, pitch=chunk, pulses=pulses)
         pool.append(torch.from_numpy(x).pin_memory())
+        pool_pulses.append(prm)
     sb = synth.sb_map_piecewise(w["seed"], w["n_sb"], w["n_chan"], w["n_tab"]).astype(np.int16)
     plan = fdd.Plan(w["n_tab"], w["n_chan"], w["n_sb"], f, t, w["ranges"], w["thr"], sb)
     # tune the batched search on one window
@@ -619,6 +622,15 @@ def run_serve(args):
         wait = np.array([r["t_launch"] - r["t_ready"] for r, _ in res])
         span = max(r["t_done"] for r, _ in res) - min(r["t_launch"] for r, _ in res) if res else 1.0
         st = srv.info()
+        # injected-pulse recall: window w of beam b starts with chunk w, whose pulses it must hold
+        injected = recovered = 0
+        for r, c in res:
+            for p_ in pool_pulses[(int(r["window"]) + 3 * int(r["beam"])) % n_pool]:
+                injected += 1
+                t_abs = int(r["window"]) * chunk + p_["t0"]
+                near = ((np.abs(c["dm"] - p_["dm"]) < 0.02 * p_["dm"] + 2.0)
+                        & (np.abs(c["t_native"] - t_abs) < 4 * p_["width"] + 64))
+                recovered += int(near.any())
         p99 = float(np.percentile(lat, 99)) if len(lat) else None
         run = {"beams": n_beams, "windows": len(res), "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
                "p99_s": p99, "max_s": float(lat.max()) if len(lat) else None,
@@ -630,7 +642,9 @@ def run_serve(args):
                "windows_per_s": len(res) / span,
                "dm_trial_samples_per_s": len(res) * units_per_step(w) / span,
                "ring_gb_per_beam": info["ring_bytes_per_beam"] / 1e9, "slot_gb": info["slot_bytes"] / 1e9,
-               "candidates": int(sum(len(c) for _, c in res))}
+               "candidates": int(sum(len(c) for _, c in res)),
+               "injected_pulses": injected, "recovered_pulses": recovered,
+               "recall": recovered / injected if injected else None}
         out["runs"].append(run)
         print(json.dumps(run), file=sys.stderr, flush=True)
         srv.close()
