@@ -568,15 +568,18 @@ def run_serve(args):
     n_pool = args.pool
     pool, pool_pulses = [], []
     sweep = int(arrivals(f, 400.0, t).max())
+    sb = synth.sb_map_piecewise(w["seed"], w["n_sb"], w["n_chan"], w["n_tab"]).astype(np.int16)
     for k in range(n_pool):
-        prm = synth.random_pulses(w["seed"] * 100 + k, 2, w["pulse_tabs"], 50.0, 400.0, [1, 2, 4, 8], 15.0, 40.0,
-                                  200, chunk - sweep - 200)
-        pulses = [dict(tab=p_["tab"], start=p_["t0"] + arrivals(f, p_["dm"], t), width=p_["width"],
-                       amp=synth.pulse_amplitude(p_["snr"], w["n_chan"], p_["width"])) for p_ in prm]
+        # sources at seeded SB positions: each pulse goes into the TAB its SB takes in every channel
+        prm = synth.random_pulses(w["seed"] * 100 + k, 2, list(range(w["n_sb"])), 50.0, 400.0, [1, 2, 4, 8],
+                                  15.0, 40.0, 200, chunk - sweep - 200)
+        pulses = []
+        for p_ in prm:
+            pulses += synth.sb_pulses(sb[p_["tab"]], p_["t0"] + arrivals(f, p_["dm"], t), p_["width"],
+                                      synth.pulse_amplitude(p_["snr"], w["n_chan"], p_["width"]))
         x = synth.filterbank(w["seed"] * 1000 + k, w["n_tab"], w["n_chan"], chunk, pitch=chunk, pulses=pulses)
         pool.append(torch.from_numpy(x).pin_memory())
         pool_pulses.append(prm)
-    sb = synth.sb_map_piecewise(w["seed"], w["n_sb"], w["n_chan"], w["n_tab"]).astype(np.int16)
     plan = fdd.Plan(w["n_tab"], w["n_chan"], w["n_sb"], f, t, w["ranges"], w["thr"], sb)
     # tune the batched search on one window
     n_in = chunk + plan.max_delay
@@ -628,7 +631,7 @@ def run_serve(args):
             for p_ in pool_pulses[(int(r["window"]) + 3 * int(r["beam"])) % n_pool]:
                 injected += 1
                 t_abs = int(r["window"]) * chunk + p_["t0"]
-                near = ((np.abs(c["dm"] - p_["dm"]) < 0.02 * p_["dm"] + 2.0)
+                near = ((c["sb"] == p_["tab"]) & (np.abs(c["dm"] - p_["dm"]) < 0.02 * p_["dm"] + 2.0)
                         & (np.abs(c["t_native"] - t_abs) < 4 * p_["width"] + 64))
                 recovered += int(near.any())
         p99 = float(np.percentile(lat, 99)) if len(lat) else None

@@ -48,6 +48,8 @@ def filterbank(seed, n_tab, n_chan, n_samp, pitch=None, mean=128.0, sd=16.0, pul
       start  -- int array [n_chan], first sample of the pulse in each channel
       width  -- pulse width in samples (boxcar)
       amp    -- counts added per sample and channel (float)
+      chans  -- optional: channels (index array or boolean mask) that get the
+                pulse; all channels if absent
     Samples in [n_samp, pitch) are zero.  The noise stream is Philox(seed),
     drawn TAB by TAB as float32 standard normals.
     """
@@ -70,9 +72,13 @@ def filterbank(seed, n_tab, n_chan, n_samp, pitch=None, mean=128.0, sd=16.0, pul
             start = np.asarray(p["start"], dtype=np.int64)
             w = int(p["width"])
             amp = np.float32(p["amp"])
+            sel = np.ones(n_chan, dtype=bool)
+            if p.get("chans") is not None:
+                sel = np.zeros(n_chan, dtype=bool)
+                sel[np.asarray(p["chans"])] = True
             for k in range(w):
                 t = start + k
-                ok = (t >= 0) & (t < n_samp)
+                ok = (t >= 0) & (t < n_samp) & sel
                 c = np.nonzero(ok)[0]
                 v[c, t[ok]] += amp
         np.rint(v, out=v)
@@ -103,3 +109,12 @@ def random_pulses(seed, n, n_tab_pool, dm_lo, dm_hi, widths, snr_lo, snr_hi, t_l
                         t0=int(rng.integers(t_lo, t_hi)),
                         tab=int(rng.choice(np.asarray(n_tab_pool)))))
     return out
+
+
+def sb_pulses(sb_row, start, width, amp):
+    """Pulse dicts (for filterbank) that put one pulse into every channel of
+    the TAB that an SB selects there (sb_row: [n_chan] TAB per channel), so
+    that SB receives the whole pulse: a source at that SB's position."""
+    sb_row = np.asarray(sb_row)
+    return [dict(tab=int(k), start=start, width=width, amp=amp, chans=np.nonzero(sb_row == k)[0])
+            for k in np.unique(sb_row)]
