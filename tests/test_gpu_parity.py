@@ -626,3 +626,41 @@ def test_subband_mode_refusals(fdd):
     plan.set_subband(0, 16, 32)
     with pytest.raises(fdd.FddError):       # batched searches stay exact
         plan.batch_prepare(1000)
+
+
+def test_edge_cases_against_oracle(fdd):
+    """Degenerate and limit shapes: one channel, one DM trial, an empty output,
+    the largest downsampling factor, the channel and TAB limits."""
+    import torch
+    cases = []
+    # one channel, one trial, widths longer than the series
+    cases.append(dict(n_tab=1, n_chan=1, n_sb=1, n_out=300,
+                      ranges=[dict(dm0=5.0, ddm=1.0, n_dm=1, downsamp=1, widths=[1, 7, 400])]))
+    # the largest downsampling factor (257) next to a native range
+    cases.append(dict(n_tab=2, n_chan=24, n_sb=2, n_out=257 * 9 + 5,
+                      ranges=[dict(dm0=0.0, ddm=3.0, n_dm=5, downsamp=1, widths=[1, 2]),
+                              dict(dm0=15.0, ddm=50.0, n_dm=3, downsamp=257, widths=[1, 2, 3])]))
+    # the channel limit, few trials and samples
+    cases.append(dict(n_tab=1, n_chan=16384, n_sb=1, n_out=600,
+                      ranges=[dict(dm0=0.0, ddm=0.05, n_dm=4, downsamp=1, widths=[1, 4])]))
+    # the TAB limit: 256 TABs, SBs picking across all of them
+    cases.append(dict(n_tab=256, n_chan=32, n_sb=3, n_out=700,
+                      ranges=[dict(dm0=0.0, ddm=2.0, n_dm=9, downsamp=1, widths=[1, 2])]))
+    for k, cs in enumerate(cases):
+        f = synth.channel_freqs(cs["n_chan"]) if cs["n_chan"] > 1 else np.array([1370.0])
+        rng = np.random.default_rng(k)
+        sb = rng.integers(0, cs["n_tab"], size=(cs["n_sb"], cs["n_chan"])).astype(np.int16)
+        need = max(int(oracle.delays(f, T_SAMP, r["dm0"], r["ddm"], r["n_dm"], r["downsamp"]).max()) * r["downsamp"]
+                   + (cs["n_out"] // r["downsamp"]) * r["downsamp"] for r in cs["ranges"]) + r["downsamp"]
+        x = synth.filterbank(40 + k, cs["n_tab"], cs["n_chan"], need)
+        plan, gpu, gs, ora, os_ = run_both(fdd, x, sb, f, cs["ranges"], 4.0, cs["n_out"], need)
+        for g, o in zip(gs, os_):
+            assert (g == o).all(), k
+        compare_candidates(gpu, ora, 4.0)
+    # an empty output: nothing searched, nothing written
+    f = synth.channel_freqs(16)
+    plan = fdd.Plan(1, 16, 1, f, T_SAMP, [dict(dm0=0.0, ddm=1.0, n_dm=4, widths=[1])], 4.0, np.zeros((1, 16)))
+    x = synth.filterbank(1, 1, 16, 200)
+    res = plan.search(to_dev(x), 200, 0, cap=16)
+    torch.cuda.synchronize()
+    assert int(res.count.item()) == 0
