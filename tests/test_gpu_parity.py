@@ -651,7 +651,8 @@ def test_edge_cases_against_oracle(fdd):
         rng = np.random.default_rng(k)
         sb = rng.integers(0, cs["n_tab"], size=(cs["n_sb"], cs["n_chan"])).astype(np.int16)
         need = max(int(oracle.delays(f, T_SAMP, r["dm0"], r["ddm"], r["n_dm"], r["downsamp"]).max()) * r["downsamp"]
-                   + (cs["n_out"] // r["downsamp"]) * r["downsamp"] for r in cs["ranges"]) + r["downsamp"]
+                   + (cs["n_out"] // r["downsamp"]) * r["downsamp"] for r in cs["ranges"])
+        need += max(r["downsamp"] for r in cs["ranges"])
         x = synth.filterbank(40 + k, cs["n_tab"], cs["n_chan"], need)
         plan, gpu, gs, ora, os_ = run_both(fdd, x, sb, f, cs["ranges"], 4.0, cs["n_out"], need)
         for g, o in zip(gs, os_):
