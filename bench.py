@@ -377,6 +377,9 @@ def run_fdd(args):
         dist.barrier()
     t_hi = time.time()
     clocks = sampler.stop(t_lo, t_hi)
+    for p_ in plans:
+        if p_.status() != 0:               # a tile-copy wait gave up: the timed output is incomplete
+            raise RuntimeError("device status word set (FDD_STATUS_TILE_WAIT): the measurement is void")
 
     dev_s = reduce_max(sum(step_ms) / 1e3, dist, dev)
     units = units_per_step(w) * args.steps * world

@@ -482,6 +482,15 @@ int fdd_cluster(const fdd_candidate* d_in, const uint64_t* d_in_count, int64_t c
 int fdd_plan_set_subband(fdd_plan* plan, int32_t r, int32_t chan_per_subband, int32_t dm_per_coarse);
 int fdd_plan_get_subband(const fdd_plan* plan, int32_t r, int32_t* chan_per_subband, int32_t* dm_per_coarse);
 
+/* Device status word of the plan, read with a blocking copy after the
+ * searches it covers have been synchronised (clear != 0 resets it).  Bit 0
+ * (FDD_STATUS_TILE_WAIT): a kernel's wait for an asynchronous tile copy
+ * gave up after its poll limit (about a second); that block stopped without
+ * writing its series, so the affected search's output is incomplete.  0 in
+ * normal operation. */
+#define FDD_STATUS_TILE_WAIT 1
+int fdd_plan_status(fdd_plan* plan, int32_t* status, int32_t clear);
+
 /* Number of kernels the last fdd_search or fdd_search_batch on this plan
  * enqueued (graph launches replay the last captured batch's kernels). */
 int fdd_plan_last_launches(const fdd_plan* plan, int64_t* n);

@@ -166,6 +166,7 @@ def _lib_raw():
     L.fdd_variant_kind.argtypes = [_I32, ctypes.POINTER(_I32)]
     L.fdd_plan_set_scratch_limit.argtypes = [_P, _I64]
     L.fdd_plan_last_launches.argtypes = [_P, ctypes.POINTER(_I64)]
+    L.fdd_plan_status.argtypes = [_P, ctypes.POINTER(_I32), _I32]
     L.fdd_plan_set_subband.argtypes = [_P, _I32, _I32, _I32]
     L.fdd_rfi_workspace_size.argtypes = [_I32, _I32, _I64, ctypes.POINTER(_SZ)]
     L.fdd_rfi_clean.argtypes = [ctypes.POINTER(_RfiDesc), _P, _I32, _I32, _I64, _I64, _P, _SZ, _P, _P, _P]
@@ -308,6 +309,7 @@ class Graph:
 
 FDD_ERR_SEQUENCE = -8
 FDD_BATCH_SB_FACTORED = 1000
+FDD_STATUS_TILE_WAIT = 1
 FDD_ERR_BUSY = -9
 
 
@@ -624,6 +626,13 @@ class Plan:
         fdd_plan_last_launches)."""
         v = _I64()
         _check(_lib_raw().fdd_plan_last_launches(self._h, ctypes.byref(v)), "fdd_plan_last_launches")
+        return int(v.value)
+
+    def status(self, clear=False):
+        """Device status word (include/fdd.h: fdd_plan_status; bit 0 =
+        FDD_STATUS_TILE_WAIT, a tile-copy wait that gave up).  Blocking."""
+        v = _I32()
+        _check(_lib_raw().fdd_plan_status(self._h, ctypes.byref(v), 1 if clear else 0), "fdd_plan_status")
         return int(v.value)
 
     def set_scratch_limit(self, nbytes):

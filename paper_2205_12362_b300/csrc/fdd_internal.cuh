@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <string>
+#include <cuda.h>  // CUtensorMap (the tensor-map encoder is reached through the runtime's entry-point query)
 #include <cuda_runtime.h>
 
 #include "fdd.h"
@@ -115,6 +116,8 @@ struct SbfPartArgs {
 };
 
 struct SbfCombArgs {
+    CUtensorMap tmap;           // P as a 4-D tensor (t, trial, segment, TAB); filled by launch_sbf_comb
+    unsigned int* status;       // device status word: bit 0 set if a tile wait gave up (kSpinLimit)
     const uint16_t* P;
     int64_t tab_stride, seg_stride;
     int32_t Np;
@@ -138,6 +141,8 @@ cudaError_t launch_sbf_part(int idx, const SbfPartArgs& a, int n_tab, cudaStream
 int sbf_comb_sbs_per_block();
 int sbf_comb_uc(int n_tab);
 size_t sbf_comb_smem_bytes(int n_tab);
+// Fills a.tmap from a.P and its strides (once per slab layout).
+cudaError_t encode_comb_map(SbfCombArgs& a);
 cudaError_t launch_sbf_comb(const SbfCombArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------------------

@@ -487,6 +487,11 @@ int fdd_plan_create(const fdd_plan_desc* desc, const int16_t* sb_map_host, fdd_p
         fdd_plan_destroy(p);
         return cuda_fail(e, "cudaMemcpy(sb_map)");
     }
+    if ((e = cudaMalloc(&p->d_status, sizeof(unsigned int))) != cudaSuccess ||
+        (e = cudaMemset(p->d_status, 0, sizeof(unsigned int))) != cudaSuccess) {
+        fdd_plan_destroy(p);
+        return cuda_fail(e, "cudaMalloc(status word)");
+    }
     for (RangeState& r : p->ranges) {
         int rc = FDD_ERR_UNSUPPORTED;
         const int E = (r.D == 1) ? 1 : 2;
@@ -511,7 +516,19 @@ int fdd_plan_destroy(fdd_plan* plan) {
         free_subband_tables(r);
     }
     if (plan->d_sb_map) cudaFree(plan->d_sb_map);
+    if (plan->d_status) cudaFree(plan->d_status);
     delete plan;
+    return FDD_OK;
+}
+
+int fdd_plan_status(fdd_plan* plan, int32_t* status, int32_t clear) {
+    if (!plan || !status) return fail(FDD_ERR_INVALID_ARG, "null argument");
+    unsigned int w = 0;
+    cudaError_t e = cudaMemcpy(&w, plan->d_status, sizeof(w), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(status word)");
+    if (clear && w && (e = cudaMemset(plan->d_status, 0, sizeof(w))) != cudaSuccess)
+        return cuda_fail(e, "cudaMemset(status word)");
+    *status = static_cast<int32_t>(w);
     return FDD_OK;
 }
 

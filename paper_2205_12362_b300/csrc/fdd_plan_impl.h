@@ -88,6 +88,7 @@ struct fdd_plan {
     std::vector<double> freq;
     std::vector<int16_t> sb_map;
     int16_t* d_sb_map = nullptr;
+    unsigned int* d_status = nullptr;  // device status word (fdd_plan_status)
     std::vector<RangeState> ranges;
     std::vector<int32_t> ds_factors;  // distinct D > 1
     int64_t max_delay_native = 0;

@@ -207,6 +207,8 @@ cudaError_t launch_range_sbf(const fdd_plan* p, const RangeState& r, const fdd::
     ca.flush = r.s_flush;
     ca.n_tab = p->n_tab;
     ca.uc = fdd::sbf_comb_uc(p->n_tab);
+    ca.status = p->d_status;
+    if (cudaError_t e = fdd::encode_comb_map(ca); e != cudaSuccess) return e;
     for (int64_t i0 = 0; i0 < r.n_dm; i0 += slab) {
         pa.i0 = static_cast<int32_t>(i0);
         pa.n_slab = static_cast<int32_t>(std::min<int64_t>(slab, r.n_dm - i0));

@@ -225,30 +225,63 @@ __global__ void __launch_bounds__(WARPS * 32) k_sbf_part(const SbfPartArgs a) {
 
 // Comb: block = CW warps x CSB SBs per warp, one DM trial, CT = 128 samples
 // (4 per lane).  The partial rows of every TAB for UC segments at a time are
-// copied into shared memory with cp.async (double-buffered), so each row is
-// read from L2/HBM once per block and then serves every SB that selects it.
-// A warp whose SBs run past n_sb repeats its last valid SB (results
-// discarded), so the inner loop has no per-SB branches.
+// one tile of P -- CT samples x UC segments x n_tab TABs -- which thread 0
+// requests with a single TMA tensor copy (cp.async.bulk.tensor) into shared
+// memory, double-buffered and completed on an mbarrier; each row is read from
+// L2/HBM once per block and then serves every SB that selects it.  Segments
+// past n_seg fall outside the tensor and arrive as zeros.  A warp whose SBs
+// run past n_sb repeats its last valid SB (results discarded), so the inner
+// loop has no per-SB branches.
 constexpr int CW = 12, CSB = 6, CT = 128, UC = 8;
 constexpr int kRowBytes = CT * 2;            // one partial row in shared memory
 constexpr int kTabBytes = UC * kRowBytes;    // UC rows of one TAB
+constexpr int kSmemAlign = 128;              // TMA destination alignment
+// Bound on the polls of one tile wait (each poll after the first 64 sleeps
+// ~256 ns, so about a second); a copy that has not landed by then sets bit 0
+// of the status word and the block stops.
+constexpr int kSpinLimit = 1 << 22;
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 __device__ __forceinline__ uint2 lds64(uint32_t addr) {
     uint2 v;
     asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
     return v;
 }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+// Wait for phase `parity` of the barrier to complete; false if kSpinLimit polls pass first.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+    for (int it = 0; it < kSpinLimit; it++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (it >= 64) __nanosleep(256);
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, int w,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar)
+        : "memory");
+}
 
-__global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const SbfCombArgs a) {
-    extern __shared__ __align__(16) uint8_t smem[];  // [2][n_tab][UC][CT] uint16
+__global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const __grid_constant__ SbfCombArgs a) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];  // [2][n_tab][UC][CT] uint16, then 2 mbarriers
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i_s = blockIdx.y;
     const int i = a.i0 + i_s;
@@ -256,9 +289,10 @@ __global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const SbfCombArgs a) {
     const int sb0 = blockIdx.z * (CW * CSB) + warp * CSB;
     const int nsb = max(0, min(CSB, a.n_sb - sb0));  // warp-uniform
     const int n_chunks = (a.n_seg + UC - 1) / UC;
-    const uint32_t s_base = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    const uint32_t s_raw = static_cast<uint32_t>(__cvta_generic_to_shared(smem_raw));
+    const uint32_t s_base = (s_raw + (kSmemAlign - 1)) & ~static_cast<uint32_t>(kSmemAlign - 1);
     const uint32_t buf_bytes = static_cast<uint32_t>(a.n_tab) * kTabBytes;
-    const uint16_t* p_trial = a.P + static_cast<int64_t>(i_s) * a.Np + t0;
+    const uint32_t s_bar = s_base + 2u * buf_bytes;  // two 8-byte mbarriers
     // the SBs of this warp (invalid slots repeat SB sb0 + nsb - 1, or SB 0 for an idle warp)
     const uint8_t* tab_row[CSB];
 #pragma unroll
@@ -267,22 +301,18 @@ __global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const SbfCombArgs a) {
         tab_row[j] = a.seg_tab + static_cast<int64_t>(sj) * a.seg_pitch;
     }
 
-    // copy chunk ch (UC segments of every TAB) into buffer buf: 16 pieces of 16 B per row
-    auto issue = [&](int ch, int buf) {
-        const int u0 = ch * UC;
-        const int nu = min(UC, a.n_seg - u0);
-        const int pieces = a.n_tab * UC * (CT / 8);
-        for (int idx = threadIdx.x; idx < pieces; idx += CW * 32) {
-            const int part = idx & (CT / 8 - 1);
-            const int row = idx >> 4;  // CT / 8 == 16
-            const int du = row & (UC - 1), k = row >> 3;  // UC == 8
-            if (du < nu) {
-                const uint16_t* src = p_trial + k * a.tab_stride + static_cast<int64_t>(u0 + du) * a.seg_stride + part * 8;
-                cp_async16(s_base + buf * buf_bytes + static_cast<uint32_t>(row * kRowBytes + part * 16), src);
-            }
-        }
-        cp_async_commit();
+    // chunk ch (UC segments of every TAB) into buffer ch & 1: one tensor copy by thread 0
+    auto issue = [&](int ch) {
+        const uint32_t bar = s_bar + 8u * (ch & 1);
+        mbar_expect_tx(bar, buf_bytes);
+        tma_load_4d(s_base + (ch & 1) * buf_bytes, &a.tmap, t0, i_s, ch * UC, 0, bar);
     };
+    if (threadIdx.x == 0) {
+        mbar_init(s_bar, 1);
+        mbar_init(s_bar + 8u, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
 
     uint32_t acc[CSB][2], tot[CSB][4];
 #pragma unroll
@@ -301,17 +331,21 @@ __global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const SbfCombArgs a) {
         }
     };
 
-    issue(0, 0);
+    if (threadIdx.x == 0) issue(0);
     int since = 0;
     for (int ch = 0; ch < n_chunks; ch++) {
         const int buf = ch & 1;
-        if (ch + 1 < n_chunks) {
-            issue(ch + 1, buf ^ 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
+        if (threadIdx.x == 0 && ch + 1 < n_chunks) issue(ch + 1);  // buffer buf ^ 1 was released below
+        const bool ok = mbar_wait_bounded(s_bar + 8u * buf, static_cast<uint32_t>(ch >> 1) & 1u);
+        if (__syncthreads_or(!ok)) {
+            // a copy did not land: flag it, let thread 0 wait (bounded) for this block's copies, stop
+            if (threadIdx.x == 0) {
+                atomicOr(a.status, 1u);
+                mbar_wait_bounded(s_bar + 8u * buf, static_cast<uint32_t>(ch >> 1) & 1u);
+                if (ch + 1 < n_chunks) mbar_wait_bounded(s_bar + 8u * (buf ^ 1), static_cast<uint32_t>((ch + 1) >> 1) & 1u);
+            }
+            return;
         }
-        __syncthreads();
         const int u0 = ch * UC;
         const int nu = min(UC, a.n_seg - u0);
         const uint32_t s_buf = s_base + buf * buf_bytes + 8u * lane;
@@ -426,7 +460,50 @@ int sbf_comb_sbs_per_block() { return CW * CSB; }
 
 int sbf_comb_uc(int) { return UC; }
 
-size_t sbf_comb_smem_bytes(int n_tab) { return 2ull * n_tab * kTabBytes; }
+size_t sbf_comb_smem_bytes(int n_tab) { return 2ull * n_tab * kTabBytes + 16 + kSmemAlign; }
+
+namespace {
+
+// cuTensorMapEncodeTiled, reached through the runtime's driver entry-point
+// query (the library links only the runtime).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled_fn() {
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<EncodeTiledFn>(ptr);
+    }();
+    return fn;
+}
+
+}  // namespace
+
+// P of a slab as a 4-D uint16 tensor: (t: Np, trial: slab rows, segment:
+// n_seg, TAB: n_tab), box (CT, 1, UC, n_tab) = one comb chunk.
+cudaError_t encode_comb_map(SbfCombArgs& a) {
+    const EncodeTiledFn enc = encode_tiled_fn();
+    if (!enc) return cudaErrorNotSupported;
+    if (a.Np <= 0 || a.seg_stride % a.Np != 0 || a.tab_stride != a.seg_stride * a.n_seg || a.n_tab > 256 ||
+        (reinterpret_cast<uintptr_t>(a.P) & 15u) != 0)
+        return cudaErrorInvalidValue;
+    const cuuint64_t dims[4] = {static_cast<cuuint64_t>(a.Np), static_cast<cuuint64_t>(a.seg_stride / a.Np),
+                                static_cast<cuuint64_t>(a.n_seg), static_cast<cuuint64_t>(a.n_tab)};
+    const cuuint64_t strides[3] = {static_cast<cuuint64_t>(a.Np) * 2, static_cast<cuuint64_t>(a.seg_stride) * 2,
+                                   static_cast<cuuint64_t>(a.tab_stride) * 2};
+    const cuuint32_t box[4] = {CT, 1, UC, static_cast<cuuint32_t>(a.n_tab)};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = enc(&a.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<uint16_t*>(a.P), dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
 
 cudaError_t launch_sbf_comb(const SbfCombArgs& a, cudaStream_t s) {
     const int per_block = CW * CSB;

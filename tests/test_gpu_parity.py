@@ -180,6 +180,7 @@ def test_fused_71_sb_sampled(fdd, kernel):
         assert plan.get_config(0)["work_ratio"] < 0.3
     res = plan.search(to_dev(x), n_in, n_out, cap=1 << 21, want_series=True)
     torch.cuda.synchronize()
+    assert plan.status() == 0                     # no tile-copy wait gave up
     gpu, n = res.candidates()
     assert n == len(gpu)
     series = plan.series_views(res.series, n_out)[0]
@@ -511,6 +512,7 @@ def test_sb_factored_piecewise_slabs(fdd):
         ran.add(v["bytes_per_sample"])
         res = plan.search(dx, n_in, n_out, want_series=True, cap=1 << 18)
         torch.cuda.synchronize()
+        assert plan.status() == 0
         g = plan.series_views(res.series, n_out)
         for k in range(2):
             assert (g[k].cpu().numpy() == os_[k]).all(), (v, k)
