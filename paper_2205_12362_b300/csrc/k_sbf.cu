@@ -235,6 +235,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_sbf_part(const SbfPartArgs a) {
 constexpr int CW = 12, CSB = 6, CT = 128, UC = 8;
 constexpr int kRowBytes = CT * 2;            // one partial row in shared memory
 constexpr int kTabBytes = UC * kRowBytes;    // UC rows of one TAB
+static_assert(kTabBytes == 1 << 11, "the TAB offset is formed as tab << 11");
 constexpr int kSmemAlign = 128;              // TMA destination alignment
 // Bound on the polls of one tile wait (each poll after the first 64 sleeps
 // ~256 ns, so about a second); a copy that has not landed by then sets bit 0
@@ -360,10 +361,9 @@ __global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const __grid_constant__
                 if (du < nu) {  // block-uniform
 #pragma unroll
                     for (int j = 0; j < CSB; j++) {
-                        // byte dq of tabs4 (the TAB) times kTabBytes (2048 = 2^11)
-                        const uint32_t koff = (dq <= 1 ? (tabs4[j] << (11 - 8 * dq)) : (tabs4[j] >> (8 * dq - 11))) &
-                                              (0xFFu << 11);
-                        const uint2 v = lds64(s_buf + koff + du * kRowBytes);
+                        // byte dq of tabs4 (the TAB; PRMT zero-fills the rest) times kTabBytes (2^11)
+                        const uint32_t tab = __byte_perm(tabs4[j], 0u, 0x4440u + dq);
+                        const uint2 v = lds64(s_buf + (tab << 11) + du * kRowBytes);
                         acc[j][0] += v.x;
                         acc[j][1] += v.y;
                     }
