@@ -17,11 +17,14 @@
 //   goff  [n_blk][n_groups][BD]  shared-memory byte offset of trial jj's pattern
 //                                row word for group g (copy = offset parity)
 //   pdesc per (block, stage) the list of pattern rows to build:
-//         {dst copy 0, dst copy 1, units of 4 samples, src offset per channel}
+//         {dst copy 0, dst copy 1, units of 4 samples, src byte address per
+//         channel (any alignment)}
 //   pd_idx [n_blk][n_stages][2]  (first descriptor, count)
 // and the raw row length Lw and the pattern region size of the layout.
-// Shared memory: [zero row | CC raw slots | pattern rows | 2 x stage offsets |
-// stage descriptors].
+// Shared memory, from a 128-byte-aligned base: [zero row | 2 raw buffers x
+// CC slots (one unshifted row each, TMA destinations, 128-byte aligned) |
+// pattern rows | 2 x stage offsets | stage descriptors | 2 mbarriers];
+// stage s builds from raw buffer s & 1.
 #include <algorithm>
 #include <map>
 #include <vector>
@@ -120,8 +123,8 @@ FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactV
                         if (k < gn) {
                             const int c = c0 + k;
                             const int32_t o = pt.rmin + pt.rel[k] - ft.base[static_cast<size_t>(b) * n_chan + c];
-                            // channel slot cc, copy (o & 3), aligned word (o & ~3); slot bases added below
-                            d[3 + k] = ((c - s * CC) << 20) | ((o & 3) << 18) | (o & ~3);
+                            // raw buffer (s & 1), channel slot cc, byte o of the row; slot bases added below
+                            d[3 + k] = ((s & 1) << 30) | ((c - s * CC) << 20) | o;
                             max_need = std::max<int64_t>(max_need, static_cast<int64_t>(o) + 4LL * nw4 + 4);
                         } else {
                             d[3 + k] = -1;  // missing channel: the zero row
@@ -150,33 +153,37 @@ FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactV
     ft.work_ratio = adds_brute > 0 ? adds_fact / adds_brute : 1.0;
     // raw row words: every staged read (brute-force span and pattern builds)
     const int64_t need_words = (max_need + 3) / 4;
-    const int64_t Lw = static_cast<int64_t>(align_up(static_cast<size_t>(need_words + 1), 4));
-    if (Lw > (1 << 16) || pat_region > (1 << 20)) {
+    int64_t Lw = static_cast<int64_t>(align_up(static_cast<size_t>(need_words + 1), 4));
+    if (Lw <= kFactMaxLw)
+        Lw = static_cast<int64_t>(align_up(static_cast<size_t>(Lw), fdd::fact_lw_align(static_cast<int>(Lw))));
+    if (Lw > kFactMaxLw || pat_region > (1 << 20)) {
         ft.Lw = -1;
         return ft;
     }
     ft.Lw = static_cast<int32_t>(Lw);
     ft.pat_bytes = static_cast<int32_t>(align_up(static_cast<size_t>(pat_region), 16));
-    // resolve shared-memory addresses: [zero row | raw slots | patterns | goff x2]
-    const int64_t zero_bytes = 4LL * ft.Lw;
-    const int64_t slot_bytes = 4LL * 4 * ft.Lw;
-    const int64_t pat_base = zero_bytes + slot_bytes * CC;
+    // resolve shared-memory addresses
+    ft.zero_off = 0;
+    ft.rb = static_cast<int32_t>(align_up(static_cast<size_t>(4 * Lw), 128));
+    ft.raw_off = static_cast<int32_t>(align_up(static_cast<size_t>(4 * Lw + 16), 128));
+    ft.pat_off = ft.raw_off + 2 * CC * ft.rb;
     for (size_t di = 0; di < ft.pdesc.size(); di += ft.desc_ints) {
-        ft.pdesc[di] += static_cast<int32_t>(pat_base);
-        ft.pdesc[di + 1] += static_cast<int32_t>(pat_base);
+        ft.pdesc[di] += ft.pat_off;
+        ft.pdesc[di + 1] += ft.pat_off;
         for (int k = 0; k < G; k++) {
             int32_t& e = ft.pdesc[di + 3 + k];
             if (e < 0) {
-                e = 0;  // zero row at the start of shared memory
+                e = ft.zero_off;  // zero row
             } else {
-                const int32_t cc = e >> 20, q = (e >> 18) & 3, w = e & ((1 << 18) - 1);
-                e = static_cast<int32_t>(zero_bytes + slot_bytes * cc + 4LL * ft.Lw * q + w);
+                const int32_t par = e >> 30, cc = (e >> 20) & 1023, o = e & ((1 << 20) - 1);
+                e = ft.raw_off + (par * CC + cc) * ft.rb + o;
             }
         }
     }
-    for (int32_t& g : ft.goff) g += static_cast<int32_t>(pat_base);
-    ft.smem_bytes = static_cast<size_t>(pat_base + ft.pat_bytes) + 2ull * gps * BD * 4 +
-                    static_cast<size_t>(ft.max_desc) * ft.desc_ints * 4;
+    for (int32_t& g : ft.goff) g += ft.pat_off;
+    ft.bar_off = ft.pat_off + ft.pat_bytes + 2 * gps * BD * 4 + ft.max_desc * ft.desc_ints * 4;
+    // + 16 bytes of mbarriers, + 128 for aligning the dynamic shared-memory base
+    ft.smem_bytes = static_cast<size_t>(ft.bar_off) + 16 + 128;
     return ft;
 }
 

@@ -62,16 +62,27 @@ cudaError_t launch_dedisp(int variant, const DedispArgs& a, cudaStream_t s);
 // ---------------------------------------------------------------------------
 // Pattern-factored dedispersion (k_dedisp_fact.cu; tables from fdd_fact.cu).
 //   G     channels per group; NW, DPW, WARPS as above; samples per word are
-//         16-bit pattern partials, so T = 64 * NW
+//         16-bit pattern partials, so T = 64 * NW.  Raw rows are staged by
+//         TMA (one unshifted copy per channel, double-buffered), so there is
+//         no staging-register budget.
 struct FactVariant {
-    int G, NW, DPW, WARPS, MAXIT;
+    int G, NW, DPW, WARPS;
     int bd() const { return WARPS * DPW; }
     int tile() const { return 64 * NW; }
     int threads() const { return WARPS * 32; }
     int desc_ints() const { return (3 + G + 3) / 4 * 4; }
 };
+// Staged raw rows (32-bit words) travel as fact_boxes(Lw) TMA boxes of
+// Lw / fact_boxes(Lw) words (at most 256); the table builder rounds Lw to a
+// multiple of fact_lw_align(Lw) so every box is whole and starts on a
+// 16-byte global and a 128-byte shared-memory boundary.
+constexpr int kFactMaxLw = 1024;
+__host__ __device__ inline int fact_boxes(int Lw) { return (Lw + 255) / 256; }
+__host__ __device__ inline int fact_lw_align(int Lw) { return fact_boxes(Lw) == 1 ? 4 : 32 * fact_boxes(Lw); }
 
 struct FactArgs {
+    CUtensorMap tmap;           // the input as a 2-D uint32 tensor (words of a row, rows); encode_fact_map
+    unsigned int* status;       // device status word: bit 0 set if a tile wait gave up
     const uint8_t* in;          // raw uint8 rows (tab, c) at in + (tab * n_chan + c) * pitch_bytes
     int64_t pitch_bytes;
     int64_t n_valid;            // valid samples per row
@@ -84,12 +95,26 @@ struct FactArgs {
     unsigned long long* stat;   // [n_sb * n_dm][2]
     int32_t n_chan, n_dm, n_out, n_sb;
     int32_t Lw, CC, n_stages, n_groups, pat_bytes;
+    int32_t zero_off;           // shared-memory layout (bytes from the 128-aligned base): zero row,
+    int32_t raw_off, rb;        //   raw slots (2 buffers x CC slots of rb bytes),
+    int32_t pat_off;            //   pattern rows (pat_bytes), then stage offsets and descriptors,
+    int32_t bar_off;            //   two mbarriers
 };
 
 int num_fact_variants();
 const FactVariant& fact_variant(int idx);
 bool fact_cc_ok(const FactVariant& v, int Lw, int CC, int max_desc);
+// Fills a.tmap for a.in (n_rows rows of a.pitch_bytes, a.n_valid valid bytes each; box = one
+// of the fact_boxes(a.Lw) pieces of a row).
+cudaError_t encode_fact_map(FactArgs& a, int64_t n_rows);
 cudaError_t launch_dedisp_fact(int variant, const FactArgs& a, size_t smem, cudaStream_t s);
+
+// cuTensorMapEncodeTiled, reached through the runtime's driver entry-point
+// query (the library links only the runtime); nullptr if unavailable.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled_fn();
 
 // ---------------------------------------------------------------------------
 // SB-factored dedispersion (k_sbf.cu; tables and slab loop in fdd_sbf.cu).

@@ -239,6 +239,11 @@ int configure_fact(fdd_plan* p, RangeState& r, int fv, int CC) {
     r.f_n_stages = best.n_stages;
     r.f_n_groups = best.n_groups;
     r.f_smem = best.smem_bytes;
+    r.f_zero_off = best.zero_off;
+    r.f_raw_off = best.raw_off;
+    r.f_rb = best.rb;
+    r.f_pat_off = best.pat_off;
+    r.f_bar_off = best.bar_off;
     r.f_work_ratio = static_cast<float>(best.work_ratio);
     return FDD_OK;
 }
@@ -275,9 +280,10 @@ int configure_range(fdd_plan* p, RangeState& r, int variant, int CC) {
 }
 
 // Launch range r's dedispersion kernel (brute force or pattern-factored).
-cudaError_t launch_range_dedisp(const RangeState& r, const fdd::DedispArgs& a, cudaStream_t s) {
+cudaError_t launch_range_dedisp(const fdd_plan* p, const RangeState& r, const fdd::DedispArgs& a, cudaStream_t s) {
     if (r.fact < 0) return fdd::launch_dedisp(r.variant, a, s);
     fdd::FactArgs fa{};
+    fa.status = p->d_status;
     fa.in = a.in;
     fa.pitch_bytes = a.pitch_bytes;
     fa.n_valid = a.n_valid;
@@ -297,6 +303,12 @@ cudaError_t launch_range_dedisp(const RangeState& r, const fdd::DedispArgs& a, c
     fa.n_stages = r.f_n_stages;
     fa.n_groups = r.f_n_groups;
     fa.pat_bytes = r.f_pat_bytes;
+    fa.zero_off = r.f_zero_off;
+    fa.raw_off = r.f_raw_off;
+    fa.rb = r.f_rb;
+    fa.pat_off = r.f_pat_off;
+    fa.bar_off = r.f_bar_off;
+    if (cudaError_t e = fdd::encode_fact_map(fa, static_cast<int64_t>(p->n_tab) * p->n_chan); e != cudaSuccess) return e;
     return fdd::launch_dedisp_fact(r.fact, fa, r.f_smem, s);
 }
 
@@ -311,7 +323,7 @@ cudaError_t launch_range(const fdd_plan* p, const RangeState& r, const fdd::Dedi
     if (r.sub_G > 0) return launch_range_subband(p, r, a, ws + L.sbf, L.sbf_bytes, s, launches);
     if (r.sbf >= 0) return launch_range_sbf(p, r, a, ws + L.sbf, L.sbf_bytes, s, launches);
     if (launches) *launches += 1;
-    return launch_range_dedisp(r, a, s);
+    return launch_range_dedisp(p, r, a, s);
 }
 
 int default_variant(int E) {
@@ -819,9 +831,9 @@ int fdd_plan_autotune(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64
             for (int cc : {16, 32, 48, 64}) {
                 if (configure_fact(plan, r, fv, cc) != FDD_OK) continue;  // does not fit
                 const fdd::DedispArgs a = dedisp_args(plan, r, ri, L, d_tabs, pitch, ws, series, stat, n_in, n_out);
-                if ((e = launch_range_dedisp(r, a, s)) != cudaSuccess) { rc = cuda_fail(e, "tuning launch"); break; }
+                if ((e = launch_range_dedisp(plan, r, a, s)) != cudaSuccess) { rc = cuda_fail(e, "tuning launch"); break; }
                 cudaEventRecord(ev0, s);
-                for (int k = 0; k < reps && e == cudaSuccess; k++) e = launch_range_dedisp(r, a, s);
+                for (int k = 0; k < reps && e == cudaSuccess; k++) e = launch_range_dedisp(plan, r, a, s);
                 cudaEventRecord(ev1, s);
                 if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
                 if (e != cudaSuccess) { rc = cuda_fail(e, "tuning launch"); break; }
@@ -901,6 +913,11 @@ int fdd_fact_tables_host(const fdd_plan_desc* desc, const int16_t* sb_map_host, 
     info[5] = static_cast<int64_t>(ft.smem_bytes);
     info[6] = ft.desc_ints ? static_cast<int64_t>(ft.pdesc.size()) / ft.desc_ints : 0;
     info[7] = n_blk;
+    info[8] = ft.zero_off;
+    info[9] = ft.raw_off;
+    info[10] = ft.rb;
+    info[11] = ft.pat_off;
+    info[12] = ft.bar_off;
     if (ft.Lw < 0) return FDD_OK;
     if (base) std::memcpy(base, ft.base.data(), ft.base.size() * sizeof(int32_t));
     if (goff) std::memcpy(goff, ft.goff.data(), ft.goff.size() * sizeof(int32_t));

@@ -3,22 +3,28 @@
 // per channel-add.  See fdd_fact.cu for the factorisation and its tables.
 //
 // Block = BD trials x T = 64*NW output samples of one SB.  Per channel stage:
-//   1. staging (as k_dedisp): the SB's TAB row of every channel, 4 byte-shifted
-//      copies, software-pipelined through registers;
+//   1. staging: TMA tensor copies (one to four boxes per channel) bring the
+//      SB's TAB row (Lw words from a 16-byte-aligned start, zero past the
+//      row's valid words) into shared memory, unshifted; raw rows are double-buffered
+//      and the copies of stage s+2 are issued as soon as stage s's builds
+//      are done, so the loads run behind two stages of work and no register
+//      holds them;
 //   2. build: each warp takes pattern rows of the stage's channel groups
-//      (descriptors staged in shared memory with the raw rows); a lane forms
-//      4 consecutive samples of R_p(tau) = sum_k X_k(tau + rel_k) from one
-//      aligned LDS.32 per channel (odd bytes split off with one PRMT, even
-//      bytes recovered by subtraction) and stores them as two copies of
-//      16-bit pairs, the
-//      second shifted by one sample (the neighbouring lane's first sample
-//      comes by shuffle), so every trial's offset is an aligned LDS.32;
+//      (descriptors staged in shared memory); a lane forms 4 consecutive
+//      samples of R_p(tau) = sum_k X_k(tau + rel_k) from two aligned LDS.32
+//      per channel joined by a funnel shift (rows start at any byte), odd
+//      bytes split off with one PRMT, even bytes recovered by subtraction,
+//      and stores them as two copies of 16-bit pairs, the second shifted by
+//      one sample (the neighbouring lane's first sample comes by shuffle), so
+//      every trial's offset is an aligned LDS.32;
 //   3. accumulate: each trial adds, per group, one word of two 16-bit
 //      partials into 16-bit lanes (two groups per IADD3), folded into 32-bit
 //      totals before a lane holds more than 256 channels.
-// The next stage's global loads are in flight during the build, and its
-// staging stores overlap the accumulation (which only reads pattern rows).
+// The raw rows are read only by the builds (a few pattern rows per group),
+// not by every trial, which is why one unshifted TMA copy beats the four
+// byte-shifted copies the brute-force kernel stages.
 #include "fdd_internal.cuh"
+#include "tma.cuh"
 
 namespace fdd {
 
@@ -69,15 +75,17 @@ __device__ __forceinline__ void load_offsets(const int32_t* p, int32_t (&o)[N]) 
 
 // Pattern-row builds (whole warp).  A row descriptor in shared memory is
 // {dst0, dst1, nw4, src[G]}: copy-0 and copy-1 destinations, units of 4
-// samples, and the staged raw word of unit 0 for each channel.  Per lane and
-// unit: acc_a = sum of the G raw words (bytes overlap), acc_b = sum of bytes
-// 1,3 in 16-bit lanes (one PRMT per word); samples 0,2 are acc_a - (acc_b <<
-// 8) (lanes hold <= 257 * 255).  Copy 0 stores [R0,R1],[R2,R3]; copy 1 stores
-// [R1,R2],[R3,R4], R4 being the next lane's R0 (shuffle; across a 32-unit
-// step it comes from lane 0 of the next step).
+// samples, and the shared-memory byte address of unit 0 of each channel's
+// raw row (any alignment: a lane reads the aligned words around it and
+// funnel-shifts).  Per lane and unit: acc_a = sum of the G raw words (bytes
+// overlap), acc_b = sum of bytes 1,3 in 16-bit lanes (one PRMT per word);
+// samples 0,2 are acc_a - (acc_b << 8) (lanes hold <= 257 * 255).  Copy 0
+// stores [R0,R1],[R2,R3]; copy 1 stores [R1,R2],[R3,R4], R4 being the next
+// lane's R0 (shuffle; across a 32-unit step it comes from lane 0 of the next
+// step).
 template <int G>
 struct RowState {
-    uint32_t dst0, dst1, src[G];
+    uint32_t dst0, dst1, src[G], sh[G];
     int nw4;
     uint32_t pend_b;
 
@@ -86,8 +94,12 @@ struct RowState {
                      : "=r"(dst0), "=r"(dst1), "=r"(nw4), "=r"(src[0])
                      : "r"(d));
 #pragma unroll
-        for (int k = 1; k < G; k++) src[k] = s0 + lds32(d + 4u * (3 + k));
-        src[0] += s0;
+        for (int k = 1; k < G; k++) src[k] = lds32(d + 4u * (3 + k));
+#pragma unroll
+        for (int k = 0; k < G; k++) {
+            sh[k] = src[k] << 3;             // funnel shift uses the low 5 bits: 8 * (byte & 3)
+            src[k] = (s0 + src[k]) & ~3u;    // aligned word holding the row's first byte (s0 is 128-aligned)
+        }
         dst0 += s0;
         dst1 += s0;
         pend_b = 0;
@@ -101,8 +113,9 @@ struct RowState {
         if (j < nw4) {
 #pragma unroll
             for (int k = 0; k < G; k += 2) {
-                const uint32_t x0 = lds32(src[k] + 4u * j);
-                const uint32_t x1 = lds32(src[k + 1] + 4u * j);
+                const uint32_t a0 = src[k] + 4u * j, a1 = src[k + 1] + 4u * j;
+                const uint32_t x0 = __funnelshift_r(lds32(a0), lds32(a0 + 4u), sh[k]);
+                const uint32_t x1 = __funnelshift_r(lds32(a1), lds32(a1 + 4u), sh[k + 1]);
                 acc_a = acc_a + x0 + x1;
                 acc_b = acc_b + __byte_perm(x0, 0u, 0x4341) + __byte_perm(x1, 0u, 0x4341);
             }
@@ -151,77 +164,71 @@ __device__ __forceinline__ void build_rows(uint32_t d0, uint32_t d1, uint32_t s0
     if (two) b.finish(lane);
 }
 
-template <int G, int NW, int DPW, int WARPS, int MAXIT>
-__global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1) k_dedisp_fact(const FactArgs a) {
+template <int G, int NW, int DPW, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
+    k_dedisp_fact(const __grid_constant__ FactArgs a) {
     constexpr int BD = WARPS * DPW;
     constexpr int T = 64 * NW;
-    constexpr int NT = WARPS * 32;
     constexpr int DI = (3 + G + 3) / 4 * 4;
     static_assert(BD % 4 == 0, "BD must be a multiple of 4");
-    extern __shared__ __align__(16) uint8_t smem[];
+    extern __shared__ __align__(16) uint8_t smem_raw[];
 
     const int Lw = a.Lw, CC = a.CC;
-    const int chunks = Lw >> 2;
     const int gps = CC / G;
-    const int slot_bytes = 16 * Lw;
-    uint8_t* s_raw = smem + 4 * Lw;
-    int32_t* s_goff = reinterpret_cast<int32_t*>(smem + 4 * Lw + CC * slot_bytes + a.pat_bytes);  // [2][gps][BD]
+    // every offset below is from the 128-byte-aligned base (TMA destinations)
+    const uint32_t s_unal = static_cast<uint32_t>(__cvta_generic_to_shared(smem_raw));
+    const uint32_t s0 = (s_unal + 127u) & ~127u;
+    uint8_t* smem = smem_raw + (s0 - s_unal);
+    int32_t* s_goff = reinterpret_cast<int32_t*>(smem + a.pat_off + a.pat_bytes);  // [2][gps][BD]
     int32_t* s_desc = s_goff + 2 * gps * BD;  // [max_desc][DI] of the stage being built
-    const uint32_t s0 = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
     const uint32_t s_desc32 = static_cast<uint32_t>(__cvta_generic_to_shared(s_desc));
+    const uint32_t s_bar = s0 + static_cast<uint32_t>(a.bar_off);  // two 8-byte mbarriers (raw buffers 0, 1)
 
     const int blk = blockIdx.y, sb = blockIdx.z;
     const int t0 = blockIdx.x * T;
     const int i0 = blk * BD;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t limit = a.n_valid;  // valid bytes per input row
     const int16_t* sbm = a.sb_map + (int64_t)sb * a.n_chan;
     const int32_t* base_blk = a.base + (int64_t)blk * a.n_chan;
     const int32_t* goff_blk = a.goff + (int64_t)blk * a.n_groups * BD;
     const int32_t* pd_blk = a.pd_idx + (int64_t)blk * a.n_stages * 2;
 
-    for (int i = threadIdx.x; i < Lw; i += NT) reinterpret_cast<uint32_t*>(smem)[i] = 0u;  // zero row
+    for (int i = threadIdx.x; i < Lw + 4; i += WARPS * 32)
+        reinterpret_cast<uint32_t*>(smem + a.zero_off)[i] = 0u;  // zero row (missing channels)
+    if (threadIdx.x == 0) {
+        tma::mbar_init(s_bar, 1);
+        tma::mbar_init(s_bar + 8u, 1);
+        tma::mbar_init_fence();
+    }
+    __syncthreads();
 
-    uint4 pv[MAXIT];
-    uint32_t pn[MAXIT];
+    // Raw rows of stage s into buffer s & 1 (warp 0): Lw words per channel
+    // (fact_boxes(Lw) boxes), from word (t0 + base) / 4 of row (TAB, c);
+    // lane 0 first arms the buffer's barrier with the stage's byte count.
+    auto issue = [&](int s) {
+        const int c0 = s * CC;
+        const int ncc = min(CC, a.n_chan - c0);
+        const uint32_t bar = s_bar + 8u * (s & 1);
+        if (lane == 0) tma::mbar_expect_tx(bar, static_cast<uint32_t>(ncc) * static_cast<uint32_t>(Lw) * 4u);
+        __syncwarp();
+        const uint32_t dst = s0 + static_cast<uint32_t>(a.raw_off + (s & 1) * CC * a.rb);
+        const int nb = fact_boxes(Lw), bw = Lw / nb;
+        for (int cc = lane; cc < ncc; cc += 32) {
+            const int c = c0 + cc;
+            const int x = (t0 + base_blk[c]) >> 2, y = sbm[c] * a.n_chan + c;
+            for (int k = 0; k < nb; k++)
+                tma::load_2d(dst + static_cast<uint32_t>(cc * a.rb + 4 * k * bw), &a.tmap, x + k * bw, y, bar);
+        }
+    };
+
     int4 po = make_int4(0, 0, 0, 0);
     int4 pdv = make_int4(0, 0, 0, 0);
     int n_desc_next = 0;
 
-    auto stage_load = [&](int s) {
-        const int c0 = s * CC;
-        const int ncc = min(CC, a.n_chan - c0);
+    // stage offsets and descriptors of stage s into registers, then shared memory
+    auto small_load = [&](int s) {
+        const int ncc = min(CC, a.n_chan - s * CC);
         const int ngs = (ncc + G - 1) / G;
-        const int items = ncc * chunks;
-#pragma unroll
-        for (int u = 0; u < MAXIT; u++) {
-            const int it = threadIdx.x + u * NT;
-            if (it < items) {
-                const int cc = it / chunks;
-                const int m = it - cc * chunks;
-                const int c = c0 + cc;
-                const uint8_t* row = a.in + ((int64_t)sbm[c] * a.n_chan + c) * a.pitch_bytes;
-                const int64_t b0 = (int64_t)(t0 + base_blk[c]) + 16 * (int64_t)m;
-                if (b0 + 20 <= limit) {
-                    pv[u] = __ldg(reinterpret_cast<const uint4*>(row + b0));
-                    pn[u] = __ldg(reinterpret_cast<const uint32_t*>(row + b0 + 16));
-                } else {
-                    uint32_t g[5];
-#pragma unroll
-                    for (int k = 0; k < 5; k++) {
-                        uint32_t w = 0;
-#pragma unroll
-                        for (int b = 0; b < 4; b++) {
-                            const int64_t p = b0 + 4 * k + b;
-                            w |= ((p < limit) ? (uint32_t)row[p] : 0u) << (8 * b);
-                        }
-                        g[k] = w;
-                    }
-                    pv[u] = make_uint4(g[0], g[1], g[2], g[3]);
-                    pn[u] = g[4];
-                }
-            }
-        }
         if (threadIdx.x < ngs * (BD / 4))
             po = __ldg(reinterpret_cast<const int4*>(goff_blk + (int64_t)(s * gps) * BD) + threadIdx.x);
         const int first = pd_blk[2 * s];
@@ -229,31 +236,9 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1) k_dedisp_fac
         if (threadIdx.x < n_desc_next * (DI / 4))
             pdv = __ldg(reinterpret_cast<const int4*>(a.pdesc + (int64_t)first * DI) + threadIdx.x);
     };
-
-    auto stage_store = [&](int s, int buf) {
-        const int c0 = s * CC;
-        const int ncc = min(CC, a.n_chan - c0);
+    auto small_store = [&](int s, int buf) {
+        const int ncc = min(CC, a.n_chan - s * CC);
         const int ngs = (ncc + G - 1) / G;
-        const int items = ncc * chunks;
-#pragma unroll
-        for (int u = 0; u < MAXIT; u++) {
-            const int it = threadIdx.x + u * NT;
-            if (it < items) {
-                const int cc = it / chunks;
-                const int m = it - cc * chunks;
-                uint8_t* dst = s_raw + cc * slot_bytes + 16 * m;
-                const uint32_t g0 = pv[u].x, g1 = pv[u].y, g2 = pv[u].z, g3 = pv[u].w, g4 = pn[u];
-#pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    uint4 o;
-                    o.x = __funnelshift_r(g0, g1, 8 * q);
-                    o.y = __funnelshift_r(g1, g2, 8 * q);
-                    o.z = __funnelshift_r(g2, g3, 8 * q);
-                    o.w = __funnelshift_r(g3, g4, 8 * q);
-                    *reinterpret_cast<uint4*>(dst + q * Lw * 4) = o;
-                }
-            }
-        }
         if (threadIdx.x < ngs * (BD / 4)) reinterpret_cast<int4*>(s_goff + buf * gps * BD)[threadIdx.x] = po;
         if (threadIdx.x < n_desc_next * (DI / 4)) reinterpret_cast<int4*>(s_desc)[threadIdx.x] = pdv;
     };
@@ -282,8 +267,12 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1) k_dedisp_fac
     };
 
     const uint32_t s_lane = s0 + 4u * lane;
-    stage_load(0);
-    stage_store(0, 0);
+    if (warp == 0) {
+        issue(0);
+        if (a.n_stages > 1) issue(1);
+    }
+    small_load(0);
+    small_store(0, 0);
     __syncthreads();
 
     int since_fold = 0;  // channels held in the 16-bit lanes
@@ -293,11 +282,25 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1) k_dedisp_fac
         const int ncc = min(CC, a.n_chan - s * CC);
         const int ngs = (ncc + G - 1) / G;
         const int n_desc = n_desc_next;
-        if (next) stage_load(s + 1);  // in flight during the build
-        for (int d = 2 * warp; d < n_desc; d += 2 * WARPS)
-            build_rows<G>(s_desc32 + 4u * DI * d, d + 1 < n_desc ? s_desc32 + 4u * DI * (d + 1) : 0xffffffffu, s0, lane);
-        __syncthreads();  // pattern rows complete; raw rows and descriptors free
-        if (next) stage_store(s + 1, buf ^ 1);
+        if (next) small_load(s + 1);
+        const bool ok = tma::mbar_wait_bounded(s_bar + 8u * buf, static_cast<uint32_t>(s >> 1) & 1u);
+        if (ok) {
+            for (int d = 2 * warp; d < n_desc; d += 2 * WARPS)
+                build_rows<G>(s_desc32 + 4u * DI * d, d + 1 < n_desc ? s_desc32 + 4u * DI * (d + 1) : 0xffffffffu, s0,
+                              lane);
+        }
+        // pattern rows complete; raw buffer buf and the descriptors free
+        if (__syncthreads_or(!ok)) {
+            // a raw-row copy did not land: flag it, let thread 0 wait (bounded) for this block's copies, stop
+            if (threadIdx.x == 0) {
+                atomicOr(a.status, 1u);
+                tma::mbar_wait_bounded(s_bar + 8u * buf, static_cast<uint32_t>(s >> 1) & 1u);
+                if (next) tma::mbar_wait_bounded(s_bar + 8u * (buf ^ 1), static_cast<uint32_t>((s + 1) >> 1) & 1u);
+            }
+            return;
+        }
+        if (warp == 0 && s + 2 < a.n_stages) issue(s + 2);  // into buffer buf, behind two stages of work
+        if (next) small_store(s + 1, buf ^ 1);
         if (since_fold + ncc > 256) {
             fold();
             since_fold = 0;
@@ -331,7 +334,7 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1) k_dedisp_fac
 #pragma unroll
                 for (int k = 0; k < NW; k++) acc[j][k] += lds32(s_lane + static_cast<uint32_t>(o0[j]) + 128u * k);
         }
-        __syncthreads();  // pattern rows consumed; next stage's rows, offsets, descriptors visible
+        __syncthreads();  // pattern rows consumed; next stage's offsets and descriptors visible
     }
     fold();
 
@@ -379,20 +382,20 @@ struct FEntry {
     FactFn fn;
 };
 
-#define FDD_F(G, NW, DPW, WARPS, MAXIT) {{G, NW, DPW, WARPS, MAXIT}, k_dedisp_fact<G, NW, DPW, WARPS, MAXIT>}
+#define FDD_F(G, NW, DPW, WARPS) {{G, NW, DPW, WARPS}, k_dedisp_fact<G, NW, DPW, WARPS>}
 const FEntry kFEntries[] = {
-    FDD_F(8, 4, 4, 16, 4),  // G 8, BD 64, T 256, 512 threads
-    FDD_F(8, 4, 2, 16, 4),  // G 8, BD 32, T 256
-    FDD_F(4, 4, 4, 16, 4),  // G 4, BD 64, T 256
-    FDD_F(8, 2, 4, 16, 4),  // G 8, BD 64, T 128
-    FDD_F(8, 8, 2, 16, 4),  // G 8, BD 32, T 512
-    FDD_F(4, 8, 2, 16, 4),  // G 4, BD 32, T 512
-    FDD_F(4, 2, 8, 8, 4),   // G 4, BD 64, T 128, 256 threads (two blocks per SM)
-    FDD_F(4, 4, 4, 8, 4),   // G 4, BD 32, T 256, 256 threads
-    FDD_F(8, 2, 8, 8, 4),   // G 8, BD 64, T 128, 256 threads
-    FDD_F(4, 4, 8, 8, 4),   // G 4, BD 64, T 256, 256 threads
-    FDD_F(4, 4, 2, 32, 1),  // G 4, BD 64, T 256, 1024 threads (32 warps for latency hiding)
-    FDD_F(4, 4, 1, 32, 1),  // G 4, BD 32, T 256, 1024 threads
+    FDD_F(8, 4, 4, 16),  // G 8, BD 64, T 256, 512 threads
+    FDD_F(8, 4, 2, 16),  // G 8, BD 32, T 256
+    FDD_F(4, 4, 4, 16),  // G 4, BD 64, T 256
+    FDD_F(8, 2, 4, 16),  // G 8, BD 64, T 128
+    FDD_F(8, 8, 2, 16),  // G 8, BD 32, T 512
+    FDD_F(4, 8, 2, 16),  // G 4, BD 32, T 512
+    FDD_F(4, 2, 8, 8),   // G 4, BD 64, T 128, 256 threads (two blocks per SM)
+    FDD_F(4, 4, 4, 8),   // G 4, BD 32, T 256, 256 threads
+    FDD_F(8, 2, 8, 8),   // G 8, BD 64, T 128, 256 threads
+    FDD_F(4, 4, 8, 8),   // G 4, BD 64, T 256, 256 threads
+    FDD_F(4, 4, 2, 32),  // G 4, BD 64, T 256, 1024 threads (32 warps for latency hiding)
+    FDD_F(4, 4, 1, 32),  // G 4, BD 32, T 256, 1024 threads
 };
 #undef FDD_F
 
@@ -404,10 +407,33 @@ const FactVariant& fact_variant(int idx) { return kFEntries[idx].v; }
 
 bool fact_cc_ok(const FactVariant& v, int Lw, int CC, int max_desc) {
     if (CC < v.G || CC % v.G != 0 || CC > 256) return false;
+    if (Lw < 4 || Lw > kFactMaxLw || Lw % fact_lw_align(Lw) != 0) return false;  // whole, aligned boxes
     if (max_desc * (v.desc_ints() / 4) > v.threads()) return false;
-    if (static_cast<int64_t>(CC) * (Lw / 4) > static_cast<int64_t>(v.MAXIT) * v.threads()) return false;
     if ((CC / v.G) * (v.bd() / 4) > v.threads()) return false;
     return true;
+}
+
+// The input rows as a 2-D uint32 tensor: dim 0 = words of a row (the valid
+// bytes rounded up to a word; TMA fills zeros past it), dim 1 = rows
+// (TAB, channel); box = Lw / fact_boxes(Lw) words of one row.  Rounding up may bring in up to
+// three bytes past the valid ones (inside the row pitch), which reach only
+// output samples at or beyond n_out.
+cudaError_t encode_fact_map(FactArgs& a, int64_t n_rows) {
+    const EncodeTiledFn enc = encode_tiled_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const int64_t words = (a.n_valid + 3) / 4;
+    if (a.Lw < 4 || a.Lw > kFactMaxLw || a.Lw % fact_lw_align(a.Lw) != 0 ||
+        (reinterpret_cast<uintptr_t>(a.in) & 15u) != 0 || a.pitch_bytes % 16 != 0 || words * 4 > a.pitch_bytes ||
+        n_rows < 1)
+        return cudaErrorInvalidValue;
+    const cuuint64_t dims[2] = {static_cast<cuuint64_t>(words), static_cast<cuuint64_t>(n_rows)};
+    const cuuint64_t strides[1] = {static_cast<cuuint64_t>(a.pitch_bytes)};
+    const cuuint32_t box[2] = {static_cast<cuuint32_t>(a.Lw / fact_boxes(a.Lw)), 1};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(&a.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint8_t*>(a.in), dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_dedisp_fact(int variant, const FactArgs& a, size_t smem, cudaStream_t s) {

@@ -18,6 +18,7 @@
 // in 16-bit lanes folded into int32 every `flush` segments, then writes the
 // series and its moments like the brute-force epilogue.
 #include "dedisp_tile.cuh"
+#include "tma.cuh"
 
 namespace fdd {
 
@@ -237,50 +238,12 @@ constexpr int kRowBytes = CT * 2;            // one partial row in shared memory
 constexpr int kTabBytes = UC * kRowBytes;    // UC rows of one TAB
 static_assert(kTabBytes == 1 << 11, "the TAB offset is formed as tab << 11");
 constexpr int kSmemAlign = 128;              // TMA destination alignment
-// Bound on the polls of one tile wait (each poll after the first 64 sleeps
-// ~256 ns, so about a second); a copy that has not landed by then sets bit 0
-// of the status word and the block stops.
-constexpr int kSpinLimit = 1 << 22;
 
 __device__ __forceinline__ uint2 lds64(uint32_t addr) {
     uint2 v;
     asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
     return v;
 }
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0u;
-}
-// Wait for phase `parity` of the barrier to complete; false if kSpinLimit polls pass first.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-    for (int it = 0; it < kSpinLimit; it++) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (it >= 64) __nanosleep(256);
-    }
-    return false;
-}
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, int w,
-                                            uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-        "[%6];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar)
-        : "memory");
-}
-
 __global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const __grid_constant__ SbfCombArgs a) {
     extern __shared__ __align__(16) uint8_t smem_raw[];  // [2][n_tab][UC][CT] uint16, then 2 mbarriers
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -305,13 +268,13 @@ __global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const __grid_constant__
     // chunk ch (UC segments of every TAB) into buffer ch & 1: one tensor copy by thread 0
     auto issue = [&](int ch) {
         const uint32_t bar = s_bar + 8u * (ch & 1);
-        mbar_expect_tx(bar, buf_bytes);
-        tma_load_4d(s_base + (ch & 1) * buf_bytes, &a.tmap, t0, i_s, ch * UC, 0, bar);
+        tma::mbar_expect_tx(bar, buf_bytes);
+        tma::load_4d(s_base + (ch & 1) * buf_bytes, &a.tmap, t0, i_s, ch * UC, 0, bar);
     };
     if (threadIdx.x == 0) {
-        mbar_init(s_bar, 1);
-        mbar_init(s_bar + 8u, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tma::mbar_init(s_bar, 1);
+        tma::mbar_init(s_bar + 8u, 1);
+        tma::mbar_init_fence();
     }
     __syncthreads();
 
@@ -337,13 +300,13 @@ __global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const __grid_constant__
     for (int ch = 0; ch < n_chunks; ch++) {
         const int buf = ch & 1;
         if (threadIdx.x == 0 && ch + 1 < n_chunks) issue(ch + 1);  // buffer buf ^ 1 was released below
-        const bool ok = mbar_wait_bounded(s_bar + 8u * buf, static_cast<uint32_t>(ch >> 1) & 1u);
+        const bool ok = tma::mbar_wait_bounded(s_bar + 8u * buf, static_cast<uint32_t>(ch >> 1) & 1u);
         if (__syncthreads_or(!ok)) {
             // a copy did not land: flag it, let thread 0 wait (bounded) for this block's copies, stop
             if (threadIdx.x == 0) {
                 atomicOr(a.status, 1u);
-                mbar_wait_bounded(s_bar + 8u * buf, static_cast<uint32_t>(ch >> 1) & 1u);
-                if (ch + 1 < n_chunks) mbar_wait_bounded(s_bar + 8u * (buf ^ 1), static_cast<uint32_t>((ch + 1) >> 1) & 1u);
+                tma::mbar_wait_bounded(s_bar + 8u * buf, static_cast<uint32_t>(ch >> 1) & 1u);
+                if (ch + 1 < n_chunks) tma::mbar_wait_bounded(s_bar + 8u * (buf ^ 1), static_cast<uint32_t>((ch + 1) >> 1) & 1u);
             }
             return;
         }
@@ -462,14 +425,6 @@ int sbf_comb_uc(int) { return UC; }
 
 size_t sbf_comb_smem_bytes(int n_tab) { return 2ull * n_tab * kTabBytes + 16 + kSmemAlign; }
 
-namespace {
-
-// cuTensorMapEncodeTiled, reached through the runtime's driver entry-point
-// query (the library links only the runtime).
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
 EncodeTiledFn encode_tiled_fn() {
     static const EncodeTiledFn fn = []() -> EncodeTiledFn {
         void* ptr = nullptr;
@@ -482,8 +437,6 @@ EncodeTiledFn encode_tiled_fn() {
     }();
     return fn;
 }
-
-}  // namespace
 
 // P of a slab as a 4-D uint16 tensor: (t: Np, trial: slab rows, segment:
 // n_seg, TAB: n_tab), box (CT, 1, UC, n_tab) = one comb chunk.

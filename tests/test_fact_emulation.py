@@ -1,10 +1,14 @@
 """CPU checks of the pattern-factored dedispersion kernel's shared-memory
 addressing and arithmetic: the library's own host tables
 (fdd_fact_tables_host) drive a numpy emulation of every block of the kernel
--- raw staging in 4 byte-shifted copies, pattern-row builds (even/odd byte
-lanes, PRMT packing, the shifted copy with the neighbouring lane's sample),
-and the per-trial accumulation -- which must stay inside each shared-memory
-region and reproduce the oracle's brute-force series exactly."""
+-- raw staging as the kernel's TMA copies do it (one unshifted row of Lw
+words per channel into raw buffer s & 1, zeros past the row's valid words,
+and arbitrary bytes between the last valid sample and the end of its word),
+pattern-row builds (two aligned words joined by a funnel shift, even/odd
+byte lanes, PRMT packing, the shifted copy with the neighbouring lane's
+sample), and the per-trial accumulation -- which must stay inside each
+shared-memory region (a build reads only the Lw words its channel's copy
+wrote) and reproduce the oracle's brute-force series exactly."""
 import numpy as np
 import pytest
 
@@ -46,20 +50,38 @@ class Smem:
             self.m[addr + k] = ((val >> np.uint32(8 * k)) & np.uint32(0xFF)).astype(np.uint8)
 
 
+def funnel_r(lo, hi, sh):
+    """__funnelshift_r: low 32 bits of (hi:lo) >> (sh & 31)."""
+    w = (np.asarray(hi, np.uint64) << np.uint64(32)) | np.asarray(lo, np.uint64)
+    return ((w >> np.uint64(sh & 31)) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+
+
 def emulate(x, n_valid, sb_map, tb, v, CC, n_dm, n_out):
     G, BD, T = v["group"], v["dm_per_block"], v["tile"]
     NW = T // 64
     Lw, pat_bytes, smem_bytes = tb["Lw"], tb["pat_bytes"], tb["smem_bytes"]
+    rb, raw_lo = tb["rb"], tb["raw_off"]
     n_chan = x.shape[1]
     gps = CC // G
-    zero_hi = 4 * Lw
-    raw_lo, raw_hi = zero_hi, zero_hi + CC * 16 * Lw
-    pat_lo, pat_hi = raw_hi, raw_hi + pat_bytes
+    zero_lo, zero_hi = tb["zero_off"], tb["zero_off"] + 4 * Lw + 16
+    assert zero_hi <= raw_lo and raw_lo % 128 == 0 and rb % 128 == 0 and rb >= 4 * Lw
+    raw_hi = raw_lo + 2 * CC * rb
+    pat_lo, pat_hi = tb["pat_off"], tb["pat_off"] + pat_bytes
+    assert pat_lo == raw_hi
     goff_lo = pat_hi
     desc_lo = goff_lo + 2 * gps * BD * 4
     max_desc = int(tb["pd_idx"][..., 1].max())
-    assert desc_lo + max_desc * tb["desc_ints"] * 4 == smem_bytes
+    assert desc_lo + max_desc * tb["desc_ints"] * 4 == tb["bar_off"] and tb["bar_off"] % 8 == 0
+    assert tb["bar_off"] + 16 + 128 == smem_bytes       # mbarriers + base alignment slack
     assert desc_lo % 16 == 0 and max_desc * (tb["desc_ints"] // 4) <= v["threads"]
+    words_valid = (n_valid + 3) // 4                     # the tensor's row length in words
+
+    def slot_of(addr):
+        """Bounds of the region a build read at addr may touch."""
+        if addr < zero_hi:
+            return zero_lo, zero_hi
+        k = (addr - raw_lo) // rb
+        return raw_lo + k * rb, raw_lo + k * rb + 4 * Lw
     n_sb = sb_map.shape[0]
     S = np.zeros((n_sb, n_dm, n_out), np.int64)
     lanes = np.arange(32)
@@ -68,23 +90,23 @@ def emulate(x, n_valid, sb_map, tb, v, CC, n_dm, n_out):
             for tile in range((n_out + T - 1) // T):
                 t0 = tile * T
                 sm = Smem(smem_bytes)
-                sm.m[:zero_hi] = 0
+                sm.m[zero_lo:zero_hi] = 0
                 acc = np.zeros((BD, T), np.int64)
                 goff_buf = {}
                 for s in range(tb["n_stages"]):
                     c0 = s * CC
                     ncc = min(CC, n_chan - c0)
                     ngs = (ncc + G - 1) // G
-                    for cc in range(ncc):          # raw staging
+                    for cc in range(ncc):          # raw staging (the TMA box of stage s)
                         c = c0 + cc
                         start = t0 + tb["base"][blk, c]
-                        idx = start + np.arange(4 * Lw + 4)
+                        assert start % 16 == 0                     # TMA x coordinate on a 16-byte boundary
+                        idx = start + np.arange(4 * Lw)
                         row = x[sb_map[sb, c], c]
-                        byts = np.where(idx < n_valid, row[np.minimum(idx, row.size - 1)], 0).astype(np.uint32)
-                        for q in range(4):
-                            w = byts[q:q + 4 * Lw].reshape(Lw, 4)
-                            words = (w << (8 * np.arange(4, dtype=np.uint32))).sum(-1)
-                            sm.wr32(raw_lo + cc * 16 * Lw + q * 4 * Lw + 4 * np.arange(Lw), words, raw_lo, raw_hi)
+                        byts = np.where(idx < 4 * words_valid, row[np.minimum(idx, row.size - 1)], 0)
+                        byts = np.where((idx >= n_valid) & (idx < 4 * words_valid), 0xE7, byts)  # pitch padding
+                        slot = raw_lo + ((s % 2) * CC + cc) * rb
+                        sm.m[slot:slot + 4 * Lw] = byts.astype(np.uint8)
                     goff_buf[s % 2] = tb["goff"][blk, s * gps:s * gps + ngs]
                     first, n_desc = tb["pd_idx"][blk, s]
                     sm.m[pat_lo:pat_hi] = 0xAB       # stale pattern bytes from an earlier stage
@@ -95,9 +117,11 @@ def emulate(x, n_valid, sb_map, tb, v, CC, n_dm, n_out):
                         ev = np.zeros(nw4, np.uint32)
                         od = np.zeros(nw4, np.uint32)
                         for k in range(G):
-                            lo = 0 if src[k] < zero_hi else raw_lo
-                            hi = zero_hi if src[k] < zero_hi else raw_hi
-                            xw = sm.rd32(src[k] + 4 * j, lo, hi)
+                            lo, hi = slot_of(int(src[k]))
+                            if src[k] >= zero_hi:                  # this stage's raw buffer
+                                assert (int(src[k]) - raw_lo) // (CC * rb) == s % 2
+                            al = (int(src[k]) & ~3) + 4 * j
+                            xw = funnel_r(sm.rd32(al, lo, hi), sm.rd32(al + 4, lo, hi), 8 * int(src[k]))
                             ev = (ev + prmt(xw, 0, 0x4240)).astype(np.uint32)
                             od = (od + prmt(xw, 0, 0x4341)).astype(np.uint32)
                         A = prmt(ev, od, 0x5410)

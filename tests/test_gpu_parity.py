@@ -153,6 +153,7 @@ def test_arts_single_sb_full_size(fdd):
     x, f, ranges, n_in, n_out, prm = arts_single_sb()
     plan, gpu, gs, ora, os_ = run_both(fdd, x, np.zeros((1, 1536), np.int16), f, ranges, 8.0, n_out, n_in)
     assert (gs[0] == os_[0]).all()
+    assert plan.status() == 0                     # no raw-row (TMA) wait gave up
     n = compare_candidates(gpu, ora, 8.0)
     assert n > 0
     # recall: every injected pulse is found near its DM and time
@@ -305,6 +306,7 @@ def test_every_kernel_variant(fdd, variant_oracle, v, cc):
     assert cfg["variant"] == v["index"] and (cc == 0 or cfg["chan_per_stage"] == cc)
     res = plan.search(to_dev(x), n_in, n_out, want_series=True, cap=1 << 18)
     torch.cuda.synchronize()
+    assert plan.status() == 0                     # no TMA tile wait gave up
     ora, os_ = variant_oracle
     g = plan.series_views(res.series, n_out)
     assert (g[r].cpu().numpy() == os_[r]).all()
