@@ -285,9 +285,11 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
         if (next) small_load(s + 1);
         const bool ok = tma::mbar_wait_bounded(s_bar + 8u * buf, static_cast<uint32_t>(s >> 1) & 1u);
         if (ok) {
-            for (int d = 2 * warp; d < n_desc; d += 2 * WARPS)
-                build_rows<G>(s_desc32 + 4u * DI * d, d + 1 < n_desc ? s_desc32 + 4u * DI * (d + 1) : 0xffffffffu, s0,
-                              lane);
+            // rows d and d + WARPS together (two build chains per lane); warp w builds
+            // rows w, w + WARPS, w + 2 WARPS, ... so the counts differ by at most one
+            for (int d = warp; d < n_desc; d += 2 * WARPS)
+                build_rows<G>(s_desc32 + 4u * DI * d,
+                              d + WARPS < n_desc ? s_desc32 + 4u * DI * (d + WARPS) : 0xffffffffu, s0, lane);
         }
         // pattern rows complete; raw buffer buf and the descriptors free
         if (__syncthreads_or(!ok)) {
