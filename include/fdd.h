@@ -493,6 +493,14 @@ int fdd_plan_get_subband(const fdd_plan* plan, int32_t r, int32_t* chan_per_subb
 #define FDD_STATUS_TILE_WAIT 1
 int fdd_plan_status(fdd_plan* plan, int32_t* status, int32_t clear);
 
+/* Self-test of the bounded wait that every TMA-staged kernel uses for its
+ * tile copies (the paper has no counterpart): one block waits on an
+ * mbarrier that nothing arrives on, giving up after `polls` polls (1 ..
+ * 2^22; each poll after the 64th sleeps ~256 ns).  *gave_up = 1 when the
+ * wait ended by its limit and the kernel returned normally, which is the
+ * expected outcome.  Blocking; uses the current device. */
+int fdd_selftest_bounded_wait(int32_t polls, int32_t* gave_up);
+
 /* Number of kernels the last fdd_search or fdd_search_batch on this plan
  * enqueued (graph launches replay the last captured batch's kernels). */
 int fdd_plan_last_launches(const fdd_plan* plan, int64_t* n);

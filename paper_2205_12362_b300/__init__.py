@@ -167,6 +167,7 @@ def _lib_raw():
     L.fdd_plan_set_scratch_limit.argtypes = [_P, _I64]
     L.fdd_plan_last_launches.argtypes = [_P, ctypes.POINTER(_I64)]
     L.fdd_plan_status.argtypes = [_P, ctypes.POINTER(_I32), _I32]
+    L.fdd_selftest_bounded_wait.argtypes = [_I32, ctypes.POINTER(_I32)]
     L.fdd_plan_set_subband.argtypes = [_P, _I32, _I32, _I32]
     L.fdd_rfi_workspace_size.argtypes = [_I32, _I32, _I64, ctypes.POINTER(_SZ)]
     L.fdd_rfi_clean.argtypes = [ctypes.POINTER(_RfiDesc), _P, _I32, _I32, _I64, _I64, _P, _SZ, _P, _P, _P]
@@ -444,6 +445,15 @@ class Stream:
             self.close()
         except Exception:
             pass
+
+
+def selftest_bounded_wait(polls=4096):
+    """Run the bounded-wait self-test (include/fdd.h: fdd_selftest_bounded_wait):
+    True when a wait on an mbarrier that nothing arrives on gave up after
+    `polls` polls and its kernel returned normally."""
+    g = _I32()
+    _check(_lib_raw().fdd_selftest_bounded_wait(int(polls), ctypes.byref(g)), "fdd_selftest_bounded_wait")
+    return bool(g.value)
 
 
 def cluster_workspace_size(cap_in):

@@ -34,9 +34,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0u;
 }
-// Wait for phase `parity` of the barrier to complete; false if kSpinLimit polls pass first.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-    for (int it = 0; it < kSpinLimit; it++) {
+// Wait for phase `parity` of the barrier to complete; false if `limit` polls pass first.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int limit = kSpinLimit) {
+    for (int it = 0; it < limit; it++) {
         if (mbar_try_wait(bar, parity)) return true;
         if (it >= 64) __nanosleep(256);
     }
