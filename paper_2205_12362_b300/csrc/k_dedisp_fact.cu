@@ -203,9 +203,26 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
     __syncthreads();
 
     // Raw rows of stage s into buffer s & 1 (warp 0): Lw words per channel
-    // (fact_boxes(Lw) boxes), from word (t0 + base) / 4 of row (TAB, c);
-    // lane 0 first arms the buffer's barrier with the stage's byte count.
-    auto issue = [&](int s) {
+    // (fact_boxes(Lw) boxes), from word (t0 + base) / 4 of row (TAB, c).
+    // coords(s) loads each lane's channels' coordinates (channel lane and
+    // lane + 32; CC <= 64) a stage before fire(s) needs them, so the global
+    // loads' latency is not in front of a barrier; fire(s) arms the buffer's
+    // barrier with the stage's byte count (lane 0) and issues the copies.
+    int cx[2] = {0, 0}, cy[2] = {0, 0};
+    auto coords = [&](int s) {
+        const int c0 = s * CC;
+        const int ncc = min(CC, a.n_chan - c0);
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            const int cc = lane + 32 * q;
+            if (cc < ncc) {
+                const int c = c0 + cc;
+                cx[q] = (t0 + base_blk[c]) >> 2;
+                cy[q] = sbm[c] * a.n_chan + c;
+            }
+        }
+    };
+    auto fire = [&](int s) {
         const int c0 = s * CC;
         const int ncc = min(CC, a.n_chan - c0);
         const uint32_t bar = s_bar + 8u * (s & 1);
@@ -213,11 +230,13 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
         __syncwarp();
         const uint32_t dst = s0 + static_cast<uint32_t>(a.raw_off + (s & 1) * CC * a.rb);
         const int nb = fact_boxes(Lw), bw = Lw / nb;
-        for (int cc = lane; cc < ncc; cc += 32) {
-            const int c = c0 + cc;
-            const int x = (t0 + base_blk[c]) >> 2, y = sbm[c] * a.n_chan + c;
-            for (int k = 0; k < nb; k++)
-                tma::load_2d(dst + static_cast<uint32_t>(cc * a.rb + 4 * k * bw), &a.tmap, x + k * bw, y, bar);
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            const int cc = lane + 32 * q;
+            if (cc < ncc)
+                for (int k = 0; k < nb; k++)
+                    tma::load_2d(dst + static_cast<uint32_t>(cc * a.rb + 4 * k * bw), &a.tmap, cx[q] + k * bw, cy[q],
+                                 bar);
         }
     };
 
@@ -268,8 +287,13 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
 
     const uint32_t s_lane = s0 + 4u * lane;
     if (warp == 0) {
-        issue(0);
-        if (a.n_stages > 1) issue(1);
+        coords(0);
+        fire(0);
+        if (a.n_stages > 1) {
+            coords(1);
+            fire(1);
+        }
+        if (a.n_stages > 2) coords(2);
     }
     small_load(0);
     small_store(0, 0);
@@ -301,7 +325,10 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
             }
             return;
         }
-        if (warp == 0 && s + 2 < a.n_stages) issue(s + 2);  // into buffer buf, behind two stages of work
+        if (warp == 0 && s + 2 < a.n_stages) {
+            fire(s + 2);                                    // into buffer buf, behind two stages of work
+            if (s + 3 < a.n_stages) coords(s + 3);
+        }
         if (next) small_store(s + 1, buf ^ 1);
         if (since_fold + ncc > 256) {
             fold();
@@ -408,7 +435,7 @@ int num_fact_variants() { return static_cast<int>(sizeof(kFEntries) / sizeof(kFE
 const FactVariant& fact_variant(int idx) { return kFEntries[idx].v; }
 
 bool fact_cc_ok(const FactVariant& v, int Lw, int CC, int max_desc) {
-    if (CC < v.G || CC % v.G != 0 || CC > 256) return false;
+    if (CC < v.G || CC % v.G != 0 || CC > 64) return false;  // two channels per lane of the copy-issuing warp
     if (Lw < 4 || Lw > kFactMaxLw || Lw % fact_lw_align(Lw) != 0) return false;  // whole, aligned boxes
     if (max_desc * (v.desc_ints() / 4) > v.threads()) return false;
     if ((CC / v.G) * (v.bd() / 4) > v.threads()) return false;
