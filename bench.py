@@ -458,6 +458,13 @@ def run_fdd(args):
     else:
         kname = kind_names[kinds[cfgs[0]["variant"]]] if cfgs else "k_dedisp"
     ratio = float(np.mean([c["work_ratio"] for c in cfgs])) if cfgs else 1.0
+    if args.subband:
+        # approximate two-step mode: step 1 (k_sbf_part over each coarse DM's subbands) + step 2
+        # (k_dedisp over the subband rows); adds per (trial, sample) against the exact method's n_chan
+        sg, sk = (int(v) for v in args.subband.split(","))
+        kname = "k_sbf_part+k_dedisp (two-step subband, approximate)"
+        n_chan = w["n_chan"]
+        ratio = (n_chan / sk + -(-n_chan // sg)) / n_chan
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s",
             "frac": (achieved / peak) if achieved else None, "traffic": profile_traffic(kname, args.workload),
             "kernel": kname, "units_per_launch": adds_launch,
@@ -465,7 +472,10 @@ def run_fdd(args):
             "method_note": "achieved counts brute-force channel-adds; the configured kernel performs "
                            "method_adds_per_launch integer adds (the pattern-factored kernel reuses partial sums "
                            "across DM trials, the SB-factored kernels (k_sbf_part + k_sbf_comb) reuse TAB x "
-                           "segment partial sums across SBs)",
+                           "segment partial sums across SBs" + (
+                               "; the two-step subband mode is approximate: it does not compute the exact "
+                               "sums, so its brute-force-equivalent rate is not comparable" if args.subband
+                               else "") + ")",
             "peak_basis": "148 SM x 128 INT32 lanes x 2 adds/IADD3 x 2032 MHz (derived; no measured INT peak)",
             "peak_at_sampled_clock": (peak * sm_mhz / SM_MAX_MHZ_NOMINAL) if sm_mhz else None,
             "avg_launch_ms": ded_ms}
