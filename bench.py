@@ -306,10 +306,11 @@ def run_fdd(args):
         for p_ in plans:
             p_.set_timing(True)
 
-        def step(src=None):
+        def step(src=None, out=None):
+            c_, n_ = (cands, count) if out is None else out
             for p_ in plans:
-                p_.search(tabs if src is None else src, n_in, w["n_out"], cap=cap, workspace=ws, cands=cands,
-                          count=count, stream=stream)
+                p_.search(tabs if src is None else src, n_in, w["n_out"], cap=cap, workspace=ws, cands=c_,
+                          count=n_, stream=stream)
     else:
         job = plan.make_job(tabs, n_in, w["n_out"], cap=cap)
         cands, count = job.cands, job.count
@@ -387,15 +388,19 @@ def run_fdd(args):
 
     # end-to-end through the public API with host buffers: every step copies its
     # chunk host-to-device from pinned memory and reads its count and candidate
-    # records back.  Per-range modes double-buffer the input so the copy of step
-    # k+1 (copy stream) overlaps the search of step k, as a pipelined caller
-    # would; batched/graph modes search a fixed job buffer, copied in turn.
+    # records back.  Per-range modes double-buffer the input and the outputs, as a
+    # pipelined caller would: the copy of step k+1 (copy stream) overlaps the search
+    # of step k, and step k-1's results are read back (their own stream) while step
+    # k runs; batched/graph modes search a fixed job buffer, copied in turn.
     e2e_units, h2d, d2h = 0, 0, 0
-    cnt_host = torch.zeros(1, dtype=torch.int64).pin_memory()
     e2e_steps = max(1, min(args.steps, 200))
     pipelined = mode in ("plain", "per_sb")
     bufs = [tabs, torch.empty_like(tabs)] if pipelined else [tabs]
+    outs = [(cands, count), (torch.empty_like(cands), torch.zeros_like(count))] if pipelined else [(cands, count)]
+    cnt_host = [torch.zeros(1, dtype=torch.int64).pin_memory() for _ in outs]
+    cnt_ev = [torch.cuda.Event() for _ in outs]
     copy_stream = torch.cuda.Stream(device=dev)
+    d2h_stream = torch.cuda.Stream(device=dev)
     ready = [torch.cuda.Event() for _ in bufs]
     done = [torch.cuda.Event() for _ in bufs]
     torch.cuda.synchronize()
@@ -409,26 +414,41 @@ def run_fdd(args):
             bufs[b].copy_(host, non_blocking=True)
             ready[b].record(copy_stream)
 
+    def read_back(b):
+        """Host copy of the count and candidates of the step that wrote outs[b]."""
+        cnt_ev[b].synchronize()
+        n = min(int(cnt_host[b].item()), cap)
+        with torch.cuda.stream(d2h_stream):
+            d2h_stream.wait_event(done[b])
+            got = outs[b][0][:n].to("cpu")            # waits for this copy only
+        return 8 + got.numel() * 4
+
     issue_copy(0)
+    pending = None
     for k in range(e2e_steps):
         b = k % len(bufs)
         if pipelined and k + 1 < e2e_steps:
             issue_copy(k + 1)
         stream.wait_event(ready[b])
         if pipelined:
-            step(bufs[b])
+            step(bufs[b], outs[b])
         else:
             step()
         done[b].record(stream)
-        cnt_host.copy_(count, non_blocking=True)
-        stream.synchronize()
-        n = min(int(cnt_host.item()), cap)
-        got = cands[:n].cpu()
-        if not pipelined and k + 1 < e2e_steps:
-            issue_copy(k + 1)
+        cnt_host[b].copy_(outs[b][1], non_blocking=True)
+        cnt_ev[b].record(stream)
+        if pipelined:
+            if pending is not None:
+                d2h += read_back(pending)              # step k-1, while step k runs
+            pending = b
+        else:
+            d2h += read_back(b)
+            if k + 1 < e2e_steps:
+                issue_copy(k + 1)
         h2d += host.numel()
-        d2h += 8 + got.numel() * 4
         e2e_units += units_per_step(w)
+    if pending is not None:
+        d2h += read_back(pending)
     torch.cuda.synchronize()
     te1 = time.perf_counter()
     e2e_s = reduce_max(te1 - te0, dist, dev)
