@@ -424,7 +424,7 @@ const FEntry kFEntries[] = {
     FDD_F(8, 2, 8, 8),   // G 8, BD 64, T 128, 256 threads
     FDD_F(4, 4, 8, 8),   // G 4, BD 64, T 256, 256 threads
     FDD_F(4, 4, 2, 32),  // G 4, BD 64, T 256, 1024 threads (32 warps for latency hiding)
-    FDD_F(4, 4, 1, 32),  // G 4, BD 32, T 256, 1024 threads
+    FDD_F(4, 3, 4, 16),  // G 4, BD 64, T 192: pattern rows of ~53 units fill 2 warp steps (83 % of lanes)
 };
 #undef FDD_F
 
