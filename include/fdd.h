@@ -49,7 +49,8 @@ enum {
     FDD_ERR_CUDA = -6,         /* CUDA runtime error; see fdd_last_error_message() */
     FDD_ERR_WORKSPACE = -7,    /* workspace smaller than fdd_workspace_size() */
     FDD_ERR_SEQUENCE = -8,     /* serving: chunk out of sequence (dropped/late/duplicate/reordered) */
-    FDD_ERR_BUSY = -9          /* serving: beam backlogged, retry after fdd_server_poll */
+    FDD_ERR_BUSY = -9,         /* serving: beam backlogged, retry after fdd_server_poll */
+    FDD_ERR_TIMEOUT = -10      /* a kernel's bounded wait for a tile copy gave up (fdd_plan_status) */
 };
 
 #define FDD_MAX_WIDTHS 16      /* boxcar widths per DM range */
@@ -489,7 +490,9 @@ int fdd_plan_get_subband(const fdd_plan* plan, int32_t r, int32_t* chan_per_subb
  * (FDD_STATUS_TILE_WAIT): a kernel's wait for an asynchronous tile copy
  * gave up after its poll limit (about a second); that block stopped without
  * writing its series, so the affected search's output is incomplete.  0 in
- * normal operation. */
+ * normal operation.  Returns FDD_ERR_TIMEOUT (with *status filled) when the
+ * word is not 0, FDD_OK when it is: this is how device-side wait failures
+ * reach a caller that checks return codes, since searches are asynchronous. */
 #define FDD_STATUS_TILE_WAIT 1
 int fdd_plan_status(fdd_plan* plan, int32_t* status, int32_t clear);
 

@@ -311,6 +311,7 @@ class Graph:
 FDD_ERR_SEQUENCE = -8
 FDD_BATCH_SB_FACTORED = 1000
 FDD_STATUS_TILE_WAIT = 1
+FDD_ERR_TIMEOUT = -10
 FDD_ERR_BUSY = -9
 
 
@@ -643,7 +644,9 @@ class Plan:
         """Device status word (include/fdd.h: fdd_plan_status; bit 0 =
         FDD_STATUS_TILE_WAIT, a tile-copy wait that gave up).  Blocking."""
         v = _I32()
-        _check(_lib_raw().fdd_plan_status(self._h, ctypes.byref(v), 1 if clear else 0), "fdd_plan_status")
+        rc = _lib_raw().fdd_plan_status(self._h, ctypes.byref(v), 1 if clear else 0)
+        if rc != FDD_ERR_TIMEOUT:          # FDD_ERR_TIMEOUT only says the word is set: return it
+            _check(rc, "fdd_plan_status")
         return int(v.value)
 
     def set_scratch_limit(self, nbytes):

@@ -471,6 +471,7 @@ const char* fdd_error_string(int code) {
         case FDD_ERR_WORKSPACE: return "workspace too small";
         case FDD_ERR_SEQUENCE: return "chunk out of sequence";
         case FDD_ERR_BUSY: return "beam backlogged";
+        case FDD_ERR_TIMEOUT: return "device wait for a tile copy gave up";
         default: return "unknown error";
     }
 }
@@ -541,7 +542,7 @@ int fdd_plan_status(fdd_plan* plan, int32_t* status, int32_t clear) {
     if (clear && w && (e = cudaMemset(plan->d_status, 0, sizeof(w))) != cudaSuccess)
         return cuda_fail(e, "cudaMemset(status word)");
     *status = static_cast<int32_t>(w);
-    return FDD_OK;
+    return w ? fail(FDD_ERR_TIMEOUT, "a kernel's bounded wait for a tile copy gave up (status word set)") : FDD_OK;
 }
 
 int fdd_plan_max_delay(const fdd_plan* plan, int64_t* max_delay_native) {
