@@ -505,6 +505,16 @@ def run_fdd(args):
         rate, cores, desc, secs, _ = oracle_sample_rate(x, sb, f, t, w, n_in, args.cpu_seconds)
         cpu = {"value": rate, "unit": "samples/s", "cores": cores, "kind": "oracle", "sample": desc,
                "seconds": secs}
+        if w["n_sb"] == 1:
+            # the same oracle on one host thread, on a smaller sample of the same workload
+            import oracle
+            oracle.set_threads(1)
+            try:
+                rate1, _, desc1, secs1, _ = oracle_sample_rate(x, sb, f, t, w, n_in, max(1.0, args.cpu_seconds / 4))
+            finally:
+                oracle.set_threads(cores)
+            cpu["single_thread"] = {"value": rate1, "unit": "samples/s", "cores": 1, "sample": desc1,
+                                    "seconds": secs1}
 
     line = {
         "metric": "DM-trial samples/s (beams x DMs x samples)",
