@@ -54,7 +54,9 @@ enum {
 };
 
 #define FDD_MAX_WIDTHS 16      /* boxcar widths per DM range */
-#define FDD_MAX_WIDTH 1024     /* largest boxcar width, in range samples */
+#define FDD_MAX_WIDTH 1024     /* largest boxcar width, in range samples; also, per range,
+                                  n_chan * 255 * downsamp * widest width must stay below 2^31 (the
+                                  box sums are exact 32-bit differences), else FDD_ERR_UNSUPPORTED */
 #define FDD_MAX_CHANNELS 16384
 #define FDD_MAX_TABS 256
 #define FDD_MAX_RANGES 8       /* DM ranges per plan in batched searches */

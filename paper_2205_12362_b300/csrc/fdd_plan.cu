@@ -418,6 +418,12 @@ static int build_host_plan(const fdd_plan_desc* desc, const int16_t* sb_map_host
             r.widths[k] = in.widths[k];
             r.wmax = std::max(r.wmax, in.widths[k]);
         }
+        // Box sums are formed as differences of wrapping 32-bit prefix sums of
+        // the series centred on round(mean): exact while |B_w - w round(mean)|
+        // < 2^31, which holds for every input when n_chan * 255 * D * w_max does.
+        if (static_cast<int64_t>(desc->n_chan) * 255 * in.downsamp * r.wmax > (1LL << 31) - 1)
+            return fail(FDD_ERR_UNSUPPORTED,
+                        "n_chan * 255 * downsamp * widest boxcar >= 2^31: box sums could leave int32");
         r.dm_index0 = dm_index;
         dm_index += in.n_dm;
         // Delay table: cold-plasma law, FP64, same operation order for every

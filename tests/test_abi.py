@@ -56,6 +56,10 @@ def test_host_rejects_bad_plans(lib):
         fdd.Plan(1, 8, 1, f, 81.92e-6, [dict(dm0=0.0, ddm=-1.0, n_dm=4, widths=[1])], 8.0, np.zeros((1, 8)))
     with pytest.raises(fdd.FddError):        # width beyond the limit
         fdd.Plan(1, 8, 1, f, 81.92e-6, [dict(dm0=0.0, ddm=1.0, n_dm=4, widths=[5000])], 8.0, np.zeros((1, 8)))
+    with pytest.raises(fdd.FddError) as e:   # box sums that could leave int32 (16384 ch x 255 x D 257 x w 1024)
+        fdd.Plan(1, 16384, 1, np.linspace(1220, 1520, 16384), 81.92e-6,
+                 [dict(dm0=0.0, ddm=1.0, n_dm=1, downsamp=257, widths=[1024])], 8.0, np.zeros((1, 16384)))
+    assert e.value.code == -5
     with pytest.raises(fdd.FddError):        # non-positive frequency
         fdd.Plan(1, 8, 1, np.zeros(8), 81.92e-6, good, 8.0, np.zeros((1, 8)))
     with pytest.raises(ValueError):          # sb_map shape
