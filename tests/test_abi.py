@@ -42,6 +42,9 @@ def test_error_strings_and_version(lib):
     lib.fdd_version.restype = ctypes.c_char_p
     assert lib.fdd_error_string(0) == b"ok"
     assert b"short" in lib.fdd_error_string(-2).lower() or b"input" in lib.fdd_error_string(-2).lower()
+    assert b"gave up" in lib.fdd_error_string(-10)          # FDD_ERR_TIMEOUT
+    for code in range(-10, 0):                                # every code has its own text
+        assert lib.fdd_error_string(code) != b"unknown error"
     assert b"sm_103a" in lib.fdd_version()
 
 
