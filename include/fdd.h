@@ -116,40 +116,49 @@ typedef struct fdd_plan fdd_plan;
  * Errors: INVALID_ARG, UNSUPPORTED, NO_MEMORY, CUDA. */
 int fdd_plan_create(const fdd_plan_desc* desc, const int16_t* sb_map_host, fdd_plan** out);
 
-/* Free the plan and its device tables.  NULL is accepted.  The caller makes
+/* Free the plan and its device tables (library bookkeeping; no counterpart in
+ * the paper).  NULL is accepted.  The caller makes
  * sure no enqueued search still uses it. */
 int fdd_plan_destroy(fdd_plan* plan);
 
-/* Largest delay over all ranges, in native samples (max_r D_r * max d_r):
+/* Largest delay over all ranges, in native samples (max_r D_r * max d_r; the
+ * overlap each chunk needs, Sec. "Dedispersion"):
  * a search of n_out output samples needs n_in >= n_out + max_delay_native
  * input samples per channel. */
 int fdd_plan_max_delay(const fdd_plan* plan, int64_t* max_delay_native);
 
-/* Plan summary for a search of n_out native output samples: the largest
+/* Plan summary (library bookkeeping) for a search of n_out native output
+ * samples: the largest
  * delay (as fdd_plan_max_delay) and the workspace bytes of a search with
  * n_in = n_out + max_delay_native whose series stay in the workspace (as
  * fdd_workspace_size(plan, n_in, n_out, 1, ...)). */
 int fdd_plan_info(const fdd_plan* plan, int64_t n_out, int64_t* max_delay_native, int64_t* workspace_bytes);
 
-/* Number of DM trials summed over all ranges (the length of the global
+/* Number of DM trials summed over all ranges (the DM plan of Table
+ * "dedispersion setup"; the length of the global
  * dm_index axis). */
 int fdd_plan_total_dms(const fdd_plan* plan, int64_t* n_dm_total);
 
-/* Copy range r's integer delay table (int32 [n_dm][n_chan], units of D_r
+/* Copy range r's integer delay table (Sec. "Dedispersion"; int32
+ * [n_dm][n_chan], units of D_r
  * native samples) to host memory dst (n_dm * n_chan entries). */
 int fdd_plan_delays(const fdd_plan* plan, int32_t r, int32_t* dst);
 
-/* Bytes of device workspace a search of (n_in, n_out) needs.
+/* Bytes of device workspace a search of (n_in, n_out) needs (library
+ * bookkeeping; no counterpart in the paper).
  * If the caller passes d_series to fdd_search, the series live there and the
  * workspace shrinks by fdd_series_size(). */
 int fdd_workspace_size(const fdd_plan* plan, int64_t n_in, int64_t n_out, int32_t with_series,
                        size_t* bytes);
 
-/* Bytes of the dedispersed-series buffer: int32, packed per range as
+/* Bytes of the dedispersed-series buffer (the dedispersed time series of
+ * Sec. "Dedispersion"): int32, packed per range as
  * [range][sb][dm][floor(n_out / D_r)]. */
 int fdd_series_size(const fdd_plan* plan, int64_t n_out, size_t* bytes);
 
-/* Search one chunk of every SB of the plan.
+/* Search one chunk of every SB of the plan: the per-chunk AMBER search of
+ * Sec. "AMBER" ("Downsampling", "Dedispersion", "Integration", "S/N
+ * evaluation", "Candidate selection").
  *   d_tabs        device uint8 [n_tab][n_chan][pitch]: TAB filterbanks; the
  *                 first n_in samples of each row are data.  16-byte aligned.
  *   pitch         row pitch in samples (bytes), multiple of 16, >= n_in.
@@ -303,7 +312,8 @@ int fdd_batch_autotune(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int6
 int fdd_batch_config(const fdd_plan* plan, int32_t* variant, int32_t* grid, int32_t* threads,
                      int32_t* dm_per_block, float* tuned_ms);
 
-/* A CUDA graph of fdd_search_batch for fixed jobs: create captures and
+/* A CUDA graph of fdd_search_batch for fixed jobs (no counterpart in the
+ * paper; launch-overhead removal for the batched search): create captures and
  * instantiates it; launch replays it on a stream; update re-captures for new
  * job buffers/offsets (same n_jobs) and updates the executable graph in
  * place; destroy frees it.  The plan must outlive the graph.  Graphs carry
@@ -359,7 +369,8 @@ typedef struct {
     int64_t ring_bytes_per_beam, slot_bytes;
 } fdd_server_stats;
 
-/* Monotonic clock (seconds) used for all server timestamps. */
+/* Monotonic clock (seconds) used for all server timestamps (no counterpart in
+ * the paper). */
 double fdd_now(void);
 
 /* Create a server.  Allocates every beam's buffers, then slots from free HBM
@@ -437,7 +448,8 @@ int fdd_stream_results(fdd_stream* st, fdd_candidate* d_cands, int64_t cap, uint
 /* Wait for the stream's last push, free everything it owns.  NULL accepted. */
 int fdd_stream_close(fdd_stream* st);
 
-/* Host helper: sort n host candidate records in place by (sb, dm_index,
+/* Host helper (no counterpart in the paper; the records are those of
+ * Sec. "DARC"): sort n host candidate records in place by (sb, dm_index,
  * width_native, t_native), the order used to compare candidate sets (the
  * search itself emits them in no particular order). */
 int fdd_sort_candidates(fdd_candidate* cands, int64_t n);
@@ -487,7 +499,8 @@ int fdd_cluster(const fdd_candidate* d_in, const uint64_t* d_in_count, int64_t c
 int fdd_plan_set_subband(fdd_plan* plan, int32_t r, int32_t chan_per_subband, int32_t dm_per_coarse);
 int fdd_plan_get_subband(const fdd_plan* plan, int32_t r, int32_t* chan_per_subband, int32_t* dm_per_coarse);
 
-/* Device status word of the plan, read with a blocking copy after the
+/* (No counterpart in the paper: failure reporting of the device-side waits.)
+ * Device status word of the plan, read with a blocking copy after the
  * searches it covers have been synchronised (clear != 0 resets it).  Bit 0
  * (FDD_STATUS_TILE_WAIT): a kernel's wait for an asynchronous tile copy
  * gave up after its poll limit (about a second); that block stopped without
@@ -506,11 +519,13 @@ int fdd_plan_status(fdd_plan* plan, int32_t* status, int32_t clear);
  * expected outcome.  Blocking; uses the current device. */
 int fdd_selftest_bounded_wait(int32_t polls, int32_t* gave_up);
 
-/* Number of kernels the last fdd_search or fdd_search_batch on this plan
+/* (Tracing; no counterpart in the paper.)  Number of kernels the last
+ * fdd_search or fdd_search_batch on this plan
  * enqueued (graph launches replay the last captured batch's kernels). */
 int fdd_plan_last_launches(const fdd_plan* plan, int64_t* n);
 
-/* Cap (bytes) on the scratch the SB-factored kernel keeps in the search
+/* (No counterpart in the paper: a memory knob of the SB-factored kernels.)
+ * Cap (bytes) on the scratch the SB-factored kernel keeps in the search
  * workspace for its partial sums (0 = default, 4 GiB).  The partials of a
  * slab of DM trials must fit: a smaller cap means smaller slabs and more
  * launches, never a different result; at least one DM block's worth is
@@ -613,13 +628,14 @@ int fdd_rfi_clean(const fdd_rfi_desc* desc, uint8_t* d_tabs, int32_t n_tab, int3
                   int64_t pitch, void* d_workspace, size_t workspace_bytes, uint8_t* d_time_flags,
                   uint8_t* d_chan_flags, fdd_stream_t stream);
 
-/* Human-readable text of an FDD_* code (static string). */
+/* Human-readable text of an FDD_* code (static string; no counterpart in the paper). */
 const char* fdd_error_string(int code);
 
-/* Text of the last CUDA error seen by this thread inside the library. */
+/* Text of the last CUDA error seen by this thread inside the library (no
+ * counterpart in the paper). */
 const char* fdd_last_error_message(void);
 
-/* Library version string. */
+/* Library version string (no counterpart in the paper). */
 const char* fdd_version(void);
 
 #ifdef __cplusplus
