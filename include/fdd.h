@@ -607,7 +607,10 @@ int fdd_sb_table(int32_t n_tab, int32_t n_sb, int32_t n_chan, const double* chan
  *     channels are filled with the unflagged channels' mean level, rounded
  *     half up.
  * mu = S1/n, var = S2/n - mu^2, sigma = sqrt(var) in FP64 from exact 64-bit
- * sums.  A threshold <= 0 disables that filter.  Run before fdd_search. */
+ * sums (the population standard deviation; equal to the exact
+ * sqrt((n S2 - S1^2)/n^2) to ~1e-11 relative, so a decision can differ from
+ * one taken with the exact numerator only for a value that sits on the
+ * threshold).  A threshold <= 0 disables that filter.  Run before fdd_search. */
 typedef struct {
     double time_thresh;   /* sigmas, zero-DM filter (e.g. 4); <= 0: off */
     int32_t time_iters;   /* 3 in ARTS */

@@ -52,6 +52,7 @@ def lib():
         L.oracle_cluster.argtypes = [_P, _I64, _P]
         L.oracle_rfi_clean.argtypes = [_P, _I32, _I32, _I64, _I64, _D, _I32, _D, _I32, _P, _P]
         L.oracle_cluster.restype = _I64
+        L.oracle_rfi_clean.restype = _I64
         _lib = L
     return _lib
 
@@ -263,15 +264,17 @@ def sb_table(n_tab, n_sb, freq_mhz, f_max_mhz, alpha, b_max_m, b_cq_m, chan_per_
     return out
 
 
-def rfi_clean(x, n_in=None, time_thresh=4.0, time_iters=3, freq_thresh=4.0, freq_iters=3):
+def rfi_clean(x, n_in=None, time_thresh=4.0, time_iters=3, freq_thresh=4.0, freq_iters=3, return_near=False):
     """RFI mitigation (oracle.c: oracle_rfi_clean) of a copy of x
     (uint8[n_tab][n_chan][pitch]).  Returns (cleaned copy, time flags
-    uint8[n_tab][n_in], channel flags uint8[n_tab][n_chan])."""
+    uint8[n_tab][n_in], channel flags uint8[n_tab][n_chan]), and with
+    return_near=True also the number of flag decisions whose two sides were
+    within 1e-9 (relative) of each other."""
     y = np.ascontiguousarray(x, dtype=np.uint8).copy()
     n_tab, n_chan, pitch = y.shape
     n_in = pitch if n_in is None else int(n_in)
     tf = np.zeros((n_tab, n_in), np.uint8)
     cf = np.zeros((n_tab, n_chan), np.uint8)
-    lib().oracle_rfi_clean(_ptr(y), n_tab, n_chan, n_in, pitch, float(time_thresh), int(time_iters),
-                           float(freq_thresh), int(freq_iters), _ptr(tf), _ptr(cf))
-    return y, tf, cf
+    near = lib().oracle_rfi_clean(_ptr(y), n_tab, n_chan, n_in, pitch, float(time_thresh), int(time_iters),
+                                  float(freq_thresh), int(freq_iters), _ptr(tf), _ptr(cf))
+    return (y, tf, cf, int(near)) if return_near else (y, tf, cf)

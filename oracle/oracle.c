@@ -449,31 +449,44 @@ int64_t oracle_cluster(const oracle_cand* in, int64_t n, oracle_cand* out) {
  *     |b[c] - mu| > thr_f*sigma (mu, sigma over unflagged channels; two-sided:
  *     hot or dead channels); flagged channels are filled with the mean level
  *     of the unflagged channels, sum b / (channels * n_in) rounded half up.
- * Moments are exact integers (S1, S2 < 2^64); mu = S1/n, var = S2/n - mu*mu,
- * sigma = sqrt(var) in FP64 in exactly this order (the flag decisions are
- * taken in that precision).  x is modified in place ([n_tab][n_chan][pitch],
+ * Moments are exact integers: S1 < 2^64 and S2 as a 128-bit sum;
+ * mu = S1/n and sigma = sqrt((n S2 - S1^2) / n^2), the population standard
+ * deviation from its exact integer numerator, formed in FP64 only after the
+ * numerator is complete.  Every flag decision compares lhs = z - mu (or
+ * |b - mu|) against rhs = thr*sigma; decisions with |lhs - rhs| <= 1e-9 |rhs|
+ * are counted in *near (the caller's report that a decision sat on the
+ * threshold, where another FP64 evaluation order of the same statistic could
+ * decide the other way).  x is modified in place ([n_tab][n_chan][pitch],
  * first n_in samples); tflags [n_tab][n_in] and cflags [n_tab][n_chan] get 1
  * for flagged samples / channels.  A threshold <= 0 disables its filter. */
 static void rfi_moments(const uint64_t* v, const uint8_t* flag, int64_t n, int64_t* cnt, double* mu, double* sigma) {
-    uint64_t s1 = 0, s2 = 0;
+    uint64_t s1 = 0;
+    unsigned __int128 s2 = 0;
     int64_t k = 0;
     for (int64_t j = 0; j < n; j++)
         if (!flag[j]) {
             s1 += v[j];
-            s2 += v[j] * v[j];
+            s2 += (unsigned __int128)v[j] * v[j];
             k++;
         }
     *cnt = k;
     if (k == 0) { *mu = 0; *sigma = 0; return; }
+    /* n S2 - S1^2 >= 0 exactly (Cauchy-Schwarz), so no clamp is needed */
+    const unsigned __int128 num = (unsigned __int128)k * s2 - (unsigned __int128)s1 * s1;
     *mu = (double)s1 / (double)k;
-    const double m2 = (double)s2 / (double)k;
-    const double var = m2 - *mu * *mu;
-    *sigma = var > 0 ? sqrt(var) : 0.0;
+    *sigma = sqrt((double)num / ((double)k * (double)k));
 }
 
-void oracle_rfi_clean(uint8_t* x, int32_t n_tab, int32_t n_chan, int64_t n_in, int64_t pitch,
-                      double time_thr, int32_t time_iters, double freq_thr, int32_t freq_iters,
-                      uint8_t* tflags, uint8_t* cflags) {
+/* lhs > rhs, counting near ties (|lhs - rhs| <= 1e-9 |rhs|) in *near */
+static int rfi_exceeds(double lhs, double rhs, int64_t* near) {
+    if (fabs(lhs - rhs) <= 1e-9 * fabs(rhs)) (*near)++;
+    return lhs > rhs;
+}
+
+int64_t oracle_rfi_clean(uint8_t* x, int32_t n_tab, int32_t n_chan, int64_t n_in, int64_t pitch,
+                         double time_thr, int32_t time_iters, double freq_thr, int32_t freq_iters,
+                         uint8_t* tflags, uint8_t* cflags) {
+    int64_t near = 0;
     uint64_t* z = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n_in > 0 ? n_in : 1));
     uint64_t* b = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)n_chan);
     for (int32_t tab = 0; tab < n_tab; tab++) {
@@ -494,7 +507,7 @@ void oracle_rfi_clean(uint8_t* x, int32_t n_tab, int32_t n_chan, int64_t n_in, i
                 rfi_moments(z, tf, n_in, &k, &mu, &sigma);
                 if (k == 0) break;
                 for (int64_t t = 0; t < n_in; t++)
-                    if (!tf[t] && (double)z[t] - mu > time_thr * sigma) tf[t] = 1;
+                    if (!tf[t] && rfi_exceeds((double)z[t] - mu, time_thr * sigma, &near)) tf[t] = 1;
             }
             int64_t n_ok = 0;
             for (int64_t t = 0; t < n_in; t++) n_ok += !tf[t];
@@ -521,7 +534,7 @@ void oracle_rfi_clean(uint8_t* x, int32_t n_tab, int32_t n_chan, int64_t n_in, i
                 rfi_moments(b, cf, n_chan, &k, &mu, &sigma);
                 if (k == 0) break;
                 for (int32_t c = 0; c < n_chan; c++)
-                    if (!cf[c] && fabs((double)b[c] - mu) > freq_thr * sigma) cf[c] = 1;
+                    if (!cf[c] && rfi_exceeds(fabs((double)b[c] - mu), freq_thr * sigma, &near)) cf[c] = 1;
             }
             uint64_t s = 0;
             int64_t n_ok = 0;
@@ -537,4 +550,5 @@ void oracle_rfi_clean(uint8_t* x, int32_t n_tab, int32_t n_chan, int64_t n_in, i
     }
     free(z);
     free(b);
+    return near;
 }

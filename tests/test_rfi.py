@@ -1,6 +1,9 @@
 """RFI mitigation on the GPU (fdd_rfi_clean) against the oracle's, exactly:
-cleaned samples, time flags and channel flags (both sides take every flag
-decision in the same FP64 operations)."""
+cleaned samples, time flags and channel flags.  The oracle takes sigma from
+the exact integer numerator n*S2 - S1^2; the kernel uses S2/n - mu^2 in FP64.
+The two agree except where a decision sits within ~1e-11 (relative) of the
+threshold; the oracle counts decisions within 1e-9 of it, and the inputs here
+have none, so every flag and sample must match."""
 import numpy as np
 import pytest
 
@@ -38,7 +41,9 @@ def test_rfi_matches_oracle(fdd, tt, ft):
     import torch
     n_tab, n_chan, n_in, pitch = 3, 200, 5001, 5024
     x = _rfi_input(7, n_tab, n_chan, n_in, pitch)
-    want, tf_o, cf_o = oracle.rfi_clean(x, n_in=n_in, time_thresh=tt, freq_thresh=ft)
+    want, tf_o, cf_o, near = oracle.rfi_clean(x, n_in=n_in, time_thresh=tt, freq_thresh=ft, return_near=True)
+    print("flag decisions within 1e-9 of the threshold: %d" % near)
+    assert near == 0
     d = torch.from_numpy(x).cuda()
     tf = torch.zeros((n_tab, n_in), dtype=torch.uint8, device="cuda")
     cf = torch.zeros((n_tab, n_chan), dtype=torch.uint8, device="cuda")
