@@ -559,17 +559,19 @@ int fdd_plan_stage_times(fdd_plan* plan, int32_t max_n, int32_t* kind, int32_t* 
  *   - The call makes no cudaMalloc/cudaFree and calls no allocating routine.
  *     Stage timing must be off on the plan (it creates CUDA events), else
  *     FDD_ERR_INVALID_ARG.
- *   - The first call on each device resolves the array's device address with
- *     cudaGetSymbolAddress, with that device current; make that first call
- *     before any stream capture.
+ *   - Every call resolves the array's device address with
+ *     cudaGetSymbolAddress on the current device.  The library's device code
+ *     is loaded per device on first use, so the FIRST call on a device loads
+ *     this array's module and commits the FDD_STATIC_SCRATCH_BYTES there (it
+ *     can fail for lack of memory); make that first call at initialisation,
+ *     before any stream capture.  Later calls allocate nothing.
  *   - Searches whose fdd_workspace_size(..., d_series == NULL) exceeds
  *     FDD_STATIC_SCRATCH_BYTES return FDD_ERR_WORKSPACE with a message.
  *   - All calls on a device share the one array, which keeps the previous
  *     call's contents (the call re-zeroes what must start at zero).  Calls
  *     whose GPU work overlaps (other streams, other host threads) race on it:
  *     serialise them.
- *   - Every GPU that loads the library's device code holds the array until
- *     the process exits. */
+ *   - Once committed on a device, the array stays until the process exits. */
 #define FDD_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
 int fdd_search_static(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitch, int64_t n_out,
                       int64_t t_offset_native, fdd_candidate* d_cands, int64_t cap, uint64_t* d_count,

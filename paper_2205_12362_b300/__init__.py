@@ -231,6 +231,23 @@ def _dev_ptr(t, name, dtype=None):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _check_outputs(plan, n_out, cands, count, series):
+    """Validate caller-given output buffers before their pointers reach the
+    library, which writes up to cands.shape[0] 32-byte records, one uint64
+    count and (with series) fdd_series_size(n_out) bytes through them."""
+    torch = _torch()
+    if not isinstance(cands, torch.Tensor) or cands.dtype != torch.int32 or cands.dim() != 2 or cands.shape[1] != 8:
+        raise TypeError("cands must be an int32 tensor of shape [cap, 8] (32-byte records)")
+    if not isinstance(count, torch.Tensor) or count.dtype != torch.int64 or count.numel() < 1:
+        raise TypeError("count must be an int64 tensor with at least one element")
+    if series is not None:
+        if not isinstance(series, torch.Tensor) or series.dtype != torch.int32:
+            raise TypeError("series must be an int32 tensor")
+        if series.numel() * 4 < plan.series_size(n_out):
+            raise ValueError("series holds %d bytes; this search writes %d" % (series.numel() * 4,
+                                                                              plan.series_size(n_out)))
+
+
 @dataclass
 class SearchResult:
     cands: "object"     # torch.int32 [cap, 8] raw 32-byte records on the device
@@ -712,9 +729,10 @@ class Plan:
             workspace = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
         if cands is None:
             cands = torch.empty((max(int(cap), 1), 8), dtype=torch.int32, device=dev)
-        cap = int(cands.shape[0])
         if count is None:
             count = torch.zeros(1, dtype=torch.int64, device=dev)
+        _check_outputs(self, n_out, cands, count, series)
+        cap = int(cands.shape[0])
         code = _lib_raw().fdd_search(
             self._h, _dev_ptr(tabs, "tabs", torch.uint8), int(n_in), pitch, int(n_out), int(t_offset),
             _dev_ptr(workspace, "workspace"), int(workspace.numel() * workspace.element_size()),
@@ -799,7 +817,7 @@ class Plan:
                                            ctypes.byref(bd), ctypes.byref(ms)), "fdd_batch_config")
         return dict(variant=v.value, grid=g.value, threads=t.value, dm_per_block=bd.value, tuned_ms=ms.value)
 
-    STATIC_SCRATCH_BYTES = 64 * 1024 * 1024
+    STATIC_SCRATCH_BYTES = 64 * 1024 * 1024   # FDD_STATIC_SCRATCH_BYTES of include/fdd.h (checked by the ABI test)
 
     def search_static(self, tabs, n_in, n_out, cands, count, t_offset=0, series=None, stream=None):
         """Allocation-free search (include/fdd.h: fdd_search_static): the
@@ -809,6 +827,7 @@ class Plan:
         torch = _torch()
         if tabs.dim() != 3 or tuple(tabs.shape[:2]) != (self.n_tab, self.n_chan):
             raise ValueError("tabs must be [n_tab][n_chan][pitch]")
+        _check_outputs(self, n_out, cands, count, series)
         code = _lib_raw().fdd_search_static(
             self._h, _dev_ptr(tabs, "tabs", torch.uint8), int(n_in), int(tabs.shape[2]), int(n_out),
             int(t_offset), _dev_ptr(cands, "cands"), int(cands.shape[0]), _dev_ptr(count, "count"),

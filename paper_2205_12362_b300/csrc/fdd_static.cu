@@ -7,22 +7,17 @@
 // to allocate only at initialisation.  Those callers still own the input,
 // candidate, counter and (optional) series buffers; only the workspace moves
 // into the library.
-#include <mutex>
 #include <string>
 
 #include "fdd_internal.cuh"
 
 namespace {
 
-// The scratch array.  Every GPU that loads this library's device code holds
-// FDD_STATIC_SCRATCH_BYTES of it until the process exits.
+// The scratch array.  The build links every .cu file as its own module and
+// CUDA loads modules lazily, so the array is committed on a device when this
+// file's module is first loaded there -- at the latest by the first
+// fdd_search_static call on that device -- and held until the process exits.
 __device__ __align__(256) uint8_t g_fdd_static_scratch[FDD_STATIC_SCRATCH_BYTES];
-
-constexpr int kMaxDevices = 128;
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};  // device address of the array, per device
-
-thread_local std::string g_static_error;
 
 }  // namespace
 
@@ -45,31 +40,16 @@ extern "C" int fdd_search_static(fdd_plan* plan, const uint8_t* d_tabs, int64_t 
                             " (pass d_series, shorten the chunk, or use fdd_search with a workspace)");
         return FDD_ERR_WORKSPACE;
     }
-    // One-time set-up per device, with that device current: resolve the
-    // array's device address (the host-side symbol is only a stand-in).
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        fdd::set_last_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-        return FDD_ERR_CUDA;
-    }
-    if (dev < 0 || dev >= kMaxDevices) {
-        fdd::set_last_error("fdd_search_static: device index beyond the supported range");
-        return FDD_ERR_UNSUPPORTED;
-    }
+    // Resolve the array's device address with the calling device current
+    // (the host-side symbol is only a stand-in).  It is resolved on every
+    // call rather than cached: after a context is torn down and re-created
+    // (cudaDeviceReset) the module is loaded afresh at another address.  The
+    // first call on a device loads the module, which commits the array.
     void* scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_scratch_addr[dev]) {
-            void* p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_fdd_static_scratch);
-            if (e != cudaSuccess) {
-                fdd::set_last_error(std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
-                return FDD_ERR_CUDA;
-            }
-            g_scratch_addr[dev] = p;
-        }
-        scratch = g_scratch_addr[dev];
+    cudaError_t e = cudaGetSymbolAddress(&scratch, g_fdd_static_scratch);
+    if (e != cudaSuccess) {
+        fdd::set_last_error(std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
+        return FDD_ERR_CUDA;
     }
     // fdd_search zeroes the parts of the workspace that must start at zero
     // (series moments) on `stream` before its kernels run.

@@ -106,3 +106,12 @@ def test_sort_candidates_host_helper():
         assert (got[k] == want[k]).all()
     assert sorted(got["snr"].tolist()) == sorted(want["snr"].tolist())
     m.sort_candidates(np.zeros(0, dtype=m.CAND_DTYPE))
+
+
+def test_static_scratch_size_matches_header():
+    """The binding's STATIC_SCRATCH_BYTES is the header's FDD_STATIC_SCRATCH_BYTES."""
+    import paper_2205_12362_b300 as fdd
+    text = open(os.path.join(ROOT, "include", "fdd.h")).read()
+    m = re.search(r"#define\s+FDD_STATIC_SCRATCH_BYTES\s+\((\d+)u\s*\*\s*(\d+)u\s*\*\s*(\d+)u\)", text)
+    assert m, "FDD_STATIC_SCRATCH_BYTES not found in include/fdd.h"
+    assert fdd.Plan.STATIC_SCRATCH_BYTES == int(m.group(1)) * int(m.group(2)) * int(m.group(3))

@@ -47,17 +47,29 @@ def test_static_search_matches_workspace_search():
     ref_c, ref_n = ref.candidates()
     assert ref_n > 0
     cap = 1 << 16
-    for call in range(2):
-        cands = torch.empty((cap, 8), dtype=torch.int32, device="cuda")
-        count = torch.zeros(1, dtype=torch.int64, device="cuda")
-        series = torch.full_like(ref.series, -1) if call == 1 else None
-        out = plan.search_static(dx, n_in, n_out, cands, count, series=series)
+    # every output buffer exists before the calls, so any drop in free device
+    # memory across a call is the library's
+    bufs = [(torch.empty((cap, 8), dtype=torch.int32, device="cuda"), torch.zeros(1, dtype=torch.int64, device="cuda"),
+             torch.full_like(ref.series, -1) if call == 1 else None) for call in range(2)]
+    torch.cuda.synchronize()
+    free = [torch.cuda.mem_get_info()[0]]
+    outs = []
+    for cands, count, series in bufs:
+        outs.append(plan.search_static(dx, n_in, n_out, cands, count, series=series))
         torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
+    for call, (out, (cands, count, series)) in enumerate(zip(outs, bufs)):
         got_c, got_n = out.candidates()
         assert got_n == ref_n, "call %d: %d candidates vs %d" % (call, got_n, ref_n)
         assert (got_c == ref_c).all(), "call %d: candidate records differ" % call
         if series is not None:
             assert torch.equal(series, ref.series), "call %d: series differ" % call
+    # the first call on the device may load the library module that holds the
+    # static array (committing it); the second allocates nothing
+    print("free device memory drop: first call %d bytes, second call %d bytes" % (free[0] - free[1],
+                                                                                    free[1] - free[2]))
+    assert free[0] - free[1] >= 0
+    assert free[2] == free[1], "the second call changed free device memory by %d bytes" % (free[1] - free[2])
 
 
 def test_static_search_rejects_oversized_and_timed_plans():
