@@ -379,6 +379,18 @@ double fdd_now(void);
 int fdd_server_create(fdd_plan* plan, const fdd_server_desc* desc, fdd_server** out);
 int fdd_server_destroy(fdd_server* server);
 
+/* Switch a new server (before its first push) to the plain per-SB path, the
+ * comparison point of the batched one: every window is searched by n_sb
+ * single-SB plans, one fdd_search each, one after another on one stream,
+ * one window per launch group (windows still overlap across the server's
+ * compute streams); plan k searches SB k (its records are relabelled sb = k,
+ * appended to the window's list, the true total counted).  sb_plans: n_sb =
+ * the server plan's SB count, each with n_sb = 1, the same TABs and channels
+ * and no larger max delay; they must outlive the server.  Errors:
+ * INVALID_ARG, WORKSPACE (a plan needs more workspace than a slot holds),
+ * CUDA. */
+int fdd_server_set_plain(fdd_server* server, fdd_plan* const* sb_plans, int32_t n_sb);
+
 /* Deliver chunk `seq` (0, 1, 2, ... per beam) of `beam`: host memory
  * uint8 [n_tab][n_chan][chunk_len] (pinned for asynchronous copies; it may be
  * reused once the call returns only if pageable).  FDD_ERR_SEQUENCE for a
@@ -632,6 +644,21 @@ int fdd_rfi_workspace_size(int32_t n_tab, int32_t n_chan, int64_t n_in, size_t* 
 int fdd_rfi_clean(const fdd_rfi_desc* desc, uint8_t* d_tabs, int32_t n_tab, int32_t n_chan, int64_t n_in,
                   int64_t pitch, void* d_workspace, size_t workspace_bytes, uint8_t* d_time_flags,
                   uint8_t* d_chan_flags, fdd_stream_t stream);
+
+/* Issue-rate probe (no counterpart in the paper; it measures the roofline
+ * denominators of this integer shift-and-add path on the current device).
+ * Launches blocks_per_sm (1..8) x SMs blocks of 256 threads, each thread
+ * running 16 independent dependency chains for `iters` (1..2^30) loop
+ * iterations of 4 rounds, once for warm-up and once timed with CUDA events.
+ *   kind 0: chains of a = a + b + c (32-bit): *per_second = integer adds/s
+ *           (two adds per three-input add);
+ *   kind 1: chains of byte permutes (ALU pipe only): *per_second = permutes/s;
+ *   kind 2: conflict-free 32-bit shared-memory loads: *per_second = bytes
+ *           loaded/s.
+ * *ms receives the timed launch's duration, *n_sm (may be NULL) the SM count.
+ * Blocking; allocates a 4-byte device word.  Errors: INVALID_ARG, CUDA. */
+int fdd_probe_issue_rate(int32_t kind, int32_t blocks_per_sm, int64_t iters, double* per_second, float* ms,
+                         int32_t* n_sm);
 
 /* Human-readable text of an FDD_* code (static string; no counterpart in the paper). */
 const char* fdd_error_string(int code);

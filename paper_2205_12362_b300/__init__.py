@@ -147,6 +147,7 @@ def _lib_raw():
     L.fdd_now.restype = ctypes.c_double
     L.fdd_server_create.argtypes = [_P, ctypes.POINTER(_ServerDesc), ctypes.POINTER(_P)]
     L.fdd_server_destroy.argtypes = [_P]
+    L.fdd_server_set_plain.argtypes = [_P, _P, _I32]
     L.fdd_server_push.argtypes = [_P, _I32, _I64, _P, ctypes.c_double]
     L.fdd_server_reset_beam.argtypes = [_P, _I32, _I64]
     L.fdd_server_poll.argtypes = [_P]
@@ -168,6 +169,8 @@ def _lib_raw():
     L.fdd_plan_last_launches.argtypes = [_P, ctypes.POINTER(_I64)]
     L.fdd_plan_status.argtypes = [_P, ctypes.POINTER(_I32), _I32]
     L.fdd_selftest_bounded_wait.argtypes = [_I32, ctypes.POINTER(_I32)]
+    L.fdd_probe_issue_rate.argtypes = [_I32, _I32, _I64, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I32)]
     L.fdd_plan_set_subband.argtypes = [_P, _I32, _I32, _I32]
     L.fdd_rfi_workspace_size.argtypes = [_I32, _I32, _I64, ctypes.POINTER(_SZ)]
     L.fdd_rfi_clean.argtypes = [ctypes.POINTER(_RfiDesc), _P, _I32, _I32, _I64, _I64, _P, _SZ, _P, _P, _P]
@@ -343,13 +346,19 @@ class Server:
     windows onto the GPU."""
 
     def __init__(self, plan, n_beams, chunk_len, max_slots=0, hbm_reserve_frac=0.1, hbm_budget_bytes=0,
-                 cap_per_window=1 << 15):
+                 cap_per_window=1 << 15, sb_plans=None):
+        """sb_plans: one single-SB Plan per SB of `plan` switches the server to
+        the plain per-SB path (include/fdd.h: fdd_server_set_plain)."""
         d = _ServerDesc(int(n_beams), int(chunk_len), int(max_slots), float(hbm_reserve_frac),
                         int(hbm_budget_bytes), int(cap_per_window))
         h = ctypes.c_void_p()
         _check(_lib_raw().fdd_server_create(plan.handle, ctypes.byref(d), ctypes.byref(h)), "fdd_server_create")
         self._h = h
         self._plan = plan
+        self._sb_plans = list(sb_plans) if sb_plans else []
+        if self._sb_plans:
+            arr = (ctypes.c_void_p * len(self._sb_plans))(*[p_.handle.value for p_ in self._sb_plans])
+            _check(_lib_raw().fdd_server_set_plain(self._h, arr, len(self._sb_plans)), "fdd_server_set_plain")
         self.n_beams, self.chunk_len, self.cap_per_window = int(n_beams), int(chunk_len), int(cap_per_window)
 
     def push(self, beam, seq, chunk, t_arrival=None):
@@ -463,6 +472,16 @@ class Stream:
             self.close()
         except Exception:
             pass
+
+
+def probe_issue_rate(kind, blocks_per_sm=8, iters=1 << 16):
+    """Issue-rate probe (include/fdd.h: fdd_probe_issue_rate) on the current
+    device: kind 0 integer adds/s, 1 byte permutes/s, 2 shared-memory bytes
+    loaded/s.  Returns dict(per_second, ms, n_sm)."""
+    v, t, n = ctypes.c_double(), ctypes.c_float(), _I32()
+    _check(_lib_raw().fdd_probe_issue_rate(int(kind), int(blocks_per_sm), int(iters), ctypes.byref(v),
+                                           ctypes.byref(t), ctypes.byref(n)), "fdd_probe_issue_rate")
+    return dict(per_second=v.value, ms=t.value, n_sm=n.value)
 
 
 def selftest_bounded_wait(polls=4096):

@@ -59,6 +59,8 @@ struct ServeSlot {
     void* ws = nullptr;
     fdd_candidate* d_cands = nullptr;
     uint64_t* d_count = nullptr;
+    fdd_candidate* d_sb_cands = nullptr;  // plain per-SB path: one SB's records before they are appended
+    uint64_t* d_sb_count = nullptr;
     fdd_candidate* h_cands = nullptr;   // pinned
     uint64_t* h_count = nullptr;        // pinned
     bool busy = false;
@@ -97,6 +99,7 @@ struct fdd_server {
     cudaStream_t compute[kComputeStreams] = {};
     int next_stream = 0;
     int64_t n_launched = 0, n_done = 0, n_batches = 0, max_queue = 0;
+    std::vector<fdd_plan*> sb_plans;  // non-empty: the plain per-SB path (fdd_server_set_plain)
 };
 
 namespace {
@@ -127,6 +130,8 @@ void destroy_server(fdd_server* s) {
         if (sl.ws) cudaFree(sl.ws);
         if (sl.d_cands) cudaFree(sl.d_cands);
         if (sl.d_count) cudaFree(sl.d_count);
+        if (sl.d_sb_cands) cudaFree(sl.d_sb_cands);
+        if (sl.d_sb_count) cudaFree(sl.d_sb_count);
         if (sl.h_cands) cudaFreeHost(sl.h_cands);
         if (sl.h_count) cudaFreeHost(sl.h_count);
     }
@@ -193,6 +198,43 @@ int retire(fdd_server* s, double t) {
     return FDD_OK;
 }
 
+// Plain per-SB path: append the records of single-SB search `sb` (sb field 0)
+// to the window's list, relabelled with the compound beam's SB index.  The
+// launches of one window are ordered on one stream, so *count is the number
+// of records (true total) appended so far; the first cap are kept.
+__global__ void k_append_sb(const fdd_candidate* __restrict__ src, const uint64_t* __restrict__ src_count,
+                            int64_t src_cap, fdd_candidate* __restrict__ dst, uint64_t* __restrict__ count,
+                            int64_t cap, int32_t sb) {
+    const uint64_t base = *count;
+    const uint64_t n_true = *src_count;
+    const uint64_t n_src = n_true < static_cast<uint64_t>(src_cap) ? n_true : static_cast<uint64_t>(src_cap);
+    for (uint64_t k = threadIdx.x; k < n_src && base + k < static_cast<uint64_t>(cap); k += blockDim.x) {
+        fdd_candidate c = src[k];
+        c.sb = sb;
+        dst[base + k] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *count = base + n_true;
+}
+
+// One window through the plain per-SB path on stream cs: n_sb single-SB
+// searches one after another, each appending its records to the slot's list.
+int launch_plain(fdd_server* s, const ServeWindow& w, ServeSlot& sl, cudaStream_t cs) {
+    const ServeBeam& b = s->beams[w.beam];
+    cudaError_t e = cudaMemsetAsync(sl.d_count, 0, sizeof(uint64_t), cs);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    for (size_t k = 0; k < s->sb_plans.size(); k++) {
+        const int rc = fdd_search(s->sb_plans[k], b.buf[w.buf], s->n_in, s->pitch, s->d.chunk_len,
+                                  w.window * s->d.chunk_len, sl.ws, s->ws_bytes, sl.d_sb_cands, s->d.cap_per_window,
+                                  sl.d_sb_count, nullptr, reinterpret_cast<fdd_stream_t>(cs));
+        if (rc != FDD_OK) return rc;
+        k_append_sb<<<1, 256, 0, cs>>>(sl.d_sb_cands, sl.d_sb_count, s->d.cap_per_window, sl.d_cands, sl.d_count,
+                                       s->d.cap_per_window, static_cast<int32_t>(k));
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_append_sb");
+    }
+    return FDD_OK;
+}
+
 // Launch every queued window that finds a free slot, as one batch.
 int schedule(fdd_server* s, double t) {
     while (!s->queue.empty()) {
@@ -200,8 +242,9 @@ int schedule(fdd_server* s, double t) {
         for (int k = 0; k < static_cast<int>(s->slots.size()); k++)
             if (!s->slots[k].busy) free_slots.push_back(k);
         if (free_slots.empty()) return FDD_OK;
+        // the plain per-SB path takes one window per launch group (no batching)
         const int n = std::min<int>({static_cast<int>(free_slots.size()), static_cast<int>(s->queue.size()),
-                                     FDD_MAX_BATCH_JOBS});
+                                     s->sb_plans.empty() ? FDD_MAX_BATCH_JOBS : 1});
         ServeBatch batch;
         batch.stream = s->next_stream;
         s->next_stream = (s->next_stream + 1) % kComputeStreams;
@@ -231,7 +274,9 @@ int schedule(fdd_server* s, double t) {
             j.d_series = nullptr;
             batch.wins.push_back(w);
         }
-        int rc = fdd_search_batch(s->plan, jobs.data(), n, s->d.chunk_len, reinterpret_cast<fdd_stream_t>(cs));
+        int rc = s->sb_plans.empty()
+                     ? fdd_search_batch(s->plan, jobs.data(), n, s->d.chunk_len, reinterpret_cast<fdd_stream_t>(cs))
+                     : launch_plain(s, batch.wins[0], s->slots[batch.wins[0].slot], cs);
         if (rc != FDD_OK) return rc;
         for (const ServeWindow& w : batch.wins) {
             ServeSlot& sl = s->slots[w.slot];
@@ -349,6 +394,31 @@ int fdd_server_create(fdd_plan* plan, const fdd_server_desc* desc, fdd_server** 
         }
     }
     *out = s;
+    return FDD_OK;
+}
+
+int fdd_server_set_plain(fdd_server* s, fdd_plan* const* sb_plans, int32_t n_sb) {
+    if (!s || !sb_plans || n_sb != s->plan->n_sb) return fail(FDD_ERR_INVALID_ARG, "need one plan per SB");
+    if (s->n_launched > 0 || !s->queue.empty()) return fail(FDD_ERR_INVALID_ARG, "server already in use");
+    for (int32_t k = 0; k < n_sb; k++) {
+        const fdd_plan* q = sb_plans[k];
+        if (!q || q->n_sb != 1 || q->n_tab != s->plan->n_tab || q->n_chan != s->plan->n_chan ||
+            q->max_delay_native > s->plan->max_delay_native)
+            return fail(FDD_ERR_INVALID_ARG, "each plan must be a single-SB plan of the server's TABs and channels, "
+                                             "with no larger delay");
+        size_t need = 0;
+        const int rc = fdd_workspace_size(q, s->n_in, s->d.chunk_len, 1, &need);
+        if (rc != FDD_OK) return rc;
+        if (need > s->ws_bytes) return fail(FDD_ERR_WORKSPACE, "a single-SB plan needs more workspace than a slot has");
+    }
+    for (ServeSlot& sl : s->slots) {
+        cudaError_t e;
+        if (!sl.d_sb_cands &&
+            ((e = cudaMalloc(&sl.d_sb_cands, sizeof(fdd_candidate) * s->d.cap_per_window)) != cudaSuccess ||
+             (e = cudaMalloc(&sl.d_sb_count, sizeof(uint64_t))) != cudaSuccess))
+            return cuda_fail(e, "slot allocation");
+    }
+    s->sb_plans.assign(sb_plans, sb_plans + n_sb);
     return FDD_OK;
 }
 

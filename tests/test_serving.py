@@ -145,3 +145,32 @@ def test_admission_refused_without_hbm(fdd):
     with pytest.raises(fdd.FddError) as e:
         fdd.Server(plan, 4, chunk, hbm_budget_bytes=1 << 20)
     assert e.value.code == -3
+
+
+def test_plain_per_sb_serving_matches_batched(fdd):
+    """The plain per-SB serving path (one single-SB search per SB and window)
+    returns, window by window, the batched path's candidate records."""
+    f, ranges, sb, streams, chunk, n_chunks = stream_case(n_beams=2, n_chunks=7)
+    plan = fdd.Plan(2, 64, 3, f, T_SAMP, ranges, 6.0, sb)
+    sb_plans = [fdd.Plan(2, 64, 1, f, T_SAMP, ranges, 6.0, sb[s:s + 1]) for s in range(3)]
+    out = {}
+    for name, kw in (("batched", {}), ("plain", dict(sb_plans=sb_plans))):
+        srv = fdd.Server(plan, len(streams), chunk, max_slots=2, cap_per_window=1 << 14, **kw)
+        for k in range(n_chunks):
+            for b, x in enumerate(streams):
+                while srv.push(b, k, chunk_of(x, k, chunk)) == fdd.FDD_ERR_BUSY:
+                    srv.drain()
+            srv.poll()
+        srv.drain()
+        out[name] = {(r["beam"], r["window"]): (r, c) for r, c in srv.results()}
+        srv.close()
+    assert set(out["plain"]) == set(out["batched"]) and len(out["plain"]) > 0
+    total = 0
+    for key, (r, c) in out["batched"].items():
+        rp, cp = out["plain"][key]
+        assert rp["n_cands"] == r["n_cands"] and rp["batch_jobs"] == 1
+        assert len(cp) == len(c) and (cp == c).all(), "window %r differs between the two paths" % (key,)
+        total += len(c)
+    assert total > 0
+    with pytest.raises(fdd.FddError):      # one plan per SB is required
+        fdd.Server(plan, 1, chunk, sb_plans=sb_plans[:2])
