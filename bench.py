@@ -192,29 +192,37 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- oracle (CPU baseline)
 def oracle_sample_rate(x, sb, f, t, w, n_in, target_s):
-    """Time the oracle as it stands on a bounded sample (leading DM trials of
-    each range, first SB) and return (samples/s, cores, description)."""
+    """Time the oracle as it stands on a bounded sample of the workload: the
+    leading DM trials of each range of the first SB, grown toward target_s of
+    CPU work (all trials first, then more SBs).  Returns (samples/s, cores,
+    description, seconds, ranges of the sample, SBs of the sample)."""
     import oracle
     cores = oracle.get_threads()
 
-    def run(frac):
-        rr = [dict(r, n_dm=max(1, int(r["n_dm"] * frac))) for r in w["ranges"]]
-        units = sum(r["n_dm"] * (w["n_out"] // r["downsamp"]) for r in rr)
+    def run(frac, n_sb):
+        rr = [dict(r, n_dm=max(1, int(round(r["n_dm"] * frac)))) for r in w["ranges"]]
+        units = n_sb * sum(r["n_dm"] * (w["n_out"] // r["downsamp"]) for r in rr)
         t0 = time.perf_counter()
-        oracle.search(x, sb[:1], f, t, rr, w["thr"], w["n_out"], n_in=n_in)
+        oracle.search(x, sb[:n_sb], f, t, rr, w["thr"], w["n_out"], n_in=n_in)
         return units, time.perf_counter() - t0, rr
 
-    frac = 1.0 / 64
-    u, dt, rr = run(frac)
-    for _ in range(4):                       # grow the sample toward target_s of CPU work
-        if dt >= 0.5 * target_s or frac >= 1.0:
+    frac, n_sb = 1.0 / 16, 1
+    u, dt, rr = run(frac, n_sb)
+    for _ in range(6):                       # grow the sample toward target_s of CPU work
+        if dt >= 0.5 * target_s:
             break
-        frac = min(1.0, frac * 0.9 * target_s / max(dt, 1e-3))
-        u, dt, rr = run(frac)
-    desc = "SB 0 of %d, first %s DM trials of each range (%s), full %d-sample chunk, %d channels" % (
-        w["n_sb"], "/".join(str(r["n_dm"]) for r in rr), "/".join(str(r["n_dm"]) for r in w["ranges"]),
+        grow = 0.9 * target_s / max(dt, 1e-3)
+        if frac < 1.0:
+            frac = min(1.0, frac * grow)
+        elif n_sb < w["n_sb"]:
+            n_sb = max(n_sb + 1, min(w["n_sb"], int(n_sb * grow)))
+        else:
+            break
+        u, dt, rr = run(frac, n_sb)
+    desc = "SBs 0-%d of %d, first %s DM trials of each range (%s), full %d-sample chunk, %d channels" % (
+        n_sb - 1, w["n_sb"], "/".join(str(r["n_dm"]) for r in rr), "/".join(str(r["n_dm"]) for r in w["ranges"]),
         w["n_out"], w["n_chan"])
-    return u / dt, cores, desc, dt, rr
+    return u / dt, cores, desc, dt, rr, n_sb
 
 
 # ----------------------------------------------------------------- profile evidence
@@ -265,14 +273,15 @@ def reduce_max(value, dist, device):
 def measure_int_peaks(fdd, gpu_index, target_s=0.25):
     """Issue-rate probes (include/fdd.h: fdd_probe_issue_rate) at full
     occupancy, timed with CUDA events, with nvidia-smi clocks sampled while
-    they run: integer adds/s (the roofline peak of the dedispersion kernels),
-    ALU-pipe permutes/s and shared-memory load bytes/s."""
+    they run: integer adds/s on the ALU pipe (three-input adds), on the FMA
+    pipe (multiply-adds) and on both together (the roofline peak of the
+    dedispersion kernels), ALU-pipe permutes/s and shared-memory bytes/s."""
     sampler = ClockSampler(gpu_index)
     sampler.start()
     time.sleep(0.25)
     t_lo = time.time()
     out = {}
-    for kind, name in ((0, "add"), (1, "prmt"), (2, "lds")):
+    for kind, name in ((0, "add"), (1, "prmt"), (2, "lds"), (3, "imad"), (4, "mix")):
         r = fdd.probe_issue_rate(kind, 8, 1 << 12)            # calibrate the iteration count
         iters = int(min(1 << 30, max(1 << 12, (1 << 12) * target_s * 1e3 / max(r["ms"], 1e-3))))
         r = fdd.probe_issue_rate(kind, 8, iters)
@@ -281,9 +290,15 @@ def measure_int_peaks(fdd, gpu_index, target_s=0.25):
     mhz = clocks.get("sm_mhz") or SM_MAX_MHZ_NOMINAL
     n_sm = out["add"]["n_sm"]
     per_clk = lambda v: v / (n_sm * mhz * 1e6)
+    best = max(out["add"]["per_second"], out["mix"]["per_second"])
     return {
-        "adds_per_s": out["add"]["per_second"],
+        "adds_per_s": best,
+        "adds_per_s_basis": "the larger of three-input adds alone and interleaved with multiply-adds",
+        "iadd3_adds_per_s": out["add"]["per_second"],
         "iadd3_thread_instr_per_sm_per_clk": per_clk(out["add"]["per_second"]) / 2.0,
+        "imad_per_s": out["imad"]["per_second"],
+        "imad_thread_instr_per_sm_per_clk": per_clk(out["imad"]["per_second"]),
+        "mixed_adds_per_s": out["mix"]["per_second"],
         "prmt_per_s": out["prmt"]["per_second"],
         "prmt_thread_instr_per_sm_per_clk": per_clk(out["prmt"]["per_second"]),
         "lds_bytes_per_s": out["lds"]["per_second"],
@@ -344,8 +359,8 @@ class Arm:
                            torch.zeros(1, dtype=torch.int64, device=dev)) for _ in self.plans] for _ in wins]
         else:
             self.jobs = [plan.make_job(wb, n_in, n_out, cap=cap) for wb in wins]
-            plan.batch_prepare(n_out)
-            if not args.no_autotune:
+            plan.batch_prepare(n_out, args.batch_variant if args.batch_variant is not None else -1)
+            if not args.no_autotune and args.batch_variant is None:
                 plan.batch_autotune(self.jobs[:1], n_out, reps=2, stream=stream)
             self.graphs = [fdd.Graph(plan, [j], n_out) for j in self.jobs] if self.mode == "graph" else None
             self.outs = [[(j.cands, j.count)] for j in self.jobs]
@@ -413,6 +428,7 @@ def timed_steps(arm, steps, flush, dist):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     out = []
+    torch.cuda.nvtx.range_push("timed")    # the range a profiler's launch list is restricted to
     for _ in range(steps):
         flush.zero_()                      # evict the input from L2 between steps
         e0.record(arm.stream)
@@ -420,6 +436,7 @@ def timed_steps(arm, steps, flush, dist):
         e1.record(arm.stream)
         e1.synchronize()
         out.append(e0.elapsed_time(e1))
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -596,8 +613,9 @@ def run_fdd(args):
                            "partial sums across DM trials)" + (
                                "; the two-step subband mode is approximate: it does not compute the exact sums"
                                if args.subband else ""),
-            "peak_basis": ("measured: fdd_probe_issue_rate kind 0 (three-input add chains, full occupancy), "
-                           "%.1f T adds/s at %s MHz" % (peaks["adds_per_s"] / 1e12, peaks["sm_mhz"]))
+            "peak_basis": ("measured: fdd_probe_issue_rate (three-input add chains, alone and interleaved with "
+                           "multiply-add chains, full occupancy), %.1f T adds/s at %s MHz"
+                           % (peaks["adds_per_s"] / 1e12, peaks["sm_mhz"]))
             if peaks else "derived: 148 SM x 128 INT32 lanes x 2 adds/IADD3 x 2032 MHz",
             "peak_derived": derived,
             "smem_bound_adds_per_s": peaks["lds_bytes_per_s"] if peaks else None,
@@ -607,7 +625,7 @@ def run_fdd(args):
 
     cpu = None
     if not args.no_cpu_baseline:
-        rate, cores, desc, secs, _ = oracle_sample_rate(x, sb, f, t, w, n_in, args.cpu_seconds)
+        rate, cores, desc, secs, _, _ = oracle_sample_rate(x, sb, f, t, w, n_in, args.cpu_seconds)
         cpu = {"value": rate, "unit": "samples/s", "cores": cores, "kind": "oracle", "sample": desc,
                "seconds": secs}
         if w["n_sb"] == 1:
@@ -615,7 +633,8 @@ def run_fdd(args):
             import oracle
             oracle.set_threads(1)
             try:
-                rate1, _, desc1, secs1, _ = oracle_sample_rate(x, sb, f, t, w, n_in, max(1.0, args.cpu_seconds / 4))
+                rate1, _, desc1, secs1, _, _ = oracle_sample_rate(x, sb, f, t, w, n_in,
+                                                                   max(1.0, args.cpu_seconds / 4))
             finally:
                 oracle.set_threads(cores)
             cpu["single_thread"] = {"value": rate1, "unit": "samples/s", "cores": 1, "sample": desc1,
@@ -704,13 +723,13 @@ def run_reference(args):
     w, f, t, x, sb, n_in = make_workload(
         args.workload, lambda nt, ns, fr, g: oracle.sb_table(nt, ns, fr, 1500.0, 0.80, 1296.0, 144.0, g))
     per_step = max(0.05, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
-    _, cores, desc, _, rr = oracle_sample_rate(x, sb, f, t, w, n_in, per_step)
-    units = sum(r["n_dm"] * (w["n_out"] // r["downsamp"]) for r in rr)
+    _, cores, desc, _, rr, n_sb = oracle_sample_rate(x, sb, f, t, w, n_in, per_step)
+    units = n_sb * sum(r["n_dm"] * (w["n_out"] // r["downsamp"]) for r in rr)
     for _ in range(args.warmup):
-        oracle.search(x, sb[:1], f, t, rr, w["thr"], w["n_out"], n_in=n_in)
+        oracle.search(x, sb[:n_sb], f, t, rr, w["thr"], w["n_out"], n_in=n_in)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.search(x, sb[:1], f, t, rr, w["thr"], w["n_out"], n_in=n_in)
+        oracle.search(x, sb[:n_sb], f, t, rr, w["thr"], w["n_out"], n_in=n_in)
     dt = time.perf_counter() - t0
     value = units * args.steps / dt
     line = {
@@ -849,7 +868,7 @@ def serving_oracle_check(w, f, t, sb, pool, pool_pulses, res, n_in, n_windows=2)
         sel = [s0, (s0 + w["n_sb"] // 2) % w["n_sb"]]
         t0 = time.perf_counter()
         ora, _ = oracle_candidate_superset(x, sb[sel], f, t, w["ranges"], w["thr"], chunk, n_in,
-                                           t_offset=win * chunk)
+                                           t_offset=win * chunk, bins_absolute=True)
         out["oracle_s"] += time.perf_counter() - t0
         ora = ora.copy()
         ora["sb"] = np.asarray(sel, dtype=np.int32)[ora["sb"]]
@@ -946,6 +965,9 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=3, help="timed steps of the plain per-SB path")
     ap.add_argument("--variant", type=int, default=None, help="force this dedispersion kernel variant")
     ap.add_argument("--cc", type=int, default=0, help="with --variant: channels per stage (0 = largest fitting)")
+    ap.add_argument("--batch-variant", type=int, default=None,
+                    help="batched/graph modes: this batch variant instead of the tuner's choice (1000 SB-factored "
+                         "launches, 1001 one persistent SB-factored launch, 0.. brute-force persistent)")
     ap.add_argument("--subband", default=None,
                     help="G,K: approximate two-step subband dedispersion (G channels per subband, K fine trials per "
                          "coarse DM) instead of the exact kernels; not the benchmark's default")

@@ -183,6 +183,32 @@ int fdd_search(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitc
                fdd_candidate* d_cands, int64_t cap, uint64_t* d_count, int32_t* d_series,
                fdd_stream_t stream);
 
+/* Streaming form of fdd_search (Sec. "Downsampling" with bins aligned to the
+ * beam's stream, so that consecutive windows tile one search of the whole
+ * stream): input sample 0 is native sample t0_native (>= 0) of the stream,
+ * and range r's downsampling bins are aligned to stream sample 0 (bin J
+ * covers stream samples [J D_r, (J+1) D_r)).  The window searches, per
+ * range, the bins whose first sample lies in [t0_native, t0_native + n_out):
+ *     n_r = ceil((t0 + n_out)/D_r) - ceil(t0/D_r) bins, read from input
+ *     sample phase_r = ceil(t0/D_r) D_r - t0 on
+ * (for D_r = 8 and 12500-sample chunks, n_r alternates 1563 and 1562); a
+ * candidate's t_native is its bin's first stream sample.  Everything else as
+ * fdd_search, except the sizes: n_in >= phase_r + D_r (n_r + max delay_r)
+ * for every range (fdd_window_sizes gives an n_in that fits every t0), the
+ * workspace and d_series (if given) as fdd_window_sizes reports, and d_series
+ * packed [range][sb][dm][ceil(n_out / D_r)] with the first n_r samples of
+ * each row written.  Errors as fdd_search; INVALID_ARG for t0_native < 0. */
+int fdd_search_window(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitch, int64_t n_out,
+                      int64_t t0_native, void* d_workspace, size_t workspace_bytes, fdd_candidate* d_cands,
+                      int64_t cap, uint64_t* d_count, int32_t* d_series, fdd_stream_t stream);
+
+/* Sizes of fdd_search_window for n_out outputs, valid for every window
+ * start: *n_in = n_out + max_r (D_r (max delay_r + 1) - 1) input samples, the
+ * workspace (series in the workspace) and the d_series buffer.  Any output
+ * pointer may be NULL (library bookkeeping; no counterpart in the paper). */
+int fdd_window_sizes(const fdd_plan* plan, int64_t n_out, int64_t* n_in, size_t* workspace_bytes,
+                     size_t* series_bytes);
+
 /* Stage entry point (Sec. "Downsampling"): d_out[row][j] =
  * sum_{k<D} d_in[row][j*D + k] for j < floor(n_in / D), rows = n_rows.
  * d_in uint8 rows at in_pitch bytes; d_out uint16 rows at out_pitch
@@ -275,6 +301,9 @@ typedef struct {
     int64_t cap;
     uint64_t* d_count;        /* device: true candidate count of this job */
     int32_t* d_series;        /* NULL, or fdd_series_size() bytes for this job's series */
+    int32_t bins_absolute;    /* 0: as fdd_search; 1: as fdd_search_window (t_offset_native is the
+                                 window's stream position; workspace and series sized by
+                                 fdd_window_sizes).  All jobs of a batch share the mode. */
 } fdd_job;
 
 /* Batch variant value selecting SB-factored mode: instead of the persistent
@@ -282,6 +311,15 @@ typedef struct {
  * DM slab per range per job), with each range's SB-factored configuration
  * (set where a range has none).  Plans with >= 2 SBs only. */
 #define FDD_BATCH_SB_FACTORED 1000
+
+/* Batch variant value selecting persistent SB-factored mode: ONE launch runs
+ * the SB-factored part and combine work of every job, range and DM slab
+ * (blocks take tasks in an order in which each task depends only on earlier
+ * ones; a job's scratch holds three slab buffers used in turn), then one
+ * boxcar launch.  Same results as FDD_BATCH_SB_FACTORED.  Plans with >= 2
+ * SBs whose scratch (fdd_plan_set_scratch_limit) holds three slabs of 32 DM
+ * trials of every range; FDD_ERR_UNSUPPORTED otherwise. */
+#define FDD_BATCH_SB_PERSISTENT 1001
 
 /* Prepare the plan's batched tables for chunks of n_out native samples with
  * persistent-kernel variant `variant` (-1: keep the current, possibly tuned,
@@ -329,14 +367,16 @@ int fdd_graph_destroy(fdd_graph* graph);
  * 1.024 s chunks are searched as they arrive, each output needing the next
  * max-delay of input; Sec. "AMBER", Sec. "Computing performance").
  * One server, one plan, many beams.  Per beam the server keeps two device
- * window buffers of chunk + max delay samples (rounded up to whole chunks);
+ * window buffers of n_in samples (fdd_window_sizes, rounded up to whole chunks);
  * a complete window is queued; "slots" (workspace + candidate buffers) are
  * allocated once from free HBM; fdd_server_poll launches every queued
  * window that finds a free slot as one batched search (continuous
  * batching), retires finished ones and copies their candidates to host.
- * Window w of a beam searches outputs [w*chunk, (w+1)*chunk) (t_native of its
- * candidates is absolute) and is complete once the chunk holding its last
- * needed sample has arrived. */
+ * Window w of a beam searches, like fdd_search_window, the outputs whose
+ * first native sample lies in [w*chunk, (w+1)*chunk) with downsampling bins
+ * aligned to the beam's stream (t_native of its candidates is absolute), and
+ * is complete once the chunk holding its last needed sample (n_in of
+ * fdd_window_sizes) has arrived. */
 typedef struct fdd_server fdd_server;
 
 typedef struct {
@@ -423,11 +463,12 @@ int fdd_server_info(const fdd_server* server, fdd_server_stats* stats);
  * pushes the beam's chunks from DEVICE memory in order; the stream keeps the
  * delay overlap in two device buffers of ceil((chunk + max delay) / chunk)
  * chunks each (owned by the stream, freed by fdd_stream_close) and searches
- * window w -- native outputs [w*chunk, (w+1)*chunk), candidate t_native
- * absolute -- with fdd_search as soon as its last needed chunk is pushed
- * (window 0 after chunk ceil((chunk + max delay) / chunk) - 1, then one
- * window per chunk).  Downsampling bins start at each window's first
- * sample.  For many beams on one GPU with batching and admission control,
+ * window w -- the outputs whose first native sample lies in
+ * [w*chunk, (w+1)*chunk), candidate t_native absolute -- with
+ * fdd_search_window (downsampling bins aligned to the beam's stream, so the
+ * windows tile one search of the whole stream) as soon as its last needed
+ * chunk is pushed (window 0 after chunk ceil(n_in / chunk) - 1 with n_in
+ * from fdd_window_sizes, then one window per chunk).  For many beams on one GPU with batching and admission control,
  * use the fdd_server_* runtime below.  Not thread-safe per stream object. */
 typedef struct fdd_stream fdd_stream;
 
@@ -654,7 +695,11 @@ int fdd_rfi_clean(const fdd_rfi_desc* desc, uint8_t* d_tabs, int32_t n_tab, int3
  *           (two adds per three-input add);
  *   kind 1: chains of byte permutes (ALU pipe only): *per_second = permutes/s;
  *   kind 2: conflict-free 32-bit shared-memory loads: *per_second = bytes
- *           loaded/s.
+ *           loaded/s;
+ *   kind 3: chains of a = a * b + c (32-bit): *per_second = adds/s (one per
+ *           multiply-add);
+ *   kind 4: three-input-add and multiply-add chains interleaved one to one:
+ *           *per_second = adds/s of both integer pipes together.
  * *ms receives the timed launch's duration, *n_sm (may be NULL) the SM count.
  * Blocking; allocates a 4-byte device word.  Errors: INVALID_ARG, CUDA. */
 int fdd_probe_issue_rate(int32_t kind, int32_t blocks_per_sm, int64_t iters, double* per_second, float* ms,

@@ -47,7 +47,7 @@ def lib():
         L.oracle_stats.argtypes = [_P, _I64, _P, _P]
         L.oracle_boxcar_snr.argtypes = [_P, _I64, _I32, _D, _D, _P]
         L.oracle_search.argtypes = [_P, _I32, _I32, _I64, _I64, _P, _I32, _P, _D, _I32,
-                                    _P, _P, _P, _P, _P, _P, _D, _I64, _I64, _P, _I64, _P, _P, _P]
+                                    _P, _P, _P, _P, _P, _P, _D, _I64, _I64, _P, _I64, _P, _P, _P, _I32]
         L.oracle_search.restype = _I64
         L.oracle_cluster.argtypes = [_P, _I64, _P]
         L.oracle_rfi_clean.argtypes = [_P, _I32, _I32, _I64, _I64, _D, _I32, _D, _I32, _P, _P]
@@ -127,9 +127,21 @@ def boxcar_snr(series, width, mean, std):
     return out
 
 
+def window_bins(t_offset_native, n_out, downsamp):
+    """(phase, n_r) of a window whose input starts at stream sample
+    t_offset_native, with bins aligned to stream sample 0 (oracle.c:
+    oracle_search, bins_absolute): the bins that start in
+    [t_offset, t_offset + n_out), read from input sample phase on."""
+    j_first = -(-int(t_offset_native) // int(downsamp))
+    j_end = -(-(int(t_offset_native) + int(n_out)) // int(downsamp))
+    return j_first * int(downsamp) - int(t_offset_native), j_end - j_first
+
+
 def search(x, sb_map, freq_mhz, t_samp_s, ranges, snr_thresh, n_out, n_in=None,
-           t_offset_native=0, cap=1 << 20, return_series=False):
+           t_offset_native=0, cap=1 << 20, return_series=False, bins_absolute=False):
     """Run the whole hot path on x: uint8[n_tab][n_chan][pitch].
+    bins_absolute: x[..., 0] is stream sample t_offset_native and the
+    downsampling bins are aligned to stream sample 0 (window_bins).
 
     ranges: list of dicts {dm0, ddm, n_dm, downsamp, widths} and optionally
     subband=(G, K): that range uses the two-step subband dedispersion of
@@ -160,15 +172,17 @@ def search(x, sb_map, freq_mhz, t_samp_s, ranges, snr_thresh, n_out, n_in=None,
     sub_k = np.array([int(r.get("subband", (0, 1))[1]) for r in ranges], dtype=np.int32)
     cands = np.zeros(max(int(cap), 1), dtype=CAND_DTYPE)
     series = None
+    n_rs = [window_bins(t_offset_native, n_out, r.get("downsamp", 1))[1] if bins_absolute
+            else int(n_out) // int(r.get("downsamp", 1)) for r in ranges]
     if return_series:
-        total = sum(int(m.shape[0]) * int(r["n_dm"]) * (int(n_out) // int(r.get("downsamp", 1)))
-                    for r in ranges)
-        series = np.empty(total, dtype=np.int64)
+        total = sum(int(m.shape[0]) * int(r["n_dm"]) * nr for r, nr in zip(ranges, n_rs))
+        series = np.empty(max(total, 1), dtype=np.int64)
     n = lib().oracle_search(_ptr(x), n_tab, n_chan, n_in, pitch, _ptr(m), m.shape[0], _ptr(f),
                             float(t_samp_s), len(ranges), _ptr(dm0), _ptr(ddm), _ptr(ndm),
                             _ptr(ds), _ptr(nw), _ptr(ws), float(snr_thresh), int(n_out),
                             int(t_offset_native), _ptr(cands), int(cap),
-                            _ptr(series) if series is not None else None, _ptr(sub_g), _ptr(sub_k))
+                            _ptr(series) if series is not None else None, _ptr(sub_g), _ptr(sub_k),
+                            1 if bins_absolute else 0)
     if n == -1:
         raise ValueError("input too short for the DM plan")
     if n < 0:
@@ -179,8 +193,7 @@ def search(x, sb_map, freq_mhz, t_samp_s, ranges, snr_thresh, n_out, n_in=None,
     if series is not None:
         out_series = []
         off = 0
-        for r in ranges:
-            nr = int(n_out) // int(r.get("downsamp", 1))
+        for r, nr in zip(ranges, n_rs):
             k = m.shape[0] * int(r["n_dm"]) * nr
             out_series.append(series[off:off + k].reshape(m.shape[0], int(r["n_dm"]), nr))
             off += k

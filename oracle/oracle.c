@@ -270,10 +270,21 @@ typedef struct {
  * native samples.  dm_index is global over the concatenated ranges.
  * Series with zero standard deviation emit nothing.
  * series_or_null, if given, receives int64 series per range, packed
- * [range][sb][dm][floor(n_out/D_r)].  Returns the total candidate count;
+ * [range][sb][dm][n_r] (n_r below).  Returns the total candidate count;
  * only the first cap are stored (order unspecified).  Returns -1 on a short
- * input (n_in < D_r * (floor(n_out/D_r) + max delay_r) for some r) and -2
- * on allocation failure. */
+ * input and -2 on allocation failure.
+ * Downsampling bins (Sec. "Downsampling"):
+ *   bins_absolute == 0: bins start at input sample 0; n_r = floor(n_out/D_r);
+ *     the input must hold D_r * (n_r + max delay_r) samples;
+ *   bins_absolute != 0: input sample 0 is sample t_offset_native (>= 0) of
+ *     the beam's stream and bins are aligned to stream sample 0 (bin J covers
+ *     stream samples [J D, J D + D)), so consecutive windows of one stream
+ *     tile the one-shot search of the whole stream.  The window searches the
+ *     bins that start in [t_offset, t_offset + n_out): J from ceil(t_offset/D)
+ *     to ceil((t_offset + n_out)/D) - 1, i.e. n_r of them, read from input
+ *     sample phase_r = ceil(t_offset/D) D - t_offset on; a candidate's
+ *     t_native is its bin's first stream sample.  The input must hold
+ *     phase_r + D_r (n_r + max delay_r) samples. */
 int64_t oracle_search(const uint8_t* x, int32_t n_tab, int32_t n_chan, int64_t n_in,
                       int64_t pitch, const int32_t* sb_map, int32_t n_sb,
                       const double* freq_mhz, double t_samp_s, int32_t n_range,
@@ -281,20 +292,29 @@ int64_t oracle_search(const uint8_t* x, int32_t n_tab, int32_t n_chan, int64_t n
                       const int32_t* downsamp, const int32_t* n_width,
                       const int32_t* widths, double thr, int64_t n_out,
                       int64_t t_offset_native, oracle_cand* cands, int64_t cap,
-                      int64_t* series_or_null, const int32_t* sub_chan, const int32_t* sub_k) {
+                      int64_t* series_or_null, const int32_t* sub_chan, const int32_t* sub_k,
+                      int32_t bins_absolute) {
     int64_t count = 0;
+    if (bins_absolute && t_offset_native < 0) return -1;
     int32_t dm_base = 0, w_base = 0;
     int64_t series_base = 0;
     for (int32_t r = 0; r < n_range; r++) {
         int32_t D = downsamp[r];
-        int64_t n_y = n_in / D, n_r = n_out / D;
+        int64_t phase = 0, n_r = n_out / D;
+        if (bins_absolute) {
+            const int64_t j_first = (t_offset_native + D - 1) / D;           /* ceil(t_offset / D) */
+            const int64_t j_end = (t_offset_native + n_out + D - 1) / D;     /* ceil((t_offset + n_out) / D) */
+            phase = j_first * D - t_offset_native;
+            n_r = j_end - j_first;
+        }
+        const int64_t n_y = (n_in - phase) / D;
         int64_t* d = (int64_t*)malloc(sizeof(int64_t) * (size_t)n_dm[r] * (size_t)n_chan);
         uint32_t* y = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)n_tab * (size_t)n_chan * (size_t)n_y);
         if (!d || !y) { free(d); free(y); return -2; }
         int64_t dmax = oracle_delays(n_chan, freq_mhz, t_samp_s, dm0[r], ddm[r], n_dm[r], D, d, NULL);
         const int two_step = sub_chan && sub_k && sub_chan[r] > 0;
         if (!two_step && n_r + dmax > n_y) { free(d); free(y); return -1; }
-        oracle_downsample(x, (int64_t)n_tab * n_chan, n_in, pitch, D, y);
+        oracle_downsample(x + phase, (int64_t)n_tab * n_chan, n_in - phase, pitch, D, y);
         int64_t n_series = (int64_t)n_sb * n_dm[r];
         int64_t* ts = NULL;  /* two-step series of this range */
         if (two_step) {
@@ -337,7 +357,7 @@ int64_t oracle_search(const uint8_t* x, int32_t n_tab, int32_t n_chan, int64_t n
                                 o->dm_index = dm_base + i;
                                 o->downsamp = D;
                                 o->width_native = w * D;
-                                o->t_native = t * D + t_offset_native;
+                                o->t_native = t * D + phase + t_offset_native;
                                 o->dm = dm0[r] + (double)i * ddm[r];
                                 o->snr = snr[t];
                             }

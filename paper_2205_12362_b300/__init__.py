@@ -61,7 +61,7 @@ class _Job(ctypes.Structure):
     _fields_ = [("d_tabs", ctypes.c_void_p), ("n_in", ctypes.c_int64), ("pitch", ctypes.c_int64),
                 ("t_offset_native", ctypes.c_int64), ("d_workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("d_cands", ctypes.c_void_p), ("cap", ctypes.c_int64),
-                ("d_count", ctypes.c_void_p), ("d_series", ctypes.c_void_p)]
+                ("d_count", ctypes.c_void_p), ("d_series", ctypes.c_void_p), ("bins_absolute", ctypes.c_int32)]
 
 
 class _ServerDesc(ctypes.Structure):
@@ -127,6 +127,8 @@ def _lib_raw():
     L.fdd_workspace_size.argtypes = [_P, _I64, _I64, _I32, ctypes.POINTER(_SZ)]
     L.fdd_series_size.argtypes = [_P, _I64, ctypes.POINTER(_SZ)]
     L.fdd_search.argtypes = [_P, _P, _I64, _I64, _I64, _I64, _P, _SZ, _P, _I64, _P, _P, _P]
+    L.fdd_search_window.argtypes = [_P, _P, _I64, _I64, _I64, _I64, _P, _SZ, _P, _I64, _P, _P, _P]
+    L.fdd_window_sizes.argtypes = [_P, _I64, ctypes.POINTER(_I64), ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]
     L.fdd_downsample_u8.argtypes = [_P, _I64, _I64, _I64, _I32, _P, _I64, _P]
     L.fdd_plan_set_timing.argtypes = [_P, _I32]
     L.fdd_num_variants.argtypes = [ctypes.POINTER(_I32)]
@@ -276,6 +278,7 @@ class Job:
     count: "object"
     t_offset: int = 0
     series: "object" = None
+    bins_absolute: bool = False   # True: a window of a stream (include/fdd.h: fdd_search_window)
 
     def result(self):
         return SearchResult(cands=self.cands, count=self.count, series=self.series, cap=int(self.cands.shape[0]))
@@ -295,6 +298,7 @@ def _jobs_array(jobs):
         arr[k].cap = int(j.cands.shape[0])
         arr[k].d_count = _dev_ptr(j.count, "count").value
         arr[k].d_series = _dev_ptr(j.series, "series", torch.int32).value if j.series is not None else None
+        arr[k].bins_absolute = 1 if j.bins_absolute else 0
     return arr
 
 
@@ -330,6 +334,7 @@ class Graph:
 
 FDD_ERR_SEQUENCE = -8
 FDD_BATCH_SB_FACTORED = 1000
+FDD_BATCH_SB_PERSISTENT = 1001
 FDD_STATUS_TILE_WAIT = 1
 FDD_ERR_TIMEOUT = -10
 FDD_ERR_BUSY = -9
@@ -720,15 +725,65 @@ class Plan:
         _check(_lib_raw().fdd_series_size(self._h, int(n_out), ctypes.byref(v)), "fdd_series_size")
         return int(v.value)
 
-    def series_views(self, series, n_out):
-        """Split a flat series buffer into per-range [n_sb][n_dm][n_out // D] views."""
+    def series_views(self, series, n_out, t0=None):
+        """Split a flat series buffer into per-range [n_sb][n_dm][n_r] views:
+        n_r = n_out // D for fdd_search; with t0 (a window's stream position,
+        fdd_search_window) rows are ceil(n_out / D) apart and hold the
+        window's n_r = ceil((t0 + n_out) / D) - ceil(t0 / D) bins."""
         out, off = [], 0
         for r in self.ranges:
-            nr = int(n_out) // r["downsamp"]
-            k = self.n_sb * r["n_dm"] * nr
-            out.append(series[off:off + k].view(self.n_sb, r["n_dm"], nr))
+            D = int(r["downsamp"])
+            if t0 is None:
+                stride = nr = int(n_out) // D
+            else:
+                stride = -(-int(n_out) // D)
+                nr = -(-(int(t0) + int(n_out)) // D) - (-(-int(t0) // D))
+            k = self.n_sb * r["n_dm"] * stride
+            out.append(series[off:off + k].view(self.n_sb, r["n_dm"], stride)[:, :, :nr])
             off += k
         return out
+
+    def window_sizes(self, n_out):
+        """(n_in, workspace bytes, series bytes) of fdd_search_window windows
+        of n_out outputs (include/fdd.h: fdd_window_sizes)."""
+        n_in, ws, sr = _I64(), _SZ(), _SZ()
+        _check(_lib_raw().fdd_window_sizes(self._h, int(n_out), ctypes.byref(n_in), ctypes.byref(ws),
+                                           ctypes.byref(sr)), "fdd_window_sizes")
+        return int(n_in.value), int(ws.value), int(sr.value)
+
+    def search_window(self, tabs, n_in, n_out, t0, cap=1 << 16, workspace=None, cands=None, count=None,
+                      series=None, want_series=False, stream=None):
+        """One window of a beam's stream (include/fdd.h: fdd_search_window):
+        tabs[..., 0] is stream sample t0; downsampling bins are aligned to the
+        stream.  Buffers not given are allocated with torch on tabs' device."""
+        torch = _torch()
+        if tabs.dim() != 3 or tuple(tabs.shape[:2]) != (self.n_tab, self.n_chan):
+            raise ValueError("tabs must be [n_tab][n_chan][pitch]")
+        dev = tabs.device
+        _, ws_bytes, sr_bytes = self.window_sizes(n_out)
+        if want_series and series is None:
+            series = torch.empty(sr_bytes // 4, dtype=torch.int32, device=dev)
+        if workspace is None:
+            workspace = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+        if cands is None:
+            cands = torch.empty((max(int(cap), 1), 8), dtype=torch.int32, device=dev)
+        if count is None:
+            count = torch.zeros(1, dtype=torch.int64, device=dev)
+        if not isinstance(cands, torch.Tensor) or cands.dtype != torch.int32 or cands.dim() != 2 or \
+                cands.shape[1] != 8:
+            raise TypeError("cands must be an int32 tensor of shape [cap, 8] (32-byte records)")
+        if not isinstance(count, torch.Tensor) or count.dtype != torch.int64 or count.numel() < 1:
+            raise TypeError("count must be an int64 tensor with at least one element")
+        if series is not None and series.numel() * 4 < sr_bytes:
+            raise ValueError("series holds %d bytes; a window writes up to %d" % (series.numel() * 4, sr_bytes))
+        code = _lib_raw().fdd_search_window(
+            self._h, _dev_ptr(tabs, "tabs", torch.uint8), int(n_in), int(tabs.shape[2]), int(n_out), int(t0),
+            _dev_ptr(workspace, "workspace"), int(workspace.numel() * workspace.element_size()),
+            _dev_ptr(cands, "cands"), int(cands.shape[0]), _dev_ptr(count, "count"),
+            _dev_ptr(series, "series", torch.int32) if series is not None else None,
+            _stream_handle(stream))
+        _check(code, "fdd_search_window")
+        return SearchResult(cands=cands, count=count, series=series, cap=int(cands.shape[0]))
 
     # -- the hot path
     def search(self, tabs, n_in, n_out, t_offset=0, cap=1 << 16, workspace=None, cands=None, count=None,
@@ -804,16 +859,23 @@ class Plan:
         return [(self.STAGE_NAMES[int(kind[i])], int(rng[i]), float(ms[i])) for i in range(k)]
 
     # -- batched search
-    def make_job(self, tabs, n_in, n_out, t_offset=0, cap=1 << 16, want_series=False):
-        """Allocate a Job's output buffers and workspace with torch on tabs' device."""
+    def make_job(self, tabs, n_in, n_out, t_offset=0, cap=1 << 16, want_series=False, bins_absolute=False):
+        """Allocate a Job's output buffers and workspace with torch on tabs' device
+        (bins_absolute: a window of a stream at t_offset, sized by window_sizes)."""
         torch = _torch()
         dev = tabs.device
-        series = torch.empty(self.series_size(n_out) // 4, dtype=torch.int32, device=dev) if want_series else None
-        ws = torch.empty(self.workspace_size(n_in, n_out, with_series=series is None), dtype=torch.uint8, device=dev)
+        if bins_absolute:
+            _, ws_b, sr_b = self.window_sizes(n_out)
+            series = torch.empty(sr_b // 4, dtype=torch.int32, device=dev) if want_series else None
+            ws = torch.empty(ws_b, dtype=torch.uint8, device=dev)
+        else:
+            series = torch.empty(self.series_size(n_out) // 4, dtype=torch.int32, device=dev) if want_series else None
+            ws = torch.empty(self.workspace_size(n_in, n_out, with_series=series is None), dtype=torch.uint8,
+                             device=dev)
         cands = torch.empty((max(int(cap), 1), 8), dtype=torch.int32, device=dev)
         count = torch.zeros(1, dtype=torch.int64, device=dev)
         return Job(tabs=tabs, n_in=int(n_in), workspace=ws, cands=cands, count=count, t_offset=int(t_offset),
-                   series=series)
+                   series=series, bins_absolute=bool(bins_absolute))
 
     def batch_prepare(self, n_out, variant=-1):
         _check(_lib_raw().fdd_batch_prepare(self._h, int(n_out), int(variant)), "fdd_batch_prepare")

@@ -77,7 +77,7 @@ __device__ __forceinline__ void boxcar_series(const BoxcarArgs& a, const int64_t
     __shared__ uint32_t s_warp[kThreads / 32];
     __shared__ uint32_t s_total;
 
-    const int n = a.n_out;
+    const int n = a.n_emit;  // samples searched; rows are a.n_out apart
     if (threadIdx.x == 0) {
         const long long sum = static_cast<long long>(a.stat[2 * q]);
         const unsigned long long sq = a.stat[2 * q + 1];
@@ -106,7 +106,7 @@ __device__ __forceinline__ void boxcar_series(const BoxcarArgs& a, const int64_t
     if (!s_ok) return;
 
     const int s = static_cast<int>(q / a.n_dm), i = static_cast<int>(q % a.n_dm);
-    const int32_t* S = a.series + q * n;
+    const int32_t* S = a.series + q * a.n_out;
     const int32_t m0 = s_m0;
     const int seg = (kTile + a.wmax - 1 + kThreads - 1) / kThreads;
     const int lane = threadIdx.x & 31;

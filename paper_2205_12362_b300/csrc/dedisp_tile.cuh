@@ -307,7 +307,7 @@ __device__ __forceinline__ void dedisp_tile(const DedispArgs& a, int tile_x, int
 #pragma unroll
             for (int e = 0; e < SPW; e++) {
                 const int t = t0 + (lane + 32 * k) * SPW + e;
-                if (t < a.n_out) {
+                if (t < a.n_emit) {
                     const uint32_t v = tot[j][k][e];
                     row[t] = static_cast<int32_t>(v);
                     s1 += v;

@@ -42,7 +42,8 @@ struct DedispArgs {
     unsigned long long* stat;   // [n_sb * n_dm][2]: sum S, sum S^2
     int32_t n_chan;
     int32_t n_dm;
-    int32_t n_out;
+    int32_t n_out;              // outputs per series row (the row stride)
+    int32_t n_emit;             // outputs written and counted in the moments: t < n_emit <= n_out
     int32_t n_sb;
     int32_t Lw;                 // 32-bit words per staged copy row
     int32_t CC;                 // channels per smem stage (divides 256 when E == 1)
@@ -94,6 +95,7 @@ struct FactArgs {
     int32_t* series;            // [n_sb][n_dm][n_out]
     unsigned long long* stat;   // [n_sb * n_dm][2]
     int32_t n_chan, n_dm, n_out, n_sb;
+    int32_t n_emit;             // outputs written and counted (<= n_out, the row stride)
     int32_t Lw, CC, n_stages, n_groups, pat_bytes;
     int32_t zero_off;           // shared-memory layout (bytes from the 128-aligned base): zero row,
     int32_t raw_off, rb;        //   raw slots (2 buffers x CC slots of rb bytes),
@@ -151,6 +153,7 @@ struct SbfCombArgs {
     int32_t* series;            // this range: [n_sb][n_dm][n_out]
     unsigned long long* stat;   // this range: [n_sb * n_dm][2]
     int32_t n_sb, n_seg, n_dm, n_out, n_tab;
+    int32_t n_emit;             // outputs written and counted (<= n_out, the row stride)
     int32_t i0, n_slab;
     int32_t flush;              // segments summed in 16-bit lanes between folds
     int32_t uc;                 // segments per shared-memory chunk (sbf_comb_uc)
@@ -177,9 +180,10 @@ struct BoxcarArgs {
     fdd_candidate* cands;
     unsigned long long* count;
     int64_t cap;
-    int64_t t_offset;
+    int64_t t_offset;                   // native sample of series sample 0
     double dm0, ddm;
-    int32_t n_sb, n_dm, n_out;
+    int32_t n_sb, n_dm, n_out;          // n_out: row stride of the series
+    int32_t n_emit;                     // samples of each series searched (<= n_out)
     int32_t dm_index0;
     int32_t D;
     int32_t n_width;
@@ -192,8 +196,10 @@ struct BoxcarArgs {
 cudaError_t launch_boxcar(const BoxcarArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
+// out[row][j] = sum_{k<D} in[row][offset + j*D + k], j < floor((n_in - offset) / D); 0 <= offset < n_in
+// (offset = the bin phase of a window whose bins are aligned to stream sample 0).
 cudaError_t launch_downsample(const uint8_t* in, int64_t n_rows, int64_t n_in, int64_t in_pitch,
-                              int D, uint16_t* out, int64_t out_pitch, cudaStream_t s);
+                              int D, uint16_t* out, int64_t out_pitch, cudaStream_t s, int64_t offset = 0);
 
 // ---------------------------------------------------------------------------
 // Batched search: many chunks ("jobs") of one plan, every range, in one
@@ -220,6 +226,42 @@ struct BatchRange {
     float inv_sqrt_w[FDD_MAX_WIDTHS];
 };
 
+// Persistent SB-factored batch (k_sbf_persist.cu): ONE launch runs the part
+// and comb tasks of every job, range and DM slab.  A job's scratch holds
+// kSbfSlots slab buffers; its groups (range, slab) are issued in the order
+// P0 P1 .. P(S-1) C0 PS C1 P(S+1) C2 ... (S = kSbfSlots), so every task
+// depends only on tasks issued before it: comb tasks of group g wait for
+// g's part tasks, part tasks of group g for the comb tasks of group g - S
+// (the previous user of their buffer).
+constexpr int kSbfSlots = 3;
+struct SbfPersistRange {
+    const int32_t* base;          // part tables of the persistent variant (BD trials per block)
+    const int32_t* off;
+    const int4* stages;
+    const int2* segs;
+    const uint8_t* seg_tab;       // [n_sb][seg_pitch]
+    int64_t slot_elems;           // uint16 elements between slab buffers (the same for every range;
+                                  //   >= n_tab * n_seg * slab * Np)
+    int64_t series_elem_off;      // this range inside a job's series buffer
+    int64_t stat_off;             // first series index of this range inside a job
+    int32_t E, D, ds_index;       // ds_index: -1 raw input, else index into job.ds
+    int32_t Lw, CC, n_stages;
+    int32_t seg_pitch, n_seg, flush;
+    int32_t n_dm, n_out, Np, slab;  // n_out: series row stride; slab: DM rows per slab buffer
+    int32_t part_tiles, comb_tiles, sb_groups;
+};
+struct SbfPersistGroup {
+    int32_t range, i0, n_slab;    // DM rows [i0, i0 + n_slab) of the range
+    int32_t n_part, n_comb;       // tasks
+    int32_t slot;                 // slab buffer
+};
+struct SbfPersistSeg {
+    int32_t start;                // first task of this segment within a job's task list
+    int32_t group;                // group (within the job)
+    int32_t kind;                 // 0 part, 1 comb
+    int32_t count;
+};
+
 struct BatchJob {
     const uint8_t* tabs;          // [n_tab][n_chan][tab_pitch]
     int64_t tab_pitch;
@@ -232,6 +274,9 @@ struct BatchJob {
     int64_t cap;
     unsigned long long* count;
     int64_t t_offset;
+    int32_t emit[kMaxRanges];     // outputs searched per range (<= the range's n_out, the row stride)
+    int32_t ds_phase[kMaxDs];     // first input sample of the downsampling bins, per distinct D
+    uint16_t* sbf_scratch;        // persistent SB-factored mode: the job's kSbfSlots slab buffers
 };
 
 struct BatchParams {
@@ -242,6 +287,14 @@ struct BatchParams {
     int64_t series_per_job;
     int32_t n_range, n_jobs, n_sb, n_chan, n_tab, n_ds;
     int32_t ds_factor[kMaxDs];
+    // persistent SB-factored mode (sp_ranges == nullptr otherwise)
+    const SbfPersistRange* sp_ranges;  // device [n_range]
+    const SbfPersistGroup* sp_groups;  // device [sp_n_groups]: one job's groups
+    const SbfPersistSeg* sp_segs;      // device [sp_n_segs]: one job's task segments, in issue order
+    unsigned int* sp_done;             // [n_jobs][sp_n_groups][2]: part / comb tasks done; zeroed by prep
+    unsigned int* status;              // plan status word (bit 0: a bounded wait gave up)
+    int32_t sp_n_groups, sp_n_segs;
+    int64_t sp_tasks_per_job;
     BatchJob jobs[kMaxBatchJobs];
 };
 
@@ -261,6 +314,14 @@ cudaError_t launch_batch_prep(const BatchParams& p, cudaStream_t s);
 cudaError_t launch_batch_downsample(const BatchParams& p, cudaStream_t s);
 cudaError_t launch_dedisp_persistent(int idx, int E, const BatchParams& p, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_boxcar_batch(const BatchParams& p, int wmax_all, int n_width_max, float thr, cudaStream_t s);
+// Persistent SB-factored batch: the part variant (one per sample width, BD trials, T samples),
+// shared memory of a block, resident blocks per SM, launch.
+DedispVariant sbf_persist_part_variant(int E);
+size_t sbf_persist_smem_bytes(size_t part_smem_max, int n_tab);
+cudaError_t sbf_persist_occupancy(size_t smem, int* blocks_per_sm);
+cudaError_t launch_sbf_persist(const BatchParams& p, int grid, size_t smem, cudaStream_t s);
+int sbf_persist_comb_sbs();       // SBs per comb task
+int sbf_persist_comb_tile();      // output samples per comb task
 
 // ---------------------------------------------------------------------------
 // Library-internal helpers shared between host files.

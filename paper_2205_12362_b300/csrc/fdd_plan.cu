@@ -127,20 +127,52 @@ int fdd::host::upload_tables(int32_t** d_off, int32_t** d_base, const HostTables
     return FDD_OK;
 }
 
-fdd::host::Layout fdd::host::make_layout(const fdd_plan* p, int64_t n_in, int64_t n_out, bool with_series) {
+fdd::host::Bins fdd::host::search_bins(const fdd_plan* p, int64_t n_out, int64_t t0, bool absolute) {
+    Bins b;
+    b.absolute = absolute;
+    for (const RangeState& r : p->ranges) {
+        if (!absolute) {
+            b.stride.push_back(static_cast<int32_t>(n_out / r.D));
+            b.emit.push_back(static_cast<int32_t>(n_out / r.D));
+            b.phase.push_back(0);
+            continue;
+        }
+        const int64_t j_first = (t0 + r.D - 1) / r.D;           // ceil(t0 / D): first bin starting in the window
+        const int64_t j_end = (t0 + n_out + r.D - 1) / r.D;     // ceil((t0 + n_out) / D)
+        b.stride.push_back(static_cast<int32_t>((n_out + r.D - 1) / r.D));
+        b.emit.push_back(static_cast<int32_t>(j_end - j_first));
+        b.phase.push_back(static_cast<int32_t>(j_first * r.D - t0));
+    }
+    for (int32_t D : p->ds_factors) b.ds_phase.push_back(absolute ? static_cast<int32_t>((D - t0 % D) % D) : 0);
+    return b;
+}
+
+int64_t fdd::host::window_input_len(const fdd_plan* p, int64_t n_out) {
+    int64_t extra = 0;
+    for (const RangeState& r : p->ranges)
+        extra = std::max<int64_t>(extra, static_cast<int64_t>(r.D) * (r.dmax + 1) - 1);
+    return n_out + extra;
+}
+
+fdd::host::Layout fdd::host::make_layout(const fdd_plan* p, int64_t n_in, int64_t n_out, bool with_series,
+                                         bool absolute) {
     Layout L;
     size_t series_elems = 0, n_series = 0;
     for (const RangeState& r : p->ranges) {
         L.series_r.push_back(series_elems);
         L.stat_r.push_back(n_series);
-        const size_t nr = static_cast<size_t>(n_out / r.D);
+        const size_t nr = static_cast<size_t>(absolute ? (n_out + r.D - 1) / r.D : n_out / r.D);
         series_elems += static_cast<size_t>(p->n_sb) * r.n_dm * nr;
         n_series += static_cast<size_t>(p->n_sb) * r.n_dm;
     }
     L.series_bytes = series_elems * sizeof(int32_t);
     L.stat_bytes = n_series * 2 * sizeof(unsigned long long);
     size_t cur = 0;
-    L.sbf_bytes = std::max(sbf_scratch_bytes(p, n_out), subband_scratch_bytes(p, n_out));
+    // absolute windows: ceil(n_out / D) <= floor((n_out + D_max - 1) / D) outputs per row
+    const int64_t n_rows = absolute ? n_out + (p->ds_factors.empty() ? 0 : *std::max_element(p->ds_factors.begin(),
+                                                                                               p->ds_factors.end()) - 1)
+                                    : n_out;
+    L.sbf_bytes = std::max(sbf_scratch_bytes(p, n_rows), subband_scratch_bytes(p, n_rows));
     if (L.sbf_bytes) {
         L.sbf = cur;
         cur = align_up(cur + L.sbf_bytes, 256);
@@ -162,7 +194,7 @@ fdd::host::Layout fdd::host::make_layout(const fdd_plan* p, int64_t n_in, int64_
 }
 
 int fdd::host::check_search_args(const fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitch, int64_t n_out,
-                      const void* d_workspace, const void* d_series) {
+                      const void* d_workspace, const void* d_series, const Bins* bins) {
     if (!plan || !d_tabs || !d_workspace || n_in < 0 || n_out < 0 || pitch < n_in)
         return fail(FDD_ERR_INVALID_ARG, "bad search argument");
     if (n_out > (1LL << 30) || n_in > (1LL << 31) - 64)
@@ -170,6 +202,16 @@ int fdd::host::check_search_args(const fdd_plan* plan, const uint8_t* d_tabs, in
     if ((reinterpret_cast<uintptr_t>(d_tabs) & 15) || (pitch & 15) ||
         (reinterpret_cast<uintptr_t>(d_workspace) & 255) || (reinterpret_cast<uintptr_t>(d_series) & 15))
         return fail(FDD_ERR_MISALIGNED, "d_tabs/pitch must be 16-byte aligned, workspace 256-byte aligned");
+    if (bins && bins->absolute) {
+        for (size_t ri = 0; ri < plan->ranges.size(); ri++) {
+            const RangeState& r = plan->ranges[ri];
+            if (bins->emit[ri] > 0 &&
+                bins->phase[ri] + static_cast<int64_t>(r.D) * (bins->emit[ri] + static_cast<int64_t>(r.dmax)) > n_in)
+                return fail(FDD_ERR_SHORT_INPUT, "n_in < phase + D * (bins + max delay) for some DM range "
+                                                 "(fdd_window_input_len)");
+        }
+        return FDD_OK;
+    }
     for (const RangeState& r : plan->ranges)
         if (n_out / r.D + r.dmax > n_in / r.D)
             return fail(FDD_ERR_SHORT_INPUT, "n_in < n_out + max delay for some DM range");
@@ -297,6 +339,7 @@ cudaError_t launch_range_dedisp(const fdd_plan* p, const RangeState& r, const fd
     fa.n_chan = a.n_chan;
     fa.n_dm = a.n_dm;
     fa.n_out = a.n_out;
+    fa.n_emit = a.n_emit;
     fa.n_sb = a.n_sb;
     fa.Lw = r.f_Lw;
     fa.CC = r.f_CC;
@@ -335,7 +378,7 @@ int default_variant(int E) {
 
 fdd::DedispArgs dedisp_args(const fdd_plan* plan, const RangeState& r, size_t ri, const Layout& L,
                             const uint8_t* d_tabs, int64_t pitch, uint8_t* ws, int32_t* series,
-                            unsigned long long* stat, int64_t n_in, int64_t n_out) {
+                            unsigned long long* stat, int64_t n_in, const Bins& bins) {
     fdd::DedispArgs a{};
     if (r.D == 1) {
         a.in = d_tabs;
@@ -345,7 +388,7 @@ fdd::DedispArgs dedisp_args(const fdd_plan* plan, const RangeState& r, size_t ri
         a.in = ws + L.ds_off[k];
         a.pitch_bytes = L.ds_pitch[k] * 2;
     }
-    a.n_valid = n_in / r.D;
+    a.n_valid = (n_in - bins.phase[ri]) / r.D;
     a.sb_map = plan->d_sb_map;
     a.base = r.d_base;
     a.off = r.d_off;
@@ -353,7 +396,8 @@ fdd::DedispArgs dedisp_args(const fdd_plan* plan, const RangeState& r, size_t ri
     a.stat = stat + 2 * L.stat_r[ri];
     a.n_chan = plan->n_chan;
     a.n_dm = r.n_dm;
-    a.n_out = static_cast<int32_t>(n_out / r.D);
+    a.n_out = bins.stride[ri];
+    a.n_emit = bins.emit[ri];
     a.n_sb = plan->n_sb;
     a.Lw = r.Lw;
     a.CC = r.CC;
@@ -460,6 +504,90 @@ static int build_host_plan(const fdd_plan_desc* desc, const int16_t* sb_map_host
 
     return FDD_OK;
 }
+
+int fdd::host::search_impl(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitch, int64_t n_out,
+                           int64_t t_offset_native, bool absolute, void* d_workspace, size_t workspace_bytes,
+                           fdd_candidate* d_cands, int64_t cap, uint64_t* d_count, int32_t* d_series, cudaStream_t s) {
+    if (!d_count || (cap > 0 && !d_cands) || cap < 0) return fail(FDD_ERR_INVALID_ARG, "bad search argument");
+    if (!plan) return fail(FDD_ERR_INVALID_ARG, "bad search argument");
+    if (absolute && t_offset_native < 0) return fail(FDD_ERR_INVALID_ARG, "window start must be >= 0");
+    // a window reads no more than fdd_window_sizes' n_in (its workspace is sized for that)
+    if (absolute && n_in > window_input_len(plan, n_out)) n_in = window_input_len(plan, n_out);
+    const Bins bins = search_bins(plan, n_out, t_offset_native, absolute);
+    {
+        const int rc = check_search_args(plan, d_tabs, n_in, pitch, n_out, d_workspace, d_series, &bins);
+        if (rc != FDD_OK) return rc;
+    }
+    const bool own_series = (d_series == nullptr);
+    const Layout L = make_layout(plan, n_in, n_out, own_series, absolute);
+    if (workspace_bytes < L.total) return fail(FDD_ERR_WORKSPACE, "workspace smaller than fdd_workspace_size()");
+
+    uint8_t* ws = static_cast<uint8_t*>(d_workspace);
+    fdd::host::stage_reset(plan);
+    auto stage_begin = [&](int kind, int range) { return fdd::host::stage_begin(plan, kind, range, s); };
+    auto stage_end = [&]() { return fdd::host::stage_end(plan, s); };
+    int32_t* series = own_series ? reinterpret_cast<int32_t*>(ws + L.series) : d_series;
+    unsigned long long* stat = reinterpret_cast<unsigned long long*>(ws + L.stat);
+
+    cudaError_t e = cudaMemsetAsync(stat, 0, L.stat_bytes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(stat)");
+    e = cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(count)");
+
+    int64_t n_launch = 0;
+    plan->last_launches = 0;
+    for (size_t k = 0; k < plan->ds_factors.size(); k++) {
+        n_launch++;
+        if ((e = stage_begin(0, plan->ds_factors[k])) != cudaSuccess) return cuda_fail(e, "timing event");
+        e = fdd::launch_downsample(d_tabs, static_cast<int64_t>(plan->n_tab) * plan->n_chan, n_in, pitch,
+                                   plan->ds_factors[k], reinterpret_cast<uint16_t*>(ws + L.ds_off[k]),
+                                   L.ds_pitch[k], s, bins.ds_phase[k]);
+        if (e != cudaSuccess) return cuda_fail(e, "downsample launch");
+        if ((e = stage_end()) != cudaSuccess) return cuda_fail(e, "timing event");
+    }
+
+    for (size_t ri = 0; ri < plan->ranges.size(); ri++) {
+        const RangeState& r = plan->ranges[ri];
+        const int64_t nr = bins.emit[ri];
+        if (nr <= 0) continue;
+        const fdd::DedispArgs a = dedisp_args(plan, r, ri, L, d_tabs, pitch, ws, series, stat, n_in, bins);
+        if ((e = stage_begin(1, static_cast<int>(ri))) != cudaSuccess) return cuda_fail(e, "timing event");
+        e = launch_range(plan, r, a, L, ws, s, &n_launch);
+        if (e != cudaSuccess) return cuda_fail(e, "dedispersion launch");
+        if ((e = stage_end()) != cudaSuccess) return cuda_fail(e, "timing event");
+
+        fdd::BoxcarArgs b{};
+        b.series = a.series;
+        b.stat = a.stat;
+        b.cands = d_cands;
+        b.count = reinterpret_cast<unsigned long long*>(d_count);
+        b.cap = cap;
+        b.t_offset = t_offset_native + bins.phase[ri];
+        b.dm0 = r.dm0;
+        b.ddm = r.ddm;
+        b.n_sb = plan->n_sb;
+        b.n_dm = r.n_dm;
+        b.n_out = bins.stride[ri];
+        b.n_emit = static_cast<int32_t>(nr);
+        b.dm_index0 = r.dm_index0;
+        b.D = r.D;
+        b.n_width = r.n_width;
+        b.wmax = r.wmax;
+        b.thr = plan->thr;
+        for (int k = 0; k < r.n_width; k++) {
+            b.widths[k] = r.widths[k];
+            b.inv_sqrt_w[k] = static_cast<float>(1.0 / std::sqrt(static_cast<double>(r.widths[k])));
+        }
+        if ((e = stage_begin(2, static_cast<int>(ri))) != cudaSuccess) return cuda_fail(e, "timing event");
+        e = fdd::launch_boxcar(b, s);
+        if (e != cudaSuccess) return cuda_fail(e, "boxcar launch");
+        n_launch++;
+        if ((e = stage_end()) != cudaSuccess) return cuda_fail(e, "timing event");
+    }
+    plan->last_launches = n_launch;
+    return FDD_OK;
+}
+
 
 extern "C" {
 
@@ -594,78 +722,24 @@ int fdd_series_size(const fdd_plan* plan, int64_t n_out, size_t* bytes) {
 int fdd_search(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitch, int64_t n_out,
                int64_t t_offset_native, void* d_workspace, size_t workspace_bytes, fdd_candidate* d_cands,
                int64_t cap, uint64_t* d_count, int32_t* d_series, fdd_stream_t stream) {
-    if (!d_count || (cap > 0 && !d_cands) || cap < 0) return fail(FDD_ERR_INVALID_ARG, "bad search argument");
-    {
-        const int rc = check_search_args(plan, d_tabs, n_in, pitch, n_out, d_workspace, d_series);
-        if (rc != FDD_OK) return rc;
-    }
-    const bool own_series = (d_series == nullptr);
-    const Layout L = make_layout(plan, n_in, n_out, own_series);
-    if (workspace_bytes < L.total) return fail(FDD_ERR_WORKSPACE, "workspace smaller than fdd_workspace_size()");
+    return search_impl(plan, d_tabs, n_in, pitch, n_out, t_offset_native, false, d_workspace, workspace_bytes,
+                       d_cands, cap, d_count, d_series, reinterpret_cast<cudaStream_t>(stream));
+}
 
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    uint8_t* ws = static_cast<uint8_t*>(d_workspace);
-    fdd::host::stage_reset(plan);
-    auto stage_begin = [&](int kind, int range) { return fdd::host::stage_begin(plan, kind, range, s); };
-    auto stage_end = [&]() { return fdd::host::stage_end(plan, s); };
-    int32_t* series = own_series ? reinterpret_cast<int32_t*>(ws + L.series) : d_series;
-    unsigned long long* stat = reinterpret_cast<unsigned long long*>(ws + L.stat);
+int fdd_search_window(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitch, int64_t n_out,
+                      int64_t t0_native, void* d_workspace, size_t workspace_bytes, fdd_candidate* d_cands,
+                      int64_t cap, uint64_t* d_count, int32_t* d_series, fdd_stream_t stream) {
+    return search_impl(plan, d_tabs, n_in, pitch, n_out, t0_native, true, d_workspace, workspace_bytes, d_cands,
+                       cap, d_count, d_series, reinterpret_cast<cudaStream_t>(stream));
+}
 
-    cudaError_t e = cudaMemsetAsync(stat, 0, L.stat_bytes, s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(stat)");
-    e = cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(count)");
-
-    int64_t n_launch = 0;
-    plan->last_launches = 0;
-    for (size_t k = 0; k < plan->ds_factors.size(); k++) {
-        n_launch++;
-        if ((e = stage_begin(0, plan->ds_factors[k])) != cudaSuccess) return cuda_fail(e, "timing event");
-        e = fdd::launch_downsample(d_tabs, static_cast<int64_t>(plan->n_tab) * plan->n_chan, n_in, pitch,
-                                   plan->ds_factors[k], reinterpret_cast<uint16_t*>(ws + L.ds_off[k]),
-                                   L.ds_pitch[k], s);
-        if (e != cudaSuccess) return cuda_fail(e, "downsample launch");
-        if ((e = stage_end()) != cudaSuccess) return cuda_fail(e, "timing event");
-    }
-
-    for (size_t ri = 0; ri < plan->ranges.size(); ri++) {
-        const RangeState& r = plan->ranges[ri];
-        const int64_t nr = n_out / r.D;
-        if (nr == 0) continue;
-        const fdd::DedispArgs a = dedisp_args(plan, r, ri, L, d_tabs, pitch, ws, series, stat, n_in, n_out);
-        if ((e = stage_begin(1, static_cast<int>(ri))) != cudaSuccess) return cuda_fail(e, "timing event");
-        e = launch_range(plan, r, a, L, ws, s, &n_launch);
-        if (e != cudaSuccess) return cuda_fail(e, "dedispersion launch");
-        if ((e = stage_end()) != cudaSuccess) return cuda_fail(e, "timing event");
-
-        fdd::BoxcarArgs b{};
-        b.series = a.series;
-        b.stat = a.stat;
-        b.cands = d_cands;
-        b.count = reinterpret_cast<unsigned long long*>(d_count);
-        b.cap = cap;
-        b.t_offset = t_offset_native;
-        b.dm0 = r.dm0;
-        b.ddm = r.ddm;
-        b.n_sb = plan->n_sb;
-        b.n_dm = r.n_dm;
-        b.n_out = static_cast<int32_t>(nr);
-        b.dm_index0 = r.dm_index0;
-        b.D = r.D;
-        b.n_width = r.n_width;
-        b.wmax = r.wmax;
-        b.thr = plan->thr;
-        for (int k = 0; k < r.n_width; k++) {
-            b.widths[k] = r.widths[k];
-            b.inv_sqrt_w[k] = static_cast<float>(1.0 / std::sqrt(static_cast<double>(r.widths[k])));
-        }
-        if ((e = stage_begin(2, static_cast<int>(ri))) != cudaSuccess) return cuda_fail(e, "timing event");
-        e = fdd::launch_boxcar(b, s);
-        if (e != cudaSuccess) return cuda_fail(e, "boxcar launch");
-        n_launch++;
-        if ((e = stage_end()) != cudaSuccess) return cuda_fail(e, "timing event");
-    }
-    plan->last_launches = n_launch;
+int fdd_window_sizes(const fdd_plan* plan, int64_t n_out, int64_t* n_in, size_t* workspace_bytes,
+                     size_t* series_bytes) {
+    if (!plan || n_out < 0) return fail(FDD_ERR_INVALID_ARG, "bad argument");
+    const int64_t need = window_input_len(plan, n_out);
+    if (n_in) *n_in = need;
+    if (workspace_bytes) *workspace_bytes = make_layout(plan, need, n_out, true, true).total;
+    if (series_bytes) *series_bytes = make_layout(plan, need, n_out, true, true).series_bytes;
     return FDD_OK;
 }
 
@@ -773,6 +847,7 @@ int fdd_plan_autotune(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64
     }
     if (reps < 1) reps = 1;
     const Layout L = make_layout(plan, n_in, n_out, true);
+    const Bins bins = search_bins(plan, n_out, 0, false);
     if (workspace_bytes < L.total) return fail(FDD_ERR_WORKSPACE, "workspace smaller than fdd_workspace_size()");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     uint8_t* ws = static_cast<uint8_t*>(d_workspace);
@@ -814,7 +889,7 @@ int fdd_plan_autotune(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64
                 r.variant = v;
                 r.Lw = h.Lw;
                 r.CC = cc;
-                const fdd::DedispArgs a = dedisp_args(plan, r, ri, L, d_tabs, pitch, ws, series, stat, n_in, n_out);
+                const fdd::DedispArgs a = dedisp_args(plan, r, ri, L, d_tabs, pitch, ws, series, stat, n_in, bins);
                 if ((e = fdd::launch_dedisp(v, a, s)) != cudaSuccess) { rc = cuda_fail(e, "tuning launch"); break; }
                 cudaEventRecord(ev0, s);
                 for (int k = 0; k < reps && e == cudaSuccess; k++) e = fdd::launch_dedisp(v, a, s);
@@ -837,7 +912,7 @@ int fdd_plan_autotune(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64
         for (int fv = 0; E == 1 && fv < fdd::num_fact_variants() && rc == FDD_OK; fv++) {
             for (int cc : {16, 32, 48, 64}) {
                 if (configure_fact(plan, r, fv, cc) != FDD_OK) continue;  // does not fit
-                const fdd::DedispArgs a = dedisp_args(plan, r, ri, L, d_tabs, pitch, ws, series, stat, n_in, n_out);
+                const fdd::DedispArgs a = dedisp_args(plan, r, ri, L, d_tabs, pitch, ws, series, stat, n_in, bins);
                 if ((e = launch_range_dedisp(plan, r, a, s)) != cudaSuccess) { rc = cuda_fail(e, "tuning launch"); break; }
                 cudaEventRecord(ev0, s);
                 for (int k = 0; k < reps && e == cudaSuccess; k++) e = launch_range_dedisp(plan, r, a, s);
@@ -864,7 +939,7 @@ int fdd_plan_autotune(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64
             if (fdd::sbf_variant(sv).E != E) continue;
             for (int cc : {16, 32, 48, 64}) {
                 if (configure_range(plan, r, nbf + sv, cc) != FDD_OK) continue;  // does not fit
-                const fdd::DedispArgs a = dedisp_args(plan, r, ri, L, d_tabs, pitch, ws, series, stat, n_in, n_out);
+                const fdd::DedispArgs a = dedisp_args(plan, r, ri, L, d_tabs, pitch, ws, series, stat, n_in, bins);
                 if ((e = launch_range(plan, r, a, L, ws, s)) != cudaSuccess) { rc = cuda_fail(e, "tuning launch"); break; }
                 cudaEventRecord(ev0, s);
                 for (int k = 0; k < reps && e == cudaSuccess; k++) e = launch_range(plan, r, a, L, ws, s);

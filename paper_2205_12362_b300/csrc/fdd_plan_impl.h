@@ -69,8 +69,18 @@ struct BatchRangeTables {
 struct BatchState {
     int variant = -1;                      // persistent kernel variant
     bool sbf = false;                      // every range through its SB-factored configuration instead
+    bool sbp = false;                      // persistent SB-factored mode (one launch, k_sbf_persist.cu)
+    fdd::SbfPersistRange* d_sp_ranges = nullptr;
+    fdd::SbfPersistGroup* d_sp_groups = nullptr;
+    fdd::SbfPersistSeg* d_sp_segs = nullptr;
+    unsigned int* d_sp_done = nullptr;     // [FDD_MAX_BATCH_JOBS][groups][2]
+    int32_t sp_n_groups = 0, sp_n_segs = 0;
+    int64_t sp_tasks_per_job = 0;
+    int sp_grid = 0;
+    size_t sp_smem = 0;
     bool big_stages = false;               // channel stages sized to the full shared-memory budget
     int64_t n_out = -1;                    // chunk length the tables below were prepared for
+    bool absolute = false;                 // prepared for windows whose bins are aligned to their stream
     std::vector<BatchRangeTables> tables;  // per range
     fdd::BatchRange* d_ranges = nullptr;   // device copy of the per-range descriptors
     std::vector<fdd::BatchRange> h_ranges;
@@ -154,7 +164,25 @@ struct Layout {
     std::vector<int64_t> ds_pitch;  // uint16 elements
     size_t total = 0;
 };
-Layout make_layout(const fdd_plan* p, int64_t n_in, int64_t n_out, bool with_series);
+// Series rows are floor(n_out / D_r) long (bins from input sample 0), or
+// ceil(n_out / D_r) in a window whose bins are aligned to its stream
+// (`absolute`), which holds one bin more when its phase allows.
+Layout make_layout(const fdd_plan* p, int64_t n_in, int64_t n_out, bool with_series, bool absolute = false);
+
+// Downsampling bins of one search (Sec. "Downsampling").  Plain: bins from
+// input sample 0, floor(n_out / D) outputs per range.  Absolute: input sample
+// 0 is stream sample t0 and bins are aligned to stream sample 0; range r
+// searches the bins starting in [t0, t0 + n_out), read from input sample
+// phase = ceil(t0 / D) D - t0 on.
+struct Bins {
+    bool absolute = false;
+    std::vector<int32_t> stride, emit, phase;  // per range: row stride, outputs searched, first input sample
+    std::vector<int32_t> ds_phase;             // per distinct D (plan order)
+};
+Bins search_bins(const fdd_plan* p, int64_t n_out, int64_t t0, bool absolute);
+// Input samples an absolute-bin window of n_out outputs needs at any start:
+// n_out + max_r (D_r (max delay_r + 1) - 1).
+int64_t window_input_len(const fdd_plan* p, int64_t n_out);
 // SB-factored kernel (fdd_sbf.cu).
 constexpr size_t kSbfScratchMax = size_t(4) << 30;
 std::vector<int2> sbf_segments(const fdd_plan* p, int D, int cap);
@@ -182,7 +210,14 @@ int restore_range_config(fdd_plan* p, RangeState& r, int variant, int CC);
 int configure_sbf_default(fdd_plan* p, RangeState& r);
 
 int check_search_args(const fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitch, int64_t n_out,
-                      const void* d_workspace, const void* d_series);
+                      const void* d_workspace, const void* d_series, const Bins* bins = nullptr);
+// Prepare the plan's batched search for n_out and a bin mode, keeping its
+// (possibly tuned) configuration; nothing if already prepared so.
+int batch_prepare_mode(fdd_plan* plan, int64_t n_out, bool absolute);
+// The search of fdd_search (absolute = false) and fdd_search_window.
+int search_impl(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64_t pitch, int64_t n_out, int64_t t_offset,
+                bool absolute, void* d_workspace, size_t workspace_bytes, fdd_candidate* d_cands, int64_t cap,
+                uint64_t* d_count, int32_t* d_series, cudaStream_t s);
 
 }  // namespace host
 }  // namespace fdd

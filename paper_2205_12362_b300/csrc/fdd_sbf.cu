@@ -70,6 +70,8 @@ size_t sbf_scratch_bytes(const fdd_plan* p, int64_t n_out) {
         const size_t full = per_trial * static_cast<size_t>(round_up64(r.n_dm, 64));
         const size_t one_block = per_trial * 64;
         bytes = std::max(bytes, std::min(full, std::max(p->sbf_scratch_cap, one_block)));
+        // the persistent batched mode keeps kSbfSlots slabs of 32 trials (+ 1 KB alignment per slab)
+        bytes = std::max(bytes, (per_trial * 32 + 2048) * static_cast<size_t>(fdd::kSbfSlots));
     }
     return align_up(bytes, 256);
 }
@@ -204,6 +206,7 @@ cudaError_t launch_range_sbf(const fdd_plan* p, const RangeState& r, const fdd::
     ca.n_seg = static_cast<int32_t>(n_seg);
     ca.n_dm = r.n_dm;
     ca.n_out = a.n_out;
+    ca.n_emit = a.n_emit;
     ca.flush = r.s_flush;
     ca.n_tab = p->n_tab;
     ca.uc = fdd::sbf_comb_uc(p->n_tab);

@@ -5,8 +5,11 @@
 // they arrive, each output needing the next max-delay of input (Sec. "AMBER";
 // Sec. "Computing performance": real time over a whole observation).  Here:
 //   * every beam owns two device window buffers [n_tab][n_chan][pitch]; a
-//     window of n_in = chunk + max_delay samples is searched for `chunk`
-//     outputs.  When window w is complete its tail is copied device-to-device
+//     window of n_in = chunk + max delay (+ D - 1) samples starting at w*chunk
+//     is searched for the outputs whose first sample lies in
+//     [w*chunk, (w+1)*chunk), with downsampling bins aligned to the beam's
+//     stream (fdd_search_window), so the windows tile one search of the
+//     whole stream.  When window w is complete its tail is copied device-to-device
 //     to the other buffer, where window w+1 is assembled from the following
 //     chunks (host-to-device 2-D copies on the copy stream);
 //   * complete windows wait in a FIFO; "slots" (workspace + candidate buffer
@@ -224,9 +227,9 @@ int launch_plain(fdd_server* s, const ServeWindow& w, ServeSlot& sl, cudaStream_
     cudaError_t e = cudaMemsetAsync(sl.d_count, 0, sizeof(uint64_t), cs);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     for (size_t k = 0; k < s->sb_plans.size(); k++) {
-        const int rc = fdd_search(s->sb_plans[k], b.buf[w.buf], s->n_in, s->pitch, s->d.chunk_len,
-                                  w.window * s->d.chunk_len, sl.ws, s->ws_bytes, sl.d_sb_cands, s->d.cap_per_window,
-                                  sl.d_sb_count, nullptr, reinterpret_cast<fdd_stream_t>(cs));
+        const int rc = search_impl(s->sb_plans[k], b.buf[w.buf], s->n_in, s->pitch, s->d.chunk_len,
+                                   w.window * s->d.chunk_len, true, sl.ws, s->ws_bytes, sl.d_sb_cands,
+                                   s->d.cap_per_window, sl.d_sb_count, nullptr, cs);
         if (rc != FDD_OK) return rc;
         k_append_sb<<<1, 256, 0, cs>>>(sl.d_sb_cands, sl.d_sb_count, s->d.cap_per_window, sl.d_cands, sl.d_count,
                                        s->d.cap_per_window, static_cast<int32_t>(k));
@@ -272,6 +275,7 @@ int schedule(fdd_server* s, double t) {
             j.cap = s->d.cap_per_window;
             j.d_count = sl.d_count;
             j.d_series = nullptr;
+            j.bins_absolute = 1;
             batch.wins.push_back(w);
         }
         int rc = s->sb_plans.empty()
@@ -324,17 +328,12 @@ int fdd_server_create(fdd_plan* plan, const fdd_server_desc* desc, fdd_server** 
     s->rows = static_cast<int64_t>(plan->n_tab) * plan->n_chan;
     // A window holds chunk + max delay samples; chunks arrive whole, so the
     // buffer holds a whole number of chunks.
-    s->n_in = desc->chunk_len + plan->max_delay_native;
+    s->n_in = window_input_len(plan, desc->chunk_len);
     const int64_t chunks_per_window = (s->n_in + desc->chunk_len - 1) / desc->chunk_len;
     s->buf_len = chunks_per_window * desc->chunk_len;
     s->pitch = static_cast<int64_t>(align_up(static_cast<size_t>(s->buf_len), 16));
-    size_t sz = 0;
-    int rc = fdd_workspace_size(plan, s->n_in, desc->chunk_len, 1, &sz);
-    if (rc != FDD_OK) {
-        destroy_server(s);
-        return rc;
-    }
-    s->ws_bytes = sz;
+    int rc = FDD_OK;
+    s->ws_bytes = make_layout(plan, s->n_in, desc->chunk_len, true, true).total;
     const size_t ring_bytes = static_cast<size_t>(s->rows) * s->pitch;
     const size_t slot_bytes = s->ws_bytes + sizeof(fdd_candidate) * desc->cap_per_window + 256;
     // Admission by free HBM: rings for every beam first, then as many slots
@@ -355,7 +354,7 @@ int fdd_server_create(fdd_plan* plan, const fdd_server_desc* desc, fdd_server** 
         destroy_server(s);
         return fail(FDD_ERR_NO_MEMORY, "free HBM does not hold the beams' rings and one search slot");
     }
-    if (plan->batch.n_out != desc->chunk_len && (rc = fdd_batch_prepare(plan, desc->chunk_len, -1)) != FDD_OK) {
+    if ((rc = batch_prepare_mode(plan, desc->chunk_len, true)) != FDD_OK) {
         destroy_server(s);
         return rc;
     }
@@ -403,13 +402,11 @@ int fdd_server_set_plain(fdd_server* s, fdd_plan* const* sb_plans, int32_t n_sb)
     for (int32_t k = 0; k < n_sb; k++) {
         const fdd_plan* q = sb_plans[k];
         if (!q || q->n_sb != 1 || q->n_tab != s->plan->n_tab || q->n_chan != s->plan->n_chan ||
-            q->max_delay_native > s->plan->max_delay_native)
+            window_input_len(q, s->d.chunk_len) > s->n_in)
             return fail(FDD_ERR_INVALID_ARG, "each plan must be a single-SB plan of the server's TABs and channels, "
                                              "with no larger delay");
-        size_t need = 0;
-        const int rc = fdd_workspace_size(q, s->n_in, s->d.chunk_len, 1, &need);
-        if (rc != FDD_OK) return rc;
-        if (need > s->ws_bytes) return fail(FDD_ERR_WORKSPACE, "a single-SB plan needs more workspace than a slot has");
+        if (make_layout(q, s->n_in, s->d.chunk_len, true, true).total > s->ws_bytes)
+            return fail(FDD_ERR_WORKSPACE, "a single-SB plan needs more workspace than a slot has");
     }
     for (ServeSlot& sl : s->slots) {
         cudaError_t e;

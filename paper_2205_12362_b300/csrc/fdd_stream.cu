@@ -5,9 +5,11 @@
 //
 // The paper's pipeline searches each 1.024 s chunk of a compound beam with
 // the following max-delay of data appended (Sec. "AMBER"; Sec. "Computing
-// performance").  Here window w searches native outputs [w*L, (w+1)*L) of
-// the beam (L = chunk length) from the L + max_delay samples that start at
-// w*L.  Two device buffers of a whole number of chunks alternate: when the
+// performance").  Here window w searches the outputs of the beam whose first
+// native sample lies in [w*L, (w+1)*L) (L = chunk length), from the samples
+// that start at w*L, with every range's downsampling bins aligned to the
+// beam's stream (fdd_search_window), so the windows tile one search of the
+// whole stream.  Two device buffers of a whole number of chunks alternate: when the
 // current one is full its window is searched, then its last buf_len - L
 // samples are copied to the other buffer, which continues the stream.  All
 // work of a push is enqueued on the caller's CUDA stream; an event recorded
@@ -84,14 +86,10 @@ int fdd_stream_open(fdd_plan* plan, int32_t beam_id, int64_t chunk_len, int64_t 
     st->L = chunk_len;
     st->cap = cap;
     st->rows = static_cast<int64_t>(plan->n_tab) * plan->n_chan;
-    st->n_in = chunk_len + plan->max_delay_native;
+    st->n_in = window_input_len(plan, chunk_len);
     st->buf_len = (st->n_in + chunk_len - 1) / chunk_len * chunk_len;
     st->pitch = static_cast<int64_t>(align_up(static_cast<size_t>(st->buf_len), 16));
-    int rc = fdd_workspace_size(plan, st->n_in, chunk_len, 1, &st->ws_bytes);
-    if (rc != FDD_OK) {
-        destroy_stream(st);
-        return rc;
-    }
+    st->ws_bytes = make_layout(plan, st->n_in, chunk_len, true, true).total;
     const size_t buf_bytes = static_cast<size_t>(st->rows) * st->pitch;
     cudaError_t e;
     for (uint8_t*& b : st->buf)
@@ -125,8 +123,8 @@ int fdd_stream_push(fdd_stream* st, const uint8_t* d_chunk, int64_t chunk_pitch,
     st->held += st->L;
     st->next_seq++;
     if (st->held == st->buf_len) {
-        const int rc = fdd_search(st->plan, st->buf[st->cur], st->n_in, st->pitch, st->L, st->window * st->L, st->ws,
-                                  st->ws_bytes, st->d_cands, st->cap, st->d_count, nullptr, stream);
+        const int rc = search_impl(st->plan, st->buf[st->cur], st->n_in, st->pitch, st->L, st->window * st->L, true,
+                                   st->ws, st->ws_bytes, st->d_cands, st->cap, st->d_count, nullptr, s);
         if (rc != FDD_OK) return rc;
         st->result_t0 = st->window * st->L;
         st->result_new = true;

@@ -27,11 +27,18 @@ __global__ void __launch_bounds__(256) k_batch_prep(const __grid_constant__ Batc
     const BatchJob& J = p.jobs[blockIdx.y];
     const int64_t words = 2 * p.series_per_job;
     for (int64_t i = blockIdx.x * 256LL + threadIdx.x; i < words; i += 256LL * gridDim.x) J.stat[i] = 0ULL;
+    if (p.sp_done) {  // task counters of the persistent SB-factored launch, this job's part
+        const int64_t n = 2LL * p.sp_n_groups;
+        unsigned int* d = p.sp_done + blockIdx.y * n;
+        for (int64_t i = blockIdx.x * 256LL + threadIdx.x; i < n; i += 256LL * gridDim.x) d[i] = 0u;
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *J.count = 0ULL;
         if (blockIdx.y == 0) {
-            p.counter[0] = 0ULL;
-            p.counter[1] = 0ULL;
+            p.counter[0] = 0ULL;  // work items, raw ranges
+            p.counter[1] = 0ULL;  // work items, downsampled ranges
+            p.counter[2] = 0ULL;  // persistent SB-factored tasks
+            p.counter[3] = 0ULL;  // persistent SB-factored abort flag
         }
     }
 }
@@ -40,11 +47,12 @@ __global__ void __launch_bounds__(256) k_batch_downsample(const __grid_constant_
     const int job = blockIdx.z / p.n_ds, k = blockIdx.z - job * p.n_ds;
     const BatchJob& J = p.jobs[job];
     const int D = p.ds_factor[k];
-    const int64_t n_y = J.n_in / D;
+    const int phase = J.ds_phase[k];
+    const int64_t n_y = (J.n_in - phase) / D;
     const int64_t j0 = 8 * (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
     if (j0 >= n_y) return;
     for (int64_t row = blockIdx.y; row < rows; row += gridDim.y)
-        detail::downsample_chunk(J.tabs + row * J.tab_pitch, J.ds[k] + row * J.ds_pitch[k], n_y, D, j0);
+        detail::downsample_chunk(J.tabs + row * J.tab_pitch + phase, J.ds[k] + row * J.ds_pitch[k], n_y, D, j0);
 }
 
 template <int E, int NW, int DPW, int WARPS, int MAXIT>
@@ -81,7 +89,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_dedisp_persistent(const __grid_c
             a.in = reinterpret_cast<const uint8_t*>(J.ds[R.ds_index]);
             a.pitch_bytes = J.ds_pitch[R.ds_index] * 2;
         }
-        a.n_valid = J.n_in / R.D;
+        a.n_valid = (J.n_in - (R.ds_index < 0 ? 0 : J.ds_phase[R.ds_index])) / R.D;
         a.sb_map = p.sb_map;
         a.base = R.base;
         a.off = R.off;
@@ -90,6 +98,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_dedisp_persistent(const __grid_c
         a.n_chan = p.n_chan;
         a.n_dm = R.n_dm;
         a.n_out = R.n_out;
+        a.n_emit = J.emit[r];
         a.n_sb = p.n_sb;
         a.Lw = R.Lw;
         a.CC = R.CC;
@@ -107,18 +116,20 @@ __global__ void __launch_bounds__(detail::kThreads) k_boxcar_batch(const __grid_
     q -= R.series_off;
     if (R.n_out == 0) return;
     const BatchJob& J = p.jobs[job];
+    if (J.emit[r] <= 0) return;
     BoxcarArgs a;
     a.series = J.series + R.series_elem_off;
     a.stat = J.stat + 2 * R.series_off;
     a.cands = J.cands;
     a.count = J.count;
     a.cap = J.cap;
-    a.t_offset = J.t_offset;
+    a.t_offset = J.t_offset + (R.ds_index < 0 ? 0 : J.ds_phase[R.ds_index]);
     a.dm0 = R.dm0;
     a.ddm = R.ddm;
     a.n_sb = p.n_sb;
     a.n_dm = R.n_dm;
     a.n_out = R.n_out;
+    a.n_emit = J.emit[r];
     a.dm_index0 = R.dm_index0;
     a.D = R.D;
     a.n_width = R.n_width;
@@ -147,6 +158,7 @@ __global__ void __launch_bounds__(detail::kBoxWarps * 32)
     q -= R.series_off;
     if (R.n_out == 0) return;
     const BatchJob& J = p.jobs[job];
+    if (J.emit[r] <= 0) return;  // warp-uniform
     const int i = static_cast<int>(q % R.n_dm);
     detail::BoxSeries v;
     v.S = J.series + R.series_elem_off + q * R.n_out;
@@ -155,9 +167,9 @@ __global__ void __launch_bounds__(detail::kBoxWarps * 32)
     v.cands = J.cands;
     v.count = J.count;
     v.cap = J.cap;
-    v.t_offset = J.t_offset;
+    v.t_offset = J.t_offset + (R.ds_index < 0 ? 0 : J.ds_phase[R.ds_index]);
     v.dm = R.dm0 + static_cast<double>(i) * R.ddm;
-    v.n = R.n_out;
+    v.n = J.emit[r];
     v.n_width = R.n_width;
     v.sb = static_cast<int>(q / R.n_dm);
     v.dm_index = R.dm_index0 + i;

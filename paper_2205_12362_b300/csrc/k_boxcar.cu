@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(detail::kBoxWarps * 32) k_boxcar_warp(const __
     v.cap = a.cap;
     v.t_offset = a.t_offset;
     v.dm = a.dm0 + static_cast<double>(i) * a.ddm;
-    v.n = a.n_out;
+    v.n = a.n_emit;
     v.n_width = a.n_width;
     v.sb = static_cast<int>(q / a.n_dm);
     v.dm_index = a.dm_index0 + i;
@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(detail::kBoxWarps * 32) k_boxcar_warp(const __
 }  // namespace
 
 cudaError_t launch_boxcar(const BoxcarArgs& a, cudaStream_t s) {
-    if (a.n_sb == 0 || a.n_dm == 0 || a.n_out == 0) return cudaSuccess;
+    if (a.n_sb == 0 || a.n_dm == 0 || a.n_emit <= 0) return cudaSuccess;
     const long long series = static_cast<long long>(a.n_sb) * a.n_dm;
     if (a.wmax <= detail::kWarpCS) {
         const unsigned blocks = static_cast<unsigned>((series + detail::kBoxWarps - 1) / detail::kBoxWarps);

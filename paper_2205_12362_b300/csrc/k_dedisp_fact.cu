@@ -381,12 +381,12 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
             const uint32_t hi = tot_hi[j][k];
             const uint32_t lo = tot_lo[j][k];
             const int t = t0 + 2 * (lane + 32 * k);
-            if (t < a.n_out) {
+            if (t < a.n_emit) {
                 row[t] = static_cast<int32_t>(lo);
                 s1 += lo;
                 s2 += static_cast<unsigned long long>(lo) * lo;
             }
-            if (t + 1 < a.n_out) {
+            if (t + 1 < a.n_emit) {
                 row[t + 1] = static_cast<int32_t>(hi);
                 s1 += hi;
                 s2 += static_cast<unsigned long long>(hi) * hi;

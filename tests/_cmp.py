@@ -15,11 +15,13 @@ THR_BAND = 1e-3
 
 
 def oracle_candidate_superset(x, sb_map, freqs, t_samp, ranges, thr, n_out, n_in, t_offset=0,
-                              return_series=False):
+                              return_series=False, bins_absolute=False):
     """Oracle candidates with S/N > thr - THR_BAND (a superset of what the
-    GPU may legally return)."""
+    GPU may legally return).  bins_absolute: x is a window of a stream at
+    t_offset with downsampling bins aligned to the stream."""
     got, n, series = oracle.search(x, sb_map, freqs, t_samp, ranges, thr - THR_BAND, n_out, n_in=n_in,
-                                   t_offset_native=t_offset, cap=1 << 22, return_series=return_series)
+                                   t_offset_native=t_offset, cap=1 << 22, return_series=return_series,
+                                   bins_absolute=bins_absolute)
     assert n == len(got), "oracle candidate buffer overflowed"
     return got, series
 

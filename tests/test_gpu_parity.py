@@ -358,7 +358,8 @@ def batch_case(seed, n_in_extra):
     return x, f, ranges, sb, n_in, n_out
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 1000])   # 1000: FDD_BATCH_SB_FACTORED
+# 1000: FDD_BATCH_SB_FACTORED, 1001: FDD_BATCH_SB_PERSISTENT (one launch for every job, range and slab)
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 1000, 1001])
 def test_batched_equals_single(fdd, variant):
     import torch
     cases = [batch_case(s, e) for s, e in [(0, 0), (1, 7), (2, 33)]]
@@ -388,7 +389,7 @@ def test_batched_equals_single(fdd, variant):
     compare_candidates(res[2].candidates()[0], ora, 5.0)
 
 
-@pytest.mark.parametrize("variant", [-1, 1000])
+@pytest.mark.parametrize("variant", [-1, 1000, 1001])
 def test_batch_graph_and_update(fdd, variant):
     import torch
     cases = [batch_case(s, 0) for s in (3, 4)]
@@ -435,7 +436,7 @@ def test_batch_autotune_keeps_parity(fdd):
     assert torch.equal(res.series, ref.series)
 
 
-@pytest.mark.parametrize("variant", [-1, 1000])
+@pytest.mark.parametrize("variant", [-1, 1000, 1001])
 def test_four_range_71_sb_batched_sampled(fdd, variant):
     """The 4-range 0-5000 plan over 71 SBs at full size, in the batched
     launch configuration the benchmark and serving loop use; one SB checked

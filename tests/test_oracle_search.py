@@ -90,3 +90,68 @@ def test_short_input_rejected():
     x = np.zeros((1, 16, 100 + dmax - 1), np.uint8)
     with pytest.raises(ValueError):
         oracle.search(x, np.zeros((1, 16)), f, T_SAMP, plan, 8.0, 100)
+
+
+def _stream_case():
+    """A stream of several windows whose length is not a multiple of the
+    largest downsampling factor (L = 500: 500 mod 8 = 4, as 12500 mod 8 in
+    ARTS), with ranges at D = 1, 2, 3 and 8."""
+    n_tab, n_chan, n_sb, L, W = 2, 48, 2, 500, 4
+    f = synth.channel_freqs(n_chan)
+    ranges = [dict(dm0=0.0, ddm=2.0, n_dm=8, downsamp=1, widths=[1, 2]),
+              dict(dm0=16.0, ddm=4.0, n_dm=6, downsamp=2, widths=[1, 4]),
+              dict(dm0=40.0, ddm=6.0, n_dm=5, downsamp=3, widths=[1, 2]),
+              dict(dm0=70.0, ddm=8.0, n_dm=4, downsamp=8, widths=[1, 2, 4])]
+    need = max((int(oracle.delays(f, T_SAMP, r["dm0"], r["ddm"], r["n_dm"], r["downsamp"]).max()) + 2)
+               * r["downsamp"] for r in ranges) + 8
+    x = synth.filterbank(21, n_tab, n_chan, W * L + need, pulses=[
+        dict(tab=1, start=777 + oracle.delays(f, T_SAMP, 50.0, 1.0, 1)[0], width=3, amp=30.0)])
+    sb = np.zeros((n_sb, n_chan), np.int32)
+    sb[1, 20:] = 1
+    return x, f, ranges, sb, L, W, need
+
+
+def test_absolute_bins_windows_tile_the_one_shot_series():
+    """Sec. "Downsampling" read with bins aligned to stream sample 0: the
+    series of consecutive windows (bins starting in [wL, (w+1)L)) laid end to
+    end equal the one-shot series of the whole stream, bin for bin, and a
+    D = 8 range alternates 63 and 62 bins per 500-sample window."""
+    x, f, ranges, sb, L, W, need = _stream_case()
+    _, _, whole = oracle.search(x, sb, f, T_SAMP, ranges, 1e9, W * L, n_in=x.shape[2], return_series=True,
+                                bins_absolute=True)
+    parts = [[] for _ in ranges]
+    for w in range(W):
+        xw = np.ascontiguousarray(x[:, :, w * L:w * L + L + need])
+        _, _, ser = oracle.search(xw, sb, f, T_SAMP, ranges, 1e9, L, n_in=L + need, t_offset_native=w * L,
+                                  return_series=True, bins_absolute=True)
+        for k, s_ in enumerate(ser):
+            parts[k].append(s_)
+    for k, r in enumerate(ranges):
+        cat = np.concatenate(parts[k], axis=2)
+        assert cat.shape == whole[k].shape
+        assert (cat == whole[k]).all(), "range %d" % k
+    assert [p.shape[2] for p in parts[3]] == [63, 62, 63, 62]
+    assert [oracle.window_bins(w * L, L, 8) for w in range(2)] == [(0, 63), (4, 62)]
+
+
+def test_absolute_bins_equal_a_shifted_plain_search():
+    """One window in the absolute-bin mode equals, range by range, the plain
+    search (bins from input sample 0) of the input advanced by the range's
+    phase, with n_r bins and the stream position added to t_native."""
+    x, f, ranges, sb, L, W, need = _stream_case()
+    t0 = 1501               # stream position 1501: phases 0, 1, 2, 3 for D = 1, 2, 3, 8
+    xw = np.ascontiguousarray(x[:, :, t0:t0 + L + need - 1])
+    got, n, ser = oracle.search(xw, sb, f, T_SAMP, ranges, 5.0, L, n_in=xw.shape[2], t_offset_native=t0,
+                                return_series=True, bins_absolute=True)
+    dm_base = 0
+    for k, r in enumerate(ranges):
+        ph, nr = oracle.window_bins(t0, L, r["downsamp"])
+        assert ph == (-t0) % r["downsamp"]
+        xs = np.ascontiguousarray(xw[:, :, ph:])
+        g2, _, s2 = oracle.search(xs, sb, f, T_SAMP, [r], 5.0, nr * r["downsamp"], n_in=xs.shape[2],
+                                  t_offset_native=t0 + ph, return_series=True)
+        assert (s2[0] == ser[k]).all()
+        mine = got[(got["dm_index"] >= dm_base) & (got["dm_index"] < dm_base + r["n_dm"])]
+        assert len(mine) == len(g2)
+        assert (mine["t_native"] == g2["t_native"]).all() and (mine["dm_index"] - dm_base == g2["dm_index"]).all()
+        dm_base += r["n_dm"]

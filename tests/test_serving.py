@@ -1,7 +1,8 @@
 """The serving runtime (continuous batching of real-time chunks from many
-beams): every window's candidates equal those of a stand-alone search of the
-same input, whatever the mix of windows it was batched with; sequence errors,
-backpressure and HBM admission are reported on the host.
+beams): every window's candidates equal those of a stand-alone window search
+(fdd_search_window) of the same input, whatever the mix of windows it was
+batched with; sequence errors, backpressure and HBM admission are reported on
+the host.
 
 Tolerance: identical candidate records (both paths run the same exact-integer
 kernels; S/N bit-identical)."""
@@ -26,11 +27,11 @@ def fdd():
     return m
 
 
-def stream_case(n_beams=3, n_chunks=9, chunk=512):
+def stream_case(n_beams=3, n_chunks=9, chunk=512, dm_scale=1.0):
     n_tab, n_chan, n_sb = 2, 64, 3
     f = synth.channel_freqs(n_chan)
-    ranges = [dict(dm0=0.0, ddm=2.0, n_dm=48, downsamp=1, widths=[1, 2, 4]),
-              dict(dm0=96.0, ddm=4.0, n_dm=24, downsamp=2, widths=[1, 4])]
+    ranges = [dict(dm0=0.0, ddm=2.0 * dm_scale, n_dm=48, downsamp=1, widths=[1, 2, 4]),
+              dict(dm0=96.0 * dm_scale, ddm=4.0 * dm_scale, n_dm=24, downsamp=2, widths=[1, 4])]
     sb = np.zeros((n_sb, n_chan), np.int16)
     sb[1] = 1
     sb[2, 16:48] = 1
@@ -57,16 +58,24 @@ def standalone(fdd, plan, x, w, chunk, n_in, cap=1 << 15):
     win = np.zeros((x.shape[0], x.shape[1], synth.padded_pitch(n_in)), np.uint8)
     seg = x[:, :, w * chunk:w * chunk + n_in]
     win[:, :, :seg.shape[2]] = seg
-    r = plan.search(torch.from_numpy(win).cuda(), n_in, chunk, t_offset=w * chunk, cap=cap)
+    r = plan.search_window(torch.from_numpy(win).cuda(), n_in, chunk, w * chunk, cap=cap)
     torch.cuda.synchronize()
     return r.candidates()[0], win
 
 
-@pytest.mark.parametrize("max_slots", [1, 2, 0])
-def test_serving_results_match_standalone(fdd, max_slots):
-    f, ranges, sb, streams, chunk, n_chunks = stream_case()
+@pytest.mark.parametrize("max_slots,variant", [(1, -1), (2, -1), (0, -1), (0, 1000), (2, 1001)])
+def test_serving_results_match_standalone(fdd, max_slots, variant):
+    """variant: the batched mode the server's batches run in (-1 the
+    default, 1000 SB-factored launches, 1001 one persistent SB-factored
+    launch per batch)."""
+    # the persistent SB-factored mode's staging fits DM steps up to about 1 per trial at 64 channels
+    f, ranges, sb, streams, chunk, n_chunks = stream_case(dm_scale=0.5 if variant == 1001 else 1.0)
     plan = fdd.Plan(2, 64, 3, f, T_SAMP, ranges, 6.0, sb)
+    if variant >= 0:
+        plan.batch_prepare(chunk, variant)
     srv = fdd.Server(plan, len(streams), chunk, max_slots=max_slots, cap_per_window=1 << 14)
+    if variant >= 0:
+        assert plan.batch_config()["variant"] == variant
     info = srv.info()
     n_in = info["window_len"]
     assert max_slots == 0 or info["n_slots"] == max_slots
@@ -100,7 +109,8 @@ def test_serving_results_match_standalone(fdd, max_slots):
     # one window holding an injected pulse (beam 1: t0 = 1537) against the oracle
     b, w = 1, 3
     _, win = standalone(fdd, plan, streams[b], w, chunk, n_in)
-    ora, _ = oracle_candidate_superset(win, sb, f, T_SAMP, ranges, 6.0, chunk, n_in, t_offset=w * chunk)
+    ora, _ = oracle_candidate_superset(win, sb, f, T_SAMP, ranges, 6.0, chunk, n_in, t_offset=w * chunk,
+                                       bins_absolute=True)
     compare_candidates(results[(b, w)][1], ora, 6.0)
     assert len(results[(b, w)][1]) > 0
     assert sum(len(c) for _, c in results.values()) > 0
