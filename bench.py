@@ -359,6 +359,12 @@ class Arm:
                            torch.zeros(1, dtype=torch.int64, device=dev)) for _ in self.plans] for _ in wins]
         else:
             self.jobs = [plan.make_job(wb, n_in, n_out, cap=cap) for wb in wins]
+            if args.variant is not None:  # per-range kernel of the SB-factored batch mode
+                for r in range(len(w["ranges"])):
+                    try:
+                        plan.set_config(r, args.variant, args.cc)
+                    except fdd.FddError:
+                        pass  # variant for the other sample width
             plan.batch_prepare(n_out, args.batch_variant if args.batch_variant is not None else -1)
             if not args.no_autotune and args.batch_variant is None:
                 plan.batch_autotune(self.jobs[:1], n_out, reps=2, stream=stream)

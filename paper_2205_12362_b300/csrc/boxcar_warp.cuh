@@ -27,6 +27,7 @@ constexpr int kWarpCS = 512;                      // samples per chunk
 constexpr int kWarpRows = kWarpCS / 32;           // rows of 32 per chunk
 constexpr int kWarpRing = 3 * kWarpCS + kWarpCS;  // three slots + mirror of slot 0, uint32 entries
 constexpr int kBoxWarps = 4;                      // warps (series) per block
+constexpr int kBoundWmax = 128;                   // widest width of the chunk pre-check
 
 // One series as the warp needs it.
 struct BoxSeries {
@@ -96,6 +97,22 @@ __device__ __forceinline__ void boxcar_series_warp(const BoxSeries& v, uint32_t*
     const int n_chunks = n / kWarpCS + 1;  // covers prefix indices 0..n
     const uint32_t ring_s = static_cast<uint32_t>(__cvta_generic_to_shared(ring));
     uint32_t carry = 0;
+    // Chunk pre-check (widths <= kBoundWmax): for bases b in {1, 8, 64}, M_b = max of B_b(s) over s in
+    // [chunk start, chunk end + wmax - 1].  A width w with base b (the largest base dividing it) has
+    // B_w(t) = sum_{j < w/b} B_b(t + j b) <= (w/b) M_b for every t of the chunk, so a chunk where
+    // (w/b) M_b <= tau_w for every width holds no candidate and is skipped; any other chunk is
+    // evaluated exactly below.
+    const bool bound = wmax <= kBoundWmax;
+    int32_t bmul[NWB];  // w / b
+    int bsel[NWB];      // base index of width k
+#pragma unroll
+    for (int k = 0; k < NWB; k++) {
+        const int w = wk[k];
+        bsel[k] = (w >= 64 && w % 64 == 0) ? 2 : ((w >= 8 && w % 8 == 0) ? 1 : 0);
+        bmul[k] = w / (bsel[k] == 2 ? 64 : (bsel[k] == 1 ? 8 : 1));
+    }
+    // the ring's mirror of slot 0 must cover the pre-check's reach into the next chunk
+    const int mirror = bound ? min(kWarpCS, 2 * wmax + 64) : wmax;
 
     for (int c = 0; c <= n_chunks; c++) {
         if (c < n_chunks) {
@@ -119,7 +136,7 @@ __device__ __forceinline__ void boxcar_series_warp(const BoxSeries& v, uint32_t*
                 const uint32_t p = carry + incl - x[m];
                 const uint32_t at = ring_s + 4u * static_cast<uint32_t>(slot * kWarpCS + 32 * m + lane);
                 asm volatile("st.shared.u32 [%0], %1;" ::"r"(at), "r"(p) : "memory");
-                if (slot == 0 && 32 * m < wmax) {
+                if (slot == 0 && 32 * m < mirror) {
                     const uint32_t am = ring_s + 4u * static_cast<uint32_t>(3 * kWarpCS + 32 * m + lane);
                     asm volatile("st.shared.u32 [%0], %1;" ::"r"(am), "r"(p) : "memory");
                 }
@@ -134,6 +151,46 @@ __device__ __forceinline__ void boxcar_series_warp(const BoxSeries& v, uint32_t*
         if (ebase >= n) break;
         const uint32_t s_slot = ring_s + 4u * static_cast<uint32_t>((e % 3) * kWarpCS + lane);
         const bool interior = ebase + kWarpCS + wmax <= n;  // no window of this chunk passes the end
+        if (bound) {
+            int32_t mx0 = -2147483647 - 1, mx1 = mx0, mx2 = mx0;
+            const int rows = kWarpRows + (wmax - 1 + 31) / 32;
+            for (int m = 0; m < rows; m++) {
+                const int s_ = ebase + 32 * m + lane;
+                const uint32_t a0 = s_slot + 128u * m;
+                if (s_ + 1 <= n) {
+                    uint32_t p0, p1;
+                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(p0) : "r"(a0));
+                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(p1) : "r"(a0 + 4u));
+                    mx0 = max(mx0, static_cast<int32_t>(p1 - p0));
+                    if (s_ + 8 <= n) {
+                        uint32_t p8;
+                        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(p8) : "r"(a0 + 32u));
+                        mx1 = max(mx1, static_cast<int32_t>(p8 - p0));
+                    }
+                    if (wmax >= 64 && s_ + 64 <= n) {
+                        uint32_t p64;
+                        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(p64) : "r"(a0 + 256u));
+                        mx2 = max(mx2, static_cast<int32_t>(p64 - p0));
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                mx0 = max(mx0, __shfl_xor_sync(0xffffffffu, mx0, o));
+                mx1 = max(mx1, __shfl_xor_sync(0xffffffffu, mx1, o));
+                mx2 = max(mx2, __shfl_xor_sync(0xffffffffu, mx2, o));
+            }
+            bool need = false;
+#pragma unroll
+            for (int k = 0; k < NWB; k++) {
+                const int32_t mb = bsel[k] == 2 ? mx2 : (bsel[k] == 1 ? mx1 : mx0);
+                need |= static_cast<int64_t>(bmul[k]) * mb > static_cast<int64_t>(tk[k]);
+            }
+            if (!need) {
+                __syncwarp();  // slot e % 3 may be rewritten by chunk c + 2
+                continue;
+            }
+        }
 #pragma unroll 2
         for (int m = 0; m < kWarpRows; m++) {
             const int t = ebase + 32 * m + lane;

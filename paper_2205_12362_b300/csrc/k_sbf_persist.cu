@@ -23,7 +23,8 @@
 //
 // The comb task copies its partial rows with 1-D bulk copies
 // (cp.async.bulk, 256 bytes per TAB and segment row, completion counted on
-// an mbarrier, double-buffered over chunks of 8 segments) issued by one warp.
+// an mbarrier per buffer; NB buffers of 8-segment chunks, NB - 1 chunks in
+// flight ahead of the one being added), one copy per thread.
 #include "sbf_part.cuh"
 #include "tma.cuh"
 
@@ -37,6 +38,7 @@ constexpr int PBD = PW * P_DPW;
 constexpr int CSB = 5;                           // SBs per warp of a comb task (40 per task)
 constexpr int CT = 128, UC = 8;                  // comb: samples per sub-tile, segments per chunk
 constexpr int CSUB = 2;                          // comb sub-tiles per task (CT * CSUB samples)
+constexpr int NB = 4;                            // comb chunk buffers (NB - 1 chunks in flight ahead)
 constexpr int kRowBytes = CT * 2;                // one partial row (uint16) in shared memory
 constexpr int kTabBytes = UC * kRowBytes;        // UC rows of one TAB
 static_assert(kTabBytes == 1 << 11, "the TAB offset is formed as tab << 11");
@@ -81,18 +83,19 @@ __global__ void __launch_bounds__(PW * 32, 2) k_sbf_persist(const __grid_constan
     extern __shared__ __align__(128) uint8_t smem_raw[];
     __shared__ SbfPartArgs s_pa;
     __shared__ Task s_task;
-    __shared__ __align__(8) unsigned long long s_bar[2];
+    __shared__ __align__(8) unsigned long long s_bar[NB];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint8_t* smem = smem_raw + ((128 - (reinterpret_cast<uintptr_t>(smem_raw) & 127)) & 127);
     const uint32_t s_base = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
     const uint32_t bar0 = static_cast<uint32_t>(__cvta_generic_to_shared(&s_bar[0]));
     unsigned long long* abort_flag = p.counter + 3;
     if (tid == 0) {
-        tma::mbar_init(bar0, 1);
-        tma::mbar_init(bar0 + 8, 1);
+        for (int b = 0; b < NB; b++) tma::mbar_init(bar0 + 8u * b, 1);
         tma::mbar_init_fence();
     }
-    uint32_t phase[2] = {0u, 0u};  // completed phases of each comb buffer's barrier (the same in every thread)
+    // comb stages this block has run so far (the same in every thread): stage g uses buffer g % NB, the
+    // (g / NB)-th use of that buffer's barrier
+    uint32_t stage0 = 0;
     const unsigned long long total = static_cast<unsigned long long>(p.sp_tasks_per_job) * p.n_jobs;
     // thread 0 takes its next task while the block works on the current one (a block holding a task it
     // has not started still lets the oldest unfinished task proceed: that task is either running or
@@ -184,154 +187,163 @@ __global__ void __launch_bounds__(PW * 32, 2) k_sbf_persist(const __grid_constan
             continue;
         }
 
-        // ---- comb task: one trial x CSUB * CT samples x PW*CSB SBs, CT samples at a time
+        // ---- comb task: one trial x CSUB * CT samples x PW*CSB SBs.  Its stages (sub-tile, chunk of UC
+        // segments) run as one pipeline over NB chunk buffers, NB - 1 chunks in flight ahead.
         const BatchJob& J = p.jobs[tk.job];
-        const int y = tk.idx % R.comb_tiles;
-        const int rest = tk.idx / R.comb_tiles;
-        const int i_s = rest % G.n_slab;
-        const int z = rest / G.n_slab;
+        // the SB groups of one (trial, tile) are consecutive tasks, so the second reads its rows from L2
+        const int z = tk.idx % R.sb_groups;
+        const int rest = tk.idx / R.sb_groups;
+        const int y = rest % R.comb_tiles;
+        const int i_s = rest / R.comb_tiles;
         const int i = G.i0 + i_s;
         const int r = G.range;
         const int emit = J.emit[r];
-        bool failed = false;
-        for (int sub = 0; sub < CSUB && !failed; sub++) {
-        const int t0 = (y * CSUB + sub) * CT;
-        if (t0 < emit) {
-            const uint16_t* P = J.sbf_scratch + static_cast<int64_t>(G.slot) * R.slot_elems;
-            const int64_t seg_stride = static_cast<int64_t>(R.slab) * R.Np;
-            const int64_t tab_stride = seg_stride * R.n_seg;
-            const uint16_t* P_row = P + static_cast<int64_t>(i_s) * R.Np + t0;
-            const int n_tab = p.n_tab;
-            const uint32_t buf_bytes = static_cast<uint32_t>(n_tab) * kTabBytes;
-            const int n_seg = R.n_seg;
-            const int n_chunks = (n_seg + UC - 1) / UC;
-            const int sb0 = z * (PW * CSB) + warp * CSB;
-            const int nsb = max(0, min(CSB, p.n_sb - sb0));  // warp-uniform
-            const uint8_t* seg_tab = R.seg_tab;
-            uint32_t tab_row[CSB];  // byte offsets of this warp's SB rows in seg_tab
+        const int n_sub = max(0, min(CSUB, (emit - y * CSUB * CT + CT - 1) / CT));  // sub-tiles with outputs
+        const int n_tab = p.n_tab;
+        const int n_seg = R.n_seg;
+        const int n_chunks = (n_seg + UC - 1) / UC;
+        const int n_stages = n_sub * n_chunks;
+        const int64_t seg_stride = static_cast<int64_t>(R.slab) * R.Np;
+        const int64_t tab_stride = seg_stride * R.n_seg;
+        const uint16_t* P_trial =
+            J.sbf_scratch + static_cast<int64_t>(G.slot) * R.slot_elems + static_cast<int64_t>(i_s) * R.Np;
+        const uint32_t buf_bytes = static_cast<uint32_t>(n_tab) * kTabBytes;
+        const int sb0 = z * (PW * CSB) + warp * CSB;
+        const int nsb = max(0, min(CSB, p.n_sb - sb0));  // warp-uniform
+        const uint8_t* seg_tab = R.seg_tab;
+        uint32_t tab_row[CSB];  // byte offsets of this warp's SB rows in seg_tab
 #pragma unroll
-            for (int j = 0; j < CSB; j++) {
-                const int sj = nsb > 0 ? sb0 + min(j, nsb - 1) : 0;
-                tab_row[j] = static_cast<uint32_t>(sj) * static_cast<uint32_t>(R.seg_pitch);
-            }
-            // chunk ch (UC segments of every TAB) into buffer ch & 1, one 256-byte bulk copy per row,
-            // issued by warp 0
-            auto issue = [&](int ch) {
-                const uint32_t bar = bar0 + 8u * (ch & 1);
-                const int u0 = ch * UC;
-                const int nu = min(UC, n_seg - u0);
+        for (int j = 0; j < CSB; j++) {
+            const int sj = nsb > 0 ? sb0 + min(j, nsb - 1) : 0;
+            tab_row[j] = static_cast<uint32_t>(sj) * static_cast<uint32_t>(R.seg_pitch);
+        }
+        // stage q: chunk q % n_chunks of sub-tile q / n_chunks into buffer (stage0 + q) % NB, one
+        // 256-byte bulk copy per (TAB, segment) row, spread over the block's threads (one copy per
+        // thread for up to 256 rows); thread 0 arms the barrier with the chunk's byte count (copies
+        // that land first only lower its pending count: the phase needs thread 0's arrival too)
+        auto issue = [&](int q) {
+            const uint32_t b = (stage0 + static_cast<uint32_t>(q)) % NB;
+            const uint32_t bar = bar0 + 8u * b;
+            const int sub = q / n_chunks, ch = q - sub * n_chunks;
+            const int u0 = ch * UC;
+            const int nu = min(UC, n_seg - u0);
+            const uint16_t* src0 = P_trial + (y * CSUB + sub) * CT;
+            if (tid == 0) tma::mbar_expect_tx(bar, static_cast<uint32_t>(n_tab * nu * kRowBytes));
+            const uint32_t dst0 = s_base + b * buf_bytes;
+            for (int it = tid; it < n_tab * nu; it += PW * 32) {
+                const int k = it / nu, du = it - k * nu;
                 fence_proxy_async_shared();
-                if (lane == 0) tma::mbar_expect_tx(bar, static_cast<uint32_t>(n_tab * nu * kRowBytes));
-                __syncwarp();
-                const uint32_t dst0 = s_base + static_cast<uint32_t>(ch & 1) * buf_bytes;
-                for (int it = lane; it < n_tab * nu; it += 32) {
-                    const int k = it / nu, du = it - k * nu;
-                    bulk_copy(dst0 + static_cast<uint32_t>(k * kTabBytes + du * kRowBytes),
-                              P_row + k * tab_stride + static_cast<int64_t>(u0 + du) * seg_stride, kRowBytes, bar);
-                }
-            };
-            uint32_t acc[CSB][2], tot[CSB][4];
+                bulk_copy(dst0 + static_cast<uint32_t>(k * kTabBytes + du * kRowBytes),
+                          src0 + k * tab_stride + static_cast<int64_t>(u0 + du) * seg_stride, kRowBytes, bar);
+            }
+        };
+        uint32_t acc[CSB][2], tot[CSB][4];
+        auto fold = [&]() {
 #pragma unroll
             for (int j = 0; j < CSB; j++) {
+                tot[j][0] += acc[j][0] & 0xFFFFu;
+                tot[j][1] += acc[j][0] >> 16;
+                tot[j][2] += acc[j][1] & 0xFFFFu;
+                tot[j][3] += acc[j][1] >> 16;
                 acc[j][0] = acc[j][1] = 0u;
-                tot[j][0] = tot[j][1] = tot[j][2] = tot[j][3] = 0u;
             }
-            auto fold = [&]() {
+        };
+        fence_proxy_async_global();  // the partials were written through the generic proxy
+        for (int q = 0; q < NB - 1 && q < n_stages; q++) issue(q);
+        int since = 0;
+        bool failed = false;
+        for (int q = 0; q < n_stages; q++) {
+            const int sub = q / n_chunks, ch = q - sub * n_chunks;
+            // the buffer of stage q + NB - 1 was released at the end of stage q - 1
+            if (q + NB - 1 < n_stages) issue(q + NB - 1);
+            const uint32_t g = stage0 + static_cast<uint32_t>(q);
+            const bool ok = tma::mbar_wait_bounded(bar0 + 8u * (g % NB), (g / NB) & 1u);
+            if (__syncthreads_or(!ok)) {
+                // a copy did not land: flag it, wait (bounded) for this block's copies in flight, stop
+                if (tid == 0) {
+                    atomicOr(p.status, 1u);
+                    atomicExch(abort_flag, 1ULL);
+                    for (int w2 = q; w2 < n_stages && w2 < q + NB - 1; w2++) {
+                        const uint32_t g2 = stage0 + static_cast<uint32_t>(w2);
+                        tma::mbar_wait_bounded(bar0 + 8u * (g2 % NB), (g2 / NB) & 1u);
+                    }
+                }
+                failed = true;
+                break;
+            }
+            if (ch == 0) {
 #pragma unroll
                 for (int j = 0; j < CSB; j++) {
-                    tot[j][0] += acc[j][0] & 0xFFFFu;
-                    tot[j][1] += acc[j][0] >> 16;
-                    tot[j][2] += acc[j][1] & 0xFFFFu;
-                    tot[j][3] += acc[j][1] >> 16;
                     acc[j][0] = acc[j][1] = 0u;
+                    tot[j][0] = tot[j][1] = tot[j][2] = tot[j][3] = 0u;
                 }
-            };
-            if (warp == 0) {
-                fence_proxy_async_global();  // the partials were written through the generic proxy
-                issue(0);
+                since = 0;
             }
-            int since = 0;
-            for (int ch = 0; ch < n_chunks; ch++) {
-                const int buf = ch & 1;
-                if (warp == 0 && ch + 1 < n_chunks) issue(ch + 1);  // buffer buf ^ 1 was released below
-                const bool ok = tma::mbar_wait_bounded(bar0 + 8u * buf, phase[buf] & 1u);
-                phase[buf]++;
-                if (__syncthreads_or(!ok)) {
-                    // a copy did not land: flag it, wait (bounded) for this block's copies, stop the launch
-                    if (tid == 0) {
-                        atomicOr(p.status, 1u);
-                        atomicExch(abort_flag, 1ULL);
-                        if (!ok) tma::mbar_wait_bounded(bar0 + 8u * buf, (phase[buf] - 1u) & 1u);
-                        if (ch + 1 < n_chunks) tma::mbar_wait_bounded(bar0 + 8u * (buf ^ 1), phase[buf ^ 1] & 1u);
-                    }
-                    failed = true;
-                    break;
-                }
-                const int u0 = ch * UC;
-                const int nu = min(UC, n_seg - u0);
-                const uint32_t s_buf = s_base + static_cast<uint32_t>(buf) * buf_bytes + 8u * lane;
+            const int u0 = ch * UC;
+            const int nu = min(UC, n_seg - u0);
+            const uint32_t s_buf = s_base + (g % NB) * buf_bytes + 8u * lane;
 #pragma unroll
-                for (int q = 0; q < UC; q += 4) {
-                    uint32_t tabs4[CSB];
+            for (int qq = 0; qq < UC; qq += 4) {
+                uint32_t tabs4[CSB];
 #pragma unroll
-                    for (int j = 0; j < CSB; j++)
-                        tabs4[j] = __ldg(reinterpret_cast<const uint32_t*>(seg_tab + tab_row[j] + u0 + q));
+                for (int j = 0; j < CSB; j++)
+                    tabs4[j] = __ldg(reinterpret_cast<const uint32_t*>(seg_tab + tab_row[j] + u0 + qq));
 #pragma unroll
-                    for (int dq = 0; dq < 4; dq++) {
-                        const int du = q + dq;
-                        if (du < nu) {  // block-uniform
+                for (int dq = 0; dq < 4; dq++) {
+                    const int du = qq + dq;
+                    if (du < nu) {  // block-uniform
 #pragma unroll
-                            for (int j = 0; j < CSB; j++) {
-                                // byte dq of tabs4 (the TAB; PRMT zero-fills the rest) times kTabBytes (2^11)
-                                const uint32_t tab = __byte_perm(tabs4[j], 0u, 0x4440u + dq);
-                                const uint2 v = lds64(s_buf + (tab << 11) + du * kRowBytes);
-                                acc[j][0] += v.x;
-                                acc[j][1] += v.y;
-                            }
-                            if (++since == R.flush) {
-                                fold();
-                                since = 0;
-                            }
+                        for (int j = 0; j < CSB; j++) {
+                            // byte dq of tabs4 (the TAB; PRMT zero-fills the rest) times kTabBytes (2^11)
+                            const uint32_t tab = __byte_perm(tabs4[j], 0u, 0x4440u + dq);
+                            const uint2 v = lds64(s_buf + (tab << 11) + du * kRowBytes);
+                            acc[j][0] += v.x;
+                            acc[j][1] += v.y;
+                        }
+                        if (++since == R.flush) {
+                            fold();
+                            since = 0;
                         }
                     }
                 }
-                __syncthreads();  // buffer free for the copy issued next iteration
             }
-            if (failed) break;
-            fold();
-            const int t = t0 + 4 * lane;
-            int32_t* series = J.series + R.series_elem_off;
-            unsigned long long* stat = J.stat + 2 * R.stat_off;
+            __syncthreads();  // buffer free for the copy issued at the next stage
+            if (ch == n_chunks - 1) {
+                // sub-tile complete: write its series samples and fold the moments
+                fold();
+                const int t = (y * CSUB + sub) * CT + 4 * lane;
+                int32_t* series = J.series + R.series_elem_off;
+                unsigned long long* stat = J.stat + 2 * R.stat_off;
 #pragma unroll
-            for (int j = 0; j < CSB; j++) {
-                unsigned long long s1 = 0, s2 = 0;
-                if (j < nsb) {
-                    int32_t* row = series + (static_cast<int64_t>(sb0 + j) * R.n_dm + i) * R.n_out;
+                for (int j = 0; j < CSB; j++) {
+                    unsigned long long s1 = 0, s2 = 0;
+                    if (j < nsb) {
+                        int32_t* row = series + (static_cast<int64_t>(sb0 + j) * R.n_dm + i) * R.n_out;
 #pragma unroll
-                    for (int e = 0; e < 4; e++) {
-                        if (t + e < emit) {
-                            const uint32_t v = tot[j][e];
-                            row[t + e] = static_cast<int32_t>(v);
-                            s1 += v;
-                            s2 += static_cast<unsigned long long>(v) * v;
+                        for (int e = 0; e < 4; e++) {
+                            if (t + e < emit) {
+                                const uint32_t v = tot[j][e];
+                                row[t + e] = static_cast<int32_t>(v);
+                                s1 += v;
+                                s2 += static_cast<unsigned long long>(v) * v;
+                            }
                         }
                     }
-                }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-                    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-                }
-                if (lane == 0 && j < nsb) {
-                    const int64_t q = static_cast<int64_t>(sb0 + j) * R.n_dm + i;
-                    atomicAdd(stat + 2 * q, s1);
-                    atomicAdd(stat + 2 * q + 1, s2);
+                    for (int o = 16; o > 0; o >>= 1) {
+                        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                    }
+                    if (lane == 0 && j < nsb) {
+                        const int64_t qs = static_cast<int64_t>(sb0 + j) * R.n_dm + i;
+                        atomicAdd(stat + 2 * qs, s1);
+                        atomicAdd(stat + 2 * qs + 1, s2);
+                    }
                 }
             }
-        }
-        __syncthreads();  // the sub-tile's buffers are free for the next one
         }
         if (failed) break;
+        stage0 += static_cast<uint32_t>(n_stages);
         if (tid == 0) {
             __threadfence();
             atomicAdd(done + 1, 1u);
@@ -344,7 +356,7 @@ __global__ void __launch_bounds__(PW * 32, 2) k_sbf_persist(const __grid_constan
 DedispVariant sbf_persist_part_variant(int E) { return DedispVariant{E, P_NW, P_DPW, PW, P_MAXIT}; }
 
 size_t sbf_persist_smem_bytes(size_t part_smem_max, int n_tab) {
-    const size_t comb = 2ull * static_cast<size_t>(n_tab) * kTabBytes;
+    const size_t comb = static_cast<size_t>(NB) * static_cast<size_t>(n_tab) * kTabBytes;
     return (part_smem_max > comb ? part_smem_max : comb) + 128;  // + alignment of the base to 128 bytes
 }
 

@@ -546,6 +546,31 @@ def test_boxcar_width_sets(fdd):
     assert compare_candidates(gpu, ora, 5.0) > 0
 
 
+def test_boxcar_chunk_precheck(fdd):
+    """The warp boxcar's chunk pre-check (widths up to 128: per 512-sample
+    chunk, maxima of the 1-, 8- and 64-sample boxcars bound every width; a
+    chunk whose bound stays under every threshold is skipped) against the
+    oracle: power-of-two widths to 128 and a mixed set, pulses inside chunks,
+    across a chunk boundary and at the series end, a low threshold so that
+    noise chunks pass and fail the bound."""
+    import torch
+    n_chan, n_out = 96, 2900
+    f = synth.channel_freqs(n_chan)
+    ranges = [dict(dm0=0.0, ddm=2.0, n_dm=20, downsamp=1, widths=[1, 2, 4, 8, 16, 32, 64, 128]),
+              dict(dm0=40.0, ddm=4.0, n_dm=12, downsamp=2, widths=[3, 6, 24, 72, 100])]
+    n_in = max(int(oracle.delays(f, T_SAMP, r["dm0"], r["ddm"], r["n_dm"], r["downsamp"]).max())
+               * r["downsamp"] + n_out for r in ranges) + 3
+    pulses = [dict(tab=0, start=t0 + oracle.delays(f, T_SAMP, dm, 1.0, 1)[0], width=w, amp=a)
+              for t0, dm, w, a in [(200, 10.0, 2, 40.0), (1000, 30.0, 60, 9.0), (2840, 60.0, 24, 14.0)]]
+    x = synth.filterbank(23, 1, n_chan, n_in, pulses=pulses)
+    sb = np.zeros((1, n_chan), np.int16)
+    for thr in (4.5, 7.0):
+        plan, gpu, gs, ora, os_ = run_both(fdd, x, sb, f, ranges, thr, n_out, n_in)
+        for g, o in zip(gs, os_):
+            assert (g == o).all()
+        assert compare_candidates(gpu, ora, thr) > 0
+
+
 def test_sb_factored_geometry_table(fdd):
     """SB-factored kernels on the SB table the library builds from the array
     geometry (Apertif-10, 71 SBs, TABs combined in 48-channel subbands):

@@ -41,7 +41,7 @@ def stream_case(n_beams=3, n_chunks=9, chunk=512, dm_scale=1.0):
         pulses = []
         for k in range(3):
             t0 = 300 + 1100 * k + 137 * b
-            dm = 20.0 + 30 * k + 7 * b
+            dm = (20.0 + 30 * k + 7 * b) * dm_scale
             pulses.append(dict(tab=(b + k) % n_tab, start=t0 + oracle.delays(f, T_SAMP, dm, 1.0, 1)[0],
                                width=2 + k, amp=26.0))
         streams.append(synth.filterbank(1000 + b, n_tab, n_chan, total, pitch=total, pulses=pulses))
@@ -68,8 +68,9 @@ def test_serving_results_match_standalone(fdd, max_slots, variant):
     """variant: the batched mode the server's batches run in (-1 the
     default, 1000 SB-factored launches, 1001 one persistent SB-factored
     launch per batch)."""
-    # the persistent SB-factored mode's staging fits DM steps up to about 1 per trial at 64 channels
-    f, ranges, sb, streams, chunk, n_chunks = stream_case(dm_scale=0.5 if variant == 1001 else 1.0)
+    # the persistent SB-factored kernel stages at most 1024 row chunks per channel stage: at 64 channels
+    # that is DM steps up to about 0.5 per trial at full rate and 1 at D = 2
+    f, ranges, sb, streams, chunk, n_chunks = stream_case(dm_scale=0.25 if variant == 1001 else 1.0)
     plan = fdd.Plan(2, 64, 3, f, T_SAMP, ranges, 6.0, sb)
     if variant >= 0:
         plan.batch_prepare(chunk, variant)
