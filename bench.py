@@ -64,6 +64,14 @@ WORKLOADS = {
     "arts_71sb_128dm": dict(n_tab=12, n_sb=71, n_chan=1536, n_out=synth.ARTS_CHUNK, seed=3, n_pulses=5,
                             pulse_tabs=[0, 3, 5, 8, 11], thr=8.0,
                             ranges=[dict(dm0=0.0, ddm=0.2, n_dm=128, downsamp=1, widths=WIDTHS)]),
+    # the 71-SB four-range plan with 1/16 of each range's DM trials: a small case of the same kernels
+    # and launch structure for detailed profiles (traffic per trial as in the full plan)
+    "arts_71sb_4range_16th": dict(n_tab=12, n_sb=71, n_chan=1536, n_out=synth.ARTS_CHUNK, seed=4, n_pulses=5,
+                                  pulse_tabs=[0, 3, 5, 8, 11], thr=8.0, mode="graph",
+                                  ranges=[dict(dm0=0.0, ddm=0.2, n_dm=128, downsamp=1, widths=WIDTHS),
+                                          dict(dm0=409.6, ddm=0.8, n_dm=64, downsamp=2, widths=WIDTHS),
+                                          dict(dm0=1228.8, ddm=1.6, n_dm=64, downsamp=4, widths=WIDTHS),
+                                          dict(dm0=2867.2, ddm=3.2, n_dm=42, downsamp=8, widths=WIDTHS)]),
     # 71 SBs, 4-range plan 0-5000 with downsampling 1/2/4/8
     "arts_71sb_4range": dict(n_tab=12, n_sb=71, n_chan=1536, n_out=synth.ARTS_CHUNK, seed=4, n_pulses=5,
                              pulse_tabs=[0, 3, 5, 8, 11], thr=8.0, mode="graph",
@@ -228,19 +236,26 @@ def oracle_sample_rate(x, sb, f, t, w, n_in, target_s):
 # ----------------------------------------------------------------- profile evidence
 def profile_traffic(kernel, workload):
     """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
-    summary profiles/<kernel>_<workload>.md, or None when there is none or the
-    kernel source changed since the counters were taken."""
+    summary profiles/<kernel>_<workload>.md, or None when there is none or a
+    source file it names changed since the counters were taken (the summary's
+    source_sha1 is the SHA-1 of its source_files, concatenated in order)."""
     path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload))
-    src = os.path.join(CSRC, kernel + ".cu")
-    if not os.path.exists(path) or not os.path.exists(src):
+    if not os.path.exists(path):
         return None
     text = open(path).read()
     m_sha = re.search(r"source_sha1:\s*([0-9a-f]{40})", text)
     m_b = re.search(r"dram_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
+    m_f = re.search(r"source_files:\s*(.+)", text)
     if not m_sha or not m_b:
         return None
-    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
-    return float(m_b.group(1)) if sha == m_sha.group(1) else None
+    files = m_f.group(1).split() if m_f else [kernel + ".cu"]
+    h = hashlib.sha1()
+    for name in files:
+        src = os.path.join(CSRC, name)
+        if not os.path.exists(src):
+            return None
+        h.update(open(src, "rb").read())
+    return float(m_b.group(1)) if h.hexdigest() == m_sha.group(1) else None
 
 
 # ----------------------------------------------------------------- arms
@@ -309,6 +324,12 @@ def measure_int_peaks(fdd, gpu_index, target_s=0.25):
     }
 
 
+def range_variant(spec, r):
+    """--variant: one variant for every range, or a comma-separated one per range."""
+    vals = [int(v) for v in str(spec).split(",")]
+    return vals[r] if r < len(vals) else vals[-1]
+
+
 class Arm:
     """One way of running the search of a workload on the device: `step()`
     searches the resident chunk; `search(b)` searches window buffer b into
@@ -347,7 +368,7 @@ class Arm:
             if args.variant is not None:
                 for r in range(len(w["ranges"])):
                     try:
-                        p0.set_config(r, args.variant, args.cc)
+                        p0.set_config(r, range_variant(args.variant, r), args.cc)
                     except fdd.FddError:
                         pass  # variant for the other sample width
             cfgs = [p0.get_config(r) for r in range(len(w["ranges"]))]
@@ -362,7 +383,7 @@ class Arm:
             if args.variant is not None:  # per-range kernel of the SB-factored batch mode
                 for r in range(len(w["ranges"])):
                     try:
-                        plan.set_config(r, args.variant, args.cc)
+                        plan.set_config(r, range_variant(args.variant, r), args.cc)
                     except fdd.FddError:
                         pass  # variant for the other sample width
             plan.batch_prepare(n_out, args.batch_variant if args.batch_variant is not None else -1)
@@ -969,7 +990,8 @@ def main():
     ap.add_argument("--no-plain-path", action="store_true", help="skip the plain per-SB path (step and serving)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving runs of the default bench")
     ap.add_argument("--plain-steps", type=int, default=3, help="timed steps of the plain per-SB path")
-    ap.add_argument("--variant", type=int, default=None, help="force this dedispersion kernel variant")
+    ap.add_argument("--variant", default=None,
+                    help="force this dedispersion kernel variant (one index, or one per DM range, comma-separated)")
     ap.add_argument("--cc", type=int, default=0, help="with --variant: channels per stage (0 = largest fitting)")
     ap.add_argument("--batch-variant", type=int, default=None,
                     help="batched/graph modes: this batch variant instead of the tuner's choice (1000 SB-factored "

@@ -25,7 +25,8 @@ namespace detail {
 
 constexpr int kWarpCS = 512;                      // samples per chunk
 constexpr int kWarpRows = kWarpCS / 32;           // rows of 32 per chunk
-constexpr int kWarpRing = 3 * kWarpCS + kWarpCS;  // three slots + mirror of slot 0, uint32 entries
+constexpr int kSlotWords = kWarpCS + kWarpCS / 32;  // one slot, one padding word per 32 entries
+constexpr int kWarpRing = 4 * kSlotWords;            // three slots + mirror of slot 0, uint32 words
 constexpr int kBoxWarps = 4;                      // warps (series) per block
 constexpr int kBoundWmax = 128;                   // widest width of the chunk pre-check
 
@@ -94,7 +95,13 @@ __device__ __forceinline__ void boxcar_series_warp(const BoxSeries& v, uint32_t*
         wmax = max(wmax, wk[k]);
     }
     const uint32_t m0u = static_cast<uint32_t>(m0);
-    const int n_chunks = n / kWarpCS + 1;  // covers prefix indices 0..n
+    // Virtual index vv = t + mis, mis = the row's misalignment in samples, so that chunk c
+    // (vv in [512 c, 512 c + 512)) starts on a 16-byte boundary of the series and lane l's 16
+    // consecutive samples vv = 512 c + 16 l + k come in as four aligned 16-byte loads.
+    const int mis = static_cast<int>((reinterpret_cast<uintptr_t>(v.S) >> 2) & 3u);
+    const int32_t* Sa = v.S - mis;  // 16-byte aligned; element vv is sample vv - mis
+    const int nv = n + mis;          // prefix entries vv = 0 .. nv
+    const int n_chunks = nv / kWarpCS + 1;
     const uint32_t ring_s = static_cast<uint32_t>(__cvta_generic_to_shared(ring));
     uint32_t carry = 0;
     // Chunk pre-check (widths <= kBoundWmax): for bases b in {1, 8, 64}, M_b = max of B_b(s) over s in
@@ -111,65 +118,91 @@ __device__ __forceinline__ void boxcar_series_warp(const BoxSeries& v, uint32_t*
         bsel[k] = (w >= 64 && w % 64 == 0) ? 2 : ((w >= 8 && w % 8 == 0) ? 1 : 0);
         bmul[k] = w / (bsel[k] == 2 ? 64 : (bsel[k] == 1 ? 8 : 1));
     }
-    // the ring's mirror of slot 0 must cover the pre-check's reach into the next chunk
+    // the ring's mirror of slot 0 must cover every read past the end of slot 2
     const int mirror = bound ? min(kWarpCS, 2 * wmax + 64) : wmax;
 
     for (int c = 0; c <= n_chunks; c++) {
         if (c < n_chunks) {
-            // centred samples of chunk c (zero past the end), exclusive prefix, into slot c mod 3
-            const int base = c * kWarpCS;
-            uint32_t x[kWarpRows];
+            // centred samples of chunk c (zero outside the series): lane l holds 16 consecutive ones
+            const int v0 = c * kWarpCS + 16 * lane;
+            const int t0 = v0 - mis;
+            uint32_t xs[16];
+            if (t0 >= 0 && t0 + 16 <= n) {
+                const int4* src = reinterpret_cast<const int4*>(Sa + v0);
 #pragma unroll
-            for (int m = 0; m < kWarpRows; m++) {
-                const int t = base + 32 * m + lane;
-                x[m] = t < n ? static_cast<uint32_t>(__ldg(v.S + t)) - m0u : 0u;
+                for (int q = 0; q < 4; q++) {
+                    const int4 a = __ldg(src + q);
+                    xs[4 * q + 0] = static_cast<uint32_t>(a.x) - m0u;
+                    xs[4 * q + 1] = static_cast<uint32_t>(a.y) - m0u;
+                    xs[4 * q + 2] = static_cast<uint32_t>(a.z) - m0u;
+                    xs[4 * q + 3] = static_cast<uint32_t>(a.w) - m0u;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; k++) {
+                    const int t = t0 + k;
+                    xs[k] = (t >= 0 && t < n) ? static_cast<uint32_t>(__ldg(v.S + t)) - m0u : 0u;
+                }
             }
+            // exclusive prefix: within the lane, then across lanes (one warp scan of the lane totals)
+            uint32_t lane_tot = 0;
+#pragma unroll
+            for (int k = 0; k < 16; k++) {
+                const uint32_t x = xs[k];
+                xs[k] = lane_tot;  // exclusive within the lane
+                lane_tot += x;
+            }
+            uint32_t incl = lane_tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const uint32_t off = carry + incl - lane_tot;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+            // padded ring layout: entry j of a slot at word j + j / 32 (conflict-free for these
+            // 16-consecutive-per-lane stores and for lane-consecutive reads); slots are kSlotWords apart
             const int slot = c % 3;
+            const uint32_t at = ring_s + 4u * static_cast<uint32_t>(slot * kSlotWords + 16 * lane + (lane >> 1));
+            const bool mir = slot == 0 && 16 * lane < mirror;
+            const uint32_t am = ring_s + 4u * static_cast<uint32_t>(3 * kSlotWords + 16 * lane + (lane >> 1));
 #pragma unroll
-            for (int m = 0; m < kWarpRows; m++) {
-                uint32_t incl = x[m];
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const uint32_t p = carry + incl - x[m];
-                const uint32_t at = ring_s + 4u * static_cast<uint32_t>(slot * kWarpCS + 32 * m + lane);
-                asm volatile("st.shared.u32 [%0], %1;" ::"r"(at), "r"(p) : "memory");
-                if (slot == 0 && 32 * m < mirror) {
-                    const uint32_t am = ring_s + 4u * static_cast<uint32_t>(3 * kWarpCS + 32 * m + lane);
-                    asm volatile("st.shared.u32 [%0], %1;" ::"r"(am), "r"(p) : "memory");
-                }
-                carry += __shfl_sync(0xffffffffu, incl, 31);
+            for (int k = 0; k < 16; k++) {
+                const uint32_t pv = off + xs[k];
+                asm volatile("st.shared.u32 [%0], %1;" ::"r"(at + 4u * k), "r"(pv) : "memory");
+                if (mir) asm volatile("st.shared.u32 [%0], %1;" ::"r"(am + 4u * k), "r"(pv) : "memory");
             }
             __syncwarp();
         }
         if (c == 0) continue;
-        // evaluate chunk c-1: t = (c-1)*CS + 32*m + lane
+        // evaluate chunk e = c - 1: vv = e*CS + 32*m + lane, sample t = vv - mis
         const int e = c - 1;
         const int ebase = e * kWarpCS;
-        if (ebase >= n) break;
-        const uint32_t s_slot = ring_s + 4u * static_cast<uint32_t>((e % 3) * kWarpCS + lane);
-        const bool interior = ebase + kWarpCS + wmax <= n;  // no window of this chunk passes the end
+        if (ebase >= nv) break;
+        const uint32_t s_slot = ring_s + 4u * static_cast<uint32_t>((e % 3) * kSlotWords);
+        // word address of chunk-relative prefix entry j (j may run past this slot into the next one,
+        // which the padding keeps contiguous: slot size = padded 512)
+        auto addr = [&](int j) { return s_slot + 4u * static_cast<uint32_t>(j + (j >> 5)); };
+        const bool interior = ebase - mis >= 0 && ebase + kWarpCS + wmax <= nv;  // every window inside
         if (bound) {
             int32_t mx0 = -2147483647 - 1, mx1 = mx0, mx2 = mx0;
             const int rows = kWarpRows + (wmax - 1 + 31) / 32;
             for (int m = 0; m < rows; m++) {
-                const int s_ = ebase + 32 * m + lane;
-                const uint32_t a0 = s_slot + 128u * m;
-                if (s_ + 1 <= n) {
+                const int j = 32 * m + lane;
+                const int t = ebase + j - mis;
+                if (t >= 0 && t + 1 <= n) {
                     uint32_t p0, p1;
-                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(p0) : "r"(a0));
-                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(p1) : "r"(a0 + 4u));
+                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(p0) : "r"(addr(j)));
+                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(p1) : "r"(addr(j + 1)));
                     mx0 = max(mx0, static_cast<int32_t>(p1 - p0));
-                    if (s_ + 8 <= n) {
+                    if (t + 8 <= n) {
                         uint32_t p8;
-                        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(p8) : "r"(a0 + 32u));
+                        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(p8) : "r"(addr(j + 8)));
                         mx1 = max(mx1, static_cast<int32_t>(p8 - p0));
                     }
-                    if (wmax >= 64 && s_ + 64 <= n) {
+                    if (wmax >= 64 && t + 64 <= n) {
                         uint32_t p64;
-                        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(p64) : "r"(a0 + 256u));
+                        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(p64) : "r"(addr(j + 64)));
                         mx2 = max(mx2, static_cast<int32_t>(p64 - p0));
                     }
                 }
@@ -193,23 +226,23 @@ __device__ __forceinline__ void boxcar_series_warp(const BoxSeries& v, uint32_t*
         }
 #pragma unroll 2
         for (int m = 0; m < kWarpRows; m++) {
-            const int t = ebase + 32 * m + lane;
-            const uint32_t a0 = s_slot + 128u * m;
+            const int j = 32 * m + lane;
+            const int t = ebase + j - mis;
             uint32_t p0;
-            asm volatile("ld.shared.u32 %0, [%1];" : "=r"(p0) : "r"(a0));
+            asm volatile("ld.shared.u32 %0, [%1];" : "=r"(p0) : "r"(addr(j)));
             bool any = false;
             if (interior) {
 #pragma unroll
                 for (int k = 0; k < NWB; k++) {
                     uint32_t pw;
-                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(pw) : "r"(a0 + wb[k]));
+                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(pw) : "r"(addr(j + wk[k])));
                     any |= static_cast<int32_t>(pw - p0) > tk[k];
                 }
-            } else {
+            } else if (t >= 0) {
 #pragma unroll
                 for (int k = 0; k < NWB; k++) {
                     uint32_t pw;
-                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(pw) : "r"(a0 + wb[k]));
+                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(pw) : "r"(addr(j + wk[k])));
                     any |= (t + wk[k] <= n) && (static_cast<int32_t>(pw - p0) > tk[k]);
                 }
             }
@@ -221,9 +254,9 @@ __device__ __forceinline__ void boxcar_series_warp(const BoxSeries& v, uint32_t*
                 const float offs = __shfl_sync(0xffffffffu, offs_l, k);
                 bool pred = false;
                 float snr = 0.f;
-                if (t + w <= n) {
+                if (t >= 0 && t + w <= n) {
                     uint32_t pw;
-                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(pw) : "r"(a0 + 4u * w));
+                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(pw) : "r"(addr(j + w)));
                     const int32_t bc = static_cast<int32_t>(pw - p0);
                     snr = (static_cast<float>(bc) - offs) * scale;
                     pred = snr > v.thr;
