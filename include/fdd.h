@@ -255,12 +255,15 @@ int fdd_variant_info(int32_t variant, int32_t* bytes_per_sample, int32_t* dm_per
 /* Diagnostics: the tables of pattern-factored variant `variant` (a global
  * variant index with *group > 0) for native-rate range r of a plan
  * description, built on the host only (no GPU), for inspection and CPU
- * checks of the kernel's shared-memory addressing.  info[0..12] receives Lw
- * (raw row words; < 0 if the layout does not fit), pattern-region bytes,
- * groups, stages, ints per descriptor, shared-memory bytes, descriptors,
- * DM blocks, then the byte offsets (from the kernel's 128-byte-aligned
- * shared-memory base) of the zero row, the raw-row buffers, one raw slot's
- * size, the pattern region and the two mbarriers.  Array arguments may be NULL (sizes first, then data): base
+ * checks of the kernel's shared-memory addressing.  info[0..13] receives Lw
+ * (raw row words; < 0 if the layout does not fit), bytes of one pattern-row
+ * buffer, groups, stages, ints per descriptor, shared-memory bytes,
+ * descriptors, DM blocks, then the byte offsets (from the kernel's
+ * 128-byte-aligned shared-memory base) of the zero row, the raw-row buffers,
+ * one raw slot's size, the pattern region and the two mbarriers, and the
+ * number of pattern-row buffers (2: stage s + 1 is built into the other
+ * buffer while stage s accumulates; the descriptor and offset tables then
+ * hold the buffer's address).  Array arguments may be NULL (sizes first, then data): base
  * [n_blk][n_chan], goff [n_blk][n_groups][BD], pdesc [n_desc][desc_ints],
  * pd_idx [n_blk][n_stages][2], delays [n_dm][n_chan]. */
 int fdd_fact_tables_host(const fdd_plan_desc* desc, const int16_t* sb_map_host, int32_t range, int32_t variant,

@@ -332,6 +332,7 @@ class Graph:
             pass
 
 
+FDD_ERR_UNSUPPORTED = -5
 FDD_ERR_SEQUENCE = -8
 FDD_BATCH_SB_FACTORED = 1000
 FDD_BATCH_SB_PERSISTENT = 1001
@@ -587,14 +588,14 @@ def fact_tables_host(n_tab, n_chan, n_sb, chan_freq_mhz, t_samp_s, ranges, sb_ma
     keep = []
     desc = _plan_desc(n_tab, n_chan, n_sb, chan_freq_mhz, t_samp_s, ranges, 0.0, keep)
     sb = np.ascontiguousarray(sb_map, dtype=np.int16)
-    info = np.zeros(13, np.int64)
+    info = np.zeros(14, np.int64)
     args = [ctypes.byref(desc), sb.ctypes.data_as(ctypes.c_void_p), int(r), int(variant), int(chan_per_stage),
             info.ctypes.data_as(ctypes.c_void_p)]
     _check(L.fdd_fact_tables_host(*args, None, None, None, None, None), "fdd_fact_tables_host")
     Lw, pat_bytes, n_groups, n_stages, desc_ints, smem, n_desc, n_blk = [int(v) for v in info[:8]]
     out = dict(Lw=Lw, pat_bytes=pat_bytes, n_groups=n_groups, n_stages=n_stages, desc_ints=desc_ints,
                smem_bytes=smem, n_desc=n_desc, n_blk=n_blk)
-    out.update(zip(["zero_off", "raw_off", "rb", "pat_off", "bar_off"], [int(v) for v in info[8:]]))
+    out.update(zip(["zero_off", "raw_off", "rb", "pat_off", "bar_off", "pat_bufs"], [int(v) for v in info[8:]]))
     if Lw < 0:
         return out
     v = variants()[int(variant)]

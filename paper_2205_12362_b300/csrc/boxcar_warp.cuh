@@ -30,6 +30,39 @@ constexpr int kWarpRing = 4 * kSlotWords;            // three slots + mirror of 
 constexpr int kBoxWarps = 4;                      // warps (series) per block
 constexpr int kBoundWmax = 128;                   // widest width of the chunk pre-check
 
+constexpr int kBoundRows = kWarpRows + (kBoundWmax - 1 + 31) / 32;  // pre-check rows at most
+
+// 32-bit shared load at a compile-time byte offset from a per-lane address.
+template <int OFF>
+__device__ __forceinline__ uint32_t lds_at(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(a), "n"(OFF));
+    return v;
+}
+
+// Pre-check of an interior chunk, rows M .. rows-1: lane l of row m takes start j = 32 m + l, whose
+// prefix entries j, j + 1, j + 8 (and j + 64) sit at the lane's base addresses + 132 m bytes in the
+// padded ring (entry J at word J + J / 32, and (32 m + l + k) / 32 = m + (l + k) / 32).
+template <int M, bool B64>
+struct PrecheckRows {
+    __device__ static __forceinline__ void run(uint32_t a0, uint32_t a1, uint32_t a8, uint32_t a64, int rows,
+                                               int32_t& mx0, int32_t& mx1, int32_t& mx2) {
+        if constexpr (M < kBoundRows) {
+            if (M >= kWarpRows && M >= rows) return;
+            const uint32_t p0 = lds_at<132 * M>(a0);
+            const uint32_t p1 = lds_at<132 * M>(a1);
+            const uint32_t p8 = lds_at<132 * M>(a8);
+            mx0 = max(mx0, static_cast<int32_t>(p1 - p0));
+            mx1 = max(mx1, static_cast<int32_t>(p8 - p0));
+            if constexpr (B64) {
+                const uint32_t p64 = lds_at<132 * M>(a64);
+                mx2 = max(mx2, static_cast<int32_t>(p64 - p0));
+            }
+            PrecheckRows<M + 1, B64>::run(a0, a1, a8, a64, rows, mx0, mx1, mx2);
+        }
+    }
+};
+
 // One series as the warp needs it.
 struct BoxSeries {
     const int32_t* S;                    // [n]
@@ -95,6 +128,7 @@ __device__ __forceinline__ void boxcar_series_warp(const BoxSeries& v, uint32_t*
         wmax = max(wmax, wk[k]);
     }
     const uint32_t m0u = static_cast<uint32_t>(m0);
+    const uint32_t negm0 = 0u - m0u, neg16m0 = 0u - 16u * m0u;
     // Virtual index vv = t + mis, mis = the row's misalignment in samples, so that chunk c
     // (vv in [512 c, 512 c + 512)) starts on a 16-byte boundary of the series and lane l's 16
     // consecutive samples vv = 512 c + 16 l + k come in as four aligned 16-byte loads.
@@ -118,48 +152,74 @@ __device__ __forceinline__ void boxcar_series_warp(const BoxSeries& v, uint32_t*
         bsel[k] = (w >= 64 && w % 64 == 0) ? 2 : ((w >= 8 && w % 8 == 0) ? 1 : 0);
         bmul[k] = w / (bsel[k] == 2 ? 64 : (bsel[k] == 1 ? 8 : 1));
     }
+    // (w/b) M_b > tau_w  <=>  M_b > floor(tau_w / (w/b)): per base, the smallest such threshold over
+    // its widths (widths k >= n_width have w = 0 and never pass)
+    int32_t thb0 = 2147483647, thb1 = 2147483647, thb2 = 2147483647;
+#pragma unroll
+    for (int k = 0; k < NWB; k++) {
+        if (bmul[k] > 0) {
+            int32_t q = tk[k] / bmul[k];
+            if (tk[k] % bmul[k] != 0 && tk[k] < 0) q -= 1;  // floor
+            if (bsel[k] == 0) thb0 = min(thb0, q);
+            if (bsel[k] == 1) thb1 = min(thb1, q);
+            if (bsel[k] == 2) thb2 = min(thb2, q);
+        }
+    }
     // the ring's mirror of slot 0 must cover every read past the end of slot 2
     const int mirror = bound ? min(kWarpCS, 2 * wmax + 64) : wmax;
 
-    for (int c = 0; c <= n_chunks; c++) {
-        if (c < n_chunks) {
-            // centred samples of chunk c (zero outside the series): lane l holds 16 consecutive ones
-            const int v0 = c * kWarpCS + 16 * lane;
-            const int t0 = v0 - mis;
-            uint32_t xs[16];
-            if (t0 >= 0 && t0 + 16 <= n) {
-                const int4* src = reinterpret_cast<const int4*>(Sa + v0);
+    // raw samples of chunk c for lane l: 16 consecutive ones, m0 outside the series (centred 0)
+    auto fetch = [&](int c, uint32_t (&dst)[16]) {
+        const int v0 = c * kWarpCS + 16 * lane;
+        const int t0 = v0 - mis;
+        if (t0 >= 0 && t0 + 16 <= n) {
+            const int4* src = reinterpret_cast<const int4*>(Sa + v0);
 #pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const int4 a = __ldg(src + q);
-                    xs[4 * q + 0] = static_cast<uint32_t>(a.x) - m0u;
-                    xs[4 * q + 1] = static_cast<uint32_t>(a.y) - m0u;
-                    xs[4 * q + 2] = static_cast<uint32_t>(a.z) - m0u;
-                    xs[4 * q + 3] = static_cast<uint32_t>(a.w) - m0u;
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < 16; k++) {
-                    const int t = t0 + k;
-                    xs[k] = (t >= 0 && t < n) ? static_cast<uint32_t>(__ldg(v.S + t)) - m0u : 0u;
-                }
+            for (int q = 0; q < 4; q++) {
+                const int4 a = __ldg(src + q);
+                dst[4 * q + 0] = static_cast<uint32_t>(a.x);
+                dst[4 * q + 1] = static_cast<uint32_t>(a.y);
+                dst[4 * q + 2] = static_cast<uint32_t>(a.z);
+                dst[4 * q + 3] = static_cast<uint32_t>(a.w);
             }
-            // exclusive prefix: within the lane, then across lanes (one warp scan of the lane totals)
-            uint32_t lane_tot = 0;
+        } else {
 #pragma unroll
             for (int k = 0; k < 16; k++) {
-                const uint32_t x = xs[k];
-                xs[k] = lane_tot;  // exclusive within the lane
-                lane_tot += x;
+                const int t = t0 + k;
+                dst[k] = (t >= 0 && t < n) ? static_cast<uint32_t>(__ldg(v.S + t)) : m0u;
             }
+        }
+    };
+    uint32_t nx[16];  // the next chunk's samples, loaded a chunk ahead
+    fetch(0, nx);
+
+    // Chunk c = n_chunks lies wholly past the series: its flat prefix entries are written too, so
+    // every chunk's pre-check can read its successor's first entries.
+    for (int c = 0; c <= n_chunks; c++) {
+        {
+            uint32_t xs[16];
+#pragma unroll
+            for (int k = 0; k < 16; k++) xs[k] = nx[k];
+            if (c < n_chunks) fetch(c + 1, nx);  // in flight while this chunk is scanned and the last one evaluated
+            // lane total of the centred samples, then one warp scan of the lane totals
+            uint32_t lane_tot = neg16m0;
+#pragma unroll
+            for (int k = 0; k < 16; k += 2) lane_tot = lane_tot + xs[k] + xs[k + 1];
             uint32_t incl = lane_tot;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += y;
             }
-            const uint32_t off = carry + incl - lane_tot;
+            // exclusive prefix entries of the lane's 16 samples
+            uint32_t pv = carry + incl - lane_tot;
             carry += __shfl_sync(0xffffffffu, incl, 31);
+#pragma unroll
+            for (int k = 0; k < 16; k++) {
+                const uint32_t x = xs[k];
+                xs[k] = pv;
+                pv = pv + x + negm0;
+            }
             // padded ring layout: entry j of a slot at word j + j / 32 (conflict-free for these
             // 16-consecutive-per-lane stores and for lane-consecutive reads); slots are kSlotWords apart
             const int slot = c % 3;
@@ -167,10 +227,12 @@ __device__ __forceinline__ void boxcar_series_warp(const BoxSeries& v, uint32_t*
             const bool mir = slot == 0 && 16 * lane < mirror;
             const uint32_t am = ring_s + 4u * static_cast<uint32_t>(3 * kSlotWords + 16 * lane + (lane >> 1));
 #pragma unroll
-            for (int k = 0; k < 16; k++) {
-                const uint32_t pv = off + xs[k];
-                asm volatile("st.shared.u32 [%0], %1;" ::"r"(at + 4u * k), "r"(pv) : "memory");
-                if (mir) asm volatile("st.shared.u32 [%0], %1;" ::"r"(am + 4u * k), "r"(pv) : "memory");
+            for (int k = 0; k < 16; k++)
+                asm volatile("st.shared.u32 [%0], %1;" ::"r"(at + 4u * k), "r"(xs[k]) : "memory");
+            if (mir) {
+#pragma unroll
+                for (int k = 0; k < 16; k++)
+                    asm volatile("st.shared.u32 [%0], %1;" ::"r"(am + 4u * k), "r"(xs[k]) : "memory");
             }
             __syncwarp();
         }
@@ -185,41 +247,20 @@ __device__ __forceinline__ void boxcar_series_warp(const BoxSeries& v, uint32_t*
         auto addr = [&](int j) { return s_slot + 4u * static_cast<uint32_t>(j + (j >> 5)); };
         const bool interior = ebase - mis >= 0 && ebase + kWarpCS + wmax <= nv;  // every window inside
         if (bound) {
+            // Every entry the pre-check reads is written (chunk c follows chunk e in the ring), and a
+            // start outside the series only adds windows of the zero-padded series to the maxima,
+            // which keeps them upper bounds.
             int32_t mx0 = -2147483647 - 1, mx1 = mx0, mx2 = mx0;
             const int rows = kWarpRows + (wmax - 1 + 31) / 32;
-            for (int m = 0; m < rows; m++) {
-                const int j = 32 * m + lane;
-                const int t = ebase + j - mis;
-                if (t >= 0 && t + 1 <= n) {
-                    uint32_t p0, p1;
-                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(p0) : "r"(addr(j)));
-                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(p1) : "r"(addr(j + 1)));
-                    mx0 = max(mx0, static_cast<int32_t>(p1 - p0));
-                    if (t + 8 <= n) {
-                        uint32_t p8;
-                        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(p8) : "r"(addr(j + 8)));
-                        mx1 = max(mx1, static_cast<int32_t>(p8 - p0));
-                    }
-                    if (wmax >= 64 && t + 64 <= n) {
-                        uint32_t p64;
-                        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(p64) : "r"(addr(j + 64)));
-                        mx2 = max(mx2, static_cast<int32_t>(p64 - p0));
-                    }
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                mx0 = max(mx0, __shfl_xor_sync(0xffffffffu, mx0, o));
-                mx1 = max(mx1, __shfl_xor_sync(0xffffffffu, mx1, o));
-                mx2 = max(mx2, __shfl_xor_sync(0xffffffffu, mx2, o));
-            }
-            bool need = false;
-#pragma unroll
-            for (int k = 0; k < NWB; k++) {
-                const int32_t mb = bsel[k] == 2 ? mx2 : (bsel[k] == 1 ? mx1 : mx0);
-                need |= static_cast<int64_t>(bmul[k]) * mb > static_cast<int64_t>(tk[k]);
-            }
-            if (!need) {
+            const uint32_t a0 = s_slot + 4u * static_cast<uint32_t>(lane);
+            const uint32_t a1 = s_slot + 4u * static_cast<uint32_t>(lane + 1 + ((lane + 1) >> 5));
+            const uint32_t a8 = s_slot + 4u * static_cast<uint32_t>(lane + 8 + ((lane + 8) >> 5));
+            const uint32_t a64 = s_slot + 4u * static_cast<uint32_t>(lane + 66);
+            if (wmax >= 64)
+                PrecheckRows<0, true>::run(a0, a1, a8, a64, rows, mx0, mx1, mx2);
+            else
+                PrecheckRows<0, false>::run(a0, a1, a8, a64, rows, mx0, mx1, mx2);
+            if (!__any_sync(0xffffffffu, mx0 > thb0 || mx1 > thb1 || mx2 > thb2)) {
                 __syncwarp();  // slot e % 3 may be rewritten by chunk c + 2
                 continue;
             }

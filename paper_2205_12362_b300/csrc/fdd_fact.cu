@@ -23,8 +23,11 @@
 // and the raw row length Lw and the pattern region size of the layout.
 // Shared memory, from a 128-byte-aligned base: [zero row | 2 raw buffers x
 // CC slots (one unshifted row each, TMA destinations, 128-byte aligned) |
-// pattern rows | 2 x stage offsets | stage descriptors | 2 mbarriers];
-// stage s builds from raw buffer s & 1.
+// PB x pattern rows | (PB + 1) x stage offsets | PB x stage descriptors |
+// 2 mbarriers]; stage s builds from raw buffer s & 1.  With PB = 2 stage s's
+// pattern rows live in pattern buffer s & 1 (its descriptors' destinations
+// and its trials' offsets carry that buffer's address), so the kernel can
+// build stage s + 1 while it accumulates stage s.
 #include <algorithm>
 #include <map>
 #include <vector>
@@ -162,11 +165,27 @@ FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactV
     }
     ft.Lw = static_cast<int32_t>(Lw);
     ft.pat_bytes = static_cast<int32_t>(align_up(static_cast<size_t>(pat_region), 16));
+    ft.pat_bufs = v.PB;
     // resolve shared-memory addresses
     ft.zero_off = 0;
     ft.rb = static_cast<int32_t>(align_up(static_cast<size_t>(4 * Lw), 128));
     ft.raw_off = static_cast<int32_t>(align_up(static_cast<size_t>(4 * Lw + 16), 128));
     ft.pat_off = ft.raw_off + 2 * CC * ft.rb;
+    if (v.PB == 2) {
+        // stage s's rows in pattern buffer s & 1
+        for (int b = 0; b < n_blk; b++)
+            for (int s = 0; s < n_stages; s++) {
+                const int32_t shift = (s & 1) * ft.pat_bytes;
+                const size_t k = (static_cast<size_t>(b) * n_stages + s) * 2;
+                for (int d = ft.pd_idx[k]; d < ft.pd_idx[k] + ft.pd_idx[k + 1]; d++) {
+                    ft.pdesc[static_cast<size_t>(d) * ft.desc_ints] += shift;
+                    ft.pdesc[static_cast<size_t>(d) * ft.desc_ints + 1] += shift;
+                }
+                for (int gl = 0; gl < gps && s * gps + gl < n_groups; gl++)
+                    for (int jj = 0; jj < BD; jj++)
+                        ft.goff[(static_cast<size_t>(b) * n_groups + s * gps + gl) * BD + jj] += shift;
+            }
+    }
     for (size_t di = 0; di < ft.pdesc.size(); di += ft.desc_ints) {
         ft.pdesc[di] += ft.pat_off;
         ft.pdesc[di + 1] += ft.pat_off;
@@ -181,7 +200,8 @@ FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactV
         }
     }
     for (int32_t& g : ft.goff) g += ft.pat_off;
-    ft.bar_off = ft.pat_off + ft.pat_bytes + 2 * gps * BD * 4 + ft.max_desc * ft.desc_ints * 4;
+    ft.desc_bytes = ft.max_desc * ft.desc_ints * 4;
+    ft.bar_off = ft.pat_off + v.PB * ft.pat_bytes + (v.PB + 1) * gps * BD * 4 + v.PB * ft.desc_bytes;
     // + 16 bytes of mbarriers, + 128 for aligning the dynamic shared-memory base
     ft.smem_bytes = static_cast<size_t>(ft.bar_off) + 16 + 128;
     return ft;

@@ -68,6 +68,8 @@ cudaError_t launch_dedisp(int variant, const DedispArgs& a, cudaStream_t s);
 //         no staging-register budget.
 struct FactVariant {
     int G, NW, DPW, WARPS;
+    int PB = 1;  // pattern-row buffers: 2 = stage s+1's rows are built while stage s accumulates
+                 // (one block barrier per stage instead of two)
     int bd() const { return WARPS * DPW; }
     int tile() const { return 64 * NW; }
     int threads() const { return WARPS * 32; }
@@ -99,7 +101,8 @@ struct FactArgs {
     int32_t Lw, CC, n_stages, n_groups, pat_bytes;
     int32_t zero_off;           // shared-memory layout (bytes from the 128-aligned base): zero row,
     int32_t raw_off, rb;        //   raw slots (2 buffers x CC slots of rb bytes),
-    int32_t pat_off;            //   pattern rows (pat_bytes), then stage offsets and descriptors,
+    int32_t pat_off;            //   pattern rows (PB buffers of pat_bytes), then stage offsets and
+    int32_t desc_bytes;         //   descriptors (PB buffers of desc_bytes),
     int32_t bar_off;            //   two mbarriers
 };
 

@@ -257,7 +257,7 @@ int configure_fact(fdd_plan* p, RangeState& r, int fv, int CC) {
     const fdd::FactVariant& v = fdd::fact_variant(fv);
     FactTables best;
     int best_cc = 0;
-    for (int cc : {64, 48, 32, 16, 8}) {
+    for (int cc : {64, 48, 32, 16, 8, 4}) {
         if (CC != 0 && cc != CC) continue;
         if (cc % v.G) continue;
         FactTables ft = build_fact_tables(p, r, v, cc);
@@ -286,6 +286,7 @@ int configure_fact(fdd_plan* p, RangeState& r, int fv, int CC) {
     r.f_rb = best.rb;
     r.f_pat_off = best.pat_off;
     r.f_bar_off = best.bar_off;
+    r.f_desc_bytes = best.desc_bytes;
     r.f_work_ratio = static_cast<float>(best.work_ratio);
     return FDD_OK;
 }
@@ -351,6 +352,7 @@ cudaError_t launch_range_dedisp(const fdd_plan* p, const RangeState& r, const fd
     fa.rb = r.f_rb;
     fa.pat_off = r.f_pat_off;
     fa.bar_off = r.f_bar_off;
+    fa.desc_bytes = r.f_desc_bytes;
     if (cudaError_t e = fdd::encode_fact_map(fa, static_cast<int64_t>(p->n_tab) * p->n_chan); e != cudaSuccess) return e;
     return fdd::launch_dedisp_fact(r.fact, fa, r.f_smem, s);
 }
@@ -1000,6 +1002,7 @@ int fdd_fact_tables_host(const fdd_plan_desc* desc, const int16_t* sb_map_host, 
     info[10] = ft.rb;
     info[11] = ft.pat_off;
     info[12] = ft.bar_off;
+    info[13] = ft.pat_bufs;
     if (ft.Lw < 0) return FDD_OK;
     if (base) std::memcpy(base, ft.base.data(), ft.base.size() * sizeof(int32_t));
     if (goff) std::memcpy(goff, ft.goff.data(), ft.goff.size() * sizeof(int32_t));

@@ -25,7 +25,7 @@ struct RangeState {
     // pattern-factored kernel (fact >= 0 selects it instead of `variant`)
     int fact = -1;
     int32_t f_CC = 0, f_Lw = 0, f_pat_bytes = 0, f_n_stages = 0, f_n_groups = 0;
-    int32_t f_zero_off = 0, f_raw_off = 0, f_rb = 0, f_pat_off = 0, f_bar_off = 0;
+    int32_t f_zero_off = 0, f_raw_off = 0, f_rb = 0, f_pat_off = 0, f_bar_off = 0, f_desc_bytes = 0;
     float f_work_ratio = 1.f;         // adds of the factored kernel per brute-force add
     size_t f_smem = 0;
     int32_t* d_fbase = nullptr;
@@ -147,6 +147,7 @@ struct FactTables {
     int32_t Lw = 0, pat_bytes = 0, n_groups = 0, n_stages = 0, desc_ints = 0;
     int32_t max_desc = 0;  // most pattern rows of one (block, stage)
     int32_t zero_off = 0, raw_off = 0, rb = 0, pat_off = 0, bar_off = 0;  // shared-memory layout (bytes)
+    int32_t desc_bytes = 0, pat_bufs = 1;  // one descriptor buffer; pattern-row (and descriptor) buffers
     double work_ratio = 1.0;  // (pattern-build adds + per-trial adds) / brute-force adds, per time tile
     size_t smem_bytes = 0;
 };

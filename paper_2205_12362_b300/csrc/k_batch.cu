@@ -55,6 +55,77 @@ __global__ void __launch_bounds__(256) k_batch_downsample(const __grid_constant_
         detail::downsample_chunk(J.tabs + row * J.tab_pitch + phase, J.ds[k] + row * J.ds_pitch[k], n_y, D, j0);
 }
 
+// Every factor in {2, 4, 8} and every bin starting at the first input sample: one pass over the
+// input.  Thread q reads bytes [8 DMAX q, 8 DMAX (q + 1)) of a row and writes every factor's bins
+// in them: the D=2 sums as 16-bit lanes of one word per input word, each coarser factor from
+// pairs of the next finer sums.
+template <int DMAX>
+__global__ void __launch_bounds__(256) k_batch_downsample_pow2(const __grid_constant__ BatchParams p, int64_t rows) {
+    constexpr int NB = 8 * DMAX;  // input bytes per thread
+    const BatchJob& J = p.jobs[blockIdx.z];
+    const int64_t b0 = NB * (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
+    if (b0 >= J.n_in) return;
+    int k2 = -1, k4 = -1, k8 = -1;
+    for (int k = 0; k < p.n_ds; k++) {
+        if (p.ds_factor[k] == 2) k2 = k;
+        if (p.ds_factor[k] == 4) k4 = k;
+        if (p.ds_factor[k] == 8) k8 = k;
+    }
+    for (int64_t row = blockIdx.y; row < rows; row += gridDim.y) {
+        const uint8_t* src = J.tabs + row * J.tab_pitch + b0;
+        if (b0 + NB <= J.n_in) {
+            uint32_t u2[2 * DMAX];  // D=2 sums, two per word
+#pragma unroll
+            for (int v = 0; v < DMAX / 2; v++) {
+                const uint4 x = __ldg(reinterpret_cast<const uint4*>(src) + v);
+                const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int e = 0; e < 4; e++) u2[4 * v + e] = (w[e] & 0x00FF00FFu) + ((w[e] >> 8) & 0x00FF00FFu);
+            }
+            if (k2 >= 0) {
+                uint4* dst = reinterpret_cast<uint4*>(J.ds[k2] + row * J.ds_pitch[k2] + b0 / 2);
+#pragma unroll
+                for (int v = 0; v < DMAX / 2; v++)
+                    dst[v] = make_uint4(u2[4 * v], u2[4 * v + 1], u2[4 * v + 2], u2[4 * v + 3]);
+            }
+            if constexpr (DMAX >= 4) {
+                uint32_t u4[DMAX];
+#pragma unroll
+                for (int i = 0; i < DMAX; i++)
+                    u4[i] = __byte_perm(u2[2 * i], u2[2 * i + 1], 0x5410) + __byte_perm(u2[2 * i], u2[2 * i + 1], 0x7632);
+                if (k4 >= 0) {
+                    uint4* dst = reinterpret_cast<uint4*>(J.ds[k4] + row * J.ds_pitch[k4] + b0 / 4);
+#pragma unroll
+                    for (int v = 0; v < DMAX / 4; v++)
+                        dst[v] = make_uint4(u4[4 * v], u4[4 * v + 1], u4[4 * v + 2], u4[4 * v + 3]);
+                }
+                if constexpr (DMAX >= 8) {
+                    uint32_t u8[DMAX / 2];
+#pragma unroll
+                    for (int i = 0; i < DMAX / 2; i++)
+                        u8[i] = __byte_perm(u4[2 * i], u4[2 * i + 1], 0x5410) +
+                                __byte_perm(u4[2 * i], u4[2 * i + 1], 0x7632);
+                    if (k8 >= 0)
+                        *reinterpret_cast<uint4*>(J.ds[k8] + row * J.ds_pitch[k8] + b0 / 8) =
+                            make_uint4(u8[0], u8[1], u8[2], u8[3]);
+                }
+            }
+        } else {
+            // ragged end of the row: the complete bins of each factor, one by one
+            for (int k = 0; k < p.n_ds; k++) {
+                const int D = p.ds_factor[k];
+                const int64_t n_y = J.n_in / D;
+                uint16_t* dst = J.ds[k] + row * J.ds_pitch[k];
+                for (int64_t j = b0 / D; j < (b0 + NB) / D && j < n_y; j++) {
+                    uint32_t acc = 0;
+                    for (int e = 0; e < D; e++) acc += src[j * D - b0 + e];
+                    dst[j] = static_cast<uint16_t>(acc);
+                }
+            }
+        }
+    }
+}
+
 template <int E, int NW, int DPW, int WARPS, int MAXIT>
 __global__ void __launch_bounds__(WARPS * 32) k_dedisp_persistent(const __grid_constant__ BatchParams p) {
     __shared__ unsigned long long s_item;
@@ -226,6 +297,30 @@ cudaError_t launch_batch_downsample(const BatchParams& p, cudaStream_t s) {
     const int64_t n_y = n_in_max / d_min;
     if (n_y == 0) return cudaSuccess;
     const int64_t rows = static_cast<int64_t>(p.n_tab) * p.n_chan;
+    // one pass for factors in {2, 4, 8} with bins from the first sample and 16-byte aligned rows
+    bool pow2 = true;
+    int d_max = 0;
+    for (int k = 0; k < p.n_ds; k++) {
+        const int D = p.ds_factor[k];
+        pow2 = pow2 && (D == 2 || D == 4 || D == 8);
+        d_max = std::max(d_max, D);
+        for (int j = 0; j < p.n_jobs && pow2; j++)
+            pow2 = p.jobs[j].ds_phase[k] == 0 && p.jobs[j].ds_pitch[k] % 8 == 0 && p.jobs[j].tab_pitch % 16 == 0 &&
+                   (reinterpret_cast<uintptr_t>(p.jobs[j].ds[k]) & 15u) == 0 &&
+                   (reinterpret_cast<uintptr_t>(p.jobs[j].tabs) & 15u) == 0;
+    }
+    if (pow2) {
+        const unsigned gy = static_cast<unsigned>(std::min<int64_t>(rows, 65535));
+        const int64_t per_block = 8LL * d_max * 256;
+        dim3 grid(static_cast<unsigned>((n_in_max + per_block - 1) / per_block), gy, static_cast<unsigned>(p.n_jobs));
+        if (d_max == 2)
+            k_batch_downsample_pow2<2><<<grid, 256, 0, s>>>(p, rows);
+        else if (d_max == 4)
+            k_batch_downsample_pow2<4><<<grid, 256, 0, s>>>(p, rows);
+        else
+            k_batch_downsample_pow2<8><<<grid, 256, 0, s>>>(p, rows);
+        return cudaGetLastError();
+    }
     dim3 grid(static_cast<unsigned>((n_y + 8 * 256 - 1) / (8 * 256)),
               static_cast<unsigned>(std::min<int64_t>(rows, 65535)), static_cast<unsigned>(p.n_jobs * p.n_ds));
     k_batch_downsample<<<grid, 256, 0, s>>>(p, rows);

@@ -164,13 +164,21 @@ __device__ __forceinline__ void build_rows(uint32_t d0, uint32_t d1, uint32_t s0
     if (two) b.finish(lane);
 }
 
-template <int G, int NW, int DPW, int WARPS>
+// PB = 1: per stage, build its pattern rows, barrier, accumulate, barrier.
+// PB = 2: two pattern-row buffers; one interval between barriers builds
+// stage s + 1 and accumulates stage s, so a warp that finishes its builds
+// goes straight on to its adds (the build rounds differ between warps) and
+// a stage costs one barrier.  Stage offsets then rotate over three buffers
+// (stage s + 2's are stored while stage s's are read) and descriptors over two.
+template <int G, int NW, int DPW, int WARPS, int PB>
 __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
     k_dedisp_fact(const __grid_constant__ FactArgs a) {
     constexpr int BD = WARPS * DPW;
     constexpr int T = 64 * NW;
     constexpr int DI = (3 + G + 3) / 4 * 4;
+    constexpr int NGB = PB + 1;  // stage-offset buffers
     static_assert(BD % 4 == 0, "BD must be a multiple of 4");
+    static_assert(PB == 1 || PB == 2, "one or two pattern-row buffers");
     extern __shared__ __align__(16) uint8_t smem_raw[];
 
     const int Lw = a.Lw, CC = a.CC;
@@ -179,8 +187,8 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
     const uint32_t s_unal = static_cast<uint32_t>(__cvta_generic_to_shared(smem_raw));
     const uint32_t s0 = (s_unal + 127u) & ~127u;
     uint8_t* smem = smem_raw + (s0 - s_unal);
-    int32_t* s_goff = reinterpret_cast<int32_t*>(smem + a.pat_off + a.pat_bytes);  // [2][gps][BD]
-    int32_t* s_desc = s_goff + 2 * gps * BD;  // [max_desc][DI] of the stage being built
+    int32_t* s_goff = reinterpret_cast<int32_t*>(smem + a.pat_off + PB * a.pat_bytes);  // [NGB][gps][BD]
+    int32_t* s_desc = s_goff + NGB * gps * BD;  // [PB][max_desc][DI]: descriptors of the stage(s) to build
     const uint32_t s_desc32 = static_cast<uint32_t>(__cvta_generic_to_shared(s_desc));
     const uint32_t s_bar = s0 + static_cast<uint32_t>(a.bar_off);  // two 8-byte mbarriers (raw buffers 0, 1)
 
@@ -255,11 +263,19 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
         if (threadIdx.x < n_desc_next * (DI / 4))
             pdv = __ldg(reinterpret_cast<const int4*>(a.pdesc + (int64_t)first * DI) + threadIdx.x);
     };
-    auto small_store = [&](int s, int buf) {
+    auto small_store = [&](int s, int buf, int dbuf) {
         const int ncc = min(CC, a.n_chan - s * CC);
         const int ngs = (ncc + G - 1) / G;
         if (threadIdx.x < ngs * (BD / 4)) reinterpret_cast<int4*>(s_goff + buf * gps * BD)[threadIdx.x] = po;
-        if (threadIdx.x < n_desc_next * (DI / 4)) reinterpret_cast<int4*>(s_desc)[threadIdx.x] = pdv;
+        if (threadIdx.x < n_desc_next * (DI / 4))
+            reinterpret_cast<int4*>(reinterpret_cast<uint8_t*>(s_desc) + dbuf * a.desc_bytes)[threadIdx.x] = pdv;
+    };
+    // every pattern row of one stage: warp w builds rows w, w + WARPS, w + 2 WARPS, ..., two at a
+    // time (two build chains per lane), so the counts differ by at most one
+    auto build_stage = [&](int n_desc, int dbuf) {
+        const uint32_t sd = s_desc32 + static_cast<uint32_t>(dbuf * a.desc_bytes);
+        for (int d = warp; d < n_desc; d += 2 * WARPS)
+            build_rows<G>(sd + 4u * DI * d, d + WARPS < n_desc ? sd + 4u * DI * (d + WARPS) : 0xffffffffu, s0, lane);
     };
 
     // Per output word: acc = two 16-bit partial sums (samples 2m, 2m+1); a
@@ -286,56 +302,17 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
     };
 
     const uint32_t s_lane = s0 + 4u * lane;
-    if (warp == 0) {
-        coords(0);
-        fire(0);
-        if (a.n_stages > 1) {
-            coords(1);
-            fire(1);
-        }
-        if (a.n_stages > 2) coords(2);
-    }
-    small_load(0);
-    small_store(0, 0);
-    __syncthreads();
-
     int since_fold = 0;  // channels held in the 16-bit lanes
-    for (int s = 0; s < a.n_stages; s++) {
-        const int buf = s & 1;
-        const bool next = s + 1 < a.n_stages;
+    // adds of stage s: every trial, one 16-bit pattern partial per group, offsets from buffer gbuf
+    auto accumulate = [&](int s, int gbuf) {
         const int ncc = min(CC, a.n_chan - s * CC);
         const int ngs = (ncc + G - 1) / G;
-        const int n_desc = n_desc_next;
-        if (next) small_load(s + 1);
-        const bool ok = tma::mbar_wait_bounded(s_bar + 8u * buf, static_cast<uint32_t>(s >> 1) & 1u);
-        if (ok) {
-            // rows d and d + WARPS together (two build chains per lane); warp w builds
-            // rows w, w + WARPS, w + 2 WARPS, ... so the counts differ by at most one
-            for (int d = warp; d < n_desc; d += 2 * WARPS)
-                build_rows<G>(s_desc32 + 4u * DI * d,
-                              d + WARPS < n_desc ? s_desc32 + 4u * DI * (d + WARPS) : 0xffffffffu, s0, lane);
-        }
-        // pattern rows complete; raw buffer buf and the descriptors free
-        if (__syncthreads_or(!ok)) {
-            // a raw-row copy did not land: flag it, let thread 0 wait (bounded) for this block's copies, stop
-            if (threadIdx.x == 0) {
-                atomicOr(a.status, 1u);
-                tma::mbar_wait_bounded(s_bar + 8u * buf, static_cast<uint32_t>(s >> 1) & 1u);
-                if (next) tma::mbar_wait_bounded(s_bar + 8u * (buf ^ 1), static_cast<uint32_t>((s + 1) >> 1) & 1u);
-            }
-            return;
-        }
-        if (warp == 0 && s + 2 < a.n_stages) {
-            fire(s + 2);                                    // into buffer buf, behind two stages of work
-            if (s + 3 < a.n_stages) coords(s + 3);
-        }
-        if (next) small_store(s + 1, buf ^ 1);
         if (since_fold + ncc > 256) {
             fold();
             since_fold = 0;
         }
         since_fold += ncc;
-        const int32_t* go = s_goff + buf * gps * BD + warp * DPW;
+        const int32_t* go = s_goff + gbuf * gps * BD + warp * DPW;
         int gl = 0;
 #pragma unroll 1
         for (; gl + 1 < ngs; gl += 2) {
@@ -363,7 +340,96 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
 #pragma unroll
                 for (int k = 0; k < NW; k++) acc[j][k] += lds32(s_lane + static_cast<uint32_t>(o0[j]) + 128u * k);
         }
-        __syncthreads();  // pattern rows consumed; next stage's offsets and descriptors visible
+    };
+    // a raw-row copy did not land: flag it, let thread 0 wait (bounded) for the copies of stages
+    // s1 and s2 (s2 < 0: none) still in flight, then the block stops
+    auto drain = [&](int s1, int s2) {
+        if (threadIdx.x == 0) {
+            atomicOr(a.status, 1u);
+            tma::mbar_wait_bounded(s_bar + 8u * (s1 & 1), static_cast<uint32_t>(s1 >> 1) & 1u);
+            if (s2 >= 0) tma::mbar_wait_bounded(s_bar + 8u * (s2 & 1), static_cast<uint32_t>(s2 >> 1) & 1u);
+        }
+    };
+
+    if (warp == 0) {
+        coords(0);
+        fire(0);
+        if (a.n_stages > 1) {
+            coords(1);
+            fire(1);
+        }
+        if (a.n_stages > 2) coords(2);
+    }
+    small_load(0);
+    small_store(0, 0, 0);
+    if constexpr (PB == 1) {
+        __syncthreads();
+        for (int s = 0; s < a.n_stages; s++) {
+            const int buf = s & 1;
+            const bool next = s + 1 < a.n_stages;
+            const int n_desc = n_desc_next;
+            if (next) small_load(s + 1);
+            const bool ok = tma::mbar_wait_bounded(s_bar + 8u * buf, static_cast<uint32_t>(s >> 1) & 1u);
+            if (ok) build_stage(n_desc, 0);
+            // pattern rows complete; raw buffer buf and the descriptors free
+            if (__syncthreads_or(!ok)) {
+                drain(s, next ? s + 1 : -1);
+                return;
+            }
+            if (warp == 0 && s + 2 < a.n_stages) {
+                fire(s + 2);                                    // into buffer buf, behind two stages of work
+                if (s + 3 < a.n_stages) coords(s + 3);
+            }
+            if (next) small_store(s + 1, buf ^ 1, 0);
+            accumulate(s, buf);
+            __syncthreads();  // pattern rows consumed; next stage's offsets and descriptors visible
+        }
+    } else {
+        // prologue: stage 1's offsets and descriptors stored, stage 0 built
+        int nd_build = n_desc_next;  // pattern rows of the stage built next
+        int nd_next = 0;
+        if (a.n_stages > 1) {
+            small_load(1);
+            small_store(1, 1, 1);
+            nd_next = n_desc_next;
+        }
+        __syncthreads();
+        {
+            const bool ok = tma::mbar_wait_bounded(s_bar, 0u);
+            if (ok) build_stage(nd_build, 0);
+            if (__syncthreads_or(!ok)) {
+                drain(0, a.n_stages > 1 ? 1 : -1);
+                return;
+            }
+        }
+        nd_build = nd_next;
+        if (warp == 0 && a.n_stages > 2) {
+            fire(2);  // raw buffer 0: stage 0 is built
+            if (a.n_stages > 3) coords(3);
+        }
+        for (int s = 0; s < a.n_stages; s++) {
+            const bool next = s + 1 < a.n_stages;
+            const bool next2 = s + 2 < a.n_stages;
+            if (next2) small_load(s + 2);
+            bool ok = true;
+            if (next) {
+                ok = tma::mbar_wait_bounded(s_bar + 8u * ((s + 1) & 1), static_cast<uint32_t>((s + 1) >> 1) & 1u);
+                if (ok) build_stage(nd_build, (s + 1) & 1);  // into pattern buffer (s + 1) & 1
+            }
+            accumulate(s, s % 3);
+            // stage s + 2's offsets: buffer (s + 2) % 3, last read by stage s - 1's adds; its
+            // descriptors: buffer s & 1, last read by stage s's builds (previous interval)
+            if (next2) small_store(s + 2, (s + 2) % 3, s & 1);
+            if (__syncthreads_or(!ok)) {
+                drain(s + 1, next2 ? s + 2 : -1);
+                return;
+            }
+            nd_build = n_desc_next;
+            if (warp == 0 && s + 3 < a.n_stages) {
+                fire(s + 3);  // raw buffer (s + 1) & 1: stage s + 1 is built
+                if (s + 4 < a.n_stages) coords(s + 4);
+            }
+        }
     }
     fold();
 
@@ -411,7 +477,8 @@ struct FEntry {
     FactFn fn;
 };
 
-#define FDD_F(G, NW, DPW, WARPS) {{G, NW, DPW, WARPS}, k_dedisp_fact<G, NW, DPW, WARPS>}
+#define FDD_F(G, NW, DPW, WARPS) {{G, NW, DPW, WARPS, 1}, k_dedisp_fact<G, NW, DPW, WARPS, 1>}
+#define FDD_F2(G, NW, DPW, WARPS) {{G, NW, DPW, WARPS, 2}, k_dedisp_fact<G, NW, DPW, WARPS, 2>}
 const FEntry kFEntries[] = {
     FDD_F(8, 4, 4, 16),  // G 8, BD 64, T 256, 512 threads
     FDD_F(8, 4, 2, 16),  // G 8, BD 32, T 256
@@ -421,12 +488,13 @@ const FEntry kFEntries[] = {
     FDD_F(4, 8, 2, 16),  // G 4, BD 32, T 512
     FDD_F(4, 2, 8, 8),   // G 4, BD 64, T 128, 256 threads (two blocks per SM)
     FDD_F(4, 4, 4, 8),   // G 4, BD 32, T 256, 256 threads
-    FDD_F(8, 2, 8, 8),   // G 8, BD 64, T 128, 256 threads
-    FDD_F(4, 4, 8, 8),   // G 4, BD 64, T 256, 256 threads
-    FDD_F(4, 4, 2, 32),  // G 4, BD 64, T 256, 1024 threads (32 warps for latency hiding)
+    FDD_F2(4, 4, 4, 16),  // two pattern-row buffers: G 4, BD 64, T 256, 512 threads
+    FDD_F2(4, 4, 4, 8),   // two pattern-row buffers: G 4, BD 32, T 256, 256 threads
+    FDD_F2(8, 4, 4, 16),  // two pattern-row buffers: G 8, BD 64, T 256, 512 threads
     FDD_F(4, 3, 4, 16),  // G 4, BD 64, T 192: pattern rows of ~53 units fill 2 warp steps (83 % of lanes)
 };
 #undef FDD_F
+#undef FDD_F2
 
 }  // namespace
 

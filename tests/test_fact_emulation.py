@@ -60,21 +60,30 @@ def emulate(x, n_valid, sb_map, tb, v, CC, n_dm, n_out):
     G, BD, T = v["group"], v["dm_per_block"], v["tile"]
     NW = T // 64
     Lw, pat_bytes, smem_bytes = tb["Lw"], tb["pat_bytes"], tb["smem_bytes"]
+    PB = tb["pat_bufs"]
     rb, raw_lo = tb["rb"], tb["raw_off"]
     n_chan = x.shape[1]
     gps = CC // G
     zero_lo, zero_hi = tb["zero_off"], tb["zero_off"] + 4 * Lw + 16
     assert zero_hi <= raw_lo and raw_lo % 128 == 0 and rb % 128 == 0 and rb >= 4 * Lw
+    assert PB in (1, 2)
     raw_hi = raw_lo + 2 * CC * rb
-    pat_lo, pat_hi = tb["pat_off"], tb["pat_off"] + pat_bytes
+    pat_lo, pat_hi = tb["pat_off"], tb["pat_off"] + PB * pat_bytes
     assert pat_lo == raw_hi
     goff_lo = pat_hi
-    desc_lo = goff_lo + 2 * gps * BD * 4
+    desc_lo = goff_lo + (PB + 1) * gps * BD * 4
     max_desc = int(tb["pd_idx"][..., 1].max())
-    assert desc_lo + max_desc * tb["desc_ints"] * 4 == tb["bar_off"] and tb["bar_off"] % 8 == 0
+    assert desc_lo + PB * max_desc * tb["desc_ints"] * 4 == tb["bar_off"] and tb["bar_off"] % 8 == 0
     assert tb["bar_off"] + 16 + 128 == smem_bytes       # mbarriers + base alignment slack
     assert desc_lo % 16 == 0 and max_desc * (tb["desc_ints"] // 4) <= v["threads"]
     words_valid = (n_valid + 3) // 4                     # the tensor's row length in words
+
+    def pat_buf(s):
+        """Pattern-row bytes stage s may write and read."""
+        if PB == 1:
+            return pat_lo, pat_hi
+        lo = pat_lo + (s % 2) * pat_bytes
+        return lo, lo + pat_bytes
 
     def slot_of(addr):
         """Bounds of the region a build read at addr may touch."""
@@ -85,6 +94,7 @@ def emulate(x, n_valid, sb_map, tb, v, CC, n_dm, n_out):
     n_sb = sb_map.shape[0]
     S = np.zeros((n_sb, n_dm, n_out), np.int64)
     lanes = np.arange(32)
+    n_stages = tb["n_stages"]
     for sb in range(n_sb):
         for blk in range(tb["n_blk"]):
             for tile in range((n_out + T - 1) // T):
@@ -92,12 +102,10 @@ def emulate(x, n_valid, sb_map, tb, v, CC, n_dm, n_out):
                 sm = Smem(smem_bytes)
                 sm.m[zero_lo:zero_hi] = 0
                 acc = np.zeros((BD, T), np.int64)
-                goff_buf = {}
-                for s in range(tb["n_stages"]):
+
+                def stage_raw(s):
                     c0 = s * CC
-                    ncc = min(CC, n_chan - c0)
-                    ngs = (ncc + G - 1) // G
-                    for cc in range(ncc):          # raw staging (the TMA box of stage s)
+                    for cc in range(min(CC, n_chan - c0)):   # raw staging (the TMA box of stage s)
                         c = c0 + cc
                         start = t0 + tb["base"][blk, c]
                         assert start % 16 == 0                     # TMA x coordinate on a 16-byte boundary
@@ -107,9 +115,12 @@ def emulate(x, n_valid, sb_map, tb, v, CC, n_dm, n_out):
                         byts = np.where((idx >= n_valid) & (idx < 4 * words_valid), 0xE7, byts)  # pitch padding
                         slot = raw_lo + ((s % 2) * CC + cc) * rb
                         sm.m[slot:slot + 4 * Lw] = byts.astype(np.uint8)
-                    goff_buf[s % 2] = tb["goff"][blk, s * gps:s * gps + ngs]
+
+                def build(s):
+                    stage_raw(s)
+                    lo_p, hi_p = pat_buf(s)
+                    sm.m[lo_p:hi_p] = 0xAB        # stale pattern bytes from an earlier stage
                     first, n_desc = tb["pd_idx"][blk, s]
-                    sm.m[pat_lo:pat_hi] = 0xAB       # stale pattern bytes from an earlier stage
                     for d in tb["pdesc"][first:first + n_desc]:   # pattern-row builds
                         dst0, dst1, nw4 = int(d[0]), int(d[1]), int(d[2])
                         src = d[3:3 + G].astype(np.int64)
@@ -129,21 +140,37 @@ def emulate(x, n_valid, sb_map, tb, v, CC, n_dm, n_out):
                         C = prmt(od, ev, 0x7610)
                         A_next = np.append(A[1:], np.uint32(0))
                         D = prmt(B, A_next, 0x5432)
-                        sm.wr32(dst0 + 8 * j, A, pat_lo, pat_hi)
-                        sm.wr32(dst0 + 8 * j + 4, B, pat_lo, pat_hi)
-                        sm.wr32(dst1 + 8 * j, C, pat_lo, pat_hi)
-                        sm.wr32(dst1 + 8 * j + 4, D, pat_lo, pat_hi)
-                    go = goff_buf[s % 2]
-                    for gl in range(ngs):             # accumulation
+                        sm.wr32(dst0 + 8 * j, A, lo_p, hi_p)
+                        sm.wr32(dst0 + 8 * j + 4, B, lo_p, hi_p)
+                        sm.wr32(dst1 + 8 * j, C, lo_p, hi_p)
+                        sm.wr32(dst1 + 8 * j + 4, D, lo_p, hi_p)
+
+                def accumulate(s):
+                    ngs = (min(CC, n_chan - s * CC) + G - 1) // G
+                    go = tb["goff"][blk, s * gps:s * gps + ngs]
+                    lo_p, hi_p = pat_buf(s)
+                    for gl in range(ngs):
                         for jj in range(BD):
                             o = int(go[gl, jj])
                             addr = o + 4 * lanes[None, :] + 128 * np.arange(NW)[:, None]
-                            wv = sm.rd32(addr, pat_lo, pat_hi)
+                            wv = sm.rd32(addr, lo_p, hi_p)
                             lo16 = (wv & 0xFFFF).astype(np.int64)
                             hi16 = (wv >> 16).astype(np.int64)
                             tt = 2 * (lanes[None, :] + 32 * np.arange(NW)[:, None])
                             acc[jj, tt.ravel()] += lo16.ravel()
                             acc[jj, tt.ravel() + 1] += hi16.ravel()
+
+                if PB == 1:
+                    for s in range(n_stages):
+                        build(s)
+                        accumulate(s)
+                else:
+                    # the kernel's order: stage s + 1 is built before stage s's adds read their rows
+                    build(0)
+                    for s in range(n_stages):
+                        if s + 1 < n_stages:
+                            build(s + 1)
+                        accumulate(s)
                 for jj in range(BD):
                     i = blk * BD + jj
                     if i < n_dm:

@@ -301,7 +301,14 @@ def test_every_kernel_variant(fdd, variant_oracle, v, cc):
         pytest.skip("stage size shorter than a channel segment")
     plan = fdd.Plan(x.shape[0], x.shape[1], sb.shape[0], f, T_SAMP, ranges, 4.0, sb)
     r = 0 if v["bytes_per_sample"] == 1 else 1
-    plan.set_config(r, v["index"], cc)
+    try:
+        plan.set_config(r, v["index"], cc)
+    except fdd.FddError as e:
+        # a given stage size may exceed a variant's shared memory on this steep-DM case (two
+        # pattern-row buffers); the largest stage that fits (cc = 0) must always configure
+        if cc == 0 or e.code != fdd.FDD_ERR_UNSUPPORTED:
+            raise
+        pytest.skip("stage size does not fit this variant's shared memory here")
     cfg = plan.get_config(r)
     assert cfg["variant"] == v["index"] and (cc == 0 or cfg["chan_per_stage"] == cc)
     res = plan.search(to_dev(x), n_in, n_out, want_series=True, cap=1 << 18)
