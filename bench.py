@@ -368,7 +368,7 @@ class Arm:
             if args.variant is not None:
                 for r in range(len(w["ranges"])):
                     try:
-                        p0.set_config(r, range_variant(args.variant, r), args.cc)
+                        p0.set_config(r, range_variant(args.variant, r), range_variant(args.cc, r))
                     except fdd.FddError:
                         pass  # variant for the other sample width
             cfgs = [p0.get_config(r) for r in range(len(w["ranges"]))]
@@ -383,7 +383,7 @@ class Arm:
             if args.variant is not None:  # per-range kernel of the SB-factored batch mode
                 for r in range(len(w["ranges"])):
                     try:
-                        plan.set_config(r, range_variant(args.variant, r), args.cc)
+                        plan.set_config(r, range_variant(args.variant, r), range_variant(args.cc, r))
                     except fdd.FddError:
                         pass  # variant for the other sample width
             plan.batch_prepare(n_out, args.batch_variant if args.batch_variant is not None else -1)
@@ -614,7 +614,7 @@ def run_fdd(args):
         ratios = [c["work_ratio"] for c in cfgs]
     method_adds_step = float(sum(b_ * q for b_, q in zip(brute_r, ratios)))
     kinds = {v["index"]: v["kind"] for v in fdd.variants()}
-    kind_names = {0: "k_dedisp", 1: "k_dedisp_fact", 2: "k_sbf"}
+    kind_names = {0: "k_dedisp", 1: "k_dedisp_fact", 2: "k_sbf", 3: "k_sbf"}
     if mode in ("batched", "graph"):
         kname = "k_sbf" if batched_sbf else "k_batch"
     else:
@@ -992,7 +992,9 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=3, help="timed steps of the plain per-SB path")
     ap.add_argument("--variant", default=None,
                     help="force this dedispersion kernel variant (one index, or one per DM range, comma-separated)")
-    ap.add_argument("--cc", type=int, default=0, help="with --variant: channels per stage (0 = largest fitting)")
+    ap.add_argument("--cc", default="0",
+                    help="with --variant: channels per stage (0 = largest fitting), one for every range or "
+                         "a comma-separated one per range")
     ap.add_argument("--batch-variant", type=int, default=None,
                     help="batched/graph modes: this batch variant instead of the tuner's choice (1000 SB-factored "
                          "launches, 1001 one persistent SB-factored launch, 0.. brute-force persistent)")

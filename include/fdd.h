@@ -247,7 +247,10 @@ int fdd_num_variants(int32_t* n);
  * dedispersed over channel segments on which every SB keeps one TAB, and
  * each SB adds the segment partials of the TABs it takes -- exact; the
  * search workspace then holds a scratch of at most 4 GiB for the partials,
- * counted by fdd_workspace_size). */
+ * counted by fdd_workspace_size); 3 SB-factored whose segment partials come
+ * from the pattern-factored kernel (native-rate ranges whose channel segments
+ * are runs of whole channel groups of size *group; FDD_ERR_UNSUPPORTED
+ * from fdd_plan_set_config otherwise). */
 int fdd_variant_kind(int32_t variant, int32_t* kind);
 int fdd_variant_info(int32_t variant, int32_t* bytes_per_sample, int32_t* dm_per_block, int32_t* tile,
                      int32_t* threads, int32_t* group);

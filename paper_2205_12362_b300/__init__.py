@@ -192,7 +192,7 @@ def version():
 def variants():
     """[{index, kind, bytes_per_sample, dm_per_block, tile, threads, group}] of the compiled
     dedispersion kernels (kind 0 brute force, 1 pattern-factored with channel groups of size
-    `group`, 2 SB-factored)."""
+    `group`, 2 SB-factored, 3 SB-factored with pattern-factored partial sums, groups of `group`)."""
     L = _lib_raw()
     n = _I32()
     _check(L.fdd_num_variants(ctypes.byref(n)), "fdd_num_variants")

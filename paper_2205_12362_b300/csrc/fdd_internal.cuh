@@ -104,6 +104,12 @@ struct FactArgs {
     int32_t pat_off;            //   pattern rows (PB buffers of pat_bytes), then stage offsets and
     int32_t desc_bytes;         //   descriptors (PB buffers of desc_bytes),
     int32_t bar_off;            //   two mbarriers
+    // part mode (the partial sums of the SB-factored dedispersion, one TAB per block z): the
+    // 16-bit sums of each channel segment go to P[tab][seg][i - i0][Np] instead of a series
+    uint16_t* P;
+    int64_t tab_stride, seg_stride;  // elements
+    int32_t Np, i0, n_slab;          // row length; first trial and trials of the slab
+    const int2* sseg;                // [n_stages]: {bit gl set = group gl closes its segment, segment of group 0}
 };
 
 int num_fact_variants();
@@ -113,6 +119,9 @@ bool fact_cc_ok(const FactVariant& v, int Lw, int CC, int max_desc);
 // of the fact_boxes(a.Lw) pieces of a row).
 cudaError_t encode_fact_map(FactArgs& a, int64_t n_rows);
 cudaError_t launch_dedisp_fact(int variant, const FactArgs& a, size_t smem, cudaStream_t s);
+// Part mode of pattern-factored variant `variant`: a.P, a.i0 (a multiple of the variant's DM
+// block), a.n_slab and a.sseg set; grid = tiles x DM blocks of the slab x n_tab.
+cudaError_t launch_sbf_part_fact(int variant, const FactArgs& a, size_t smem, int n_tab, cudaStream_t s);
 
 // cuTensorMapEncodeTiled, reached through the runtime's driver entry-point
 // query (the library links only the runtime); nullptr if unavailable.
@@ -162,8 +171,12 @@ struct SbfCombArgs {
     int32_t uc;                 // segments per shared-memory chunk (sbf_comb_uc)
 };
 
+// SB-factored variants: part kernels of the brute-force tile, then part kernels of the pattern-
+// factored tile (sbf_fact_variant(idx) >= 0: that pattern-factored variant in part mode; its
+// DedispVariant gives E = 1, the DM block and the tile, MAXIT = 0).
 int num_sbf_variants();
 const DedispVariant& sbf_variant(int idx);
+int sbf_fact_variant(int idx);
 // Shared memory of a part block: CC channel rows (4/E copies) + offsets.
 size_t sbf_smem_bytes(const DedispVariant& v, int Lw, int CC);
 bool sbf_cc_ok(const DedispVariant& v, int Lw, int CC, size_t smem_budget);

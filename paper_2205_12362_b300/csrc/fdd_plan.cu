@@ -299,7 +299,7 @@ int configure_range(fdd_plan* p, RangeState& r, int variant, int CC) {
         const int rc = configure_sbf(p, r, variant - nbf, CC);
         if (rc == FDD_OK) {
             free_brute_tables(r);
-            free_fact_tables(r);
+            if (r.s_fact < 0) free_fact_tables(r);  // a pattern-factored part keeps its tables
         }
         return rc;
     }
@@ -760,7 +760,7 @@ int fdd_num_variants(int32_t* n) {
 int fdd_variant_kind(int32_t variant, int32_t* kind) {
     const int nb = fdd::num_dedisp_variants(), nf = fdd::num_fact_variants(), ns = fdd::num_sbf_variants();
     if (!kind || variant < 0 || variant >= nb + nf + ns) return fail(FDD_ERR_INVALID_ARG, "bad variant");
-    *kind = variant < nb ? 0 : (variant < nb + nf ? 1 : 2);
+    *kind = variant < nb ? 0 : (variant < nb + nf ? 1 : (fdd::sbf_fact_variant(variant - nb - nf) >= 0 ? 3 : 2));
     return FDD_OK;
 }
 
@@ -770,11 +770,12 @@ int fdd_variant_info(int32_t variant, int32_t* bytes_per_sample, int32_t* dm_per
     if (variant < 0 || variant >= nb + nf + fdd::num_sbf_variants()) return fail(FDD_ERR_INVALID_ARG, "bad variant");
     if (variant >= nb + nf) {
         const fdd::DedispVariant& v = fdd::sbf_variant(variant - nb - nf);
+        const int fvi = fdd::sbf_fact_variant(variant - nb - nf);
         if (bytes_per_sample) *bytes_per_sample = v.E;
         if (dm_per_block) *dm_per_block = v.bd();
         if (tile) *tile = v.tile();
         if (threads) *threads = v.threads();
-        if (group) *group = 0;
+        if (group) *group = fvi >= 0 ? fdd::fact_variant(fvi).G : 0;
         return FDD_OK;
     }
     if (variant >= nb) {

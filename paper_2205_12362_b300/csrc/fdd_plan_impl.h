@@ -45,6 +45,10 @@ struct RangeState {
     int32_t* d_sbase = nullptr;
     int32_t* d_soff = nullptr;
     int4* d_sstages = nullptr;
+    // SB-factored with pattern-factored partial sums (s_fact >= 0: that pattern-factored variant in
+    // part mode; its tables in d_fbase ... d_pdidx and the f_* layout, per stage d_fsseg)
+    int s_fact = -1;
+    int2* d_fsseg = nullptr;
     // two-step subband mode (approximate; sub_G > 0 selects it for fdd_search)
     int32_t sub_G = 0, sub_K = 0, sub_n = 0, sub_nq = 0;   // channels per subband, fine trials per coarse DM
     int32_t sub_d1max = 0, sub_d2max = 0, sub_dmax_exact = 0;

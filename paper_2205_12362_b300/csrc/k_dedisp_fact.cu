@@ -170,7 +170,10 @@ __device__ __forceinline__ void build_rows(uint32_t d0, uint32_t d1, uint32_t s0
 // goes straight on to its adds (the build rounds differ between warps) and
 // a stage costs one barrier.  Stage offsets then rotate over three buffers
 // (stage s + 2's are stored while stage s's are read) and descriptors over two.
-template <int G, int NW, int DPW, int WARPS, int PB>
+// PART: the block's z index is a TAB, every channel row comes from that TAB, and each channel
+// segment's 16-bit sums are stored to P when its last group is added (the SB-factored part step;
+// segments are whole groups), instead of accumulating all channels into a series.
+template <int G, int NW, int DPW, int WARPS, int PB, bool PART>
 __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
     k_dedisp_fact(const __grid_constant__ FactArgs a) {
     constexpr int BD = WARPS * DPW;
@@ -192,11 +195,13 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
     const uint32_t s_desc32 = static_cast<uint32_t>(__cvta_generic_to_shared(s_desc));
     const uint32_t s_bar = s0 + static_cast<uint32_t>(a.bar_off);  // two 8-byte mbarriers (raw buffers 0, 1)
 
-    const int blk = blockIdx.y, sb = blockIdx.z;
+    // DM block of the range (in part mode the grid covers the slab starting at trial a.i0)
+    const int blk = PART ? a.i0 / BD + static_cast<int>(blockIdx.y) : static_cast<int>(blockIdx.y);
+    const int sb = blockIdx.z;  // SB, or the TAB in part mode
     const int t0 = blockIdx.x * T;
     const int i0 = blk * BD;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int16_t* sbm = a.sb_map + (int64_t)sb * a.n_chan;
+    const int16_t* sbm = PART ? nullptr : a.sb_map + (int64_t)sb * a.n_chan;
     const int32_t* base_blk = a.base + (int64_t)blk * a.n_chan;
     const int32_t* goff_blk = a.goff + (int64_t)blk * a.n_groups * BD;
     const int32_t* pd_blk = a.pd_idx + (int64_t)blk * a.n_stages * 2;
@@ -226,7 +231,7 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
             if (cc < ncc) {
                 const int c = c0 + cc;
                 cx[q] = (t0 + base_blk[c]) >> 2;
-                cy[q] = sbm[c] * a.n_chan + c;
+                cy[q] = (PART ? sb : sbm[c]) * a.n_chan + c;
             }
         }
     };
@@ -303,19 +308,49 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
 
     const uint32_t s_lane = s0 + 4u * lane;
     int since_fold = 0;  // channels held in the 16-bit lanes
+    // part mode: the 16-bit sums of segment seg to P (two samples per word), lanes restarted
+    auto store_segment = [&](int seg) {
+#pragma unroll
+        for (int j = 0; j < DPW; j++) {
+            const int i = i0 + warp * DPW + j;
+            const bool valid = i < a.n_dm && i - a.i0 < a.n_slab;  // warp-uniform
+            uint32_t* row = reinterpret_cast<uint32_t*>(a.P + sb * a.tab_stride + seg * a.seg_stride +
+                                                        static_cast<int64_t>(i - a.i0) * a.Np + t0) + lane;
+#pragma unroll
+            for (int k = 0; k < NW; k++) {
+                if (valid) row[32 * k] = acc[j][k];
+                acc[j][k] = 0u;
+            }
+        }
+    };
     // adds of stage s: every trial, one 16-bit pattern partial per group, offsets from buffer gbuf
     auto accumulate = [&](int s, int gbuf) {
         const int ncc = min(CC, a.n_chan - s * CC);
         const int ngs = (ncc + G - 1) / G;
-        if (since_fold + ncc > 256) {
-            fold();
-            since_fold = 0;
+        if constexpr (!PART) {
+            if (since_fold + ncc > 256) {
+                fold();
+                since_fold = 0;
+            }
+            since_fold += ncc;
         }
-        since_fold += ncc;
+        int2 ss = make_int2(0, 0);  // part mode: segment-closing groups of the stage, first segment
+        if constexpr (PART) ss = __ldg(&a.sseg[s]);
+        int seg = ss.y;
         const int32_t* go = s_goff + gbuf * gps * BD + warp * DPW;
         int gl = 0;
 #pragma unroll 1
-        for (; gl + 1 < ngs; gl += 2) {
+        while (gl < ngs) {
+            // two groups at a time unless the first closes a segment (part mode)
+            if (gl + 1 >= ngs || (PART && ((ss.x >> gl) & 1))) {
+                int32_t o0[DPW];
+                load_offsets<DPW>(go + gl * BD, o0);
+#pragma unroll
+                for (int j = 0; j < DPW; j++)
+#pragma unroll
+                    for (int k = 0; k < NW; k++) acc[j][k] += lds32(s_lane + static_cast<uint32_t>(o0[j]) + 128u * k);
+                gl += 1;
+            } else {
             int32_t o0[DPW], o1[DPW];
             load_offsets<DPW>(go + gl * BD, o0);
             load_offsets<DPW>(go + (gl + 1) * BD, o1);
@@ -331,14 +366,11 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
             for (int j = 0; j < DPW; j++)
 #pragma unroll
                 for (int k = 0; k < NW; k++) acc[j][k] = acc[j][k] + x[0][j][k] + x[1][j][k];
-        }
-        if (gl < ngs) {
-            int32_t o0[DPW];
-            load_offsets<DPW>(go + gl * BD, o0);
-#pragma unroll
-            for (int j = 0; j < DPW; j++)
-#pragma unroll
-                for (int k = 0; k < NW; k++) acc[j][k] += lds32(s_lane + static_cast<uint32_t>(o0[j]) + 128u * k);
+                gl += 2;
+            }
+            if constexpr (PART) {
+                if ((ss.x >> (gl - 1)) & 1) store_segment(seg++);
+            }
         }
     };
     // a raw-row copy did not land: flag it, let thread 0 wait (bounded) for the copies of stages
@@ -431,6 +463,7 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
             }
         }
     }
+    if constexpr (PART) return;  // every segment is stored
     fold();
 
     // Epilogue: two samples per word; write the series and fold the moments.
@@ -475,25 +508,29 @@ using FactFn = void (*)(const FactArgs);
 struct FEntry {
     FactVariant v;
     FactFn fn;
+    FactFn part;  // part mode (the SB-factored partial sums), or nullptr
 };
 
-#define FDD_F(G, NW, DPW, WARPS) {{G, NW, DPW, WARPS, 1}, k_dedisp_fact<G, NW, DPW, WARPS, 1>}
-#define FDD_F2(G, NW, DPW, WARPS) {{G, NW, DPW, WARPS, 2}, k_dedisp_fact<G, NW, DPW, WARPS, 2>}
+#define FDD_F(G, NW, DPW, WARPS) {{G, NW, DPW, WARPS, 1}, k_dedisp_fact<G, NW, DPW, WARPS, 1, false>, nullptr}
+#define FDD_FP(G, NW, DPW, WARPS) \
+    {{G, NW, DPW, WARPS, 1}, k_dedisp_fact<G, NW, DPW, WARPS, 1, false>, k_dedisp_fact<G, NW, DPW, WARPS, 1, true>}
+#define FDD_F2(G, NW, DPW, WARPS) {{G, NW, DPW, WARPS, 2}, k_dedisp_fact<G, NW, DPW, WARPS, 2, false>, nullptr}
 const FEntry kFEntries[] = {
-    FDD_F(8, 4, 4, 16),  // G 8, BD 64, T 256, 512 threads
+    FDD_FP(8, 4, 4, 16),  // G 8, BD 64, T 256, 512 threads
     FDD_F(8, 4, 2, 16),  // G 8, BD 32, T 256
-    FDD_F(4, 4, 4, 16),  // G 4, BD 64, T 256
+    FDD_FP(4, 4, 4, 16),  // G 4, BD 64, T 256
     FDD_F(8, 2, 4, 16),  // G 8, BD 64, T 128
     FDD_F(8, 8, 2, 16),  // G 8, BD 32, T 512
     FDD_F(4, 8, 2, 16),  // G 4, BD 32, T 512
     FDD_F(4, 2, 8, 8),   // G 4, BD 64, T 128, 256 threads (two blocks per SM)
-    FDD_F(4, 4, 4, 8),   // G 4, BD 32, T 256, 256 threads
+    FDD_FP(4, 4, 4, 8),   // G 4, BD 32, T 256, 256 threads
     FDD_F2(4, 4, 4, 16),  // two pattern-row buffers: G 4, BD 64, T 256, 512 threads
     FDD_F2(4, 4, 4, 8),   // two pattern-row buffers: G 4, BD 32, T 256, 256 threads
     FDD_F2(8, 4, 4, 16),  // two pattern-row buffers: G 8, BD 64, T 256, 512 threads
     FDD_F(4, 3, 4, 16),  // G 4, BD 64, T 192: pattern rows of ~53 units fill 2 warp steps (83 % of lanes)
 };
 #undef FDD_F
+#undef FDD_FP
 #undef FDD_F2
 
 }  // namespace
@@ -540,6 +577,18 @@ cudaError_t launch_dedisp_fact(int variant, const FactArgs& a, size_t smem, cuda
     const int T = e.v.tile(), BD = e.v.bd();
     dim3 grid((a.n_out + T - 1) / T, (a.n_dm + BD - 1) / BD, a.n_sb);
     e.fn<<<grid, e.v.threads(), smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sbf_part_fact(int variant, const FactArgs& a, size_t smem, int n_tab, cudaStream_t s) {
+    if (variant < 0 || variant >= num_fact_variants() || !kFEntries[variant].part) return cudaErrorInvalidValue;
+    const FEntry& e = kFEntries[variant];
+    const int T = e.v.tile(), BD = e.v.bd();
+    if (a.i0 % BD != 0 || a.n_slab <= 0 || !a.P || !a.sseg) return cudaErrorInvalidValue;
+    cudaError_t err = cudaFuncSetAttribute(e.part, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (err != cudaSuccess) return err;
+    dim3 grid((a.n_out + T - 1) / T, (a.n_slab + BD - 1) / BD, n_tab);
+    e.part<<<grid, e.v.threads(), smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -182,7 +182,7 @@ def emulate(x, n_valid, sb_map, tb, v, CC, n_dm, n_out):
 def fact_variants():
     try:
         import paper_2205_12362_b300 as fdd
-        return [v for v in fdd.variants() if v["group"] > 0]
+        return [v for v in fdd.variants() if v["kind"] == 1]
     except Exception:
         return []
 

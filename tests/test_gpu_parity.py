@@ -261,6 +261,18 @@ def segment_lengths(sb, cap):
     return out
 
 
+def segments_whole_groups(sb, G):
+    """True if every SB-factored segment (cut at 16 channels) is a run of
+    whole channel groups of size G (the pattern-factored part's condition)."""
+    n_chan, c0 = sb.shape[1], 0
+    for n in segment_lengths(sb, 16):
+        end = c0 + n
+        if c0 % G or (end % G and end != n_chan):
+            return False
+        c0 = end
+    return True
+
+
 def variant_case():
     rng = np.random.default_rng(42)
     n_tab, n_chan, n_sb, n_out = 2, 70, 3, 1500
@@ -299,6 +311,8 @@ def test_every_kernel_variant(fdd, variant_oracle, v, cc):
     x, f, ranges, sb, n_in, n_out = variant_case()
     if v["kind"] == 2 and cc and cc < max(segment_lengths(sb, 16)):
         pytest.skip("stage size shorter than a channel segment")
+    if v["kind"] == 3 and not segments_whole_groups(sb, v["group"]):
+        pytest.skip("segments of this SB table are not whole channel groups (test_sb_factored_pattern_part)")
     plan = fdd.Plan(x.shape[0], x.shape[1], sb.shape[0], f, T_SAMP, ranges, 4.0, sb)
     r = 0 if v["bytes_per_sample"] == 1 else 1
     try:
@@ -529,6 +543,66 @@ def test_sb_factored_piecewise_slabs(fdd):
         gpu, n = res.candidates()
         compare_candidates(gpu, ora, 6.0)
     assert ran == {1, 2}
+
+
+def test_sb_factored_pattern_part(fdd):
+    """SB-factored dedispersion whose segment partials come from the
+    pattern-factored kernel in part mode (kind 3): piecewise TAB table with
+    16- and 8-channel segments, the scratch capped to one DM block per slab
+    (several slabs, a ragged last one), a ragged last tile; every series
+    bit-exact against the oracle and candidates equal, for every such variant
+    and stage size; the batched search in SB-factored mode equal to the single
+    search with the same configuration."""
+    import torch
+    n_tab, n_chan, n_sb, n_out = 6, 176, 20, 1900
+    f = synth.channel_freqs(n_chan)
+    ranges = [dict(dm0=0.0, ddm=0.5, n_dm=150, downsamp=1, widths=[1, 2, 8]),
+              dict(dm0=75.0, ddm=4.0, n_dm=30, downsamp=4, widths=[1, 4])]
+    sb = synth.sb_map_piecewise(11, n_sb, n_chan, n_tab).astype(np.int16)
+    sb[5, 32:40] = (sb[5, 32:40] + 1) % n_tab        # two 8-channel segments
+    assert min(segment_lengths(sb, 16)) == 8
+    n_in = max(int(oracle.delays(f, T_SAMP, r["dm0"], r["ddm"], r["n_dm"], r["downsamp"]).max())
+               * r["downsamp"] + n_out for r in ranges) + 5
+    pulses = [dict(tab=k % n_tab, start=t0 + oracle.delays(f, T_SAMP, dm, 1.0, 1)[0], width=w, amp=40.0)
+              for k, (t0, dm, w) in enumerate([(300, 20.0, 2), (900, 60.0, 4), (1500, 150.0, 8)])]
+    x = synth.filterbank(31, n_tab, n_chan, n_in, pulses=pulses)
+    ora, os_ = oracle_candidate_superset(x, sb, f, T_SAMP, ranges, 6.0, n_out, n_in, return_series=True)
+    dx = to_dev(x)
+    vs = [v for v in fdd.variants() if v["kind"] == 3]
+    assert vs and {v["group"] for v in vs} == {4, 8}
+    for v in vs:
+        for cc in (0, 8, 16):
+            plan = fdd.Plan(n_tab, n_chan, n_sb, f, T_SAMP, ranges, 6.0, sb)
+            plan.set_scratch_limit(1)                 # one DM block per slab
+            try:
+                plan.set_config(0, v["index"], cc)
+            except fdd.FddError as e:
+                # the pattern rows of this steep DM step exceed shared memory at a given stage
+                # size; the largest stage that fits (cc = 0) always configures
+                assert cc != 0 and e.code == fdd.FDD_ERR_UNSUPPORTED
+                continue
+            cfg = plan.get_config(0)
+            assert cfg["variant"] == v["index"] and (cc == 0 or cfg["chan_per_stage"] == cc)
+            assert cfg["work_ratio"] < 0.5
+            res = plan.search(dx, n_in, n_out, want_series=True, cap=1 << 18)
+            torch.cuda.synchronize()
+            assert plan.status() == 0
+            g = plan.series_views(res.series, n_out)
+            for k in range(2):
+                assert (g[k].cpu().numpy() == os_[k]).all(), (v, cc, k)
+            gpu, n = res.candidates()
+            compare_candidates(gpu, ora, 6.0)
+        plan = fdd.Plan(n_tab, n_chan, n_sb, f, T_SAMP, ranges, 6.0, sb)
+        plan.set_scratch_limit(1)
+        plan.set_config(0, v["index"], 0)
+        res = plan.search(dx, n_in, n_out, want_series=True, cap=1 << 18)
+        plan.batch_prepare(n_out, fdd.FDD_BATCH_SB_FACTORED)
+        assert plan.get_config(0)["variant"] == v["index"]
+        job = plan.make_job(dx, n_in, n_out, cap=1 << 18, want_series=True)
+        bres = plan.search_batch([job], n_out)[0]
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        assert torch.equal(bres.series, res.series)
 
 
 def test_boxcar_width_sets(fdd):
