@@ -30,10 +30,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_sbf_part(const SbfPartArgs a) {
     detail::sbf_part_tile<E, NW, DPW, WARPS, MAXIT>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
 }
 
-// Comb: block = CW warps x CSB SBs per warp, one DM trial, CT = 128 samples.
-// Each half-warp takes one SB of a pair (the warp's SBs in CSB / 2 pairs) and
-// a lane 8 consecutive samples, read as one 16-byte shared load per segment,
-// so one TAB lookup and address serve 8 adds.  The partial rows of every TAB for UC segments at a time are
+// Comb: block = CW warps x CSB SBs per warp, one DM trial, CT = 128 samples
+// (4 per lane).  The partial rows of every TAB for UC segments at a time are
 // one tile of P -- CT samples x UC segments x n_tab TABs -- which thread 0
 // requests with a single TMA tensor copy (cp.async.bulk.tensor) into shared
 // memory, double-buffered and completed on an mbarrier; each row is read from
@@ -47,12 +45,9 @@ constexpr int kTabBytes = UC * kRowBytes;    // UC rows of one TAB
 static_assert(kTabBytes == 1 << 11, "the TAB offset is formed as tab << 11");
 constexpr int kSmemAlign = 128;              // TMA destination alignment
 
-constexpr int CP = CSB / 2;                  // SB pairs per warp (one SB per half-warp)
-static_assert(CSB % 2 == 0, "SBs per warp come in pairs");
-
-__device__ __forceinline__ uint4 lds128(uint32_t addr) {
-    uint4 v;
-    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+__device__ __forceinline__ uint2 lds64(uint32_t addr) {
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
     return v;
 }
 __global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const __grid_constant__ SbfCombArgs a) {
@@ -68,15 +63,12 @@ __global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const __grid_constant__
     const uint32_t s_base = (s_raw + (kSmemAlign - 1)) & ~static_cast<uint32_t>(kSmemAlign - 1);
     const uint32_t buf_bytes = static_cast<uint32_t>(a.n_tab) * kTabBytes;
     const uint32_t s_bar = s_base + 2u * buf_bytes;  // two 8-byte mbarriers
-    // this lane's SB in pair p is slot 2 p + half (invalid slots repeat SB sb0 + nsb - 1, or SB 0 for
-    // an idle warp); the lane holds samples 8 hl .. 8 hl + 7 of the tile
-    const int half = lane >> 4, hl = lane & 15;
-    const uint8_t* tab_row[CP];
+    // the SBs of this warp (invalid slots repeat SB sb0 + nsb - 1, or SB 0 for an idle warp)
+    const uint8_t* tab_row[CSB];
 #pragma unroll
-    for (int q = 0; q < CP; q++) {
-        const int j = 2 * q + half;
+    for (int j = 0; j < CSB; j++) {
         const int sj = nsb > 0 ? sb0 + min(j, nsb - 1) : 0;
-        tab_row[q] = a.seg_tab + static_cast<int64_t>(sj) * a.seg_pitch;
+        tab_row[j] = a.seg_tab + static_cast<int64_t>(sj) * a.seg_pitch;
     }
 
     // chunk ch (UC segments of every TAB) into buffer ch & 1: one tensor copy by thread 0
@@ -92,24 +84,21 @@ __global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const __grid_constant__
     }
     __syncthreads();
 
-    // 16-bit lanes: word w holds samples 2w, 2w + 1 of the lane's 8
-    uint32_t acc[CP][4], tot[CP][8];
+    uint32_t acc[CSB][2], tot[CSB][4];
 #pragma unroll
-    for (int q = 0; q < CP; q++)
-#pragma unroll
-        for (int w = 0; w < 4; w++) {
-            acc[q][w] = 0u;
-            tot[q][2 * w] = tot[q][2 * w + 1] = 0u;
-        }
+    for (int j = 0; j < CSB; j++) {
+        acc[j][0] = acc[j][1] = 0u;
+        tot[j][0] = tot[j][1] = tot[j][2] = tot[j][3] = 0u;
+    }
     auto fold = [&]() {
 #pragma unroll
-        for (int q = 0; q < CP; q++)
-#pragma unroll
-            for (int w = 0; w < 4; w++) {
-                tot[q][2 * w] += acc[q][w] & 0xFFFFu;
-                tot[q][2 * w + 1] += acc[q][w] >> 16;
-                acc[q][w] = 0u;
-            }
+        for (int j = 0; j < CSB; j++) {
+            tot[j][0] += acc[j][0] & 0xFFFFu;
+            tot[j][1] += acc[j][0] >> 16;
+            tot[j][2] += acc[j][1] & 0xFFFFu;
+            tot[j][3] += acc[j][1] >> 16;
+            acc[j][0] = acc[j][1] = 0u;
+        }
     };
 
     if (threadIdx.x == 0) issue(0);
@@ -129,25 +118,23 @@ __global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const __grid_constant__
         }
         const int u0 = ch * UC;
         const int nu = min(UC, a.n_seg - u0);
-        const uint32_t s_buf = s_base + buf * buf_bytes + 16u * hl;
+        const uint32_t s_buf = s_base + buf * buf_bytes + 8u * lane;
 #pragma unroll
-        for (int qd = 0; qd < UC; qd += 4) {
-            uint32_t tabs4[CP];
+        for (int q = 0; q < UC; q += 4) {
+            uint32_t tabs4[CSB];
 #pragma unroll
-            for (int q = 0; q < CP; q++) tabs4[q] = __ldg(reinterpret_cast<const uint32_t*>(tab_row[q] + u0 + qd));
+            for (int j = 0; j < CSB; j++) tabs4[j] = __ldg(reinterpret_cast<const uint32_t*>(tab_row[j] + u0 + q));
 #pragma unroll
             for (int dq = 0; dq < 4; dq++) {
-                const int du = qd + dq;
+                const int du = q + dq;
                 if (du < nu) {  // block-uniform
 #pragma unroll
-                    for (int q = 0; q < CP; q++) {
+                    for (int j = 0; j < CSB; j++) {
                         // byte dq of tabs4 (the TAB; PRMT zero-fills the rest) times kTabBytes (2^11)
-                        const uint32_t tab = __byte_perm(tabs4[q], 0u, 0x4440u + dq);
-                        const uint4 v = lds128(s_buf + (tab << 11) + du * kRowBytes);
-                        acc[q][0] += v.x;
-                        acc[q][1] += v.y;
-                        acc[q][2] += v.z;
-                        acc[q][3] += v.w;
+                        const uint32_t tab = __byte_perm(tabs4[j], 0u, 0x4440u + dq);
+                        const uint2 v = lds64(s_buf + (tab << 11) + du * kRowBytes);
+                        acc[j][0] += v.x;
+                        acc[j][1] += v.y;
                     }
                     if (++since == a.flush) {
                         fold();
@@ -159,30 +146,28 @@ __global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const __grid_constant__
         __syncthreads();  // buffer free for the copy issued next iteration
     }
     fold();
-    const int t = t0 + 8 * hl;
+    const int t = t0 + 4 * lane;
 #pragma unroll
-    for (int q = 0; q < CP; q++) {
-        const int j = 2 * q + half;
+    for (int j = 0; j < CSB; j++) {
         unsigned long long s1 = 0, s2 = 0;
         if (j < nsb) {
             int32_t* row = a.series + (static_cast<int64_t>(sb0 + j) * a.n_dm + i) * a.n_out;
 #pragma unroll
-            for (int e = 0; e < 8; e++) {
+            for (int e = 0; e < 4; e++) {
                 if (t + e < a.n_emit) {
-                    const uint32_t v = tot[q][e];
+                    const uint32_t v = tot[j][e];
                     row[t + e] = static_cast<int32_t>(v);
                     s1 += v;
                     s2 += static_cast<unsigned long long>(v) * v;
                 }
             }
         }
-        // moments over the 16 lanes of the half-warp (xor offsets below 16 stay inside it)
 #pragma unroll
-        for (int o = 8; o > 0; o >>= 1) {
+        for (int o = 16; o > 0; o >>= 1) {
             s1 += __shfl_xor_sync(0xffffffffu, s1, o);
             s2 += __shfl_xor_sync(0xffffffffu, s2, o);
         }
-        if (hl == 0 && j < nsb) {
+        if (lane == 0 && j < nsb) {
             const int64_t qq = static_cast<int64_t>(sb0 + j) * a.n_dm + i;
             atomicAdd(a.stat + 2 * qq, s1);
             atomicAdd(a.stat + 2 * qq + 1, s2);
