@@ -42,6 +42,7 @@ namespace host {
 FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactVariant& v, int CC) {
     FactTables ft;
     const int G = v.G, BD = v.bd(), T = v.tile();
+    const int E = r.D == 1 ? 1 : 2;  // bytes per staged sample
     const int n_chan = p->n_chan;
     const int n_blk = (r.n_dm + BD - 1) / BD;
     const int n_groups = (n_chan + G - 1) / G;
@@ -125,10 +126,11 @@ FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactV
                     for (int k = 0; k < G; k++) {
                         if (k < gn) {
                             const int c = c0 + k;
-                            const int32_t o = pt.rmin + pt.rel[k] - ft.base[static_cast<size_t>(b) * n_chan + c];
+                            // byte of the pattern's first sample in the channel's staged row
+                            const int32_t o = E * (pt.rmin + pt.rel[k] - ft.base[static_cast<size_t>(b) * n_chan + c]);
                             // raw buffer (s & 1), channel slot cc, byte o of the row; slot bases added below
                             d[3 + k] = ((s & 1) << 30) | ((c - s * CC) << 20) | o;
-                            max_need = std::max<int64_t>(max_need, static_cast<int64_t>(o) + 4LL * nw4 + 4);
+                            max_need = std::max<int64_t>(max_need, static_cast<int64_t>(o) + 4LL * E * nw4 + 4);
                         } else {
                             d[3 + k] = -1;  // missing channel: the zero row
                         }

@@ -89,6 +89,8 @@ struct FactArgs {
     const uint8_t* in;          // raw uint8 rows (tab, c) at in + (tab * n_chan + c) * pitch_bytes
     int64_t pitch_bytes;
     int64_t n_valid;            // valid samples per row
+    int32_t E;                  // bytes per sample: 1 (raw rows) or 2 (downsampled rows)
+    int32_t fold_ch;            // channels summed in the 16-bit lanes between folds (256 / D)
     const int16_t* sb_map;      // [n_sb][n_chan]
     const int32_t* base;        // [n_blk][n_chan]
     const int32_t* goff;        // [n_blk][n_groups][BD]
@@ -118,6 +120,8 @@ bool fact_cc_ok(const FactVariant& v, int Lw, int CC, int max_desc);
 // Fills a.tmap for a.in (n_rows rows of a.pitch_bytes, a.n_valid valid bytes each; box = one
 // of the fact_boxes(a.Lw) pieces of a row).
 cudaError_t encode_fact_map(FactArgs& a, int64_t n_rows);
+// True if pattern-factored variant `variant` is built for E bytes per sample (plain or part mode).
+bool fact_has_width(int variant, int E, bool part);
 cudaError_t launch_dedisp_fact(int variant, const FactArgs& a, size_t smem, cudaStream_t s);
 // Part mode of pattern-factored variant `variant`: a.P, a.i0 (a multiple of the variant's DM
 // block), a.n_slab and a.sseg set; grid = tiles x DM blocks of the slab x n_tab.

@@ -253,7 +253,8 @@ int upload_vec(int32_t** dst, const std::vector<int32_t>& v, const char* what) {
 // stage (0 = the largest that fits).
 int configure_fact(fdd_plan* p, RangeState& r, int fv, int CC) {
     if (fv < 0 || fv >= fdd::num_fact_variants()) return fail(FDD_ERR_INVALID_ARG, "kernel variant out of range");
-    if (r.D != 1) return fail(FDD_ERR_INVALID_ARG, "the factored kernel serves native-rate ranges only");
+    if (!fdd::fact_has_width(fv, r.D == 1 ? 1 : 2, false))
+        return fail(FDD_ERR_INVALID_ARG, "this factored variant is not built for the range's sample width");
     const fdd::FactVariant& v = fdd::fact_variant(fv);
     FactTables best;
     int best_cc = 0;
@@ -330,6 +331,8 @@ cudaError_t launch_range_dedisp(const fdd_plan* p, const RangeState& r, const fd
     fa.in = a.in;
     fa.pitch_bytes = a.pitch_bytes;
     fa.n_valid = a.n_valid;
+    fa.E = r.D == 1 ? 1 : 2;
+    fa.fold_ch = 256 / r.D;  // 16-bit lanes hold at most 256 / D channels of 255 D
     fa.sb_map = a.sb_map;
     fa.base = r.d_fbase;
     fa.goff = r.d_goff;
@@ -912,7 +915,8 @@ int fdd_plan_autotune(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64
                 }
             }
         }
-        for (int fv = 0; E == 1 && fv < fdd::num_fact_variants() && rc == FDD_OK; fv++) {
+        for (int fv = 0; fv < fdd::num_fact_variants() && rc == FDD_OK; fv++) {
+            if (!fdd::fact_has_width(fv, E, false)) continue;
             for (int cc : {16, 32, 48, 64}) {
                 if (configure_fact(plan, r, fv, cc) != FDD_OK) continue;  // does not fit
                 const fdd::DedispArgs a = dedisp_args(plan, r, ri, L, d_tabs, pitch, ws, series, stat, n_in, bins);
@@ -983,7 +987,7 @@ int fdd_fact_tables_host(const fdd_plan_desc* desc, const int16_t* sb_map_host, 
     if (rc != FDD_OK) return rc;
     const int fv = variant - fdd::num_dedisp_variants();
     if (range < 0 || range >= static_cast<int32_t>(p.ranges.size()) || fv < 0 || fv >= fdd::num_fact_variants() ||
-        p.ranges[range].D != 1 || chan_per_stage < 1)
+        chan_per_stage < 1)
         return fail(FDD_ERR_INVALID_ARG, "bad range, variant or stage size");
     const fdd::FactVariant& v = fdd::fact_variant(fv);
     if (chan_per_stage % v.G) return fail(FDD_ERR_INVALID_ARG, "stage size must be a multiple of G");

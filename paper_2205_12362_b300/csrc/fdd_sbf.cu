@@ -129,12 +129,13 @@ int upload_segments(fdd_plan* p, RangeState& r, const std::vector<int2>& segs) {
 }
 
 // SB-factored variant sv whose partial sums come from pattern-factored variant fdd::sbf_fact_variant(sv)
-// in part mode (native-rate ranges; every segment a run of whole channel groups).
+// in part mode (every segment a run of whole channel groups; raw or downsampled rows by the variant's E).
 int configure_sbf_fact(fdd_plan* p, RangeState& r, int sv, int CC) {
     const int fvi = fdd::sbf_fact_variant(sv);
-    if (r.D != 1) return fail(FDD_ERR_INVALID_ARG, "kernel variant for the wrong sample width");
+    if (fdd::sbf_variant(sv).E != (r.D == 1 ? 1 : 2) || !fdd::fact_has_width(fvi, r.D == 1 ? 1 : 2, true))
+        return fail(FDD_ERR_INVALID_ARG, "kernel variant for the wrong sample width");
     const fdd::FactVariant& v = fdd::fact_variant(fvi);
-    const std::vector<int2> segs = sbf_segments(p, 1, 16);
+    const std::vector<int2> segs = sbf_segments(p, r.D, 16);
     if (segs.size() > r.segs.size()) return fail(FDD_ERR_UNSUPPORTED, "more segments than the scratch was sized for");
     for (const int2& sg : segs)
         if (sg.x % v.G != 0 || ((sg.x + sg.y) % v.G != 0 && sg.x + sg.y != p->n_chan))
@@ -318,6 +319,8 @@ cudaError_t launch_range_sbf(const fdd_plan* p, const RangeState& r, const fdd::
         fa.in = a.in;
         fa.pitch_bytes = a.pitch_bytes;
         fa.n_valid = a.n_valid;
+        fa.E = r.D == 1 ? 1 : 2;
+        fa.fold_ch = 256 / r.D;  // unused in part mode (segments fit the 16-bit lanes)
         fa.base = r.d_fbase;
         fa.goff = r.d_goff;
         fa.pdesc = r.d_pdesc;

@@ -83,7 +83,9 @@ __device__ __forceinline__ void load_offsets(const int32_t* p, int32_t (&o)[N]) 
 // stores [R0,R1],[R2,R3]; copy 1 stores [R1,R2],[R3,R4], R4 being the next
 // lane's R0 (shuffle; across a 32-unit step it comes from lane 0 of the next
 // step).
-template <int G>
+// E = bytes per input sample: 1 (raw 8-bit rows, byte lanes split into even and odd samples) or 2
+// (downsampled 16-bit rows: a unit's four samples are two words, summed in 16-bit lanes directly).
+template <int G, int E>
 struct RowState {
     uint32_t dst0, dst1, src[G], sh[G];
     int nw4;
@@ -109,22 +111,41 @@ struct RowState {
     __device__ __forceinline__ void step(int jb, int lane) {
         if (jb >= nw4) return;  // warp-uniform
         const int j = jb + lane;
-        uint32_t acc_a = 0, acc_b = 0;
-        if (j < nw4) {
+        uint32_t A, B, C;  // [R0, R1], [R2, R3], [R1, R2]
+        if constexpr (E == 1) {
+            uint32_t acc_a = 0, acc_b = 0;
+            if (j < nw4) {
 #pragma unroll
-            for (int k = 0; k < G; k += 2) {
-                const uint32_t a0 = src[k] + 4u * j, a1 = src[k + 1] + 4u * j;
-                const uint32_t x0 = __funnelshift_r(lds32(a0), lds32(a0 + 4u), sh[k]);
-                const uint32_t x1 = __funnelshift_r(lds32(a1), lds32(a1 + 4u), sh[k + 1]);
-                acc_a = acc_a + x0 + x1;
-                acc_b = acc_b + __byte_perm(x0, 0u, 0x4341) + __byte_perm(x1, 0u, 0x4341);
+                for (int k = 0; k < G; k += 2) {
+                    const uint32_t a0 = src[k] + 4u * j, a1 = src[k + 1] + 4u * j;
+                    const uint32_t x0 = __funnelshift_r(lds32(a0), lds32(a0 + 4u), sh[k]);
+                    const uint32_t x1 = __funnelshift_r(lds32(a1), lds32(a1 + 4u), sh[k + 1]);
+                    acc_a = acc_a + x0 + x1;
+                    acc_b = acc_b + __byte_perm(x0, 0u, 0x4341) + __byte_perm(x1, 0u, 0x4341);
+                }
             }
+            const uint32_t od = acc_b;                 // [R1, R3]
+            const uint32_t ev = acc_a - (acc_b << 8);  // [R0, R2]
+            A = __byte_perm(ev, od, 0x5410);
+            B = __byte_perm(ev, od, 0x7632);
+            C = __byte_perm(od, ev, 0x7610);
+        } else {
+            // 16-bit samples: unit j is bytes [8 j, 8 j + 8) of each channel's row (sums of G samples of
+            // at most 255 D each stay below 2^16)
+            uint32_t acc0 = 0, acc1 = 0;
+            if (j < nw4) {
+#pragma unroll
+                for (int k = 0; k < G; k++) {
+                    const uint32_t a0 = src[k] + 8u * j;
+                    const uint32_t w0 = lds32(a0), w1 = lds32(a0 + 4u), w2 = lds32(a0 + 8u);
+                    acc0 += __funnelshift_r(w0, w1, sh[k]);
+                    acc1 += __funnelshift_r(w1, w2, sh[k]);
+                }
+            }
+            A = acc0;
+            B = acc1;
+            C = __byte_perm(acc0, acc1, 0x5432);
         }
-        const uint32_t od = acc_b;                       // [R1, R3]
-        const uint32_t ev = acc_a - (acc_b << 8);        // [R0, R2]
-        const uint32_t A = __byte_perm(ev, od, 0x5410);  // [R0, R1]
-        const uint32_t B = __byte_perm(ev, od, 0x7632);  // [R2, R3]
-        const uint32_t C = __byte_perm(od, ev, 0x7610);  // [R1, R2]
         const uint32_t next_a = __shfl_down_sync(0xffffffffu, A, 1);
         const uint32_t first_a = __shfl_sync(0xffffffffu, A, 0);
         if (j < nw4) {
@@ -144,9 +165,9 @@ struct RowState {
 
 // Rows d0 and d1 (d1 == 0xffffffff: none) interleaved step by step, so a
 // lane has two independent build chains in flight.
-template <int G>
+template <int G, int E>
 __device__ __forceinline__ void build_rows(uint32_t d0, uint32_t d1, uint32_t s0, int lane) {
-    RowState<G> a, b;
+    RowState<G, E> a, b;
     a.load(d0, s0);
     const bool two = d1 != 0xffffffffu;
     if (two) {
@@ -173,7 +194,7 @@ __device__ __forceinline__ void build_rows(uint32_t d0, uint32_t d1, uint32_t s0
 // PART: the block's z index is a TAB, every channel row comes from that TAB, and each channel
 // segment's 16-bit sums are stored to P when its last group is added (the SB-factored part step;
 // segments are whole groups), instead of accumulating all channels into a series.
-template <int G, int NW, int DPW, int WARPS, int PB, bool PART>
+template <int G, int NW, int DPW, int WARPS, int PB, bool PART, int E>
 __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
     k_dedisp_fact(const __grid_constant__ FactArgs a) {
     constexpr int BD = WARPS * DPW;
@@ -230,7 +251,7 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
             const int cc = lane + 32 * q;
             if (cc < ncc) {
                 const int c = c0 + cc;
-                cx[q] = (t0 + base_blk[c]) >> 2;
+                cx[q] = ((t0 + base_blk[c]) * E) >> 2;  // word of the row's first staged sample
                 cy[q] = (PART ? sb : sbm[c]) * a.n_chan + c;
             }
         }
@@ -280,7 +301,8 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
     auto build_stage = [&](int n_desc, int dbuf) {
         const uint32_t sd = s_desc32 + static_cast<uint32_t>(dbuf * a.desc_bytes);
         for (int d = warp; d < n_desc; d += 2 * WARPS)
-            build_rows<G>(sd + 4u * DI * d, d + WARPS < n_desc ? sd + 4u * DI * (d + WARPS) : 0xffffffffu, s0, lane);
+            build_rows<G, E>(sd + 4u * DI * d, d + WARPS < n_desc ? sd + 4u * DI * (d + WARPS) : 0xffffffffu, s0,
+                             lane);
     };
 
     // Per output word: acc = two 16-bit partial sums (samples 2m, 2m+1); a
@@ -328,7 +350,7 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
         const int ncc = min(CC, a.n_chan - s * CC);
         const int ngs = (ncc + G - 1) / G;
         if constexpr (!PART) {
-            if (since_fold + ncc > 256) {
+            if (since_fold + ncc > a.fold_ch) {
                 fold();
                 since_fold = 0;
             }
@@ -507,14 +529,18 @@ using FactFn = void (*)(const FactArgs);
 
 struct FEntry {
     FactVariant v;
-    FactFn fn;
-    FactFn part;  // part mode (the SB-factored partial sums), or nullptr
+    FactFn fn[2];    // by bytes per sample (E = 1, 2); nullptr: not built for that width
+    FactFn part[2];  // part mode (the SB-factored partial sums), or nullptr
 };
 
-#define FDD_F(G, NW, DPW, WARPS) {{G, NW, DPW, WARPS, 1}, k_dedisp_fact<G, NW, DPW, WARPS, 1, false>, nullptr}
-#define FDD_FP(G, NW, DPW, WARPS) \
-    {{G, NW, DPW, WARPS, 1}, k_dedisp_fact<G, NW, DPW, WARPS, 1, false>, k_dedisp_fact<G, NW, DPW, WARPS, 1, true>}
-#define FDD_F2(G, NW, DPW, WARPS) {{G, NW, DPW, WARPS, 2}, k_dedisp_fact<G, NW, DPW, WARPS, 2, false>, nullptr}
+#define FDD_F(G, NW, DPW, WARPS) \
+    {{G, NW, DPW, WARPS, 1}, {k_dedisp_fact<G, NW, DPW, WARPS, 1, false, 1>, nullptr}, {nullptr, nullptr}}
+#define FDD_FP(G, NW, DPW, WARPS)                                                                              \
+    {{G, NW, DPW, WARPS, 1},                                                                                   \
+     {k_dedisp_fact<G, NW, DPW, WARPS, 1, false, 1>, k_dedisp_fact<G, NW, DPW, WARPS, 1, false, 2>},        \
+     {k_dedisp_fact<G, NW, DPW, WARPS, 1, true, 1>, k_dedisp_fact<G, NW, DPW, WARPS, 1, true, 2>}}
+#define FDD_F2(G, NW, DPW, WARPS) \
+    {{G, NW, DPW, WARPS, 2}, {k_dedisp_fact<G, NW, DPW, WARPS, 2, false, 1>, nullptr}, {nullptr, nullptr}}
 const FEntry kFEntries[] = {
     FDD_FP(8, 4, 4, 16),  // G 8, BD 64, T 256, 512 threads
     FDD_F(8, 4, 2, 16),  // G 8, BD 32, T 256
@@ -555,7 +581,7 @@ bool fact_cc_ok(const FactVariant& v, int Lw, int CC, int max_desc) {
 cudaError_t encode_fact_map(FactArgs& a, int64_t n_rows) {
     const EncodeTiledFn enc = encode_tiled_fn();
     if (!enc) return cudaErrorNotSupported;
-    const int64_t words = (a.n_valid + 3) / 4;
+    const int64_t words = (a.n_valid * a.E + 3) / 4;
     if (a.Lw < 4 || a.Lw > kFactMaxLw || a.Lw % fact_lw_align(a.Lw) != 0 ||
         (reinterpret_cast<uintptr_t>(a.in) & 15u) != 0 || a.pitch_bytes % 16 != 0 || words * 4 > a.pitch_bytes ||
         n_rows < 1)
@@ -570,25 +596,33 @@ cudaError_t encode_fact_map(FactArgs& a, int64_t n_rows) {
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+bool fact_has_width(int variant, int E, bool part) {
+    if (variant < 0 || variant >= num_fact_variants() || (E != 1 && E != 2)) return false;
+    return (part ? kFEntries[variant].part[E - 1] : kFEntries[variant].fn[E - 1]) != nullptr;
+}
+
 cudaError_t launch_dedisp_fact(int variant, const FactArgs& a, size_t smem, cudaStream_t s) {
+    if (!fact_has_width(variant, a.E, false)) return cudaErrorInvalidValue;
     const FEntry& e = kFEntries[variant];
-    cudaError_t err = cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    const FactFn fn = e.fn[a.E - 1];
+    cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (err != cudaSuccess) return err;
     const int T = e.v.tile(), BD = e.v.bd();
     dim3 grid((a.n_out + T - 1) / T, (a.n_dm + BD - 1) / BD, a.n_sb);
-    e.fn<<<grid, e.v.threads(), smem, s>>>(a);
+    fn<<<grid, e.v.threads(), smem, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sbf_part_fact(int variant, const FactArgs& a, size_t smem, int n_tab, cudaStream_t s) {
-    if (variant < 0 || variant >= num_fact_variants() || !kFEntries[variant].part) return cudaErrorInvalidValue;
+    if (!fact_has_width(variant, a.E, true)) return cudaErrorInvalidValue;
     const FEntry& e = kFEntries[variant];
+    const FactFn fn = e.part[a.E - 1];
     const int T = e.v.tile(), BD = e.v.bd();
     if (a.i0 % BD != 0 || a.n_slab <= 0 || !a.P || !a.sseg) return cudaErrorInvalidValue;
-    cudaError_t err = cudaFuncSetAttribute(e.part, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (err != cudaSuccess) return err;
     dim3 grid((a.n_out + T - 1) / T, (a.n_slab + BD - 1) / BD, n_tab);
-    e.part<<<grid, e.v.threads(), smem, s>>>(a);
+    fn<<<grid, e.v.threads(), smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -184,8 +184,10 @@ struct Entry {
 };
 
 #define FDD_S(E, NW, DPW, WARPS, MAXIT) {{E, NW, DPW, WARPS, MAXIT}, k_sbf_part<E, NW, DPW, WARPS, MAXIT>, -1}
-// pattern-factored part: tile 64 * NWF samples = 128 * (NWF / 2) of a DedispVariant with E = 1
+// pattern-factored part: tile 64 * NWF samples = 128 * (NWF / 2) of a DedispVariant with E = 1,
+// = 64 * NWF of one with E = 2
 #define FDD_SF(NWF, DPW, WARPS, FV) {{1, (NWF) / 2, DPW, WARPS, 0}, nullptr, FV}
+#define FDD_SF2(NWF, DPW, WARPS, FV) {{2, NWF, DPW, WARPS, 0}, nullptr, FV}
 const Entry kEntries[] = {
     FDD_S(1, 4, 2, 8, 4),   // BD 16, T 512
     FDD_S(1, 4, 4, 8, 4),   // BD 32, T 512
@@ -200,9 +202,13 @@ const Entry kEntries[] = {
     FDD_SF(4, 4, 16, 2),    // pattern-factored part, G 4, BD 64, T 256
     FDD_SF(4, 4, 16, 0),    // pattern-factored part, G 8, BD 64, T 256
     FDD_SF(4, 4, 8, 7),     // pattern-factored part, G 4, BD 32, T 256, 256 threads
+    FDD_SF2(4, 4, 16, 2),   // pattern-factored part of 16-bit (downsampled) rows, G 4, BD 64, T 256
+    FDD_SF2(4, 4, 16, 0),   // the same with G 8
+    FDD_SF2(4, 4, 8, 7),    // the same, G 4, BD 32, 256 threads
 };
 #undef FDD_S
 #undef FDD_SF
+#undef FDD_SF2
 
 }  // namespace
 

@@ -56,7 +56,8 @@ def funnel_r(lo, hi, sh):
     return ((w >> np.uint64(sh & 31)) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
 
 
-def emulate(x, n_valid, sb_map, tb, v, CC, n_dm, n_out):
+def emulate(x, n_valid, sb_map, tb, v, CC, n_dm, n_out, E=1):
+    """x: uint8 rows (E = 1) or the uint16 rows of a downsampled range (E = 2), n_valid samples."""
     G, BD, T = v["group"], v["dm_per_block"], v["tile"]
     NW = T // 64
     Lw, pat_bytes, smem_bytes = tb["Lw"], tb["pat_bytes"], tb["smem_bytes"]
@@ -76,7 +77,7 @@ def emulate(x, n_valid, sb_map, tb, v, CC, n_dm, n_out):
     assert desc_lo + PB * max_desc * tb["desc_ints"] * 4 == tb["bar_off"] and tb["bar_off"] % 8 == 0
     assert tb["bar_off"] + 16 + 128 == smem_bytes       # mbarriers + base alignment slack
     assert desc_lo % 16 == 0 and max_desc * (tb["desc_ints"] // 4) <= v["threads"]
-    words_valid = (n_valid + 3) // 4                     # the tensor's row length in words
+    words_valid = (n_valid * E + 3) // 4                 # the tensor's row length in words
 
     def pat_buf(s):
         """Pattern-row bytes stage s may write and read."""
@@ -107,12 +108,12 @@ def emulate(x, n_valid, sb_map, tb, v, CC, n_dm, n_out):
                     c0 = s * CC
                     for cc in range(min(CC, n_chan - c0)):   # raw staging (the TMA box of stage s)
                         c = c0 + cc
-                        start = t0 + tb["base"][blk, c]
+                        start = (t0 + tb["base"][blk, c]) * E      # byte of the row's first staged sample
                         assert start % 16 == 0                     # TMA x coordinate on a 16-byte boundary
                         idx = start + np.arange(4 * Lw)
-                        row = x[sb_map[sb, c], c]
+                        row = np.ascontiguousarray(x[sb_map[sb, c], c]).view(np.uint8)   # little-endian bytes
                         byts = np.where(idx < 4 * words_valid, row[np.minimum(idx, row.size - 1)], 0)
-                        byts = np.where((idx >= n_valid) & (idx < 4 * words_valid), 0xE7, byts)  # pitch padding
+                        byts = np.where((idx >= n_valid * E) & (idx < 4 * words_valid), 0xE7, byts)  # pitch padding
                         slot = raw_lo + ((s % 2) * CC + cc) * rb
                         sm.m[slot:slot + 4 * Lw] = byts.astype(np.uint8)
 
@@ -131,13 +132,25 @@ def emulate(x, n_valid, sb_map, tb, v, CC, n_dm, n_out):
                             lo, hi = slot_of(int(src[k]))
                             if src[k] >= zero_hi:                  # this stage's raw buffer
                                 assert (int(src[k]) - raw_lo) // (CC * rb) == s % 2
-                            al = (int(src[k]) & ~3) + 4 * j
-                            xw = funnel_r(sm.rd32(al, lo, hi), sm.rd32(al + 4, lo, hi), 8 * int(src[k]))
-                            ev = (ev + prmt(xw, 0, 0x4240)).astype(np.uint32)
-                            od = (od + prmt(xw, 0, 0x4341)).astype(np.uint32)
-                        A = prmt(ev, od, 0x5410)
-                        B = prmt(ev, od, 0x7632)
-                        C = prmt(od, ev, 0x7610)
+                            if E == 1:
+                                al = (int(src[k]) & ~3) + 4 * j
+                                xw = funnel_r(sm.rd32(al, lo, hi), sm.rd32(al + 4, lo, hi), 8 * int(src[k]))
+                                ev = (ev + prmt(xw, 0, 0x4240)).astype(np.uint32)
+                                od = (od + prmt(xw, 0, 0x4341)).astype(np.uint32)
+                            else:
+                                # 16-bit samples: a unit is two words, summed in 16-bit lanes (no carry)
+                                assert int(src[k]) % 2 == 0
+                                al = (int(src[k]) & ~3) + 8 * j
+                                w0, w1, w2 = (sm.rd32(al + 4 * q, lo, hi) for q in range(3))
+                                ev = (ev + funnel_r(w0, w1, 8 * int(src[k]))).astype(np.uint32)   # [R0, R1]
+                                od = (od + funnel_r(w1, w2, 8 * int(src[k]))).astype(np.uint32)   # [R2, R3]
+                        if E == 1:
+                            A = prmt(ev, od, 0x5410)
+                            B = prmt(ev, od, 0x7632)
+                            C = prmt(od, ev, 0x7610)
+                        else:
+                            A, B = ev, od
+                            C = prmt(A, B, 0x5432)
                         A_next = np.append(A[1:], np.uint32(0))
                         D = prmt(B, A_next, 0x5432)
                         sm.wr32(dst0 + 8 * j, A, lo_p, hi_p)
@@ -210,6 +223,39 @@ def test_factored_kernel_emulation(v, CC):
     assert (tb["delays"] == d).all()
     S = emulate(x, n_in, sb, tb, v, CC, n_dm, n_out)
     want = oracle.dedisperse(oracle.downsample(x, 1, n_in=n_in), sb, d, n_out)
+    assert (S == want).all()
+
+
+@pytest.mark.parametrize("v", fact_variants(), ids=lambda v: "v%d_G%d_bd%d_t%d" % (
+    v["index"], v["group"], v["dm_per_block"], v["tile"]))
+@pytest.mark.parametrize("D", [2, 4])
+def test_factored_kernel_emulation_16bit(v, D):
+    """The same emulation for a downsampled range: the staged rows are the
+    16-bit sums of D samples (byte offsets twice the sample offsets, a build
+    unit two words summed in 16-bit lanes), against the oracle's brute-force
+    dedispersion of the oracle's downsampled rows."""
+    import paper_2205_12362_b300 as fdd
+    CC = 8 if v["group"] <= 8 else 16
+    rng = np.random.default_rng(v["index"] + D)
+    n_tab, n_chan, n_sb, n_out = 2, 37, 2, 150
+    f = synth.channel_freqs(n_chan)
+    n_dm = v["dm_per_block"] + 5
+    ranges = [dict(dm0=3.0, ddm=2.5 * D, n_dm=n_dm, downsamp=D, widths=[1])]
+    d = oracle.delays(f, T_SAMP, 3.0, 2.5 * D, n_dm, D)
+    n_in = (n_out + int(d.max()) + 3) * D
+    x = rng.integers(0, 256, size=(n_tab, n_chan, synth.padded_pitch(n_in)), dtype=np.int64).astype(np.uint8)
+    sb = rng.integers(0, n_tab, size=(n_sb, n_chan)).astype(np.int16)
+    tb = fdd.fact_tables_host(n_tab, n_chan, n_sb, f, T_SAMP, ranges, sb, 0, v["index"], CC)
+    if tb["Lw"] < 0:
+        pytest.skip("staged rows of twice the bytes exceed the kernel's row limit for this tile")
+    if int(tb["pd_idx"][..., 1].max()) * (tb["desc_ints"] // 4) > v["threads"]:
+        pytest.skip("layout the library refuses (stage descriptors exceed one int4 per thread)")
+    assert (tb["delays"] == d).all()
+    y = oracle.downsample(x, D, n_in=n_in)                  # the range's rows (sums of D bytes)
+    assert y.max() < 1 << 16
+    n_y = n_in // D
+    S = emulate(y.astype(np.uint16), n_y, sb, tb, v, CC, n_dm, n_out, E=2)   # staged as 16-bit samples
+    want = oracle.dedisperse(y, sb, d, n_out)
     assert (S == want).all()
 
 

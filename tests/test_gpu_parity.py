@@ -569,19 +569,20 @@ def test_sb_factored_pattern_part(fdd):
     ora, os_ = oracle_candidate_superset(x, sb, f, T_SAMP, ranges, 6.0, n_out, n_in, return_series=True)
     dx = to_dev(x)
     vs = [v for v in fdd.variants() if v["kind"] == 3]
-    assert vs and {v["group"] for v in vs} == {4, 8}
+    assert vs and {v["group"] for v in vs} == {4, 8} and {v["bytes_per_sample"] for v in vs} == {1, 2}
     for v in vs:
+        r = 0 if v["bytes_per_sample"] == 1 else 1   # raw rows, or the D = 4 range's 16-bit rows
         for cc in (0, 8, 16):
             plan = fdd.Plan(n_tab, n_chan, n_sb, f, T_SAMP, ranges, 6.0, sb)
             plan.set_scratch_limit(1)                 # one DM block per slab
             try:
-                plan.set_config(0, v["index"], cc)
+                plan.set_config(r, v["index"], cc)
             except fdd.FddError as e:
                 # the pattern rows of this steep DM step exceed shared memory at a given stage
                 # size; the largest stage that fits (cc = 0) always configures
                 assert cc != 0 and e.code == fdd.FDD_ERR_UNSUPPORTED
                 continue
-            cfg = plan.get_config(0)
+            cfg = plan.get_config(r)
             assert cfg["variant"] == v["index"] and (cc == 0 or cfg["chan_per_stage"] == cc)
             assert cfg["work_ratio"] < 0.5
             res = plan.search(dx, n_in, n_out, want_series=True, cap=1 << 18)
@@ -594,15 +595,49 @@ def test_sb_factored_pattern_part(fdd):
             compare_candidates(gpu, ora, 6.0)
         plan = fdd.Plan(n_tab, n_chan, n_sb, f, T_SAMP, ranges, 6.0, sb)
         plan.set_scratch_limit(1)
-        plan.set_config(0, v["index"], 0)
+        plan.set_config(r, v["index"], 0)
         res = plan.search(dx, n_in, n_out, want_series=True, cap=1 << 18)
         plan.batch_prepare(n_out, fdd.FDD_BATCH_SB_FACTORED)
-        assert plan.get_config(0)["variant"] == v["index"]
+        assert plan.get_config(r)["variant"] == v["index"]
         job = plan.make_job(dx, n_in, n_out, cap=1 << 18, want_series=True)
         bres = plan.search_batch([job], n_out)[0]
         torch.cuda.synchronize()
         assert plan.status() == 0
         assert torch.equal(bres.series, res.series)
+
+
+def test_factored_downsampled_range(fdd):
+    """The pattern-factored kernel on 16-bit (downsampled) rows: a single-SB
+    plan whose D = 2 and D = 4 ranges run a pattern-factored variant built for
+    16-bit samples (the lanes fold every 256 / D channels); every series
+    bit-exact against the oracle, candidates equal."""
+    import torch
+    n_chan, n_out = 300, 1700
+    f = synth.channel_freqs(n_chan)
+    ranges = [dict(dm0=0.0, ddm=0.4, n_dm=70, downsamp=1, widths=[1, 4]),
+              dict(dm0=28.0, ddm=0.8, n_dm=130, downsamp=2, widths=[1, 2, 8]),
+              dict(dm0=132.0, ddm=1.6, n_dm=65, downsamp=4, widths=[1, 4])]
+    n_in = max(int(oracle.delays(f, T_SAMP, r["dm0"], r["ddm"], r["n_dm"], r["downsamp"]).max())
+               * r["downsamp"] + n_out for r in ranges) + 7
+    pulses = [dict(tab=0, start=t0 + oracle.delays(f, T_SAMP, dm, 1.0, 1)[0], width=w, amp=12.0)
+              for t0, dm, w in [(400, 60.0, 4), (1200, 170.0, 8)]]
+    x = synth.filterbank(41, 1, n_chan, n_in, pulses=pulses)
+    sb = np.zeros((1, n_chan), np.int16)
+    ora, os_ = oracle_candidate_superset(x, sb, f, T_SAMP, ranges, 6.0, n_out, n_in, return_series=True)
+    fv = [v for v in fdd.variants() if v["kind"] == 1 and v["group"] == 4 and v["dm_per_block"] == 64
+          and v["tile"] == 256][0]
+    plan = fdd.Plan(1, n_chan, 1, f, T_SAMP, ranges, 6.0, sb)
+    for r in (1, 2):
+        plan.set_config(r, fv["index"], 0)
+        assert plan.get_config(r)["variant"] == fv["index"]
+    res = plan.search(to_dev(x), n_in, n_out, want_series=True, cap=1 << 18)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    g = plan.series_views(res.series, n_out)
+    for k in range(3):
+        assert (g[k].cpu().numpy() == os_[k]).all(), k
+    gpu, n = res.candidates()
+    assert compare_candidates(gpu, ora, 6.0) > 0
 
 
 def test_boxcar_width_sets(fdd):
