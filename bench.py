@@ -481,6 +481,9 @@ def e2e_streaming(arm, host_chunk, steps):
     import torch
     wins, L, n_in, stream = arm.wins, arm.n_out, arm.n_in, arm.stream
     keep = n_in - L
+    pitch = int(wins[0].shape[-1])
+    rows = int(wins[0].shape[0] * wins[0].shape[1])
+    assert tuple(host_chunk.shape) == (wins[0].shape[0], wins[0].shape[1], L) and host_chunk.is_contiguous()
     copy_stream = torch.cuda.Stream(device=wins[0].device)
     ready = [torch.cuda.Event() for _ in wins]
     done = [torch.cuda.Event() for _ in wins]
@@ -506,8 +509,9 @@ def e2e_streaming(arm, host_chunk, steps):
         with torch.cuda.stream(copy_stream):
             if k >= 2:
                 copy_stream.wait_event(done[b])          # search k-2 has finished reading buffer b
-            wins[b][:, :, :keep].copy_(wins[o][:, :, L:n_in], non_blocking=True)   # overlap carried on
-            wins[b][:, :, keep:n_in].copy_(host_chunk, non_blocking=True)        # the new chunk
+            # 2-D copies on a copy engine: the overlap carried on, then the new chunk from host memory
+            arm.fdd.copy_rows(wins[b], 0, pitch, wins[o], L, pitch, keep, rows, stream=copy_stream)
+            arm.fdd.copy_rows(wins[b], keep, pitch, host_chunk, 0, L, L, rows, stream=copy_stream)
             ready[b].record(copy_stream)
         h2d += host_chunk.numel()
         stream.wait_event(ready[b])

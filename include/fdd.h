@@ -494,6 +494,16 @@ int fdd_stream_open(fdd_plan* plan, int32_t beam_id, int64_t chunk_len, int64_t 
  * INVALID_ARG, CUDA. */
 int fdd_stream_push(fdd_stream* st, const uint8_t* d_chunk, int64_t chunk_pitch, int64_t seq, fdd_stream_t stream);
 
+/* (No counterpart in the paper: window assembly for a caller that streams
+ * chunks into its own window buffers.)  Enqueue on `stream` a copy of `rows`
+ * rows of `width` bytes from src (row r at src + r * src_pitch) to dst (row
+ * r at dst + r * dst_pitch); either side may be device or page-locked host
+ * memory (the direction follows from the pointers).  Runs on a copy engine,
+ * not on the SMs.  Errors: INVALID_ARG (null pointer, negative size, a
+ * pitch below the width), CUDA. */
+int fdd_copy_rows(void* dst, int64_t dst_pitch, const void* src, int64_t src_pitch, int64_t width, int64_t rows,
+                  fdd_stream_t stream);
+
 /* Results of the window searched last, if no fdd_stream_results call has
  * taken them yet: enqueues, on the CUDA stream of the last push, a copy of
  * the first min(true count, cap, stream cap) candidate records to device

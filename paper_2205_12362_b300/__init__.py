@@ -130,6 +130,7 @@ def _lib_raw():
     L.fdd_search_window.argtypes = [_P, _P, _I64, _I64, _I64, _I64, _P, _SZ, _P, _I64, _P, _P, _P]
     L.fdd_window_sizes.argtypes = [_P, _I64, ctypes.POINTER(_I64), ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]
     L.fdd_downsample_u8.argtypes = [_P, _I64, _I64, _I64, _I32, _P, _I64, _P]
+    L.fdd_copy_rows.argtypes = [_P, _I64, _P, _I64, _I64, _I64, _P]
     L.fdd_plan_set_timing.argtypes = [_P, _I32]
     L.fdd_num_variants.argtypes = [ctypes.POINTER(_I32)]
     L.fdd_variant_info.argtypes = [_I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32),
@@ -927,6 +928,29 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def copy_rows(dst, dst_offset, dst_pitch, src, src_offset, src_pitch, width, rows, stream=None):
+    """Row copy on a copy engine (include/fdd.h: fdd_copy_rows): `rows` rows
+    of `width` bytes from contiguous tensor `src` (byte offset src_offset,
+    row pitch src_pitch) to contiguous tensor `dst`; each is a CUDA tensor or
+    page-locked host memory.  The byte ranges are checked against both
+    tensors before the call."""
+    torch = _torch()
+
+    def ptr(t, off, pitch, name):
+        if not isinstance(t, torch.Tensor) or not (t.is_cuda or t.is_pinned()):
+            raise TypeError("%s must be a CUDA tensor or page-locked host memory" % name)
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        nbytes = t.numel() * t.element_size()
+        if off < 0 or (rows > 0 and off + (rows - 1) * pitch + width > nbytes):
+            raise ValueError("%s: rows reach past the tensor" % name)
+        return ctypes.c_void_p(t.data_ptr() + int(off))
+    code = _lib_raw().fdd_copy_rows(ptr(dst, dst_offset, dst_pitch, "dst"), int(dst_pitch),
+                                    ptr(src, src_offset, src_pitch, "src"), int(src_pitch), int(width), int(rows),
+                                    _stream_handle(stream))
+    _check(code, "fdd_copy_rows")
 
 
 def downsample_u8(x, n_in, downsamp, out=None, stream=None):

@@ -40,25 +40,24 @@ __device__ __forceinline__ uint32_t lds_at(uint32_t a) {
     return v;
 }
 
-// Pre-check of an interior chunk, rows M .. rows-1: lane l of row m takes start j = 32 m + l, whose
-// prefix entries j, j + 1, j + 8 (and j + 64) sit at the lane's base addresses + 132 m bytes in the
-// padded ring (entry J at word J + J / 32, and (32 m + l + k) / 32 = m + (l + k) / 32).
+// Pre-check of a chunk, rows M .. rows-1: lane l of row m takes start j = 32 m + l, whose prefix
+// entries j, j + 8 (and j + 64) sit at the lane's base addresses + 132 m bytes in the padded ring
+// (entry J at word J + J / 32, and (32 m + l + k) / 32 = m + (l + k) / 32).  (The 1-sample maxima
+// come from the samples themselves, in registers.)
 template <int M, bool B64>
 struct PrecheckRows {
-    __device__ static __forceinline__ void run(uint32_t a0, uint32_t a1, uint32_t a8, uint32_t a64, int rows,
-                                               int32_t& mx0, int32_t& mx1, int32_t& mx2) {
+    __device__ static __forceinline__ void run(uint32_t a0, uint32_t a8, uint32_t a64, int rows, int32_t& mx1,
+                                               int32_t& mx2) {
         if constexpr (M < kBoundRows) {
             if (M >= kWarpRows && M >= rows) return;
             const uint32_t p0 = lds_at<132 * M>(a0);
-            const uint32_t p1 = lds_at<132 * M>(a1);
             const uint32_t p8 = lds_at<132 * M>(a8);
-            mx0 = max(mx0, static_cast<int32_t>(p1 - p0));
             mx1 = max(mx1, static_cast<int32_t>(p8 - p0));
             if constexpr (B64) {
                 const uint32_t p64 = lds_at<132 * M>(a64);
                 mx2 = max(mx2, static_cast<int32_t>(p64 - p0));
             }
-            PrecheckRows<M + 1, B64>::run(a0, a1, a8, a64, rows, mx0, mx1, mx2);
+            PrecheckRows<M + 1, B64>::run(a0, a8, a64, rows, mx1, mx2);
         }
     }
 };
@@ -138,7 +137,7 @@ __device__ __forceinline__ void boxcar_series_warp(const BoxSeries& v, uint32_t*
     const int n_chunks = nv / kWarpCS + 1;
     const uint32_t ring_s = static_cast<uint32_t>(__cvta_generic_to_shared(ring));
     uint32_t carry = 0;
-    // Chunk pre-check (widths <= kBoundWmax): for bases b in {1, 8, 64}, M_b = max of B_b(s) over s in
+    // Chunk pre-check (widths <= kBoundWmax): for bases b in {1, 8, 64}, M_b >= max of B_b(s) over s in
     // [chunk start, chunk end + wmax - 1].  A width w with base b (the largest base dividing it) has
     // B_w(t) = sum_{j < w/b} B_b(t + j b) <= (w/b) M_b for every t of the chunk, so a chunk where
     // (w/b) M_b <= tau_w for every width holds no candidate and is skipped; any other chunk is
@@ -192,6 +191,9 @@ __device__ __forceinline__ void boxcar_series_warp(const BoxSeries& v, uint32_t*
     };
     uint32_t nx[16];  // the next chunk's samples, loaded a chunk ahead
     fetch(0, nx);
+    // the lane's largest sample of chunk c - 1 and of chunk c (raw values; m0 stands in outside the
+    // series): the 1-sample pre-check maximum of chunk e = c - 1 is bounded by the larger of the two
+    int32_t lmax_prev = -2147483647 - 1, lmax_cur = lmax_prev;
 
     // Chunk c = n_chunks lies wholly past the series: its flat prefix entries are written too, so
     // every chunk's pre-check can read its successor's first entries.
@@ -201,6 +203,10 @@ __device__ __forceinline__ void boxcar_series_warp(const BoxSeries& v, uint32_t*
 #pragma unroll
             for (int k = 0; k < 16; k++) xs[k] = nx[k];
             if (c < n_chunks) fetch(c + 1, nx);  // in flight while this chunk is scanned and the last one evaluated
+            lmax_prev = lmax_cur;
+            lmax_cur = static_cast<int32_t>(xs[0]);
+#pragma unroll
+            for (int k = 1; k < 16; k++) lmax_cur = max(lmax_cur, static_cast<int32_t>(xs[k]));
             // lane total of the centred samples, then one warp scan of the lane totals
             uint32_t lane_tot = neg16m0;
 #pragma unroll
@@ -250,16 +256,17 @@ __device__ __forceinline__ void boxcar_series_warp(const BoxSeries& v, uint32_t*
             // Every entry the pre-check reads is written (chunk c follows chunk e in the ring), and a
             // start outside the series only adds windows of the zero-padded series to the maxima,
             // which keeps them upper bounds.
-            int32_t mx0 = -2147483647 - 1, mx1 = mx0, mx2 = mx0;
+            int32_t mx1 = -2147483647 - 1, mx2 = mx1;
             const int rows = kWarpRows + (wmax - 1 + 31) / 32;
             const uint32_t a0 = s_slot + 4u * static_cast<uint32_t>(lane);
-            const uint32_t a1 = s_slot + 4u * static_cast<uint32_t>(lane + 1 + ((lane + 1) >> 5));
             const uint32_t a8 = s_slot + 4u * static_cast<uint32_t>(lane + 8 + ((lane + 8) >> 5));
             const uint32_t a64 = s_slot + 4u * static_cast<uint32_t>(lane + 66);
             if (wmax >= 64)
-                PrecheckRows<0, true>::run(a0, a1, a8, a64, rows, mx0, mx1, mx2);
+                PrecheckRows<0, true>::run(a0, a8, a64, rows, mx1, mx2);
             else
-                PrecheckRows<0, false>::run(a0, a1, a8, a64, rows, mx0, mx1, mx2);
+                PrecheckRows<0, false>::run(a0, a8, a64, rows, mx1, mx2);
+            // 1-sample boxes: every start of the pre-check lies in chunk e or e + 1 (rows <= 2 chunks)
+            const int32_t mx0 = static_cast<int32_t>(static_cast<uint32_t>(max(lmax_prev, lmax_cur)) - m0u);
             if (!__any_sync(0xffffffffu, mx0 > thb0 || mx1 > thb1 || mx2 > thb2)) {
                 __syncwarp();  // slot e % 3 may be rewritten by chunk c + 2
                 continue;

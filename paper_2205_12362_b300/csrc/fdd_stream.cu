@@ -162,4 +162,15 @@ int fdd_stream_close(fdd_stream* st) {
     return FDD_OK;
 }
 
+int fdd_copy_rows(void* dst, int64_t dst_pitch, const void* src, int64_t src_pitch, int64_t width, int64_t rows,
+                  fdd_stream_t stream) {
+    if (!dst || !src || width < 0 || rows < 0 || dst_pitch < width || src_pitch < width)
+        return fail(FDD_ERR_INVALID_ARG, "bad row copy");
+    if (width == 0 || rows == 0) return FDD_OK;
+    const cudaError_t e = cudaMemcpy2DAsync(dst, static_cast<size_t>(dst_pitch), src, static_cast<size_t>(src_pitch),
+                                            static_cast<size_t>(width), static_cast<size_t>(rows), cudaMemcpyDefault,
+                                            reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FDD_OK : cuda_fail(e, "row copy");
+}
+
 }  // extern "C"

@@ -115,3 +115,18 @@ def test_static_scratch_size_matches_header():
     m = re.search(r"#define\s+FDD_STATIC_SCRATCH_BYTES\s+\((\d+)u\s*\*\s*(\d+)u\s*\*\s*(\d+)u\)", text)
     assert m, "FDD_STATIC_SCRATCH_BYTES not found in include/fdd.h"
     assert fdd.Plan.STATIC_SCRATCH_BYTES == int(m.group(1)) * int(m.group(2)) * int(m.group(3))
+
+
+def test_copy_rows_rejects_bad_arguments(lib):
+    """fdd_copy_rows refuses null pointers and pitches below the width on the
+    host, before any CUDA call."""
+    f = lib.fdd_copy_rows
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                  ctypes.c_void_p]
+    buf = ctypes.create_string_buffer(64)
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    assert f(None, 16, p, 16, 8, 2, None) == -1
+    assert f(p, 16, None, 16, 8, 2, None) == -1
+    assert f(p, 4, p, 16, 8, 2, None) == -1          # destination pitch below the width
+    assert f(p, 16, p, 4, 8, 2, None) == -1          # source pitch below the width
+    assert f(p, 16, p, 16, -1, 2, None) == -1

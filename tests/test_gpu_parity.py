@@ -640,6 +640,25 @@ def test_factored_downsampled_range(fdd):
     assert compare_candidates(gpu, ora, 6.0) > 0
 
 
+def test_copy_rows(fdd):
+    """fdd_copy_rows: rows from page-locked host memory into a strided
+    device window and a device-to-device carry of row tails, equal to numpy
+    slicing; ranges past a tensor are refused before the call."""
+    import torch
+    rows, L, pitch, keep = 37, 1000, 1312, 300
+    host = torch.from_numpy(np.arange(rows * L, dtype=np.int64).astype(np.uint8).reshape(rows, L)).pin_memory()
+    win = torch.zeros((rows, pitch), dtype=torch.uint8, device="cuda")
+    fdd.copy_rows(win, keep, pitch, host, 0, L, L, rows)
+    nxt = torch.zeros_like(win)
+    fdd.copy_rows(nxt, 0, pitch, win, L, pitch, keep, rows)           # tail of each row to the head
+    torch.cuda.synchronize()
+    w = win.cpu().numpy()
+    assert (w[:, keep:keep + L] == host.numpy()).all() and (w[:, :keep] == 0).all()
+    assert (nxt.cpu().numpy()[:, :keep] == w[:, L:L + keep]).all()
+    with pytest.raises(ValueError):
+        fdd.copy_rows(win, keep + 100, pitch, host, 0, L, L, rows)    # last row past the window
+
+
 def test_boxcar_width_sets(fdd):
     """Both boxcar forms: one warp per series (widths <= 512; 4, 8 and 16
     width slots) and one block per series (a width above 512), against the
