@@ -119,26 +119,46 @@ __global__ void __launch_bounds__(CW * 32, 2) k_sbf_comb(const __grid_constant__
         const int u0 = ch * UC;
         const int nu = min(UC, a.n_seg - u0);
         const uint32_t s_buf = s_base + buf * buf_bytes + 8u * lane;
+        // segment du of the chunk for every SB of the warp: the TAB (byte dq of tabs4; PRMT zero-fills
+        // the rest) times kTabBytes (2^11) picks the row
+        auto add_segment = [&](const uint32_t (&tabs4)[CSB], int dq, int du) {
 #pragma unroll
-        for (int q = 0; q < UC; q += 4) {
-            uint32_t tabs4[CSB];
+            for (int j = 0; j < CSB; j++) {
+                const uint32_t tab = __byte_perm(tabs4[j], 0u, 0x4440u + dq);
+                const uint2 v = lds64(s_buf + (tab << 11) + du * kRowBytes);
+                acc[j][0] += v.x;
+                acc[j][1] += v.y;
+            }
+        };
+        if (nu == UC && a.flush % UC == 0) {  // block-uniform: a whole chunk, folds only at its end
 #pragma unroll
-            for (int j = 0; j < CSB; j++) tabs4[j] = __ldg(reinterpret_cast<const uint32_t*>(tab_row[j] + u0 + q));
+            for (int q = 0; q < UC; q += 4) {
+                uint32_t tabs4[CSB];
 #pragma unroll
-            for (int dq = 0; dq < 4; dq++) {
-                const int du = q + dq;
-                if (du < nu) {  // block-uniform
+                for (int j = 0; j < CSB; j++) tabs4[j] = __ldg(reinterpret_cast<const uint32_t*>(tab_row[j] + u0 + q));
 #pragma unroll
-                    for (int j = 0; j < CSB; j++) {
-                        // byte dq of tabs4 (the TAB; PRMT zero-fills the rest) times kTabBytes (2^11)
-                        const uint32_t tab = __byte_perm(tabs4[j], 0u, 0x4440u + dq);
-                        const uint2 v = lds64(s_buf + (tab << 11) + du * kRowBytes);
-                        acc[j][0] += v.x;
-                        acc[j][1] += v.y;
-                    }
-                    if (++since == a.flush) {
-                        fold();
-                        since = 0;
+                for (int dq = 0; dq < 4; dq++) add_segment(tabs4, dq, q + dq);
+            }
+            since += UC;
+            if (since == a.flush) {
+                fold();
+                since = 0;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < UC; q += 4) {
+                uint32_t tabs4[CSB];
+#pragma unroll
+                for (int j = 0; j < CSB; j++) tabs4[j] = __ldg(reinterpret_cast<const uint32_t*>(tab_row[j] + u0 + q));
+#pragma unroll
+                for (int dq = 0; dq < 4; dq++) {
+                    const int du = q + dq;
+                    if (du < nu) {  // block-uniform
+                        add_segment(tabs4, dq, du);
+                        if (++since == a.flush) {
+                            fold();
+                            since = 0;
+                        }
                     }
                 }
             }
