@@ -258,7 +258,7 @@ int fdd_variant_info(int32_t variant, int32_t* bytes_per_sample, int32_t* dm_per
 /* Diagnostics: the tables of pattern-factored variant `variant` (a global
  * variant index with *group > 0) for native-rate range r of a plan
  * description, built on the host only (no GPU), for inspection and CPU
- * checks of the kernel's shared-memory addressing.  info[0..13] receives Lw
+ * checks of the kernel's shared-memory addressing.  info[0..14] receives Lw
  * (raw row words; < 0 if the layout does not fit), bytes of one pattern-row
  * buffer, groups, stages, ints per descriptor, shared-memory bytes,
  * descriptors, DM blocks, then the byte offsets (from the kernel's
@@ -266,12 +266,16 @@ int fdd_variant_info(int32_t variant, int32_t* bytes_per_sample, int32_t* dm_per
  * one raw slot's size, the pattern region and the two mbarriers, and the
  * number of pattern-row buffers (2: stage s + 1 is built into the other
  * buffer while stage s accumulates; the descriptor and offset tables then
- * hold the buffer's address).  Array arguments may be NULL (sizes first, then data): base
+ * hold the buffer's address), and in info[14] the channels per TMA copy (4:
+ * the rows of 4 consecutive channels travel as one box of slot-size rows
+ * from the box's least staged start, bbase [n_blk][ceil(n_chan / 4)], each
+ * channel's data shifted by its start's distance to it, as the descriptors
+ * record; 1: one copy per row).  Array arguments may be NULL (sizes first, then data): base
  * [n_blk][n_chan], goff [n_blk][n_groups][BD], pdesc [n_desc][desc_ints],
  * pd_idx [n_blk][n_stages][2], delays [n_dm][n_chan]. */
 int fdd_fact_tables_host(const fdd_plan_desc* desc, const int16_t* sb_map_host, int32_t range, int32_t variant,
                          int32_t chan_per_stage, int64_t* info, int32_t* base, int32_t* goff, int32_t* pdesc,
-                         int32_t* pd_idx, int32_t* delays);
+                         int32_t* pd_idx, int32_t* delays, int32_t* bbase);
 
 /* Current kernel configuration of range r. */
 int fdd_plan_get_config(const fdd_plan* plan, int32_t r, fdd_kernel_config* out);

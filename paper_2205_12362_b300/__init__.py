@@ -158,7 +158,7 @@ def _lib_raw():
     L.fdd_server_results.argtypes = [_P, ctypes.POINTER(_WindowResult), _I32, _P, _I64, ctypes.POINTER(_I32),
                                      ctypes.POINTER(_I64)]
     L.fdd_server_info.argtypes = [_P, ctypes.POINTER(_ServerStats)]
-    L.fdd_fact_tables_host.argtypes = [ctypes.POINTER(_PlanDesc), _P, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P]
+    L.fdd_fact_tables_host.argtypes = [ctypes.POINTER(_PlanDesc), _P, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P]
     L.fdd_search_static.argtypes = [_P, _P, _I64, _I64, _I64, _I64, _P, _I64, _P, _P, _P]
     L.fdd_plan_stage_times.argtypes = [_P, _I32, _P, _P, _P, ctypes.POINTER(_I32)]
     L.fdd_plan_info.argtypes = [_P, _I64, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]
@@ -589,14 +589,15 @@ def fact_tables_host(n_tab, n_chan, n_sb, chan_freq_mhz, t_samp_s, ranges, sb_ma
     keep = []
     desc = _plan_desc(n_tab, n_chan, n_sb, chan_freq_mhz, t_samp_s, ranges, 0.0, keep)
     sb = np.ascontiguousarray(sb_map, dtype=np.int16)
-    info = np.zeros(14, np.int64)
+    info = np.zeros(15, np.int64)
     args = [ctypes.byref(desc), sb.ctypes.data_as(ctypes.c_void_p), int(r), int(variant), int(chan_per_stage),
             info.ctypes.data_as(ctypes.c_void_p)]
-    _check(L.fdd_fact_tables_host(*args, None, None, None, None, None), "fdd_fact_tables_host")
+    _check(L.fdd_fact_tables_host(*args, None, None, None, None, None, None), "fdd_fact_tables_host")
     Lw, pat_bytes, n_groups, n_stages, desc_ints, smem, n_desc, n_blk = [int(v) for v in info[:8]]
     out = dict(Lw=Lw, pat_bytes=pat_bytes, n_groups=n_groups, n_stages=n_stages, desc_ints=desc_ints,
                smem_bytes=smem, n_desc=n_desc, n_blk=n_blk)
-    out.update(zip(["zero_off", "raw_off", "rb", "pat_off", "bar_off", "pat_bufs"], [int(v) for v in info[8:]]))
+    out.update(zip(["zero_off", "raw_off", "rb", "pat_off", "bar_off", "pat_bufs", "box_rows"],
+                   [int(v) for v in info[8:]]))
     if Lw < 0:
         return out
     v = variants()[int(variant)]
@@ -607,9 +608,10 @@ def fact_tables_host(n_tab, n_chan, n_sb, chan_freq_mhz, t_samp_s, ranges, sb_ma
     out["pdesc"] = np.zeros((max(n_desc, 1), desc_ints), np.int32)
     out["pd_idx"] = np.zeros((n_blk, n_stages, 2), np.int32)
     out["delays"] = np.zeros((n_dm, n_chan), np.int32)
+    out["bbase"] = np.zeros((n_blk, (n_chan + 3) // 4), np.int32)
     ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     _check(L.fdd_fact_tables_host(*args, ptr(out["base"]), ptr(out["goff"]), ptr(out["pdesc"]), ptr(out["pd_idx"]),
-                                  ptr(out["delays"])), "fdd_fact_tables_host")
+                                  ptr(out["delays"]), ptr(out["bbase"])), "fdd_fact_tables_host")
     return out
 
 

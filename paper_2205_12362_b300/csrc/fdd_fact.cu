@@ -39,7 +39,8 @@ using namespace fdd::host;
 namespace fdd {
 namespace host {
 
-FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactVariant& v, int CC) {
+FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactVariant& v, int CC,
+                             bool consecutive_rows) {
     FactTables ft;
     const int G = v.G, BD = v.bd(), T = v.tile();
     const int E = r.D == 1 ? 1 : 2;  // bytes per staged sample
@@ -168,9 +169,30 @@ FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactV
     ft.Lw = static_cast<int32_t>(Lw);
     ft.pat_bytes = static_cast<int32_t>(align_up(static_cast<size_t>(pat_region), 16));
     ft.pat_bufs = v.PB;
+    // channel boxes: 4 consecutive channels per TMA copy, when their rows are consecutive in the tensor
+    // and a box row (the row plus the spread of the 4 starts) stays within one TMA box of 256 words
+    constexpr int kBoxRows = 4;
+    const int n_boxes4 = (n_chan + kBoxRows - 1) / kBoxRows;
+    std::vector<int32_t> bb(static_cast<size_t>(n_blk) * n_boxes4);
+    int64_t spread = 0;  // words
+    for (int b = 0; b < n_blk; b++)
+        for (int k = 0; k < n_boxes4; k++) {
+            int32_t lo = ft.base[static_cast<size_t>(b) * n_chan + k * kBoxRows];
+            for (int c = k * kBoxRows; c < std::min(n_chan, (k + 1) * kBoxRows); c++)
+                lo = std::min(lo, ft.base[static_cast<size_t>(b) * n_chan + c]);
+            bb[static_cast<size_t>(b) * n_boxes4 + k] = lo;
+            for (int c = k * kBoxRows; c < std::min(n_chan, (k + 1) * kBoxRows); c++)
+                spread = std::max<int64_t>(spread, (static_cast<int64_t>(ft.base[static_cast<size_t>(b) * n_chan + c]) - lo) *
+                                                       E / 4);
+        }
+    const int64_t rb4 = static_cast<int64_t>(align_up(static_cast<size_t>(4 * (Lw + spread)), 128));
+    const bool boxes = consecutive_rows && fdd::fact_boxes(static_cast<int>(Lw)) == 1 && rb4 / 4 <= 256 &&
+                       CC % kBoxRows == 0;
+    ft.box_rows = boxes ? kBoxRows : 1;
+    if (boxes) ft.bbase.swap(bb);
     // resolve shared-memory addresses
     ft.zero_off = 0;
-    ft.rb = static_cast<int32_t>(align_up(static_cast<size_t>(4 * Lw), 128));
+    ft.rb = boxes ? static_cast<int32_t>(rb4) : static_cast<int32_t>(align_up(static_cast<size_t>(4 * Lw), 128));
     ft.raw_off = static_cast<int32_t>(align_up(static_cast<size_t>(4 * Lw + 16), 128));
     ft.pat_off = ft.raw_off + 2 * CC * ft.rb;
     if (v.PB == 2) {
@@ -188,6 +210,20 @@ FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactV
                         ft.goff[(static_cast<size_t>(b) * n_groups + s * gps + gl) * BD + jj] += shift;
             }
     }
+    // DM block and stage of every descriptor (for the channel-box shifts)
+    std::vector<int32_t> desc_blk, desc_stage;
+    if (boxes) {
+        desc_blk.assign(ft.pdesc.size() / ft.desc_ints, 0);
+        desc_stage.assign(ft.pdesc.size() / ft.desc_ints, 0);
+        for (int b = 0; b < n_blk; b++)
+            for (int s = 0; s < n_stages; s++) {
+                const size_t k = (static_cast<size_t>(b) * n_stages + s) * 2;
+                for (int d = ft.pd_idx[k]; d < ft.pd_idx[k] + ft.pd_idx[k + 1]; d++) {
+                    desc_blk[d] = b;
+                    desc_stage[d] = s;
+                }
+            }
+    }
     for (size_t di = 0; di < ft.pdesc.size(); di += ft.desc_ints) {
         ft.pdesc[di] += ft.pat_off;
         ft.pdesc[di + 1] += ft.pat_off;
@@ -198,6 +234,12 @@ FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactV
             } else {
                 const int32_t par = e >> 30, cc = (e >> 20) & 1023, o = e & ((1 << 20) - 1);
                 e = ft.raw_off + (par * CC + cc) * ft.rb + o;
+                if (boxes) {  // the channel's row sits after the gap between its box's start and its own
+                    const int b = desc_blk[di / ft.desc_ints];
+                    const int c = desc_stage[di / ft.desc_ints] * CC + cc;
+                    e += (ft.base[static_cast<size_t>(b) * n_chan + c] -
+                          ft.bbase[static_cast<size_t>(b) * n_boxes4 + c / kBoxRows]) * E;
+                }
             }
         }
     }

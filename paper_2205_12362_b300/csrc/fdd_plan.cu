@@ -221,7 +221,7 @@ int fdd::host::check_search_args(const fdd_plan* plan, const uint8_t* d_tabs, in
 namespace {
 
 void free_fact_tables(RangeState& r) {
-    for (int32_t** ptr : {&r.d_fbase, &r.d_goff, &r.d_pdesc, &r.d_pdidx}) {
+    for (int32_t** ptr : {&r.d_fbase, &r.d_goff, &r.d_pdesc, &r.d_pdidx, &r.d_fbbase}) {
         if (*ptr) cudaFree(*ptr);
         *ptr = nullptr;
     }
@@ -261,7 +261,7 @@ int configure_fact(fdd_plan* p, RangeState& r, int fv, int CC) {
     for (int cc : {64, 48, 32, 16, 8, 4}) {
         if (CC != 0 && cc != CC) continue;
         if (cc % v.G) continue;
-        FactTables ft = build_fact_tables(p, r, v, cc);
+        FactTables ft = build_fact_tables(p, r, v, cc, p->n_tab == 1);
         if (ft.Lw < 0 || !fdd::fact_cc_ok(v, ft.Lw, cc, ft.max_desc) || ft.smem_bytes > kSmemBudget) continue;
         best = std::move(ft);
         best_cc = cc;
@@ -275,6 +275,8 @@ int configure_fact(fdd_plan* p, RangeState& r, int fv, int CC) {
     if ((rc = upload_vec(&r.d_goff, best.goff, "factored offset table")) != FDD_OK) return rc;
     if ((rc = upload_vec(&r.d_pdesc, best.pdesc, "factored descriptors")) != FDD_OK) return rc;
     if ((rc = upload_vec(&r.d_pdidx, best.pd_idx, "factored descriptor index")) != FDD_OK) return rc;
+    if ((rc = upload_vec(&r.d_fbbase, best.bbase, "factored box starts")) != FDD_OK) return rc;
+    r.f_box_rows = best.box_rows;
     r.fact = fv;
     r.f_CC = best_cc;
     r.f_Lw = best.Lw;
@@ -338,6 +340,8 @@ cudaError_t launch_range_dedisp(const fdd_plan* p, const RangeState& r, const fd
     fa.goff = r.d_goff;
     fa.pdesc = r.d_pdesc;
     fa.pd_idx = r.d_pdidx;
+    fa.bbase = r.d_fbbase;
+    fa.box_rows = r.f_box_rows;
     fa.series = a.series;
     fa.stat = a.stat;
     fa.n_chan = a.n_chan;
@@ -980,7 +984,7 @@ int fdd_plan_autotune(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64
 
 int fdd_fact_tables_host(const fdd_plan_desc* desc, const int16_t* sb_map_host, int32_t range, int32_t variant,
                          int32_t chan_per_stage, int64_t* info, int32_t* base, int32_t* goff, int32_t* pdesc,
-                         int32_t* pd_idx, int32_t* delays) {
+                         int32_t* pd_idx, int32_t* delays, int32_t* bbase) {
     if (!info) return fail(FDD_ERR_INVALID_ARG, "null info");
     fdd_plan p;
     int rc = build_host_plan(desc, sb_map_host, &p);
@@ -992,7 +996,7 @@ int fdd_fact_tables_host(const fdd_plan_desc* desc, const int16_t* sb_map_host, 
     const fdd::FactVariant& v = fdd::fact_variant(fv);
     if (chan_per_stage % v.G) return fail(FDD_ERR_INVALID_ARG, "stage size must be a multiple of G");
     const RangeState& r = p.ranges[range];
-    const FactTables ft = build_fact_tables(&p, r, v, chan_per_stage);
+    const FactTables ft = build_fact_tables(&p, r, v, chan_per_stage, p.n_tab == 1);
     const int64_t n_blk = (r.n_dm + v.bd() - 1) / v.bd();
     info[0] = ft.Lw;
     info[1] = ft.pat_bytes;
@@ -1008,12 +1012,14 @@ int fdd_fact_tables_host(const fdd_plan_desc* desc, const int16_t* sb_map_host, 
     info[11] = ft.pat_off;
     info[12] = ft.bar_off;
     info[13] = ft.pat_bufs;
+    info[14] = ft.box_rows;
     if (ft.Lw < 0) return FDD_OK;
     if (base) std::memcpy(base, ft.base.data(), ft.base.size() * sizeof(int32_t));
     if (goff) std::memcpy(goff, ft.goff.data(), ft.goff.size() * sizeof(int32_t));
     if (pdesc) std::memcpy(pdesc, ft.pdesc.data(), ft.pdesc.size() * sizeof(int32_t));
     if (pd_idx) std::memcpy(pd_idx, ft.pd_idx.data(), ft.pd_idx.size() * sizeof(int32_t));
     if (delays) std::memcpy(delays, r.delay.data(), r.delay.size() * sizeof(int32_t));
+    if (bbase && !ft.bbase.empty()) std::memcpy(bbase, ft.bbase.data(), ft.bbase.size() * sizeof(int32_t));
     return FDD_OK;
 }
 

@@ -91,7 +91,7 @@ void free_sbf_tables(RangeState& r, bool geometry) {
     if (r.d_sstages) cudaFree(r.d_sstages);
     r.d_sstages = nullptr;
     if (r.s_fact >= 0) {  // the pattern-factored part's tables
-        for (int32_t** ptr : {&r.d_fbase, &r.d_goff, &r.d_pdesc, &r.d_pdidx}) {
+        for (int32_t** ptr : {&r.d_fbase, &r.d_goff, &r.d_pdesc, &r.d_pdidx, &r.d_fbbase}) {
             if (*ptr) cudaFree(*ptr);
             *ptr = nullptr;
         }
@@ -145,7 +145,7 @@ int configure_sbf_fact(fdd_plan* p, RangeState& r, int sv, int CC) {
     for (int cc : {64, 48, 32, 16, 8, 4}) {
         if (CC != 0 && cc != CC) continue;
         if (cc % v.G) continue;
-        FactTables ft = build_fact_tables(p, r, v, cc);
+        FactTables ft = build_fact_tables(p, r, v, cc, true);  // one TAB per block: consecutive rows
         if (ft.Lw < 0 || !fdd::fact_cc_ok(v, ft.Lw, cc, ft.max_desc) || ft.smem_bytes > kSmemBudget) continue;
         best = std::move(ft);
         cc_pick = cc;
@@ -171,7 +171,8 @@ int configure_sbf_fact(fdd_plan* p, RangeState& r, int sv, int CC) {
         sseg[st] = make_int2(mask, seg_of[st * cc_pick]);
     }
     free_sbf_tables(r, true);
-    for (int32_t** ptr : {&r.d_fbase, &r.d_goff, &r.d_pdesc, &r.d_pdidx}) {  // a pattern-factored range's tables
+    // the tables of a pattern-factored configuration of this range
+    for (int32_t** ptr : {&r.d_fbase, &r.d_goff, &r.d_pdesc, &r.d_pdidx, &r.d_fbbase}) {
         if (*ptr) cudaFree(*ptr);
         *ptr = nullptr;
     }
@@ -184,6 +185,8 @@ int configure_sbf_fact(fdd_plan* p, RangeState& r, int sv, int CC) {
     if ((rc = upload(&r.d_pdesc, best.pdesc, "factored descriptors")) != FDD_OK) return rc;
     if ((rc = upload(&r.d_pdidx, best.pd_idx, "factored descriptor index")) != FDD_OK) return rc;
     if ((rc = upload(&r.d_fsseg, sseg, "segment closings per stage")) != FDD_OK) return rc;
+    if ((rc = upload(&r.d_fbbase, best.bbase, "factored box starts")) != FDD_OK) return rc;
+    r.f_box_rows = best.box_rows;
     r.f_CC = cc_pick;
     r.f_Lw = best.Lw;
     r.f_pat_bytes = best.pat_bytes;
@@ -325,6 +328,8 @@ cudaError_t launch_range_sbf(const fdd_plan* p, const RangeState& r, const fdd::
         fa.goff = r.d_goff;
         fa.pdesc = r.d_pdesc;
         fa.pd_idx = r.d_pdidx;
+        fa.bbase = r.d_fbbase;
+        fa.box_rows = r.f_box_rows;
         fa.n_chan = p->n_chan;
         fa.n_dm = r.n_dm;
         fa.n_out = a.n_out;

@@ -91,7 +91,7 @@ def emulate(x, n_valid, sb_map, tb, v, CC, n_dm, n_out, E=1):
         if addr < zero_hi:
             return zero_lo, zero_hi
         k = (addr - raw_lo) // rb
-        return raw_lo + k * rb, raw_lo + k * rb + 4 * Lw
+        return raw_lo + k * rb, raw_lo + k * rb + (rb if tb["box_rows"] == 4 else 4 * Lw)
     n_sb = sb_map.shape[0]
     S = np.zeros((n_sb, n_dm, n_out), np.int64)
     lanes = np.arange(32)
@@ -108,14 +108,20 @@ def emulate(x, n_valid, sb_map, tb, v, CC, n_dm, n_out, E=1):
                     c0 = s * CC
                     for cc in range(min(CC, n_chan - c0)):   # raw staging (the TMA box of stage s)
                         c = c0 + cc
-                        start = (t0 + tb["base"][blk, c]) * E      # byte of the row's first staged sample
+                        if tb["box_rows"] == 4:
+                            # the channel's row arrives in its 4-channel box: rb bytes from the box's start
+                            start = (t0 + tb["bbase"][blk, c // 4]) * E
+                            width = rb
+                        else:
+                            start = (t0 + tb["base"][blk, c]) * E  # byte of the row's first staged sample
+                            width = 4 * Lw
                         assert start % 16 == 0                     # TMA x coordinate on a 16-byte boundary
-                        idx = start + np.arange(4 * Lw)
+                        idx = start + np.arange(width)
                         row = np.ascontiguousarray(x[sb_map[sb, c], c]).view(np.uint8)   # little-endian bytes
                         byts = np.where(idx < 4 * words_valid, row[np.minimum(idx, row.size - 1)], 0)
                         byts = np.where((idx >= n_valid * E) & (idx < 4 * words_valid), 0xE7, byts)  # pitch padding
                         slot = raw_lo + ((s % 2) * CC + cc) * rb
-                        sm.m[slot:slot + 4 * Lw] = byts.astype(np.uint8)
+                        sm.m[slot:slot + width] = byts.astype(np.uint8)
 
                 def build(s):
                     stage_raw(s)
@@ -256,6 +262,33 @@ def test_factored_kernel_emulation_16bit(v, D):
     n_y = n_in // D
     S = emulate(y.astype(np.uint16), n_y, sb, tb, v, CC, n_dm, n_out, E=2)   # staged as 16-bit samples
     want = oracle.dedisperse(y, sb, d, n_out)
+    assert (S == want).all()
+
+
+@pytest.mark.parametrize("v", fact_variants(), ids=lambda v: "v%d_G%d_bd%d_t%d" % (
+    v["index"], v["group"], v["dm_per_block"], v["tile"]))
+def test_factored_kernel_emulation_channel_boxes(v):
+    """A one-TAB plan, where consecutive channels are consecutive tensor
+    rows: the raw rows of 4 channels travel as one TMA box from the least of
+    their staged starts, each channel's data shifted in its slot by its
+    start's distance to that one, as the descriptors record."""
+    import paper_2205_12362_b300 as fdd
+    CC = 16 if 16 % v["group"] == 0 else 8
+    rng = np.random.default_rng(v["index"] + 7)
+    n_chan, n_out = 61, 300
+    f = synth.channel_freqs(n_chan)
+    n_dm = v["dm_per_block"] + 5
+    ranges = [dict(dm0=3.0, ddm=0.5, n_dm=n_dm, downsamp=1, widths=[1])]   # rows of at most 256 words
+    d = oracle.delays(f, T_SAMP, 3.0, 0.5, n_dm)
+    n_in = n_out + int(d.max()) + 3
+    x = rng.integers(0, 256, size=(1, n_chan, synth.padded_pitch(n_in)), dtype=np.int64).astype(np.uint8)
+    sb = np.zeros((1, n_chan), np.int16)
+    tb = fdd.fact_tables_host(1, n_chan, 1, f, T_SAMP, ranges, sb, 0, v["index"], CC)
+    if tb["Lw"] < 0 or int(tb["pd_idx"][..., 1].max()) * (tb["desc_ints"] // 4) > v["threads"]:
+        pytest.skip("layout the library refuses")
+    assert tb["box_rows"] == 4
+    S = emulate(x, n_in, sb, tb, v, CC, n_dm, n_out)
+    want = oracle.dedisperse(oracle.downsample(x, 1, n_in=n_in), sb, d, n_out)
     assert (S == want).all()
 
 
