@@ -266,9 +266,9 @@ int fdd_variant_info(int32_t variant, int32_t* bytes_per_sample, int32_t* dm_per
  * one raw slot's size, the pattern region and the two mbarriers, and the
  * number of pattern-row buffers (2: stage s + 1 is built into the other
  * buffer while stage s accumulates; the descriptor and offset tables then
- * hold the buffer's address), and in info[14] the channels per TMA copy (4:
- * the rows of 4 consecutive channels travel as one box of slot-size rows
- * from the box's least staged start, bbase [n_blk][ceil(n_chan / 4)], each
+ * hold the buffer's address), and in info[14] the channels per TMA copy R
+ * (8 or 4: the rows of R consecutive channels travel as one box of slot-size
+ * rows from the box's least staged start, bbase [n_blk][ceil(n_chan / R)], each
  * channel's data shifted by its start's distance to it, as the descriptors
  * record; 1: one copy per row).  Array arguments may be NULL (sizes first, then data): base
  * [n_blk][n_chan], goff [n_blk][n_groups][BD], pdesc [n_desc][desc_ints],

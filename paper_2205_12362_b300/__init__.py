@@ -608,7 +608,7 @@ def fact_tables_host(n_tab, n_chan, n_sb, chan_freq_mhz, t_samp_s, ranges, sb_ma
     out["pdesc"] = np.zeros((max(n_desc, 1), desc_ints), np.int32)
     out["pd_idx"] = np.zeros((n_blk, n_stages, 2), np.int32)
     out["delays"] = np.zeros((n_dm, n_chan), np.int32)
-    out["bbase"] = np.zeros((n_blk, (n_chan + 3) // 4), np.int32)
+    out["bbase"] = np.zeros((n_blk, (n_chan + out["box_rows"] - 1) // out["box_rows"]), np.int32)
     ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     _check(L.fdd_fact_tables_host(*args, ptr(out["base"]), ptr(out["goff"]), ptr(out["pdesc"]), ptr(out["pd_idx"]),
                                   ptr(out["delays"]), ptr(out["bbase"])), "fdd_fact_tables_host")

@@ -169,30 +169,42 @@ FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactV
     ft.Lw = static_cast<int32_t>(Lw);
     ft.pat_bytes = static_cast<int32_t>(align_up(static_cast<size_t>(pat_region), 16));
     ft.pat_bufs = v.PB;
-    // channel boxes: 4 consecutive channels per TMA copy, when their rows are consecutive in the tensor
-    // and a box row (the row plus the spread of the 4 starts) stays within one TMA box of 256 words
-    constexpr int kBoxRows = 4;
-    const int n_boxes4 = (n_chan + kBoxRows - 1) / kBoxRows;
-    std::vector<int32_t> bb(static_cast<size_t>(n_blk) * n_boxes4);
-    int64_t spread = 0;  // words
-    for (int b = 0; b < n_blk; b++)
-        for (int k = 0; k < n_boxes4; k++) {
-            int32_t lo = ft.base[static_cast<size_t>(b) * n_chan + k * kBoxRows];
-            for (int c = k * kBoxRows; c < std::min(n_chan, (k + 1) * kBoxRows); c++)
-                lo = std::min(lo, ft.base[static_cast<size_t>(b) * n_chan + c]);
-            bb[static_cast<size_t>(b) * n_boxes4 + k] = lo;
-            for (int c = k * kBoxRows; c < std::min(n_chan, (k + 1) * kBoxRows); c++)
-                spread = std::max<int64_t>(spread, (static_cast<int64_t>(ft.base[static_cast<size_t>(b) * n_chan + c]) - lo) *
-                                                       E / 4);
-        }
-    const int64_t rb4 = static_cast<int64_t>(align_up(static_cast<size_t>(4 * (Lw + spread)), 128));
-    const bool boxes = consecutive_rows && fdd::fact_boxes(static_cast<int>(Lw)) == 1 && rb4 / 4 <= 256 &&
-                       CC % kBoxRows == 0;
-    ft.box_rows = boxes ? kBoxRows : 1;
+    // channel boxes: R = 8 (else 4) consecutive channels per TMA copy, when their rows are consecutive
+    // in the tensor and a box row (the row plus the spread of the R starts) stays within one TMA box of
+    // 256 words; the wider R that fits wins (fewer copies per stage)
+    int kBoxRows = 1;
+    int n_boxes = n_chan;
+    std::vector<int32_t> bb;
+    int64_t rb_box = 0;
+    for (int R : {8, 4}) {
+        if (!consecutive_rows || fdd::fact_boxes(static_cast<int>(Lw)) != 1 || CC % R != 0) continue;
+        const int nbx = (n_chan + R - 1) / R;
+        std::vector<int32_t> bbr(static_cast<size_t>(n_blk) * nbx);
+        int64_t spread = 0;  // words
+        for (int b = 0; b < n_blk; b++)
+            for (int k = 0; k < nbx; k++) {
+                int32_t lo = ft.base[static_cast<size_t>(b) * n_chan + k * R];
+                for (int c = k * R; c < std::min(n_chan, (k + 1) * R); c++)
+                    lo = std::min(lo, ft.base[static_cast<size_t>(b) * n_chan + c]);
+                bbr[static_cast<size_t>(b) * nbx + k] = lo;
+                for (int c = k * R; c < std::min(n_chan, (k + 1) * R); c++)
+                    spread = std::max<int64_t>(
+                        spread, (static_cast<int64_t>(ft.base[static_cast<size_t>(b) * n_chan + c]) - lo) * E / 4);
+            }
+        const int64_t rbr = static_cast<int64_t>(align_up(static_cast<size_t>(4 * (Lw + spread)), 128));
+        if (rbr / 4 > 256) continue;
+        kBoxRows = R;
+        n_boxes = nbx;
+        bb.swap(bbr);
+        rb_box = rbr;
+        break;
+    }
+    const bool boxes = kBoxRows > 1;
+    ft.box_rows = kBoxRows;
     if (boxes) ft.bbase.swap(bb);
     // resolve shared-memory addresses
     ft.zero_off = 0;
-    ft.rb = boxes ? static_cast<int32_t>(rb4) : static_cast<int32_t>(align_up(static_cast<size_t>(4 * Lw), 128));
+    ft.rb = boxes ? static_cast<int32_t>(rb_box) : static_cast<int32_t>(align_up(static_cast<size_t>(4 * Lw), 128));
     ft.raw_off = static_cast<int32_t>(align_up(static_cast<size_t>(4 * Lw + 16), 128));
     ft.pat_off = ft.raw_off + 2 * CC * ft.rb;
     if (v.PB == 2) {
@@ -238,7 +250,7 @@ FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactV
                     const int b = desc_blk[di / ft.desc_ints];
                     const int c = desc_stage[di / ft.desc_ints] * CC + cc;
                     e += (ft.base[static_cast<size_t>(b) * n_chan + c] -
-                          ft.bbase[static_cast<size_t>(b) * n_boxes4 + c / kBoxRows]) * E;
+                          ft.bbase[static_cast<size_t>(b) * n_boxes + c / kBoxRows]) * E;
                 }
             }
         }

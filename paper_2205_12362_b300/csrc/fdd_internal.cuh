@@ -96,8 +96,8 @@ struct FactArgs {
     const int32_t* goff;        // [n_blk][n_groups][BD]
     const int32_t* pdesc;       // pattern-row descriptors
     const int32_t* pd_idx;      // [n_blk][n_stages][2]
-    const int32_t* bbase;       // [n_blk][ceil(n_chan / 4)] first staged sample of each 4-channel box
-    int32_t box_rows;           // channels per TMA copy: 4 (bbase used, rows of rb / 4 words) or 1
+    const int32_t* bbase;       // [n_blk][ceil(n_chan / box_rows)] first staged sample of each box
+    int32_t box_rows;           // channels per TMA copy: 8 or 4 (bbase used, rows of rb / 4 words) or 1
     int32_t* series;            // [n_sb][n_dm][n_out]
     unsigned long long* stat;   // [n_sb * n_dm][2]
     int32_t n_chan, n_dm, n_out, n_sb;

@@ -26,7 +26,7 @@ struct RangeState {
     int fact = -1;
     int32_t f_CC = 0, f_Lw = 0, f_pat_bytes = 0, f_n_stages = 0, f_n_groups = 0;
     int32_t f_zero_off = 0, f_raw_off = 0, f_rb = 0, f_pat_off = 0, f_bar_off = 0, f_desc_bytes = 0, f_box_rows = 1;
-    int32_t* d_fbbase = nullptr;      // [n_blk][n_boxes] first staged sample of each channel box
+    int32_t* d_fbbase = nullptr;      // [n_blk][ceil(n_chan / box_rows)] first staged sample of each box
     float f_work_ratio = 1.f;         // adds of the factored kernel per brute-force add
     size_t f_smem = 0;
     int32_t* d_fbase = nullptr;
@@ -149,10 +149,10 @@ int pick_cc(const DedispVariant& v, int Lw);
 
 struct FactTables {
     std::vector<int32_t> base, goff, pdesc, pd_idx;
-    // Raw rows travel as TMA boxes of box_rows consecutive channels (4 where the block's channels are
-    // consecutive tensor rows -- one TAB per block, or a one-TAB plan -- and the layout allows, else 1)
-    // of rb / 4 words: box k of DM block b starts at sample bbase[b][k], the least staged start of its
-    // channels, and each channel's row lands in its own slot, shifted by its start's distance to bbase.
+    // Raw rows travel as TMA boxes of box_rows consecutive channels (8 or 4 where the block's channels
+    // are consecutive tensor rows -- one TAB per block, or a one-TAB plan -- and the layout allows,
+    // else 1) of rb / 4 words: box k of DM block b starts at sample bbase[b][k], the least staged start
+    // of its channels, and each channel's row lands in its own slot, shifted by its start's distance.
     std::vector<int32_t> bbase;
     int32_t box_rows = 1;
     int32_t Lw = 0, pat_bytes = 0, n_groups = 0, n_stages = 0, desc_ints = 0;

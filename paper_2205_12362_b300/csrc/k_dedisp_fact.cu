@@ -242,19 +242,19 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
     // lane + 32; CC <= 64) a stage before fire(s) needs them, so the global
     // loads' latency is not in front of a barrier; fire(s) arms the buffer's
     // barrier with the stage's byte count (lane 0) and issues the copies.
-    // With 4-channel boxes (a.box_rows == 4) lane q < ceil(ncc / 4) copies channels 4q .. 4q + 3 of
-    // the stage as one box of rb / 4 words from the box's least start (bbase); their rows land in
+    // With channel boxes (R = a.box_rows > 1) lane q < ceil(ncc / R) copies channels R q .. R q + R - 1
+    // of the stage as one box of rb / 4 words from the box's least start (bbase); their rows land in
     // their own slots (the box row pitch is the slot size).
-    const int n_boxes4 = (a.n_chan + 3) >> 2;
-    const int32_t* bbase_blk = a.bbase + (int64_t)blk * n_boxes4;
+    const int R = a.box_rows;
+    const int32_t* bbase_blk = a.bbase + (int64_t)blk * ((a.n_chan + R - 1) / R);
     int cx[2] = {0, 0}, cy[2] = {0, 0};
     auto coords = [&](int s) {
         const int c0 = s * CC;
         const int ncc = min(CC, a.n_chan - c0);
-        if (a.box_rows == 4) {
-            if (4 * lane < ncc) {
-                const int c = c0 + 4 * lane;
-                cx[0] = ((t0 + bbase_blk[c >> 2]) * E) >> 2;
+        if (R > 1) {
+            if (R * lane < ncc) {
+                const int c = c0 + R * lane;
+                cx[0] = ((t0 + bbase_blk[c / R]) * E) >> 2;
                 cy[0] = (PART ? sb : sbm[c]) * a.n_chan + c;
             }
             return;
@@ -274,12 +274,12 @@ __global__ void __launch_bounds__(WARPS * 32, (WARPS <= 8) ? 2 : 1)
         const int ncc = min(CC, a.n_chan - c0);
         const uint32_t bar = s_bar + 8u * (s & 1);
         const uint32_t dst = s0 + static_cast<uint32_t>(a.raw_off + (s & 1) * CC * a.rb);
-        if (a.box_rows == 4) {
-            const int nbox = (ncc + 3) >> 2;
-            if (lane == 0) tma::mbar_expect_tx(bar, static_cast<uint32_t>(nbox) * 4u * static_cast<uint32_t>(a.rb));
+        if (R > 1) {
+            const int nbox = (ncc + R - 1) / R;
+            if (lane == 0)
+                tma::mbar_expect_tx(bar, static_cast<uint32_t>(nbox * R) * static_cast<uint32_t>(a.rb));
             __syncwarp();
-            if (lane < nbox)
-                tma::load_2d(dst + static_cast<uint32_t>(4 * lane * a.rb), &a.tmap, cx[0], cy[0], bar);
+            if (lane < nbox) tma::load_2d(dst + static_cast<uint32_t>(R * lane * a.rb), &a.tmap, cx[0], cy[0], bar);
             return;
         }
         if (lane == 0) tma::mbar_expect_tx(bar, static_cast<uint32_t>(ncc) * static_cast<uint32_t>(Lw) * 4u);
@@ -604,15 +604,16 @@ cudaError_t encode_fact_map(FactArgs& a, int64_t n_rows) {
     if (!enc) return cudaErrorNotSupported;
     const int64_t words = (a.n_valid * a.E + 3) / 4;
     if (a.Lw < 4 || a.Lw > kFactMaxLw || a.Lw % fact_lw_align(a.Lw) != 0 ||
-        (a.box_rows == 4 && (a.rb / 4 > 256 || a.rb % 128 != 0 || !a.bbase)) || (a.box_rows != 4 && a.box_rows != 1) ||
+        (a.box_rows > 1 && (a.rb / 4 > 256 || a.rb % 128 != 0 || !a.bbase || a.CC % a.box_rows != 0)) ||
+        (a.box_rows != 8 && a.box_rows != 4 && a.box_rows != 1) ||
         (reinterpret_cast<uintptr_t>(a.in) & 15u) != 0 || a.pitch_bytes % 16 != 0 || words * 4 > a.pitch_bytes ||
         n_rows < 1)
         return cudaErrorInvalidValue;
     const cuuint64_t dims[2] = {static_cast<cuuint64_t>(words), static_cast<cuuint64_t>(n_rows)};
     const cuuint64_t strides[1] = {static_cast<cuuint64_t>(a.pitch_bytes)};
-    // a box of 4 channel rows of rb / 4 words, or one row's piece of Lw / fact_boxes(Lw) words
-    const cuuint32_t box[2] = {static_cast<cuuint32_t>(a.box_rows == 4 ? a.rb / 4 : a.Lw / fact_boxes(a.Lw)),
-                               static_cast<cuuint32_t>(a.box_rows == 4 ? 4 : 1)};
+    // a box of box_rows channel rows of rb / 4 words, or one row's piece of Lw / fact_boxes(Lw) words
+    const cuuint32_t box[2] = {static_cast<cuuint32_t>(a.box_rows > 1 ? a.rb / 4 : a.Lw / fact_boxes(a.Lw)),
+                               static_cast<cuuint32_t>(a.box_rows)};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = enc(&a.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint8_t*>(a.in), dims, strides, box,
                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

@@ -91,7 +91,7 @@ def emulate(x, n_valid, sb_map, tb, v, CC, n_dm, n_out, E=1):
         if addr < zero_hi:
             return zero_lo, zero_hi
         k = (addr - raw_lo) // rb
-        return raw_lo + k * rb, raw_lo + k * rb + (rb if tb["box_rows"] == 4 else 4 * Lw)
+        return raw_lo + k * rb, raw_lo + k * rb + (rb if tb["box_rows"] > 1 else 4 * Lw)
     n_sb = sb_map.shape[0]
     S = np.zeros((n_sb, n_dm, n_out), np.int64)
     lanes = np.arange(32)
@@ -108,9 +108,9 @@ def emulate(x, n_valid, sb_map, tb, v, CC, n_dm, n_out, E=1):
                     c0 = s * CC
                     for cc in range(min(CC, n_chan - c0)):   # raw staging (the TMA box of stage s)
                         c = c0 + cc
-                        if tb["box_rows"] == 4:
-                            # the channel's row arrives in its 4-channel box: rb bytes from the box's start
-                            start = (t0 + tb["bbase"][blk, c // 4]) * E
+                        if tb["box_rows"] > 1:
+                            # the channel's row arrives in its channel box: rb bytes from the box's start
+                            start = (t0 + tb["bbase"][blk, c // tb["box_rows"]]) * E
                             width = rb
                         else:
                             start = (t0 + tb["base"][blk, c]) * E  # byte of the row's first staged sample
@@ -269,9 +269,9 @@ def test_factored_kernel_emulation_16bit(v, D):
     v["index"], v["group"], v["dm_per_block"], v["tile"]))
 def test_factored_kernel_emulation_channel_boxes(v):
     """A one-TAB plan, where consecutive channels are consecutive tensor
-    rows: the raw rows of 4 channels travel as one TMA box from the least of
-    their staged starts, each channel's data shifted in its slot by its
-    start's distance to that one, as the descriptors record."""
+    rows: the raw rows of 8 (or 4) channels travel as one TMA box from the
+    least of their staged starts, each channel's data shifted in its slot by
+    its start's distance to that one, as the descriptors record."""
     import paper_2205_12362_b300 as fdd
     CC = 16 if 16 % v["group"] == 0 else 8
     rng = np.random.default_rng(v["index"] + 7)
@@ -286,7 +286,7 @@ def test_factored_kernel_emulation_channel_boxes(v):
     tb = fdd.fact_tables_host(1, n_chan, 1, f, T_SAMP, ranges, sb, 0, v["index"], CC)
     if tb["Lw"] < 0 or int(tb["pd_idx"][..., 1].max()) * (tb["desc_ints"] // 4) > v["threads"]:
         pytest.skip("layout the library refuses")
-    assert tb["box_rows"] == 4
+    assert tb["box_rows"] in (4, 8)
     S = emulate(x, n_in, sb, tb, v, CC, n_dm, n_out)
     want = oracle.dedisperse(oracle.downsample(x, 1, n_in=n_in), sb, d, n_out)
     assert (S == want).all()
