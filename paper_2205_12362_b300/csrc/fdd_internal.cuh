@@ -11,6 +11,12 @@
 
 namespace fdd {
 
+// Raise a kernel's dynamic shared-memory limit to at least smem bytes; never lowers it.  One kernel
+// launched with different sizes (one instantiation serves several DM ranges) keeps a limit that covers
+// every size asked so far, so a CUDA graph node captured with a larger request than a later launch's
+// still passes the launch check when it is launched again on its own.
+cudaError_t allow_dynamic_smem(const void* fn, size_t smem);
+
 // ---------------------------------------------------------------------------
 // Dedispersion kernel variants (template instantiations of k_dedisp).
 //   E     bytes per input sample: 1 = raw uint8 filterbank, 2 = uint16 sums

@@ -275,8 +275,7 @@ const PersistentVariant& persistent_variant(int idx) { return kPEntries[idx].v; 
 
 cudaError_t persistent_occupancy(int idx, int E, size_t smem, int* blocks_per_sm) {
     const PEntry& e = kPEntries[idx];
-    cudaError_t err =
-        cudaFuncSetAttribute(e.fn[E - 1], cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t err = allow_dynamic_smem(reinterpret_cast<const void*>(e.fn[E - 1]), smem);
     if (err != cudaSuccess) return err;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, e.fn[E - 1], e.v.threads(), smem);
 }
@@ -329,8 +328,7 @@ cudaError_t launch_batch_downsample(const BatchParams& p, cudaStream_t s) {
 
 cudaError_t launch_dedisp_persistent(int idx, int E, const BatchParams& p, int grid, size_t smem, cudaStream_t s) {
     const PEntry& e = kPEntries[idx];
-    cudaError_t err =
-        cudaFuncSetAttribute(e.fn[E - 1], cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t err = allow_dynamic_smem(reinterpret_cast<const void*>(e.fn[E - 1]), smem);
     if (err != cudaSuccess) return err;
     e.fn[E - 1]<<<grid, e.v.threads(), smem, s>>>(p);
     return cudaGetLastError();

@@ -1,6 +1,8 @@
 // k_dedisp.cu -- per-range dedispersion launches: one grid per DM range,
 // (time tiles x DM blocks x SBs), each block running one dedisp_tile (see
 // dedisp_tile.cuh for the algorithm), and the table of compiled variants.
+#include <mutex>
+
 #include "dedisp_tile.cuh"
 
 namespace fdd {
@@ -56,11 +58,20 @@ bool dedisp_cc_ok(const DedispVariant& v, int Lw, int CC, size_t smem_budget) {
     return dedisp_smem_bytes(v, Lw, CC) <= smem_budget;
 }
 
+cudaError_t allow_dynamic_smem(const void* fn, size_t smem) {
+    static std::mutex mu;  // read and raise as one step when several host threads launch
+    std::lock_guard<std::mutex> lock(mu);
+    cudaFuncAttributes fa;
+    cudaError_t err = cudaFuncGetAttributes(&fa, fn);
+    if (err != cudaSuccess) return err;
+    if (smem <= static_cast<size_t>(fa.maxDynamicSharedSizeBytes)) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+}
+
 cudaError_t launch_dedisp(int variant, const DedispArgs& a, cudaStream_t s) {
     const Entry& e = kEntries[variant];
     const size_t smem = dedisp_smem_bytes(e.v, a.Lw, a.CC);
-    cudaError_t err = cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(smem));
+    cudaError_t err = allow_dynamic_smem(reinterpret_cast<const void*>(e.fn), smem);
     if (err != cudaSuccess) return err;
     const int T = e.v.tile(), BD = e.v.bd();
     dim3 grid((a.n_out + T - 1) / T, (a.n_dm + BD - 1) / BD, a.n_sb);

@@ -630,7 +630,7 @@ cudaError_t launch_dedisp_fact(int variant, const FactArgs& a, size_t smem, cuda
     if (!fact_has_width(variant, a.E, false)) return cudaErrorInvalidValue;
     const FEntry& e = kFEntries[variant];
     const FactFn fn = e.fn[a.E - 1];
-    cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t err = allow_dynamic_smem(reinterpret_cast<const void*>(fn), smem);
     if (err != cudaSuccess) return err;
     const int T = e.v.tile(), BD = e.v.bd();
     dim3 grid((a.n_out + T - 1) / T, (a.n_dm + BD - 1) / BD, a.n_sb);
@@ -644,7 +644,7 @@ cudaError_t launch_sbf_part_fact(int variant, const FactArgs& a, size_t smem, in
     const FactFn fn = e.part[a.E - 1];
     const int T = e.v.tile(), BD = e.v.bd();
     if (a.i0 % BD != 0 || a.n_slab <= 0 || !a.P || !a.sseg) return cudaErrorInvalidValue;
-    cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t err = allow_dynamic_smem(reinterpret_cast<const void*>(fn), smem);
     if (err != cudaSuccess) return err;
     dim3 grid((a.n_out + T - 1) / T, (a.n_slab + BD - 1) / BD, n_tab);
     fn<<<grid, e.v.threads(), smem, s>>>(a);

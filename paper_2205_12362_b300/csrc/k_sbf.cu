@@ -253,7 +253,7 @@ cudaError_t launch_sbf_part(int idx, const SbfPartArgs& a, int n_tab, cudaStream
     const Entry& e = kEntries[idx];
     if (!e.fn) return cudaErrorInvalidValue;  // pattern-factored parts launch through launch_sbf_part_fact
     const size_t smem = sbf_smem_bytes(e.v, a.Lw, a.CC);
-    cudaError_t err = cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t err = allow_dynamic_smem(reinterpret_cast<const void*>(e.fn), smem);
     if (err != cudaSuccess) return err;
     const int T = e.v.tile(), BD = e.v.bd();
     dim3 grid((a.n_out + T - 1) / T, (a.n_slab + BD - 1) / BD, n_tab);
@@ -304,8 +304,7 @@ cudaError_t launch_sbf_comb(const SbfCombArgs& a, cudaStream_t s) {
     const int per_block = CW * CSB;
     const int n_valid = a.n_dm - a.i0 < a.n_slab ? a.n_dm - a.i0 : a.n_slab;
     const size_t smem = sbf_comb_smem_bytes(a.n_tab);
-    cudaError_t err = cudaFuncSetAttribute(k_sbf_comb, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(smem));
+    cudaError_t err = allow_dynamic_smem(reinterpret_cast<const void*>(k_sbf_comb), smem);
     if (err != cudaSuccess) return err;
     dim3 grid((a.n_out + CT - 1) / CT, n_valid, (a.n_sb + per_block - 1) / per_block);
     k_sbf_comb<<<grid, CW * 32, smem, s>>>(a);

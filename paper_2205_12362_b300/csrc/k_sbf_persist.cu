@@ -361,15 +361,13 @@ size_t sbf_persist_smem_bytes(size_t part_smem_max, int n_tab) {
 }
 
 cudaError_t sbf_persist_occupancy(size_t smem, int* blocks_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(k_sbf_persist, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(k_sbf_persist), smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_sbf_persist, PW * 32, smem);
 }
 
 cudaError_t launch_sbf_persist(const BatchParams& p, int grid, size_t smem, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_sbf_persist, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(k_sbf_persist), smem);
     if (e != cudaSuccess) return e;
     k_sbf_persist<<<grid, PW * 32, smem, s>>>(p);
     return cudaGetLastError();
