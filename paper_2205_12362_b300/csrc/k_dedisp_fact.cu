@@ -562,6 +562,10 @@ struct FEntry {
      {k_dedisp_fact<G, NW, DPW, WARPS, 1, true, 1>, k_dedisp_fact<G, NW, DPW, WARPS, 1, true, 2>}}
 #define FDD_F2(G, NW, DPW, WARPS) \
     {{G, NW, DPW, WARPS, 2}, {k_dedisp_fact<G, NW, DPW, WARPS, 2, false, 1>, nullptr}, {nullptr, nullptr}}
+#define FDD_F2P(G, NW, DPW, WARPS)                                                                             \
+    {{G, NW, DPW, WARPS, 2},                                                                                   \
+     {k_dedisp_fact<G, NW, DPW, WARPS, 2, false, 1>, nullptr},                                                \
+     {k_dedisp_fact<G, NW, DPW, WARPS, 2, true, 1>, k_dedisp_fact<G, NW, DPW, WARPS, 2, true, 2>}}
 const FEntry kFEntries[] = {
     FDD_FP(8, 4, 4, 16),  // G 8, BD 64, T 256, 512 threads
     FDD_F(8, 4, 2, 16),  // G 8, BD 32, T 256
@@ -572,13 +576,14 @@ const FEntry kFEntries[] = {
     FDD_F(4, 2, 8, 8),   // G 4, BD 64, T 128, 256 threads (two blocks per SM)
     FDD_FP(4, 4, 4, 8),   // G 4, BD 32, T 256, 256 threads
     FDD_F2(4, 4, 4, 16),  // two pattern-row buffers: G 4, BD 64, T 256, 512 threads
-    FDD_F2(4, 4, 4, 8),   // two pattern-row buffers: G 4, BD 32, T 256, 256 threads
+    FDD_F2P(4, 4, 4, 8),  // two pattern-row buffers: G 4, BD 32, T 256, 256 threads (also in part mode)
     FDD_F2(8, 4, 4, 16),  // two pattern-row buffers: G 8, BD 64, T 256, 512 threads
     FDD_F(4, 3, 4, 16),  // G 4, BD 64, T 192: pattern rows of ~53 units fill 2 warp steps (83 % of lanes)
 };
 #undef FDD_F
 #undef FDD_FP
 #undef FDD_F2
+#undef FDD_F2P
 
 }  // namespace
 

@@ -225,6 +225,8 @@ const Entry kEntries[] = {
     FDD_SF2(4, 4, 16, 2),   // pattern-factored part of 16-bit (downsampled) rows, G 4, BD 64, T 256
     FDD_SF2(4, 4, 16, 0),   // the same with G 8
     FDD_SF2(4, 4, 8, 7),    // the same, G 4, BD 32, 256 threads
+    FDD_SF(4, 4, 8, 9),     // pattern-factored part with two pattern-row buffers (one barrier per
+    FDD_SF2(4, 4, 8, 9),    // stage), G 4, BD 32, 256 threads: 8-bit and 16-bit rows
 };
 #undef FDD_S
 #undef FDD_SF
