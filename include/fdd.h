@@ -147,7 +147,10 @@ int fdd_plan_delays(const fdd_plan* plan, int32_t r, int32_t* dst);
 /* Bytes of device workspace a search of (n_in, n_out) needs (library
  * bookkeeping; no counterpart in the paper).
  * If the caller passes d_series to fdd_search, the series live there and the
- * workspace shrinks by fdd_series_size(). */
+ * workspace shrinks by fdd_series_size().  For plans with two or more SBs and
+ * DM ranges the size holds two lanes of SB-factored partial-sum scratch, which
+ * a batched search runs concurrently (fdd_search_batch); a plain search uses
+ * one of them. */
 int fdd_workspace_size(const fdd_plan* plan, int64_t n_in, int64_t n_out, int32_t with_series,
                        size_t* bytes);
 
@@ -344,7 +347,13 @@ int fdd_batch_prepare(fdd_plan* plan, int64_t n_out, int32_t variant);
  * downsampled ranges -- and one boxcar/threshold launch.  Results per job are
  * identical to fdd_search on that job alone.  Prepares on first use of an
  * n_out (not allowed while the stream is capturing).  Batched searches of
- * one plan must not overlap on the GPU (they share the work counter). */
+ * one plan must not overlap on the GPU (they share the work counter).
+ * In SB-factored mode the part / combine launches of the range with the most
+ * trial-samples run on one library-owned side stream and those of the other
+ * ranges on a second (a pair per caller stream, created on first use and
+ * freed with the plan), forked from and joined back into `stream` before the
+ * boxcar launch: `stream` still orders the whole search, and a CUDA graph
+ * captured from it holds the two branches. */
 int fdd_search_batch(fdd_plan* plan, const fdd_job* jobs, int32_t n_jobs, int64_t n_out, fdd_stream_t stream);
 
 /* Time every persistent variant on these jobs (`reps` batches each) and, for

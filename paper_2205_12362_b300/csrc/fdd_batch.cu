@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -20,6 +21,46 @@
 using namespace fdd::host;
 
 namespace {
+
+// Side streams of a plan's batched searches (freed with the plan, not on a re-prepare).
+void free_lanes(BatchState& b) {
+    for (LanePair& lp : b.lanes) {
+        for (cudaStream_t st : lp.st)
+            if (st) cudaStreamDestroy(st);
+        for (cudaEvent_t ev : lp.ev)
+            if (ev) cudaEventDestroy(ev);
+    }
+    b.lanes.clear();
+}
+
+std::mutex g_lanes_mu;  // guards BatchState::lanes (caller streams may enqueue from several host threads)
+
+// The side-stream pair of caller stream s (copied to *out), created on first use; false if it cannot be
+// created (the launches then stay on s, which is correct: the lanes' scratch regions are disjoint).
+bool lanes_for(fdd_plan* p, cudaStream_t s, LanePair* out) {
+    std::lock_guard<std::mutex> lock(g_lanes_mu);
+    for (const LanePair& lp : p->batch.lanes)
+        if (lp.caller == s) {
+            *out = lp;
+            return true;
+        }
+    LanePair lp;
+    lp.caller = s;
+    bool ok = true;
+    for (cudaStream_t& st : lp.st) ok = ok && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+    for (cudaEvent_t& ev : lp.ev) ok = ok && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        for (cudaStream_t st : lp.st)
+            if (st) cudaStreamDestroy(st);
+        for (cudaEvent_t ev : lp.ev)
+            if (ev) cudaEventDestroy(ev);
+        cudaGetLastError();
+        return false;
+    }
+    p->batch.lanes.push_back(lp);
+    *out = lp;
+    return true;
+}
 
 void free_batch(BatchState& b) {
     for (BatchRangeTables& t : b.tables) {
@@ -74,7 +115,7 @@ int prepare_sb_persistent(fdd_plan* p, int64_t n_out, bool absolute, const Layou
     // every range's slab buffers sit at the same kSbfSlots offsets of the scratch (slot k starts at
     // k * slot_elems elements, 1 KB aligned), so a range's layout never reaches into a slot another
     // range's group is still using
-    const int64_t slot_elems = static_cast<int64_t>(L.sbf_bytes) / 2 / fdd::kSbfSlots / 512 * 512;
+    const int64_t slot_elems = static_cast<int64_t>(L.sbf_lane_bytes) / 2 / fdd::kSbfSlots / 512 * 512;
     const int comb_sbs = fdd::sbf_persist_comb_sbs();
     const int comb_tile = fdd::sbf_persist_comb_tile();
     for (size_t ri = 0; ri < p->ranges.size(); ri++) {
@@ -305,6 +346,7 @@ struct SbfJobRange {
     uint8_t* scratch;
     size_t scratch_bytes;
     int range;
+    int lane;  // 0: the caller's stream's first side stream (the heaviest range), 1: the second
 };
 
 struct BatchLaunch {
@@ -373,6 +415,12 @@ int fill_params(const fdd_plan* p, const fdd_job* jobs, int32_t n_jobs, int64_t 
         for (size_t k = 0; k < bins.ds_phase.size(); k++) B.ds_phase[k] = bins.ds_phase[k];
         B.sbf_scratch = b.sbp ? reinterpret_cast<uint16_t*>(ws + L.sbf) : nullptr;
         if (!b.sbf) continue;
+        // lanes: the range with the most trial-samples in lane 0, the others in lane 1
+        size_t heavy = 0;
+        for (size_t ri = 1; ri < p->ranges.size(); ri++)
+            if (static_cast<int64_t>(p->ranges[ri].n_dm) * b.h_ranges[ri].n_out >
+                static_cast<int64_t>(p->ranges[heavy].n_dm) * b.h_ranges[heavy].n_out)
+                heavy = ri;
         for (size_t ri = 0; ri < p->ranges.size(); ri++) {
             const RangeState& r = p->ranges[ri];
             const fdd::BatchRange& R = b.h_ranges[ri];
@@ -389,8 +437,9 @@ int fill_params(const fdd_plan* p, const fdd_job* jobs, int32_t n_jobs, int64_t 
             q.a.n_out = R.n_out;
             q.a.n_emit = bins.emit[ri];
             q.a.n_sb = p->n_sb;
-            q.scratch = ws + L.sbf;
-            q.scratch_bytes = L.sbf_bytes;
+            q.lane = L.sbf_lanes > 1 && ri != heavy ? 1 : 0;
+            q.scratch = ws + L.sbf + static_cast<size_t>(q.lane) * L.sbf_lane_bytes;
+            q.scratch_bytes = L.sbf_lane_bytes;
             BL.sbf.push_back(q);
         }
     }
@@ -426,10 +475,28 @@ int enqueue(fdd_plan* p, const BatchLaunch& BL, cudaStream_t s) {
     }
     if (!BL.sbf.empty()) {
         if ((e = stage_begin(p, 1, -1, s)) != cudaSuccess) return cuda_fail(e, "timing event");
+        // two lanes: fork onto the caller stream's side streams, lane by lane in order, then join
+        bool two = false;
+        for (const SbfJobRange& q : BL.sbf) two = two || q.lane == 1;
+        LanePair lanes;
+        const LanePair* lp = two && lanes_for(p, s, &lanes) ? &lanes : nullptr;
+        if (lp) {
+            if ((e = cudaEventRecord(lp->ev[0], s)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(lp->st[0], lp->ev[0], 0)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(lp->st[1], lp->ev[0], 0)) != cudaSuccess)
+                return cuda_fail(e, "lane fork");
+        }
         for (const SbfJobRange& q : BL.sbf)
-            if ((e = launch_range_sbf(p, p->ranges[q.range], q.a, q.scratch, q.scratch_bytes, s, &n_launch)) !=
-                cudaSuccess)
+            if ((e = launch_range_sbf(p, p->ranges[q.range], q.a, q.scratch, q.scratch_bytes, lp ? lp->st[q.lane] : s,
+                                      &n_launch)) != cudaSuccess)
                 return cuda_fail(e, "SB-factored dedispersion launch");
+        if (lp) {
+            if ((e = cudaEventRecord(lp->ev[1], lp->st[0])) != cudaSuccess ||
+                (e = cudaEventRecord(lp->ev[2], lp->st[1])) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(s, lp->ev[1], 0)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(s, lp->ev[2], 0)) != cudaSuccess)
+                return cuda_fail(e, "lane join");
+        }
         if ((e = stage_end(p, s)) != cudaSuccess) return cuda_fail(e, "timing event");
     }
     for (int E = 1; E <= 2; E++) {
@@ -462,6 +529,8 @@ struct fdd_graph {
 namespace {
 
 int capture(fdd_graph* g, const BatchLaunch& P, cudaGraph_t* out) {
+    LanePair lanes;
+    if (g->plan->batch.sbf) lanes_for(g->plan, g->cap_stream, &lanes);  // side streams exist before capture
     cudaError_t e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
     // Events recorded under capture only order nodes; they carry no timestamps,
@@ -757,6 +826,7 @@ int fdd::host::batch_prepare_mode(fdd_plan* plan, int64_t n_out, bool absolute) 
 }
 
 void fdd_free_batch_state(fdd_plan* plan) {
+    free_lanes(plan->batch);
     free_batch(plan->batch);
     if (plan->batch.d_counter) cudaFree(plan->batch.d_counter);
     plan->batch.d_counter = nullptr;

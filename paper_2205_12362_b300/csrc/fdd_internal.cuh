@@ -17,6 +17,10 @@ namespace fdd {
 // still passes the launch check when it is launched again on its own.
 cudaError_t allow_dynamic_smem(const void* fn, size_t smem);
 
+// Workspace bytes of a plain (not batched) search: fdd_workspace_size without the second lane of
+// SB-factored scratch that batched searches use.
+size_t plain_workspace_bytes(const fdd_plan* plan, int64_t n_in, int64_t n_out, bool with_series);
+
 // ---------------------------------------------------------------------------
 // Dedispersion kernel variants (template instantiations of k_dedisp).
 //   E     bytes per input sample: 1 = raw uint8 filterbank, 2 = uint16 sums

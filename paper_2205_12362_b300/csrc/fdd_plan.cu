@@ -154,8 +154,14 @@ int64_t fdd::host::window_input_len(const fdd_plan* p, int64_t n_out) {
     return n_out + extra;
 }
 
+int fdd::host::sbf_lanes(const fdd_plan* p) { return p->n_sb >= 2 && p->ranges.size() >= 2 ? 2 : 1; }
+
+size_t fdd::plain_workspace_bytes(const fdd_plan* plan, int64_t n_in, int64_t n_out, bool with_series) {
+    return fdd::host::make_layout(plan, n_in, n_out, with_series, false, 1).total;
+}
+
 fdd::host::Layout fdd::host::make_layout(const fdd_plan* p, int64_t n_in, int64_t n_out, bool with_series,
-                                         bool absolute) {
+                                         bool absolute, int lanes) {
     Layout L;
     size_t series_elems = 0, n_series = 0;
     for (const RangeState& r : p->ranges) {
@@ -172,7 +178,9 @@ fdd::host::Layout fdd::host::make_layout(const fdd_plan* p, int64_t n_in, int64_
     const int64_t n_rows = absolute ? n_out + (p->ds_factors.empty() ? 0 : *std::max_element(p->ds_factors.begin(),
                                                                                                p->ds_factors.end()) - 1)
                                     : n_out;
-    L.sbf_bytes = std::max(sbf_scratch_bytes(p, n_rows), subband_scratch_bytes(p, n_rows));
+    L.sbf_lane_bytes = align_up(std::max(sbf_scratch_bytes(p, n_rows), subband_scratch_bytes(p, n_rows)), 256);
+    L.sbf_lanes = lanes > 0 ? lanes : sbf_lanes(p);
+    L.sbf_bytes = L.sbf_lane_bytes * static_cast<size_t>(L.sbf_lanes);
     if (L.sbf_bytes) {
         L.sbf = cur;
         cur = align_up(cur + L.sbf_bytes, 256);
@@ -372,8 +380,8 @@ int range_variant_index(const RangeState& r) {
 // Dedispersion of one range with whichever kernel it is configured for.
 cudaError_t launch_range(const fdd_plan* p, const RangeState& r, const fdd::DedispArgs& a, const Layout& L,
                          uint8_t* ws, cudaStream_t s, int64_t* launches = nullptr) {
-    if (r.sub_G > 0) return launch_range_subband(p, r, a, ws + L.sbf, L.sbf_bytes, s, launches);
-    if (r.sbf >= 0) return launch_range_sbf(p, r, a, ws + L.sbf, L.sbf_bytes, s, launches);
+    if (r.sub_G > 0) return launch_range_subband(p, r, a, ws + L.sbf, L.sbf_lane_bytes, s, launches);
+    if (r.sbf >= 0) return launch_range_sbf(p, r, a, ws + L.sbf, L.sbf_lane_bytes, s, launches);
     if (launches) *launches += 1;
     return launch_range_dedisp(p, r, a, s);
 }
@@ -528,7 +536,7 @@ int fdd::host::search_impl(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, 
         if (rc != FDD_OK) return rc;
     }
     const bool own_series = (d_series == nullptr);
-    const Layout L = make_layout(plan, n_in, n_out, own_series, absolute);
+    const Layout L = make_layout(plan, n_in, n_out, own_series, absolute, 1);  // one scratch lane
     if (workspace_bytes < L.total) return fail(FDD_ERR_WORKSPACE, "workspace smaller than fdd_workspace_size()");
 
     uint8_t* ws = static_cast<uint8_t*>(d_workspace);
@@ -856,7 +864,7 @@ int fdd_plan_autotune(fdd_plan* plan, const uint8_t* d_tabs, int64_t n_in, int64
         if (rc != FDD_OK) return rc;
     }
     if (reps < 1) reps = 1;
-    const Layout L = make_layout(plan, n_in, n_out, true);
+    const Layout L = make_layout(plan, n_in, n_out, true, false, 1);  // plain searches: one scratch lane
     const Bins bins = search_bins(plan, n_out, 0, false);
     if (workspace_bytes < L.total) return fail(FDD_ERR_WORKSPACE, "workspace smaller than fdd_workspace_size()");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -71,6 +71,14 @@ struct BatchRangeTables {
     int32_t* d_base = nullptr;
 };
 
+// Two side streams and their fork / join events for one caller stream of batched searches (a
+// caller stream gets its own pair, so batches enqueued on different streams stay independent).
+struct LanePair {
+    cudaStream_t caller = nullptr;
+    cudaStream_t st[2] = {nullptr, nullptr};
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // fork (on the caller), join of lane 0, join of lane 1
+};
+
 struct BatchState {
     int variant = -1;                      // persistent kernel variant
     bool sbf = false;                      // every range through its SB-factored configuration instead
@@ -95,6 +103,7 @@ struct BatchState {
     int grid_e[2] = {0, 0};                // resident blocks of each persistent launch
     size_t smem_e[2] = {0, 0};
     float tuned_ms = 0.f;
+    std::vector<LanePair> lanes;           // per caller stream, created on first use, freed with the plan
 };
 
 struct fdd_plan {
@@ -168,7 +177,9 @@ FactTables build_fact_tables(const fdd_plan* p, const RangeState& r, const FactV
                              bool consecutive_rows);
 
 struct Layout {
-    size_t sbf = 0, sbf_bytes = 0;  // scratch of the SB-factored kernel's partial sums
+    size_t sbf = 0, sbf_bytes = 0;  // scratch of the SB-factored kernel's partial sums (every lane)
+    size_t sbf_lane_bytes = 0;      // one lane of it (lane k starts at sbf + k * sbf_lane_bytes)
+    int sbf_lanes = 1;
     size_t series = 0, series_bytes = 0;
     size_t stat = 0, stat_bytes = 0;
     std::vector<size_t> series_r;   // element offset of range r inside the series buffer
@@ -180,7 +191,12 @@ struct Layout {
 // Series rows are floor(n_out / D_r) long (bins from input sample 0), or
 // ceil(n_out / D_r) in a window whose bins are aligned to its stream
 // (`absolute`), which holds one bin more when its phase allows.
-Layout make_layout(const fdd_plan* p, int64_t n_in, int64_t n_out, bool with_series, bool absolute = false);
+// Lanes of the SB-factored scratch: a batched search runs its heaviest range in lane 0 and the other
+// ranges in lane 1 on a second stream, at the same time (2 lanes for plans with two or more ranges and
+// SBs); plain searches use lane 0 only.  lanes = 0: sbf_lanes(p).
+int sbf_lanes(const fdd_plan* p);
+Layout make_layout(const fdd_plan* p, int64_t n_in, int64_t n_out, bool with_series, bool absolute = false,
+                   int lanes = 0);
 
 // Downsampling bins of one search (Sec. "Downsampling").  Plain: bins from
 // input sample 0, floor(n_out / D) outputs per range.  Absolute: input sample

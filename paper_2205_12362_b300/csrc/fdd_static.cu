@@ -30,9 +30,8 @@ extern "C" int fdd_search_static(fdd_plan* plan, const uint8_t* d_tabs, int64_t 
         fdd::set_last_error("fdd_search_static: disable stage timing (fdd_plan_set_timing(plan, 0)) first");
         return FDD_ERR_INVALID_ARG;
     }
-    size_t need = 0;
-    int rc = fdd_workspace_size(plan, n_in, n_out, d_series == nullptr, &need);
-    if (rc != FDD_OK) return rc;
+    if (n_in < 0 || n_out < 0) return FDD_ERR_INVALID_ARG;
+    const size_t need = fdd::plain_workspace_bytes(plan, n_in, n_out, d_series == nullptr);
     if (need > FDD_STATIC_SCRATCH_BYTES) {
         fdd::set_last_error("fdd_search_static: this search needs " + std::to_string(need) +
                             " bytes of scratch, more than the static array's " +

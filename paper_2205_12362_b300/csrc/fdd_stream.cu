@@ -89,7 +89,7 @@ int fdd_stream_open(fdd_plan* plan, int32_t beam_id, int64_t chunk_len, int64_t 
     st->n_in = window_input_len(plan, chunk_len);
     st->buf_len = (st->n_in + chunk_len - 1) / chunk_len * chunk_len;
     st->pitch = static_cast<int64_t>(align_up(static_cast<size_t>(st->buf_len), 16));
-    st->ws_bytes = make_layout(plan, st->n_in, chunk_len, true, true).total;
+    st->ws_bytes = make_layout(plan, st->n_in, chunk_len, true, true, 1).total;  // plain window searches
     const size_t buf_bytes = static_cast<size_t>(st->rows) * st->pitch;
     cudaError_t e;
     for (uint8_t*& b : st->buf)
