@@ -62,6 +62,21 @@ bool lanes_for(fdd_plan* p, cudaStream_t s, LanePair* out) {
     return true;
 }
 
+// Free the side-stream pair of caller stream s, if any (a graph's capture stream, when the graph goes).
+void release_lanes(fdd_plan* p, cudaStream_t s) {
+    std::lock_guard<std::mutex> lock(g_lanes_mu);
+    std::vector<LanePair>& v = p->batch.lanes;
+    for (size_t k = 0; k < v.size(); k++)
+        if (v[k].caller == s) {
+            for (cudaStream_t st : v[k].st)
+                if (st) cudaStreamDestroy(st);
+            for (cudaEvent_t ev : v[k].ev)
+                if (ev) cudaEventDestroy(ev);
+            v.erase(v.begin() + static_cast<std::ptrdiff_t>(k));
+            return;
+        }
+}
+
 void free_batch(BatchState& b) {
     for (BatchRangeTables& t : b.tables) {
         if (t.d_off) cudaFree(t.d_off);
@@ -813,7 +828,10 @@ int fdd_graph_destroy(fdd_graph* g) {
     if (!g) return FDD_OK;
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
-    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    if (g->cap_stream) {
+        if (g->plan) release_lanes(g->plan, g->cap_stream);  // the plan outlives its graphs
+        cudaStreamDestroy(g->cap_stream);
+    }
     delete g;
     return FDD_OK;
 }
