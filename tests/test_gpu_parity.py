@@ -443,6 +443,48 @@ def test_batch_graph_and_update(fdd, variant):
     g.close()
 
 
+def test_sb_factored_batches_on_two_streams(fdd):
+    """SB-factored batches of one four-range plan run their ranges on two forked stream lanes (a
+    side-stream pair per caller stream): two batches enqueued back to back on two different streams,
+    with no synchronisation between them, each equal the single searches of their jobs; graphs
+    created and destroyed repeatedly (each frees its capture stream's lanes) keep giving the same
+    results."""
+    import torch
+    cases = [batch_case(s, 0) for s in (5, 6, 7, 8)]
+    x0, f, ranges, sb, n_in, n_out = cases[0]
+    plan = fdd.Plan(x0.shape[0], x0.shape[1], sb.shape[0], f, T_SAMP, ranges, 5.0, sb)
+    plan.batch_prepare(n_out, fdd.FDD_BATCH_SB_FACTORED)
+    dxs = [to_dev(c[0]) for c in cases]
+    ref = [plan.search(dx, c[4], n_out, t_offset=11 * k, want_series=True)
+           for k, (dx, c) in enumerate(zip(dxs, cases))]
+    torch.cuda.synchronize()
+    jobs = [plan.make_job(dx, c[4], n_out, t_offset=11 * k, want_series=True)
+            for k, (dx, c) in enumerate(zip(dxs, cases))]
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    for _ in range(2):
+        for j in jobs:
+            j.series.fill_(-1)
+        torch.cuda.synchronize()
+        plan.search_batch(jobs[:2], n_out, stream=s1)
+        plan.search_batch(jobs[2:], n_out, stream=s2)
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        for j, r in zip(jobs, ref):
+            assert torch.equal(j.series, r.series)
+            a, na = j.result().candidates()
+            b, nb = r.candidates()
+            assert na == nb and (a == b).all()
+    for _ in range(6):
+        g = fdd.Graph(plan, jobs[1:3], n_out)
+        jobs[1].series.fill_(-1)
+        jobs[2].series.fill_(-1)
+        g.launch()
+        torch.cuda.synchronize()
+        g.close()
+        for j, r in zip(jobs[1:3], ref[1:3]):
+            assert torch.equal(j.series, r.series)
+
+
 def test_batch_autotune_keeps_parity(fdd):
     import torch
     x, f, ranges, sb, n_in, n_out = batch_case(5, 0)
