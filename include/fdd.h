@@ -346,8 +346,10 @@ int fdd_batch_prepare(fdd_plan* plan, int64_t n_out, int32_t variant);
  * block, time tile) -- one launch for the native-rate ranges and one for the
  * downsampled ranges -- and one boxcar/threshold launch.  Results per job are
  * identical to fdd_search on that job alone.  Prepares on first use of an
- * n_out (not allowed while the stream is capturing).  Batched searches of
- * one plan must not overlap on the GPU (they share the work counter).
+ * n_out (not allowed while the stream is capturing).  In the persistent
+ * modes, batched searches of one plan must not overlap on the GPU (they share
+ * the plan's work counters); SB-factored batches of one plan may run at the
+ * same time on different streams (the serving runtime overlaps them).
  * In SB-factored mode the part / combine launches of the range with the most
  * trial-samples run on one library-owned side stream and those of the other
  * ranges on a second (a pair per caller stream, created on first use and

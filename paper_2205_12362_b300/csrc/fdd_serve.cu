@@ -249,8 +249,12 @@ int schedule(fdd_server* s, double t) {
         const int n = std::min<int>({static_cast<int>(free_slots.size()), static_cast<int>(s->queue.size()),
                                      s->sb_plans.empty() ? FDD_MAX_BATCH_JOBS : 1});
         ServeBatch batch;
-        batch.stream = s->next_stream;
-        s->next_stream = (s->next_stream + 1) % kComputeStreams;
+        // SB-factored batches (and the plain path) are independent of one another and rotate over the
+        // compute streams; the persistent modes share the plan's work counters, so their batches stay
+        // in order on one stream
+        const bool shared_counters = s->sb_plans.empty() && !s->plan->batch.sbf;
+        batch.stream = shared_counters ? 0 : s->next_stream;
+        if (!shared_counters) s->next_stream = (s->next_stream + 1) % kComputeStreams;
         cudaStream_t cs = s->compute[batch.stream];
         std::vector<fdd_job> jobs(n);
         for (int k = 0; k < n; k++) {
